@@ -1,0 +1,180 @@
+"""Seeded synthetic inputs shared by the FP64 oracle and the CUDA library.
+
+This module holds none of the multigrid method's arithmetic. It makes gauge
+fields, sources and gauge transformations from counter-based random numbers
+(Philox4x32-10, Salmon et al., SC'11) so that the oracle and the GPU path can be
+fed bit-identical inputs. The heavy loops live in ``gen.c`` (plain C, OpenMP),
+compiled in-tree with gcc on first use or by ``__graft_entry__.build()``.
+
+Input recipe (the paper's gauge ensembles: quenched U(1), Wilson plaquette
+action, periodic, beta = 6 and 10):
+  * links: Metropolis from a cold start, ``sweeps`` sweeps, ``hits`` hits per link
+    with proposals uniform in [-step, step] rad;
+  * sources: complex Gaussian, Re and Im independent N(0, 1) (Box-Muller);
+  * gauge transforms: uniform U(1) phases.
+
+Layouts: site x = x0 + L0*x1; links U[x, mu] complex128; spinors psi[x, s]
+complex128 (2d: two spin components).
+"""
+from __future__ import annotations
+
+import ctypes
+import hashlib
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gen.c")
+_LIB = os.path.join(_HERE, "libmginputs.so")
+_lock = threading.Lock()
+_lib = None
+
+# Root seed of every workload; each workload adds its own id (see DESIGN).
+ROOT_SEED = 20070704
+
+
+def build(force: bool = False) -> str:
+    """Compile gen.c into an in-tree shared library with gcc and return its path."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            u32p = ctypes.POINTER(ctypes.c_uint32)
+            dp = ctypes.POINTER(ctypes.c_double)
+            lib.philox4x32_10.argtypes = [u32p, u32p, u32p]
+            lib.gen_gaussian_complex.argtypes = [ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, dp]
+            lib.gen_uniform.argtypes = [ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, dp]
+            lib.metropolis_u1_2d.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_double, ctypes.c_uint64, dp, ctypes.POINTER(ctypes.c_int64)]
+            lib.links_from_angles.argtypes = [ctypes.c_int64, dp, dp]
+            lib.gen_u1_phases.argtypes = [ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, dp]
+            lib.gen_num_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def philox4x32_10(ctr, key):
+    """One Philox4x32-10 block: four uint32 counter words, two uint32 key words."""
+    lib = _load()
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    lib.philox4x32_10(c.ctypes.data_as(u32p), k.ctypes.data_as(u32p), out.ctypes.data_as(u32p))
+    return out
+
+
+def gaussian_complex(n: int, seed: int, tag: int) -> np.ndarray:
+    """n complex128 Gaussians (Re, Im ~ N(0,1)), Philox counter (i, tag), key seed."""
+    out = np.empty(2 * n, dtype=np.float64)
+    _load().gen_gaussian_complex(n, seed, tag, _dp(out))
+    return out.view(np.complex128)
+
+
+def uniform(n: int, seed: int, tag: int) -> np.ndarray:
+    out = np.empty(n, dtype=np.float64)
+    _load().gen_uniform(n, seed, tag, _dp(out))
+    return out
+
+
+def num_threads() -> int:
+    return int(_load().gen_num_threads())
+
+
+def metropolis_u1_2d(L0: int, L1: int, beta: float, sweeps: int, seed: int, hits: int = 10, step: float = 0.5,
+                     theta0: np.ndarray | None = None):
+    """Quenched U(1) link angles theta[x, mu] after ``sweeps`` Metropolis sweeps.
+
+    Starts cold (theta = 0) unless ``theta0`` is given. Returns (theta, acceptance).
+    """
+    if L0 % 2 or L1 % 2:
+        raise ValueError("Metropolis checkerboard needs even extents")
+    theta = np.zeros((L0 * L1, 2), dtype=np.float64) if theta0 is None else np.array(theta0, dtype=np.float64)
+    acc = ctypes.c_int64(0)
+    _load().metropolis_u1_2d(L0, L1, float(beta), int(sweeps), int(hits), float(step), int(seed), _dp(theta),
+                             ctypes.byref(acc))
+    tot = max(1, sweeps * hits * 2 * L0 * L1)
+    return theta, acc.value / tot
+
+
+def links_from_angles(theta: np.ndarray) -> np.ndarray:
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    out = np.empty(2 * th.size, dtype=np.float64)
+    _load().links_from_angles(th.size, _dp(th), _dp(out))
+    return out.view(np.complex128).reshape(th.shape)
+
+
+def u1_phases(nsites: int, seed: int, tag: int) -> np.ndarray:
+    out = np.empty(2 * nsites, dtype=np.float64)
+    _load().gen_u1_phases(nsites, seed, tag, _dp(out))
+    return out.view(np.complex128)
+
+
+def plaquette_angles(theta: np.ndarray, L0: int, L1: int) -> np.ndarray:
+    """theta_p(x) = t0(x) + t1(x+0) - t0(x+1) - t1(x) wrapped to (-pi, pi], shape (L1, L0)."""
+    t = theta.reshape(L1, L0, 2)
+    tp = t[:, :, 0] + np.roll(t[:, :, 1], -1, axis=1) - np.roll(t[:, :, 0], -1, axis=0) - t[:, :, 1]
+    w = np.remainder(tp + np.pi, 2 * np.pi) - np.pi
+    w[w <= -np.pi] += 2 * np.pi
+    return w
+
+
+def topological_charge(theta: np.ndarray, L0: int, L1: int) -> float:
+    """Q = (1/2pi) sum_x arg U_p(x), arg in (-pi, pi]; an integer up to rounding on a torus."""
+    return float(plaquette_angles(theta, L0, L1).sum() / (2 * np.pi))
+
+
+def field_digest(a: np.ndarray) -> str:
+    """Short hash of an array's bytes (identifies a generated gauge field across hosts)."""
+    return hashlib.sha256(np.ascontiguousarray(a).tobytes()).hexdigest()[:16]
+
+
+# ---------------------------------------------------------------------------
+# Workload recipes (seeds and sizes of the synthetic ensembles)
+# ---------------------------------------------------------------------------
+
+def workload_seed(workload_id: int, L: int, beta: float) -> int:
+    """Seed of one gauge ensemble member: root seed + workload id, with L and beta mixed in."""
+    return (ROOT_SEED + workload_id) * 1000003 + L * 101 + int(round(beta * 1000))
+
+
+def schwinger_links(L: int, beta: float, sweeps: int = 2000, workload_id: int = 0, hits: int = 10,
+                    step: float = 0.5):
+    """Gauge field U[x, mu] (complex128, (L*L, 2)) of the 2d U(1) ensemble recipe plus its angles."""
+    seed = workload_seed(workload_id, L, beta)
+    theta, acc = metropolis_u1_2d(L, L, beta, sweeps, seed, hits=hits, step=step)
+    return links_from_angles(theta), theta, acc
+
+
+def gaussian_source(L0: int, L1: int, seed: int, index: int = 0, ns: int = 2) -> np.ndarray:
+    """Gaussian complex source chi[x, s] for right-hand side ``index``."""
+    return gaussian_complex(L0 * L1 * ns, seed, 0x5352430000 + index).reshape(L0 * L1, ns)
+
+
+def free_links(L0: int, L1: int, phi=(0.0, 0.0)) -> np.ndarray:
+    """Constant U(1) links exp(i phi_mu) (phi = 0 is the free field)."""
+    U = np.empty((L0 * L1, 2), dtype=np.complex128)
+    U[:, 0] = np.exp(1j * phi[0])
+    U[:, 1] = np.exp(1j * phi[1])
+    return U
+
+
+def hot_links(L0: int, L1: int, seed: int) -> np.ndarray:
+    """Uniformly random U(1) links (infinite-temperature field)."""
+    return u1_phases(L0 * L1 * 2, seed, 0x484F54).reshape(L0 * L1, 2)

@@ -1,0 +1,56 @@
+"""Writes mcrit.json: the critical mass m_c of each synthetic gauge field used by the
+workloads, computed by the FP64 oracle (oracle.spectrum: m_c = -min Re lambda(D(0))).
+
+Run from the repository root:  python tests/golden/make_mcrit.py [--only L,beta]
+Each entry records the generator recipe, the digest of the link angles (identical on
+every host: the chain depends on libm only through accept decisions) and m_c.
+"""
+import argparse
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import inputs  # noqa: E402
+from oracle import spectrum  # noqa: E402
+from oracle.lattice import Lattice  # noqa: E402
+
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "mcrit.json")
+
+# (workload id, L, beta): 64^2 beta=6 (the small two-level case) and the 256^2 points
+# of the three-level sweep over beta in {3, 6, 10}
+FIELDS = [(0, 64, 6.0), (1, 256, 3.0), (1, 256, 6.0), (1, 256, 10.0)]
+
+
+def key(wid, L, beta):
+    return f"w{wid}_L{L}_b{beta:g}"
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--only", default=None)
+    args = ap.parse_args()
+    table = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    for wid, L, beta in FIELDS:
+        if args.only and args.only != f"{L},{beta:g}":
+            continue
+        t0 = time.time()
+        U, theta, acc = inputs.schwinger_links(L, beta, sweeps=2000, workload_id=wid)
+        t1 = time.time()
+        lat = Lattice((L, L))
+        mc = spectrum.critical_mass(U, lat)
+        t2 = time.time()
+        table[key(wid, L, beta)] = dict(workload_id=wid, L=L, beta=beta, sweeps=2000, hits=10, step=0.5,
+                                        seed=inputs.workload_seed(wid, L, beta), acceptance=acc,
+                                        Q=round(inputs.topological_charge(theta, L, L)),
+                                        theta_digest=inputs.field_digest(theta), m_crit=mc,
+                                        gen_seconds=round(t1 - t0, 1), scan_seconds=round(t2 - t1, 1))
+        print(key(wid, L, beta), table[key(wid, L, beta)], flush=True)
+        json.dump(table, open(OUT, "w"), indent=1, sort_keys=True)
+
+
+if __name__ == "__main__":
+    main()
