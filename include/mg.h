@@ -1,0 +1,194 @@
+/*
+ * mg.h -- C ABI of the GB300 (sm_103a) adaptive multigrid solver for the
+ * Wilson-Dirac equation D(U) psi = chi (Brannick, Brower, Clark, Osborn, Rebbi,
+ * "Adaptive Multigrid Algorithm for Lattice QCD", arXiv:0707.4018).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Lattice: d = 2, extents dims[0] = L0, dims[1] = L1, periodic in every
+ *    direction; site index x = x0 + L0 * x1 (x0 fastest).
+ *  - Gauge field U: complex128 (interleaved re, im) U[x][mu], mu = 0, 1; U_x^mu
+ *    is the U(1) link from x to x + mu-hat (Nc = 1).
+ *  - Fine spinor: complex128 psi[x][s], s = 0, 1 (two spin components).
+ *  - Wilson operator (paper, definition following Eq. 1), with gamma_1 = sigma_1,
+ *    gamma_2 = sigma_2 and the diagonal read as (d + m):
+ *        (D psi)_x = (d + m) psi_x - 1/2 sum_mu [ (1 - gamma_mu) U_x^mu psi_{x+mu}
+ *                                              + (1 + gamma_mu) U_{x-mu}^mu* psi_{x-mu} ]
+ *  - Levels are numbered 0 (finest) .. levels-1 (coarsest). Level l+1 is the
+ *    blocking of level l into blocks of block[l][0] x block[l][1] sites (the
+ *    paper's geometric blocks S_j); coarse site j = block index
+ *        j = (x0 / B0) + (L0 / B0) * (x1 / B1),
+ *    in-block position s = (x0 % B0) + B0 * (x1 % B1).
+ *  - A level-l vector is complex128 v[site][a], a < n_int(l), where n_int(0) = 2
+ *    and n_int(l) = Nv[l-1] (the paper's intrinsic index s on coarse sites).
+ *  - Coarse operator of level l >= 1 (paper, Eq. Galerkin, with A = D):
+ *        y_j = sum_dir Y[j][dir] x_{j + offset(dir)},
+ *    dir 0 = self, dir 1 = +0, 2 = -0, 3 = +1, 4 = -1 (source j + offset);
+ *    exported row-major: Y[j][dir][row][col], complex128.
+ *  - Near-null vectors / prolongator of level l: Nv[l] level-l vectors,
+ *    exported as v[k][site][a]. The prolongator columns are the vectors cut to
+ *    each block and block-orthonormalised (paper, Eq. P1 and the adaptive step).
+ *
+ * Memory and streams
+ * ------------------
+ *  All field pointers are DEVICE pointers on the current CUDA device unless a
+ *  call says otherwise; the caller owns them. mg_setup copies U into library
+ *  storage, so the caller may free U afterwards. A context owns its device
+ *  workspace (allocated in mg_setup, freed in mg_destroy). Every call runs on
+ *  the context's stream and returns after synchronising it.
+ *
+ * Errors
+ * ------
+ *  Every int-returning call returns MG_OK (0) or an mg_status code; a message
+ *  is then available from mg_last_error() (thread-local). No C++ exception
+ *  crosses this interface. On MG_ERR_NOT_CONVERGED, psi holds the last iterate
+ *  and the stats are filled in.
+ */
+#ifndef MG_GB300_H
+#define MG_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MG_MAX_LEVELS 4
+
+typedef enum {
+  MG_OK = 0,
+  MG_ERR_INVALID_ARG = 1,   /* bad geometry, blocking, parameters or null pointer */
+  MG_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed */
+  MG_ERR_OOM = 3,           /* device allocation failed */
+  MG_ERR_NOT_CONVERGED = 4, /* max_iter reached before the tolerance */
+  MG_ERR_NAN = 5,           /* a NaN/Inf or breakdown appeared in a reduction */
+  MG_ERR_UNSUPPORTED = 6,   /* a valid request this build does not implement */
+  MG_ERR_STATE = 7          /* the hierarchy is incomplete for the request */
+} mg_status;
+
+typedef enum {
+  MG_FP64 = 0, /* every level in FP64 */
+  MG_FP32 = 1  /* FP64 outer flexible GCR; V-cycle (smoother, transfer, coarse ops) in FP32 */
+} mg_precision;
+
+typedef struct {
+  int d;       /* number of dimensions; 2 */
+  int dims[4]; /* lattice extents (dims[0] = L0, dims[1] = L1) */
+  int Nc;      /* colours; 1 (U(1)) */
+} mg_geom;
+
+typedef struct {
+  int levels;                       /* number of levels, 2..MG_MAX_LEVELS */
+  int block[MG_MAX_LEVELS - 1][4];  /* block extents from level l to l+1 */
+  int Nv[MG_MAX_LEVELS - 1];        /* near-null vectors kept on level l */
+  int nu_pre, nu_post;              /* MR smoothing iterations before / after the coarse correction */
+  double omega;                     /* MR under-relaxation (paper: 0.8) */
+  int n_pass;                       /* adaptive setup passes (1 = relaxation only) */
+  int nu_setup;                     /* MR iterations of the null-space relaxation (paper: Eq. relax) */
+  int gcr_restart;                  /* outer flexible GCR restart length */
+  int max_iter;                     /* outer iteration limit */
+  int coarsest_lu_max;              /* coarsest dimension up to which a dense LU is used */
+  double coarsest_tol;              /* relative residual of the iterative coarsest solve */
+  int coarsest_restart;             /* restart length of the iterative coarsest solve */
+  int coarsest_max_iter;            /* iteration limit of the iterative coarsest solve */
+  int precision;                    /* mg_precision */
+  uint64_t seed;                    /* Philox4x32-10 key of the setup's random vectors */
+} mg_params;
+
+typedef struct {
+  int iters;                         /* outer iterations */
+  int converged;                     /* 1 if the true residual met the tolerance */
+  double true_rel_residual;          /* |chi - D psi| / |chi|, recomputed in FP64 */
+  long long level_apps[MG_MAX_LEVELS]; /* operator applications per level (level 0: fine D) */
+  long long coarsest_iters;          /* iterations of the iterative coarsest solve */
+  double ms;                         /* wall time of the call, stream-synchronised */
+} mg_stats;
+
+typedef struct mg_ctx mg_ctx;
+
+/* Defaults: 2 levels, 4x4 blocks, Nv = 8, MR 4 + 4 with omega = 0.8, 5 passes,
+ * nu_setup = 8, GCR(16), max_iter 500, coarsest LU up to 2048, coarsest GCR
+ * tol 1e-12 / restart 64 / 20000 iterations, FP64, seed 20070704. */
+void mg_default_params(mg_params *p);
+
+/*
+ * Adaptive setup (paper: Eq. relax, Eq. P1, the adaptive passes and the
+ * recursion to further levels; Eq. Galerkin for every coarse operator).
+ *   ctx   out: new context (NULL on error)
+ *   g     geometry (d = 2, Nc = 1 supported)
+ *   U     device complex128 U[x][mu]; read during the call only
+ *   m     mass (diagonal d + m)
+ *   p     parameters (copied)
+ *   stream  cudaStream_t to run on (NULL: the legacy default stream)
+ * Random vectors: level-l vector k, complex dof i, is Philox4x32-10 with key
+ * (seed lo, seed hi) and counter (i lo, i hi, k, l), followed by Box-Muller.
+ * Errors: INVALID_ARG (extents not divisible by blocks, odd sizes, Nv larger
+ * than a block's dofs, levels out of range), OOM, CUDA.
+ */
+int mg_setup(mg_ctx **ctx, const mg_geom *g, const void *U, double m, const mg_params *p, void *stream);
+
+/* Solve D psi = chi to relative true residual tol by flexible GCR preconditioned
+ * with one V-cycle per iteration (FP64 outer loop, true residual at restarts).
+ * chi, psi: device complex128 [x][s]; psi is overwritten (initial guess 0).
+ * st may be NULL. Returns NOT_CONVERGED (psi = last iterate) after max_iter. */
+int mg_solve(mg_ctx *ctx, const void *chi, void *psi, double tol, mg_stats *st);
+
+/* Reuse the near-null vectors for another mass (paper: setup at the lightest
+ * mass only, reused for heavier ones): rebuilds every Galerkin operator with
+ * the kept prolongators and re-prepares the coarsest solve. */
+int mg_update_mass(mg_ctx *ctx, double m);
+
+/* Frees every device buffer of the context. NULL is a no-op. */
+void mg_destroy(mg_ctx *ctx);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *mg_last_error(void);
+
+/* ---- step-level entry points (one step of the hot path each) ------------- */
+
+/* Fine Wilson operator out = D(U) in without a context (paper, definition of D).
+ * precision MG_FP64: U, in, out complex128; MG_FP32: complex64. in and out must
+ * not alias. stream: cudaStream_t. Asynchronous on the stream (no sync). */
+int mg_dslash(const mg_geom *g, const void *U, double m, const void *in, void *out, int precision, void *stream);
+
+/* Apply the level-l operator (l = 0: D; l >= 1: the Galerkin stencil) in FP64. */
+int mg_level_apply(mg_ctx *ctx, int level, const void *in, void *out);
+
+/* Restriction r_c = P_l^dagger r (level l -> l+1) and prolongation f = P_l e_c,
+ * FP64, level vectors in the canonical layouts above. */
+int mg_restrict(mg_ctx *ctx, int level, const void *fine, void *coarse);
+int mg_prolong(mg_ctx *ctx, int level, const void *coarse, void *fine);
+
+/* One V-cycle x = V b on the finest level in the context's precision
+ * (paper: the five V-cycle steps). b, x: device complex128 [x][s]. */
+int mg_vcycle(mg_ctx *ctx, const void *b, void *x);
+
+/* nu MR iterations x = R b from x = 0 on level l (FP64), omega from the params. */
+int mg_smooth(mg_ctx *ctx, int level, const void *b, void *x, int nu);
+
+/* Replace the near-null vectors of level l by Nv[l] caller vectors (device,
+ * complex128 [k][site][a]), then block-orthonormalise them into P_l and
+ * rebuild the Galerkin operator of level l+1 (and the coarsest solve if l+1 is
+ * the coarsest). Levels below l+1 become stale until rebuilt (MG_ERR_STATE
+ * from calls that need them). */
+int mg_build_level(mg_ctx *ctx, int level, const void *vectors);
+
+/* Export level data (device destination buffers, complex128):
+ *   mg_get_null_vectors: the Nv[l] near-null vectors of level l (before orthonormalisation)
+ *   mg_get_prolongator:  the block-orthonormal columns of P_l as Nv[l] level vectors
+ *   mg_get_coarse_op:    Y of level l >= 1, [j][dir][row][col]
+ * and sizes: n_sites(l), n_int(l). */
+int mg_get_null_vectors(mg_ctx *ctx, int level, void *out);
+int mg_get_prolongator(mg_ctx *ctx, int level, void *out);
+int mg_get_coarse_op(mg_ctx *ctx, int level, void *out);
+int mg_level_size(mg_ctx *ctx, int level, long long *n_sites, int *n_int);
+
+/* Number of kernels this library has launched since the process started. */
+long long mg_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MG_GB300_H */

@@ -153,3 +153,23 @@ def transform_spinor(psi, omega, lat: Lattice, Nc: int = 1):
     shape = np.shape(psi)
     p = _as_spinor(psi, lat, Nc)
     return np.einsum("xab,xsb->xsa", om, p).reshape(shape)
+
+
+def apply_D_at(U, psi, m: float, lat: Lattice, sites):
+    """(D psi)_x at the given sites only, from the same definition (for sampled checks
+    of fields too large to apply D to as a whole)."""
+    U = _as_links(U, lat)
+    Nc = U.shape[-1]
+    p = _as_spinor(psi, lat, Nc)
+    sites = np.asarray(sites, dtype=np.int64)
+    g, _ = gammas(lat.d)
+    one = np.eye(n_spin(lat.d), dtype=np.complex128)
+    out = diag_value(lat, m) * p[sites]
+    for mu in range(lat.d):
+        fwd = lat.neighbour(sites, mu, +1)
+        bwd = lat.neighbour(sites, mu, -1)
+        t = np.einsum("xab,xsb->xsa", U[sites, mu], p[fwd])
+        out = out - 0.5 * np.einsum("st,xta->xsa", one - g[mu], t)
+        t = np.einsum("xba,xsb->xsa", U[bwd, mu].conj(), p[bwd])
+        out = out - 0.5 * np.einsum("st,xta->xsa", one + g[mu], t)
+    return out.reshape((len(sites),) + np.shape(psi)[1:])

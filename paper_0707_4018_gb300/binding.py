@@ -1,0 +1,282 @@
+"""Thin ctypes binding of the C ABI in ``include/mg.h`` (argument marshalling only).
+
+Every step of the solver runs in the CUDA library ``libmg_gb300.so``; this
+module only converts torch tensors (device memory, streams) into pointers and
+sizes and turns status codes into exceptions. There is no fallback: if the
+library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+MG_MAX_LEVELS = 4
+MG_FP64, MG_FP32 = 0, 1
+
+STATUS = {0: "MG_OK", 1: "MG_ERR_INVALID_ARG", 2: "MG_ERR_CUDA", 3: "MG_ERR_OOM", 4: "MG_ERR_NOT_CONVERGED",
+          5: "MG_ERR_NAN", 6: "MG_ERR_UNSUPPORTED", 7: "MG_ERR_STATE"}
+
+
+class MGError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class mg_geom(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("dims", ctypes.c_int * 4), ("Nc", ctypes.c_int)]
+
+
+class mg_params(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("block", (ctypes.c_int * 4) * (MG_MAX_LEVELS - 1)),
+                ("Nv", ctypes.c_int * (MG_MAX_LEVELS - 1)), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
+                ("omega", ctypes.c_double), ("n_pass", ctypes.c_int), ("nu_setup", ctypes.c_int),
+                ("gcr_restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("coarsest_lu_max", ctypes.c_int),
+                ("coarsest_tol", ctypes.c_double), ("coarsest_restart", ctypes.c_int),
+                ("coarsest_max_iter", ctypes.c_int), ("precision", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+class mg_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("true_rel_residual", ctypes.c_double),
+                ("level_apps", ctypes.c_longlong * MG_MAX_LEVELS), ("coarsest_iters", ctypes.c_longlong),
+                ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return dict(iters=self.iters, converged=bool(self.converged), true_rel_residual=self.true_rel_residual,
+                    level_apps=list(self.level_apps), coarsest_iters=self.coarsest_iters, ms=self.ms)
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libmg_gb300.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError("CUDA library libmg_gb300.so is missing")
+    lib = ctypes.CDLL(path)
+    P, I, D, VP = ctypes.POINTER, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    ctxp = ctypes.c_void_p
+    sig = {
+        "mg_default_params": (None, [P(mg_params)]),
+        "mg_setup": (I, [P(ctxp), P(mg_geom), VP, D, P(mg_params), VP]),
+        "mg_solve": (I, [ctxp, VP, VP, D, P(mg_stats)]),
+        "mg_update_mass": (I, [ctxp, D]),
+        "mg_destroy": (None, [ctxp]),
+        "mg_last_error": (ctypes.c_char_p, []),
+        "mg_dslash": (I, [P(mg_geom), VP, D, VP, VP, I, VP]),
+        "mg_level_apply": (I, [ctxp, I, VP, VP]),
+        "mg_restrict": (I, [ctxp, I, VP, VP]),
+        "mg_prolong": (I, [ctxp, I, VP, VP]),
+        "mg_vcycle": (I, [ctxp, VP, VP]),
+        "mg_smooth": (I, [ctxp, I, VP, VP, I]),
+        "mg_build_level": (I, [ctxp, I, VP]),
+        "mg_get_null_vectors": (I, [ctxp, I, VP]),
+        "mg_get_prolongator": (I, [ctxp, I, VP]),
+        "mg_get_coarse_op": (I, [ctxp, I, VP]),
+        "mg_level_size": (I, [ctxp, I, P(ctypes.c_longlong), P(I)]),
+        "mg_kernel_launches": (ctypes.c_longlong, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names of the C ABI entry points this binding expects."""
+    return ["mg_default_params", "mg_setup", "mg_solve", "mg_update_mass", "mg_destroy", "mg_last_error",
+            "mg_dslash", "mg_level_apply", "mg_restrict", "mg_prolong", "mg_vcycle", "mg_smooth", "mg_build_level",
+            "mg_get_null_vectors", "mg_get_prolongator", "mg_get_coarse_op", "mg_level_size", "mg_kernel_launches"]
+
+
+def _check(code: int):
+    if code != 0:
+        raise MGError(code, load().mg_last_error().decode())
+
+
+def _ptr(t: torch.Tensor, dtype=None, numel=None) -> ctypes.c_void_p:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_geom(dims, Nc: int = 1) -> mg_geom:
+    g = mg_geom()
+    g.d = len(dims)
+    for i, L in enumerate(dims):
+        g.dims[i] = int(L)
+    g.Nc = Nc
+    return g
+
+
+def mg_default_params(**overrides) -> mg_params:
+    """Library defaults, then ``overrides`` (blocks / Nv may be given as lists per level)."""
+    p = mg_params()
+    load().mg_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k == "blocks":
+            for l, blk in enumerate(v):
+                for i, b in enumerate(blk):
+                    p.block[l][i] = int(b)
+        elif k == "Nv":
+            for l, n in enumerate(v):
+                p.Nv[l] = int(n)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def mg_dslash(U: torch.Tensor, inp: torch.Tensor, out: torch.Tensor, m: float, dims, precision: int = MG_FP64,
+              stream=None):
+    """out = D(U) inp on the fine lattice (asynchronous on the stream)."""
+    dt = torch.complex128 if precision == MG_FP64 else torch.complex64
+    V = int(dims[0]) * int(dims[1])
+    g = make_geom(dims)
+    _check(load().mg_dslash(ctypes.byref(g), _ptr(U, dt, 2 * V), float(m), _ptr(inp, dt, 2 * V),
+                            _ptr(out, dt, 2 * V), precision, _stream(stream)))
+
+
+def mg_kernel_launches() -> int:
+    return int(load().mg_kernel_launches())
+
+
+class Context:
+    """A set-up multigrid hierarchy (wraps mg_ctx*). Use ``Context.setup``."""
+
+    def __init__(self, handle, dims, params, stream):
+        self._h = handle
+        self.dims = tuple(dims)
+        self.params = params
+        self.stream = stream
+        self.volume = int(dims[0]) * int(dims[1])
+
+    @classmethod
+    def setup(cls, U: torch.Tensor, m: float, dims, params: mg_params | None = None, stream=None) -> "Context":
+        """mg_setup: adaptive setup of the hierarchy for D(U) with mass m."""
+        lib = load()
+        p = params if params is not None else mg_default_params()
+        g = make_geom(dims)
+        V = int(dims[0]) * int(dims[1])
+        h = ctypes.c_void_p()
+        s = _stream(stream)
+        _check(lib.mg_setup(ctypes.byref(h), ctypes.byref(g), _ptr(U, torch.complex128, 2 * V), float(m),
+                            ctypes.byref(p), s))
+        return cls(h, dims, p, s)
+
+    def close(self):
+        if self._h:
+            load().mg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _need(self):
+        if not self._h:
+            raise RuntimeError("context is closed")
+        return self._h
+
+    def level_size(self, level: int):
+        n = ctypes.c_longlong()
+        k = ctypes.c_int()
+        _check(load().mg_level_size(self._need(), level, ctypes.byref(n), ctypes.byref(k)))
+        return int(n.value), int(k.value)
+
+    def _numel(self, level: int) -> int:
+        n, k = self.level_size(level)
+        return n * k
+
+    def solve(self, chi: torch.Tensor, psi: torch.Tensor, tol: float, raise_on_fail: bool = True) -> dict:
+        """mg_solve: psi = D^{-1} chi to relative true residual tol; returns the stats."""
+        st = mg_stats()
+        n = 2 * self.volume
+        code = load().mg_solve(self._need(), _ptr(chi, torch.complex128, n), _ptr(psi, torch.complex128, n),
+                               float(tol), ctypes.byref(st))
+        if code != 0 and (raise_on_fail or code != 4):
+            _check(code)
+        return st.as_dict()
+
+    def update_mass(self, m: float):
+        _check(load().mg_update_mass(self._need(), float(m)))
+
+    def level_apply(self, level: int, inp: torch.Tensor, out: torch.Tensor):
+        n = self._numel(level)
+        _check(load().mg_level_apply(self._need(), level, _ptr(inp, torch.complex128, n),
+                                     _ptr(out, torch.complex128, n)))
+
+    def restrict(self, level: int, fine: torch.Tensor, coarse: torch.Tensor):
+        _check(load().mg_restrict(self._need(), level, _ptr(fine, torch.complex128, self._numel(level)),
+                                  _ptr(coarse, torch.complex128, self._numel(level + 1))))
+
+    def prolong(self, level: int, coarse: torch.Tensor, fine: torch.Tensor):
+        _check(load().mg_prolong(self._need(), level, _ptr(coarse, torch.complex128, self._numel(level + 1)),
+                                 _ptr(fine, torch.complex128, self._numel(level))))
+
+    def vcycle(self, b: torch.Tensor, x: torch.Tensor):
+        n = self._numel(0)
+        _check(load().mg_vcycle(self._need(), _ptr(b, torch.complex128, n), _ptr(x, torch.complex128, n)))
+
+    def smooth(self, level: int, b: torch.Tensor, x: torch.Tensor, nu: int):
+        n = self._numel(level)
+        _check(load().mg_smooth(self._need(), level, _ptr(b, torch.complex128, n), _ptr(x, torch.complex128, n),
+                                int(nu)))
+
+    def build_level(self, level: int, vectors: torch.Tensor):
+        nv = self.params.Nv[level]
+        _check(load().mg_build_level(self._need(), level, _ptr(vectors, torch.complex128, nv * self._numel(level))))
+
+    def null_vectors(self, level: int) -> torch.Tensor:
+        nv = self.params.Nv[level]
+        n, k = self.level_size(level)
+        out = torch.empty((nv, n, k), dtype=torch.complex128, device="cuda")
+        _check(load().mg_get_null_vectors(self._need(), level, _ptr(out)))
+        return out
+
+    def prolongator(self, level: int) -> torch.Tensor:
+        nv = self.params.Nv[level]
+        n, k = self.level_size(level)
+        out = torch.empty((nv, n, k), dtype=torch.complex128, device="cuda")
+        _check(load().mg_get_prolongator(self._need(), level, _ptr(out)))
+        return out
+
+    def coarse_op(self, level: int) -> torch.Tensor:
+        n, k = self.level_size(level)
+        out = torch.empty((n, 5, k, k), dtype=torch.complex128, device="cuda")
+        _check(load().mg_get_coarse_op(self._need(), level, _ptr(out)))
+        return out

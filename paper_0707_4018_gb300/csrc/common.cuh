@@ -1,0 +1,241 @@
+// Internal definitions shared by the CUDA translation units of the multigrid
+// library: complex arithmetic on interleaved (re, im) pairs, error handling,
+// device buffers, lattice geometry and deterministic block reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <utility>
+
+#include "../../include/mg.h"
+
+namespace mg {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+struct Error {
+  int code;
+  std::string msg;
+};
+
+[[noreturn]] inline void fail(int code, const std::string &msg) { throw Error{code, msg}; }
+
+#define MG_CUDA(call)                                                                            \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) ::mg::fail(MG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+extern std::atomic<long long> g_launches;
+
+// Checks a kernel launch and counts it.
+#define MG_LAUNCHED()                                                                           \
+  do {                                                                                          \
+    ::mg::g_launches.fetch_add(1, std::memory_order_relaxed);                                   \
+    cudaError_t e_ = cudaGetLastError();                                                        \
+    if (e_ != cudaSuccess) ::mg::fail(MG_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// complex numbers (interleaved, same layout as complex128 / complex64)
+// ---------------------------------------------------------------------------
+template <typename R>
+struct alignas(2 * sizeof(R)) Cx {
+  R re, im;
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ Cx<R> mk(R re, R im) {
+  Cx<R> c;
+  c.re = re;
+  c.im = im;
+  return c;
+}
+template <typename R>
+__host__ __device__ __forceinline__ Cx<R> operator+(Cx<R> a, Cx<R> b) { return mk(a.re + b.re, a.im + b.im); }
+template <typename R>
+__host__ __device__ __forceinline__ Cx<R> operator-(Cx<R> a, Cx<R> b) { return mk(a.re - b.re, a.im - b.im); }
+template <typename R>
+__host__ __device__ __forceinline__ Cx<R> operator*(Cx<R> a, Cx<R> b) {
+  return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename R>
+__host__ __device__ __forceinline__ Cx<R> operator*(R s, Cx<R> a) { return mk(s * a.re, s * a.im); }
+// conj(a) * b
+template <typename R>
+__host__ __device__ __forceinline__ Cx<R> cmul_conj(Cx<R> a, Cx<R> b) {
+  return mk(a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re);
+}
+// i * a
+template <typename R>
+__host__ __device__ __forceinline__ Cx<R> times_i(Cx<R> a) { return mk(-a.im, a.re); }
+// acc += a * b
+template <typename R>
+__host__ __device__ __forceinline__ void cmac(Cx<R> &acc, Cx<R> a, Cx<R> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+}
+// acc += conj(a) * b
+template <typename R>
+__host__ __device__ __forceinline__ void cmac_conj(Cx<R> &acc, Cx<R> a, Cx<R> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+}
+template <typename R>
+__host__ __device__ __forceinline__ R norm2(Cx<R> a) { return a.re * a.re + a.im * a.im; }
+
+template <typename To, typename From>
+__host__ __device__ __forceinline__ Cx<To> cvt(Cx<From> a) { return mk((To)a.re, (To)a.im); }
+
+// ---------------------------------------------------------------------------
+// device buffers
+// ---------------------------------------------------------------------------
+template <typename T>
+struct DevBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  DevBuf(DevBuf &&o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DevBuf &operator=(DevBuf &&o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void alloc(size_t count) {
+    release();
+    if (count == 0) return;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      fail(MG_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes: " + cudaGetErrorString(e));
+    }
+    p = static_cast<T *>(q);
+    n = count;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// geometry of one 2d level and of a blocking between two levels
+// ---------------------------------------------------------------------------
+struct Geo2 {
+  int L0, L1;
+  long long nsites;
+};
+
+// fine level (extents L0 x L1, nint dofs per site) blocked by B0 x B1 into a
+// coarse level of extents nb0 x nb1; a block holds bvol = B0*B1 sites and
+// Nb = bvol * nint dofs ordered (in-block site s, internal dof a) -> s*nint + a.
+struct BlockGeo {
+  int L0, L1, B0, B1, nb0, nb1, bvol, nint, Nb;
+  long long nblocks;
+};
+
+__host__ __device__ __forceinline__ long long fine_site_of(const BlockGeo &g, long long b, int s) {
+  int cb0 = (int)(b % g.nb0), cb1 = (int)(b / g.nb0);
+  int x0 = cb0 * g.B0 + s % g.B0, x1 = cb1 * g.B1 + s / g.B0;
+  return (long long)x0 + (long long)g.L0 * x1;
+}
+
+// ---------------------------------------------------------------------------
+// deterministic reductions: fixed thread->element map and fixed trees
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum of NOUT doubles over a block of blockDim.x (multiple of 32, <= 1024)
+// threads; the result is valid in thread 0. Uses `sh` (>= 32*NOUT doubles).
+template <int NOUT>
+__device__ __forceinline__ void block_sum(double (&v)[NOUT], double *sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NOUT; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NOUT; ++k) sh[wid * NOUT + k] = v[k];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < NOUT; ++k) v[k] = (lane < nw) ? sh[lane * NOUT + k] : 0.0;
+#pragma unroll
+    for (int k = 0; k < NOUT; ++k) v[k] = warp_sum(v[k]);
+  }
+  __syncthreads();
+}
+
+// Grid reduction epilogue: every block writes its NOUT partials; the last
+// block to finish sums all partials in block order and stores them in out[].
+// `ticket` must be zero before the launch; the last block resets it.
+template <int NOUT>
+__device__ __forceinline__ void grid_finish(double (&v)[NOUT], double *partials, double *out, unsigned int *ticket,
+                                            double *sh) {
+  block_sum<NOUT>(v, sh);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NOUT; ++k) partials[blockIdx.x * NOUT + k] = v[k];
+    __threadfence();
+    unsigned int t = atomicAdd(ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double w[NOUT];
+#pragma unroll
+  for (int k = 0; k < NOUT; ++k) w[k] = 0.0;
+  // fixed order: thread t sums partials t, t + blockDim, ...; then the block tree
+  for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < NOUT; ++k) w[k] += ((volatile double *)partials)[b * NOUT + k];
+  }
+  block_sum<NOUT>(w, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NOUT; ++k) out[k] = w[k];
+    *ticket = 0u;
+  }
+}
+
+// Workspace for grid reductions (partials + ticket) owned by a context.
+struct ReduceWs {
+  double *partials;
+  unsigned int *ticket;
+  int max_blocks;
+};
+
+constexpr int kReduceThreads = 256;
+inline int reduce_blocks(long long n, int max_blocks) {
+  long long b = (n + kReduceThreads - 1) / kReduceThreads;
+  if (b < 1) b = 1;
+  if (b > max_blocks) b = max_blocks;
+  return (int)b;
+}
+
+inline unsigned int grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  return (unsigned int)b;
+}
+
+}  // namespace mg

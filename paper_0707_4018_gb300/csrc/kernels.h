@@ -1,0 +1,99 @@
+// Host-side launchers of the multigrid kernels (one launch each, asynchronous
+// on the given stream). R is double or float; complex fields are Cx<R>.
+#pragma once
+
+#include "common.cuh"
+
+namespace mg {
+
+// ---- fine Wilson operator (2d, U(1), gamma_1 = sigma_1, gamma_2 = sigma_2) ----
+// out = a * D in + c * b   (b may be null when c == 0); D has diagonal `diag` = d + m
+template <typename R>
+void launch_dslash(const Cx<R> *U, const Cx<R> *in, Cx<R> *out, Geo2 g, double diag, const Cx<R> *b, double a,
+                   double c, cudaStream_t s);
+
+// ---- coarse stencil operator, N x N blocks, internal layout Y[j][dir][col][row] ----
+// out = a * A in + c * b
+template <typename R>
+void launch_coarse_apply(const Cx<R> *Y, const Cx<R> *in, Cx<R> *out, Geo2 g, int N, const Cx<R> *b, double a,
+                         double c, cudaStream_t s);
+
+// ---- BLAS-1 ----
+template <typename R>
+void launch_zero(Cx<R> *x, long long n, cudaStream_t s);
+template <typename R>
+void launch_copy(const Cx<R> *x, Cx<R> *y, long long n, cudaStream_t s);
+template <typename To, typename From>
+void launch_convert(const Cx<From> *x, Cx<To> *y, long long n, cudaStream_t s);
+// y += alpha x, alpha read from device (complex at alpha_dev[0..1], times sign)
+template <typename R>
+void launch_axpy_dev(const double *alpha_dev, double sign, const Cx<R> *x, Cx<R> *y, long long n, cudaStream_t s);
+// y = x - y (in place on y)
+template <typename R>
+void launch_xmy(const Cx<R> *x, Cx<R> *y, long long n, cudaStream_t s);
+
+// ---- reductions (deterministic, results in FP64 on the device) ----
+// out[0..1] = <a, b> (complex), out[2] = |a|^2
+template <typename R>
+void launch_dot_norm(const Cx<R> *a, const Cx<R> *b, long long n, double *out, const ReduceWs &ws, cudaStream_t s);
+// out[0] = |a|^2
+template <typename R>
+void launch_norm2(const Cx<R> *a, long long n, double *out, const ReduceWs &ws, cudaStream_t s);
+// out[2j..2j+1] = <W_j, w> for j < k  (W: k vectors with stride n)
+template <typename R>
+void launch_multi_dot(const Cx<R> *W, int k, const Cx<R> *w, long long n, double *out, const ReduceWs &ws,
+                      cudaStream_t s);
+// w -= sum_j beta_j W_j, z -= sum_j beta_j Z_j (beta from device, complex pairs); Z/z may be null
+template <typename R>
+void launch_multi_axpy(const double *beta, int k, const Cx<R> *W, Cx<R> *w, const Cx<R> *Z, Cx<R> *z, long long n,
+                       cudaStream_t s);
+// w *= 1/sqrt(nrm2_dev[0]), z *= same (z may be null)
+template <typename R>
+void launch_normalize(const double *nrm2_dev, Cx<R> *w, Cx<R> *z, long long n, cudaStream_t s);
+// MR step: alpha = omega <Ar, r>/|Ar|^2 (sc[0..2]); x += alpha r; r -= alpha Ar
+template <typename R>
+void launch_mr_update(const double *sc, double omega, Cx<R> *x, Cx<R> *r, const Cx<R> *Ar, long long n,
+                      cudaStream_t s);
+// GCR step: alpha = <w, r> (sc[0..1]); x += alpha z; r -= alpha w; out_nrm[0] = |r|^2 (grid reduction)
+template <typename R>
+void launch_gcr_update(const double *sc, Cx<R> *x, const Cx<R> *z, Cx<R> *r, const Cx<R> *w, long long n,
+                       double *out_nrm, const ReduceWs &ws, cudaStream_t s);
+
+// ---- transfer between levels ----
+// coarse[b][k] = sum_i conj(V[b][k][i]) fine[site(b,s)][a]
+template <typename R>
+void launch_restrict(const Cx<R> *V, const Cx<R> *fine, Cx<R> *coarse, BlockGeo bg, int Nv, cudaStream_t s);
+// fine[site(b,s)][a] += sum_k V[b][k][i] coarse[b][k]
+template <typename R>
+void launch_prolong_add(const Cx<R> *V, const Cx<R> *coarse, Cx<R> *fine, BlockGeo bg, int Nv, cudaStream_t s);
+// fine[site(b,s)][a] = V[b][k][i] for every b (column k of P as a level vector), FP64
+void launch_prolongator_column(const Cx<double> *V, Cx<double> *fine, BlockGeo bg, int Nv, int k, cudaStream_t s);
+// block Gram-Schmidt (modified, twice, k order) of Nv level vectors into V[b][k][i]; FP64
+void launch_block_mgs(const Cx<double> *vecs, long long vec_stride, Cx<double> *V, BlockGeo bg, int Nv,
+                      double *min_norm_dev, cudaStream_t s);
+// Galerkin coarse operator Yc[b][dir][col][row] (internal layout) of P^dagger A P
+void launch_galerkin_wilson(const Cx<double> *U, double diag, const Cx<double> *V, Cx<double> *Yc, BlockGeo bg,
+                            int Nv, cudaStream_t s);
+void launch_galerkin_stencil(const Cx<double> *Y, const Cx<double> *V, Cx<double> *Yc, BlockGeo bg, int Nv,
+                             cudaStream_t s);
+// Yc[b][0] += dm * I  (mass update of a Galerkin operator with orthonormal P)
+void launch_shift_diag(Cx<double> *Y, long long nsites, int N, double dm, cudaStream_t s);
+
+// ---- layout conversions at the boundary ----
+// internal Y[j][dir][col][row] <-> canonical Y[j][dir][row][col]
+void launch_coarse_to_canonical(const Cx<double> *Yi, Cx<double> *Yc, long long nsites, int N, cudaStream_t s);
+// P columns: internal V[b][k][i] -> canonical v[k][site][a]
+void launch_prolongator_to_canonical(const Cx<double> *V, Cx<double> *out, BlockGeo bg, int Nv, cudaStream_t s);
+
+// ---- random vectors: Philox4x32-10 + Box-Muller, counter (i lo, i hi, k, level) ----
+void launch_gaussian(Cx<double> *out, long long n, unsigned long long seed, int k, int level, cudaStream_t s);
+
+// ---- coarsest level: dense LU with partial pivoting, column-major ----
+void launch_dense_from_stencil(const Cx<double> *Y, Cx<double> *A, Geo2 g, int N, cudaStream_t s);
+// factor in place; ipiv[k] = pivot row of step k; info_dev[0] = 1 + first zero pivot (0 if none)
+void lu_factor(Cx<double> *A, int n, int *ipiv, int *info_dev, cudaStream_t s);
+// x = A^{-1} b with the factors; work: n entries, must alias neither b nor x (b may equal work)
+void lu_solve_ws(const Cx<double> *LU, const int *ipiv, int n, const Cx<double> *b, Cx<double> *x, Cx<double> *work,
+                 cudaStream_t s);
+
+}  // namespace mg

@@ -1,0 +1,754 @@
+// Host orchestration of the adaptive multigrid solver and the C ABI (mg.h).
+//
+// Paper structure followed here:
+//   * adaptive setup (Eq. relax, Eq. P1, the adaptive passes, recursion to
+//     further levels) with the Galerkin operator P^dagger A P (Eq. Galerkin);
+//   * V-cycle in five steps (pre-relaxation, restriction of the residual,
+//     coarse cycle or exact coarsest solve, coarse-grid correction,
+//     post-relaxation), 2 nu + 2 operator applications per level;
+//   * outer Krylov loop preconditioned with one V-cycle per iteration
+//     (flexible GCR on D, FP64, true residual at every restart).
+// Every arithmetic step runs in the kernels of this library on the context's
+// stream; the host only sequences launches and reads convergence scalars.
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+#include "kernels.h"
+
+namespace mg {
+
+std::atomic<long long> g_launches{0};
+
+static thread_local std::string t_last_error;
+
+template <typename R>
+struct Work {
+  DevBuf<Cx<R>> b, x, r, Ar;
+};
+
+struct Level {
+  Geo2 geo{};
+  int nint = 0;
+  long long n = 0;  // complex dofs
+  // coarse operator of this level (level >= 1), internal layout
+  DevBuf<Cx<double>> Y64;
+  DevBuf<Cx<float>> Y32;
+  // transfer to the next level
+  BlockGeo bg{};
+  int Nv = 0;
+  DevBuf<Cx<double>> nullv;  // Nv level vectors
+  DevBuf<Cx<double>> V64;    // prolongator [b][k][i]
+  DevBuf<Cx<float>> V32;
+  DevBuf<double> mgs_min;    // per-block smallest Gram-Schmidt norm
+  Work<double> w64;
+  Work<float> w32;
+  DevBuf<Cx<double>> tA, tB;  // setup temporaries
+  bool stale = false;
+};
+
+// scalar slots on the device (FP64)
+enum : int {
+  kSlotMR = 0,          // 4 per level
+  kSlotOuter = 64,      // outer GCR: beta (2 * 128), then nrm / alpha / rnrm
+  kSlotCoarse = 512,    // coarsest GCR: same layout
+  kSlotCount = 1024
+};
+constexpr int kBeta = 0, kNrm = 300, kAlpha = 304, kRnrm = 308, kBnrm = 312;
+
+}  // namespace mg
+
+struct mg_ctx {
+  mg_geom geom{};
+  mg_params p{};
+  double m = 0.0;
+  cudaStream_t s = nullptr;
+  std::vector<mg::Level> lv;
+  mg::DevBuf<mg::Cx<double>> U64;
+  mg::DevBuf<mg::Cx<float>> U32;
+  // coarsest
+  bool use_lu = false;
+  int nc = 0;
+  mg::DevBuf<mg::Cx<double>> LU, lu_work;
+  mg::DevBuf<int> ipiv, info;
+  mg::DevBuf<mg::Cx<double>> cZ, cW, cr, cb, cx;
+  // outer
+  mg::DevBuf<mg::Cx<double>> oZ, oW, orr;
+  mg::DevBuf<mg::Cx<float>> z32;
+  // reductions and scalars
+  mg::DevBuf<double> partials, scal;
+  mg::DevBuf<unsigned int> tickets;
+  mg::ReduceWs ws{};
+  double *host = nullptr;  // pinned scalars
+  long long apps[MG_MAX_LEVELS] = {0, 0, 0, 0};
+  long long coarsest_iters = 0;
+  ~mg_ctx() {
+    if (host) cudaFreeHost(host);
+  }
+};
+
+namespace mg {
+
+static double diag_of(const mg_ctx &c) { return c.geom.d + c.m; }
+
+template <typename R>
+static Work<R> &work(Level &L);
+template <>
+Work<double> &work<double>(Level &L) { return L.w64; }
+template <>
+Work<float> &work<float>(Level &L) { return L.w32; }
+
+template <typename R>
+static const Cx<R> *Uof(const mg_ctx &c);
+template <>
+const Cx<double> *Uof<double>(const mg_ctx &c) { return c.U64.p; }
+template <>
+const Cx<float> *Uof<float>(const mg_ctx &c) { return c.U32.p; }
+
+template <typename R>
+static const Cx<R> *Yof(const Level &L);
+template <>
+const Cx<double> *Yof<double>(const Level &L) { return L.Y64.p; }
+template <>
+const Cx<float> *Yof<float>(const Level &L) { return L.Y32.p; }
+
+template <typename R>
+static const Cx<R> *Vof(const Level &L);
+template <>
+const Cx<double> *Vof<double>(const Level &L) { return L.V64.p; }
+template <>
+const Cx<float> *Vof<float>(const Level &L) { return L.V32.p; }
+
+static double read_scalar(mg_ctx &c, int slot) {
+  MG_CUDA(cudaMemcpyAsync(c.host, c.scal.p + slot, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+  MG_CUDA(cudaStreamSynchronize(c.s));
+  return c.host[0];
+}
+
+// out = a * A_l in + c * b
+template <typename R>
+static void apply_op(mg_ctx &c, int l, const Cx<R> *in, Cx<R> *out, const Cx<R> *b = nullptr, double a = 1.0,
+                     double cc = 0.0) {
+  Level &L = c.lv[l];
+  if (l == 0)
+    launch_dslash<R>(Uof<R>(c), in, out, L.geo, diag_of(c), b, a, cc, c.s);
+  else
+    launch_coarse_apply<R>(Yof<R>(L), in, out, L.geo, L.nint, b, a, cc, c.s);
+  c.apps[l]++;
+}
+
+// x (+)= nu MR iterations for A_l x = b from zero; r is the MR residual buffer
+// (b may equal r: then it is consumed in place).
+template <typename R>
+static void smooth(mg_ctx &c, int l, const Cx<R> *b, Cx<R> *x, Cx<R> *r, Cx<R> *Ar, int nu, bool accumulate) {
+  Level &L = c.lv[l];
+  if (!accumulate) launch_zero<R>(x, L.n, c.s);
+  if (r != b) launch_copy<R>(b, r, L.n, c.s);
+  double *sc = c.scal.p + kSlotMR + 4 * l;
+  for (int i = 0; i < nu; ++i) {
+    apply_op<R>(c, l, r, Ar);
+    launch_dot_norm<R>(Ar, r, L.n, sc, c.ws, c.s);
+    launch_mr_update<R>(sc, c.p.omega, x, r, Ar, L.n, c.s);
+  }
+}
+
+struct GcrOut {
+  int iters = 0;
+  bool converged = false;
+  double rel = 0.0;
+};
+
+// (flexible) GCR with classical Gram-Schmidt applied twice; the true residual is
+// recomputed at every restart. precond(r, z) writes z = M r; null -> identity.
+template <typename R, typename P>
+static GcrOut gcr(mg_ctx &c, int l, const Cx<R> *b, Cx<R> *x, double tol, int restart, int max_iter, Cx<R> *Z,
+                  Cx<R> *W, Cx<R> *r, int slot, P &&precond, bool has_precond) {
+  Level &L = c.lv[l];
+  const long long n = L.n;
+  double *sc = c.scal.p + slot;
+  GcrOut out;
+  launch_zero<R>(x, n, c.s);
+  launch_copy<R>(b, r, n, c.s);
+  launch_norm2<R>(b, n, sc + kBnrm, c.ws, c.s);
+  const double bn2 = read_scalar(c, slot + kBnrm);
+  if (!(bn2 > 0.0)) {
+    if (std::isnan(bn2)) fail(MG_ERR_NAN, "GCR: right-hand side norm is NaN");
+    out.converged = true;
+    return out;
+  }
+  double rel = 1.0;
+  while (out.iters < max_iter) {
+    int k = 0;
+    while (k < restart && out.iters < max_iter) {
+      Cx<R> *z = Z + (long long)k * n, *w = W + (long long)k * n;
+      if (has_precond)
+        precond(r, z);
+      else
+        launch_copy<R>(r, z, n, c.s);
+      apply_op<R>(c, l, z, w);
+      if (k > 0) {
+        for (int rep = 0; rep < 2; ++rep) {
+          launch_multi_dot<R>(W, k, w, n, sc + kBeta, c.ws, c.s);
+          launch_multi_axpy<R>(sc + kBeta, k, W, w, Z, z, n, c.s);
+        }
+      }
+      launch_norm2<R>(w, n, sc + kNrm, c.ws, c.s);
+      launch_normalize<R>(sc + kNrm, w, z, n, c.s);
+      launch_dot_norm<R>(w, r, n, sc + kAlpha, c.ws, c.s);
+      launch_gcr_update<R>(sc + kAlpha, x, z, r, w, n, sc + kRnrm, c.ws, c.s);
+      ++k;
+      ++out.iters;
+      const double rn2 = read_scalar(c, slot + kRnrm);
+      if (std::isnan(rn2)) fail(MG_ERR_NAN, "GCR: residual norm is NaN");
+      rel = std::sqrt(rn2 / bn2);
+      if (rel <= tol) break;
+    }
+    apply_op<R>(c, l, x, r, b, -1.0, 1.0);  // true residual r = b - A x
+    launch_norm2<R>(r, n, sc + kRnrm, c.ws, c.s);
+    const double tr2 = read_scalar(c, slot + kRnrm);
+    if (std::isnan(tr2)) fail(MG_ERR_NAN, "GCR: true residual norm is NaN");
+    rel = std::sqrt(tr2 / bn2);
+    if (rel <= tol) {
+      out.converged = true;
+      break;
+    }
+  }
+  out.rel = rel;
+  return out;
+}
+
+// exact solve on the coarsest level (FP64): dense LU or GCR to coarsest_tol
+static void coarsest_solve64(mg_ctx &c, const Cx<double> *b, Cx<double> *x) {
+  const int l = c.p.levels - 1;
+  if (c.use_lu) {
+    lu_solve_ws(c.LU.p, c.ipiv.p, c.nc, b, x, c.lu_work.p, c.s);
+    c.apps[l]++;
+    return;
+  }
+  auto none = [](const Cx<double> *, Cx<double> *) {};
+  GcrOut o = gcr<double>(c, l, b, x, c.p.coarsest_tol, c.p.coarsest_restart, c.p.coarsest_max_iter, c.cZ.p, c.cW.p,
+                         c.cr.p, kSlotCoarse, none, false);
+  c.coarsest_iters += o.iters;
+}
+
+template <typename R>
+static void coarsest_solve(mg_ctx &c, const Cx<R> *b, Cx<R> *x);
+template <>
+void coarsest_solve<double>(mg_ctx &c, const Cx<double> *b, Cx<double> *x) {
+  coarsest_solve64(c, b, x);
+}
+template <>
+void coarsest_solve<float>(mg_ctx &c, const Cx<float> *b, Cx<float> *x) {
+  const long long n = c.lv.back().n;
+  launch_convert<double, float>(b, c.cb.p, n, c.s);
+  coarsest_solve64(c, c.cb.p, c.cx.p);
+  launch_convert<float, double>(c.cx.p, x, n, c.s);
+}
+
+static void check_fresh(const mg_ctx &c) {
+  for (const Level &L : c.lv)
+    if (L.stale) fail(MG_ERR_STATE, "hierarchy has a level whose prolongator predates its operator; rebuild it");
+}
+
+// x = V^(l) b (the five steps); b must not alias the level's work vectors or x
+template <typename R>
+static void vcycle(mg_ctx &c, int l, const Cx<R> *b, Cx<R> *x) {
+  if (l == c.p.levels - 1) {
+    coarsest_solve<R>(c, b, x);
+    return;
+  }
+  Level &L = c.lv[l];
+  Level &C = c.lv[l + 1];
+  Work<R> &w = work<R>(L);
+  Work<R> &wc = work<R>(C);
+  // 1. pre-relaxation from zero
+  smooth<R>(c, l, b, x, w.r.p, w.Ar.p, c.p.nu_pre, false);
+  // 2. restrict the residual
+  apply_op<R>(c, l, x, w.r.p, b, -1.0, 1.0);
+  launch_restrict<R>(Vof<R>(L), w.r.p, wc.b.p, L.bg, L.Nv, c.s);
+  // 3. coarse V-cycle (or exact coarsest solve)
+  vcycle<R>(c, l + 1, wc.b.p, wc.x.p);
+  // 4. coarse-grid correction
+  launch_prolong_add<R>(Vof<R>(L), wc.x.p, x, L.bg, L.Nv, c.s);
+  // 5. post-relaxation on the final residual
+  apply_op<R>(c, l, x, w.r.p, b, -1.0, 1.0);
+  smooth<R>(c, l, w.r.p, x, w.r.p, w.Ar.p, c.p.nu_post, true);
+}
+
+// z = V r on the finest level in the context precision (r, z FP64)
+static void precondition(mg_ctx &c, const Cx<double> *r, Cx<double> *z) {
+  Level &F = c.lv[0];
+  if (c.p.precision == MG_FP32) {
+    launch_convert<float, double>(r, F.w32.b.p, F.n, c.s);
+    vcycle<float>(c, 0, F.w32.b.p, c.z32.p);
+    launch_convert<double, float>(c.z32.p, z, F.n, c.s);
+  } else {
+    vcycle<double>(c, 0, r, z);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// setup
+// ---------------------------------------------------------------------------
+static void prepare_coarsest(mg_ctx &c) {
+  Level &L = c.lv.back();
+  if (!c.use_lu) return;
+  launch_dense_from_stencil(L.Y64.p, c.LU.p, L.geo, L.nint, c.s);
+  lu_factor(c.LU.p, c.nc, c.ipiv.p, c.info.p, c.s);
+  int info = 0;
+  MG_CUDA(cudaMemcpyAsync(&info, c.info.p, sizeof(int), cudaMemcpyDeviceToHost, c.s));
+  MG_CUDA(cudaStreamSynchronize(c.s));
+  if (info != 0) fail(MG_ERR_NAN, "coarsest LU: zero pivot at column " + std::to_string(info - 1));
+}
+
+// block Gram-Schmidt of the level's vectors and the Galerkin operator of l+1
+static void build_level(mg_ctx &c, int l) {
+  Level &L = c.lv[l];
+  Level &C = c.lv[l + 1];
+  launch_block_mgs(L.nullv.p, L.n, L.V64.p, L.bg, L.Nv, L.mgs_min.p, c.s);
+  if (l == 0)
+    launch_galerkin_wilson(c.U64.p, diag_of(c), L.V64.p, C.Y64.p, L.bg, L.Nv, c.s);
+  else
+    launch_galerkin_stencil(L.Y64.p, L.V64.p, C.Y64.p, L.bg, L.Nv, c.s);
+}
+
+static void setup_level(mg_ctx &c, int l, bool full) {
+  Level &L = c.lv[l];
+  const long long n = L.n;
+  double *sc = c.scal.p + kSlotMR + 4 * l;
+  // pass 1: random vectors relaxed on A x = 0 (nu_setup MR iterations from x = v)
+  for (int k = 0; k < L.Nv; ++k) {
+    Cx<double> *v = L.nullv.p + (long long)k * n;
+    launch_gaussian(v, n, c.p.seed, k, l, c.s);
+    apply_op<double>(c, l, v, L.tA.p, nullptr, -1.0, 0.0);  // r = -A v
+    for (int i = 0; i < c.p.nu_setup; ++i) {
+      apply_op<double>(c, l, L.tA.p, L.tB.p);
+      launch_dot_norm<double>(L.tB.p, L.tA.p, n, sc, c.ws, c.s);
+      launch_mr_update<double>(sc, c.p.omega, v, L.tA.p, L.tB.p, n, c.s);
+    }
+  }
+  const int n_pass = full ? c.p.n_pass : 1;
+  for (int pass = 1; pass <= n_pass; ++pass) {
+    if (pass > 1) {
+      // v <- v - V(A v): one V-cycle on the homogeneous problem
+      for (int k = 0; k < L.Nv; ++k) {
+        Cx<double> *v = L.nullv.p + (long long)k * n;
+        apply_op<double>(c, l, v, L.tA.p);
+        vcycle<double>(c, l, L.tA.p, L.tB.p);
+        launch_xmy<double>(v, L.tB.p, n, c.s);  // tB = v - V(A v)
+        launch_copy<double>(L.tB.p, v, n, c.s);
+      }
+    }
+    build_level(c, l);
+    if (l + 1 == c.p.levels - 1)
+      prepare_coarsest(c);
+    else
+      setup_level(c, l + 1, full && pass == n_pass);
+  }
+  L.stale = false;
+}
+
+static void make_fp32_copies(mg_ctx &c) {
+  if (c.p.precision != MG_FP32) return;
+  launch_convert<float, double>(c.U64.p, c.U32.p, c.lv[0].geo.nsites * 2, c.s);
+  for (size_t l = 0; l < c.lv.size(); ++l) {
+    Level &L = c.lv[l];
+    if (l + 1 < c.lv.size()) launch_convert<float, double>(L.V64.p, L.V32.p, L.V64.n, c.s);
+    if (l > 0) launch_convert<float, double>(L.Y64.p, L.Y32.p, L.Y64.n, c.s);
+  }
+}
+
+static void validate(const mg_geom *g, const mg_params *p) {
+  if (!g || !p) fail(MG_ERR_INVALID_ARG, "null geometry or parameters");
+  if (g->d != 2) fail(MG_ERR_UNSUPPORTED, "only d = 2 is built");
+  if (g->Nc != 1) fail(MG_ERR_UNSUPPORTED, "only Nc = 1 (U(1)) is built");
+  if (g->dims[0] < 2 || g->dims[1] < 2) fail(MG_ERR_INVALID_ARG, "lattice extents must be >= 2");
+  if (p->levels < 2 || p->levels > MG_MAX_LEVELS) fail(MG_ERR_INVALID_ARG, "levels must be in [2, 4]");
+  if (p->precision != MG_FP64 && p->precision != MG_FP32) fail(MG_ERR_INVALID_ARG, "unknown precision");
+  if (p->n_pass < 1 || p->nu_pre < 0 || p->nu_post < 0 || p->nu_setup < 0) fail(MG_ERR_INVALID_ARG, "bad counts");
+  if (p->gcr_restart < 1 || p->gcr_restart > 128 || p->coarsest_restart < 1 || p->coarsest_restart > 128)
+    fail(MG_ERR_INVALID_ARG, "restart lengths must be in [1, 128]");
+  if (p->max_iter < 1 || p->coarsest_max_iter < 1) fail(MG_ERR_INVALID_ARG, "iteration limits must be >= 1");
+  int L0 = g->dims[0], L1 = g->dims[1], nint = 2;
+  for (int l = 0; l + 1 < p->levels; ++l) {
+    const int B0 = p->block[l][0], B1 = p->block[l][1];
+    if (B0 < 1 || B1 < 1 || L0 % B0 || L1 % B1)
+      fail(MG_ERR_INVALID_ARG, "level " + std::to_string(l) + ": extents not divisible by the block");
+    const int Nb = B0 * B1 * nint;
+    if (p->Nv[l] < 1 || p->Nv[l] > Nb || p->Nv[l] > 32)
+      fail(MG_ERR_INVALID_ARG, "level " + std::to_string(l) + ": Nv must be in [1, min(block dofs, 32)]");
+    L0 /= B0;
+    L1 /= B1;
+    nint = p->Nv[l];
+  }
+}
+
+static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_params *p, void *stream) {
+  validate(g, p);
+  auto c = std::make_unique<mg_ctx>();
+  c->geom = *g;
+  c->p = *p;
+  c->m = m;
+  c->s = static_cast<cudaStream_t>(stream);
+  MG_CUDA(cudaMallocHost(&c->host, 16 * sizeof(double)));
+  c->lv.resize(p->levels);
+  int L0 = g->dims[0], L1 = g->dims[1], nint = 2;
+  const bool f32 = p->precision == MG_FP32;
+  for (int l = 0; l < p->levels; ++l) {
+    Level &L = c->lv[l];
+    L.geo = Geo2{L0, L1, (long long)L0 * L1};
+    L.nint = nint;
+    L.n = L.geo.nsites * nint;
+    if (l > 0) {
+      L.Y64.alloc(L.geo.nsites * 5 * (size_t)nint * nint);
+      if (f32) L.Y32.alloc(L.Y64.n);
+    }
+    L.w64.b.alloc(L.n);
+    L.w64.x.alloc(L.n);
+    L.w64.r.alloc(L.n);
+    L.w64.Ar.alloc(L.n);
+    if (f32) {
+      L.w32.b.alloc(L.n);
+      L.w32.x.alloc(L.n);
+      L.w32.r.alloc(L.n);
+      L.w32.Ar.alloc(L.n);
+    }
+    if (l + 1 < p->levels) {
+      const int B0 = p->block[l][0], B1 = p->block[l][1];
+      L.Nv = p->Nv[l];
+      L.bg = BlockGeo{L0, L1, B0, B1, L0 / B0, L1 / B1, B0 * B1, nint, B0 * B1 * nint,
+                      (long long)(L0 / B0) * (L1 / B1)};
+      L.nullv.alloc((size_t)L.Nv * L.n);
+      L.V64.alloc((size_t)L.Nv * L.n);
+      if (f32) L.V32.alloc(L.V64.n);
+      L.mgs_min.alloc(L.bg.nblocks);
+      L.tA.alloc(L.n);
+      L.tB.alloc(L.n);
+      L0 /= B0;
+      L1 /= B1;
+      nint = L.Nv;
+    }
+  }
+  const Level &F = c->lv[0];
+  c->U64.alloc(F.geo.nsites * 2);
+  if (f32) c->U32.alloc(F.geo.nsites * 2);
+  // coarsest
+  const Level &Cst = c->lv.back();
+  c->nc = (int)Cst.n;
+  c->use_lu = Cst.n <= p->coarsest_lu_max;
+  if (c->use_lu) {
+    c->LU.alloc((size_t)Cst.n * Cst.n);
+    c->lu_work.alloc(Cst.n);
+    c->ipiv.alloc(Cst.n);
+    c->info.alloc(1);
+  } else {
+    c->cZ.alloc((size_t)p->coarsest_restart * Cst.n);
+    c->cW.alloc((size_t)p->coarsest_restart * Cst.n);
+    c->cr.alloc(Cst.n);
+  }
+  if (f32) {
+    c->cb.alloc(Cst.n);
+    c->cx.alloc(Cst.n);
+    c->z32.alloc(F.n);
+  }
+  // outer
+  c->oZ.alloc((size_t)p->gcr_restart * F.n);
+  c->oW.alloc((size_t)p->gcr_restart * F.n);
+  c->orr.alloc(F.n);
+  // reductions
+  c->ws.max_blocks = 152 * 8;
+  c->partials.alloc((size_t)c->ws.max_blocks * 4 + 16);
+  c->tickets.alloc(128);
+  MG_CUDA(cudaMemsetAsync(c->tickets.p, 0, 128 * sizeof(unsigned int), c->s));
+  c->scal.alloc(kSlotCount);
+  MG_CUDA(cudaMemsetAsync(c->scal.p, 0, kSlotCount * sizeof(double), c->s));
+  c->ws.partials = c->partials.p;
+  c->ws.ticket = c->tickets.p;
+  return c;
+}
+
+}  // namespace mg
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+using namespace mg;
+
+template <typename F>
+static int guarded(F &&f) {
+  try {
+    f();
+    t_last_error.clear();
+    return MG_OK;
+  } catch (const Error &e) {
+    t_last_error = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc &) {
+    t_last_error = "host allocation failed";
+    return MG_ERR_OOM;
+  } catch (...) {
+    t_last_error = "unexpected exception";
+    return MG_ERR_CUDA;
+  }
+}
+
+static void need_ctx(mg_ctx *c) {
+  if (!c) fail(MG_ERR_INVALID_ARG, "null context");
+}
+static void need_level(mg_ctx *c, int l, bool needs_next) {
+  need_ctx(c);
+  if (l < 0 || l >= c->p.levels || (needs_next && l + 1 >= c->p.levels))
+    fail(MG_ERR_INVALID_ARG, "level out of range");
+}
+static void need_ptr(const void *p) {
+  if (!p) fail(MG_ERR_INVALID_ARG, "null pointer");
+}
+
+extern "C" {
+
+void mg_default_params(mg_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->levels = 2;
+  for (int l = 0; l < MG_MAX_LEVELS - 1; ++l) {
+    p->block[l][0] = 4;
+    p->block[l][1] = 4;
+    p->block[l][2] = 1;
+    p->block[l][3] = 1;
+    p->Nv[l] = 8;
+  }
+  p->nu_pre = 4;
+  p->nu_post = 4;
+  p->omega = 0.8;
+  p->n_pass = 5;
+  p->nu_setup = 8;
+  p->gcr_restart = 16;
+  p->max_iter = 500;
+  p->coarsest_lu_max = 2048;
+  p->coarsest_tol = 1e-12;
+  p->coarsest_restart = 64;
+  p->coarsest_max_iter = 20000;
+  p->precision = MG_FP64;
+  p->seed = 20070704ULL;
+}
+
+const char *mg_last_error(void) { return t_last_error.c_str(); }
+
+long long mg_kernel_launches(void) { return g_launches.load(); }
+
+int mg_setup(mg_ctx **ctx, const mg_geom *g, const void *U, double m, const mg_params *p, void *stream) {
+  return guarded([&] {
+    if (!ctx) fail(MG_ERR_INVALID_ARG, "null context out-pointer");
+    *ctx = nullptr;
+    need_ptr(U);
+    auto c = create(g, m, p, stream);
+    MG_CUDA(cudaMemcpyAsync(c->U64.p, U, c->U64.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, c->s));
+    setup_level(*c, 0, true);
+    make_fp32_copies(*c);
+    MG_CUDA(cudaStreamSynchronize(c->s));
+    *ctx = c.release();
+  });
+}
+
+int mg_solve(mg_ctx *c, const void *chi, void *psi, double tol, mg_stats *st) {
+  int status = MG_OK;
+  int rc = guarded([&] {
+    need_ctx(c);
+    need_ptr(chi);
+    need_ptr(psi);
+    check_fresh(*c);
+    for (long long &a : c->apps) a = 0;
+    c->coarsest_iters = 0;
+    cudaEvent_t e0, e1;
+    MG_CUDA(cudaEventCreate(&e0));
+    MG_CUDA(cudaEventCreate(&e1));
+    MG_CUDA(cudaEventRecord(e0, c->s));
+    auto pre = [&](const Cx<double> *r, Cx<double> *z) { precondition(*c, r, z); };
+    GcrOut o = gcr<double>(*c, 0, static_cast<const Cx<double> *>(chi), static_cast<Cx<double> *>(psi), tol,
+                           c->p.gcr_restart, c->p.max_iter, c->oZ.p, c->oW.p, c->orr.p, kSlotOuter, pre, true);
+    MG_CUDA(cudaEventRecord(e1, c->s));
+    MG_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    MG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) {
+      st->iters = o.iters;
+      st->converged = o.converged ? 1 : 0;
+      st->true_rel_residual = o.rel;
+      for (int l = 0; l < MG_MAX_LEVELS; ++l) st->level_apps[l] = c->apps[l];
+      st->coarsest_iters = c->coarsest_iters;
+      st->ms = ms;
+    }
+    if (!o.converged) status = MG_ERR_NOT_CONVERGED;
+  });
+  if (rc == MG_OK && status != MG_OK) {
+    t_last_error = "not converged within max_iter";
+    return status;
+  }
+  return rc;
+}
+
+int mg_update_mass(mg_ctx *c, double m) {
+  return guarded([&] {
+    need_ctx(c);
+    check_fresh(*c);
+    c->m = m;
+    for (int l = 0; l + 1 < c->p.levels; ++l) {
+      Level &L = c->lv[l];
+      if (l == 0)
+        launch_galerkin_wilson(c->U64.p, diag_of(*c), L.V64.p, c->lv[1].Y64.p, L.bg, L.Nv, c->s);
+      else
+        launch_galerkin_stencil(L.Y64.p, L.V64.p, c->lv[l + 1].Y64.p, L.bg, L.Nv, c->s);
+    }
+    prepare_coarsest(*c);
+    make_fp32_copies(*c);
+    MG_CUDA(cudaStreamSynchronize(c->s));
+  });
+}
+
+void mg_destroy(mg_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->s);
+  delete c;
+}
+
+int mg_dslash(const mg_geom *g, const void *U, double m, const void *in, void *out, int precision, void *stream) {
+  return guarded([&] {
+    if (!g) fail(MG_ERR_INVALID_ARG, "null geometry");
+    if (g->d != 2 || g->Nc != 1) fail(MG_ERR_UNSUPPORTED, "only d = 2, Nc = 1 is built");
+    if (g->dims[0] < 2 || g->dims[1] < 2) fail(MG_ERR_INVALID_ARG, "lattice extents must be >= 2");
+    need_ptr(U);
+    need_ptr(in);
+    need_ptr(out);
+    if (in == out) fail(MG_ERR_INVALID_ARG, "in and out must not alias");
+    Geo2 geo{g->dims[0], g->dims[1], (long long)g->dims[0] * g->dims[1]};
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision == MG_FP64)
+      launch_dslash<double>(static_cast<const Cx<double> *>(U), static_cast<const Cx<double> *>(in),
+                            static_cast<Cx<double> *>(out), geo, 2.0 + m, nullptr, 1.0, 0.0, s);
+    else if (precision == MG_FP32)
+      launch_dslash<float>(static_cast<const Cx<float> *>(U), static_cast<const Cx<float> *>(in),
+                           static_cast<Cx<float> *>(out), geo, 2.0 + m, nullptr, 1.0, 0.0, s);
+    else
+      fail(MG_ERR_INVALID_ARG, "unknown precision");
+  });
+}
+
+int mg_level_apply(mg_ctx *c, int level, const void *in, void *out) {
+  return guarded([&] {
+    need_level(c, level, false);
+    need_ptr(in);
+    need_ptr(out);
+    apply_op<double>(*c, level, static_cast<const Cx<double> *>(in), static_cast<Cx<double> *>(out));
+    MG_CUDA(cudaStreamSynchronize(c->s));
+  });
+}
+
+int mg_restrict(mg_ctx *c, int level, const void *fine, void *coarse) {
+  return guarded([&] {
+    need_level(c, level, true);
+    need_ptr(fine);
+    need_ptr(coarse);
+    Level &L = c->lv[level];
+    launch_restrict<double>(L.V64.p, static_cast<const Cx<double> *>(fine), static_cast<Cx<double> *>(coarse), L.bg,
+                            L.Nv, c->s);
+    MG_CUDA(cudaStreamSynchronize(c->s));
+  });
+}
+
+int mg_prolong(mg_ctx *c, int level, const void *coarse, void *fine) {
+  return guarded([&] {
+    need_level(c, level, true);
+    need_ptr(fine);
+    need_ptr(coarse);
+    Level &L = c->lv[level];
+    launch_zero<double>(static_cast<Cx<double> *>(fine), L.n, c->s);
+    launch_prolong_add<double>(L.V64.p, static_cast<const Cx<double> *>(coarse), static_cast<Cx<double> *>(fine),
+                               L.bg, L.Nv, c->s);
+    MG_CUDA(cudaStreamSynchronize(c->s));
+  });
+}
+
+int mg_vcycle(mg_ctx *c, const void *b, void *x) {
+  return guarded([&] {
+    need_ctx(c);
+    need_ptr(b);
+    need_ptr(x);
+    check_fresh(*c);
+    precondition(*c, static_cast<const Cx<double> *>(b), static_cast<Cx<double> *>(x));
+    MG_CUDA(cudaStreamSynchronize(c->s));
+  });
+}
+
+int mg_smooth(mg_ctx *c, int level, const void *b, void *x, int nu) {
+  return guarded([&] {
+    need_level(c, level, false);
+    need_ptr(b);
+    need_ptr(x);
+    if (nu < 0) fail(MG_ERR_INVALID_ARG, "nu must be >= 0");
+    Level &L = c->lv[level];
+    smooth<double>(*c, level, static_cast<const Cx<double> *>(b), static_cast<Cx<double> *>(x), L.w64.r.p,
+                   L.w64.Ar.p, nu, false);
+    MG_CUDA(cudaStreamSynchronize(c->s));
+  });
+}
+
+int mg_build_level(mg_ctx *c, int level, const void *vectors) {
+  return guarded([&] {
+    need_level(c, level, true);
+    need_ptr(vectors);
+    Level &L = c->lv[level];
+    MG_CUDA(cudaMemcpyAsync(L.nullv.p, vectors, L.nullv.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, c->s));
+    build_level(*c, level);
+    if (level + 1 == c->p.levels - 1)
+      prepare_coarsest(*c);
+    else
+      c->lv[level + 1].stale = true;
+    L.stale = false;
+    make_fp32_copies(*c);
+    MG_CUDA(cudaStreamSynchronize(c->s));
+  });
+}
+
+int mg_get_null_vectors(mg_ctx *c, int level, void *out) {
+  return guarded([&] {
+    need_level(c, level, true);
+    need_ptr(out);
+    Level &L = c->lv[level];
+    MG_CUDA(cudaMemcpyAsync(out, L.nullv.p, L.nullv.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, c->s));
+    MG_CUDA(cudaStreamSynchronize(c->s));
+  });
+}
+
+int mg_get_prolongator(mg_ctx *c, int level, void *out) {
+  return guarded([&] {
+    need_level(c, level, true);
+    need_ptr(out);
+    Level &L = c->lv[level];
+    launch_prolongator_to_canonical(L.V64.p, static_cast<Cx<double> *>(out), L.bg, L.Nv, c->s);
+    MG_CUDA(cudaStreamSynchronize(c->s));
+  });
+}
+
+int mg_get_coarse_op(mg_ctx *c, int level, void *out) {
+  return guarded([&] {
+    need_level(c, level, false);
+    if (level < 1) fail(MG_ERR_INVALID_ARG, "level 0 has no stencil blocks");
+    need_ptr(out);
+    Level &L = c->lv[level];
+    launch_coarse_to_canonical(L.Y64.p, static_cast<Cx<double> *>(out), L.geo.nsites, L.nint, c->s);
+    MG_CUDA(cudaStreamSynchronize(c->s));
+  });
+}
+
+int mg_level_size(mg_ctx *c, int level, long long *n_sites, int *n_int) {
+  return guarded([&] {
+    need_level(c, level, false);
+    if (n_sites) *n_sites = c->lv[level].geo.nsites;
+    if (n_int) *n_int = c->lv[level].nint;
+  });
+}
+
+}  // extern "C"

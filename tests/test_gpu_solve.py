@@ -1,0 +1,164 @@
+"""GPU multigrid solves against the oracle: the solution psi = D^{-1} chi.
+
+Small lattices: psi is compared element by element with the oracle's dense LU
+or its own MG solve to a 1e-13 true residual (|dpsi|/|psi| <= 1e-8); every
+solve's true residual is recomputed in FP64 by the oracle's D (<= the
+requested tolerance). Full-size workloads use the residual property.
+"""
+import numpy as np
+import pytest
+
+import inputs
+from oracle import setup, solvers, spectrum, wilson
+from oracle.lattice import Lattice
+from tests._util import mcrit_for, rel_err, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def _mg():
+    import paper_0707_4018_gb300 as mg
+    return mg
+
+
+def _solve(U, m, dims, chi, tol, **params):
+    import torch
+    mg = _mg()
+    ctx = mg.Context.setup(to_dev(U), m, dims, mg.mg_default_params(**params))
+    psi = torch.empty((dims[0] * dims[1], 2), dtype=torch.complex128, device="cuda")
+    st = ctx.solve(to_dev(chi), psi, tol)
+    return to_host(psi), st, ctx
+
+
+def _true_rel(U, m, lat, psi, chi):
+    return np.linalg.norm(chi - wilson.apply_D(U, psi, m, lat)) / np.linalg.norm(chi)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_two_level_64x64_beta6_matches_oracle(precision):
+    # the two-level workload: 64^2, beta = 6, m = m_c + 0.02, 4x4 blocks, Nv = 8, 5 passes, MR 4+4
+    L = 64
+    lat = Lattice((L, L))
+    U, theta, _ = inputs.schwinger_links(L, 6.0, sweeps=2000, workload_id=0)
+    mc = mcrit_for(L, 6.0, 0, U, theta)
+    if mc is None:
+        mc = spectrum.critical_mass(U, lat)
+    m = mc + 0.02
+    chi = inputs.gaussian_source(L, L, seed=inputs.workload_seed(0, L, 6.0))
+    psi, st, _ = _solve(U, m, (L, L), chi, 1e-13, precision=precision)
+    assert st["converged"]
+    assert _true_rel(U, m, lat, psi, chi) <= 1e-12
+    p = setup.MGParams(levels=2, blocks=((4, 4),), Nv=(8,))
+    ref, info = solvers.mg_solve(setup.adaptive_setup(U, m, lat, p), chi, 1e-13)
+    assert info["converged"]
+    assert rel_err(psi, ref) <= 1e-8
+    # production tolerance 1e-10: residual recomputed by the oracle
+    psi10, st10, _ = _solve(U, m, (L, L), chi, 1e-10, precision=precision)
+    assert st10["converged"] and _true_rel(U, m, lat, psi10, chi) <= 1e-10
+
+
+@pytest.mark.parametrize("dims,blocks,Nv", [((16, 16), [(4, 4)], [8]), ((8, 8), [(4, 4)], [8]),
+                                            ((4, 8), [(4, 4)], [4]), ((32, 16), [(4, 4), (2, 2)], [8, 8]),
+                                            ((48, 40), [(4, 4), (3, 2)], [6, 8])])
+def test_small_lattices_match_dense_lu(dims, blocks, Nv):
+    lat = Lattice(dims)
+    U = inputs.hot_links(*dims, seed=3) if dims[0] < 16 else \
+        inputs.links_from_angles(inputs.metropolis_u1_2d(dims[0], dims[1], 6.0, 200, seed=4)[0])
+    m = 0.1
+    chi = inputs.gaussian_source(*dims, seed=5)
+    psi, st, _ = _solve(U, m, dims, chi, 1e-13, levels=len(blocks) + 1, blocks=blocks, Nv=Nv,
+                        coarsest_lu_max=100000)
+    assert st["converged"]
+    want = np.linalg.solve(wilson.dense_D(U, m, lat), chi.reshape(-1)).reshape(-1, 2)
+    assert rel_err(psi, want) <= 1e-10
+
+
+def test_zero_source_gives_zero():
+    L = 16
+    U = inputs.hot_links(L, L, seed=1)
+    psi, st, _ = _solve(U, 0.2, (L, L), np.zeros((L * L, 2), dtype=np.complex128), 1e-10)
+    assert st["converged"] and st["iters"] == 0
+    assert np.all(psi == 0)
+
+
+def test_gauge_covariant_solution():
+    L = 32
+    lat = Lattice((L, L))
+    U = inputs.links_from_angles(inputs.metropolis_u1_2d(L, L, 6.0, 200, seed=9)[0])
+    omega = inputs.u1_phases(lat.volume, 2, 2)
+    Ug = wilson.gauge_transform(U, omega, lat)[:, :, 0, 0]
+    chi = inputs.gaussian_source(L, L, seed=7)
+    psi, _, _ = _solve(U, 0.05, (L, L), chi, 1e-13)
+    psig, _, _ = _solve(Ug, 0.05, (L, L), wilson.transform_spinor(chi, omega, lat), 1e-13)
+    assert rel_err(psig, wilson.transform_spinor(psi, omega, lat)) < 1e-9
+
+
+def test_update_mass_matches_fresh_galerkin():
+    mg = _mg()
+    dims = (32, 32)
+    U = inputs.links_from_angles(inputs.metropolis_u1_2d(32, 32, 6.0, 200, seed=9)[0])
+    ctx = mg.Context.setup(to_dev(U), 0.0, dims, mg.mg_default_params(levels=3, blocks=[(4, 4), (2, 2)], Nv=[8, 8],
+                                                                       n_pass=2))
+    Y1 = to_host(ctx.coarse_op(1))
+    Y2 = to_host(ctx.coarse_op(2))
+    ctx.update_mass(0.25)
+    # P^dagger P = I on every level: a mass shift moves only the self blocks, by dm * I
+    for Y_old, lvl in ((Y1, 1), (Y2, 2)):
+        Y_new = to_host(ctx.coarse_op(lvl))
+        d = Y_new[:, 0] - Y_old[:, 0]
+        assert np.abs(d - 0.25 * np.eye(8)[None]).max() < 1e-12
+        assert np.abs(Y_new[:, 1:] - Y_old[:, 1:]).max() < 1e-13
+    import torch
+    chi = inputs.gaussian_source(32, 32, seed=3)
+    psi = torch.empty((1024, 2), dtype=torch.complex128, device="cuda")
+    st = ctx.solve(to_dev(chi), psi, 1e-12)
+    assert st["converged"]
+    lat = Lattice(dims)
+    assert _true_rel(U, 0.25, lat, to_host(psi), chi) <= 1e-12
+
+
+def test_invalid_arguments_raise():
+    mg = _mg()
+    U = to_dev(inputs.hot_links(16, 16, seed=1))
+    with pytest.raises(mg.MGError) as e:
+        mg.Context.setup(U, 0.1, (16, 16), mg.mg_default_params(blocks=[(5, 4)]))
+    assert e.value.code == 1
+    with pytest.raises(mg.MGError):
+        mg.Context.setup(U, 0.1, (16, 16), mg.mg_default_params(Nv=[40]))
+    with pytest.raises(mg.MGError):
+        mg.Context.setup(U, 0.1, (16, 16), mg.mg_default_params(levels=5))
+
+
+def test_not_converged_reports_last_iterate():
+    import torch
+    mg = _mg()
+    L = 32
+    lat = Lattice((L, L))
+    U = inputs.links_from_angles(inputs.metropolis_u1_2d(L, L, 6.0, 200, seed=9)[0])
+    ctx = mg.Context.setup(to_dev(U), 0.0, (L, L), mg.mg_default_params(max_iter=2, n_pass=1))
+    chi = inputs.gaussian_source(L, L, seed=3)
+    psi = torch.empty((L * L, 2), dtype=torch.complex128, device="cuda")
+    with pytest.raises(mg.MGError) as e:
+        ctx.solve(to_dev(chi), psi, 1e-14)
+    assert e.value.code == 4
+    st = ctx.solve(to_dev(chi), psi, 1e-14, raise_on_fail=False)
+    assert st["iters"] == 2 and not st["converged"]
+    assert abs(_true_rel(U, 0.0, lat, to_host(psi), chi) - st["true_rel_residual"]) < 1e-10
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("beta", [6.0])
+def test_three_level_256_full_size(precision, beta):
+    # the three-level sweep point used for the throughput measurement: 256^2, 4x4 then 2x2, Nv = 8
+    L = 256
+    lat = Lattice((L, L))
+    U, theta, _ = inputs.schwinger_links(L, beta, sweeps=2000, workload_id=1)
+    mc = mcrit_for(L, beta, 1, U, theta)
+    if mc is None:
+        pytest.skip("critical mass table entry missing for this field")
+    chi = inputs.gaussian_source(L, L, seed=inputs.workload_seed(1, L, beta))
+    for dm in (0.005, 0.02, 0.1):
+        psi, st, _ = _solve(U, mc + dm, (L, L), chi, 1e-10, levels=3, blocks=[(4, 4), (2, 2)], Nv=[8, 8],
+                            precision=precision, coarsest_tol=1e-6)
+        assert st["converged"]
+        assert _true_rel(U, mc + dm, lat, psi, chi) <= 1e-10

@@ -135,3 +135,12 @@ def test_each_hop_is_nearest_neighbour():
             allowed[xs, lat.neighbour(xs, mu, s)] = True
     blk = np.abs(M).sum(axis=(1, 3))
     assert np.all(blk[~allowed] == 0)
+
+
+def test_sampled_apply_matches_whole_field_apply():
+    lat = Lattice((12, 10))
+    U = inputs.hot_links(12, 10, seed=13)
+    psi = inputs.gaussian_complex(lat.volume * 2, 1, 5).reshape(-1, 2)
+    sites = np.array([0, 5, 11, 12, 59, 119])
+    np.testing.assert_allclose(wilson.apply_D_at(U, psi, 0.3, lat, sites),
+                               wilson.apply_D(U, psi, 0.3, lat)[sites], atol=1e-14)
