@@ -1,0 +1,420 @@
+"""Throughput of the adaptive multigrid Wilson-Dirac solve on GB300.
+
+Workload (three-level sweep point, 2d U(1) Schwinger model): 256 x 256 periodic
+lattice, quenched links from 2000 Metropolis sweeps (cold start, 10 hits,
+step 0.5 rad) at beta in {3, 6, 10}; for each beta the adaptive setup (4x4 then
+2x2 blocks, Nv = 8, 5 passes, MR 4 + 4, omega 0.8) runs once at the lightest
+mass m_c + 0.005 and is reused for m_c + 0.02 and m_c + 0.1; one Gaussian source
+per mass, solved to a 1e-10 true residual by FP64 flexible GCR.
+
+One step = the three setups and nine solves (the whole hot path once over the
+batch). The metric is MG solves per second including setup. The default run
+uses the mixed-precision V-cycle (FP32 inside the FP64 outer loop); the all-FP64
+solver is timed beside it. L2 is flushed (512 MiB write) before every timed step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs the same per-rank workload with its own seeds
+(independent solves: weak scaling, no data-path collective); rank 0 prints one
+JSON line with the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import inputs  # noqa: E402
+
+L = 256
+BETAS = (3.0, 6.0, 10.0)
+DMS = (0.005, 0.02, 0.1)
+TOL = 1e-10
+WORKLOAD_ID = 1
+METRIC = "MG solves/s to 1e-10 true residual (incl. setup)"
+WORKLOAD = ("2d U(1) Wilson-Dirac 256x256, beta in {3,6,10}, m-m_c in {0.005,0.02,0.1}; "
+            "3-level MG 4x4/2x2 Nv=8, 5 passes, MR 4+4; setup once per beta, 9 solves per step")
+
+
+def mg_params(precision: int):
+    import paper_0707_4018_gb300 as mg
+    return mg.mg_default_params(levels=3, blocks=[(4, 4), (2, 2)], Nv=[8, 8], precision=precision,
+                                coarsest_tol=1e-6, coarsest_restart=64)
+
+
+def mcrit_table():
+    return json.load(open(os.path.join(ROOT, "tests", "golden", "mcrit.json")))
+
+
+def make_inputs(rank: int):
+    """Links, critical masses and sources of the workload (host numpy)."""
+    table = mcrit_table()
+    fields = []
+    for beta in BETAS:
+        U, theta, _ = inputs.schwinger_links(L, beta, sweeps=2000, workload_id=WORKLOAD_ID + 100 * rank)
+        row = table.get(f"w{WORKLOAD_ID}_L{L}_b{beta:g}")
+        if row is None:
+            raise RuntimeError(f"no critical mass stored for L={L} beta={beta}")
+        digest_ok = rank == 0 and row["theta_digest"] == inputs.field_digest(theta)
+        seed = inputs.workload_seed(WORKLOAD_ID + 100 * rank, L, beta)
+        chis = [inputs.gaussian_source(L, L, seed=seed, index=i) for i in range(len(DMS))]
+        fields.append(dict(beta=beta, U=U, m_c=row["m_crit"], digest_ok=digest_ok, chis=chis))
+    return fields
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_step(fields_dev, precision: int, stats_out=None, host_io=None):
+    """One pass over the batch: per beta, setup at the lightest mass and three solves."""
+    import torch
+    import paper_0707_4018_gb300 as mg
+    n_solves = 0
+    for f in fields_dev:
+        if host_io is not None:
+            U = f["U_host"].to("cuda", non_blocking=True)
+        else:
+            U = f["U_dev"]
+        ctx = mg.Context.setup(U, f["m_c"] + DMS[0], (L, L), mg_params(precision))
+        for i, dm in enumerate(DMS):
+            if i > 0:
+                ctx.update_mass(f["m_c"] + dm)
+            chi = f["chi_host"][i].to("cuda", non_blocking=True) if host_io is not None else f["chi_dev"][i]
+            psi = f["psi_dev"][i]
+            st = ctx.solve(chi, psi, TOL)
+            if host_io is not None:
+                host_io[f["beta"]][i].copy_(psi, non_blocking=True)
+            if stats_out is not None:
+                stats_out.append(dict(beta=f["beta"], dm=dm, **st))
+            n_solves += 1
+        ctx.close()
+    torch.cuda.current_stream().synchronize()
+    return n_solves
+
+
+def timed_steps(fields_dev, precision, steps, warmup, flush, dist_ctx, host_io=None, sampler=None):
+    import torch
+    import paper_0707_4018_gb300 as mg
+    for _ in range(warmup):
+        run_step(fields_dev, precision, host_io=host_io)
+    stats = []
+    barrier(dist_ctx)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    launches0 = mg.mg_kernel_launches()
+    total_ms = 0.0
+    solves = 0
+    stream = torch.cuda.current_stream()
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solves += run_step(fields_dev, precision, stats_out=stats, host_io=host_io)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    launches = mg.mg_kernel_launches() - launches0
+    clocks = sampler.stop() if sampler else None
+    barrier(dist_ctx)
+    total_ms = max_over_ranks(total_ms, dist_ctx)
+    return dict(ms=total_ms, solves=solves, stats=stats, launches=launches, clocks=clocks)
+
+
+def dslash_roofline(precision: int, L_big: int = 4096, iters: int = 20):
+    """Fine Wilson apply alone on a lattice far larger than L2: algorithmic bytes / time."""
+    import torch
+    import paper_0707_4018_gb300 as mg
+    dt = torch.complex128 if precision == 0 else torch.complex64
+    V = L_big * L_big
+    g = torch.Generator(device="cuda").manual_seed(5)
+    ang = torch.rand((V, 2), device="cuda", generator=g, dtype=torch.float64) * 2 * np.pi
+    U = torch.polar(torch.ones_like(ang), ang).to(dt)
+    psi = torch.randn((V, 2), device="cuda", generator=g, dtype=dt)
+    out = torch.empty_like(psi)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        mg.mg_dslash(U, psi, out, 0.01, (L_big, L_big), precision)
+    ms = []
+    for _ in range(iters):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mg.mg_dslash(U, psi, out, 0.01, (L_big, L_big), precision)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = statistics.median(ms) * 1e-3
+    cplx = 16 if precision == 0 else 8
+    bytes_alg = V * 6 * cplx  # psi in (2), U (2), psi out (2) complex per site
+    return dict(lattice=f"{L_big}x{L_big}", dtype="f64" if precision == 0 else "f32", bytes_per_site=6 * cplx,
+                ms=t * 1e3, gbs=bytes_alg / t / 1e9)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(budget_s: float = 25.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: beta = 6 only,
+    adaptive setup at the lightest mass then solves at the three masses until the budget."""
+    from oracle import setup as osetup, solvers as osolvers
+    from oracle.lattice import Lattice
+    table = mcrit_table()
+    beta = 6.0
+    U, _, _ = inputs.schwinger_links(L, beta, sweeps=2000, workload_id=WORKLOAD_ID)
+    mc = table[f"w{WORKLOAD_ID}_L{L}_b{beta:g}"]["m_crit"]
+    lat = Lattice((L, L))
+    p = osetup.MGParams(levels=3, blocks=((4, 4), (2, 2)), Nv=(8, 8), coarsest_tol=1e-6, coarsest_lu_max=2048)
+    seed = inputs.workload_seed(WORKLOAD_ID, L, beta)
+    t0 = time.perf_counter()
+    hier = osetup.adaptive_setup(U, mc + DMS[0], lat, p)
+    solves = 0
+    for i, dm in enumerate(DMS):
+        if i > 0:
+            osetup.update_mass(hier, mc + dm)
+        chi = inputs.gaussian_source(L, L, seed=seed, index=i)
+        osolvers.mg_solve(hier, chi, TOL)
+        solves += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    try:
+        import threadpoolctl
+        cores = max(info.get("num_threads", 1) for info in threadpoolctl.threadpool_info()) or 1
+    except Exception:
+        cores = os.cpu_count() or 1
+    return dict(value=solves / dt, unit="solves/s", cores=cores, kind="oracle", seconds=dt,
+                sample=f"beta=6 only: oracle setup at m_c+0.005 then {solves} solve(s) "
+                       f"(of the 9-solve step), 256x256, tol 1e-10")
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; independent solves per rank)
+# ---------------------------------------------------------------------------
+def init_dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world <= 1:
+        return None
+    import torch
+    import torch.distributed as dist
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(d):
+    if d is not None:
+        d.barrier()
+
+
+def max_over_ranks(x: float, d) -> float:
+    if d is None:
+        return x
+    import torch
+    dev = "cuda" if d.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    d.all_reduce(t, op=d.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, d) -> float:
+    if d is None:
+        return x
+    import torch
+    dev = "cuda" if d.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    d.all_reduce(t, op=d.ReduceOp.SUM)
+    return float(t.item())
+
+
+def rank_of(d) -> int:
+    return 0 if d is None else d.get_rank()
+
+
+def world_of(d) -> int:
+    return 1 if d is None else d.get_world_size()
+
+
+def run_reference(args, d):
+    """The oracle arm: the FP64 CPU oracle timed on the host cores (rank 0 only)."""
+    if rank_of(d) != 0:
+        return
+    per_step = []
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        pass
+    for _ in range(max(1, args.steps)):
+        cb = cpu_baseline(budget_s=min(25.0, 60.0 / max(1, args.steps)))
+        per_step.append(cb)
+    v = float(np.mean([c["value"] for c in per_step]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": per_step[0]["sample"]},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": per_step[0]["cores"], "kind": "oracle",
+                             "sample": per_step[0]["sample"]},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("warmup must be >= 3")
+    d = init_dist()
+    if args.impl == "reference":
+        run_reference(args, d)
+        return
+    import torch
+    import paper_0707_4018_gb300 as mg
+    rank = rank_of(d)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    mg.load()
+    fields = make_inputs(rank)
+    fields_dev = []
+    for f in fields:
+        fd = dict(beta=f["beta"], m_c=f["m_c"], U_dev=torch.from_numpy(f["U"]).cuda(),
+                  chi_dev=[torch.from_numpy(c).cuda() for c in f["chis"]],
+                  psi_dev=[torch.empty((L * L, 2), dtype=torch.complex128, device="cuda") for _ in DMS],
+                  U_host=torch.from_numpy(f["U"]).pin_memory(),
+                  chi_host=[torch.from_numpy(c).pin_memory() for c in f["chis"]])
+        fields_dev.append(fd)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    sampler = ClockSampler(local)
+    mixed = timed_steps(fields_dev, mg.MG_FP32, args.steps, args.warmup, flush, d, sampler=sampler)
+    total_solves = sum_over_ranks(mixed["solves"], d)
+    value = total_solves / (mixed["ms"] * 1e-3)
+    worst_res = max(s["true_rel_residual"] for s in mixed["stats"])
+    iters = [s["iters"] for s in mixed["stats"]]
+
+    fp64 = None
+    if not args.no_fp64:
+        r = timed_steps(fields_dev, mg.MG_FP64, args.steps, 3, flush, d)
+        fp64 = dict(value=sum_over_ranks(r["solves"], d) / (r["ms"] * 1e-3), unit="solves/s",
+                    ms_per_step=r["ms"] / args.steps, iters=[s["iters"] for s in r["stats"]],
+                    worst_true_rel_residual=max(s["true_rel_residual"] for s in r["stats"]))
+
+    e2e = None
+    if not args.no_e2e:
+        host_out = {f["beta"]: [torch.empty((L * L, 2), dtype=torch.complex128).pin_memory() for _ in DMS]
+                    for f in fields_dev}
+        r = timed_steps(fields_dev, mg.MG_FP32, args.steps, 3, flush, d, host_io=host_out)
+        h2d = sum(f["U_host"].numel() * 16 + sum(c.numel() * 16 for c in f["chi_host"]) for f in fields_dev)
+        d2h = sum(len(DMS) * L * L * 2 * 16 for _ in fields_dev)
+        e2e = dict(value=sum_over_ranks(r["solves"], d) / (r["ms"] * 1e-3), unit="solves/s",
+                   h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h)
+
+    peak, peak_kind = measured_peaks()
+    ds32 = dslash_roofline(1)
+    ds64 = dslash_roofline(0)
+
+    cpu = None
+    if rank == 0 and world_of(d) == 1 and not args.no_cpu:
+        cpu = cpu_baseline()
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world_of(d), "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mixed["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": f"{L}x{L}", "betas": list(BETAS), "m_minus_mc": list(DMS),
+                   "solves_per_step": len(BETAS) * len(DMS), "precision": "FP64 outer GCR, FP32 V-cycle",
+                   "l2": "flushed before every timed step (512 MiB write)", "tol": TOL,
+                   "gauge_digest_matches_table": all(f["digest_ok"] for f in fields) if rank == 0 else None},
+        "solver": {"iters": iters, "worst_true_rel_residual": worst_res},
+        "fp64_mg": fp64,
+        "e2e": e2e,
+        "gpu_launches": mixed["launches"],
+        "clocks": mixed["clocks"],
+        "roofline": {"bound": "hbm", "kernel": "dslash_kernel<float> (fine Wilson apply, 4096^2, alone)",
+                     "achieved": ds32["gbs"], "peak": peak, "unit": "GB/s", "frac": ds32["gbs"] / peak,
+                     "traffic": None, "peak_kind": peak_kind},
+        "dslash_hbm": {"f32": ds32, "f64": ds64, "peak_gbs": peak},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()
