@@ -48,7 +48,7 @@ WORKLOAD = ("2d U(1) Wilson-Dirac 256x256, beta in {3,6,10}, m-m_c in {0.005,0.0
 def mg_params(precision: int):
     import paper_0707_4018_gb300 as mg
     return mg.mg_default_params(levels=3, blocks=[(4, 4), (2, 2)], Nv=[8, 8], precision=precision,
-                                coarsest_tol=1e-6, coarsest_restart=64)
+                                coarsest_tol=1e-4, coarsest_restart=16)
 
 
 def mcrit_table():
@@ -232,7 +232,8 @@ def cpu_baseline(budget_s: float = 25.0):
     U, _, _ = inputs.schwinger_links(L, beta, sweeps=2000, workload_id=WORKLOAD_ID)
     mc = table[f"w{WORKLOAD_ID}_L{L}_b{beta:g}"]["m_crit"]
     lat = Lattice((L, L))
-    p = osetup.MGParams(levels=3, blocks=((4, 4), (2, 2)), Nv=(8, 8), coarsest_tol=1e-6, coarsest_lu_max=2048)
+    p = osetup.MGParams(levels=3, blocks=((4, 4), (2, 2)), Nv=(8, 8), coarsest_tol=1e-4, coarsest_restart=16,
+                        coarsest_lu_max=2048)
     seed = inputs.workload_seed(WORKLOAD_ID, L, beta)
     t0 = time.perf_counter()
     hier = osetup.adaptive_setup(U, mc + DMS[0], lat, p)
@@ -327,6 +328,27 @@ def run_reference(args, d):
     print(json.dumps(line), flush=True)
 
 
+def run_only(case: str):
+    """Small fixed cases for profiler captures (no timing claims are made from them)."""
+    import torch
+    import paper_0707_4018_gb300 as mg
+    mg.load()
+    if case.startswith("dslash"):
+        r = dslash_roofline(1 if case == "dslash-f32" else 0, iters=3)
+        print(json.dumps({"case": case, **r}))
+        return
+    beta = 6.0
+    U, _, _ = inputs.schwinger_links(L, beta, sweeps=2000, workload_id=WORKLOAD_ID)
+    mc = mcrit_table()[f"w{WORKLOAD_ID}_L{L}_b{beta:g}"]["m_crit"]
+    seed = inputs.workload_seed(WORKLOAD_ID, L, beta)
+    fd = dict(beta=beta, m_c=mc, U_dev=torch.from_numpy(U).cuda(),
+              chi_dev=[torch.from_numpy(inputs.gaussian_source(L, L, seed=seed, index=i)).cuda() for i in range(3)],
+              psi_dev=[torch.empty((L * L, 2), dtype=torch.complex128, device="cuda") for _ in DMS])
+    stats = []
+    run_step([fd], mg.MG_FP32, stats_out=stats)
+    print(json.dumps({"case": case, "iters": [s["iters"] for s in stats]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -336,9 +358,14 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--only", default=None, choices=["dslash-f32", "dslash-f64", "solve"],
+                    help="profiling cases: the Dslash timing loop alone, or one beta's setup + 3 solves")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("warmup must be >= 3")
+    if args.only is not None:
+        run_only(args.only)
+        return
     d = init_dist()
     if args.impl == "reference":
         run_reference(args, d)

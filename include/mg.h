@@ -64,7 +64,8 @@ typedef enum {
   MG_ERR_NOT_CONVERGED = 4, /* max_iter reached before the tolerance */
   MG_ERR_NAN = 5,           /* a NaN/Inf or breakdown appeared in a reduction */
   MG_ERR_UNSUPPORTED = 6,   /* a valid request this build does not implement */
-  MG_ERR_STATE = 7          /* the hierarchy is incomplete for the request */
+  MG_ERR_STATE = 7,         /* the hierarchy is incomplete for the request */
+  MG_ERR_TIMEOUT = 8        /* a bounded device-side wait (grid barrier) ran out */
 } mg_status;
 
 typedef enum {
@@ -90,7 +91,7 @@ typedef struct {
   int max_iter;                     /* outer iteration limit */
   int coarsest_lu_max;              /* coarsest dimension up to which a dense LU is used */
   double coarsest_tol;              /* relative residual of the iterative coarsest solve */
-  int coarsest_restart;             /* restart length of the iterative coarsest solve */
+  int coarsest_restart;             /* restart length of the iterative coarsest solve (1..32) */
   int coarsest_max_iter;            /* iteration limit of the iterative coarsest solve */
   int precision;                    /* mg_precision */
   uint64_t seed;                    /* Philox4x32-10 key of the setup's random vectors */
@@ -103,13 +104,14 @@ typedef struct {
   long long level_apps[MG_MAX_LEVELS]; /* operator applications per level (level 0: fine D) */
   long long coarsest_iters;          /* iterations of the iterative coarsest solve */
   double ms;                         /* wall time of the call, stream-synchronised */
+  int graphs;                        /* 1 if the V-cycles replayed a captured CUDA graph */
 } mg_stats;
 
 typedef struct mg_ctx mg_ctx;
 
 /* Defaults: 2 levels, 4x4 blocks, Nv = 8, MR 4 + 4 with omega = 0.8, 5 passes,
  * nu_setup = 8, GCR(16), max_iter 500, coarsest LU up to 2048, coarsest GCR
- * tol 1e-12 / restart 64 / 20000 iterations, FP64, seed 20070704. */
+ * tol 1e-12 / restart 32 / 20000 iterations, FP64, seed 20070704. */
 void mg_default_params(mg_params *p);
 
 /*

@@ -18,7 +18,7 @@ MG_MAX_LEVELS = 4
 MG_FP64, MG_FP32 = 0, 1
 
 STATUS = {0: "MG_OK", 1: "MG_ERR_INVALID_ARG", 2: "MG_ERR_CUDA", 3: "MG_ERR_OOM", 4: "MG_ERR_NOT_CONVERGED",
-          5: "MG_ERR_NAN", 6: "MG_ERR_UNSUPPORTED", 7: "MG_ERR_STATE"}
+          5: "MG_ERR_NAN", 6: "MG_ERR_UNSUPPORTED", 7: "MG_ERR_STATE", 8: "MG_ERR_TIMEOUT"}
 
 
 class MGError(RuntimeError):
@@ -43,11 +43,12 @@ class mg_params(ctypes.Structure):
 class mg_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("true_rel_residual", ctypes.c_double),
                 ("level_apps", ctypes.c_longlong * MG_MAX_LEVELS), ("coarsest_iters", ctypes.c_longlong),
-                ("ms", ctypes.c_double)]
+                ("ms", ctypes.c_double), ("graphs", ctypes.c_int)]
 
     def as_dict(self):
         return dict(iters=self.iters, converged=bool(self.converged), true_rel_residual=self.true_rel_residual,
-                    level_apps=list(self.level_apps), coarsest_iters=self.coarsest_iters, ms=self.ms)
+                    level_apps=list(self.level_apps), coarsest_iters=self.coarsest_iters, ms=self.ms,
+                    graphs=bool(self.graphs))
 
 
 _lib = None

@@ -1,0 +1,431 @@
+// Coarsest-level solve as one persistent kernel (paper: the coarsest level of
+// the V-cycle is an exact solve). The coarsest system of the three-level
+// hierarchy is far too large for a dense factorisation at every setup pass, so
+// it is iterated to a relative residual `tol` with restarted GCR, entirely on
+// the device:
+//
+//  * right block-Jacobi preconditioning folded into the stencil: with
+//    M = blockdiag(X_j^{-1}) (X_j the coarse self blocks), GCR runs on
+//    A M y = b, whose blocks are Y_{j,dir} X_{src}^{-1} (same sparsity, self
+//    blocks = I); its residual is the true residual b - A x with x = M y;
+//  * one cooperative launch of G CTAs (all co-resident); each thread owns the
+//    dofs i = gid, gid + G*T, ... for the whole solve;
+//  * grid-wide barriers are a counter + generation flag with a bounded spin:
+//    after `spin_limit` polls a CTA records timeout status and returns, so the
+//    kernel always terminates;
+//  * deterministic reductions: fixed warp/block trees, per-CTA partials staged
+//    into shared memory by every CTA and summed in CTA order (identical in
+//    every CTA);
+//  * classical Gram-Schmidt applied twice; the second pass shares its grid
+//    reduction with |w|^2 and <w, r> (|w - W b|^2 = |w|^2 - |b|^2 for the
+//    orthonormal W), so an iteration costs 3 grid synchronisations.
+// Arithmetic: FP64 throughout (the coarsest solve stays in FP64 in every mode).
+#include "kernels.h"
+
+namespace mg {
+
+constexpr int kMaxRestart = 32;
+constexpr int kSlots = 2 * kMaxRestart + 4;
+static_assert(kSlots == kCoarsestSlots, "slot count shared with the host");
+
+struct CgArgs {
+  const Cx<double> *Y;     // preconditioned stencil A M, internal layout
+  const Cx<double> *Minv;  // X_j^{-1}, [j][col][row]
+  int L0, L1, N;
+  long long n;
+  const Cx<double> *b;
+  Cx<double> *x, *y, *r, *Z, *W;
+  double *partials;   // [G][kSlots]
+  unsigned int *bar;  // [0] count, [1] generation
+  double tol;
+  int restart, max_iter;
+  long long spin_limit;
+  int *out;         // [0] iterations (accumulated), [1] sticky status (1 = barrier timeout),
+                    // [2] solves that missed the tolerance (accumulated)
+  double *out_rel;  // relative true residual of the last solve
+};
+
+// bounded grid barrier; clears `ok` (and sets the status) when the wait gave up
+__device__ __forceinline__ void grid_sync(const CgArgs &a, bool &ok) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int *gen = a.bar + 1;
+    const unsigned int g = *gen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(a.bar, 1u);
+    int good = 1;
+    if (arrived == gridDim.x - 1) {
+      atomicExch(a.bar, 0u);
+      __threadfence();
+      atomicAdd(a.bar + 1, 1u);
+    } else {
+      long long polls = 0;
+      while (*gen == g) {
+        if (++polls > a.spin_limit) {
+          good = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    if (!good) atomicExch(a.out + 1, 1);
+    s_ok = good;
+  }
+  __syncthreads();
+  ok = ok && s_ok;
+}
+
+// warp tree of one per-thread value; lane 0 stores it as slot s of its warp
+__device__ __forceinline__ void warp_put(double t, int s, double *swarp) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if ((threadIdx.x & 31) == 0) swarp[(threadIdx.x >> 5) * kSlots + s] = t;
+}
+
+// Sum slots [0, nv) of every warp across the grid. Block tree -> per-CTA
+// partials -> barrier -> every CTA stages all partials in shared memory with
+// independent loads -> one warp per slot sums them in CTA order.
+__device__ __forceinline__ void grid_sum(const CgArgs &a, int nv, double *swarp, double *stage, double *sres,
+                                         bool &ok) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  for (int s = threadIdx.x; s < nv; s += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += swarp[w * kSlots + s];
+    a.partials[(long long)blockIdx.x * kSlots + s] = t;
+  }
+  __threadfence();
+  grid_sync(a, ok);
+  const int total = (int)gridDim.x * nv;
+  for (int q = threadIdx.x; q < total; q += blockDim.x) {
+    const int c = q / nv, s = q - c * nv;
+    stage[q] = __ldcg(a.partials + (long long)c * kSlots + s);
+  }
+  __syncthreads();
+  for (int s = wid; s < nv; s += nw) {
+    double t = 0.0;
+    for (unsigned int c = lane; c < gridDim.x; c += 32) t += stage[c * nv + s];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) sres[s] = t;
+  }
+  __syncthreads();
+}
+
+template <int NT>
+__device__ __forceinline__ Cx<double> apply_row(const CgArgs &a, long long i, const Cx<double> *v) {
+  const int N = NT > 0 ? NT : a.N;
+  const long long j = i / N;
+  const int row = (int)(i - j * N);
+  const int x1 = (int)(j / a.L0), x0 = (int)(j - (long long)x1 * a.L0);
+  const long long rowo = (long long)x1 * a.L0;
+  long long src[5];
+  src[0] = j;
+  src[1] = rowo + (x0 + 1 == a.L0 ? 0 : x0 + 1);
+  src[2] = rowo + (x0 == 0 ? a.L0 - 1 : x0 - 1);
+  src[3] = (x1 + 1 == a.L1 ? 0 : rowo + a.L0) + x0;
+  src[4] = (x1 == 0 ? (long long)(a.L1 - 1) * a.L0 : rowo - a.L0) + x0;
+  Cx<double> acc = mk(0.0, 0.0);
+#pragma unroll
+  for (int dir = 0; dir < 5; ++dir) {
+    const Cx<double> *Yd = a.Y + (j * 5 + dir) * (long long)N * N + row;
+    const Cx<double> *xs = v + src[dir] * N;
+#pragma unroll(NT > 0 ? NT : 1)
+    for (int c = 0; c < N; ++c) {
+      // neighbour values were written by other CTAs: read through L2 (no stale L1 lines)
+      const double2 xv = __ldcg(reinterpret_cast<const double2 *>(xs + c));
+      cmac(acc, Yd[(long long)c * N], mk(xv.x, xv.y));
+    }
+  }
+  return acc;
+}
+
+// sum over own dofs of conj(W_j) * Wk for j < k, into warp slots off + 2j, off + 2j + 1
+__device__ __forceinline__ void gs_dots(const CgArgs &a, int k, const Cx<double> *Wk, long long gid, long long gs,
+                                        double *swarp, int off) {
+  for (int j = 0; j < k; ++j) {
+    double re = 0.0, im = 0.0;
+    for (long long i = gid; i < a.n; i += gs) {
+      const Cx<double> wj = a.W[(long long)j * a.n + i], w = Wk[i];
+      re += wj.re * w.re + wj.im * w.im;
+      im += wj.re * w.im - wj.im * w.re;
+    }
+    warp_put(re, off + 2 * j, swarp);
+    warp_put(im, off + 2 * j + 1, swarp);
+  }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(256) coarsest_gcr_kernel(CgArgs a) {
+  extern __shared__ double sdyn[];
+  double *swarp = sdyn;               // 8 warps x kSlots
+  double *sres = sdyn + 8 * kSlots;   // kSlots
+  double *stage = sdyn + 9 * kSlots;  // G x kSlots
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long gs = (long long)gridDim.x * blockDim.x;
+  const long long n = a.n;
+  const int N = NT > 0 ? NT : a.N;
+  bool ok = true;
+
+  // y = 0, r = b, |b|^2
+  double t0 = 0.0;
+  for (long long i = gid; i < n; i += gs) {
+    const Cx<double> bi = a.b[i];
+    a.y[i] = mk(0.0, 0.0);
+    a.r[i] = bi;
+    t0 += norm2(bi);
+  }
+  warp_put(t0, 0, swarp);
+  grid_sum(a, 1, swarp, stage, sres, ok);
+  if (!ok) return;
+  const double bn2 = sres[0];
+  const double tol2 = a.tol * a.tol * bn2;
+  int it = 0;
+  bool converged = !(bn2 > 0.0);
+  double rn2 = bn2;
+  while (!converged && it < a.max_iter) {
+    for (int k = 0; k < a.restart && it < a.max_iter; ++k) {
+      Cx<double> *Zk = a.Z + (long long)k * n, *Wk = a.W + (long long)k * n;
+      // z_k = r, w_k = (A M) r
+      for (long long i = gid; i < n; i += gs) {
+        Wk[i] = apply_row<NT>(a, i, a.r);
+        Zk[i] = a.r[i];
+      }
+      if (k > 0) {
+        // first classical Gram-Schmidt pass
+        gs_dots(a, k, Wk, gid, gs, swarp, 0);
+        grid_sum(a, 2 * k, swarp, stage, sres, ok);
+        if (!ok) return;
+        for (long long i = gid; i < n; i += gs) {
+          Cx<double> w = Wk[i], z = Zk[i];
+          for (int j = 0; j < k; ++j) {
+            const Cx<double> bj = mk(-sres[2 * j], -sres[2 * j + 1]);
+            cmac(w, bj, a.W[(long long)j * n + i]);
+            cmac(z, bj, a.Z[(long long)j * n + i]);
+          }
+          Wk[i] = w;
+          Zk[i] = z;
+        }
+        // second pass dots (slots 3 + 2j) share the reduction with the norms below
+        gs_dots(a, k, Wk, gid, gs, swarp, 3);
+      }
+      double nn = 0.0, wr = 0.0, wi = 0.0;
+      for (long long i = gid; i < n; i += gs) {
+        const Cx<double> w = Wk[i], ri = a.r[i];
+        nn += norm2(w);
+        wr += w.re * ri.re + w.im * ri.im;
+        wi += w.re * ri.im - w.im * ri.re;
+      }
+      warp_put(nn, 0, swarp);
+      warp_put(wr, 1, swarp);
+      warp_put(wi, 2, swarp);
+      grid_sum(a, 3 + 2 * k, swarp, stage, sres, ok);
+      if (!ok) return;
+      // second pass: w -= W beta2; |w|^2 -= |beta2|^2; <w, r> unchanged to O(eps^2)
+      double nw2 = sres[0];
+      for (int j = 0; j < k; ++j) nw2 -= sres[3 + 2 * j] * sres[3 + 2 * j] + sres[4 + 2 * j] * sres[4 + 2 * j];
+      const bool breakdown = !(nw2 > 1e-28 * sres[0]);
+      const double inv = breakdown ? 0.0 : 1.0 / sqrt(nw2);
+      const Cx<double> alpha = mk(sres[1] * inv, sres[2] * inv);  // <w_hat, r>
+      for (long long i = gid; i < n; i += gs) {
+        Cx<double> w = Wk[i], z = Zk[i];
+        for (int j = 0; j < k; ++j) {
+          const Cx<double> bj = mk(-sres[3 + 2 * j], -sres[4 + 2 * j]);
+          cmac(w, bj, a.W[(long long)j * n + i]);
+          cmac(z, bj, a.Z[(long long)j * n + i]);
+        }
+        w = inv * w;
+        z = inv * z;
+        Wk[i] = w;
+        Zk[i] = z;
+        cmac(a.y[i], alpha, z);
+        Cx<double> ri = a.r[i];
+        cmac(ri, mk(-alpha.re, -alpha.im), w);
+        a.r[i] = ri;
+      }
+      rn2 = fmax(rn2 - norm2(alpha), 0.0);
+      ++it;
+      grid_sync(a, ok);
+      if (!ok) return;
+      if (rn2 <= tol2 || breakdown) break;
+    }
+    // true residual r = b - (A M) y
+    double tr = 0.0;
+    for (long long i = gid; i < n; i += gs) {
+      const Cx<double> ri = a.b[i] - apply_row<NT>(a, i, a.y);
+      a.r[i] = ri;
+      tr += norm2(ri);
+    }
+    warp_put(tr, 0, swarp);
+    grid_sum(a, 1, swarp, stage, sres, ok);
+    if (!ok) return;
+    rn2 = sres[0];
+    converged = rn2 <= tol2;
+    if (!(rn2 == rn2)) break;  // NaN: stop; reported through out_rel
+  }
+  // x = M y (site-local; y is complete after the last grid reduction)
+  for (long long i = gid; i < n; i += gs) {
+    const long long j = i / N;
+    const int row = (int)(i - j * N);
+    const Cx<double> *Mj = a.Minv + j * (long long)N * N + row;
+    Cx<double> acc = mk(0.0, 0.0);
+    for (int c = 0; c < N; ++c) {
+      const double2 yv = __ldcg(reinterpret_cast<const double2 *>(a.y + j * N + c));
+      cmac(acc, Mj[(long long)c * N], mk(yv.x, yv.y));
+    }
+    a.x[i] = acc;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    atomicAdd(a.out, it);
+    if (!converged) atomicAdd(a.out + 2, 1);
+    a.out_rel[0] = bn2 > 0.0 ? sqrt(rn2 / bn2) : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// block-Jacobi preparation: Minv_j = X_j^{-1} (Gauss-Jordan with partial
+// pivoting, one thread per coarse site) and the stencil A M
+// ---------------------------------------------------------------------------
+__global__ void self_block_inverse_kernel(const Cx<double> *__restrict__ Y, Cx<double> *__restrict__ Minv,
+                                          Cx<double> *__restrict__ work, long long nsites, int N, int *info) {
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= nsites) return;
+  // work[j]: augmented [X | I] as two column-major N x N matrices
+  Cx<double> *Aw = work + j * 2LL * N * N;
+  Cx<double> *Iw = Aw + (long long)N * N;
+  const Cx<double> *X = Y + (j * 5) * (long long)N * N;  // [col][row]
+  for (int q = 0; q < N * N; ++q) {
+    Aw[q] = X[q];
+    Iw[q] = mk((q % N) == (q / N) ? 1.0 : 0.0, 0.0);
+  }
+  for (int c = 0; c < N; ++c) {
+    int p = c;
+    double best = norm2(Aw[c * N + c]);
+    for (int rr = c + 1; rr < N; ++rr) {
+      const double v = norm2(Aw[c * N + rr]);
+      if (v > best) {
+        best = v;
+        p = rr;
+      }
+    }
+    if (!(best > 0.0)) {
+      atomicExch(info, 1);
+      return;
+    }
+    if (p != c) {
+      for (int cc = 0; cc < N; ++cc) {
+        Cx<double> t = Aw[cc * N + c];
+        Aw[cc * N + c] = Aw[cc * N + p];
+        Aw[cc * N + p] = t;
+        t = Iw[cc * N + c];
+        Iw[cc * N + c] = Iw[cc * N + p];
+        Iw[cc * N + p] = t;
+      }
+    }
+    const Cx<double> pv = Aw[c * N + c];
+    const double d = norm2(pv);
+    const Cx<double> inv = mk(pv.re / d, -pv.im / d);
+    for (int cc = 0; cc < N; ++cc) {
+      Aw[cc * N + c] = Aw[cc * N + c] * inv;
+      Iw[cc * N + c] = Iw[cc * N + c] * inv;
+    }
+    for (int rr = 0; rr < N; ++rr) {
+      if (rr == c) continue;
+      const Cx<double> f = Aw[c * N + rr];
+      const Cx<double> mf = mk(-f.re, -f.im);
+      for (int cc = 0; cc < N; ++cc) {
+        cmac(Aw[cc * N + rr], mf, Aw[cc * N + c]);
+        cmac(Iw[cc * N + rr], mf, Iw[cc * N + c]);
+      }
+    }
+  }
+  Cx<double> *Mj = Minv + j * (long long)N * N;
+  for (int q = 0; q < N * N; ++q) Mj[q] = Iw[q];
+}
+
+// Yt[j][dir] = Y[j][dir] * Minv[src(j, dir)]  (column-major blocks); thread per (j, dir, col, row)
+__global__ void precondition_stencil_kernel(const Cx<double> *__restrict__ Y, const Cx<double> *__restrict__ Minv,
+                                            Cx<double> *__restrict__ Yt, int L0, int L1, int N) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nsites = (long long)L0 * L1;
+  const long long per = 5LL * N * N;
+  if (t >= nsites * per) return;
+  const long long j = t / per;
+  const int rem = (int)(t - j * per), dir = rem / (N * N), cr = rem - dir * N * N, col = cr / N, row = cr - col * N;
+  const int x1 = (int)(j / L0), x0 = (int)(j - (long long)x1 * L0);
+  const long long rowo = (long long)x1 * L0;
+  long long src;
+  switch (dir) {
+    case 0: src = j; break;
+    case 1: src = rowo + (x0 + 1 == L0 ? 0 : x0 + 1); break;
+    case 2: src = rowo + (x0 == 0 ? L0 - 1 : x0 - 1); break;
+    case 3: src = (x1 + 1 == L1 ? 0 : rowo + L0) + x0; break;
+    default: src = (x1 == 0 ? (long long)(L1 - 1) * L0 : rowo - L0) + x0; break;
+  }
+  const Cx<double> *Yd = Y + (j * 5 + dir) * (long long)N * N;
+  const Cx<double> *Ms = Minv + src * (long long)N * N;
+  Cx<double> acc = mk(0.0, 0.0);
+  for (int q = 0; q < N; ++q) cmac(acc, Yd[(long long)q * N + row], Ms[(long long)col * N + q]);
+  Yt[t] = acc;
+}
+
+void prepare_coarsest_gcr(const Cx<double> *Y, Geo2 g, int N, Cx<double> *Minv, Cx<double> *Yt, Cx<double> *work,
+                          int *info_dev, cudaStream_t s) {
+  MG_CUDA(cudaMemsetAsync(info_dev, 0, sizeof(int), s));
+  self_block_inverse_kernel<<<grid_for(g.nsites, 128), 128, 0, s>>>(Y, Minv, work, g.nsites, N, info_dev);
+  MG_LAUNCHED();
+  precondition_stencil_kernel<<<grid_for(g.nsites * 5LL * N * N, 256), 256, 0, s>>>(Y, Minv, Yt, g.L0, g.L1, N);
+  MG_LAUNCHED();
+}
+
+int coarsest_gcr_grid(int device) {
+  int sms = 0;
+  MG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  return sms;
+}
+
+void launch_coarsest_gcr(const Cx<double> *Yt, const Cx<double> *Minv, Geo2 g, int N, const Cx<double> *b,
+                         Cx<double> *x, Cx<double> *y, Cx<double> *r, Cx<double> *Z, Cx<double> *W, double *partials,
+                         unsigned int *bar, double tol, int restart, int max_iter, int *out, double *out_rel, int grid,
+                         cudaStream_t s) {
+  if (restart > kMaxRestart) fail(MG_ERR_INVALID_ARG, "coarsest restart exceeds 32");
+  CgArgs a;
+  a.Y = Yt;
+  a.Minv = Minv;
+  a.L0 = g.L0;
+  a.L1 = g.L1;
+  a.N = N;
+  a.n = g.nsites * N;
+  a.b = b;
+  a.x = x;
+  a.y = y;
+  a.r = r;
+  a.Z = Z;
+  a.W = W;
+  a.partials = partials;
+  a.bar = bar;
+  a.tol = tol;
+  a.restart = restart;
+  a.max_iter = max_iter;
+  a.spin_limit = 1LL << 24;  // about a second of polling
+  a.out = out;
+  a.out_rel = out_rel;
+  long long per = (a.n + grid - 1) / grid;
+  int threads = (int)((per + 31) / 32) * 32;
+  if (threads < 64) threads = 64;
+  if (threads > 256) threads = 256;
+  const size_t smem = (size_t)(9 + grid) * kSlots * sizeof(double);
+  const void *fn = (N == 8) ? (const void *)coarsest_gcr_kernel<8> : (const void *)coarsest_gcr_kernel<0>;
+  MG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessorWithFlags(&per_sm, fn, threads, smem, 0));
+  if (per_sm < 1) fail(MG_ERR_CUDA, "coarsest solve kernel cannot be resident");
+  MG_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s));
+  void *args[] = {&a};
+  MG_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, smem, s));
+  MG_LAUNCHED();
+}
+
+}  // namespace mg

@@ -96,4 +96,19 @@ void lu_factor(Cx<double> *A, int n, int *ipiv, int *info_dev, cudaStream_t s);
 void lu_solve_ws(const Cx<double> *LU, const int *ipiv, int n, const Cx<double> *b, Cx<double> *x, Cx<double> *work,
                  cudaStream_t s);
 
+// ---- coarsest level: restarted GCR as one persistent cooperative kernel (FP64) ----
+// Preparation: Minv[j] = X_j^{-1} (self blocks) and Yt = stencil of A M, M = blockdiag(Minv);
+// work: nsites * 2 N^2 entries; info_dev[0] = 1 if a self block is singular.
+void prepare_coarsest_gcr(const Cx<double> *Y, Geo2 g, int N, Cx<double> *Minv, Cx<double> *Yt, Cx<double> *work,
+                          int *info_dev, cudaStream_t s);
+// x = A^{-1} b to relative true residual tol (GCR on A M y = b, x = M y); y, r: n entries;
+// Z/W: restart * n each (restart <= 32); partials: grid * kCoarsestSlots doubles; bar: 2 uints;
+// out[0] += iterations, out[1] = 1 on a barrier timeout, out[2] += 1 if the tolerance was missed.
+void launch_coarsest_gcr(const Cx<double> *Yt, const Cx<double> *Minv, Geo2 g, int N, const Cx<double> *b,
+                         Cx<double> *x, Cx<double> *y, Cx<double> *r, Cx<double> *Z, Cx<double> *W, double *partials,
+                         unsigned int *bar, double tol, int restart, int max_iter, int *out, double *out_rel, int grid,
+                         cudaStream_t s);
+int coarsest_gcr_grid(int device);
+constexpr int kCoarsestSlots = 68;
+
 }  // namespace mg

@@ -11,6 +11,7 @@
 // Every arithmetic step runs in the kernels of this library on the context's
 // stream; the host only sequences launches and reads convergence scalars.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <vector>
@@ -57,13 +58,27 @@ enum : int {
 };
 constexpr int kBeta = 0, kNrm = 300, kAlpha = 304, kRnrm = 308, kBnrm = 312;
 
+// an instantiated graph of one V-cycle with the launches and operator
+// applications it replays
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;
+  long long apps[MG_MAX_LEVELS] = {0, 0, 0, 0};
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+  }
+};
+
 }  // namespace mg
 
 struct mg_ctx {
   mg_geom geom{};
   mg_params p{};
   double m = 0.0;
-  cudaStream_t s = nullptr;
+  cudaStream_t s = nullptr;      // the context's own stream (all library work)
+  cudaStream_t user = nullptr;   // the caller's stream given to mg_setup
+  cudaEvent_t ev = nullptr;      // orders the context stream after the caller's stream
   std::vector<mg::Level> lv;
   mg::DevBuf<mg::Cx<double>> U64;
   mg::DevBuf<mg::Cx<float>> U32;
@@ -73,6 +88,12 @@ struct mg_ctx {
   mg::DevBuf<mg::Cx<double>> LU, lu_work;
   mg::DevBuf<int> ipiv, info;
   mg::DevBuf<mg::Cx<double>> cZ, cW, cr, cb, cx;
+  mg::DevBuf<double> cg_partials, cg_rel;
+  mg::DevBuf<mg::Cx<double>> cg_Minv, cg_Yt, cg_work, cg_y;
+  mg::DevBuf<int> cg_info;
+  mg::DevBuf<unsigned int> cg_bar;
+  mg::DevBuf<int> cg_out;  // [0] iterations, [1] timeout flag, [2] solves above tolerance
+  int cg_grid = 0;
   // outer
   mg::DevBuf<mg::Cx<double>> oZ, oW, orr;
   mg::DevBuf<mg::Cx<float>> z32;
@@ -83,7 +104,16 @@ struct mg_ctx {
   double *host = nullptr;  // pinned scalars
   long long apps[MG_MAX_LEVELS] = {0, 0, 0, 0};
   long long coarsest_iters = 0;
+  // CUDA graphs of the V-cycle: preconditioner (per precision) and setup cycles (per level)
+  mg::GraphCache pre[2];
+  mg::GraphCache setup_vc[MG_MAX_LEVELS];
+  bool graphs_ok = true;
+  mg::DevBuf<mg::Cx<double>> z64;
   ~mg_ctx() {
+    for (auto &g : pre) g.reset();
+    for (auto &g : setup_vc) g.reset();
+    if (s) cudaStreamDestroy(s);
+    if (ev) cudaEventDestroy(ev);
     if (host) cudaFreeHost(host);
   }
 };
@@ -226,10 +256,21 @@ static void coarsest_solve64(mg_ctx &c, const Cx<double> *b, Cx<double> *x) {
     c.apps[l]++;
     return;
   }
-  auto none = [](const Cx<double> *, Cx<double> *) {};
-  GcrOut o = gcr<double>(c, l, b, x, c.p.coarsest_tol, c.p.coarsest_restart, c.p.coarsest_max_iter, c.cZ.p, c.cW.p,
-                         c.cr.p, kSlotCoarse, none, false);
-  c.coarsest_iters += o.iters;
+  const Level &L = c.lv[l];
+  launch_coarsest_gcr(c.cg_Yt.p, c.cg_Minv.p, L.geo, L.nint, b, x, c.cg_y.p, c.cr.p, c.cZ.p, c.cW.p,
+                      c.cg_partials.p, c.cg_bar.p, c.p.coarsest_tol, c.p.coarsest_restart, c.p.coarsest_max_iter,
+                      c.cg_out.p, c.cg_rel.p, c.cg_grid, c.s);
+}
+
+// iterations of the persistent coarsest solves since the last reset; fails on a barrier timeout
+static long long collect_coarsest(mg_ctx &c) {
+  if (c.use_lu) return 0;
+  int out[3] = {0, 0, 0};
+  MG_CUDA(cudaMemcpyAsync(out, c.cg_out.p, sizeof(out), cudaMemcpyDeviceToHost, c.s));
+  MG_CUDA(cudaStreamSynchronize(c.s));
+  MG_CUDA(cudaMemsetAsync(c.cg_out.p, 0, 3 * sizeof(int), c.s));
+  if (out[1] != 0) fail(MG_ERR_TIMEOUT, "coarsest solve: a grid barrier wait ran out (kernel returned early)");
+  return out[0];
 }
 
 template <typename R>
@@ -276,15 +317,74 @@ static void vcycle(mg_ctx &c, int l, const Cx<R> *b, Cx<R> *x) {
   smooth<R>(c, l, w.r.p, x, w.r.p, w.Ar.p, c.p.nu_post, true);
 }
 
-// z = V r on the finest level in the context precision (r, z FP64)
+// Runs `body` (a fixed sequence of launches on the context stream) through a
+// CUDA graph captured on first use; later calls replay it. When capture is not
+// possible the body runs as ordinary launches.
+template <typename F>
+static void graph_run(mg_ctx &c, GraphCache &g, F &&body) {
+  if (c.graphs_ok && g.exec == nullptr) {
+    const long long l0 = g_launches.load();
+    long long a0[MG_MAX_LEVELS];
+    for (int l = 0; l < MG_MAX_LEVELS; ++l) a0[l] = c.apps[l];
+    bool ok = cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      try {
+        body();
+      } catch (const Error &) {
+        ok = false;
+      }
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(c.s, &graph);
+      ok = ok && e == cudaSuccess && graph != nullptr;
+      if (ok) ok = cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess;
+      if (ok) {
+        size_t nn = 0;
+        cudaGraphGetNodes(graph, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        cudaGraphGetNodes(graph, nodes.data(), &nn);
+        long long k = 0;
+        for (auto nd : nodes) {
+          cudaGraphNodeType t;
+          if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+        }
+        g.kernels = k;
+        for (int l = 0; l < MG_MAX_LEVELS; ++l) g.apps[l] = c.apps[l] - a0[l];
+      }
+      if (graph) cudaGraphDestroy(graph);
+    }
+    (void)cudaGetLastError();
+    g_launches.store(l0);
+    for (int l = 0; l < MG_MAX_LEVELS; ++l) c.apps[l] = a0[l];
+    if (!ok) {
+      g.reset();
+      c.graphs_ok = false;
+    }
+  }
+  if (g.exec != nullptr) {
+    MG_CUDA(cudaGraphLaunch(g.exec, c.s));
+    g_launches.fetch_add(g.kernels);
+    for (int l = 0; l < MG_MAX_LEVELS; ++l) c.apps[l] += g.apps[l];
+  } else {
+    body();
+  }
+}
+
+// z = V r on the finest level in the context precision (r, z FP64). The cycle
+// reads r from the fixed buffer `rfix` (the outer residual) and leaves its result
+// in a fixed buffer, so one captured graph serves every call.
 static void precondition(mg_ctx &c, const Cx<double> *r, Cx<double> *z) {
   Level &F = c.lv[0];
+  const Cx<double> *rfix = c.orr.p;
+  if (r != rfix) launch_copy<double>(r, c.orr.p, F.n, c.s);
   if (c.p.precision == MG_FP32) {
-    launch_convert<float, double>(r, F.w32.b.p, F.n, c.s);
-    vcycle<float>(c, 0, F.w32.b.p, c.z32.p);
+    graph_run(c, c.pre[1], [&] {
+      launch_convert<float, double>(rfix, F.w32.b.p, F.n, c.s);
+      vcycle<float>(c, 0, F.w32.b.p, c.z32.p);
+    });
     launch_convert<double, float>(c.z32.p, z, F.n, c.s);
   } else {
-    vcycle<double>(c, 0, r, z);
+    graph_run(c, c.pre[0], [&] { vcycle<double>(c, 0, rfix, c.z64.p); });
+    launch_copy<double>(c.z64.p, z, F.n, c.s);
   }
 }
 
@@ -293,7 +393,14 @@ static void precondition(mg_ctx &c, const Cx<double> *r, Cx<double> *z) {
 // ---------------------------------------------------------------------------
 static void prepare_coarsest(mg_ctx &c) {
   Level &L = c.lv.back();
-  if (!c.use_lu) return;
+  if (!c.use_lu) {
+    prepare_coarsest_gcr(L.Y64.p, L.geo, L.nint, c.cg_Minv.p, c.cg_Yt.p, c.cg_work.p, c.cg_info.p, c.s);
+    int info = 0;
+    MG_CUDA(cudaMemcpyAsync(&info, c.cg_info.p, sizeof(int), cudaMemcpyDeviceToHost, c.s));
+    MG_CUDA(cudaStreamSynchronize(c.s));
+    if (info != 0) fail(MG_ERR_NAN, "coarsest level: a self block is singular");
+    return;
+  }
   launch_dense_from_stencil(L.Y64.p, c.LU.p, L.geo, L.nint, c.s);
   lu_factor(c.LU.p, c.nc, c.ipiv.p, c.info.p, c.s);
   int info = 0;
@@ -335,7 +442,7 @@ static void setup_level(mg_ctx &c, int l, bool full) {
       for (int k = 0; k < L.Nv; ++k) {
         Cx<double> *v = L.nullv.p + (long long)k * n;
         apply_op<double>(c, l, v, L.tA.p);
-        vcycle<double>(c, l, L.tA.p, L.tB.p);
+        graph_run(c, c.setup_vc[l], [&] { vcycle<double>(c, l, L.tA.p, L.tB.p); });
         launch_xmy<double>(v, L.tB.p, n, c.s);  // tB = v - V(A v)
         launch_copy<double>(L.tB.p, v, n, c.s);
       }
@@ -367,8 +474,9 @@ static void validate(const mg_geom *g, const mg_params *p) {
   if (p->levels < 2 || p->levels > MG_MAX_LEVELS) fail(MG_ERR_INVALID_ARG, "levels must be in [2, 4]");
   if (p->precision != MG_FP64 && p->precision != MG_FP32) fail(MG_ERR_INVALID_ARG, "unknown precision");
   if (p->n_pass < 1 || p->nu_pre < 0 || p->nu_post < 0 || p->nu_setup < 0) fail(MG_ERR_INVALID_ARG, "bad counts");
-  if (p->gcr_restart < 1 || p->gcr_restart > 128 || p->coarsest_restart < 1 || p->coarsest_restart > 128)
-    fail(MG_ERR_INVALID_ARG, "restart lengths must be in [1, 128]");
+  if (p->gcr_restart < 1 || p->gcr_restart > 128) fail(MG_ERR_INVALID_ARG, "gcr_restart must be in [1, 128]");
+  if (p->coarsest_restart < 1 || p->coarsest_restart > 32)
+    fail(MG_ERR_INVALID_ARG, "coarsest_restart must be in [1, 32]");
   if (p->max_iter < 1 || p->coarsest_max_iter < 1) fail(MG_ERR_INVALID_ARG, "iteration limits must be >= 1");
   int L0 = g->dims[0], L1 = g->dims[1], nint = 2;
   for (int l = 0; l + 1 < p->levels; ++l) {
@@ -384,13 +492,24 @@ static void validate(const mg_geom *g, const mg_params *p) {
   }
 }
 
+// order the context stream after the caller's stream (work the caller queued
+// before this call, e.g. writing the inputs, completes first)
+static void enter(mg_ctx &c) {
+  MG_CUDA(cudaEventRecord(c.ev, c.user));
+  MG_CUDA(cudaStreamWaitEvent(c.s, c.ev, 0));
+}
+
 static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_params *p, void *stream) {
   validate(g, p);
   auto c = std::make_unique<mg_ctx>();
   c->geom = *g;
   c->p = *p;
   c->m = m;
-  c->s = static_cast<cudaStream_t>(stream);
+  c->user = static_cast<cudaStream_t>(stream);
+  MG_CUDA(cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking));
+  MG_CUDA(cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming));
+  enter(*c);
+  c->graphs_ok = std::getenv("MG_NO_GRAPHS") == nullptr;
   MG_CUDA(cudaMallocHost(&c->host, 16 * sizeof(double)));
   c->lv.resize(p->levels);
   int L0 = g->dims[0], L1 = g->dims[1], nint = 2;
@@ -446,6 +565,19 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
     c->cZ.alloc((size_t)p->coarsest_restart * Cst.n);
     c->cW.alloc((size_t)p->coarsest_restart * Cst.n);
     c->cr.alloc(Cst.n);
+    int dev = 0;
+    MG_CUDA(cudaGetDevice(&dev));
+    c->cg_grid = coarsest_gcr_grid(dev);
+    c->cg_partials.alloc((size_t)c->cg_grid * kCoarsestSlots);
+    c->cg_bar.alloc(2);
+    c->cg_out.alloc(3);
+    c->cg_rel.alloc(1);
+    c->cg_Minv.alloc((size_t)Cst.geo.nsites * Cst.nint * Cst.nint);
+    c->cg_Yt.alloc((size_t)Cst.geo.nsites * 5 * Cst.nint * Cst.nint);
+    c->cg_work.alloc((size_t)Cst.geo.nsites * 2 * Cst.nint * Cst.nint);
+    c->cg_y.alloc(Cst.n);
+    c->cg_info.alloc(1);
+    MG_CUDA(cudaMemsetAsync(c->cg_out.p, 0, 3 * sizeof(int), c->s));
   }
   if (f32) {
     c->cb.alloc(Cst.n);
@@ -453,6 +585,7 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
     c->z32.alloc(F.n);
   }
   // outer
+  c->z64.alloc(F.n);
   c->oZ.alloc((size_t)p->gcr_restart * F.n);
   c->oW.alloc((size_t)p->gcr_restart * F.n);
   c->orr.alloc(F.n);
@@ -493,8 +626,10 @@ static int guarded(F &&f) {
   }
 }
 
+// every call on a context first orders the context stream after the caller's stream
 static void need_ctx(mg_ctx *c) {
   if (!c) fail(MG_ERR_INVALID_ARG, "null context");
+  enter(*c);
 }
 static void need_level(mg_ctx *c, int l, bool needs_next) {
   need_ctx(c);
@@ -527,7 +662,7 @@ void mg_default_params(mg_params *p) {
   p->max_iter = 500;
   p->coarsest_lu_max = 2048;
   p->coarsest_tol = 1e-12;
-  p->coarsest_restart = 64;
+  p->coarsest_restart = 32;
   p->coarsest_max_iter = 20000;
   p->precision = MG_FP64;
   p->seed = 20070704ULL;
@@ -546,6 +681,7 @@ int mg_setup(mg_ctx **ctx, const mg_geom *g, const void *U, double m, const mg_p
     MG_CUDA(cudaMemcpyAsync(c->U64.p, U, c->U64.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, c->s));
     setup_level(*c, 0, true);
     make_fp32_copies(*c);
+    collect_coarsest(*c);
     MG_CUDA(cudaStreamSynchronize(c->s));
     *ctx = c.release();
   });
@@ -559,6 +695,7 @@ int mg_solve(mg_ctx *c, const void *chi, void *psi, double tol, mg_stats *st) {
     need_ptr(psi);
     check_fresh(*c);
     for (long long &a : c->apps) a = 0;
+    collect_coarsest(*c);
     c->coarsest_iters = 0;
     cudaEvent_t e0, e1;
     MG_CUDA(cudaEventCreate(&e0));
@@ -569,6 +706,8 @@ int mg_solve(mg_ctx *c, const void *chi, void *psi, double tol, mg_stats *st) {
                            c->p.gcr_restart, c->p.max_iter, c->oZ.p, c->oW.p, c->orr.p, kSlotOuter, pre, true);
     MG_CUDA(cudaEventRecord(e1, c->s));
     MG_CUDA(cudaEventSynchronize(e1));
+    c->coarsest_iters = collect_coarsest(*c);
+    if (!c->use_lu) c->apps[c->p.levels - 1] += c->coarsest_iters;
     float ms = 0.f;
     MG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     cudaEventDestroy(e0);
@@ -580,6 +719,7 @@ int mg_solve(mg_ctx *c, const void *chi, void *psi, double tol, mg_stats *st) {
       for (int l = 0; l < MG_MAX_LEVELS; ++l) st->level_apps[l] = c->apps[l];
       st->coarsest_iters = c->coarsest_iters;
       st->ms = ms;
+      st->graphs = (c->graphs_ok && c->pre[c->p.precision == MG_FP32 ? 1 : 0].exec != nullptr) ? 1 : 0;
     }
     if (!o.converged) status = MG_ERR_NOT_CONVERGED;
   });
@@ -613,6 +753,7 @@ void mg_destroy(mg_ctx *c) {
   cudaStreamSynchronize(c->s);
   delete c;
 }
+
 
 int mg_dslash(const mg_geom *g, const void *U, double m, const void *in, void *out, int precision, void *stream) {
   return guarded([&] {
