@@ -186,6 +186,22 @@ int mg_get_prolongator(mg_ctx *ctx, int level, void *out);
 int mg_get_coarse_op(mg_ctx *ctx, int level, void *out);
 int mg_level_size(mg_ctx *ctx, int level, long long *n_sites, int *n_int);
 
+/* Fine-level MR smoother that allocates nothing: x = nu MR iterations (omega) for
+ * D(U) x = b from x = 0, the same computation as mg_smooth at level 0, for callers
+ * that cannot allocate device memory when they smooth (inside a stream capture, or
+ * under a framework that owns the whole memory pool). The paper has no counterpart;
+ * this is a library convenience.
+ *   g: d = 2, Nc = 1, at most 65536 sites (256 x 256); larger lattices are rejected
+ *      with MG_ERR_INVALID_ARG before any device work.
+ *   U, b, x: device complex128 ([x][mu], [x][s], [x][s]); b and x must not alias.
+ *   stream: cudaStream_t; the call is asynchronous on it.
+ * Scratch lives in one fixed device array (about 4 MB, held on every GPU that
+ * loads the library until exit), shared by all calls on a device; calls whose
+ * work overlaps on the GPU race on it. The first call on a device looks up the
+ * array's device address; make that first call before any stream capture. */
+int mg_smooth_fine_noalloc(const mg_geom *g, const void *U, double m, const void *b, void *x, int nu, double omega,
+                           void *stream);
+
 /* Number of kernels this library has launched since the process started. */
 long long mg_kernel_launches(void);
 

@@ -88,6 +88,7 @@ def load():
         "mg_get_coarse_op": (I, [ctxp, I, VP]),
         "mg_level_size": (I, [ctxp, I, P(ctypes.c_longlong), P(I)]),
         "mg_kernel_launches": (ctypes.c_longlong, []),
+        "mg_smooth_fine_noalloc": (I, [P(mg_geom), VP, D, VP, VP, I, D, VP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -101,7 +102,8 @@ def exported_symbols():
     """Names of the C ABI entry points this binding expects."""
     return ["mg_default_params", "mg_setup", "mg_solve", "mg_update_mass", "mg_destroy", "mg_last_error",
             "mg_dslash", "mg_level_apply", "mg_restrict", "mg_prolong", "mg_vcycle", "mg_smooth", "mg_build_level",
-            "mg_get_null_vectors", "mg_get_prolongator", "mg_get_coarse_op", "mg_level_size", "mg_kernel_launches"]
+            "mg_get_null_vectors", "mg_get_prolongator", "mg_get_coarse_op", "mg_level_size", "mg_kernel_launches",
+            "mg_smooth_fine_noalloc"]
 
 
 def _check(code: int):
@@ -162,6 +164,16 @@ def mg_dslash(U: torch.Tensor, inp: torch.Tensor, out: torch.Tensor, m: float, d
     g = make_geom(dims)
     _check(load().mg_dslash(ctypes.byref(g), _ptr(U, dt, 2 * V), float(m), _ptr(inp, dt, 2 * V),
                             _ptr(out, dt, 2 * V), precision, _stream(stream)))
+
+
+def mg_smooth_fine_noalloc(U: torch.Tensor, b: torch.Tensor, x: torch.Tensor, m: float, dims, nu: int,
+                           omega: float = 0.8, stream=None):
+    """x = nu MR iterations on D(U) x = b, with no device allocation (lattices up to 256 x 256)."""
+    V = int(dims[0]) * int(dims[1])
+    g = make_geom(dims)
+    _check(load().mg_smooth_fine_noalloc(ctypes.byref(g), _ptr(U, torch.complex128, 2 * V), float(m),
+                                         _ptr(b, torch.complex128, 2 * V), _ptr(x, torch.complex128, 2 * V),
+                                         int(nu), float(omega), _stream(stream)))
 
 
 def mg_kernel_launches() -> int:

@@ -6,6 +6,9 @@
 
 namespace mg {
 
+// message returned by mg_last_error() on this thread
+void set_last_error(const std::string &msg);
+
 // ---- fine Wilson operator (2d, U(1), gamma_1 = sigma_1, gamma_2 = sigma_2) ----
 // out = a * D in + c * b   (b may be null when c == 0); D has diagonal `diag` = d + m
 template <typename R>

@@ -24,6 +24,8 @@ std::atomic<long long> g_launches{0};
 
 static thread_local std::string t_last_error;
 
+void set_last_error(const std::string &msg) { t_last_error = msg; }
+
 template <typename R>
 struct Work {
   DevBuf<Cx<R>> b, x, r, Ar;
