@@ -111,7 +111,7 @@ typedef struct mg_ctx mg_ctx;
 
 /* Defaults: 2 levels, 4x4 blocks, Nv = 8, MR 4 + 4 with omega = 0.8, 5 passes,
  * nu_setup = 8, GCR(16), max_iter 500, coarsest LU up to 2048, coarsest GCR
- * tol 1e-12 / restart 32 / 20000 iterations, FP64, seed 20070704. */
+ * tol 1e-12 / restart 16 / 20000 iterations, FP64, seed 20070704. */
 void mg_default_params(mg_params *p);
 
 /*

@@ -48,7 +48,7 @@ class MGParams:
     max_iter: int = 500
     coarsest_lu_max: int = 2048
     coarsest_tol: float = 1e-12
-    coarsest_restart: int = 32
+    coarsest_restart: int = 16
     coarsest_max_iter: int = 20000
     seed: int = 20070704
 

@@ -429,3 +429,364 @@ void launch_coarsest_gcr(const Cx<double> *Yt, const Cx<double> *Minv, Geo2 g, i
 }
 
 }  // namespace mg
+
+namespace mg {
+
+// ---------------------------------------------------------------------------
+// Shared-memory-resident variant for small coarsest systems (N = 8, at most
+// 8 coarse sites = 64 dofs per CTA, restart <= 16). Each CTA owns whole coarse
+// sites and keeps, for the whole solve, its rows of A M, its blocks of M, its
+// chunks of b, r, y and of the Krylov basis Z, W in shared memory; only r (and
+// y at restarts) is published to global memory for the neighbours' stencil
+// reads. Gram-Schmidt is classical with the Pythagorean norm; a second pass
+// runs only when |w'|^2 < |w|^2 / 2 (the decision is made from the same grid
+// sums in every CTA, so all CTAs take the same branch). A typical iteration
+// costs 2 grid barriers: after the stencil + dot products, after the update.
+// ---------------------------------------------------------------------------
+constexpr int kSmMaxDofs = 64;
+constexpr int kSmMaxRestart = 16;
+constexpr int kSmSlots = 2 * kSmMaxRestart + 4;  // |w|^2, <w, r>, then 2 per basis vector
+
+struct Cg3Args {
+  const Cx<double> *Yt;    // A M, internal layout [j][dir][col][row], N = 8
+  const Cx<double> *Minv;  // [j][col][row]
+  int L0, L1;
+  long long nsites;
+  int spc;  // sites per CTA
+  const Cx<double> *b;
+  Cx<double> *x, *rpub, *ypub;
+  double *partials;
+  unsigned int *bar;
+  double tol;
+  int restart, max_iter;
+  long long spin_limit;
+  int *out;
+  double *out_rel;
+};
+
+__device__ __forceinline__ void grid_sync3(const Cg3Args &a, bool &ok) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int *gen = a.bar + 1;
+    const unsigned int g = *gen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(a.bar, 1u);
+    int good = 1;
+    if (arrived == gridDim.x - 1) {
+      atomicExch(a.bar, 0u);
+      __threadfence();
+      atomicAdd(a.bar + 1, 1u);
+    } else {
+      long long polls = 0;
+      while (*gen == g) {
+        if (++polls > a.spin_limit) {
+          good = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    if (!good) atomicExch(a.out + 1, 1);
+    s_ok = good;
+  }
+  __syncthreads();
+  ok = ok && s_ok;
+}
+
+// cpart[0..nv) holds this CTA's sums; publish, barrier, stage every CTA's
+// partials, sum each slot in CTA order into sres
+__device__ __forceinline__ void grid_sum3(const Cg3Args &a, int nv, const double *cpart, double *stage, double *sres,
+                                          bool &ok) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  for (int s = threadIdx.x; s < nv; s += blockDim.x) a.partials[(long long)blockIdx.x * kSmSlots + s] = cpart[s];
+  __threadfence();
+  grid_sync3(a, ok);
+  const int total = (int)gridDim.x * nv;
+  for (int q = threadIdx.x; q < total; q += blockDim.x) {
+    const int c = q / nv, s = q - c * nv;
+    stage[q] = __ldcg(a.partials + (long long)c * kSmSlots + s);
+  }
+  __syncthreads();
+  for (int s = wid; s < nv; s += nw) {
+    double t = 0.0;
+    for (unsigned int c = lane; c < gridDim.x; c += 32) t += stage[c * nv + s];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) sres[s] = t;
+  }
+  __syncthreads();
+}
+
+// out[d] = (A M v)_d for the CTA's rows, v read from global (published) memory;
+// 4 threads per row, 10 of the 40 (dir, col) terms each, combined by shuffles
+__device__ __forceinline__ void stencil_rows(const Cg3Args &a, const Cx<double> *Ys, const Cx<double> *v,
+                                             long long site0, int nd, Cx<double> *outs) {
+  const int t = threadIdx.x, d = t >> 2, q = t & 3;
+  Cx<double> acc = mk(0.0, 0.0);
+  if (d < nd) {
+    const long long j = site0 + (d >> 3);
+    const int x1 = (int)(j / a.L0), x0 = (int)(j - (long long)x1 * a.L0);
+    const long long rowo = (long long)x1 * a.L0;
+    long long src[5];
+    src[0] = j;
+    src[1] = rowo + (x0 + 1 == a.L0 ? 0 : x0 + 1);
+    src[2] = rowo + (x0 == 0 ? a.L0 - 1 : x0 - 1);
+    src[3] = (x1 + 1 == a.L1 ? 0 : rowo + a.L0) + x0;
+    src[4] = (x1 == 0 ? (long long)(a.L1 - 1) * a.L0 : rowo - a.L0) + x0;
+#pragma unroll
+    for (int u = 0; u < 10; ++u) {
+      const int term = q * 10 + u, dir = term >> 3, col = term & 7;
+      const double2 vv = __ldcg(reinterpret_cast<const double2 *>(v + src[dir] * 8 + col));
+      cmac(acc, Ys[(d * 5 + dir) * 8 + col], mk(vv.x, vv.y));
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < 4; o <<= 1) {
+    acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
+    acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
+  }
+  if (d < nd && q == 0) outs[d] = acc;
+}
+
+// CTA-local sums: slot 0 |w|^2, slots 1, 2 <w, r>, slots 3 + 2j, 4 + 2j <W_j, w> (j < k);
+// one warp per dot product, lanes over the CTA's dofs
+__device__ __forceinline__ void cta_dots(int k, int nd, const Cx<double> *Ws, const Cx<double> *w,
+                                         const Cx<double> *rs, double *cpart) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int t = wid; t < k + 2; t += nw) {
+    double re = 0.0, im = 0.0;
+    for (int d = lane; d < nd; d += 32) {
+      const Cx<double> wd = w[d];
+      if (t == 0) {
+        re += norm2(wd);
+      } else {
+        const Cx<double> u = (t == 1) ? wd : Ws[(t - 2) * kSmMaxDofs + d];
+        const Cx<double> v = (t == 1) ? rs[d] : wd;
+        re += u.re * v.re + u.im * v.im;
+        im += u.re * v.im - u.im * v.re;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) {
+      if (t == 0) {
+        cpart[0] = re;
+      } else if (t == 1) {
+        cpart[1] = re;
+        cpart[2] = im;
+      } else {
+        cpart[3 + 2 * (t - 2)] = re;
+        cpart[4 + 2 * (t - 2)] = im;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256, 1) coarsest_gcr_smem_kernel(Cg3Args a) {
+  extern __shared__ double sm3[];
+  Cx<double> *Ys = reinterpret_cast<Cx<double> *>(sm3);  // [64 rows][5][8]
+  Cx<double> *Ms = Ys + kSmMaxDofs * 40;                  // [8 sites][64]
+  Cx<double> *bs = Ms + 8 * 64;
+  Cx<double> *rs = bs + kSmMaxDofs;
+  Cx<double> *ys = rs + kSmMaxDofs;
+  Cx<double> *Zs = ys + kSmMaxDofs;                       // [16][64]
+  Cx<double> *Ws = Zs + kSmMaxRestart * kSmMaxDofs;       // [16][64]
+  double *cpart = reinterpret_cast<double *>(Ws + kSmMaxRestart * kSmMaxDofs);  // [kSmSlots]
+  double *sres = cpart + kSmSlots;
+  double *stage = sres + kSmSlots;                        // [G][kSmSlots]
+  const int tid = threadIdx.x;
+  const long long site0 = blockIdx.x * (long long)a.spc;
+  long long ns = a.nsites - site0;
+  if (ns > a.spc) ns = a.spc;
+  if (ns < 0) ns = 0;
+  const int nd = (int)ns * 8;
+  const long long dof0 = site0 * 8;
+  bool ok = true;
+
+  for (int q = tid; q < nd * 40; q += blockDim.x) {
+    const int d = q / 40, rem = q - d * 40, dir = rem >> 3, col = rem & 7;
+    const long long j = site0 + (d >> 3);
+    Ys[q] = a.Yt[(j * 5 + dir) * 64 + col * 8 + (d & 7)];
+  }
+  for (int q = tid; q < (int)ns * 64; q += blockDim.x) Ms[q] = a.Minv[site0 * 64 + q];
+  for (int d = tid; d < nd; d += blockDim.x) {
+    const Cx<double> bd = a.b[dof0 + d];
+    bs[d] = bd;
+    rs[d] = bd;
+    ys[d] = mk(0.0, 0.0);
+    a.rpub[dof0 + d] = bd;
+  }
+  __syncthreads();
+  // |b|^2
+  if (tid < 32) {
+    double t = 0.0;
+    for (int d = tid; d < nd; d += 32) t += norm2(bs[d]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (tid == 0) cpart[0] = t;
+  }
+  grid_sum3(a, 1, cpart, stage, sres, ok);
+  if (!ok) return;
+  const double bn2 = sres[0];
+  const double tol2 = a.tol * a.tol * bn2;
+  int it = 0;
+  bool converged = !(bn2 > 0.0);
+  double rn2 = bn2;
+  while (!converged && it < a.max_iter) {
+    for (int k = 0; k < a.restart && it < a.max_iter; ++k) {
+      Cx<double> *Wk = Ws + k * kSmMaxDofs, *Zk = Zs + k * kSmMaxDofs;
+      // w_k = (A M) r (neighbours from the published r), z_k = r
+      stencil_rows(a, Ys, a.rpub, site0, nd, Wk);
+      for (int d = tid; d < nd; d += blockDim.x) Zk[d] = rs[d];
+      __syncthreads();
+      cta_dots(k, nd, Ws, Wk, rs, cpart);
+      grid_sum3(a, 3 + 2 * k, cpart, stage, sres, ok);
+      if (!ok) return;
+      double nw0 = sres[0];
+      double nw2 = nw0;
+      for (int j = 0; j < k; ++j) nw2 -= sres[3 + 2 * j] * sres[3 + 2 * j] + sres[4 + 2 * j] * sres[4 + 2 * j];
+      const double wr = sres[1], wi = sres[2];
+      // first projection
+      for (int d = tid; d < nd; d += blockDim.x) {
+        Cx<double> w = Wk[d], z = Zk[d];
+        for (int j = 0; j < k; ++j) {
+          const Cx<double> bj = mk(-sres[3 + 2 * j], -sres[4 + 2 * j]);
+          cmac(w, bj, Ws[j * kSmMaxDofs + d]);
+          cmac(z, bj, Zs[j * kSmMaxDofs + d]);
+        }
+        Wk[d] = w;
+        Zk[d] = z;
+      }
+      if (k > 0 && !(nw2 > 0.5 * nw0)) {
+        // cancellation: project once more against the basis (same branch in every CTA)
+        __syncthreads();
+        cta_dots(k, nd, Ws, Wk, rs, cpart);
+        grid_sum3(a, 3 + 2 * k, cpart, stage, sres, ok);
+        if (!ok) return;
+        nw2 = sres[0];
+        for (int j = 0; j < k; ++j) nw2 -= sres[3 + 2 * j] * sres[3 + 2 * j] + sres[4 + 2 * j] * sres[4 + 2 * j];
+        for (int d = tid; d < nd; d += blockDim.x) {
+          Cx<double> w = Wk[d], z = Zk[d];
+          for (int j = 0; j < k; ++j) {
+            const Cx<double> bj = mk(-sres[3 + 2 * j], -sres[4 + 2 * j]);
+            cmac(w, bj, Ws[j * kSmMaxDofs + d]);
+            cmac(z, bj, Zs[j * kSmMaxDofs + d]);
+          }
+          Wk[d] = w;
+          Zk[d] = z;
+        }
+      }
+      const bool breakdown = !(nw2 > 1e-28 * nw0);
+      const double inv = breakdown ? 0.0 : 1.0 / sqrt(nw2);
+      // <w', r> = <w, r> - sum conj(beta_j) <W_j, r>, and <W_j, r> vanishes (r is orthogonal to W_j)
+      const Cx<double> alpha = mk(wr * inv, wi * inv);
+      for (int d = tid; d < nd; d += blockDim.x) {
+        const Cx<double> w = inv * Wk[d], z = inv * Zk[d];
+        Wk[d] = w;
+        Zk[d] = z;
+        cmac(ys[d], alpha, z);
+        Cx<double> rd = rs[d];
+        cmac(rd, mk(-alpha.re, -alpha.im), w);
+        rs[d] = rd;
+        a.rpub[dof0 + d] = rd;
+      }
+      rn2 = fmax(rn2 - norm2(alpha), 0.0);
+      ++it;
+      __threadfence();
+      grid_sync3(a, ok);
+      if (!ok) return;
+      if (rn2 <= tol2 || breakdown) break;
+    }
+    // true residual r = b - (A M) y with the published y
+    for (int d = tid; d < nd; d += blockDim.x) a.ypub[dof0 + d] = ys[d];
+    __threadfence();
+    grid_sync3(a, ok);
+    if (!ok) return;
+    stencil_rows(a, Ys, a.ypub, site0, nd, rs);
+    __syncthreads();
+    for (int d = tid; d < nd; d += blockDim.x) {
+      const Cx<double> rd = bs[d] - rs[d];
+      rs[d] = rd;
+      a.rpub[dof0 + d] = rd;
+    }
+    __syncthreads();
+    if (tid < 32) {
+      double t = 0.0;
+      for (int d = tid; d < nd; d += 32) t += norm2(rs[d]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (tid == 0) cpart[0] = t;
+    }
+    __threadfence();
+    grid_sum3(a, 1, cpart, stage, sres, ok);
+    if (!ok) return;
+    rn2 = sres[0];
+    converged = rn2 <= tol2;
+    if (!(rn2 == rn2)) break;
+  }
+  // x = M y on the CTA's sites (site-local)
+  for (int d = tid; d < nd; d += blockDim.x) {
+    const int sl = d >> 3, row = d & 7;
+    Cx<double> acc = mk(0.0, 0.0);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) cmac(acc, Ms[sl * 64 + c * 8 + row], ys[sl * 8 + c]);
+    a.x[dof0 + d] = acc;
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    atomicAdd(a.out, it);
+    if (!converged) atomicAdd(a.out + 2, 1);
+    a.out_rel[0] = bn2 > 0.0 ? sqrt(rn2 / bn2) : 0.0;
+  }
+}
+
+bool coarsest_smem_fits(Geo2 g, int N, int restart, int sms) {
+  if (N != 8 || restart > kSmMaxRestart) return false;
+  const long long spc = (g.nsites + sms - 1) / sms;
+  return spc * 8 <= kSmMaxDofs;
+}
+
+void launch_coarsest_gcr_smem(const Cx<double> *Yt, const Cx<double> *Minv, Geo2 g, const Cx<double> *b,
+                              Cx<double> *x, Cx<double> *rpub, Cx<double> *ypub, double *partials, unsigned int *bar,
+                              double tol, int restart, int max_iter, int *out, double *out_rel, int sms,
+                              cudaStream_t s) {
+  Cg3Args a;
+  a.Yt = Yt;
+  a.Minv = Minv;
+  a.L0 = g.L0;
+  a.L1 = g.L1;
+  a.nsites = g.nsites;
+  a.spc = (int)((g.nsites + sms - 1) / sms);
+  const int grid = (int)((g.nsites + a.spc - 1) / a.spc);
+  a.b = b;
+  a.x = x;
+  a.rpub = rpub;
+  a.ypub = ypub;
+  a.partials = partials;
+  a.bar = bar;
+  a.tol = tol;
+  a.restart = restart;
+  a.max_iter = max_iter;
+  a.spin_limit = 1LL << 24;
+  a.out = out;
+  a.out_rel = out_rel;
+  const size_t smem = (size_t)(kSmMaxDofs * 40 + 8 * 64 + 3 * kSmMaxDofs + 2 * kSmMaxRestart * kSmMaxDofs) *
+                          sizeof(Cx<double>) +
+                      (size_t)(2 + grid) * kSmSlots * sizeof(double);
+  const void *fn = (const void *)coarsest_gcr_smem_kernel;
+  MG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessorWithFlags(&per_sm, fn, 256, smem, 0));
+  if (per_sm < 1) fail(MG_ERR_CUDA, "coarsest solve kernel (shared-memory variant) cannot be resident");
+  MG_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s));
+  void *args[] = {&a};
+  MG_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, smem, s));
+  MG_LAUNCHED();
+}
+
+}  // namespace mg

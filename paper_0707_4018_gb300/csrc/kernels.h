@@ -113,5 +113,13 @@ void launch_coarsest_gcr(const Cx<double> *Yt, const Cx<double> *Minv, Geo2 g, i
                          cudaStream_t s);
 int coarsest_gcr_grid(int device);
 constexpr int kCoarsestSlots = 68;
+// Same solve with each CTA's rows, vectors and Krylov basis resident in shared memory
+// (N = 8, restart <= 16, at most 64 dofs per CTA when spread over `sms` CTAs): rpub, ypub
+// are n-entry publication buffers for the neighbours' reads; 2 grid barriers per iteration.
+bool coarsest_smem_fits(Geo2 g, int N, int restart, int sms);
+void launch_coarsest_gcr_smem(const Cx<double> *Yt, const Cx<double> *Minv, Geo2 g, const Cx<double> *b,
+                              Cx<double> *x, Cx<double> *rpub, Cx<double> *ypub, double *partials, unsigned int *bar,
+                              double tol, int restart, int max_iter, int *out, double *out_rel, int sms,
+                              cudaStream_t s);
 
 }  // namespace mg

@@ -96,6 +96,7 @@ struct mg_ctx {
   mg::DevBuf<unsigned int> cg_bar;
   mg::DevBuf<int> cg_out;  // [0] iterations, [1] timeout flag, [2] solves above tolerance
   int cg_grid = 0;
+  bool cg_smem = false;  // shared-memory-resident coarsest solver
   // outer
   mg::DevBuf<mg::Cx<double>> oZ, oW, orr;
   mg::DevBuf<mg::Cx<float>> z32;
@@ -259,9 +260,14 @@ static void coarsest_solve64(mg_ctx &c, const Cx<double> *b, Cx<double> *x) {
     return;
   }
   const Level &L = c.lv[l];
-  launch_coarsest_gcr(c.cg_Yt.p, c.cg_Minv.p, L.geo, L.nint, b, x, c.cg_y.p, c.cr.p, c.cZ.p, c.cW.p,
-                      c.cg_partials.p, c.cg_bar.p, c.p.coarsest_tol, c.p.coarsest_restart, c.p.coarsest_max_iter,
-                      c.cg_out.p, c.cg_rel.p, c.cg_grid, c.s);
+  if (c.cg_smem)
+    launch_coarsest_gcr_smem(c.cg_Yt.p, c.cg_Minv.p, L.geo, b, x, c.cr.p, c.cg_y.p, c.cg_partials.p, c.cg_bar.p,
+                             c.p.coarsest_tol, c.p.coarsest_restart, c.p.coarsest_max_iter, c.cg_out.p, c.cg_rel.p,
+                             c.cg_grid, c.s);
+  else
+    launch_coarsest_gcr(c.cg_Yt.p, c.cg_Minv.p, L.geo, L.nint, b, x, c.cg_y.p, c.cr.p, c.cZ.p, c.cW.p,
+                        c.cg_partials.p, c.cg_bar.p, c.p.coarsest_tol, c.p.coarsest_restart, c.p.coarsest_max_iter,
+                        c.cg_out.p, c.cg_rel.p, c.cg_grid, c.s);
 }
 
 // iterations of the persistent coarsest solves since the last reset; fails on a barrier timeout
@@ -570,6 +576,8 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
     int dev = 0;
     MG_CUDA(cudaGetDevice(&dev));
     c->cg_grid = coarsest_gcr_grid(dev);
+    c->cg_smem = coarsest_smem_fits(Cst.geo, Cst.nint, p->coarsest_restart, c->cg_grid) &&
+                 std::getenv("MG_NO_SMEM_COARSEST") == nullptr;
     c->cg_partials.alloc((size_t)c->cg_grid * kCoarsestSlots);
     c->cg_bar.alloc(2);
     c->cg_out.alloc(3);
@@ -664,7 +672,7 @@ void mg_default_params(mg_params *p) {
   p->max_iter = 500;
   p->coarsest_lu_max = 2048;
   p->coarsest_tol = 1e-12;
-  p->coarsest_restart = 32;
+  p->coarsest_restart = 16;
   p->coarsest_max_iter = 20000;
   p->precision = MG_FP64;
   p->seed = 20070704ULL;
