@@ -290,17 +290,21 @@ __global__ void __launch_bounds__(256) coarsest_gcr_kernel(CgArgs a) {
 // ---------------------------------------------------------------------------
 __global__ void self_block_inverse_kernel(const Cx<double> *__restrict__ Y, Cx<double> *__restrict__ Minv,
                                           Cx<double> *__restrict__ work, long long nsites, int N, int *info) {
-  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  // one warp per coarse site; the augmented matrix [X | I] lives in `work` (2 N^2 entries per
+  // site, column-major); lane r < N owns row r and lane N + r its copy of the identity part
+  const long long j = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (j >= nsites) return;
-  // work[j]: augmented [X | I] as two column-major N x N matrices
   Cx<double> *Aw = work + j * 2LL * N * N;
   Cx<double> *Iw = Aw + (long long)N * N;
   const Cx<double> *X = Y + (j * 5) * (long long)N * N;  // [col][row]
-  for (int q = 0; q < N * N; ++q) {
+  for (int q = lane; q < N * N; q += 32) {
     Aw[q] = X[q];
     Iw[q] = mk((q % N) == (q / N) ? 1.0 : 0.0, 0.0);
   }
+  __syncwarp();
   for (int c = 0; c < N; ++c) {
+    // pivot: largest |A(r, c)|, r >= c, ties to the smallest r (same answer in every lane)
     int p = c;
     double best = norm2(Aw[c * N + c]);
     for (int rr = c + 1; rr < N; ++rr) {
@@ -311,38 +315,50 @@ __global__ void self_block_inverse_kernel(const Cx<double> *__restrict__ Y, Cx<d
       }
     }
     if (!(best > 0.0)) {
-      atomicExch(info, 1);
+      if (lane == 0) atomicExch(info, 1);
       return;
     }
+    __syncwarp();
     if (p != c) {
-      for (int cc = 0; cc < N; ++cc) {
-        Cx<double> t = Aw[cc * N + c];
-        Aw[cc * N + c] = Aw[cc * N + p];
-        Aw[cc * N + p] = t;
-        t = Iw[cc * N + c];
-        Iw[cc * N + c] = Iw[cc * N + p];
-        Iw[cc * N + p] = t;
+      for (int cc = lane; cc < 2 * N; cc += 32) {
+        Cx<double> *M = cc < N ? Aw : Iw;
+        const int col = cc < N ? cc : cc - N;
+        const Cx<double> t = M[col * N + c];
+        M[col * N + c] = M[col * N + p];
+        M[col * N + p] = t;
       }
     }
+    __syncwarp();
     const Cx<double> pv = Aw[c * N + c];
     const double d = norm2(pv);
     const Cx<double> inv = mk(pv.re / d, -pv.im / d);
-    for (int cc = 0; cc < N; ++cc) {
-      Aw[cc * N + c] = Aw[cc * N + c] * inv;
-      Iw[cc * N + c] = Iw[cc * N + c] * inv;
+    __syncwarp();
+    for (int cc = lane; cc < 2 * N; cc += 32) {
+      Cx<double> *M = cc < N ? Aw : Iw;
+      const int col = cc < N ? cc : cc - N;
+      M[col * N + c] = M[col * N + c] * inv;
     }
-    for (int rr = 0; rr < N; ++rr) {
-      if (rr == c) continue;
-      const Cx<double> f = Aw[c * N + rr];
-      const Cx<double> mf = mk(-f.re, -f.im);
-      for (int cc = 0; cc < N; ++cc) {
-        cmac(Aw[cc * N + rr], mf, Aw[cc * N + c]);
-        cmac(Iw[cc * N + rr], mf, Iw[cc * N + c]);
+    __syncwarp();
+    // eliminate column c from every other row: element (rr, col) of [A | I]. The
+    // multipliers A(rr, c) are taken first (lane rr) and broadcast, because the
+    // update overwrites column c itself.
+    const Cx<double> fl = lane < N ? Aw[c * N + lane] : mk(0.0, 0.0);
+    __syncwarp();
+    for (int base = 0; base < 2 * N * N; base += 32) {
+      const int q = base + lane;
+      const int cc = q / N, rr = q - cc * N;
+      const double fre = __shfl_sync(0xffffffffu, fl.re, rr & 31);
+      const double fim = __shfl_sync(0xffffffffu, fl.im, rr & 31);
+      if (q < 2 * N * N && rr != c) {
+        Cx<double> *M = cc < N ? Aw : Iw;
+        const int col = cc < N ? cc : cc - N;
+        cmac(M[col * N + rr], mk(-fre, -fim), M[col * N + c]);
       }
     }
+    __syncwarp();
   }
   Cx<double> *Mj = Minv + j * (long long)N * N;
-  for (int q = 0; q < N * N; ++q) Mj[q] = Iw[q];
+  for (int q = lane; q < N * N; q += 32) Mj[q] = Iw[q];
 }
 
 // Yt[j][dir] = Y[j][dir] * Minv[src(j, dir)]  (column-major blocks); thread per (j, dir, col, row)
@@ -374,7 +390,7 @@ __global__ void precondition_stencil_kernel(const Cx<double> *__restrict__ Y, co
 void prepare_coarsest_gcr(const Cx<double> *Y, Geo2 g, int N, Cx<double> *Minv, Cx<double> *Yt, Cx<double> *work,
                           int *info_dev, cudaStream_t s) {
   MG_CUDA(cudaMemsetAsync(info_dev, 0, sizeof(int), s));
-  self_block_inverse_kernel<<<grid_for(g.nsites, 128), 128, 0, s>>>(Y, Minv, work, g.nsites, N, info_dev);
+  self_block_inverse_kernel<<<grid_for(g.nsites * 32, 128), 128, 0, s>>>(Y, Minv, work, g.nsites, N, info_dev);
   MG_LAUNCHED();
   precondition_stencil_kernel<<<grid_for(g.nsites * 5LL * N * N, 256), 256, 0, s>>>(Y, Minv, Yt, g.L0, g.L1, N);
   MG_LAUNCHED();

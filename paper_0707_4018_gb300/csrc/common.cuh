@@ -221,7 +221,8 @@ __device__ __forceinline__ void grid_finish(double (&v)[NOUT], double *partials,
 struct ReduceWs {
   double *partials;
   unsigned int *ticket;
-  int max_blocks;
+  int max_blocks;         // grid cap of the grid-stride reductions
+  long long capacity = 0; // doubles available in partials
 };
 
 constexpr int kReduceThreads = 256;

@@ -9,6 +9,31 @@ namespace mg {
 // message returned by mg_last_error() on this thread
 void set_last_error(const std::string &msg);
 
+// one level's operator: the fine Wilson D (wilson) or a coarse stencil Y with N x N blocks
+template <typename R>
+struct OpDesc {
+  bool wilson;
+  const Cx<R> *U;
+  const Cx<R> *Y;
+  Geo2 geo;
+  int N;
+  double diag;
+};
+
+// ---- fused MR smoothing (one launch per iteration) ----
+// step = false: Ar_new = A r_old and sc_new = (<Ar_new, r_old>, |Ar_new|^2).
+// step = true: alpha = omega <Ar_old, r_old>/|Ar_old|^2 from sc_old; x (+)= alpha r_old
+// (x_init: x = alpha r_old); r_new = r_old - alpha Ar_old; Ar_new = A r_new; sc_new as above.
+// r_new / Ar_new must differ from r_old / Ar_old, sc_new from sc_old.
+template <typename R>
+void launch_mr_iteration(const OpDesc<R> &op, bool step, const Cx<R> *r_old, const Cx<R> *Ar_old, const double *sc_old,
+                         double omega, Cx<R> *x, bool x_init, Cx<R> *r_new, Cx<R> *Ar_new, double *sc_new,
+                         const ReduceWs &ws, cudaStream_t s);
+// x (+)= alpha r_old, alpha from sc_old (the last MR update)
+template <typename R>
+void launch_mr_last(const Cx<R> *r_old, const double *sc_old, double omega, Cx<R> *x, bool x_init, long long n,
+                    cudaStream_t s);
+
 // ---- fine Wilson operator (2d, U(1), gamma_1 = sigma_1, gamma_2 = sigma_2) ----
 // out = a * D in + c * b   (b may be null when c == 0); D has diagonal `diag` = d + m
 template <typename R>

@@ -11,6 +11,7 @@
 // Every arithmetic step runs in the kernels of this library on the context's
 // stream; the host only sequences launches and reads convergence scalars.
 #include <cmath>
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <memory>
@@ -28,7 +29,7 @@ void set_last_error(const std::string &msg) { t_last_error = msg; }
 
 template <typename R>
 struct Work {
-  DevBuf<Cx<R>> b, x, r, Ar;
+  DevBuf<Cx<R>> b, x, r, Ar, r2, Ar2;  // r / r2 and Ar / Ar2 alternate inside the MR smoother
 };
 
 struct Level {
@@ -53,7 +54,7 @@ struct Level {
 
 // scalar slots on the device (FP64)
 enum : int {
-  kSlotMR = 0,          // 4 per level
+  kSlotMR = 0,          // 8 per level (two alternating MR reductions)
   kSlotOuter = 64,      // outer GCR: beta (2 * 128), then nrm / alpha / rnrm
   kSlotCoarse = 512,    // coarsest GCR: same layout
   kSlotCount = 1024
@@ -171,19 +172,48 @@ static void apply_op(mg_ctx &c, int l, const Cx<R> *in, Cx<R> *out, const Cx<R> 
   c.apps[l]++;
 }
 
-// x (+)= nu MR iterations for A_l x = b from zero; r is the MR residual buffer
-// (b may equal r: then it is consumed in place).
 template <typename R>
-static void smooth(mg_ctx &c, int l, const Cx<R> *b, Cx<R> *x, Cx<R> *r, Cx<R> *Ar, int nu, bool accumulate) {
+static OpDesc<R> op_of(mg_ctx &c, int l) {
   Level &L = c.lv[l];
-  if (!accumulate) launch_zero<R>(x, L.n, c.s);
-  if (r != b) launch_copy<R>(b, r, L.n, c.s);
-  double *sc = c.scal.p + kSlotMR + 4 * l;
-  for (int i = 0; i < nu; ++i) {
-    apply_op<R>(c, l, r, Ar);
-    launch_dot_norm<R>(Ar, r, L.n, sc, c.ws, c.s);
-    launch_mr_update<R>(sc, c.p.omega, x, r, Ar, L.n, c.s);
+  OpDesc<R> o;
+  o.wilson = (l == 0);
+  o.U = Uof<R>(c);
+  o.Y = l > 0 ? Yof<R>(L) : nullptr;
+  o.geo = L.geo;
+  o.N = L.nint;
+  o.diag = diag_of(c);
+  return o;
+}
+
+// x (+)= nu MR iterations for A_l x = b from zero (accumulate: added to x), with the
+// fused kernels: nu + 1 launches. b may be the level's r buffer (consumed then).
+template <typename R>
+static void smooth(mg_ctx &c, int l, const Cx<R> *b, Cx<R> *x, int nu, bool accumulate) {
+  Level &L = c.lv[l];
+  Work<R> &w = work<R>(L);
+  if (nu <= 0) {
+    if (!accumulate) launch_zero<R>(x, L.n, c.s);
+    return;
   }
+  double *sc[2] = {c.scal.p + kSlotMR + 8 * l, c.scal.p + kSlotMR + 8 * l + 4};
+  const OpDesc<R> op = op_of<R>(c, l);
+  Cx<R> *rbuf[2] = {w.r.p, w.r2.p};
+  Cx<R> *Arbuf[2] = {w.Ar.p, w.Ar2.p};
+  launch_mr_iteration<R>(op, false, b, nullptr, nullptr, c.p.omega, nullptr, false, nullptr, Arbuf[0], sc[0], c.ws,
+                         c.s);
+  c.apps[l]++;
+  const Cx<R> *r_old = b;
+  int rsel = (b == rbuf[0]) ? 1 : 0, asel = 1, ssel = 1;
+  for (int i = 1; i < nu; ++i) {
+    launch_mr_iteration<R>(op, true, r_old, Arbuf[asel ^ 1], sc[ssel ^ 1], c.p.omega, x, i == 1 && !accumulate,
+                           rbuf[rsel], Arbuf[asel], sc[ssel], c.ws, c.s);
+    c.apps[l]++;
+    r_old = rbuf[rsel];
+    rsel ^= 1;
+    asel ^= 1;
+    ssel ^= 1;
+  }
+  launch_mr_last<R>(r_old, sc[ssel ^ 1], c.p.omega, x, nu == 1 && !accumulate, L.n, c.s);
 }
 
 struct GcrOut {
@@ -312,7 +342,7 @@ static void vcycle(mg_ctx &c, int l, const Cx<R> *b, Cx<R> *x) {
   Work<R> &w = work<R>(L);
   Work<R> &wc = work<R>(C);
   // 1. pre-relaxation from zero
-  smooth<R>(c, l, b, x, w.r.p, w.Ar.p, c.p.nu_pre, false);
+  smooth<R>(c, l, b, x, c.p.nu_pre, false);
   // 2. restrict the residual
   apply_op<R>(c, l, x, w.r.p, b, -1.0, 1.0);
   launch_restrict<R>(Vof<R>(L), w.r.p, wc.b.p, L.bg, L.Nv, c.s);
@@ -322,7 +352,7 @@ static void vcycle(mg_ctx &c, int l, const Cx<R> *b, Cx<R> *x) {
   launch_prolong_add<R>(Vof<R>(L), wc.x.p, x, L.bg, L.Nv, c.s);
   // 5. post-relaxation on the final residual
   apply_op<R>(c, l, x, w.r.p, b, -1.0, 1.0);
-  smooth<R>(c, l, w.r.p, x, w.r.p, w.Ar.p, c.p.nu_post, true);
+  smooth<R>(c, l, w.r.p, x, c.p.nu_post, true);
 }
 
 // Runs `body` (a fixed sequence of launches on the context stream) through a
@@ -431,17 +461,13 @@ static void build_level(mg_ctx &c, int l) {
 static void setup_level(mg_ctx &c, int l, bool full) {
   Level &L = c.lv[l];
   const long long n = L.n;
-  double *sc = c.scal.p + kSlotMR + 4 * l;
-  // pass 1: random vectors relaxed on A x = 0 (nu_setup MR iterations from x = v)
+  // pass 1: random vectors relaxed on A x = 0 (nu_setup MR iterations from x = v: the
+  // corrections solve A d = -A v from d = 0)
   for (int k = 0; k < L.Nv; ++k) {
     Cx<double> *v = L.nullv.p + (long long)k * n;
     launch_gaussian(v, n, c.p.seed, k, l, c.s);
     apply_op<double>(c, l, v, L.tA.p, nullptr, -1.0, 0.0);  // r = -A v
-    for (int i = 0; i < c.p.nu_setup; ++i) {
-      apply_op<double>(c, l, L.tA.p, L.tB.p);
-      launch_dot_norm<double>(L.tB.p, L.tA.p, n, sc, c.ws, c.s);
-      launch_mr_update<double>(sc, c.p.omega, v, L.tA.p, L.tB.p, n, c.s);
-    }
+    smooth<double>(c, l, L.tA.p, v, c.p.nu_setup, true);
   }
   const int n_pass = full ? c.p.n_pass : 1;
   for (int pass = 1; pass <= n_pass; ++pass) {
@@ -558,6 +584,15 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
     }
   }
   const Level &F = c->lv[0];
+  for (int l = 0; l < p->levels; ++l) {
+    Level &L = c->lv[l];
+    L.w64.r2.alloc(L.n);
+    L.w64.Ar2.alloc(L.n);
+    if (f32) {
+      L.w32.r2.alloc(L.n);
+      L.w32.Ar2.alloc(L.n);
+    }
+  }
   c->U64.alloc(F.geo.nsites * 2);
   if (f32) c->U32.alloc(F.geo.nsites * 2);
   // coarsest
@@ -601,7 +636,14 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
   c->orr.alloc(F.n);
   // reductions
   c->ws.max_blocks = 152 * 8;
-  c->partials.alloc((size_t)c->ws.max_blocks * 4 + 16);
+  // the fused MR kernels reduce over one block per 256 sites (fine) or dofs (coarse)
+  long long cap = (long long)c->ws.max_blocks * 4;
+  for (int l = 0; l < p->levels; ++l) {
+    const long long units = l == 0 ? c->lv[l].geo.nsites : c->lv[l].n;
+    cap = std::max(cap, 3 * ((units + 255) / 256));
+  }
+  c->partials.alloc((size_t)cap + 16);
+  c->ws.capacity = cap;
   c->tickets.alloc(128);
   MG_CUDA(cudaMemsetAsync(c->tickets.p, 0, 128 * sizeof(unsigned int), c->s));
   c->scal.alloc(kSlotCount);
@@ -840,8 +882,8 @@ int mg_smooth(mg_ctx *c, int level, const void *b, void *x, int nu) {
     need_ptr(x);
     if (nu < 0) fail(MG_ERR_INVALID_ARG, "nu must be >= 0");
     Level &L = c->lv[level];
-    smooth<double>(*c, level, static_cast<const Cx<double> *>(b), static_cast<Cx<double> *>(x), L.w64.r.p,
-                   L.w64.Ar.p, nu, false);
+    (void)L;
+    smooth<double>(*c, level, static_cast<const Cx<double> *>(b), static_cast<Cx<double> *>(x), nu, false);
     MG_CUDA(cudaStreamSynchronize(c->s));
   });
 }

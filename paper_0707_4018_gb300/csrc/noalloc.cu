@@ -75,7 +75,7 @@ extern "C" int mg_smooth_fine_noalloc(const mg_geom *g, const void *U, double m,
     double *partials = S + 4 * kNoAllocMaxDofs;
     double *sc = partials + 3 * kNoAllocMaxBlocks;
     unsigned int *ticket = reinterpret_cast<unsigned int *>(sc + 8);
-    ReduceWs ws{partials, ticket, kNoAllocMaxBlocks};
+    ReduceWs ws{partials, ticket, kNoAllocMaxBlocks, 3LL * kNoAllocMaxBlocks};
     const Geo2 geo{g->dims[0], g->dims[1], sites};
     const Cx<double> *Ud = static_cast<const Cx<double> *>(U);
     Cx<double> *xd = static_cast<Cx<double> *>(x);
