@@ -25,14 +25,6 @@ __global__ void convert_kernel(const Cx<From> *__restrict__ x, Cx<To> *__restric
 }
 
 template <typename R>
-__global__ void axpy_dev_kernel(const double *__restrict__ alpha, double sign, const Cx<R> *__restrict__ x,
-                                Cx<R> *__restrict__ y, long long n) {
-  const Cx<R> a = mk((R)(sign * alpha[0]), (R)(sign * alpha[1]));
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    cmac(y[i], a, x[i]);
-}
-
-template <typename R>
 __global__ void xmy_kernel(const Cx<R> *__restrict__ x, Cx<R> *__restrict__ y, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] = x[i] - y[i];
@@ -66,52 +58,6 @@ __global__ void __launch_bounds__(kReduceThreads) norm2_kernel(const Cx<R> *__re
   grid_finish<1>(v, partials, out, ticket, sh);
 }
 
-// blockIdx.y = j: <W_j, w>; partials/ticket are per j
-template <typename R>
-__global__ void __launch_bounds__(kReduceThreads) multi_dot_kernel(const Cx<R> *__restrict__ W,
-                                                                   const Cx<R> *__restrict__ w, long long n,
-                                                                   double *partials, double *out,
-                                                                   unsigned int *ticket, int pstride) {
-  __shared__ double sh[32 * 2];
-  const int j = blockIdx.y;
-  const Cx<R> *Wj = W + (long long)j * n;
-  double v[2] = {0.0, 0.0};
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const Cx<double> x = cvt<double>(Wj[i]), y = cvt<double>(w[i]);
-    v[0] += x.re * y.re + x.im * y.im;
-    v[1] += x.re * y.im - x.im * y.re;
-  }
-  grid_finish<2>(v, partials + (long long)j * pstride, out + 2 * j, ticket + j, sh);
-}
-
-template <typename R>
-__global__ void multi_axpy_kernel(const double *__restrict__ beta, int k, const Cx<R> *__restrict__ W,
-                                  Cx<R> *__restrict__ w, const Cx<R> *__restrict__ Z, Cx<R> *__restrict__ z,
-                                  long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    Cx<R> acc = w[i];
-    Cx<R> accz = z ? z[i] : mk((R)0, (R)0);
-    for (int j = 0; j < k; ++j) {
-      const Cx<R> bj = mk((R)-beta[2 * j], (R)-beta[2 * j + 1]);
-      cmac(acc, bj, W[(long long)j * n + i]);
-      if (z) cmac(accz, bj, Z[(long long)j * n + i]);
-    }
-    w[i] = acc;
-    if (z) z[i] = accz;
-  }
-}
-
-template <typename R>
-__global__ void normalize_kernel(const double *__restrict__ nrm2, Cx<R> *__restrict__ w, Cx<R> *__restrict__ z,
-                                 long long n) {
-  const double s = nrm2[0] > 0.0 ? 1.0 / sqrt(nrm2[0]) : 0.0;
-  const R sr = (R)s;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    w[i] = sr * w[i];
-    if (z) z[i] = sr * z[i];
-  }
-}
-
 template <typename R>
 __global__ void mr_update_kernel(const double *__restrict__ sc, double omega, Cx<R> *__restrict__ x,
                                  Cx<R> *__restrict__ r, const Cx<R> *__restrict__ Ar, long long n) {
@@ -129,24 +75,71 @@ __global__ void mr_update_kernel(const double *__restrict__ sc, double omega, Cx
   }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(kReduceThreads) gcr_update_kernel(const double *__restrict__ sc, Cx<R> *__restrict__ x,
-                                                                    const Cx<R> *__restrict__ z, Cx<R> *__restrict__ r,
-                                                                    const Cx<R> *__restrict__ w, long long n,
-                                                                    double *partials, double *out,
-                                                                    unsigned int *ticket) {
-  __shared__ double sh[32];
-  const Cx<R> alpha = mk((R)sc[0], (R)sc[1]), malpha = mk((R)-sc[0], (R)-sc[1]);
-  double v[1] = {0.0};
+// rows j < k: <W_j, w>; row k: <w, w>; row k + 1: <w, r>  (blockIdx.y = row)
+__global__ void __launch_bounds__(kReduceThreads) gcr_dots_kernel(const Cx<double> *__restrict__ W,
+                                                                  const Cx<double> *__restrict__ w,
+                                                                  const Cx<double> *__restrict__ r, int k,
+                                                                  long long n, double *partials, double *out,
+                                                                  unsigned int *ticket, int pstride) {
+  __shared__ double sh[32 * 2];
+  const int row = blockIdx.y;
+  const Cx<double> *a = row < k ? W + (long long)row * n : w;
+  const Cx<double> *b = row == k + 1 ? r : w;
+  double v[2] = {0.0, 0.0};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    cmac(x[i], alpha, z[i]);
-    Cx<R> rn = r[i];
-    cmac(rn, malpha, w[i]);
-    r[i] = rn;
-    const Cx<double> rd = cvt<double>(rn);
-    v[0] += rd.re * rd.re + rd.im * rd.im;
+    const Cx<double> x = a[i], y = b[i];
+    v[0] += x.re * y.re + x.im * y.im;
+    v[1] += x.re * y.im - x.im * y.re;
   }
-  grid_finish<1>(v, partials, out, ticket, sh);
+  grid_finish<2>(v, partials + (long long)row * pstride, out + 2 * row, ticket + row, sh);
+}
+
+// w <- (w - sum_j beta_j W_j) * inv, z likewise; W_k = w, Z_k = z; x += alpha z; r -= alpha w
+__global__ void gcr_project_update_kernel(const Cx<double> *__restrict__ W, Cx<double> *__restrict__ Wk,
+                                          const Cx<double> *__restrict__ Z, Cx<double> *__restrict__ Zk, int k,
+                                          const double *__restrict__ beta, double inv, double are, double aim,
+                                          Cx<double> *__restrict__ x, Cx<double> *__restrict__ r, long long n,
+                                          int update_xr) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    Cx<double> w = Wk[i], z = Zk[i];
+    for (int j = 0; j < k; ++j) {
+      const Cx<double> bj = mk(-beta[2 * j], -beta[2 * j + 1]);
+      cmac(w, bj, W[(long long)j * n + i]);
+      cmac(z, bj, Z[(long long)j * n + i]);
+    }
+    w = inv * w;
+    z = inv * z;
+    Wk[i] = w;
+    Zk[i] = z;
+    if (update_xr) {
+      cmac(x[i], mk(are, aim), z);
+      Cx<double> ri = r[i];
+      cmac(ri, mk(-are, -aim), w);
+      r[i] = ri;
+    }
+  }
+}
+
+void launch_gcr_dots(const Cx<double> *W, const Cx<double> *w, const Cx<double> *r, int k, long long n, double *out,
+                     const ReduceWs &ws, cudaStream_t s) {
+  const int rows = k + 2;
+  if (rows > 128) fail(MG_ERR_UNSUPPORTED, "gcr_dots: too many basis vectors");
+  int per = (int)(ws.capacity / (2 * rows));
+  if (per > ws.max_blocks) per = ws.max_blocks;
+  if (per < 1) per = 1;
+  dim3 grid(reduce_blocks(n, per), rows);
+  gcr_dots_kernel<<<grid, kReduceThreads, 0, s>>>(W, w, r, k, n, ws.partials, out, ws.ticket, 2 * (int)grid.x);
+  MG_LAUNCHED();
+}
+
+void launch_gcr_project_update(const Cx<double> *W, Cx<double> *Wk, const Cx<double> *Z, Cx<double> *Zk, int k,
+                               const double *beta_dev, double inv, double are, double aim, Cx<double> *x,
+                               Cx<double> *r, long long n, bool update_xr, cudaStream_t s) {
+  long long b = (n + 255) / 256;
+  if (b > 152LL * 16) b = 152LL * 16;
+  gcr_project_update_kernel<<<(unsigned int)(b < 1 ? 1 : b), 256, 0, s>>>(W, Wk, Z, Zk, k, beta_dev, inv, are, aim, x,
+                                                                          r, n, update_xr ? 1 : 0);
+  MG_LAUNCHED();
 }
 
 // ---------------------------------------------------------------------------
@@ -173,11 +166,6 @@ void launch_convert(const Cx<From> *x, Cx<To> *y, long long n, cudaStream_t s) {
   MG_LAUNCHED();
 }
 template <typename R>
-void launch_axpy_dev(const double *alpha_dev, double sign, const Cx<R> *x, Cx<R> *y, long long n, cudaStream_t s) {
-  axpy_dev_kernel<R><<<stream_grid(n), 256, 0, s>>>(alpha_dev, sign, x, y, n);
-  MG_LAUNCHED();
-}
-template <typename R>
 void launch_xmy(const Cx<R> *x, Cx<R> *y, long long n, cudaStream_t s) {
   xmy_kernel<R><<<stream_grid(n), 256, 0, s>>>(x, y, n);
   MG_LAUNCHED();
@@ -193,59 +181,20 @@ void launch_norm2(const Cx<R> *a, long long n, double *out, const ReduceWs &ws, 
   MG_LAUNCHED();
 }
 template <typename R>
-void launch_multi_dot(const Cx<R> *W, int k, const Cx<R> *w, long long n, double *out, const ReduceWs &ws,
-                      cudaStream_t s) {
-  if (k <= 0) return;
-  // the workspace holds max_blocks * 4 partials and 128 tickets: split the blocks across the k rows
-  int per = ws.max_blocks * 4 / (2 * k);
-  if (per < 1) per = 1;
-  if (k > 128) fail(MG_ERR_UNSUPPORTED, "multi_dot: more than 128 vectors");
-  dim3 grid(reduce_blocks(n, per), k);
-  multi_dot_kernel<R><<<grid, kReduceThreads, 0, s>>>(W, w, n, ws.partials, out, ws.ticket, 2 * (int)grid.x);
-  MG_LAUNCHED();
-}
-template <typename R>
-void launch_multi_axpy(const double *beta, int k, const Cx<R> *W, Cx<R> *w, const Cx<R> *Z, Cx<R> *z, long long n,
-                       cudaStream_t s) {
-  if (k <= 0) return;
-  multi_axpy_kernel<R><<<stream_grid(n), 256, 0, s>>>(beta, k, W, w, Z, z, n);
-  MG_LAUNCHED();
-}
-template <typename R>
-void launch_normalize(const double *nrm2_dev, Cx<R> *w, Cx<R> *z, long long n, cudaStream_t s) {
-  normalize_kernel<R><<<stream_grid(n), 256, 0, s>>>(nrm2_dev, w, z, n);
-  MG_LAUNCHED();
-}
-template <typename R>
 void launch_mr_update(const double *sc, double omega, Cx<R> *x, Cx<R> *r, const Cx<R> *Ar, long long n,
                       cudaStream_t s) {
   mr_update_kernel<R><<<stream_grid(n), 256, 0, s>>>(sc, omega, x, r, Ar, n);
   MG_LAUNCHED();
 }
-template <typename R>
-void launch_gcr_update(const double *sc, Cx<R> *x, const Cx<R> *z, Cx<R> *r, const Cx<R> *w, long long n,
-                       double *out_nrm, const ReduceWs &ws, cudaStream_t s) {
-  gcr_update_kernel<R><<<reduce_blocks(n, ws.max_blocks), kReduceThreads, 0, s>>>(sc, x, z, r, w, n, ws.partials,
-                                                                                  out_nrm, ws.ticket);
-  MG_LAUNCHED();
-}
-
 #define MG_INST_BLAS(R)                                                                                          \
   template void launch_zero<R>(Cx<R> *, long long, cudaStream_t);                                                \
   template void launch_copy<R>(const Cx<R> *, Cx<R> *, long long, cudaStream_t);                                 \
-  template void launch_axpy_dev<R>(const double *, double, const Cx<R> *, Cx<R> *, long long, cudaStream_t);     \
   template void launch_xmy<R>(const Cx<R> *, Cx<R> *, long long, cudaStream_t);                                  \
   template void launch_dot_norm<R>(const Cx<R> *, const Cx<R> *, long long, double *, const ReduceWs &, cudaStream_t); \
   template void launch_norm2<R>(const Cx<R> *, long long, double *, const ReduceWs &, cudaStream_t);             \
-  template void launch_multi_dot<R>(const Cx<R> *, int, const Cx<R> *, long long, double *, const ReduceWs &,    \
-                                    cudaStream_t);                                                               \
-  template void launch_multi_axpy<R>(const double *, int, const Cx<R> *, Cx<R> *, const Cx<R> *, Cx<R> *,        \
-                                     long long, cudaStream_t);                                                   \
-  template void launch_normalize<R>(const double *, Cx<R> *, Cx<R> *, long long, cudaStream_t);                  \
   template void launch_mr_update<R>(const double *, double, Cx<R> *, Cx<R> *, const Cx<R> *, long long,          \
                                     cudaStream_t);                                                               \
-  template void launch_gcr_update<R>(const double *, Cx<R> *, const Cx<R> *, Cx<R> *, const Cx<R> *, long long,  \
-                                     double *, const ReduceWs &, cudaStream_t);
+
 
 MG_INST_BLAS(double)
 MG_INST_BLAS(float)

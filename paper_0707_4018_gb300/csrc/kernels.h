@@ -53,9 +53,6 @@ template <typename R>
 void launch_copy(const Cx<R> *x, Cx<R> *y, long long n, cudaStream_t s);
 template <typename To, typename From>
 void launch_convert(const Cx<From> *x, Cx<To> *y, long long n, cudaStream_t s);
-// y += alpha x, alpha read from device (complex at alpha_dev[0..1], times sign)
-template <typename R>
-void launch_axpy_dev(const double *alpha_dev, double sign, const Cx<R> *x, Cx<R> *y, long long n, cudaStream_t s);
 // y = x - y (in place on y)
 template <typename R>
 void launch_xmy(const Cx<R> *x, Cx<R> *y, long long n, cudaStream_t s);
@@ -67,25 +64,19 @@ void launch_dot_norm(const Cx<R> *a, const Cx<R> *b, long long n, double *out, c
 // out[0] = |a|^2
 template <typename R>
 void launch_norm2(const Cx<R> *a, long long n, double *out, const ReduceWs &ws, cudaStream_t s);
-// out[2j..2j+1] = <W_j, w> for j < k  (W: k vectors with stride n)
-template <typename R>
-void launch_multi_dot(const Cx<R> *W, int k, const Cx<R> *w, long long n, double *out, const ReduceWs &ws,
-                      cudaStream_t s);
-// w -= sum_j beta_j W_j, z -= sum_j beta_j Z_j (beta from device, complex pairs); Z/z may be null
-template <typename R>
-void launch_multi_axpy(const double *beta, int k, const Cx<R> *W, Cx<R> *w, const Cx<R> *Z, Cx<R> *z, long long n,
-                       cudaStream_t s);
-// w *= 1/sqrt(nrm2_dev[0]), z *= same (z may be null)
-template <typename R>
-void launch_normalize(const double *nrm2_dev, Cx<R> *w, Cx<R> *z, long long n, cudaStream_t s);
 // MR step: alpha = omega <Ar, r>/|Ar|^2 (sc[0..2]); x += alpha r; r -= alpha Ar
 template <typename R>
 void launch_mr_update(const double *sc, double omega, Cx<R> *x, Cx<R> *r, const Cx<R> *Ar, long long n,
                       cudaStream_t s);
-// GCR step: alpha = <w, r> (sc[0..1]); x += alpha z; r -= alpha w; out_nrm[0] = |r|^2 (grid reduction)
-template <typename R>
-void launch_gcr_update(const double *sc, Cx<R> *x, const Cx<R> *z, Cx<R> *r, const Cx<R> *w, long long n,
-                       double *out_nrm, const ReduceWs &ws, cudaStream_t s);
+
+// outer GCR, FP64: out[2j..2j+1] = <W_j, w> (j < k), out[2k] = |w|^2, out[2k+2..2k+3] = <w, r>
+void launch_gcr_dots(const Cx<double> *W, const Cx<double> *w, const Cx<double> *r, int k, long long n, double *out,
+                     const ReduceWs &ws, cudaStream_t s);
+// w = (w - sum beta_j W_j) inv and z likewise (written to Wk / Zk); then, if update_xr,
+// x += alpha z and r -= alpha w. beta_dev: 2k doubles on the device.
+void launch_gcr_project_update(const Cx<double> *W, Cx<double> *Wk, const Cx<double> *Z, Cx<double> *Zk, int k,
+                               const double *beta_dev, double inv, double are, double aim, Cx<double> *x,
+                               Cx<double> *r, long long n, bool update_xr, cudaStream_t s);
 
 // ---- transfer between levels ----
 // coarse[b][k] = sum_i conj(V[b][k][i]) fine[site(b,s)][a]
@@ -94,8 +85,6 @@ void launch_restrict(const Cx<R> *V, const Cx<R> *fine, Cx<R> *coarse, BlockGeo 
 // fine[site(b,s)][a] += sum_k V[b][k][i] coarse[b][k]
 template <typename R>
 void launch_prolong_add(const Cx<R> *V, const Cx<R> *coarse, Cx<R> *fine, BlockGeo bg, int Nv, cudaStream_t s);
-// fine[site(b,s)][a] = V[b][k][i] for every b (column k of P as a level vector), FP64
-void launch_prolongator_column(const Cx<double> *V, Cx<double> *fine, BlockGeo bg, int Nv, int k, cudaStream_t s);
 // block Gram-Schmidt (modified, twice, k order) of Nv level vectors into V[b][k][i]; FP64
 void launch_block_mgs(const Cx<double> *vecs, long long vec_stride, Cx<double> *V, BlockGeo bg, int Nv,
                       double *min_norm_dev, cudaStream_t s);
@@ -104,8 +93,6 @@ void launch_galerkin_wilson(const Cx<double> *U, double diag, const Cx<double> *
                             int Nv, cudaStream_t s);
 void launch_galerkin_stencil(const Cx<double> *Y, const Cx<double> *V, Cx<double> *Yc, BlockGeo bg, int Nv,
                              cudaStream_t s);
-// Yc[b][0] += dm * I  (mass update of a Galerkin operator with orthonormal P)
-void launch_shift_diag(Cx<double> *Y, long long nsites, int N, double dm, cudaStream_t s);
 
 // ---- layout conversions at the boundary ----
 // internal Y[j][dir][col][row] <-> canonical Y[j][dir][row][col]

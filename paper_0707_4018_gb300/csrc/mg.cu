@@ -55,11 +55,9 @@ struct Level {
 // scalar slots on the device (FP64)
 enum : int {
   kSlotMR = 0,          // 8 per level (two alternating MR reductions)
-  kSlotOuter = 64,      // outer GCR: beta (2 * 128), then nrm / alpha / rnrm
-  kSlotCoarse = 512,    // coarsest GCR: same layout
+  kSlotOuter = 64,      // outer GCR reductions: 2 (restart + 2) doubles
   kSlotCount = 1024
 };
-constexpr int kBeta = 0, kNrm = 300, kAlpha = 304, kRnrm = 308, kBnrm = 312;
 
 // an instantiated graph of one V-cycle with the launches and operator
 // applications it replays
@@ -154,12 +152,6 @@ const Cx<double> *Vof<double>(const Level &L) { return L.V64.p; }
 template <>
 const Cx<float> *Vof<float>(const Level &L) { return L.V32.p; }
 
-static double read_scalar(mg_ctx &c, int slot) {
-  MG_CUDA(cudaMemcpyAsync(c.host, c.scal.p + slot, sizeof(double), cudaMemcpyDeviceToHost, c.s));
-  MG_CUDA(cudaStreamSynchronize(c.s));
-  return c.host[0];
-}
-
 // out = a * A_l in + c * b
 template <typename R>
 static void apply_op(mg_ctx &c, int l, const Cx<R> *in, Cx<R> *out, const Cx<R> *b = nullptr, double a = 1.0,
@@ -222,60 +214,83 @@ struct GcrOut {
   double rel = 0.0;
 };
 
-// (flexible) GCR with classical Gram-Schmidt applied twice; the true residual is
-// recomputed at every restart. precond(r, z) writes z = M r; null -> identity.
-template <typename R, typename P>
-static GcrOut gcr(mg_ctx &c, int l, const Cx<R> *b, Cx<R> *x, double tol, int restart, int max_iter, Cx<R> *Z,
-                  Cx<R> *W, Cx<R> *r, int slot, P &&precond, bool has_precond) {
-  Level &L = c.lv[l];
-  const long long n = L.n;
-  double *sc = c.scal.p + slot;
+static void precondition(mg_ctx &c, const Cx<double> *r, Cx<double> *z);
+
+// Outer flexible GCR on D (FP64) with the V-cycle as right preconditioner.
+// Per iteration: z = V r, w = D z, one fused reduction of <W_j, w>, |w|^2, <w, r>;
+// the host forms the classical Gram-Schmidt coefficients, the Pythagorean norm
+// |w - W beta|^2 = |w|^2 - |beta|^2 and alpha = <w_hat, r>, and runs a second
+// projection only when that norm shows cancellation (< half of |w|^2); then one
+// fused kernel projects, normalises and updates x and r. The residual norm is
+// tracked as |r|^2 - |alpha|^2 and the true residual b - D x is recomputed at
+// every restart (defect correction).
+static GcrOut outer_fgcr(mg_ctx &c, const Cx<double> *b, Cx<double> *x, double tol, int restart, int max_iter) {
+  Level &F = c.lv[0];
+  const long long n = F.n;
+  Cx<double> *Z = c.oZ.p, *W = c.oW.p, *r = c.orr.p;
+  double *dots = c.scal.p + kSlotOuter;  // 2 (k + 2) doubles
+  double *h = c.host;
   GcrOut out;
-  launch_zero<R>(x, n, c.s);
-  launch_copy<R>(b, r, n, c.s);
-  launch_norm2<R>(b, n, sc + kBnrm, c.ws, c.s);
-  const double bn2 = read_scalar(c, slot + kBnrm);
+  auto fetch = [&](int count) {
+    MG_CUDA(cudaMemcpyAsync(h, dots, count * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+    MG_CUDA(cudaStreamSynchronize(c.s));
+    for (int i = 0; i < count; ++i)
+      if (std::isnan(h[i])) fail(MG_ERR_NAN, "outer GCR: NaN in a reduction");
+  };
+  launch_zero<double>(x, n, c.s);
+  launch_copy<double>(b, r, n, c.s);
+  launch_norm2<double>(b, n, dots, c.ws, c.s);
+  fetch(1);
+  const double bn2 = h[0];
   if (!(bn2 > 0.0)) {
-    if (std::isnan(bn2)) fail(MG_ERR_NAN, "GCR: right-hand side norm is NaN");
     out.converged = true;
     return out;
   }
-  double rel = 1.0;
+  double rn2 = bn2, rel = 1.0;
   while (out.iters < max_iter) {
     int k = 0;
-    while (k < restart && out.iters < max_iter) {
-      Cx<R> *z = Z + (long long)k * n, *w = W + (long long)k * n;
-      if (has_precond)
-        precond(r, z);
-      else
-        launch_copy<R>(r, z, n, c.s);
-      apply_op<R>(c, l, z, w);
-      if (k > 0) {
-        for (int rep = 0; rep < 2; ++rep) {
-          launch_multi_dot<R>(W, k, w, n, sc + kBeta, c.ws, c.s);
-          launch_multi_axpy<R>(sc + kBeta, k, W, w, Z, z, n, c.s);
-        }
+    for (; k < restart && out.iters < max_iter; ++k) {
+      Cx<double> *z = Z + (long long)k * n, *w = W + (long long)k * n;
+      precondition(c, r, z);
+      apply_op<double>(c, 0, z, w);
+      launch_gcr_dots(W, w, r, k, n, dots, c.ws, c.s);
+      fetch(2 * (k + 2));
+      double nw0 = h[2 * k], nw2 = nw0;
+      for (int j = 0; j < k; ++j) nw2 -= h[2 * j] * h[2 * j] + h[2 * j + 1] * h[2 * j + 1];
+      double wr = h[2 * k + 2], wi = h[2 * k + 3];
+      if (k > 0 && !(nw2 > 0.5 * nw0)) {
+        // cancellation: project once, then take fresh coefficients for a second projection
+        launch_gcr_project_update(W, w, Z, z, k, dots, 1.0, 0.0, 0.0, x, r, n, false, c.s);
+        launch_gcr_dots(W, w, r, k, n, dots, c.ws, c.s);
+        fetch(2 * (k + 2));
+        nw0 = h[2 * k];
+        nw2 = nw0;
+        for (int j = 0; j < k; ++j) nw2 -= h[2 * j] * h[2 * j] + h[2 * j + 1] * h[2 * j + 1];
+        wr = h[2 * k + 2];
+        wi = h[2 * k + 3];
       }
-      launch_norm2<R>(w, n, sc + kNrm, c.ws, c.s);
-      launch_normalize<R>(sc + kNrm, w, z, n, c.s);
-      launch_dot_norm<R>(w, r, n, sc + kAlpha, c.ws, c.s);
-      launch_gcr_update<R>(sc + kAlpha, x, z, r, w, n, sc + kRnrm, c.ws, c.s);
-      ++k;
+      if (!(nw2 > 1e-28 * nw0)) break;  // breakdown: restart from the true residual
+      const double inv = 1.0 / std::sqrt(nw2);
+      const double are = wr * inv, aim = wi * inv;
+      launch_gcr_project_update(W, w, Z, z, k, dots, inv, are, aim, x, r, n, true, c.s);
+      rn2 = std::max(rn2 - (are * are + aim * aim), 0.0);
       ++out.iters;
-      const double rn2 = read_scalar(c, slot + kRnrm);
-      if (std::isnan(rn2)) fail(MG_ERR_NAN, "GCR: residual norm is NaN");
       rel = std::sqrt(rn2 / bn2);
-      if (rel <= tol) break;
+      if (rel <= tol) {
+        ++k;
+        break;
+      }
     }
-    apply_op<R>(c, l, x, r, b, -1.0, 1.0);  // true residual r = b - A x
-    launch_norm2<R>(r, n, sc + kRnrm, c.ws, c.s);
-    const double tr2 = read_scalar(c, slot + kRnrm);
-    if (std::isnan(tr2)) fail(MG_ERR_NAN, "GCR: true residual norm is NaN");
-    rel = std::sqrt(tr2 / bn2);
+    apply_op<double>(c, 0, x, r, b, -1.0, 1.0);  // true residual r = b - D x
+    launch_norm2<double>(r, n, dots, c.ws, c.s);
+    fetch(1);
+    rn2 = h[0];
+    rel = std::sqrt(rn2 / bn2);
     if (rel <= tol) {
       out.converged = true;
       break;
     }
+    if (k == 0) break;  // no progress possible
   }
   out.rel = rel;
   return out;
@@ -544,7 +559,7 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
   MG_CUDA(cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming));
   enter(*c);
   c->graphs_ok = std::getenv("MG_NO_GRAPHS") == nullptr;
-  MG_CUDA(cudaMallocHost(&c->host, 16 * sizeof(double)));
+  MG_CUDA(cudaMallocHost(&c->host, 512 * sizeof(double)));
   c->lv.resize(p->levels);
   int L0 = g->dims[0], L1 = g->dims[1], nint = 2;
   const bool f32 = p->precision == MG_FP32;
@@ -753,9 +768,8 @@ int mg_solve(mg_ctx *c, const void *chi, void *psi, double tol, mg_stats *st) {
     MG_CUDA(cudaEventCreate(&e0));
     MG_CUDA(cudaEventCreate(&e1));
     MG_CUDA(cudaEventRecord(e0, c->s));
-    auto pre = [&](const Cx<double> *r, Cx<double> *z) { precondition(*c, r, z); };
-    GcrOut o = gcr<double>(*c, 0, static_cast<const Cx<double> *>(chi), static_cast<Cx<double> *>(psi), tol,
-                           c->p.gcr_restart, c->p.max_iter, c->oZ.p, c->oW.p, c->orr.p, kSlotOuter, pre, true);
+    GcrOut o = outer_fgcr(*c, static_cast<const Cx<double> *>(chi), static_cast<Cx<double> *>(psi), tol,
+                          c->p.gcr_restart, c->p.max_iter);
     MG_CUDA(cudaEventRecord(e1, c->s));
     MG_CUDA(cudaEventSynchronize(e1));
     c->coarsest_iters = collect_coarsest(*c);

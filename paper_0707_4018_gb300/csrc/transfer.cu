@@ -72,18 +72,6 @@ __global__ void __launch_bounds__(128) prolong_add_kernel(const Cx<R> *__restric
   }
 }
 
-__global__ void prolongator_column_kernel(const Cx<double> *__restrict__ V, Cx<double> *__restrict__ fine, BlockGeo g,
-                                          int Nv, int k) {
-  const long long b = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (b >= g.nblocks) return;
-  const Cx<double> *Vb = V + (b * Nv + k) * (long long)g.Nb;
-  for (int i = lane; i < g.Nb; i += 32) {
-    const int s = i / g.nint, a = i - s * g.nint;
-    fine[fine_site_of(g, b, s) * g.nint + a] = Vb[i];
-  }
-}
-
 // ---------------------------------------------------------------------------
 // block Gram-Schmidt: modified GS in k order, two passes, FP64; each lane only
 // touches its own dofs (kept in shared memory), sums go through shuffles
@@ -255,14 +243,6 @@ __global__ void galerkin_kernel(const Cx<double> *__restrict__ U_or_Y, double di
   }
 }
 
-__global__ void shift_diag_kernel(Cx<double> *Y, long long nsites, int N, double dm) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= nsites * N) return;
-  const long long j = t / N;
-  const int a = (int)(t - j * N);
-  Y[(j * 5) * (long long)N * N + (long long)a * N + a].re += dm;
-}
-
 __global__ void coarse_to_canonical_kernel(const Cx<double> *__restrict__ Yi, Cx<double> *__restrict__ Yc,
                                            long long nsites, int N) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -342,12 +322,6 @@ void launch_prolong_add(const Cx<R> *V, const Cx<R> *coarse, Cx<R> *fine, BlockG
   MG_LAUNCHED();
 }
 
-void launch_prolongator_column(const Cx<double> *V, Cx<double> *fine, BlockGeo bg, int Nv, int k, cudaStream_t s) {
-  const int threads = 128;
-  prolongator_column_kernel<<<grid_for(bg.nblocks * 32, threads), threads, 0, s>>>(V, fine, bg, Nv, k);
-  MG_LAUNCHED();
-}
-
 static int warps_for_smem(size_t per_warp, size_t limit) {
   int w = (int)(limit / per_warp);
   if (w > 4) w = 4;
@@ -389,11 +363,6 @@ void launch_galerkin_wilson(const Cx<double> *U, double diag, const Cx<double> *
 void launch_galerkin_stencil(const Cx<double> *Y, const Cx<double> *V, Cx<double> *Yc, BlockGeo bg, int Nv,
                              cudaStream_t s) {
   launch_galerkin_impl<false>(Y, 0.0, V, Yc, bg, Nv, s);
-}
-
-void launch_shift_diag(Cx<double> *Y, long long nsites, int N, double dm, cudaStream_t s) {
-  shift_diag_kernel<<<grid_for(nsites * N, 256), 256, 0, s>>>(Y, nsites, N, dm);
-  MG_LAUNCHED();
 }
 
 void launch_coarse_to_canonical(const Cx<double> *Yi, Cx<double> *Yc, long long nsites, int N, cudaStream_t s) {
