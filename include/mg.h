@@ -166,6 +166,14 @@ int mg_prolong(mg_ctx *ctx, int level, const void *coarse, void *fine);
  * (paper: the five V-cycle steps). b, x: device complex128 [x][s]. */
 int mg_vcycle(mg_ctx *ctx, const void *b, void *x);
 
+/* One coarsest-level solve x = A_c^{-1} b (paper: the coarsest level of the
+ * V-cycle is an exact solve), FP64, coarsest-level layout [site][a]: dense LU
+ * when the coarsest dimension is <= coarsest_lu_max, else the persistent GCR
+ * kernel to relative residual coarsest_tol. iters (may be NULL): iterations of
+ * the iterative solve (0 for LU). ms (may be NULL): device time of the solve,
+ * from CUDA events recorded on the context's stream around it. */
+int mg_coarsest_solve(mg_ctx *ctx, const void *b, void *x, long long *iters, double *ms);
+
 /* nu MR iterations x = R b from x = 0 on level l (FP64), omega from the params. */
 int mg_smooth(mg_ctx *ctx, int level, const void *b, void *x, int nu);
 

@@ -89,6 +89,7 @@ def load():
         "mg_level_size": (I, [ctxp, I, P(ctypes.c_longlong), P(I)]),
         "mg_kernel_launches": (ctypes.c_longlong, []),
         "mg_smooth_fine_noalloc": (I, [P(mg_geom), VP, D, VP, VP, I, D, VP]),
+        "mg_coarsest_solve": (I, [ctxp, VP, VP, P(ctypes.c_longlong), P(D)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -103,7 +104,7 @@ def exported_symbols():
     return ["mg_default_params", "mg_setup", "mg_solve", "mg_update_mass", "mg_destroy", "mg_last_error",
             "mg_dslash", "mg_level_apply", "mg_restrict", "mg_prolong", "mg_vcycle", "mg_smooth", "mg_build_level",
             "mg_get_null_vectors", "mg_get_prolongator", "mg_get_coarse_op", "mg_level_size", "mg_kernel_launches",
-            "mg_smooth_fine_noalloc"]
+            "mg_smooth_fine_noalloc", "mg_coarsest_solve"]
 
 
 def _check(code: int):
@@ -264,6 +265,15 @@ class Context:
     def vcycle(self, b: torch.Tensor, x: torch.Tensor):
         n = self._numel(0)
         _check(load().mg_vcycle(self._need(), _ptr(b, torch.complex128, n), _ptr(x, torch.complex128, n)))
+
+    def coarsest_solve(self, b: torch.Tensor, x: torch.Tensor):
+        """mg_coarsest_solve: x = A_c^{-1} b on the coarsest level; returns (iterations, device ms)."""
+        n = self._numel(int(self.params.levels) - 1)
+        it = ctypes.c_longlong(0)
+        ms = ctypes.c_double(0.0)
+        _check(load().mg_coarsest_solve(self._need(), _ptr(b, torch.complex128, n), _ptr(x, torch.complex128, n),
+                                        ctypes.byref(it), ctypes.byref(ms)))
+        return int(it.value), float(ms.value)
 
     def smooth(self, level: int, b: torch.Tensor, x: torch.Tensor, nu: int):
         n = self._numel(level)

@@ -889,6 +889,30 @@ int mg_vcycle(mg_ctx *c, const void *b, void *x) {
   });
 }
 
+int mg_coarsest_solve(mg_ctx *c, const void *b, void *x, long long *iters, double *ms) {
+  return guarded([&] {
+    need_ctx(c);
+    need_ptr(b);
+    need_ptr(x);
+    check_fresh(*c);
+    collect_coarsest(*c);
+    cudaEvent_t e0, e1;
+    MG_CUDA(cudaEventCreate(&e0));
+    MG_CUDA(cudaEventCreate(&e1));
+    MG_CUDA(cudaEventRecord(e0, c->s));
+    coarsest_solve64(*c, static_cast<const Cx<double> *>(b), static_cast<Cx<double> *>(x));
+    MG_CUDA(cudaEventRecord(e1, c->s));
+    MG_CUDA(cudaEventSynchronize(e1));
+    float t = 0.f;
+    MG_CUDA(cudaEventElapsedTime(&t, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const long long it = collect_coarsest(*c);
+    if (iters) *iters = it;
+    if (ms) *ms = t;
+  });
+}
+
 int mg_smooth(mg_ctx *c, int level, const void *b, void *x, int nu) {
   return guarded([&] {
     need_level(c, level, false);

@@ -154,3 +154,18 @@ def test_full_adaptive_setup_matches_oracle(levels):
     for l in range(levels - 1):
         assert rel_err(to_host(ctx.null_vectors(l)), np.stack(hier.vecs[l])) < 1e-9, l
         assert rel_err(to_host(ctx.coarse_op(l + 1)), hier.ops[l + 1].Y) < 1e-9, l
+
+
+@pytest.mark.parametrize("dims,lu_max", [((32, 32), 100000), ((32, 32), 0), ((64, 64), 0)])
+def test_coarsest_solve_matches_oracle(dims, lu_max):
+    # the coarsest exact solve alone: dense LU, or the persistent GCR kernel to 1e-12
+    import torch
+    U, _, _ = inputs.schwinger_links(dims[0], 6.0, sweeps=100, workload_id=5)
+    hier, ctx, _ = make_pair(dims, 0.02, [(4, 4), (2, 2)], [8, 8], U, coarsest_lu_max=lu_max, coarsest_tol=1e-12)
+    n, k = ctx.level_size(2)
+    b = inputs.gaussian_complex(n * k, 8, 80).reshape(n, k)
+    x = torch.empty((n, k), dtype=torch.complex128, device="cuda")
+    iters, ms = ctx.coarsest_solve(to_dev(b), x)
+    assert (iters == 0) == (lu_max > 0) and ms > 0
+    want = np.linalg.solve(solvers.stencil_matrix(hier.ops[2]), b.reshape(-1)).reshape(n, k)
+    assert rel_err(to_host(x), want) < 1e-9
