@@ -210,6 +210,15 @@ int mg_level_size(mg_ctx *ctx, int level, long long *n_sites, int *n_int);
 int mg_smooth_fine_noalloc(const mg_geom *g, const void *U, double m, const void *b, void *x, int nu, double omega,
                            void *stream);
 
+/* Self-test of the bounded device-side wait used by the persistent kernels (a
+ * failure-detection check; the paper has no counterpart). Launches a 2-CTA
+ * cooperative kernel whose grid barrier expects 2 + missing_arrivals arrivals
+ * (missing_arrivals 0 or 1). With 1, nothing ever releases the barrier: each
+ * wait gives up after a bounded number of polls (milliseconds), the kernel
+ * returns and the call reports MG_ERR_TIMEOUT; the context stays usable.
+ * With 0 the barrier completes and the call returns MG_OK. */
+int mg_selftest_barrier(int missing_arrivals, void *stream);
+
 /* Number of kernels this library has launched since the process started. */
 long long mg_kernel_launches(void);
 

@@ -90,6 +90,7 @@ def load():
         "mg_kernel_launches": (ctypes.c_longlong, []),
         "mg_smooth_fine_noalloc": (I, [P(mg_geom), VP, D, VP, VP, I, D, VP]),
         "mg_coarsest_solve": (I, [ctxp, VP, VP, P(ctypes.c_longlong), P(D)]),
+        "mg_selftest_barrier": (I, [I, VP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -104,7 +105,8 @@ def exported_symbols():
     return ["mg_default_params", "mg_setup", "mg_solve", "mg_update_mass", "mg_destroy", "mg_last_error",
             "mg_dslash", "mg_level_apply", "mg_restrict", "mg_prolong", "mg_vcycle", "mg_smooth", "mg_build_level",
             "mg_get_null_vectors", "mg_get_prolongator", "mg_get_coarse_op", "mg_level_size", "mg_kernel_launches",
-            "mg_smooth_fine_noalloc", "mg_coarsest_solve"]
+            "mg_smooth_fine_noalloc", "mg_coarsest_solve",
+            "mg_selftest_barrier"]
 
 
 def _check(code: int):
@@ -175,6 +177,11 @@ def mg_smooth_fine_noalloc(U: torch.Tensor, b: torch.Tensor, x: torch.Tensor, m:
     _check(load().mg_smooth_fine_noalloc(ctypes.byref(g), _ptr(U, torch.complex128, 2 * V), float(m),
                                          _ptr(b, torch.complex128, 2 * V), _ptr(x, torch.complex128, 2 * V),
                                          int(nu), float(omega), _stream(stream)))
+
+
+def mg_selftest_barrier(missing_arrivals: int, stream=None):
+    """Bounded grid-barrier self-test: raises MGError(MG_ERR_TIMEOUT) when an arrival is missing."""
+    _check(load().mg_selftest_barrier(int(missing_arrivals), _stream(stream)))
 
 
 def mg_kernel_launches() -> int:

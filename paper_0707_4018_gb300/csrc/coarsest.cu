@@ -806,3 +806,59 @@ void launch_coarsest_gcr_smem(const Cx<double> *Yt, const Cx<double> *Minv, Geo2
 }
 
 }  // namespace mg
+
+namespace mg {
+
+// ---------------------------------------------------------------------------
+// Self-test of the bounded grid barrier: a 2-CTA cooperative kernel waits at a
+// barrier that expects `expected` arrivals. With expected = 3 the generation
+// flag never advances (nothing sets it), every wait gives up after
+// `spin_limit` polls, status[0] records the timeout and the kernel returns.
+// ---------------------------------------------------------------------------
+__global__ void barrier_selftest_kernel(unsigned int *bar, unsigned int expected, long long spin_limit, int *status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int *gen = bar + 1;
+    const unsigned int g = *gen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(bar, 1u);
+    int good = 1;
+    if (arrived == expected - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long polls = 0;
+      while (*gen == g) {
+        if (++polls > spin_limit) {
+          good = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    if (!good) atomicExch(status, 1);
+    s_ok = good;
+  }
+  __syncthreads();
+  if (!s_ok) return;
+}
+
+int barrier_selftest(unsigned int expected, long long spin_limit, cudaStream_t s) {
+  DevBuf<unsigned int> bar;
+  DevBuf<int> status;
+  bar.alloc(2);
+  status.alloc(1);
+  MG_CUDA(cudaMemsetAsync(bar.p, 0, 2 * sizeof(unsigned int), s));
+  MG_CUDA(cudaMemsetAsync(status.p, 0, sizeof(int), s));
+  void *args[] = {&bar.p, &expected, &spin_limit, &status.p};
+  MG_CUDA(cudaLaunchCooperativeKernel((const void *)barrier_selftest_kernel, dim3(2), dim3(32), args, 0, s));
+  MG_LAUNCHED();
+  int h = 0;
+  MG_CUDA(cudaMemcpyAsync(&h, status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MG_CUDA(cudaStreamSynchronize(s));
+  return h;
+}
+
+}  // namespace mg

@@ -124,6 +124,8 @@ void launch_coarsest_gcr(const Cx<double> *Yt, const Cx<double> *Minv, Geo2 g, i
                          unsigned int *bar, double tol, int restart, int max_iter, int *out, double *out_rel, int grid,
                          cudaStream_t s);
 int coarsest_gcr_grid(int device);
+// bounded-barrier self-test (2 CTAs, `expected` arrivals); returns 1 if a wait gave up
+int barrier_selftest(unsigned int expected, long long spin_limit, cudaStream_t s);
 constexpr int kCoarsestSlots = 68;
 // Same solve with each CTA's rows, vectors and Krylov basis resident in shared memory
 // (N = 8, restart <= 16, at most 64 dofs per CTA when spread over `sms` CTAs): rpub, ypub

@@ -889,6 +889,15 @@ int mg_vcycle(mg_ctx *c, const void *b, void *x) {
   });
 }
 
+int mg_selftest_barrier(int missing_arrivals, void *stream) {
+  return guarded([&] {
+    if (missing_arrivals < 0 || missing_arrivals > 1) fail(MG_ERR_INVALID_ARG, "missing_arrivals must be 0 or 1");
+    // about 2^16 polls of >= 64 ns: the wait gives up within a few milliseconds
+    const int timed_out = barrier_selftest(2u + (unsigned)missing_arrivals, 1LL << 16, static_cast<cudaStream_t>(stream));
+    if (timed_out) fail(MG_ERR_TIMEOUT, "grid barrier self-test: the wait ran out (as arranged when an arrival is missing)");
+  });
+}
+
 int mg_coarsest_solve(mg_ctx *c, const void *b, void *x, long long *iters, double *ms) {
   return guarded([&] {
     need_ctx(c);
