@@ -169,3 +169,53 @@ def test_coarsest_solve_matches_oracle(dims, lu_max):
     assert (iters == 0) == (lu_max > 0) and ms > 0
     want = np.linalg.solve(solvers.stencil_matrix(hier.ops[2]), b.reshape(-1)).reshape(n, k)
     assert rel_err(to_host(x), want) < 1e-9
+
+
+def test_mixed_precision_vcycle_close_to_oracle():
+    # FP32 smoother / transfers / coarse operators (FP64 coarsest) against the FP64 oracle cycle:
+    # the difference is FP32 rounding amplified by the cycle, far below the cycle's own action
+    import torch
+    dims = (32, 32)
+    U, _, _ = inputs.schwinger_links(32, 6.0, sweeps=100, workload_id=5)
+    hier, ctx, _ = make_pair(dims, 0.02, [(4, 4), (2, 2)], [8, 8], U, precision=1, coarsest_lu_max=4096)
+    b = inputs.gaussian_source(*dims, seed=6)
+    x = torch.empty((1024, 2), dtype=torch.complex128, device="cuda")
+    ctx.vcycle(to_dev(b), x)
+    want = solvers.vcycle(hier, 0, b)
+    err = rel_err(to_host(x), want)
+    assert err < 1e-5, err
+
+
+def test_update_mass_matches_oracle():
+    import torch
+    dims = (32, 32)
+    U, _, _ = inputs.schwinger_links(32, 6.0, sweeps=100, workload_id=5)
+    hier, ctx, _ = make_pair(dims, 0.0, [(4, 4), (2, 2)], [8, 8], U, coarsest_lu_max=4096)
+    ctx.update_mass(0.31)
+    setup.update_mass(hier, 0.31)
+    for l in (1, 2):
+        assert rel_err(to_host(ctx.coarse_op(l)), hier.ops[l].Y) < 1e-13
+    b = inputs.gaussian_source(*dims, seed=7)
+    x = torch.empty((1024, 2), dtype=torch.complex128, device="cuda")
+    ctx.vcycle(to_dev(b), x)
+    assert rel_err(to_host(x), solvers.vcycle(hier, 0, b)) < 1e-10
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_is_bitwise_reproducible(precision):
+    # fixed-order reductions everywhere: two runs give identical bits
+    import torch
+    import paper_0707_4018_gb300 as mg
+    L = 64
+    U = to_dev(inputs.links_from_angles(inputs.metropolis_u1_2d(L, L, 6.0, 100, seed=3)[0]))
+    chi = to_dev(inputs.gaussian_source(L, L, seed=4))
+    outs = []
+    for _ in range(2):
+        ctx = mg.Context.setup(U, 0.0, (L, L), mg.mg_default_params(levels=3, blocks=[(4, 4), (2, 2)], Nv=[8, 8],
+                                                                     precision=precision, coarsest_lu_max=0,
+                                                                     coarsest_tol=1e-3))
+        psi = torch.empty_like(chi)
+        ctx.solve(chi, psi, 1e-10)
+        outs.append(to_host(psi))
+        ctx.close()
+    assert np.array_equal(outs[0].view(np.uint64), outs[1].view(np.uint64))

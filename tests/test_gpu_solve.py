@@ -162,3 +162,20 @@ def test_three_level_256_full_size(precision, beta):
                             precision=precision, coarsest_tol=1e-6)
         assert st["converged"]
         assert _true_rel(U, mc + dm, lat, psi, chi) <= 1e-10
+
+
+@pytest.mark.parametrize("precision", [1])
+def test_three_level_1024_large_size_paths(precision):
+    # 1024^2 exercises the large-size code paths: the global-memory coarsest kernel
+    # (128^2 coarse sites do not fit the shared-memory variant) and wide reductions.
+    # A random U(1) field with a heavy mass keeps the solve short; the true residual
+    # is recomputed by the oracle's D.
+    L = 1024
+    lat = Lattice((L, L))
+    U = inputs.hot_links(L, L, seed=21)
+    chi = inputs.gaussian_source(L, L, seed=22)
+    m = 0.5
+    psi, st, _ = _solve(U, m, (L, L), chi, 1e-10, levels=3, blocks=[(4, 4), (2, 2)], Nv=[8, 8],
+                        precision=precision, coarsest_tol=1e-2, n_pass=2)
+    assert st["converged"]
+    assert _true_rel(U, m, lat, psi, chi) <= 1e-10
