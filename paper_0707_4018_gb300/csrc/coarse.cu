@@ -14,7 +14,10 @@ namespace mg {
 template <typename R, int NT>
 __global__ void __launch_bounds__(256) coarse_apply_kernel(const Cx<R> *__restrict__ Y, const Cx<R> *__restrict__ in,
                                                            Cx<R> *__restrict__ out, int L0, int L1, int Nrt,
-                                                           const Cx<R> *__restrict__ b, R a, R c) {
+                                                           const Cx<R> *__restrict__ b, R a, R c, long long ldv) {
+  in += blockIdx.y * ldv;
+  out += blockIdx.y * ldv;
+  if (b != nullptr) b += blockIdx.y * ldv;
   const int N = NT > 0 ? NT : Nrt;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long j = t / N;
@@ -46,20 +49,21 @@ __global__ void __launch_bounds__(256) coarse_apply_kernel(const Cx<R> *__restri
 
 template <typename R>
 void launch_coarse_apply(const Cx<R> *Y, const Cx<R> *in, Cx<R> *out, Geo2 g, int N, const Cx<R> *b, double a,
-                         double c, cudaStream_t s) {
+                         double c, cudaStream_t s, int nvec) {
   const int threads = 256;
-  const unsigned int grid = grid_for(g.nsites * N, threads);
+  const dim3 grid(grid_for(g.nsites * N, threads), nvec);
+  const long long ldv = g.nsites * N;
   if (N == 8)
-    coarse_apply_kernel<R, 8><<<grid, threads, 0, s>>>(Y, in, out, g.L0, g.L1, N, b, (R)a, (R)c);
+    coarse_apply_kernel<R, 8><<<grid, threads, 0, s>>>(Y, in, out, g.L0, g.L1, N, b, (R)a, (R)c, ldv);
   else
-    coarse_apply_kernel<R, 0><<<grid, threads, 0, s>>>(Y, in, out, g.L0, g.L1, N, b, (R)a, (R)c);
+    coarse_apply_kernel<R, 0><<<grid, threads, 0, s>>>(Y, in, out, g.L0, g.L1, N, b, (R)a, (R)c, ldv);
   MG_LAUNCHED();
 }
 
 template void launch_coarse_apply<double>(const Cx<double> *, const Cx<double> *, Cx<double> *, Geo2, int,
-                                          const Cx<double> *, double, double, cudaStream_t);
+                                          const Cx<double> *, double, double, cudaStream_t, int);
 template void launch_coarse_apply<float>(const Cx<float> *, const Cx<float> *, Cx<float> *, Geo2, int,
-                                         const Cx<float> *, double, double, cudaStream_t);
+                                         const Cx<float> *, double, double, cudaStream_t, int);
 
 // ---------------------------------------------------------------------------
 // dense matrix of the coarsest stencil, column-major A[col * n + row]

@@ -25,26 +25,28 @@ struct OpDesc {
 // step = true: alpha = omega <Ar_old, r_old>/|Ar_old|^2 from sc_old; x (+)= alpha r_old
 // (x_init: x = alpha r_old); r_new = r_old - alpha Ar_old; Ar_new = A r_new; sc_new as above.
 // r_new / Ar_new must differ from r_old / Ar_old, sc_new from sc_old.
+// Batched over nvec vectors stored with stride n (the level's dofs); vector v uses the
+// scalars sc[4 v .. 4 v + 2].
 template <typename R>
 void launch_mr_iteration(const OpDesc<R> &op, bool step, const Cx<R> *r_old, const Cx<R> *Ar_old, const double *sc_old,
                          double omega, Cx<R> *x, bool x_init, Cx<R> *r_new, Cx<R> *Ar_new, double *sc_new,
-                         const ReduceWs &ws, cudaStream_t s);
+                         const ReduceWs &ws, cudaStream_t s, int nvec = 1);
 // x (+)= alpha r_old, alpha from sc_old (the last MR update)
 template <typename R>
 void launch_mr_last(const Cx<R> *r_old, const double *sc_old, double omega, Cx<R> *x, bool x_init, long long n,
-                    cudaStream_t s);
+                    cudaStream_t s, int nvec = 1);
 
 // ---- fine Wilson operator (2d, U(1), gamma_1 = sigma_1, gamma_2 = sigma_2) ----
 // out = a * D in + c * b   (b may be null when c == 0); D has diagonal `diag` = d + m
 template <typename R>
 void launch_dslash(const Cx<R> *U, const Cx<R> *in, Cx<R> *out, Geo2 g, double diag, const Cx<R> *b, double a,
-                   double c, cudaStream_t s);
+                   double c, cudaStream_t s, int nvec = 1);
 
 // ---- coarse stencil operator, N x N blocks, internal layout Y[j][dir][col][row] ----
 // out = a * A in + c * b
 template <typename R>
 void launch_coarse_apply(const Cx<R> *Y, const Cx<R> *in, Cx<R> *out, Geo2 g, int N, const Cx<R> *b, double a,
-                         double c, cudaStream_t s);
+                         double c, cudaStream_t s, int nvec = 1);
 
 // ---- BLAS-1 ----
 template <typename R>
@@ -81,10 +83,12 @@ void launch_gcr_project_update(const Cx<double> *W, Cx<double> *Wk, const Cx<dou
 // ---- transfer between levels ----
 // coarse[b][k] = sum_i conj(V[b][k][i]) fine[site(b,s)][a]
 template <typename R>
-void launch_restrict(const Cx<R> *V, const Cx<R> *fine, Cx<R> *coarse, BlockGeo bg, int Nv, cudaStream_t s);
+void launch_restrict(const Cx<R> *V, const Cx<R> *fine, Cx<R> *coarse, BlockGeo bg, int Nv, cudaStream_t s,
+                     int nvec = 1);
 // fine[site(b,s)][a] += sum_k V[b][k][i] coarse[b][k]
 template <typename R>
-void launch_prolong_add(const Cx<R> *V, const Cx<R> *coarse, Cx<R> *fine, BlockGeo bg, int Nv, cudaStream_t s);
+void launch_prolong_add(const Cx<R> *V, const Cx<R> *coarse, Cx<R> *fine, BlockGeo bg, int Nv, cudaStream_t s,
+                        int nvec = 1);
 // block Gram-Schmidt (modified, twice, k order) of Nv level vectors into V[b][k][i]; FP64
 void launch_block_mgs(const Cx<double> *vecs, long long vec_stride, Cx<double> *V, BlockGeo bg, int Nv,
                       double *min_norm_dev, cudaStream_t s);

@@ -54,10 +54,11 @@ struct Level {
 
 // scalar slots on the device (FP64)
 enum : int {
-  kSlotMR = 0,          // 8 per level (two alternating MR reductions)
-  kSlotOuter = 64,      // outer GCR reductions: 2 (restart + 2) doubles
-  kSlotCount = 1024
+  kSlotMR = 0,          // per level: two alternating MR reductions of 4 doubles per batched vector
+  kSlotOuter = 1024,    // outer GCR reductions: 2 (restart + 2) doubles
+  kSlotCount = 2048
 };
+constexpr int kMaxBatch = 32;  // vectors per batched V-cycle (the setup batches the Nv near-null vectors)
 
 // an instantiated graph of one V-cycle with the launches and operator
 // applications it replays
@@ -96,6 +97,7 @@ struct mg_ctx {
   mg::DevBuf<int> cg_out;  // [0] iterations, [1] timeout flag, [2] solves above tolerance
   int cg_grid = 0;
   bool cg_smem = false;  // shared-memory-resident coarsest solver
+  int nbatch = 1;        // vectors the FP64 level work buffers hold
   // outer
   mg::DevBuf<mg::Cx<double>> oZ, oW, orr;
   mg::DevBuf<mg::Cx<float>> z32;
@@ -155,13 +157,13 @@ const Cx<float> *Vof<float>(const Level &L) { return L.V32.p; }
 // out = a * A_l in + c * b
 template <typename R>
 static void apply_op(mg_ctx &c, int l, const Cx<R> *in, Cx<R> *out, const Cx<R> *b = nullptr, double a = 1.0,
-                     double cc = 0.0) {
+                     double cc = 0.0, int nvec = 1) {
   Level &L = c.lv[l];
   if (l == 0)
-    launch_dslash<R>(Uof<R>(c), in, out, L.geo, diag_of(c), b, a, cc, c.s);
+    launch_dslash<R>(Uof<R>(c), in, out, L.geo, diag_of(c), b, a, cc, c.s, nvec);
   else
-    launch_coarse_apply<R>(Yof<R>(L), in, out, L.geo, L.nint, b, a, cc, c.s);
-  c.apps[l]++;
+    launch_coarse_apply<R>(Yof<R>(L), in, out, L.geo, L.nint, b, a, cc, c.s, nvec);
+  c.apps[l] += nvec;
 }
 
 template <typename R>
@@ -178,43 +180,44 @@ static OpDesc<R> op_of(mg_ctx &c, int l) {
 }
 
 // x (+)= nu MR iterations for A_l x = b from zero (accumulate: added to x), with the
-// fused kernels: nu + 1 launches. b may be the level's r buffer (consumed then).
+// fused kernels: nu + 1 launches for a batch of nvec vectors (stride n). b may be the
+// level's r buffer (consumed then).
 template <typename R>
-static void smooth(mg_ctx &c, int l, const Cx<R> *b, Cx<R> *x, int nu, bool accumulate) {
+static void smooth(mg_ctx &c, int l, const Cx<R> *b, Cx<R> *x, int nu, bool accumulate, int nvec = 1) {
   Level &L = c.lv[l];
   Work<R> &w = work<R>(L);
   if (nu <= 0) {
-    if (!accumulate) launch_zero<R>(x, L.n, c.s);
+    if (!accumulate) launch_zero<R>(x, L.n * nvec, c.s);
     return;
   }
-  double *sc[2] = {c.scal.p + kSlotMR + 8 * l, c.scal.p + kSlotMR + 8 * l + 4};
+  double *sc[2] = {c.scal.p + kSlotMR + 8 * kMaxBatch * l, c.scal.p + kSlotMR + 8 * kMaxBatch * l + 4 * kMaxBatch};
   const OpDesc<R> op = op_of<R>(c, l);
   Cx<R> *rbuf[2] = {w.r.p, w.r2.p};
   Cx<R> *Arbuf[2] = {w.Ar.p, w.Ar2.p};
   launch_mr_iteration<R>(op, false, b, nullptr, nullptr, c.p.omega, nullptr, false, nullptr, Arbuf[0], sc[0], c.ws,
-                         c.s);
-  c.apps[l]++;
+                         c.s, nvec);
+  c.apps[l] += nvec;
   const Cx<R> *r_old = b;
   int rsel = (b == rbuf[0]) ? 1 : 0, asel = 1, ssel = 1;
   for (int i = 1; i < nu; ++i) {
     launch_mr_iteration<R>(op, true, r_old, Arbuf[asel ^ 1], sc[ssel ^ 1], c.p.omega, x, i == 1 && !accumulate,
-                           rbuf[rsel], Arbuf[asel], sc[ssel], c.ws, c.s);
-    c.apps[l]++;
+                           rbuf[rsel], Arbuf[asel], sc[ssel], c.ws, c.s, nvec);
+    c.apps[l] += nvec;
     r_old = rbuf[rsel];
     rsel ^= 1;
     asel ^= 1;
     ssel ^= 1;
   }
-  launch_mr_last<R>(r_old, sc[ssel ^ 1], c.p.omega, x, nu == 1 && !accumulate, L.n, c.s);
+  launch_mr_last<R>(r_old, sc[ssel ^ 1], c.p.omega, x, nu == 1 && !accumulate, L.n, c.s, nvec);
 }
+
+static void precondition(mg_ctx &c, const Cx<double> *r, Cx<double> *z);
 
 struct GcrOut {
   int iters = 0;
   bool converged = false;
   double rel = 0.0;
 };
-
-static void precondition(mg_ctx &c, const Cx<double> *r, Cx<double> *z);
 
 // Outer flexible GCR on D (FP64) with the V-cycle as right preconditioner.
 // Per iteration: z = V r, w = D z, one fused reduction of <W_j, w>, |w|^2, <w, r>;
@@ -345,11 +348,13 @@ static void check_fresh(const mg_ctx &c) {
     if (L.stale) fail(MG_ERR_STATE, "hierarchy has a level whose prolongator predates its operator; rebuild it");
 }
 
-// x = V^(l) b (the five steps); b must not alias the level's work vectors or x
+// x = V^(l) b (the five steps) for a batch of nvec vectors (stride: the level's dofs);
+// b must not alias the level's work vectors or x
 template <typename R>
-static void vcycle(mg_ctx &c, int l, const Cx<R> *b, Cx<R> *x) {
+static void vcycle(mg_ctx &c, int l, const Cx<R> *b, Cx<R> *x, int nvec = 1) {
   if (l == c.p.levels - 1) {
-    coarsest_solve<R>(c, b, x);
+    const long long n = c.lv[l].n;
+    for (int v = 0; v < nvec; ++v) coarsest_solve<R>(c, b + v * n, x + v * n);
     return;
   }
   Level &L = c.lv[l];
@@ -357,17 +362,17 @@ static void vcycle(mg_ctx &c, int l, const Cx<R> *b, Cx<R> *x) {
   Work<R> &w = work<R>(L);
   Work<R> &wc = work<R>(C);
   // 1. pre-relaxation from zero
-  smooth<R>(c, l, b, x, c.p.nu_pre, false);
+  smooth<R>(c, l, b, x, c.p.nu_pre, false, nvec);
   // 2. restrict the residual
-  apply_op<R>(c, l, x, w.r.p, b, -1.0, 1.0);
-  launch_restrict<R>(Vof<R>(L), w.r.p, wc.b.p, L.bg, L.Nv, c.s);
+  apply_op<R>(c, l, x, w.r.p, b, -1.0, 1.0, nvec);
+  launch_restrict<R>(Vof<R>(L), w.r.p, wc.b.p, L.bg, L.Nv, c.s, nvec);
   // 3. coarse V-cycle (or exact coarsest solve)
-  vcycle<R>(c, l + 1, wc.b.p, wc.x.p);
+  vcycle<R>(c, l + 1, wc.b.p, wc.x.p, nvec);
   // 4. coarse-grid correction
-  launch_prolong_add<R>(Vof<R>(L), wc.x.p, x, L.bg, L.Nv, c.s);
+  launch_prolong_add<R>(Vof<R>(L), wc.x.p, x, L.bg, L.Nv, c.s, nvec);
   // 5. post-relaxation on the final residual
-  apply_op<R>(c, l, x, w.r.p, b, -1.0, 1.0);
-  smooth<R>(c, l, w.r.p, x, c.p.nu_post, true);
+  apply_op<R>(c, l, x, w.r.p, b, -1.0, 1.0, nvec);
+  smooth<R>(c, l, w.r.p, x, c.p.nu_post, true, nvec);
 }
 
 // Runs `body` (a fixed sequence of launches on the context stream) through a
@@ -477,24 +482,20 @@ static void setup_level(mg_ctx &c, int l, bool full) {
   Level &L = c.lv[l];
   const long long n = L.n;
   // pass 1: random vectors relaxed on A x = 0 (nu_setup MR iterations from x = v: the
-  // corrections solve A d = -A v from d = 0)
-  for (int k = 0; k < L.Nv; ++k) {
-    Cx<double> *v = L.nullv.p + (long long)k * n;
-    launch_gaussian(v, n, c.p.seed, k, l, c.s);
-    apply_op<double>(c, l, v, L.tA.p, nullptr, -1.0, 0.0);  // r = -A v
-    smooth<double>(c, l, L.tA.p, v, c.p.nu_setup, true);
-  }
+  // corrections solve A d = -A v from d = 0), all Nv vectors as one batch
+  Cx<double> *V = L.nullv.p;
+  const int nv = L.Nv;
+  for (int k = 0; k < nv; ++k) launch_gaussian(V + (long long)k * n, n, c.p.seed, k, l, c.s);
+  apply_op<double>(c, l, V, L.tA.p, nullptr, -1.0, 0.0, nv);  // r = -A v
+  smooth<double>(c, l, L.tA.p, V, c.p.nu_setup, true, nv);
   const int n_pass = full ? c.p.n_pass : 1;
   for (int pass = 1; pass <= n_pass; ++pass) {
     if (pass > 1) {
-      // v <- v - V(A v): one V-cycle on the homogeneous problem
-      for (int k = 0; k < L.Nv; ++k) {
-        Cx<double> *v = L.nullv.p + (long long)k * n;
-        apply_op<double>(c, l, v, L.tA.p);
-        graph_run(c, c.setup_vc[l], [&] { vcycle<double>(c, l, L.tA.p, L.tB.p); });
-        launch_xmy<double>(v, L.tB.p, n, c.s);  // tB = v - V(A v)
-        launch_copy<double>(L.tB.p, v, n, c.s);
-      }
+      // v <- v - V(A v): one V-cycle on the homogeneous problem, batched over the Nv vectors
+      apply_op<double>(c, l, V, L.tA.p, nullptr, 1.0, 0.0, nv);
+      graph_run(c, c.setup_vc[l], [&] { vcycle<double>(c, l, L.tA.p, L.tB.p, nv); });
+      launch_xmy<double>(V, L.tB.p, n * nv, c.s);  // tB = v - V(A v)
+      launch_copy<double>(L.tB.p, V, n * nv, c.s);
     }
     build_level(c, l);
     if (l + 1 == c.p.levels - 1)
@@ -561,6 +562,8 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
   c->graphs_ok = std::getenv("MG_NO_GRAPHS") == nullptr;
   MG_CUDA(cudaMallocHost(&c->host, 512 * sizeof(double)));
   c->lv.resize(p->levels);
+  c->nbatch = 1;
+  for (int l = 0; l + 1 < p->levels; ++l) c->nbatch = std::max(c->nbatch, p->Nv[l]);
   int L0 = g->dims[0], L1 = g->dims[1], nint = 2;
   const bool f32 = p->precision == MG_FP32;
   for (int l = 0; l < p->levels; ++l) {
@@ -572,10 +575,11 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
       L.Y64.alloc(L.geo.nsites * 5 * (size_t)nint * nint);
       if (f32) L.Y32.alloc(L.Y64.n);
     }
-    L.w64.b.alloc(L.n);
-    L.w64.x.alloc(L.n);
-    L.w64.r.alloc(L.n);
-    L.w64.Ar.alloc(L.n);
+    const size_t nb = (size_t)c->nbatch;
+    L.w64.b.alloc(L.n * nb);
+    L.w64.x.alloc(L.n * nb);
+    L.w64.r.alloc(L.n * nb);
+    L.w64.Ar.alloc(L.n * nb);
     if (f32) {
       L.w32.b.alloc(L.n);
       L.w32.x.alloc(L.n);
@@ -591,8 +595,8 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
       L.V64.alloc((size_t)L.Nv * L.n);
       if (f32) L.V32.alloc(L.V64.n);
       L.mgs_min.alloc(L.bg.nblocks);
-      L.tA.alloc(L.n);
-      L.tB.alloc(L.n);
+      L.tA.alloc(L.n * (size_t)L.Nv);
+      L.tB.alloc(L.n * (size_t)L.Nv);
       L0 /= B0;
       L1 /= B1;
       nint = L.Nv;
@@ -601,8 +605,8 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
   const Level &F = c->lv[0];
   for (int l = 0; l < p->levels; ++l) {
     Level &L = c->lv[l];
-    L.w64.r2.alloc(L.n);
-    L.w64.Ar2.alloc(L.n);
+    L.w64.r2.alloc(L.n * (size_t)c->nbatch);
+    L.w64.Ar2.alloc(L.n * (size_t)c->nbatch);
     if (f32) {
       L.w32.r2.alloc(L.n);
       L.w32.Ar2.alloc(L.n);
@@ -655,7 +659,7 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
   long long cap = (long long)c->ws.max_blocks * 4;
   for (int l = 0; l < p->levels; ++l) {
     const long long units = l == 0 ? c->lv[l].geo.nsites : c->lv[l].n;
-    cap = std::max(cap, 3 * ((units + 255) / 256));
+    cap = std::max(cap, 3 * ((units + 255) / 256) * c->nbatch);
   }
   c->partials.alloc((size_t)cap + 16);
   c->ws.capacity = cap;

@@ -44,6 +44,20 @@ __global__ void __launch_bounds__(256) mr_wilson_kernel(const Cx<R> *__restrict_
   __shared__ double sh[32 * 3];
   const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long V = (long long)L0 * L1;
+  {  // vector blockIdx.y of the batch (stride 2 V); scalars, partials and ticket per vector
+    const long long off = blockIdx.y * 2 * V;
+    r_old += off;
+    if (STEP) {
+      Ar_old += off;
+      sc_old += 4 * blockIdx.y;
+      x += off;
+      r_new += off;
+    }
+    Ar_new += off;
+    sc_new += 4 * blockIdx.y;
+    partials += 3LL * gridDim.x * blockIdx.y;
+    ticket += blockIdx.y;
+  }
   double v[3] = {0.0, 0.0, 0.0};
   if (s < V) {
     MrSrc<R, STEP> src;
@@ -105,6 +119,20 @@ __global__ void __launch_bounds__(256) mr_stencil_kernel(const Cx<R> *__restrict
                                                          unsigned int *ticket) {
   __shared__ double sh[32 * 3];
   const int N = NT > 0 ? NT : Nrt;
+  {
+    const long long off = blockIdx.y * (long long)L0 * L1 * N;
+    r_old += off;
+    if (STEP) {
+      Ar_old += off;
+      sc_old += 4 * blockIdx.y;
+      x += off;
+      r_new += off;
+    }
+    Ar_new += off;
+    sc_new += 4 * blockIdx.y;
+    partials += 3LL * gridDim.x * blockIdx.y;
+    ticket += blockIdx.y;
+  }
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long j = t / N;
   const int row = (int)(t - j * N);
@@ -154,7 +182,9 @@ __global__ void __launch_bounds__(256) mr_stencil_kernel(const Cx<R> *__restrict
 template <typename R>
 __global__ void mr_last_kernel(const Cx<R> *__restrict__ r_old, const double *__restrict__ sc_old, double omega,
                                Cx<R> *__restrict__ x, int x_init, long long n) {
-  const Cx<R> alpha = mr_alpha<R>(sc_old, omega);
+  r_old += blockIdx.y * n;
+  x += blockIdx.y * n;
+  const Cx<R> alpha = mr_alpha<R>(sc_old + 4 * blockIdx.y, omega);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     Cx<R> xv = x_init ? mk((R)0, (R)0) : x[i];
     cmac(xv, alpha, r_old[i]);
@@ -166,11 +196,12 @@ __global__ void mr_last_kernel(const Cx<R> *__restrict__ r_old, const double *__
 template <typename R>
 void launch_mr_iteration(const OpDesc<R> &op, bool step, const Cx<R> *r_old, const Cx<R> *Ar_old, const double *sc_old,
                          double omega, Cx<R> *x, bool x_init, Cx<R> *r_new, Cx<R> *Ar_new, double *sc_new,
-                         const ReduceWs &ws, cudaStream_t s) {
+                         const ReduceWs &ws, cudaStream_t s, int nvec) {
   const int threads = 256;
+  if (nvec > 128) fail(MG_ERR_UNSUPPORTED, "MR batch larger than 128 vectors");
   if (op.wilson) {
-    const unsigned int grid = grid_for(op.geo.nsites, threads);
-    if ((long long)grid * 3 > ws.capacity) fail(MG_ERR_STATE, "MR reduction workspace too small");
+    const dim3 grid(grid_for(op.geo.nsites, threads), nvec);
+    if ((long long)grid.x * 3 * nvec > ws.capacity) fail(MG_ERR_STATE, "MR reduction workspace too small");
     if (step)
       mr_wilson_kernel<R, true><<<grid, threads, 0, s>>>(op.U, r_old, Ar_old, sc_old, omega, x, x_init ? 1 : 0, r_new,
                                                          Ar_new, op.geo.L0, op.geo.L1, (R)op.diag, ws.partials,
@@ -180,8 +211,8 @@ void launch_mr_iteration(const OpDesc<R> &op, bool step, const Cx<R> *r_old, con
                                                           op.geo.L0, op.geo.L1, (R)op.diag, ws.partials, sc_new,
                                                           ws.ticket);
   } else {
-    const unsigned int grid = grid_for(op.geo.nsites * op.N, threads);
-    if ((long long)grid * 3 > ws.capacity) fail(MG_ERR_STATE, "MR reduction workspace too small");
+    const dim3 grid(grid_for(op.geo.nsites * op.N, threads), nvec);
+    if ((long long)grid.x * 3 * nvec > ws.capacity) fail(MG_ERR_STATE, "MR reduction workspace too small");
 #define MG_MR_STENCIL(STEPV, NTV)                                                                                    \
   mr_stencil_kernel<R, STEPV, NTV><<<grid, threads, 0, s>>>(op.Y, r_old, Ar_old, sc_old, omega, x, x_init ? 1 : 0,   \
                                                             r_new, Ar_new, op.geo.L0, op.geo.L1, op.N, ws.partials, \
@@ -198,22 +229,23 @@ void launch_mr_iteration(const OpDesc<R> &op, bool step, const Cx<R> *r_old, con
 
 template <typename R>
 void launch_mr_last(const Cx<R> *r_old, const double *sc_old, double omega, Cx<R> *x, bool x_init, long long n,
-                    cudaStream_t s) {
+                    cudaStream_t s, int nvec) {
   long long b = (n + 255) / 256;
   if (b > 152LL * 16) b = 152LL * 16;
-  mr_last_kernel<R><<<(unsigned int)(b < 1 ? 1 : b), 256, 0, s>>>(r_old, sc_old, omega, x, x_init ? 1 : 0, n);
+  mr_last_kernel<R><<<dim3((unsigned int)(b < 1 ? 1 : b), nvec), 256, 0, s>>>(r_old, sc_old, omega, x,
+                                                                              x_init ? 1 : 0, n);
   MG_LAUNCHED();
 }
 
 template void launch_mr_iteration<double>(const OpDesc<double> &, bool, const Cx<double> *, const Cx<double> *,
                                           const double *, double, Cx<double> *, bool, Cx<double> *, Cx<double> *,
-                                          double *, const ReduceWs &, cudaStream_t);
+                                          double *, const ReduceWs &, cudaStream_t, int);
 template void launch_mr_iteration<float>(const OpDesc<float> &, bool, const Cx<float> *, const Cx<float> *,
                                          const double *, double, Cx<float> *, bool, Cx<float> *, Cx<float> *,
-                                         double *, const ReduceWs &, cudaStream_t);
+                                         double *, const ReduceWs &, cudaStream_t, int);
 template void launch_mr_last<double>(const Cx<double> *, const double *, double, Cx<double> *, bool, long long,
-                                     cudaStream_t);
+                                     cudaStream_t, int);
 template void launch_mr_last<float>(const Cx<float> *, const double *, double, Cx<float> *, bool, long long,
-                                    cudaStream_t);
+                                    cudaStream_t, int);
 
 }  // namespace mg

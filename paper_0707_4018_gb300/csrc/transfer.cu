@@ -27,6 +27,9 @@ __device__ __forceinline__ R shfl_sum(R v) {
 template <typename R, int NVM>
 __global__ void __launch_bounds__(128) restrict_kernel(const Cx<R> *__restrict__ V, const Cx<R> *__restrict__ fine,
                                                        Cx<R> *__restrict__ coarse, BlockGeo g, int Nv) {
+  // vector blockIdx.y of a batch: fine stride nblocks * Nb, coarse stride nblocks * Nv
+  fine += blockIdx.y * (g.nblocks * (long long)g.Nb);
+  coarse += blockIdx.y * (g.nblocks * (long long)Nv);
   const long long b = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (b >= g.nblocks) return;
@@ -58,6 +61,8 @@ __global__ void __launch_bounds__(128) restrict_kernel(const Cx<R> *__restrict__
 template <typename R>
 __global__ void __launch_bounds__(128) prolong_add_kernel(const Cx<R> *__restrict__ V, const Cx<R> *__restrict__ coarse,
                                                           Cx<R> *__restrict__ fine, BlockGeo g, int Nv) {
+  fine += blockIdx.y * (g.nblocks * (long long)g.Nb);
+  coarse += blockIdx.y * (g.nblocks * (long long)Nv);
   const long long b = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (b >= g.nblocks) return;
@@ -301,9 +306,10 @@ __global__ void gaussian_kernel(Cx<double> *out, long long n, unsigned long long
 
 // ---------------------------------------------------------------------------
 template <typename R>
-void launch_restrict(const Cx<R> *V, const Cx<R> *fine, Cx<R> *coarse, BlockGeo bg, int Nv, cudaStream_t s) {
+void launch_restrict(const Cx<R> *V, const Cx<R> *fine, Cx<R> *coarse, BlockGeo bg, int Nv, cudaStream_t s,
+                     int nvec) {
   const int threads = 128;
-  const unsigned int grid = grid_for(bg.nblocks * 32, threads);
+  const dim3 grid(grid_for(bg.nblocks * 32, threads), nvec);
   if (Nv <= 8)
     restrict_kernel<R, 8><<<grid, threads, 0, s>>>(V, fine, coarse, bg, Nv);
   else if (Nv <= 16)
@@ -316,9 +322,10 @@ void launch_restrict(const Cx<R> *V, const Cx<R> *fine, Cx<R> *coarse, BlockGeo 
 }
 
 template <typename R>
-void launch_prolong_add(const Cx<R> *V, const Cx<R> *coarse, Cx<R> *fine, BlockGeo bg, int Nv, cudaStream_t s) {
+void launch_prolong_add(const Cx<R> *V, const Cx<R> *coarse, Cx<R> *fine, BlockGeo bg, int Nv, cudaStream_t s,
+                        int nvec) {
   const int threads = 128;
-  prolong_add_kernel<R><<<grid_for(bg.nblocks * 32, threads), threads, 0, s>>>(V, coarse, fine, bg, Nv);
+  prolong_add_kernel<R><<<dim3(grid_for(bg.nblocks * 32, threads), nvec), threads, 0, s>>>(V, coarse, fine, bg, Nv);
   MG_LAUNCHED();
 }
 
@@ -381,11 +388,12 @@ void launch_gaussian(Cx<double> *out, long long n, unsigned long long seed, int 
 }
 
 template void launch_restrict<double>(const Cx<double> *, const Cx<double> *, Cx<double> *, BlockGeo, int,
-                                      cudaStream_t);
-template void launch_restrict<float>(const Cx<float> *, const Cx<float> *, Cx<float> *, BlockGeo, int, cudaStream_t);
+                                      cudaStream_t, int);
+template void launch_restrict<float>(const Cx<float> *, const Cx<float> *, Cx<float> *, BlockGeo, int, cudaStream_t,
+                                     int);
 template void launch_prolong_add<double>(const Cx<double> *, const Cx<double> *, Cx<double> *, BlockGeo, int,
-                                         cudaStream_t);
+                                         cudaStream_t, int);
 template void launch_prolong_add<float>(const Cx<float> *, const Cx<float> *, Cx<float> *, BlockGeo, int,
-                                        cudaStream_t);
+                                        cudaStream_t, int);
 
 }  // namespace mg
