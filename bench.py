@@ -48,7 +48,7 @@ WORKLOAD = ("2d U(1) Wilson-Dirac 256x256, beta in {3,6,10}, m-m_c in {0.005,0.0
 def mg_params(precision: int):
     import paper_0707_4018_gb300 as mg
     return mg.mg_default_params(levels=3, blocks=[(4, 4), (2, 2)], Nv=[8, 8], precision=precision,
-                                coarsest_tol=1e-2, coarsest_restart=16)
+                                coarsest_tol=0.2, coarsest_restart=16)
 
 
 def mcrit_table():
@@ -279,7 +279,7 @@ def cpu_baseline(budget_s: float = 25.0):
     U, _, _ = inputs.schwinger_links(L, beta, sweeps=2000, workload_id=WORKLOAD_ID)
     mc = table[f"w{WORKLOAD_ID}_L{L}_b{beta:g}"]["m_crit"]
     lat = Lattice((L, L))
-    p = osetup.MGParams(levels=3, blocks=((4, 4), (2, 2)), Nv=(8, 8), coarsest_tol=1e-2, coarsest_restart=16,
+    p = osetup.MGParams(levels=3, blocks=((4, 4), (2, 2)), Nv=(8, 8), coarsest_tol=0.2, coarsest_restart=16,
                         coarsest_lu_max=2048)
     seed = inputs.workload_seed(WORKLOAD_ID, L, beta)
     t0 = time.perf_counter()

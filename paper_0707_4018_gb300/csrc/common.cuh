@@ -217,6 +217,53 @@ __device__ __forceinline__ void grid_finish(double (&v)[NOUT], double *partials,
   }
 }
 
+// Same epilogue with the per-thread values and the block tree in type T (float
+// for FP32 vectors: GB300's FP64 unit is far slower) and FP64 partials / final sum.
+template <int NOUT, typename T>
+__device__ __forceinline__ void grid_finish_t(T (&v)[NOUT], double *partials, double *out, unsigned int *ticket,
+                                              T *sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NOUT; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NOUT; ++k) sh[wid * NOUT + k] = v[k];
+  }
+  __syncthreads();
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NOUT; ++k) {
+      T t = (T)0;
+      for (int w = 0; w < nw; ++w) t += sh[w * NOUT + k];
+      partials[blockIdx.x * NOUT + k] = (double)t;
+    }
+    __threadfence();
+    const unsigned int t = atomicAdd(ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double w[NOUT];
+#pragma unroll
+  for (int k = 0; k < NOUT; ++k) w[k] = 0.0;
+  for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < NOUT; ++k) w[k] += ((volatile double *)partials)[b * NOUT + k];
+  }
+  __shared__ double shd[32 * NOUT];
+  block_sum<NOUT>(w, shd);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NOUT; ++k) out[k] = w[k];
+    *ticket = 0u;
+  }
+}
+
 // Workspace for grid reductions (partials + ticket) owned by a context.
 struct ReduceWs {
   double *partials;

@@ -6,7 +6,8 @@
 // an iteration is one kernel: it reads the previous r and A r, forms
 // r_new = r - alpha A r on the fly at the neighbours it needs, updates x and r
 // at its own site, applies A to r_new and reduces <A r_new, r_new> and
-// |A r_new|^2 (last-block reduction, fixed order). r and A r alternate between
+// |A r_new|^2 (last-block reduction, fixed order; within a block the sums are
+// in the vectors' precision, across blocks in FP64). r and A r alternate between
 // two buffers, so no thread overwrites a value another thread still reads.
 // nu MR iterations therefore cost nu + 1 launches.
 #include "kernels.h"
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(256) mr_wilson_kernel(const Cx<R> *__restrict_
                                                         Cx<R> *x, int x_init, Cx<R> *r_new, Cx<R> *Ar_new, int L0,
                                                         int L1, R diag, double *partials, double *sc_new,
                                                         unsigned int *ticket) {
-  __shared__ double sh[32 * 3];
+  __shared__ R sh[32 * 3];
   const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long V = (long long)L0 * L1;
   {  // vector blockIdx.y of the batch (stride 2 V); scalars, partials and ticket per vector
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(256) mr_wilson_kernel(const Cx<R> *__restrict_
     partials += 3LL * gridDim.x * blockIdx.y;
     ticket += blockIdx.y;
   }
-  double v[3] = {0.0, 0.0, 0.0};
+  R v[3] = {(R)0, (R)0, (R)0};
   if (s < V) {
     MrSrc<R, STEP> src;
     src.r = r_old;
@@ -102,12 +103,11 @@ __global__ void __launch_bounds__(256) mr_wilson_kernel(const Cx<R> *__restrict_
     const Cx<R> a1 = mk(diag * s1.re - h * hl.re, diag * s1.im - h * hl.im);
     Ar_new[2 * s] = a0;
     Ar_new[2 * s + 1] = a1;
-    const Cx<double> A0 = cvt<double>(a0), A1 = cvt<double>(a1), S0 = cvt<double>(s0), S1 = cvt<double>(s1);
-    v[0] = A0.re * S0.re + A0.im * S0.im + A1.re * S1.re + A1.im * S1.im;
-    v[1] = A0.re * S0.im - A0.im * S0.re + A1.re * S1.im - A1.im * S1.re;
-    v[2] = A0.re * A0.re + A0.im * A0.im + A1.re * A1.re + A1.im * A1.im;
+    v[0] = a0.re * s0.re + a0.im * s0.im + a1.re * s1.re + a1.im * s1.im;
+    v[1] = a0.re * s0.im - a0.im * s0.re + a1.re * s1.im - a1.im * s1.re;
+    v[2] = a0.re * a0.re + a0.im * a0.im + a1.re * a1.re + a1.im * a1.im;
   }
-  grid_finish<3>(v, partials, sc_new, ticket, sh);
+  grid_finish_t<3, R>(v, partials, sc_new, ticket, sh);
 }
 
 // ---- coarse stencil level: one thread per (site, row) ----
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256) mr_stencil_kernel(const Cx<R> *__restrict
                                                          Cx<R> *x, int x_init, Cx<R> *r_new, Cx<R> *Ar_new, int L0,
                                                          int L1, int Nrt, double *partials, double *sc_new,
                                                          unsigned int *ticket) {
-  __shared__ double sh[32 * 3];
+  __shared__ R sh[32 * 3];
   const int N = NT > 0 ? NT : Nrt;
   {
     const long long off = blockIdx.y * (long long)L0 * L1 * N;
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(256) mr_stencil_kernel(const Cx<R> *__restrict
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long j = t / N;
   const int row = (int)(t - j * N);
-  double v[3] = {0.0, 0.0, 0.0};
+  R v[3] = {(R)0, (R)0, (R)0};
   if (j < (long long)L0 * L1) {
     MrSrc<R, STEP> src;
     src.r = r_old;
@@ -170,12 +170,11 @@ __global__ void __launch_bounds__(256) mr_stencil_kernel(const Cx<R> *__restrict
       for (int col = 0; col < N; ++col) cmac(acc, Yd[(long long)col * N], src.at(base + col));
     }
     Ar_new[t] = acc;
-    const Cx<double> A = cvt<double>(acc), S = cvt<double>(self);
-    v[0] = A.re * S.re + A.im * S.im;
-    v[1] = A.re * S.im - A.im * S.re;
-    v[2] = A.re * A.re + A.im * A.im;
+    v[0] = acc.re * self.re + acc.im * self.im;
+    v[1] = acc.re * self.im - acc.im * self.re;
+    v[2] = acc.re * acc.re + acc.im * acc.im;
   }
-  grid_finish<3>(v, partials, sc_new, ticket, sh);
+  grid_finish_t<3, R>(v, partials, sc_new, ticket, sh);
 }
 
 // x (+)= alpha r for the last MR iteration
