@@ -49,6 +49,7 @@ struct Level {
   Work<double> w64;
   Work<float> w32;
   DevBuf<Cx<double>> tA, tB;  // setup temporaries
+  DevBuf<Cx<float>> sv, sA, sB;  // FP32 setup copies of the near-null vectors and temporaries
   bool stale = false;
 };
 
@@ -478,26 +479,75 @@ static void build_level(mg_ctx &c, int l) {
     launch_galerkin_stencil(L.Y64.p, L.V64.p, C.Y64.p, L.bg, L.Nv, c.s);
 }
 
+// One adaptive-setup level in the context precision. In FP32 mode the relaxation
+// and the adaptive V-cycles run in FP32 on an FP32 copy of the vectors, which are
+// kept in FP64 for the block Gram-Schmidt and the Galerkin build.
+template <typename R>
+static void relax_and_adapt(mg_ctx &c, int l, int pass);
+
+template <>
+void relax_and_adapt<double>(mg_ctx &c, int l, int pass) {
+  Level &L = c.lv[l];
+  const long long n = L.n;
+  const int nv = L.Nv;
+  Cx<double> *V = L.nullv.p;
+  if (pass == 1) {
+    apply_op<double>(c, l, V, L.tA.p, nullptr, -1.0, 0.0, nv);  // r = -A v
+    smooth<double>(c, l, L.tA.p, V, c.p.nu_setup, true, nv);
+  } else {
+    apply_op<double>(c, l, V, L.tA.p, nullptr, 1.0, 0.0, nv);
+    graph_run(c, c.setup_vc[l], [&] { vcycle<double>(c, l, L.tA.p, L.tB.p, nv); });
+    launch_xmy<double>(V, L.tB.p, n * nv, c.s);  // tB = v - V(A v)
+    launch_copy<double>(L.tB.p, V, n * nv, c.s);
+  }
+}
+
+template <>
+void relax_and_adapt<float>(mg_ctx &c, int l, int pass) {
+  Level &L = c.lv[l];
+  const long long n = L.n;
+  const int nv = L.Nv;
+  launch_convert<float, double>(L.nullv.p, L.sv.p, n * nv, c.s);
+  if (pass == 1) {
+    apply_op<float>(c, l, L.sv.p, L.sA.p, nullptr, -1.0, 0.0, nv);
+    smooth<float>(c, l, L.sA.p, L.sv.p, c.p.nu_setup, true, nv);
+  } else {
+    apply_op<float>(c, l, L.sv.p, L.sA.p, nullptr, 1.0, 0.0, nv);
+    graph_run(c, c.setup_vc[l], [&] { vcycle<float>(c, l, L.sA.p, L.sB.p, nv); });
+    launch_xmy<float>(L.sv.p, L.sB.p, n * nv, c.s);
+    launch_copy<float>(L.sB.p, L.sv.p, n * nv, c.s);
+  }
+  launch_convert<double, float>(L.sv.p, L.nullv.p, n * nv, c.s);
+}
+
 static void setup_level(mg_ctx &c, int l, bool full) {
   Level &L = c.lv[l];
   const long long n = L.n;
   // pass 1: random vectors relaxed on A x = 0 (nu_setup MR iterations from x = v: the
-  // corrections solve A d = -A v from d = 0), all Nv vectors as one batch
+  // corrections solve A d = -A v from d = 0); later passes v <- v - V(A v), one V-cycle
+  // on the homogeneous problem. All Nv vectors form one batch.
   Cx<double> *V = L.nullv.p;
   const int nv = L.Nv;
+  const bool f32 = c.p.precision == MG_FP32;
   for (int k = 0; k < nv; ++k) launch_gaussian(V + (long long)k * n, n, c.p.seed, k, l, c.s);
-  apply_op<double>(c, l, V, L.tA.p, nullptr, -1.0, 0.0, nv);  // r = -A v
-  smooth<double>(c, l, L.tA.p, V, c.p.nu_setup, true, nv);
+  if (f32)
+    relax_and_adapt<float>(c, l, 1);
+  else
+    relax_and_adapt<double>(c, l, 1);
   const int n_pass = full ? c.p.n_pass : 1;
   for (int pass = 1; pass <= n_pass; ++pass) {
     if (pass > 1) {
-      // v <- v - V(A v): one V-cycle on the homogeneous problem, batched over the Nv vectors
-      apply_op<double>(c, l, V, L.tA.p, nullptr, 1.0, 0.0, nv);
-      graph_run(c, c.setup_vc[l], [&] { vcycle<double>(c, l, L.tA.p, L.tB.p, nv); });
-      launch_xmy<double>(V, L.tB.p, n * nv, c.s);  // tB = v - V(A v)
-      launch_copy<double>(L.tB.p, V, n * nv, c.s);
+      if (f32)
+        relax_and_adapt<float>(c, l, pass);
+      else
+        relax_and_adapt<double>(c, l, pass);
     }
     build_level(c, l);
+    if (f32) {
+      launch_convert<float, double>(L.V64.p, L.V32.p, L.V64.n, c.s);
+      Level &C = c.lv[l + 1];
+      launch_convert<float, double>(C.Y64.p, C.Y32.p, C.Y64.n, c.s);
+    }
     if (l + 1 == c.p.levels - 1)
       prepare_coarsest(c);
     else
@@ -581,10 +631,10 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
     L.w64.r.alloc(L.n * nb);
     L.w64.Ar.alloc(L.n * nb);
     if (f32) {
-      L.w32.b.alloc(L.n);
-      L.w32.x.alloc(L.n);
-      L.w32.r.alloc(L.n);
-      L.w32.Ar.alloc(L.n);
+      L.w32.b.alloc(L.n * nb);
+      L.w32.x.alloc(L.n * nb);
+      L.w32.r.alloc(L.n * nb);
+      L.w32.Ar.alloc(L.n * nb);
     }
     if (l + 1 < p->levels) {
       const int B0 = p->block[l][0], B1 = p->block[l][1];
@@ -597,6 +647,11 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
       L.mgs_min.alloc(L.bg.nblocks);
       L.tA.alloc(L.n * (size_t)L.Nv);
       L.tB.alloc(L.n * (size_t)L.Nv);
+      if (f32) {
+        L.sv.alloc(L.n * (size_t)L.Nv);
+        L.sA.alloc(L.n * (size_t)L.Nv);
+        L.sB.alloc(L.n * (size_t)L.Nv);
+      }
       L0 /= B0;
       L1 /= B1;
       nint = L.Nv;
@@ -608,8 +663,8 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
     L.w64.r2.alloc(L.n * (size_t)c->nbatch);
     L.w64.Ar2.alloc(L.n * (size_t)c->nbatch);
     if (f32) {
-      L.w32.r2.alloc(L.n);
-      L.w32.Ar2.alloc(L.n);
+      L.w32.r2.alloc(L.n * (size_t)c->nbatch);
+      L.w32.Ar2.alloc(L.n * (size_t)c->nbatch);
     }
   }
   c->U64.alloc(F.geo.nsites * 2);
@@ -750,6 +805,7 @@ int mg_setup(mg_ctx **ctx, const mg_geom *g, const void *U, double m, const mg_p
     need_ptr(U);
     auto c = create(g, m, p, stream);
     MG_CUDA(cudaMemcpyAsync(c->U64.p, U, c->U64.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, c->s));
+    if (c->p.precision == MG_FP32) launch_convert<float, double>(c->U64.p, c->U32.p, c->U64.n, c->s);
     setup_level(*c, 0, true);
     make_fp32_copies(*c);
     collect_coarsest(*c);

@@ -156,6 +156,32 @@ def test_full_adaptive_setup_matches_oracle(levels):
         assert rel_err(to_host(ctx.coarse_op(l + 1)), hier.ops[l + 1].Y) < 1e-9, l
 
 
+@pytest.mark.parametrize("n_pass", [1, 3])
+def test_fp32_setup_close_to_oracle(n_pass):
+    # mixed-precision contexts relax and adapt the near-null vectors in FP32 (Gram-Schmidt and
+    # the Galerkin build stay FP64): the vectors and coarse operators agree with the FP64 oracle
+    # setup to FP32 rounding amplified by the relaxation, and both solve in the same number of
+    # outer iterations
+    mg = _mg()
+    dims = (32, 32)
+    lat = Lattice(dims)
+    U, _, _ = inputs.schwinger_links(32, 6.0, sweeps=200, workload_id=5)
+    p = setup.MGParams(levels=3, blocks=((4, 4), (2, 2)), Nv=(8, 8), n_pass=n_pass, seed=777, coarsest_lu_max=4096)
+    hier = setup.adaptive_setup(U, 0.02, lat, p)
+    gp = mg.mg_default_params(levels=3, blocks=[(4, 4), (2, 2)], Nv=[8, 8], n_pass=n_pass, seed=777,
+                              coarsest_lu_max=4096, precision=1)
+    ctx = mg.Context.setup(to_dev(U), 0.02, dims, gp)
+    for l in range(2):
+        assert rel_err(to_host(ctx.null_vectors(l)), np.stack(hier.vecs[l])) < 1e-4, l
+        assert rel_err(to_host(ctx.coarse_op(l + 1)), hier.ops[l + 1].Y) < 1e-4, l
+    import torch
+    chi = inputs.gaussian_source(*dims, seed=9)
+    psi = torch.empty((1024, 2), dtype=torch.complex128, device="cuda")
+    st = ctx.solve(to_dev(chi), psi, 1e-10)
+    _, info = solvers.mg_solve(hier, chi, 1e-10)
+    assert st["converged"] and abs(st["iters"] - info["iters"]) <= 1
+
+
 @pytest.mark.parametrize("dims,lu_max", [((32, 32), 100000), ((32, 32), 0), ((64, 64), 0)])
 def test_coarsest_solve_matches_oracle(dims, lu_max):
     # the coarsest exact solve alone: dense LU, or the persistent GCR kernel to 1e-12
