@@ -95,6 +95,7 @@ typedef struct {
   int coarsest_max_iter;            /* iteration limit of the iterative coarsest solve */
   int precision;                    /* mg_precision */
   uint64_t seed;                    /* Philox4x32-10 key of the setup's random vectors */
+  int max_rhs;                      /* right-hand sides one mg_solve_batch call may take (1..32) */
 } mg_params;
 
 typedef struct {
@@ -111,7 +112,7 @@ typedef struct mg_ctx mg_ctx;
 
 /* Defaults: 2 levels, 4x4 blocks, Nv = 8, MR 4 + 4 with omega = 0.8, 5 passes,
  * nu_setup = 8, GCR(16), max_iter 500, coarsest LU up to 2048, coarsest GCR
- * tol 1e-12 / restart 16 / 20000 iterations, FP64, seed 20070704. */
+ * tol 1e-12 / restart 16 / 20000 iterations, FP64, seed 20070704, max_rhs 1. */
 void mg_default_params(mg_params *p);
 
 /*
@@ -135,6 +136,27 @@ int mg_setup(mg_ctx **ctx, const mg_geom *g, const void *U, double m, const mg_p
  * chi, psi: device complex128 [x][s]; psi is overwritten (initial guess 0).
  * st may be NULL. Returns NOT_CONVERGED (psi = last iterate) after max_iter. */
 int mg_solve(mg_ctx *ctx, const void *chi, void *psi, double tol, mg_stats *st);
+
+/* Solve nrhs systems D(m_v) psi_v = chi_v with one hierarchy (paper: many
+ * right-hand sides amortise one setup; mass reuse, the setup at the lightest
+ * mass serving heavier ones), in lockstep: every outer iteration applies one
+ * batched V-cycle to all unfinished right-hand sides.
+ *   nrhs  1..max_rhs of the setup parameters
+ *   chi, psi  device complex128 [v][x][s], nrhs vectors back to back; psi is
+ *         overwritten (initial guess 0)
+ *   mass  host array of nrhs masses, or NULL for the context mass. Vector v
+ *         sees every level's operator shifted by m_v - m: D(m_v) on the fine
+ *         level and P^dagger D(m) P + (m_v - m) on the coarse ones, which is
+ *         P^dagger D(m_v) P because the block-orthonormal P has P^dagger P = 1;
+ *         the coarsest factors / preconditioners are prepared per mass
+ *   st    NULL or nrhs entries: iters, converged and true_rel_residual per
+ *         vector; level_apps, coarsest_iters, ms and graphs for the whole batch
+ * A vector stops when its tracked residual meets tol and is confirmed by the
+ * true residual at the next restart. Returns NOT_CONVERGED if any vector
+ * missed tol within max_iter (outer iterations of the batch), INVALID_ARG for
+ * nrhs outside 1..max_rhs or a non-finite mass. */
+int mg_solve_batch(mg_ctx *ctx, int nrhs, const void *chi, void *psi, const double *mass, double tol,
+                   mg_stats *st);
 
 /* Reuse the near-null vectors for another mass (paper: setup at the lightest
  * mass only, reused for heavier ones): rebuilds every Galerkin operator with

@@ -37,7 +37,8 @@ class mg_params(ctypes.Structure):
                 ("omega", ctypes.c_double), ("n_pass", ctypes.c_int), ("nu_setup", ctypes.c_int),
                 ("gcr_restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("coarsest_lu_max", ctypes.c_int),
                 ("coarsest_tol", ctypes.c_double), ("coarsest_restart", ctypes.c_int),
-                ("coarsest_max_iter", ctypes.c_int), ("precision", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("coarsest_max_iter", ctypes.c_int), ("precision", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("max_rhs", ctypes.c_int)]
 
 
 class mg_stats(ctypes.Structure):
@@ -73,6 +74,7 @@ def load():
         "mg_default_params": (None, [P(mg_params)]),
         "mg_setup": (I, [P(ctxp), P(mg_geom), VP, D, P(mg_params), VP]),
         "mg_solve": (I, [ctxp, VP, VP, D, P(mg_stats)]),
+        "mg_solve_batch": (I, [ctxp, I, VP, VP, P(D), D, P(mg_stats)]),
         "mg_update_mass": (I, [ctxp, D]),
         "mg_destroy": (None, [ctxp]),
         "mg_last_error": (ctypes.c_char_p, []),
@@ -105,8 +107,7 @@ def exported_symbols():
     return ["mg_default_params", "mg_setup", "mg_solve", "mg_update_mass", "mg_destroy", "mg_last_error",
             "mg_dslash", "mg_level_apply", "mg_restrict", "mg_prolong", "mg_vcycle", "mg_smooth", "mg_build_level",
             "mg_get_null_vectors", "mg_get_prolongator", "mg_get_coarse_op", "mg_level_size", "mg_kernel_launches",
-            "mg_smooth_fine_noalloc", "mg_coarsest_solve",
-            "mg_selftest_barrier"]
+            "mg_smooth_fine_noalloc", "mg_coarsest_solve", "mg_selftest_barrier", "mg_solve_batch"]
 
 
 def _check(code: int):
@@ -252,6 +253,24 @@ class Context:
         if code != 0 and (raise_on_fail or code != 4):
             _check(code)
         return st.as_dict()
+
+    def solve_batch(self, chi: torch.Tensor, psi: torch.Tensor, tol: float, masses=None,
+                    raise_on_fail: bool = True) -> list:
+        """mg_solve_batch: psi[v] = D(m_v)^{-1} chi[v] for the nrhs = chi.shape[0] vectors
+        (masses: one per vector, or None for the context mass); returns the stats per vector."""
+        nrhs = int(chi.shape[0])
+        n = 2 * self.volume * nrhs
+        st = (mg_stats * nrhs)()
+        mp = None
+        if masses is not None:
+            if len(masses) != nrhs:
+                raise ValueError("one mass per right-hand side")
+            mp = (ctypes.c_double * nrhs)(*[float(m) for m in masses])
+        code = load().mg_solve_batch(self._need(), nrhs, _ptr(chi, torch.complex128, n),
+                                     _ptr(psi, torch.complex128, n), mp, float(tol), st)
+        if code != 0 and (raise_on_fail or code != 4):
+            _check(code)
+        return [st[v].as_dict() for v in range(nrhs)]
 
     def update_mass(self, m: float):
         _check(load().mg_update_mass(self._need(), float(m)))

@@ -61,11 +61,15 @@ __global__ void __launch_bounds__(kReduceThreads) norm2_kernel(const Cx<R> *__re
 template <typename R>
 __global__ void mr_update_kernel(const double *__restrict__ sc, double omega, Cx<R> *__restrict__ x,
                                  Cx<R> *__restrict__ r, const Cx<R> *__restrict__ Ar, long long n) {
-  // alpha = omega <Ar, r> / <Ar, Ar>  (zero when Ar vanishes)
-  const double den = sc[2];
-  const double ar = den > 0.0 ? omega * sc[0] / den : 0.0;
-  const double ai = den > 0.0 ? omega * sc[1] / den : 0.0;
-  const Cx<R> alpha = mk((R)ar, (R)ai), malpha = mk((R)-ar, (R)-ai);
+  // alpha = omega <Ar, r> / <Ar, Ar>  (zero when Ar vanishes), once per block
+  __shared__ double s_a[2];
+  if (threadIdx.x == 0) {
+    const double den = sc[2];
+    s_a[0] = den > 0.0 ? omega * sc[0] / den : 0.0;
+    s_a[1] = den > 0.0 ? omega * sc[1] / den : 0.0;
+  }
+  __syncthreads();
+  const Cx<R> alpha = mk((R)s_a[0], (R)s_a[1]), malpha = mk((R)-s_a[0], (R)-s_a[1]);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const Cx<R> ri = r[i];
     cmac(x[i], alpha, ri);
@@ -139,6 +143,122 @@ void launch_gcr_project_update(const Cx<double> *W, Cx<double> *Wk, const Cx<dou
   if (b > 152LL * 16) b = 152LL * 16;
   gcr_project_update_kernel<<<(unsigned int)(b < 1 ? 1 : b), 256, 0, s>>>(W, Wk, Z, Zk, k, beta_dev, inv, are, aim, x,
                                                                           r, n, update_xr ? 1 : 0);
+  MG_LAUNCHED();
+}
+
+
+// ---------------------------------------------------------------------------
+// batched outer GCR (FP64): nb systems in lockstep, vector v of a batch at v * n;
+// Krylov bases W[j][v][n], Z[j][v][n]
+// ---------------------------------------------------------------------------
+
+// y_v = x_v for the vectors with mask bit v, else 0
+__global__ void copy_masked_kernel(const Cx<double> *__restrict__ x, Cx<double> *__restrict__ y, long long n,
+                                   unsigned int mask) {
+  const long long off = blockIdx.y * n;
+  const bool on = (mask >> blockIdx.y) & 1u;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[off + i] = on ? x[off + i] : mk(0.0, 0.0);
+}
+
+// out[v] = |a_v|^2 (blockIdx.y = v)
+__global__ void __launch_bounds__(kReduceThreads) norm2_batch_kernel(const Cx<double> *__restrict__ a, long long n,
+                                                                     double *partials, double *out,
+                                                                     unsigned int *ticket) {
+  __shared__ double sh[32];
+  const Cx<double> *av = a + blockIdx.y * n;
+  double v[1] = {0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    v[0] += norm2(av[i]);
+  grid_finish<1>(v, partials + (long long)blockIdx.y * gridDim.x, out + blockIdx.y, ticket + blockIdx.y, sh);
+}
+
+// vector v = blockIdx.z, row = blockIdx.y: rows j < k <W_j, w>, row k |w|^2, row k + 1 <w, r>;
+// results at out[v * 2 (k + 2) + 2 row]
+__global__ void __launch_bounds__(kReduceThreads) gcr_dots_batch_kernel(const Cx<double> *__restrict__ W,
+                                                                        const Cx<double> *__restrict__ r, int k,
+                                                                        int nb, long long n, double *partials,
+                                                                        double *out, unsigned int *ticket) {
+  __shared__ double sh[32 * 2];
+  const int row = blockIdx.y, v = blockIdx.z, rows = k + 2;
+  const Cx<double> *w = W + ((long long)k * nb + v) * n;
+  const Cx<double> *a = row < k ? W + ((long long)row * nb + v) * n : w;
+  const Cx<double> *b = row == k + 1 ? r + (long long)v * n : w;
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const Cx<double> x = a[i], y = b[i];
+    acc[0] += x.re * y.re + x.im * y.im;
+    acc[1] += x.re * y.im - x.im * y.re;
+  }
+  const long long slot = (long long)v * rows + row;
+  grid_finish<2>(acc, partials + slot * 2 * gridDim.x, out + 2 * slot, ticket + slot, sh);
+}
+
+// per vector v (blockIdx.y), coef[4 v .. 4 v + 3] = (inv, alpha re, alpha im, mode):
+// mode 0 leaves the vector alone; mode 2 projects w_k, z_k against the basis with beta_j =
+// dots[v * 2 (k + 2) + 2 j]; mode 1 projects, scales both by inv and updates x += alpha z_k,
+// r -= alpha w_k
+__global__ void gcr_update_batch_kernel(Cx<double> *__restrict__ W, Cx<double> *__restrict__ Z, int k, int nb,
+                                        const double *__restrict__ dots, const double *__restrict__ coef,
+                                        Cx<double> *__restrict__ x, Cx<double> *__restrict__ r, long long n) {
+  const int v = blockIdx.y;
+  const int mode = (int)coef[4 * v + 3];
+  if (mode == 0) return;
+  const double *beta = dots + (long long)v * 2 * (k + 2);
+  const double inv = mode == 1 ? coef[4 * v] : 1.0;
+  const Cx<double> alpha = mk(coef[4 * v + 1], coef[4 * v + 2]);
+  Cx<double> *Wk = W + ((long long)k * nb + v) * n, *Zk = Z + ((long long)k * nb + v) * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    Cx<double> w = Wk[i], z = Zk[i];
+    for (int j = 0; j < k; ++j) {
+      const Cx<double> bj = mk(-beta[2 * j], -beta[2 * j + 1]);
+      const long long o = ((long long)j * nb + v) * n + i;
+      cmac(w, bj, W[o]);
+      cmac(z, bj, Z[o]);
+    }
+    w = inv * w;
+    z = inv * z;
+    Wk[i] = w;
+    Zk[i] = z;
+    if (mode == 1) {
+      cmac(x[(long long)v * n + i], alpha, z);
+      Cx<double> ri = r[(long long)v * n + i];
+      cmac(ri, mk(-alpha.re, -alpha.im), w);
+      r[(long long)v * n + i] = ri;
+    }
+  }
+}
+
+static unsigned int stream_grid(long long n);
+
+void launch_copy_masked(const Cx<double> *x, Cx<double> *y, long long n, int nb, unsigned int mask, cudaStream_t s) {
+  copy_masked_kernel<<<dim3(stream_grid(n), nb), 256, 0, s>>>(x, y, n, mask);
+  MG_LAUNCHED();
+}
+
+void launch_norm2_batch(const Cx<double> *a, long long n, int nb, double *out, const ReduceWs &ws, cudaStream_t s) {
+  int per = (int)(ws.capacity / nb);
+  if (per > ws.max_blocks) per = ws.max_blocks;
+  if (per < 1) per = 1;
+  norm2_batch_kernel<<<dim3(reduce_blocks(n, per), nb), kReduceThreads, 0, s>>>(a, n, ws.partials, out, ws.ticket);
+  MG_LAUNCHED();
+}
+
+void launch_gcr_dots_batch(const Cx<double> *W, const Cx<double> *r, int k, int nb, long long n, double *out,
+                           const ReduceWs &ws, cudaStream_t s) {
+  const int rows = k + 2;
+  if ((long long)rows * nb > ws.tickets) fail(MG_ERR_UNSUPPORTED, "gcr_dots_batch: too many reductions");
+  int per = (int)(ws.capacity / (2LL * rows * nb));
+  if (per > ws.max_blocks) per = ws.max_blocks;
+  if (per < 1) fail(MG_ERR_STATE, "gcr_dots_batch: reduction workspace too small");
+  gcr_dots_batch_kernel<<<dim3(reduce_blocks(n, per), rows, nb), kReduceThreads, 0, s>>>(W, r, k, nb, n, ws.partials,
+                                                                                         out, ws.ticket);
+  MG_LAUNCHED();
+}
+
+void launch_gcr_update_batch(Cx<double> *W, Cx<double> *Z, int k, int nb, const double *dots, const double *coef,
+                             Cx<double> *x, Cx<double> *r, long long n, cudaStream_t s) {
+  gcr_update_batch_kernel<<<dim3(stream_grid(n), nb), 256, 0, s>>>(W, Z, k, nb, dots, coef, x, r, n);
   MG_LAUNCHED();
 }
 

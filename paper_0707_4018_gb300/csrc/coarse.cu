@@ -14,7 +14,8 @@ namespace mg {
 template <typename R, int NT>
 __global__ void __launch_bounds__(256) coarse_apply_kernel(const Cx<R> *__restrict__ Y, const Cx<R> *__restrict__ in,
                                                            Cx<R> *__restrict__ out, int L0, int L1, int Nrt,
-                                                           const Cx<R> *__restrict__ b, R a, R c, long long ldv) {
+                                                           const Cx<R> *__restrict__ b, R a, R c, long long ldv,
+                                                           const double *__restrict__ shift) {
   in += blockIdx.y * ldv;
   out += blockIdx.y * ldv;
   if (b != nullptr) b += blockIdx.y * ldv;
@@ -39,6 +40,59 @@ __global__ void __launch_bounds__(256) coarse_apply_kernel(const Cx<R> *__restri
 #pragma unroll(NT > 0 ? NT : 1)
     for (int col = 0; col < N; ++col) cmac(acc, Yd[(long long)col * N], xs[col]);
   }
+  if (shift != nullptr) {  // vector blockIdx.y: self block + shift * identity
+    const R sv = (R)shift[blockIdx.y];
+    const Cx<R> xt = in[t];
+    acc.re = fma(sv, xt.re, acc.re);
+    acc.im = fma(sv, xt.im, acc.im);
+  }
+  Cx<R> o = mk(a * acc.re, a * acc.im);
+  if (b != nullptr) {
+    const Cx<R> bb = b[t];
+    o = mk(o.re + c * bb.re, o.im + c * bb.im);
+  }
+  out[t] = o;
+}
+
+// N = 8: four threads per (site, row), a warp per site (10 of the 40 terms each,
+// combined by shuffles)
+template <typename R>
+__global__ void __launch_bounds__(256) coarse_apply8_kernel(const Cx<R> *__restrict__ Y, const Cx<R> *__restrict__ in,
+                                                            Cx<R> *__restrict__ out, int L0, int L1,
+                                                            const Cx<R> *__restrict__ b, R a, R c, long long ldv,
+                                                            const double *__restrict__ shift) {
+  in += blockIdx.y * ldv;
+  out += blockIdx.y * ldv;
+  if (b != nullptr) b += blockIdx.y * ldv;
+  const long long j = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int row = (threadIdx.x >> 2) & 7, q = threadIdx.x & 3;
+  if (j >= (long long)L0 * L1) return;  // whole warps
+  const int x1 = (int)(j / L0), x0 = (int)(j - (long long)x1 * L0);
+  const long long rowo = (long long)x1 * L0;
+  const long long xp0 = rowo + (x0 + 1 == L0 ? 0 : x0 + 1);
+  const long long xm0 = rowo + (x0 == 0 ? L0 - 1 : x0 - 1);
+  const long long xp1 = (x1 + 1 == L1 ? 0 : rowo + L0) + x0;
+  const long long xm1 = (x1 == 0 ? (long long)(L1 - 1) * L0 : rowo - L0) + x0;
+  Cx<R> acc = mk((R)0, (R)0);
+#pragma unroll
+  for (int u = 0; u < 10; ++u) {
+    const int term = q * 10 + u, dir = term >> 3, col = term & 7;
+    const long long nbj = dir == 0 ? j : dir == 1 ? xp0 : dir == 2 ? xm0 : dir == 3 ? xp1 : xm1;
+    cmac(acc, Y[(j * 5 + dir) * 64 + col * 8 + row], in[nbj * 8 + col]);
+  }
+#pragma unroll
+  for (int o = 1; o < 4; o <<= 1) {
+    acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
+    acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
+  }
+  if (q != 0) return;
+  const long long t = j * 8 + row;
+  if (shift != nullptr) {
+    const R sv = (R)shift[blockIdx.y];
+    const Cx<R> xt = in[t];
+    acc.re = fma(sv, xt.re, acc.re);
+    acc.im = fma(sv, xt.im, acc.im);
+  }
   Cx<R> o = mk(a * acc.re, a * acc.im);
   if (b != nullptr) {
     const Cx<R> bb = b[t];
@@ -49,27 +103,28 @@ __global__ void __launch_bounds__(256) coarse_apply_kernel(const Cx<R> *__restri
 
 template <typename R>
 void launch_coarse_apply(const Cx<R> *Y, const Cx<R> *in, Cx<R> *out, Geo2 g, int N, const Cx<R> *b, double a,
-                         double c, cudaStream_t s, int nvec) {
+                         double c, cudaStream_t s, int nvec, const double *shift) {
   const int threads = 256;
   const dim3 grid(grid_for(g.nsites * N, threads), nvec);
   const long long ldv = g.nsites * N;
   if (N == 8)
-    coarse_apply_kernel<R, 8><<<grid, threads, 0, s>>>(Y, in, out, g.L0, g.L1, N, b, (R)a, (R)c, ldv);
+    coarse_apply8_kernel<R><<<dim3(grid_for(g.nsites * 32, threads), nvec), threads, 0, s>>>(Y, in, out, g.L0, g.L1, b,
+                                                                                            (R)a, (R)c, ldv, shift);
   else
-    coarse_apply_kernel<R, 0><<<grid, threads, 0, s>>>(Y, in, out, g.L0, g.L1, N, b, (R)a, (R)c, ldv);
+    coarse_apply_kernel<R, 0><<<grid, threads, 0, s>>>(Y, in, out, g.L0, g.L1, N, b, (R)a, (R)c, ldv, shift);
   MG_LAUNCHED();
 }
 
 template void launch_coarse_apply<double>(const Cx<double> *, const Cx<double> *, Cx<double> *, Geo2, int,
-                                          const Cx<double> *, double, double, cudaStream_t, int);
+                                          const Cx<double> *, double, double, cudaStream_t, int, const double *);
 template void launch_coarse_apply<float>(const Cx<float> *, const Cx<float> *, Cx<float> *, Geo2, int,
-                                         const Cx<float> *, double, double, cudaStream_t, int);
+                                         const Cx<float> *, double, double, cudaStream_t, int, const double *);
 
 // ---------------------------------------------------------------------------
 // dense matrix of the coarsest stencil, column-major A[col * n + row]
 // ---------------------------------------------------------------------------
 __global__ void dense_from_stencil_kernel(const Cx<double> *__restrict__ Y, Cx<double> *__restrict__ A, int L0, int L1,
-                                          int N) {
+                                          int N, double shift) {
   const long long n = (long long)L0 * L1 * N;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= n * n) return;
@@ -87,12 +142,13 @@ __global__ void dense_from_stencil_kernel(const Cx<double> *__restrict__ Y, Cx<d
   Cx<double> v = mk(0.0, 0.0);
   for (int dir = 0; dir < 5; ++dir)
     if (src[dir] == sc) v = v + Y[(j * 5 + dir) * (long long)N * N + (long long)ac * N + ar];
+  if (row == col) v.re += shift;
   A[t] = v;
 }
 
-void launch_dense_from_stencil(const Cx<double> *Y, Cx<double> *A, Geo2 g, int N, cudaStream_t s) {
+void launch_dense_from_stencil(const Cx<double> *Y, Cx<double> *A, Geo2 g, int N, cudaStream_t s, double shift) {
   const long long n = g.nsites * N;
-  dense_from_stencil_kernel<<<grid_for(n * n, 256), 256, 0, s>>>(Y, A, g.L0, g.L1, N);
+  dense_from_stencil_kernel<<<grid_for(n * n, 256), 256, 0, s>>>(Y, A, g.L0, g.L1, N, shift);
   MG_LAUNCHED();
 }
 

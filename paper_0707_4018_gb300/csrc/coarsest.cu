@@ -289,7 +289,8 @@ __global__ void __launch_bounds__(256) coarsest_gcr_kernel(CgArgs a) {
 // pivoting, one thread per coarse site) and the stencil A M
 // ---------------------------------------------------------------------------
 __global__ void self_block_inverse_kernel(const Cx<double> *__restrict__ Y, Cx<double> *__restrict__ Minv,
-                                          Cx<double> *__restrict__ work, long long nsites, int N, int *info) {
+                                          Cx<double> *__restrict__ work, long long nsites, int N, int *info,
+                                          double shift) {
   // one warp per coarse site; the augmented matrix [X | I] lives in `work` (2 N^2 entries per
   // site, column-major); lane r < N owns row r and lane N + r its copy of the identity part
   const long long j = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -299,8 +300,9 @@ __global__ void self_block_inverse_kernel(const Cx<double> *__restrict__ Y, Cx<d
   Cx<double> *Iw = Aw + (long long)N * N;
   const Cx<double> *X = Y + (j * 5) * (long long)N * N;  // [col][row]
   for (int q = lane; q < N * N; q += 32) {
-    Aw[q] = X[q];
-    Iw[q] = mk((q % N) == (q / N) ? 1.0 : 0.0, 0.0);
+    const bool dg = (q % N) == (q / N);
+    Aw[q] = dg ? mk(X[q].re + shift, X[q].im) : X[q];
+    Iw[q] = mk(dg ? 1.0 : 0.0, 0.0);
   }
   __syncwarp();
   for (int c = 0; c < N; ++c) {
@@ -363,7 +365,7 @@ __global__ void self_block_inverse_kernel(const Cx<double> *__restrict__ Y, Cx<d
 
 // Yt[j][dir] = Y[j][dir] * Minv[src(j, dir)]  (column-major blocks); thread per (j, dir, col, row)
 __global__ void precondition_stencil_kernel(const Cx<double> *__restrict__ Y, const Cx<double> *__restrict__ Minv,
-                                            Cx<double> *__restrict__ Yt, int L0, int L1, int N) {
+                                            Cx<double> *__restrict__ Yt, int L0, int L1, int N, double shift) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nsites = (long long)L0 * L1;
   const long long per = 5LL * N * N;
@@ -384,15 +386,19 @@ __global__ void precondition_stencil_kernel(const Cx<double> *__restrict__ Y, co
   const Cx<double> *Ms = Minv + src * (long long)N * N;
   Cx<double> acc = mk(0.0, 0.0);
   for (int q = 0; q < N; ++q) cmac(acc, Yd[(long long)q * N + row], Ms[(long long)col * N + q]);
+  if (dir == 0) acc = acc + shift * Ms[(long long)col * N + row];  // (X + shift) Minv
   Yt[t] = acc;
 }
 
 void prepare_coarsest_gcr(const Cx<double> *Y, Geo2 g, int N, Cx<double> *Minv, Cx<double> *Yt, Cx<double> *work,
-                          int *info_dev, cudaStream_t s) {
+                          int *info_dev, cudaStream_t s, double shift) {
   MG_CUDA(cudaMemsetAsync(info_dev, 0, sizeof(int), s));
-  self_block_inverse_kernel<<<grid_for(g.nsites * 32, 128), 128, 0, s>>>(Y, Minv, work, g.nsites, N, info_dev);
+  self_block_inverse_kernel<<<grid_for(g.nsites * 32, 128), 128, 0, s>>>(Y, Minv, work, g.nsites, N, info_dev,
+                                                                         shift);
   MG_LAUNCHED();
-  precondition_stencil_kernel<<<grid_for(g.nsites * 5LL * N * N, 256), 256, 0, s>>>(Y, Minv, Yt, g.L0, g.L1, N);
+  if (Yt == nullptr) return;
+  precondition_stencil_kernel<<<grid_for(g.nsites * 5LL * N * N, 256), 256, 0, s>>>(Y, Minv, Yt, g.L0, g.L1, N,
+                                                                                    shift);
   MG_LAUNCHED();
 }
 
@@ -859,6 +865,553 @@ int barrier_selftest(unsigned int expected, long long spin_limit, cudaStream_t s
   MG_CUDA(cudaMemcpyAsync(&h, status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   MG_CUDA(cudaStreamSynchronize(s));
   return h;
+}
+
+}  // namespace mg
+
+namespace mg {
+
+// ---------------------------------------------------------------------------
+// Batched shared-memory coarsest GCR: up to kBatchMaxVecs right-hand sides in
+// lockstep in one persistent cooperative launch, so that all of them share
+// the grid barriers (2 per iteration). Vector v solves (Y + shift_v) x_v = b_v
+// with right block-Jacobi preconditioning M_v = blockdiag((X_j + shift_v)^-1)
+// (the raw stencil Y is kept once in shared memory, the blocks of M_v per
+// vector). The Krylov directions are kept in x-space: z_k = M_v r, w_k = A_v z_k,
+// x += alpha z_k, so no final M multiply is needed. Each CTA owns whole coarse
+// sites; z = M r is formed on the CTA's own sites right after the update and
+// published for the neighbours' stencil reads. A vector whose tracked residual
+// meets the tolerance, or whose basis breaks down, stops for the rest of the
+// cycle; every restart recomputes the true residuals and reactivates the
+// vectors that missed it. Grid sums are in fixed order (partials stored slot-
+// major, each warp summing whole slots over the CTAs in CTA order).
+// ---------------------------------------------------------------------------
+constexpr int kBatchMaxVecs = 4;
+
+struct CgBArgs {
+  const Cx<double> *Y;     // stencil at the context mass, [j][dir][col][row], N = 8
+  const Cx<double> *Minv;  // vector v: Minv + v * minv_stride, [j][col][row]
+  long long minv_stride;
+  const double *shift;     // vector v: diagonal shift (device) or null
+  int L0, L1;
+  long long nsites;
+  int spc;  // sites per CTA
+  int nb;   // vectors (<= kBatchMaxVecs)
+  const Cx<double> *b;
+  Cx<double> *x, *upub, *xpub;  // vector stride n
+  double *partials;             // [slot][cta]
+  unsigned int *bar;
+  double tol;
+  int restart, max_iter;
+  long long spin_limit;
+  int *out;
+  double *out_rel;
+};
+
+__device__ __forceinline__ void grid_sync_b(const CgBArgs &a, bool &ok) {
+  __shared__ int s_okb;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int *gen = a.bar + 1;
+    const unsigned int g = *gen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(a.bar, 1u);
+    int good = 1;
+    if (arrived == gridDim.x - 1) {
+      atomicExch(a.bar, 0u);
+      __threadfence();
+      atomicAdd(a.bar + 1, 1u);
+    } else {
+      long long polls = 0;
+      while (*gen == g) {
+        if (++polls > a.spin_limit) {
+          good = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    if (!good) atomicExch(a.out + 1, 1);
+    s_okb = good;
+  }
+  __syncthreads();
+  ok = ok && s_okb;
+}
+
+// cpart[v * kSmSlots + s] (s < ns) holds this CTA's sums; the grid totals land in sres.
+// Each warp takes four slots at a time and each lane loads all its partials of them at
+// once (at most kMaxGridB CTAs), so a sum costs one L2 round trip per four slots. Lane l
+// adds CTAs l, l + 32, ... in that order, then the shuffle tree: a fixed order.
+constexpr int kMaxGridB = 256;
+__device__ __forceinline__ void grid_sum_b(const CgBArgs &a, int ns, const double *cpart, double *sres, bool &ok) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int G = (int)gridDim.x;
+  const int S = a.nb * ns;
+  __syncthreads();
+  for (int q = threadIdx.x; q < S; q += blockDim.x) {
+    const int v = q / ns, sl = q - v * ns;
+    a.partials[(long long)(v * kSmSlots + sl) * G + blockIdx.x] = cpart[v * kSmSlots + sl];
+  }
+  __threadfence();
+  grid_sync_b(a, ok);
+  for (int q0 = wid * 4; q0 < S; q0 += nw * 4) {
+    double vals[4][kMaxGridB / 32];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int q = q0 + u;
+      const int v = q / ns, sl = q - v * ns;
+      const double *src = a.partials + (long long)(v * kSmSlots + sl) * G;
+#pragma unroll
+      for (int i = 0; i < kMaxGridB / 32; ++i) {
+        const int c = lane + 32 * i;
+        vals[u][i] = (q < S && c < G) ? __ldcg(src + c) : 0.0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      double t = 0.0;
+#pragma unroll
+      for (int i = 0; i < kMaxGridB / 32; ++i) t += vals[u][i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      const int q = q0 + u;
+      if (lane == 0 && q < S) {
+        const int v = q / ns, sl = q - v * ns;
+        sres[v * kSmSlots + sl] = t;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// per-vector shared-memory block: M blocks, then b, r, x, z (= M r) chunks, then Z, W
+struct BVec {
+  Cx<double> *Ms, *bs, *rs, *xs, *us, *Zs, *Ws;
+};
+
+__device__ __forceinline__ BVec bvec_at(Cx<double> *base, int v, int restart) {
+  const int per = 8 * 64 + 4 * kSmMaxDofs + 2 * restart * kSmMaxDofs;
+  Cx<double> *p = base + (long long)v * per;
+  BVec r;
+  r.Ms = p;
+  r.bs = p + 8 * 64;
+  r.rs = r.bs + kSmMaxDofs;
+  r.xs = r.rs + kSmMaxDofs;
+  r.us = r.xs + kSmMaxDofs;
+  r.Zs = r.us + kSmMaxDofs;
+  r.Ws = r.Zs + restart * kSmMaxDofs;
+  return r;
+}
+
+// out_v[d] = ((Y + shift_v) pub_v)_d on the CTA's rows for the vectors with mask bit v;
+// pub_v in global memory (neighbours), the self shift from the CTA's own copy self_v
+// (us or xs, selected by `self_x`); 4 threads per row, 10 of the 40 terms each
+__device__ __forceinline__ void stencil_rows_b(const CgBArgs &a, const Cx<double> *Ys, const Cx<double> *pub,
+                                               Cx<double> *vbase, int restart, unsigned mask, bool self_x,
+                                               long long site0, int nd, int kout) {
+  const int t = threadIdx.x, d = t >> 2, q = t & 3;
+  const long long n = a.nsites * 8;
+  Cx<double> acc[kBatchMaxVecs];
+#pragma unroll
+  for (int v = 0; v < kBatchMaxVecs; ++v) acc[v] = mk(0.0, 0.0);
+  if (d < nd) {
+    const long long j = site0 + (d >> 3);
+    const int x1 = (int)(j / a.L0), x0 = (int)(j - (long long)x1 * a.L0);
+    const long long rowo = (long long)x1 * a.L0;
+    long long src[5];
+    src[0] = j;
+    src[1] = rowo + (x0 + 1 == a.L0 ? 0 : x0 + 1);
+    src[2] = rowo + (x0 == 0 ? a.L0 - 1 : x0 - 1);
+    src[3] = (x1 + 1 == a.L1 ? 0 : rowo + a.L0) + x0;
+    src[4] = (x1 == 0 ? (long long)(a.L1 - 1) * a.L0 : rowo - a.L0) + x0;
+#pragma unroll
+    for (int u = 0; u < 10; ++u) {
+      const int term = q * 10 + u, dir = term >> 3, col = term & 7;
+      const Cx<double> yv = Ys[(d * 5 + dir) * 8 + col];
+      const long long off = src[dir] * 8 + col;
+#pragma unroll
+      for (int v = 0; v < kBatchMaxVecs; ++v) {
+        if (v < a.nb && ((mask >> v) & 1u)) {
+          const double2 vv = __ldcg(reinterpret_cast<const double2 *>(pub + v * n + off));
+          cmac(acc[v], yv, mk(vv.x, vv.y));
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < kBatchMaxVecs; ++v) {
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+      acc[v].re += __shfl_xor_sync(0xffffffffu, acc[v].re, o);
+      acc[v].im += __shfl_xor_sync(0xffffffffu, acc[v].im, o);
+    }
+  }
+  if (d < nd && q == 0) {
+#pragma unroll
+    for (int v = 0; v < kBatchMaxVecs; ++v) {
+      if (v < a.nb && ((mask >> v) & 1u)) {
+        BVec B = bvec_at(vbase, v, restart);
+        Cx<double> w = acc[v];
+        if (a.shift != nullptr) {
+          const double sv = a.shift[v];
+          const Cx<double> own = self_x ? B.xs[d] : B.us[d];
+          w.re = fma(sv, own.re, w.re);
+          w.im = fma(sv, own.im, w.im);
+        }
+        if (kout < 0)
+          B.rs[d] = B.bs[d] - w;  // residual form (restart): r = b - A x
+        else
+          B.Ws[kout * kSmMaxDofs + d] = w;
+      }
+    }
+  }
+}
+
+// z = M_v r on the CTA's sites for the vectors in `mask`; stored in us and published
+__device__ __forceinline__ void apply_m_b(const CgBArgs &a, Cx<double> *vbase, int restart, unsigned mask, int nd,
+                                          long long dof0) {
+  const long long n = a.nsites * 8;
+  for (int q = threadIdx.x; q < a.nb * nd; q += blockDim.x) {
+    const int v = q / nd, d = q - v * nd;
+    if (!((mask >> v) & 1u)) continue;
+    BVec B = bvec_at(vbase, v, restart);
+    const int sl = d >> 3, row = d & 7;
+    Cx<double> acc = mk(0.0, 0.0);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) cmac(acc, B.Ms[sl * 64 + c * 8 + row], B.rs[sl * 8 + c]);
+    B.us[d] = acc;
+    a.upub[v * n + dof0 + d] = acc;
+  }
+}
+
+// CTA sums for the vectors in mask: slot 0 |w_k|^2, 1-2 <w_k, r>, 3 + 2j, 4 + 2j <W_j, w_k>
+__device__ __forceinline__ void cta_dots_b(const CgBArgs &a, Cx<double> *vbase, int restart, unsigned mask, int k,
+                                           int nd, double *cpart) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int per = k + 2;
+  for (int task = wid; task < a.nb * per; task += nw) {
+    const int v = task / per, t = task - v * per;
+    double re = 0.0, im = 0.0;
+    if ((mask >> v) & 1u) {
+      BVec B = bvec_at(vbase, v, restart);
+      const Cx<double> *w = B.Ws + k * kSmMaxDofs;
+      for (int d = lane; d < nd; d += 32) {
+        const Cx<double> wd = w[d];
+        if (t == 0) {
+          re += norm2(wd);
+        } else {
+          const Cx<double> u = (t == 1) ? wd : B.Ws[(t - 2) * kSmMaxDofs + d];
+          const Cx<double> vv = (t == 1) ? B.rs[d] : wd;
+          re += u.re * vv.re + u.im * vv.im;
+          im += u.re * vv.im - u.im * vv.re;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) {
+      double *cp = cpart + v * kSmSlots;
+      if (t == 0) {
+        cp[0] = re;
+      } else if (t == 1) {
+        cp[1] = re;
+        cp[2] = im;
+      } else {
+        cp[3 + 2 * (t - 2)] = re;
+        cp[4 + 2 * (t - 2)] = im;
+      }
+    }
+  }
+}
+
+// w_k -= sum_j beta_j W_j, z_k likewise, for the vectors in mask (beta from sres)
+__device__ __forceinline__ void project_b(const CgBArgs &a, Cx<double> *vbase, int restart, unsigned mask, int k,
+                                          int nd, const double *sres) {
+  for (int q = threadIdx.x; q < a.nb * nd; q += blockDim.x) {
+    const int v = q / nd, d = q - v * nd;
+    if (!((mask >> v) & 1u)) continue;
+    BVec B = bvec_at(vbase, v, restart);
+    const double *sr = sres + v * kSmSlots;
+    Cx<double> w = B.Ws[k * kSmMaxDofs + d], z = B.Zs[k * kSmMaxDofs + d];
+    for (int j = 0; j < k; ++j) {
+      const Cx<double> bj = mk(-sr[3 + 2 * j], -sr[4 + 2 * j]);
+      cmac(w, bj, B.Ws[j * kSmMaxDofs + d]);
+      cmac(z, bj, B.Zs[j * kSmMaxDofs + d]);
+    }
+    B.Ws[k * kSmMaxDofs + d] = w;
+    B.Zs[k * kSmMaxDofs + d] = z;
+  }
+}
+
+__device__ __forceinline__ double pyth_norm(const double *sr, int k) {
+  double nw2 = sr[0];
+  for (int j = 0; j < k; ++j) nw2 -= sr[3 + 2 * j] * sr[3 + 2 * j] + sr[4 + 2 * j] * sr[4 + 2 * j];
+  return nw2;
+}
+
+__global__ void __launch_bounds__(256, 1) coarsest_gcr_batch_kernel(CgBArgs a) {
+  extern __shared__ double smb[];
+  Cx<double> *Ys = reinterpret_cast<Cx<double> *>(smb);  // [64 rows][5][8]
+  Cx<double> *vbase = Ys + kSmMaxDofs * 40;
+  const int restart = a.restart;
+  const int per = 8 * 64 + 4 * kSmMaxDofs + 2 * restart * kSmMaxDofs;
+  double *cpart = reinterpret_cast<double *>(vbase + (long long)kBatchMaxVecs * per);  // [v][kSmSlots]
+  double *sres = cpart + kBatchMaxVecs * kSmSlots;
+  __shared__ double s_bn2[kBatchMaxVecs], s_rn2[kBatchMaxVecs], s_nw0[kBatchMaxVecs], s_nw2[kBatchMaxVecs],
+      s_wr[kBatchMaxVecs], s_wi[kBatchMaxVecs];
+  __shared__ int s_it[kBatchMaxVecs];
+  const int tid = threadIdx.x;
+  const int nb = a.nb;
+  const long long n = a.nsites * 8;
+  const long long site0 = blockIdx.x * (long long)a.spc;
+  long long ns = a.nsites - site0;
+  if (ns > a.spc) ns = a.spc;
+  if (ns < 0) ns = 0;
+  const int nd = (int)ns * 8;
+  const long long dof0 = site0 * 8;
+  bool ok = true;
+  const unsigned all = (1u << nb) - 1u;
+
+  for (int q = tid; q < nd * 40; q += blockDim.x) {
+    const int d = q / 40, rem = q - d * 40, dir = rem >> 3, col = rem & 7;
+    const long long j = site0 + (d >> 3);
+    Ys[q] = a.Y[(j * 5 + dir) * 64 + col * 8 + (d & 7)];
+  }
+  for (int q = tid; q < nb * (int)ns * 64; q += blockDim.x) {
+    const int v = q / ((int)ns * 64), e = q - v * (int)ns * 64;
+    bvec_at(vbase, v, restart).Ms[e] = a.Minv[v * a.minv_stride + site0 * 64 + e];
+  }
+  for (int q = tid; q < nb * nd; q += blockDim.x) {
+    const int v = q / nd, d = q - v * nd;
+    BVec B = bvec_at(vbase, v, restart);
+    const Cx<double> bd = a.b[v * n + dof0 + d];
+    B.bs[d] = bd;
+    B.rs[d] = bd;
+    B.xs[d] = mk(0.0, 0.0);
+  }
+  __syncthreads();
+  apply_m_b(a, vbase, restart, all, nd, dof0);
+  // |b_v|^2
+  for (int v = tid >> 5; v < nb; v += blockDim.x >> 5) {
+    const int lane = tid & 31;
+    BVec B = bvec_at(vbase, v, restart);
+    double t = 0.0;
+    for (int d = lane; d < nd; d += 32) t += norm2(B.bs[d]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) cpart[v * kSmSlots] = t;
+  }
+  __threadfence();
+  grid_sum_b(a, 1, cpart, sres, ok);
+  if (!ok) return;
+  unsigned done = 0u;  // vectors whose true residual met the tolerance
+  if (tid < nb) {
+    s_bn2[tid] = sres[tid * kSmSlots];
+    s_rn2[tid] = s_bn2[tid];
+    s_it[tid] = 0;
+  }
+  __syncthreads();
+  for (int v = 0; v < nb; ++v)
+    if (!(s_bn2[v] > 0.0)) done |= 1u << v;
+  const double tol2f = a.tol * a.tol;
+  int iter = 0;
+  while (done != all && iter < a.max_iter) {
+    unsigned act = all & ~done;
+    int k = 0;
+    for (; k < restart && iter < a.max_iter && act != 0u; ++k) {
+      // w_k = A_v z with z = M_v r published; z_k = z
+      stencil_rows_b(a, Ys, a.upub, vbase, restart, act, false, site0, nd, k);
+      for (int q = tid; q < nb * nd; q += blockDim.x) {
+        const int v = q / nd, d = q - v * nd;
+        if ((act >> v) & 1u) {
+          BVec B = bvec_at(vbase, v, restart);
+          B.Zs[k * kSmMaxDofs + d] = B.us[d];
+        }
+      }
+      __syncthreads();
+      cta_dots_b(a, vbase, restart, act, k, nd, cpart);
+      grid_sum_b(a, 3 + 2 * k, cpart, sres, ok);
+      if (!ok) return;
+      unsigned cancel = 0u;
+      for (int v = 0; v < nb; ++v) {
+        if (!((act >> v) & 1u)) continue;
+        const double *sr = sres + v * kSmSlots;
+        const double nw2 = pyth_norm(sr, k);
+        if (k > 0 && !(nw2 > 0.5 * sr[0])) cancel |= 1u << v;
+      }
+      __syncthreads();
+      if (tid < nb && ((act >> tid) & 1u)) {
+        const double *sr = sres + tid * kSmSlots;
+        s_nw0[tid] = sr[0];
+        s_nw2[tid] = pyth_norm(sr, k);
+        s_wr[tid] = sr[1];
+        s_wi[tid] = sr[2];
+      }
+      project_b(a, vbase, restart, act, k, nd, sres);
+      if (cancel != 0u) {
+        // second projection for the vectors that lost precision (same branch in every CTA)
+        __syncthreads();
+        cta_dots_b(a, vbase, restart, cancel, k, nd, cpart);
+        grid_sum_b(a, 3 + 2 * k, cpart, sres, ok);
+        if (!ok) return;
+        if (tid < nb && ((cancel >> tid) & 1u)) s_nw2[tid] = pyth_norm(sres + tid * kSmSlots, k);
+        project_b(a, vbase, restart, cancel, k, nd, sres);
+        __syncthreads();
+      }
+      __syncthreads();
+      // normalise and update; vectors that break down or meet the tolerance stop for this cycle
+      unsigned upd = 0u;
+      for (int v = 0; v < nb; ++v) {
+        if (!((act >> v) & 1u)) continue;
+        if (s_nw2[v] > 1e-28 * s_nw0[v]) upd |= 1u << v;
+      }
+      for (int q = tid; q < nb * nd; q += blockDim.x) {
+        const int v = q / nd, d = q - v * nd;
+        if (!((upd >> v) & 1u)) continue;
+        BVec B = bvec_at(vbase, v, restart);
+        const double inv = 1.0 / sqrt(s_nw2[v]);
+        const Cx<double> alpha = mk(s_wr[v] * inv, s_wi[v] * inv);
+        const Cx<double> w = inv * B.Ws[k * kSmMaxDofs + d], z = inv * B.Zs[k * kSmMaxDofs + d];
+        B.Ws[k * kSmMaxDofs + d] = w;
+        B.Zs[k * kSmMaxDofs + d] = z;
+        cmac(B.xs[d], alpha, z);
+        Cx<double> rd = B.rs[d];
+        cmac(rd, mk(-alpha.re, -alpha.im), w);
+        B.rs[d] = rd;
+      }
+      __syncthreads();
+      apply_m_b(a, vbase, restart, upd, nd, dof0);
+      for (int v = 0; v < nb; ++v) {
+        if (!((act >> v) & 1u)) continue;
+        if (!((upd >> v) & 1u)) {
+          act &= ~(1u << v);  // breakdown: wait for the restart
+          continue;
+        }
+        const double inv2 = 1.0 / s_nw2[v];
+        const double rn2 = fmax(s_rn2[v] - (s_wr[v] * s_wr[v] + s_wi[v] * s_wi[v]) * inv2, 0.0);
+        __syncthreads();
+        if (tid == 0) {
+          s_rn2[v] = rn2;
+          s_it[v] += 1;
+        }
+        __syncthreads();
+        if (rn2 <= tol2f * s_bn2[v]) act &= ~(1u << v);
+      }
+      ++iter;
+      __threadfence();
+      grid_sync_b(a, ok);
+      if (!ok) return;
+    }
+    // true residuals r = b - A x of the unfinished vectors from the published x
+    const unsigned live = all & ~done;
+    for (int q = tid; q < nb * nd; q += blockDim.x) {
+      const int v = q / nd, d = q - v * nd;
+      if ((live >> v) & 1u) a.xpub[v * n + dof0 + d] = bvec_at(vbase, v, restart).xs[d];
+    }
+    __threadfence();
+    grid_sync_b(a, ok);
+    if (!ok) return;
+    stencil_rows_b(a, Ys, a.xpub, vbase, restart, live, true, site0, nd, -1);
+    __syncthreads();
+    apply_m_b(a, vbase, restart, live, nd, dof0);
+    for (int v = tid >> 5; v < nb; v += blockDim.x >> 5) {
+      const int lane = tid & 31;
+      double t = 0.0;
+      if ((live >> v) & 1u) {
+        BVec B = bvec_at(vbase, v, restart);
+        for (int d = lane; d < nd; d += 32) t += norm2(B.rs[d]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) cpart[v * kSmSlots] = t;
+    }
+    __threadfence();
+    grid_sum_b(a, 1, cpart, sres, ok);
+    if (!ok) return;
+    bool bad = false;
+    for (int v = 0; v < nb; ++v) {
+      if (!((live >> v) & 1u)) continue;
+      const double rn2 = sres[v * kSmSlots];
+      if (!(rn2 == rn2)) bad = true;
+      if (rn2 <= tol2f * s_bn2[v]) done |= 1u << v;
+    }
+    __syncthreads();
+    if (tid < nb && ((live >> tid) & 1u)) s_rn2[tid] = sres[tid * kSmSlots];
+    __syncthreads();
+    if (bad || k == 0) break;
+  }
+  for (int q = tid; q < nb * nd; q += blockDim.x) {
+    const int v = q / nd, d = q - v * nd;
+    a.x[v * n + dof0 + d] = bvec_at(vbase, v, restart).xs[d];
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    int its = 0, missed = 0;
+    double worst = 0.0;
+    for (int v = 0; v < nb; ++v) {
+      its += s_it[v];
+      if (!((done >> v) & 1u)) ++missed;
+      if (s_bn2[v] > 0.0) worst = fmax(worst, sqrt(s_rn2[v] / s_bn2[v]));
+    }
+    atomicAdd(a.out, its);
+    if (missed) atomicAdd(a.out + 2, missed);
+    a.out_rel[0] = worst;
+  }
+}
+
+static size_t batch_smem_bytes(int restart) {
+  const size_t per = 8 * 64 + 4 * kSmMaxDofs + 2 * (size_t)restart * kSmMaxDofs;
+  return ((size_t)kSmMaxDofs * 40 + kBatchMaxVecs * per) * sizeof(Cx<double>) +
+         2 * (size_t)kBatchMaxVecs * kSmSlots * sizeof(double);
+}
+
+bool coarsest_batch_fits(Geo2 g, int N, int restart, int sms) {
+  if (!coarsest_smem_fits(g, N, restart, sms)) return false;
+  return batch_smem_bytes(restart) <= 227 * 1024;
+}
+
+void launch_coarsest_gcr_batch(const Cx<double> *Y, const Cx<double> *Minv, long long minv_stride,
+                               const double *shift, Geo2 g, int nb, const Cx<double> *b, Cx<double> *x,
+                               Cx<double> *upub, Cx<double> *xpub, double *partials, unsigned int *bar, double tol,
+                               int restart, int max_iter, int *out, double *out_rel, int sms, cudaStream_t s) {
+  if (nb < 1 || nb > kBatchMaxVecs) fail(MG_ERR_INVALID_ARG, "batched coarsest solve: 1..4 vectors per launch");
+  CgBArgs a;
+  a.Y = Y;
+  a.Minv = Minv;
+  a.minv_stride = minv_stride;
+  a.shift = shift;
+  a.L0 = g.L0;
+  a.L1 = g.L1;
+  a.nsites = g.nsites;
+  a.spc = (int)((g.nsites + sms - 1) / sms);
+  a.nb = nb;
+  const int grid = (int)((g.nsites + a.spc - 1) / a.spc);
+  if (grid > kMaxGridB) fail(MG_ERR_UNSUPPORTED, "batched coarsest solve: more than 256 CTAs");
+  a.b = b;
+  a.x = x;
+  a.upub = upub;
+  a.xpub = xpub;
+  a.partials = partials;
+  a.bar = bar;
+  a.tol = tol;
+  a.restart = restart;
+  a.max_iter = max_iter;
+  a.spin_limit = 1LL << 24;
+  a.out = out;
+  a.out_rel = out_rel;
+  const size_t smem = batch_smem_bytes(restart);
+  const void *fn = (const void *)coarsest_gcr_batch_kernel;
+  MG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessorWithFlags(&per_sm, fn, 256, smem, 0));
+  if (per_sm < 1) fail(MG_ERR_CUDA, "batched coarsest solve kernel cannot be resident");
+  MG_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s));
+  void *args[] = {&a};
+  MG_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, smem, s));
+  MG_LAUNCHED();
 }
 
 }  // namespace mg

@@ -270,6 +270,7 @@ struct ReduceWs {
   unsigned int *ticket;
   int max_blocks;         // grid cap of the grid-stride reductions
   long long capacity = 0; // doubles available in partials
+  long long tickets = 0;  // counters available in ticket
 };
 
 constexpr int kReduceThreads = 256;

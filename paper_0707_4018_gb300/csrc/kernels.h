@@ -18,6 +18,7 @@ struct OpDesc {
   Geo2 geo;
   int N;
   double diag;
+  const double *shift = nullptr;  // per batched vector: diagonal + shift[v] (null: none)
 };
 
 // ---- fused MR smoothing (one launch per iteration) ----
@@ -31,22 +32,24 @@ template <typename R>
 void launch_mr_iteration(const OpDesc<R> &op, bool step, const Cx<R> *r_old, const Cx<R> *Ar_old, const double *sc_old,
                          double omega, Cx<R> *x, bool x_init, Cx<R> *r_new, Cx<R> *Ar_new, double *sc_new,
                          const ReduceWs &ws, cudaStream_t s, int nvec = 1);
-// x (+)= alpha r_old, alpha from sc_old (the last MR update)
+// x (+)= alpha r_old, alpha from sc_old (the last MR update); with r_out, also the final
+// residual r_out = r_old - alpha Ar_old (r_out may equal r_old)
 template <typename R>
 void launch_mr_last(const Cx<R> *r_old, const double *sc_old, double omega, Cx<R> *x, bool x_init, long long n,
-                    cudaStream_t s, int nvec = 1);
+                    cudaStream_t s, int nvec = 1, const Cx<R> *Ar_old = nullptr, Cx<R> *r_out = nullptr);
 
 // ---- fine Wilson operator (2d, U(1), gamma_1 = sigma_1, gamma_2 = sigma_2) ----
-// out = a * D in + c * b   (b may be null when c == 0); D has diagonal `diag` = d + m
+// out = a * D in + c * b   (b may be null when c == 0); D has diagonal `diag` = d + m,
+// plus shift[v] for batched vector v when `shift` (device, nvec doubles) is given
 template <typename R>
 void launch_dslash(const Cx<R> *U, const Cx<R> *in, Cx<R> *out, Geo2 g, double diag, const Cx<R> *b, double a,
-                   double c, cudaStream_t s, int nvec = 1);
+                   double c, cudaStream_t s, int nvec = 1, const double *shift = nullptr);
 
 // ---- coarse stencil operator, N x N blocks, internal layout Y[j][dir][col][row] ----
-// out = a * A in + c * b
+// out = a * A in + c * b; with `shift`, vector v sees A + shift[v] * identity
 template <typename R>
 void launch_coarse_apply(const Cx<R> *Y, const Cx<R> *in, Cx<R> *out, Geo2 g, int N, const Cx<R> *b, double a,
-                         double c, cudaStream_t s, int nvec = 1);
+                         double c, cudaStream_t s, int nvec = 1, const double *shift = nullptr);
 
 // ---- BLAS-1 ----
 template <typename R>
@@ -80,6 +83,19 @@ void launch_gcr_project_update(const Cx<double> *W, Cx<double> *Wk, const Cx<dou
                                const double *beta_dev, double inv, double are, double aim, Cx<double> *x,
                                Cx<double> *r, long long n, bool update_xr, cudaStream_t s);
 
+// batched outer GCR over nb systems (vector v at v * n; bases W[j][v][n], Z[j][v][n]):
+// y_v = mask bit v ? x_v : 0
+void launch_copy_masked(const Cx<double> *x, Cx<double> *y, long long n, int nb, unsigned int mask, cudaStream_t s);
+// out[v] = |a_v|^2
+void launch_norm2_batch(const Cx<double> *a, long long n, int nb, double *out, const ReduceWs &ws, cudaStream_t s);
+// out[v * 2 (k + 2) + 2 j] = <W_j,v, W_k,v> (j < k), then |W_k,v|^2 and <W_k,v, r_v>
+void launch_gcr_dots_batch(const Cx<double> *W, const Cx<double> *r, int k, int nb, long long n, double *out,
+                           const ReduceWs &ws, cudaStream_t s);
+// per vector, coef[4 v .. 4 v + 3] = (inv, alpha, mode): mode 0 skip, 2 project W_k / Z_k
+// with the betas in dots, 1 project, scale by inv, x += alpha Z_k, r -= alpha W_k
+void launch_gcr_update_batch(Cx<double> *W, Cx<double> *Z, int k, int nb, const double *dots, const double *coef,
+                             Cx<double> *x, Cx<double> *r, long long n, cudaStream_t s);
+
 // ---- transfer between levels ----
 // coarse[b][k] = sum_i conj(V[b][k][i]) fine[site(b,s)][a]
 template <typename R>
@@ -108,7 +124,8 @@ void launch_prolongator_to_canonical(const Cx<double> *V, Cx<double> *out, Block
 void launch_gaussian(Cx<double> *out, long long n, unsigned long long seed, int k, int level, cudaStream_t s);
 
 // ---- coarsest level: dense LU with partial pivoting, column-major ----
-void launch_dense_from_stencil(const Cx<double> *Y, Cx<double> *A, Geo2 g, int N, cudaStream_t s);
+// dense matrix of the stencil plus shift * identity
+void launch_dense_from_stencil(const Cx<double> *Y, Cx<double> *A, Geo2 g, int N, cudaStream_t s, double shift = 0.0);
 // factor in place; ipiv[k] = pivot row of step k; info_dev[0] = 1 + first zero pivot (0 if none)
 void lu_factor(Cx<double> *A, int n, int *ipiv, int *info_dev, cudaStream_t s);
 // x = A^{-1} b with the factors; work: n entries, must alias neither b nor x (b may equal work)
@@ -116,10 +133,11 @@ void lu_solve_ws(const Cx<double> *LU, const int *ipiv, int n, const Cx<double> 
                  cudaStream_t s);
 
 // ---- coarsest level: restarted GCR as one persistent cooperative kernel (FP64) ----
-// Preparation: Minv[j] = X_j^{-1} (self blocks) and Yt = stencil of A M, M = blockdiag(Minv);
-// work: nsites * 2 N^2 entries; info_dev[0] = 1 if a self block is singular.
+// Preparation for A = Y + shift * identity: Minv[j] = (X_j + shift)^{-1} (self blocks) and,
+// unless Yt is null, Yt = stencil of A M, M = blockdiag(Minv); work: nsites * 2 N^2 entries;
+// info_dev[0] = 1 if a self block is singular.
 void prepare_coarsest_gcr(const Cx<double> *Y, Geo2 g, int N, Cx<double> *Minv, Cx<double> *Yt, Cx<double> *work,
-                          int *info_dev, cudaStream_t s);
+                          int *info_dev, cudaStream_t s, double shift = 0.0);
 // x = A^{-1} b to relative true residual tol (GCR on A M y = b, x = M y); y, r: n entries;
 // Z/W: restart * n each (restart <= 32); partials: grid * kCoarsestSlots doubles; bar: 2 uints;
 // out[0] += iterations, out[1] = 1 on a barrier timeout, out[2] += 1 if the tolerance was missed.
@@ -139,5 +157,18 @@ void launch_coarsest_gcr_smem(const Cx<double> *Yt, const Cx<double> *Minv, Geo2
                               Cx<double> *x, Cx<double> *rpub, Cx<double> *ypub, double *partials, unsigned int *bar,
                               double tol, int restart, int max_iter, int *out, double *out_rel, int sms,
                               cudaStream_t s);
+
+// Batched variant: nb <= 4 right-hand sides in one launch, vector v solving
+// (Y + shift[v]) x_v = b_v (shift: device, null for none) with M_v = Minv + v * minv_stride
+// (minv_stride 0: one preconditioner for all); Y is the raw stencil. b, x, upub, xpub hold
+// nb vectors of n; partials: kBatchPartials(grid) doubles; out / out_rel as above (out[0]
+// adds the iterations of every vector, out_rel[0] the largest relative residual).
+bool coarsest_batch_fits(Geo2 g, int N, int restart, int sms);
+constexpr int kCoarsestBatchVecs = 4;
+inline long long coarsest_batch_partials(int grid) { return 4LL * (2 * 16 + 4) * grid; }
+void launch_coarsest_gcr_batch(const Cx<double> *Y, const Cx<double> *Minv, long long minv_stride,
+                               const double *shift, Geo2 g, int nb, const Cx<double> *b, Cx<double> *x,
+                               Cx<double> *upub, Cx<double> *xpub, double *partials, unsigned int *bar, double tol,
+                               int restart, int max_iter, int *out, double *out_rel, int sms, cudaStream_t s);
 
 }  // namespace mg

@@ -98,7 +98,24 @@ struct mg_ctx {
   mg::DevBuf<int> cg_out;  // [0] iterations, [1] timeout flag, [2] solves above tolerance
   int cg_grid = 0;
   bool cg_smem = false;  // shared-memory-resident coarsest solver
-  int nbatch = 1;        // vectors the FP64 level work buffers hold
+  int nbatch = 1;        // vectors the level work buffers hold (max of Nv and max_rhs)
+  // batched solves: vector v of a batch sees every level's operator shifted by shift[v]
+  // (mass_v - m; exact on the coarse levels because P^dagger P = 1) and uses coarsest slot v
+  const double *cur_shift = nullptr;  // set while a batched solve records or runs its V-cycles
+  mg::DevBuf<double> shift_dev;
+  std::vector<double> slot_shift;     // shift each slot was prepared for (NaN: not prepared)
+  mg::DevBuf<mg::Cx<double>> bMinv, bYt;               // per slot (iterative coarsest)
+  std::vector<mg::DevBuf<mg::Cx<double>>> bLU;         // per slot (dense coarsest)
+  std::vector<mg::DevBuf<int>> bipiv;
+  bool cg_batch = false;  // batched shared-memory coarsest kernel usable
+  mg::DevBuf<mg::Cx<double>> cgb_u, cgb_x;
+  mg::DevBuf<double> cgb_partials;
+  // batched outer GCR
+  mg::DevBuf<mg::Cx<double>> bZ, bW, br, brin, bz64;
+  mg::DevBuf<mg::Cx<float>> bz32;
+  mg::DevBuf<double> bdots, bcoef;
+  double *bhost = nullptr;  // pinned: dots, then coefficients
+  std::vector<mg::GraphCache> preb[2];  // batched preconditioner graphs, per precision and batch size
   // outer
   mg::DevBuf<mg::Cx<double>> oZ, oW, orr;
   mg::DevBuf<mg::Cx<float>> z32;
@@ -116,6 +133,9 @@ struct mg_ctx {
   mg::DevBuf<mg::Cx<double>> z64;
   ~mg_ctx() {
     for (auto &g : pre) g.reset();
+    for (auto &v : preb)
+      for (auto &g : v) g.reset();
+    if (bhost) cudaFreeHost(bhost);
     for (auto &g : setup_vc) g.reset();
     if (s) cudaStreamDestroy(s);
     if (ev) cudaEventDestroy(ev);
@@ -161,9 +181,9 @@ static void apply_op(mg_ctx &c, int l, const Cx<R> *in, Cx<R> *out, const Cx<R> 
                      double cc = 0.0, int nvec = 1) {
   Level &L = c.lv[l];
   if (l == 0)
-    launch_dslash<R>(Uof<R>(c), in, out, L.geo, diag_of(c), b, a, cc, c.s, nvec);
+    launch_dslash<R>(Uof<R>(c), in, out, L.geo, diag_of(c), b, a, cc, c.s, nvec, c.cur_shift);
   else
-    launch_coarse_apply<R>(Yof<R>(L), in, out, L.geo, L.nint, b, a, cc, c.s, nvec);
+    launch_coarse_apply<R>(Yof<R>(L), in, out, L.geo, L.nint, b, a, cc, c.s, nvec, c.cur_shift);
   c.apps[l] += nvec;
 }
 
@@ -177,18 +197,23 @@ static OpDesc<R> op_of(mg_ctx &c, int l) {
   o.geo = L.geo;
   o.N = L.nint;
   o.diag = diag_of(c);
+  o.shift = c.cur_shift;
   return o;
 }
 
 // x (+)= nu MR iterations for A_l x = b from zero (accumulate: added to x), with the
 // fused kernels: nu + 1 launches for a batch of nvec vectors (stride n). b may be the
-// level's r buffer (consumed then).
+// level's r buffer (consumed then). With r_out (not accumulating), the last launch also
+// leaves the smoothed residual b - A x there (the MR recurrence r <- r - alpha A r;
+// r_out may be the level's r buffer).
 template <typename R>
-static void smooth(mg_ctx &c, int l, const Cx<R> *b, Cx<R> *x, int nu, bool accumulate, int nvec = 1) {
+static void smooth(mg_ctx &c, int l, const Cx<R> *b, Cx<R> *x, int nu, bool accumulate, int nvec = 1,
+                   Cx<R> *r_out = nullptr) {
   Level &L = c.lv[l];
   Work<R> &w = work<R>(L);
   if (nu <= 0) {
     if (!accumulate) launch_zero<R>(x, L.n * nvec, c.s);
+    if (r_out != nullptr && r_out != b) launch_copy<R>(b, r_out, L.n * nvec, c.s);
     return;
   }
   double *sc[2] = {c.scal.p + kSlotMR + 8 * kMaxBatch * l, c.scal.p + kSlotMR + 8 * kMaxBatch * l + 4 * kMaxBatch};
@@ -209,7 +234,8 @@ static void smooth(mg_ctx &c, int l, const Cx<R> *b, Cx<R> *x, int nu, bool accu
     asel ^= 1;
     ssel ^= 1;
   }
-  launch_mr_last<R>(r_old, sc[ssel ^ 1], c.p.omega, x, nu == 1 && !accumulate, L.n, c.s, nvec);
+  launch_mr_last<R>(r_old, sc[ssel ^ 1], c.p.omega, x, nu == 1 && !accumulate, L.n, c.s, nvec, Arbuf[asel ^ 1],
+                    r_out);
 }
 
 static void precondition(mg_ctx &c, const Cx<double> *r, Cx<double> *z);
@@ -300,23 +326,51 @@ static GcrOut outer_fgcr(mg_ctx &c, const Cx<double> *b, Cx<double> *x, double t
   return out;
 }
 
-// exact solve on the coarsest level (FP64): dense LU or GCR to coarsest_tol
-static void coarsest_solve64(mg_ctx &c, const Cx<double> *b, Cx<double> *x) {
+// exact solve on the coarsest level (FP64): dense LU or GCR to coarsest_tol. Slot 0 holds
+// the factors / preconditioner at the context mass, slot 1 + v those of batched vector v.
+static void coarsest_solve64(mg_ctx &c, const Cx<double> *b, Cx<double> *x, int slot = 0) {
   const int l = c.p.levels - 1;
+  const Level &L = c.lv[l];
   if (c.use_lu) {
-    lu_solve_ws(c.LU.p, c.ipiv.p, c.nc, b, x, c.lu_work.p, c.s);
+    const Cx<double> *LU = slot == 0 ? c.LU.p : c.bLU[slot - 1].p;
+    const int *piv = slot == 0 ? c.ipiv.p : c.bipiv[slot - 1].p;
+    lu_solve_ws(LU, piv, c.nc, b, x, c.lu_work.p, c.s);
     c.apps[l]++;
     return;
   }
-  const Level &L = c.lv[l];
+  const long long m2 = L.geo.nsites * (long long)L.nint * L.nint;
+  const Cx<double> *Minv = slot == 0 ? c.cg_Minv.p : c.bMinv.p + (slot - 1) * m2;
+  const Cx<double> *Yt = slot == 0 ? c.cg_Yt.p : c.bYt.p + (slot - 1) * 5 * m2;
   if (c.cg_smem)
-    launch_coarsest_gcr_smem(c.cg_Yt.p, c.cg_Minv.p, L.geo, b, x, c.cr.p, c.cg_y.p, c.cg_partials.p, c.cg_bar.p,
+    launch_coarsest_gcr_smem(Yt, Minv, L.geo, b, x, c.cr.p, c.cg_y.p, c.cg_partials.p, c.cg_bar.p,
                              c.p.coarsest_tol, c.p.coarsest_restart, c.p.coarsest_max_iter, c.cg_out.p, c.cg_rel.p,
                              c.cg_grid, c.s);
   else
-    launch_coarsest_gcr(c.cg_Yt.p, c.cg_Minv.p, L.geo, L.nint, b, x, c.cg_y.p, c.cr.p, c.cZ.p, c.cW.p,
+    launch_coarsest_gcr(Yt, Minv, L.geo, L.nint, b, x, c.cg_y.p, c.cr.p, c.cZ.p, c.cW.p,
                         c.cg_partials.p, c.cg_bar.p, c.p.coarsest_tol, c.p.coarsest_restart, c.p.coarsest_max_iter,
                         c.cg_out.p, c.cg_rel.p, c.cg_grid, c.s);
+}
+
+// coarsest solves of nvec vectors (stride n). In a batched solve (cur_shift set) vector v
+// uses slot 1 + v; otherwise every vector uses slot 0. Several vectors at once go through
+// the batched shared-memory kernel (up to 4 per launch) when it applies.
+static void coarsest_vectors64(mg_ctx &c, const Cx<double> *b, Cx<double> *x, int nvec) {
+  const int l = c.p.levels - 1;
+  const Level &L = c.lv[l];
+  const long long n = L.n;
+  const bool batch = c.cur_shift != nullptr;
+  if (c.cg_batch && (nvec > 1 || batch)) {
+    const long long m2 = L.geo.nsites * 64LL;
+    for (int v0 = 0; v0 < nvec; v0 += kCoarsestBatchVecs) {
+      const int nb = std::min(kCoarsestBatchVecs, nvec - v0);
+      launch_coarsest_gcr_batch(L.Y64.p, batch ? c.bMinv.p + v0 * m2 : c.cg_Minv.p, batch ? m2 : 0,
+                                batch ? c.cur_shift + v0 : nullptr, L.geo, nb, b + v0 * n, x + v0 * n, c.cgb_u.p,
+                                c.cgb_x.p, c.cgb_partials.p, c.cg_bar.p, c.p.coarsest_tol, c.p.coarsest_restart,
+                                c.p.coarsest_max_iter, c.cg_out.p, c.cg_rel.p, c.cg_grid, c.s);
+    }
+    return;
+  }
+  for (int v = 0; v < nvec; ++v) coarsest_solve64(c, b + v * n, x + v * n, batch ? 1 + v : 0);
 }
 
 // iterations of the persistent coarsest solves since the last reset; fails on a barrier timeout
@@ -331,16 +385,16 @@ static long long collect_coarsest(mg_ctx &c) {
 }
 
 template <typename R>
-static void coarsest_solve(mg_ctx &c, const Cx<R> *b, Cx<R> *x);
+static void coarsest_solve(mg_ctx &c, const Cx<R> *b, Cx<R> *x, int nvec);
 template <>
-void coarsest_solve<double>(mg_ctx &c, const Cx<double> *b, Cx<double> *x) {
-  coarsest_solve64(c, b, x);
+void coarsest_solve<double>(mg_ctx &c, const Cx<double> *b, Cx<double> *x, int nvec) {
+  coarsest_vectors64(c, b, x, nvec);
 }
 template <>
-void coarsest_solve<float>(mg_ctx &c, const Cx<float> *b, Cx<float> *x) {
-  const long long n = c.lv.back().n;
+void coarsest_solve<float>(mg_ctx &c, const Cx<float> *b, Cx<float> *x, int nvec) {
+  const long long n = c.lv.back().n * nvec;
   launch_convert<double, float>(b, c.cb.p, n, c.s);
-  coarsest_solve64(c, c.cb.p, c.cx.p);
+  coarsest_vectors64(c, c.cb.p, c.cx.p, nvec);
   launch_convert<float, double>(c.cx.p, x, n, c.s);
 }
 
@@ -354,18 +408,16 @@ static void check_fresh(const mg_ctx &c) {
 template <typename R>
 static void vcycle(mg_ctx &c, int l, const Cx<R> *b, Cx<R> *x, int nvec = 1) {
   if (l == c.p.levels - 1) {
-    const long long n = c.lv[l].n;
-    for (int v = 0; v < nvec; ++v) coarsest_solve<R>(c, b + v * n, x + v * n);
+    coarsest_solve<R>(c, b, x, nvec);
     return;
   }
   Level &L = c.lv[l];
   Level &C = c.lv[l + 1];
   Work<R> &w = work<R>(L);
   Work<R> &wc = work<R>(C);
-  // 1. pre-relaxation from zero
-  smooth<R>(c, l, b, x, c.p.nu_pre, false, nvec);
+  // 1. pre-relaxation from zero, leaving the residual b - A x in w.r
+  smooth<R>(c, l, b, x, c.p.nu_pre, false, nvec, w.r.p);
   // 2. restrict the residual
-  apply_op<R>(c, l, x, w.r.p, b, -1.0, 1.0, nvec);
   launch_restrict<R>(Vof<R>(L), w.r.p, wc.b.p, L.bg, L.Nv, c.s, nvec);
   // 3. coarse V-cycle (or exact coarsest solve)
   vcycle<R>(c, l + 1, wc.b.p, wc.x.p, nvec);
@@ -448,10 +500,179 @@ static void precondition(mg_ctx &c, const Cx<double> *r, Cx<double> *z) {
 }
 
 // ---------------------------------------------------------------------------
+// batched solves: nb systems (D + shift_v) psi_v = chi_v sharing one hierarchy
+// ---------------------------------------------------------------------------
+
+// coarsest slots 1..nb for the shifts (prepared again only when a shift changed)
+static void prepare_slots(mg_ctx &c, int nb, const double *shift) {
+  Level &L = c.lv.back();
+  const long long m2 = L.geo.nsites * (long long)L.nint * L.nint;
+  for (int v = 0; v < nb; ++v) {
+    if (c.slot_shift[v] == shift[v]) continue;
+    if (c.use_lu) {
+      if (c.bLU[v].p == nullptr) {
+        c.bLU[v].alloc((size_t)c.nc * c.nc);
+        c.bipiv[v].alloc(c.nc);
+      }
+      launch_dense_from_stencil(L.Y64.p, c.bLU[v].p, L.geo, L.nint, c.s, shift[v]);
+      lu_factor(c.bLU[v].p, c.nc, c.bipiv[v].p, c.info.p, c.s);
+      int info = 0;
+      MG_CUDA(cudaMemcpyAsync(&info, c.info.p, sizeof(int), cudaMemcpyDeviceToHost, c.s));
+      MG_CUDA(cudaStreamSynchronize(c.s));
+      if (info != 0) fail(MG_ERR_NAN, "coarsest LU (batched mass): zero pivot at column " + std::to_string(info - 1));
+    } else {
+      prepare_coarsest_gcr(L.Y64.p, L.geo, L.nint, c.bMinv.p + v * m2, c.cg_batch ? nullptr : c.bYt.p + v * 5 * m2,
+                           c.cg_work.p, c.cg_info.p, c.s, shift[v]);
+      int info = 0;
+      MG_CUDA(cudaMemcpyAsync(&info, c.cg_info.p, sizeof(int), cudaMemcpyDeviceToHost, c.s));
+      MG_CUDA(cudaStreamSynchronize(c.s));
+      if (info != 0) fail(MG_ERR_NAN, "coarsest level (batched mass): a self block is singular");
+    }
+    c.slot_shift[v] = shift[v];
+  }
+}
+
+// z_v = V r_v for the vectors in mask (0 for the others), all nb in one batched V-cycle
+// in the context precision; the cycle reads the fixed buffer brin, so one captured graph
+// per batch size serves every call
+static void precondition_batch(mg_ctx &c, int nb, const Cx<double> *r, unsigned int mask, Cx<double> *z) {
+  Level &F = c.lv[0];
+  const long long n = F.n;
+  launch_copy_masked(r, c.brin.p, n, nb, mask, c.s);
+  if (c.p.precision == MG_FP32) {
+    graph_run(c, c.preb[1][nb], [&] {
+      launch_convert<float, double>(c.brin.p, F.w32.b.p, n * nb, c.s);
+      vcycle<float>(c, 0, F.w32.b.p, c.bz32.p, nb);
+    });
+    launch_convert<double, float>(c.bz32.p, z, n * nb, c.s);
+  } else {
+    graph_run(c, c.preb[0][nb], [&] { vcycle<double>(c, 0, c.brin.p, c.bz64.p, nb); });
+    launch_copy<double>(c.bz64.p, z, n * nb, c.s);
+  }
+}
+
+// Outer flexible GCR over nb systems in lockstep (the single-system loop above, per
+// vector): one batched V-cycle, one batched D apply and one batched reduction per
+// iteration; the host forms each vector's coefficients from one fetch. A vector whose
+// tracked residual meets tol (or whose basis breaks down) stops until the next restart,
+// where the true residuals b - D x decide which vectors continue.
+static void outer_fgcr_batch(mg_ctx &c, int nb, const Cx<double> *b, Cx<double> *x, double tol,
+                             std::vector<GcrOut> &out) {
+  Level &F = c.lv[0];
+  const long long n = F.n;
+  const int restart = c.p.gcr_restart;
+  Cx<double> *Z = c.bZ.p, *W = c.bW.p, *r = c.br.p;
+  double *h = c.bhost;
+  double *hcoef = c.bhost + (size_t)c.p.max_rhs * 2 * (restart + 2);
+  out.assign(nb, GcrOut{});
+  auto fetch = [&](const double *dev, int count) {
+    MG_CUDA(cudaMemcpyAsync(h, dev, count * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+    MG_CUDA(cudaStreamSynchronize(c.s));
+    for (int i = 0; i < count; ++i)
+      if (std::isnan(h[i])) fail(MG_ERR_NAN, "outer GCR (batched): NaN in a reduction");
+  };
+  launch_zero<double>(x, n * nb, c.s);
+  launch_copy<double>(b, r, n * nb, c.s);
+  launch_norm2_batch(b, n, nb, c.bdots.p, c.ws, c.s);
+  fetch(c.bdots.p, nb);
+  std::vector<double> bn2(h, h + nb), rn2(bn2);
+  unsigned int done = 0u;
+  for (int v = 0; v < nb; ++v) {
+    if (!(bn2[v] > 0.0)) {
+      done |= 1u << v;
+      out[v].converged = true;
+    }
+  }
+  const unsigned int all = nb == 32 ? 0xffffffffu : (1u << nb) - 1u;
+  int iters = 0;
+  std::vector<double> nw0(nb), nw2(nb), wr(nb), wi(nb);
+  while (done != all && iters < c.p.max_iter) {
+    unsigned int act = all & ~done;
+    int k = 0;
+    for (; k < restart && iters < c.p.max_iter && act != 0u; ++k) {
+      Cx<double> *Zk = Z + (long long)k * nb * n, *Wk = W + (long long)k * nb * n;
+      precondition_batch(c, nb, r, act, Zk);
+      apply_op<double>(c, 0, Zk, Wk, nullptr, 1.0, 0.0, nb);
+      launch_gcr_dots_batch(W, r, k, nb, n, c.bdots.p, c.ws, c.s);
+      const int stride = 2 * (k + 2);
+      fetch(c.bdots.p, nb * stride);
+      unsigned int cancel = 0u;
+      for (int v = 0; v < nb; ++v) {
+        const double *hv = h + v * stride;
+        nw0[v] = hv[2 * k];
+        nw2[v] = nw0[v];
+        for (int j = 0; j < k; ++j) nw2[v] -= hv[2 * j] * hv[2 * j] + hv[2 * j + 1] * hv[2 * j + 1];
+        wr[v] = hv[2 * k + 2];
+        wi[v] = hv[2 * k + 3];
+        if (((act >> v) & 1u) && k > 0 && !(nw2[v] > 0.5 * nw0[v])) cancel |= 1u << v;
+      }
+      if (cancel != 0u) {
+        // cancellation: project those vectors once, then take fresh coefficients for them
+        for (int v = 0; v < nb; ++v) {
+          hcoef[4 * v] = 1.0;
+          hcoef[4 * v + 1] = hcoef[4 * v + 2] = 0.0;
+          hcoef[4 * v + 3] = ((cancel >> v) & 1u) ? 2.0 : 0.0;
+        }
+        MG_CUDA(cudaMemcpyAsync(c.bcoef.p, hcoef, 4 * nb * sizeof(double), cudaMemcpyHostToDevice, c.s));
+        launch_gcr_update_batch(W, Z, k, nb, c.bdots.p, c.bcoef.p, x, r, n, c.s);
+        launch_gcr_dots_batch(W, r, k, nb, n, c.bdots.p, c.ws, c.s);
+        fetch(c.bdots.p, nb * stride);
+        for (int v = 0; v < nb; ++v) {
+          if (!((cancel >> v) & 1u)) continue;
+          const double *hv = h + v * stride;
+          nw0[v] = hv[2 * k];
+          nw2[v] = nw0[v];
+          for (int j = 0; j < k; ++j) nw2[v] -= hv[2 * j] * hv[2 * j] + hv[2 * j + 1] * hv[2 * j + 1];
+        }
+        // vectors without cancellation keep their first coefficients: their w is unchanged,
+        // so the fresh reduction reproduced them
+      }
+      for (int v = 0; v < nb; ++v) {
+        hcoef[4 * v + 3] = 0.0;
+        if (!((act >> v) & 1u)) continue;
+        if (!(nw2[v] > 1e-28 * nw0[v])) {
+          act &= ~(1u << v);  // breakdown: this vector waits for the restart
+          continue;
+        }
+        const double inv = 1.0 / std::sqrt(nw2[v]);
+        const double are = wr[v] * inv, aim = wi[v] * inv;
+        hcoef[4 * v] = inv;
+        hcoef[4 * v + 1] = are;
+        hcoef[4 * v + 2] = aim;
+        hcoef[4 * v + 3] = 1.0;
+        rn2[v] = std::max(rn2[v] - (are * are + aim * aim), 0.0);
+        ++out[v].iters;
+        if (std::sqrt(rn2[v] / bn2[v]) <= tol) act &= ~(1u << v);
+      }
+      // mode 1 projects with the betas now in bdots: fresh ones for the vectors that were
+      // projected once already, the original ones (the same reduction again) for the others
+      MG_CUDA(cudaMemcpyAsync(c.bcoef.p, hcoef, 4 * nb * sizeof(double), cudaMemcpyHostToDevice, c.s));
+      launch_gcr_update_batch(W, Z, k, nb, c.bdots.p, c.bcoef.p, x, r, n, c.s);
+      ++iters;
+    }
+    // true residuals r = b - D x of every unfinished vector (defect correction)
+    apply_op<double>(c, 0, x, r, b, -1.0, 1.0, nb);
+    launch_norm2_batch(r, n, nb, c.bdots.p, c.ws, c.s);
+    fetch(c.bdots.p, nb);
+    for (int v = 0; v < nb; ++v) {
+      if ((done >> v) & 1u) continue;
+      rn2[v] = h[v];
+      out[v].rel = std::sqrt(rn2[v] / bn2[v]);
+      if (out[v].rel <= tol) {
+        done |= 1u << v;
+        out[v].converged = true;
+      }
+    }
+    if (k == 0) break;  // no progress possible
+  }
+}
+
+// ---------------------------------------------------------------------------
 // setup
 // ---------------------------------------------------------------------------
 static void prepare_coarsest(mg_ctx &c) {
   Level &L = c.lv.back();
+  std::fill(c.slot_shift.begin(), c.slot_shift.end(), std::nan(""));  // batched slots are stale
   if (!c.use_lu) {
     prepare_coarsest_gcr(L.Y64.p, L.geo, L.nint, c.cg_Minv.p, c.cg_Yt.p, c.cg_work.p, c.cg_info.p, c.s);
     int info = 0;
@@ -578,6 +799,7 @@ static void validate(const mg_geom *g, const mg_params *p) {
   if (p->coarsest_restart < 1 || p->coarsest_restart > 32)
     fail(MG_ERR_INVALID_ARG, "coarsest_restart must be in [1, 32]");
   if (p->max_iter < 1 || p->coarsest_max_iter < 1) fail(MG_ERR_INVALID_ARG, "iteration limits must be >= 1");
+  if (p->max_rhs < 1 || p->max_rhs > kMaxBatch) fail(MG_ERR_INVALID_ARG, "max_rhs must be in [1, 32]");
   int L0 = g->dims[0], L1 = g->dims[1], nint = 2;
   for (int l = 0; l + 1 < p->levels; ++l) {
     const int B0 = p->block[l][0], B1 = p->block[l][1];
@@ -614,6 +836,7 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
   c->lv.resize(p->levels);
   c->nbatch = 1;
   for (int l = 0; l + 1 < p->levels; ++l) c->nbatch = std::max(c->nbatch, p->Nv[l]);
+  c->nbatch = std::max(c->nbatch, p->max_rhs);
   int L0 = g->dims[0], L1 = g->dims[1], nint = 2;
   const bool f32 = p->precision == MG_FP32;
   for (int l = 0; l < p->levels; ++l) {
@@ -697,11 +920,45 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
     c->cg_y.alloc(Cst.n);
     c->cg_info.alloc(1);
     MG_CUDA(cudaMemsetAsync(c->cg_out.p, 0, 3 * sizeof(int), c->s));
+    c->cg_batch = c->cg_smem && coarsest_batch_fits(Cst.geo, Cst.nint, p->coarsest_restart, c->cg_grid) &&
+                  std::getenv("MG_NO_BATCH_COARSEST") == nullptr;
+    if (c->cg_batch) {
+      c->cgb_u.alloc((size_t)kCoarsestBatchVecs * Cst.n);
+      c->cgb_x.alloc((size_t)kCoarsestBatchVecs * Cst.n);
+      c->cgb_partials.alloc((size_t)coarsest_batch_partials(c->cg_grid));
+    }
   }
   if (f32) {
-    c->cb.alloc(Cst.n);
-    c->cx.alloc(Cst.n);
+    c->cb.alloc(Cst.n * (size_t)c->nbatch);
+    c->cx.alloc(Cst.n * (size_t)c->nbatch);
     c->z32.alloc(F.n);
+  }
+  // batched solves
+  c->shift_dev.alloc(std::max(p->max_rhs, 1));
+  c->slot_shift.assign(p->max_rhs, std::nan(""));
+  c->preb[0].resize(p->max_rhs + 1);
+  c->preb[1].resize(p->max_rhs + 1);
+  if (p->max_rhs > 1) {
+    const size_t nr = (size_t)p->max_rhs;
+    const size_t m2 = (size_t)Cst.geo.nsites * Cst.nint * Cst.nint;
+    if (c->use_lu) {
+      c->bLU.resize(nr);
+      c->bipiv.resize(nr);
+    } else {
+      c->bMinv.alloc(nr * m2);
+      if (!c->cg_batch) c->bYt.alloc(nr * 5 * m2);
+    }
+    c->bZ.alloc((size_t)p->gcr_restart * nr * F.n);
+    c->bW.alloc((size_t)p->gcr_restart * nr * F.n);
+    c->br.alloc(nr * F.n);
+    c->brin.alloc(nr * F.n);
+    if (f32)
+      c->bz32.alloc(nr * F.n);
+    else
+      c->bz64.alloc(nr * F.n);
+    c->bdots.alloc(nr * 2 * (p->gcr_restart + 2));
+    c->bcoef.alloc(nr * 4);
+    MG_CUDA(cudaMallocHost(&c->bhost, (nr * 2 * (p->gcr_restart + 2) + nr * 4) * sizeof(double)));
   }
   // outer
   c->z64.alloc(F.n);
@@ -713,13 +970,16 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
   // the fused MR kernels reduce over one block per 256 sites (fine) or dofs (coarse)
   long long cap = (long long)c->ws.max_blocks * 4;
   for (int l = 0; l < p->levels; ++l) {
-    const long long units = l == 0 ? c->lv[l].geo.nsites : c->lv[l].n;
+    // fine: a thread per site; coarse N = 8: four threads per dof; other N: a thread per dof
+    const long long units = l == 0 ? c->lv[l].geo.nsites : (c->lv[l].nint == 8 ? 4 : 1) * c->lv[l].n;
     cap = std::max(cap, 3 * ((units + 255) / 256) * c->nbatch);
   }
+  cap = std::max(cap, 2LL * (p->gcr_restart + 2) * p->max_rhs * 64);
   c->partials.alloc((size_t)cap + 16);
   c->ws.capacity = cap;
-  c->tickets.alloc(128);
-  MG_CUDA(cudaMemsetAsync(c->tickets.p, 0, 128 * sizeof(unsigned int), c->s));
+  c->ws.tickets = std::max(128, (p->gcr_restart + 2) * p->max_rhs);
+  c->tickets.alloc((size_t)c->ws.tickets);
+  MG_CUDA(cudaMemsetAsync(c->tickets.p, 0, c->ws.tickets * sizeof(unsigned int), c->s));
   c->scal.alloc(kSlotCount);
   MG_CUDA(cudaMemsetAsync(c->scal.p, 0, kSlotCount * sizeof(double), c->s));
   c->ws.partials = c->partials.p;
@@ -792,6 +1052,7 @@ void mg_default_params(mg_params *p) {
   p->coarsest_max_iter = 20000;
   p->precision = MG_FP64;
   p->seed = 20070704ULL;
+  p->max_rhs = 1;
 }
 
 const char *mg_last_error(void) { return t_last_error.c_str(); }
@@ -851,6 +1112,66 @@ int mg_solve(mg_ctx *c, const void *chi, void *psi, double tol, mg_stats *st) {
   });
   if (rc == MG_OK && status != MG_OK) {
     t_last_error = "not converged within max_iter";
+    return status;
+  }
+  return rc;
+}
+
+int mg_solve_batch(mg_ctx *c, int nrhs, const void *chi, void *psi, const double *mass, double tol, mg_stats *st) {
+  int status = MG_OK;
+  int rc = guarded([&] {
+    need_ctx(c);
+    need_ptr(chi);
+    need_ptr(psi);
+    if (nrhs < 1 || nrhs > c->p.max_rhs) fail(MG_ERR_INVALID_ARG, "nrhs must be in [1, max_rhs]");
+    check_fresh(*c);
+    std::vector<double> sh(nrhs, 0.0);
+    for (int v = 0; v < nrhs; ++v) {
+      if (mass != nullptr) sh[v] = mass[v] - c->m;
+      if (!std::isfinite(sh[v])) fail(MG_ERR_INVALID_ARG, "mass must be finite");
+    }
+    prepare_slots(*c, nrhs, sh.data());
+    MG_CUDA(cudaMemcpyAsync(c->shift_dev.p, sh.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, c->s));
+    for (long long &a : c->apps) a = 0;
+    collect_coarsest(*c);
+    c->coarsest_iters = 0;
+    cudaEvent_t e0, e1;
+    MG_CUDA(cudaEventCreate(&e0));
+    MG_CUDA(cudaEventCreate(&e1));
+    MG_CUDA(cudaEventRecord(e0, c->s));
+    std::vector<GcrOut> o;
+    c->cur_shift = c->shift_dev.p;
+    try {
+      outer_fgcr_batch(*c, nrhs, static_cast<const Cx<double> *>(chi), static_cast<Cx<double> *>(psi), tol, o);
+    } catch (...) {
+      c->cur_shift = nullptr;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      throw;
+    }
+    c->cur_shift = nullptr;
+    MG_CUDA(cudaEventRecord(e1, c->s));
+    MG_CUDA(cudaEventSynchronize(e1));
+    c->coarsest_iters = collect_coarsest(*c);
+    if (!c->use_lu) c->apps[c->p.levels - 1] += c->coarsest_iters;
+    float ms = 0.f;
+    MG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int v = 0; v < nrhs; ++v) {
+      if (!o[v].converged) status = MG_ERR_NOT_CONVERGED;
+      if (!st) continue;
+      st[v].iters = o[v].iters;
+      st[v].converged = o[v].converged ? 1 : 0;
+      st[v].true_rel_residual = o[v].rel;
+      for (int l = 0; l < MG_MAX_LEVELS; ++l) st[v].level_apps[l] = c->apps[l];
+      st[v].coarsest_iters = c->coarsest_iters;
+      st[v].ms = ms;
+      st[v].graphs = (c->graphs_ok && c->preb[c->p.precision == MG_FP32 ? 1 : 0][nrhs].exec != nullptr) ? 1 : 0;
+    }
+  });
+  if (rc == MG_OK && status != MG_OK) {
+    t_last_error = "a right-hand side did not converge within max_iter";
     return status;
   }
   return rc;

@@ -15,12 +15,19 @@
 
 namespace mg {
 
+// alpha = omega <A r, r> / |A r|^2 from the FP64 sums, formed once per block by thread 0
+// and broadcast through shared memory (an FP64 division per thread would cost GB300's
+// slow FP64 unit more than the rest of these kernels); every thread must call it
 template <typename R>
 __device__ __forceinline__ Cx<R> mr_alpha(const double *sc, double omega) {
-  const double den = sc[2];
-  const double ar = den > 0.0 ? omega * sc[0] / den : 0.0;
-  const double ai = den > 0.0 ? omega * sc[1] / den : 0.0;
-  return mk((R)ar, (R)ai);
+  __shared__ R s_alpha[2];
+  if (threadIdx.x == 0) {
+    const double den = sc[2];
+    s_alpha[0] = (R)(den > 0.0 ? omega * sc[0] / den : 0.0);
+    s_alpha[1] = (R)(den > 0.0 ? omega * sc[1] / den : 0.0);
+  }
+  __syncthreads();
+  return mk(s_alpha[0], s_alpha[1]);
 }
 
 // value of the MR residual at a site: r (first iteration) or r - alpha A r
@@ -41,8 +48,9 @@ __global__ void __launch_bounds__(256) mr_wilson_kernel(const Cx<R> *__restrict_
                                                         const Cx<R> *Ar_old, const double *sc_old, double omega,
                                                         Cx<R> *x, int x_init, Cx<R> *r_new, Cx<R> *Ar_new, int L0,
                                                         int L1, R diag, double *partials, double *sc_new,
-                                                        unsigned int *ticket) {
+                                                        unsigned int *ticket, const double *shift) {
   __shared__ R sh[32 * 3];
+  if (shift != nullptr) diag += (R)shift[blockIdx.y];
   const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long V = (long long)L0 * L1;
   {  // vector blockIdx.y of the batch (stride 2 V); scalars, partials and ticket per vector
@@ -60,15 +68,13 @@ __global__ void __launch_bounds__(256) mr_wilson_kernel(const Cx<R> *__restrict_
     ticket += blockIdx.y;
   }
   R v[3] = {(R)0, (R)0, (R)0};
+  Cx<R> alpha = mk((R)0, (R)0);
+  if (STEP) alpha = mr_alpha<R>(sc_old, omega);  // all threads of the block
   if (s < V) {
     MrSrc<R, STEP> src;
     src.r = r_old;
     src.Ar = Ar_old;
-    Cx<R> alpha = mk((R)0, (R)0);
-    if (STEP) {
-      alpha = mr_alpha<R>(sc_old, omega);
-      src.malpha = mk(-alpha.re, -alpha.im);
-    }
+    if (STEP) src.malpha = mk(-alpha.re, -alpha.im);
     const int x1 = (int)(s / L0), x0 = (int)(s - (long long)x1 * L0);
     const long long row = (long long)x1 * L0;
     const long long xp0 = row + (x0 + 1 == L0 ? 0 : x0 + 1);
@@ -116,7 +122,7 @@ __global__ void __launch_bounds__(256) mr_stencil_kernel(const Cx<R> *__restrict
                                                          const Cx<R> *Ar_old, const double *sc_old, double omega,
                                                          Cx<R> *x, int x_init, Cx<R> *r_new, Cx<R> *Ar_new, int L0,
                                                          int L1, int Nrt, double *partials, double *sc_new,
-                                                         unsigned int *ticket) {
+                                                         unsigned int *ticket, const double *shift) {
   __shared__ R sh[32 * 3];
   const int N = NT > 0 ? NT : Nrt;
   {
@@ -137,15 +143,13 @@ __global__ void __launch_bounds__(256) mr_stencil_kernel(const Cx<R> *__restrict
   const long long j = t / N;
   const int row = (int)(t - j * N);
   R v[3] = {(R)0, (R)0, (R)0};
+  Cx<R> alpha = mk((R)0, (R)0);
+  if (STEP) alpha = mr_alpha<R>(sc_old, omega);  // all threads of the block
   if (j < (long long)L0 * L1) {
     MrSrc<R, STEP> src;
     src.r = r_old;
     src.Ar = Ar_old;
-    Cx<R> alpha = mk((R)0, (R)0);
-    if (STEP) {
-      alpha = mr_alpha<R>(sc_old, omega);
-      src.malpha = mk(-alpha.re, -alpha.im);
-    }
+    if (STEP) src.malpha = mk(-alpha.re, -alpha.im);
     const int x1 = (int)(j / L0), x0 = (int)(j - (long long)x1 * L0);
     const long long rowo = (long long)x1 * L0;
     long long nb[5];
@@ -169,6 +173,11 @@ __global__ void __launch_bounds__(256) mr_stencil_kernel(const Cx<R> *__restrict
 #pragma unroll(NT > 0 ? NT : 1)
       for (int col = 0; col < N; ++col) cmac(acc, Yd[(long long)col * N], src.at(base + col));
     }
+    if (shift != nullptr) {  // self block + shift * identity for this vector
+      const R sv = (R)shift[blockIdx.y];
+      acc.re = fma(sv, self.re, acc.re);
+      acc.im = fma(sv, self.im, acc.im);
+    }
     Ar_new[t] = acc;
     v[0] = acc.re * self.re + acc.im * self.im;
     v[1] = acc.re * self.im - acc.im * self.re;
@@ -177,17 +186,111 @@ __global__ void __launch_bounds__(256) mr_stencil_kernel(const Cx<R> *__restrict
   grid_finish_t<3, R>(v, partials, sc_new, ticket, sh);
 }
 
-// x (+)= alpha r for the last MR iteration
+// ---- coarse stencil level with N = 8: four threads per (site, row), a warp per site ----
+// Thread q of a row takes 10 of the 40 (direction, column) terms; the four partial rows
+// are combined by shuffles. Four times the threads of the one-thread-per-row form and
+// short FMA chains: these levels are small and latency-bound.
 template <typename R>
-__global__ void mr_last_kernel(const Cx<R> *__restrict__ r_old, const double *__restrict__ sc_old, double omega,
-                               Cx<R> *__restrict__ x, int x_init, long long n) {
+__device__ __forceinline__ long long nbr_of(int dir, long long j, long long xp0, long long xm0, long long xp1,
+                                            long long xm1) {
+  return dir == 0 ? j : dir == 1 ? xp0 : dir == 2 ? xm0 : dir == 3 ? xp1 : xm1;
+}
+
+template <typename R, bool STEP>
+__global__ void __launch_bounds__(256) mr_stencil8_kernel(const Cx<R> *__restrict__ Y, const Cx<R> *r_old,
+                                                          const Cx<R> *Ar_old, const double *sc_old, double omega,
+                                                          Cx<R> *x, int x_init, Cx<R> *r_new, Cx<R> *Ar_new, int L0,
+                                                          int L1, double *partials, double *sc_new,
+                                                          unsigned int *ticket, const double *shift) {
+  __shared__ R sh[32 * 3];
+  {
+    const long long off = blockIdx.y * (long long)L0 * L1 * 8;
+    r_old += off;
+    if (STEP) {
+      Ar_old += off;
+      sc_old += 4 * blockIdx.y;
+      x += off;
+      r_new += off;
+    }
+    Ar_new += off;
+    sc_new += 4 * blockIdx.y;
+    partials += 3LL * gridDim.x * blockIdx.y;
+    ticket += blockIdx.y;
+  }
+  const long long j = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int row = (threadIdx.x >> 2) & 7, q = threadIdx.x & 3;
+  R v[3] = {(R)0, (R)0, (R)0};
+  Cx<R> alpha = mk((R)0, (R)0);
+  if (STEP) alpha = mr_alpha<R>(sc_old, omega);  // all threads of the block
+  if (j < (long long)L0 * L1) {  // uniform over the warp
+    MrSrc<R, STEP> src;
+    src.r = r_old;
+    src.Ar = Ar_old;
+    if (STEP) src.malpha = mk(-alpha.re, -alpha.im);
+    const int x1 = (int)(j / L0), x0 = (int)(j - (long long)x1 * L0);
+    const long long rowo = (long long)x1 * L0;
+    const long long xp0 = rowo + (x0 + 1 == L0 ? 0 : x0 + 1);
+    const long long xm0 = rowo + (x0 == 0 ? L0 - 1 : x0 - 1);
+    const long long xp1 = (x1 + 1 == L1 ? 0 : rowo + L0) + x0;
+    const long long xm1 = (x1 == 0 ? (long long)(L1 - 1) * L0 : rowo - L0) + x0;
+    Cx<R> acc = mk((R)0, (R)0);
+#pragma unroll
+    for (int u = 0; u < 10; ++u) {
+      const int term = q * 10 + u, dir = term >> 3, col = term & 7;
+      const long long nbj = nbr_of<R>(dir, j, xp0, xm0, xp1, xm1);
+      cmac(acc, Y[(j * 5 + dir) * 64 + col * 8 + row], src.at(nbj * 8 + col));
+    }
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+      acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
+      acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
+    }
+    if (q == 0) {
+      const long long i = j * 8 + row;
+      const Cx<R> self = src.at(i);
+      if (STEP) {
+        Cx<R> xv = x_init ? mk((R)0, (R)0) : x[i];
+        cmac(xv, alpha, r_old[i]);
+        x[i] = xv;
+        r_new[i] = self;
+      }
+      if (shift != nullptr) {
+        const R sv = (R)shift[blockIdx.y];
+        acc.re = fma(sv, self.re, acc.re);
+        acc.im = fma(sv, self.im, acc.im);
+      }
+      Ar_new[i] = acc;
+      v[0] = acc.re * self.re + acc.im * self.im;
+      v[1] = acc.re * self.im - acc.im * self.re;
+      v[2] = acc.re * acc.re + acc.im * acc.im;
+    }
+  }
+  grid_finish_t<3, R>(v, partials, sc_new, ticket, sh);
+}
+
+// x (+)= alpha r for the last MR iteration; with r_out, also the final residual
+// r_out = r_old - alpha A r_old (= b - A x; r_out may be r_old)
+template <typename R>
+__global__ void mr_last_kernel(const Cx<R> *r_old, const Cx<R> *__restrict__ Ar_old, const double *__restrict__ sc_old,
+                               double omega, Cx<R> *__restrict__ x, int x_init, Cx<R> *r_out, long long n) {
   r_old += blockIdx.y * n;
   x += blockIdx.y * n;
   const Cx<R> alpha = mr_alpha<R>(sc_old + 4 * blockIdx.y, omega);
+  const Cx<R> malpha = mk(-alpha.re, -alpha.im);
+  if (r_out != nullptr) {
+    Ar_old += blockIdx.y * n;
+    r_out += blockIdx.y * n;
+  }
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const Cx<R> ri = r_old[i];
     Cx<R> xv = x_init ? mk((R)0, (R)0) : x[i];
-    cmac(xv, alpha, r_old[i]);
+    cmac(xv, alpha, ri);
     x[i] = xv;
+    if (r_out != nullptr) {
+      Cx<R> rn = ri;
+      cmac(rn, malpha, Ar_old[i]);
+      r_out[i] = rn;
+    }
   }
 }
 
@@ -204,23 +307,30 @@ void launch_mr_iteration(const OpDesc<R> &op, bool step, const Cx<R> *r_old, con
     if (step)
       mr_wilson_kernel<R, true><<<grid, threads, 0, s>>>(op.U, r_old, Ar_old, sc_old, omega, x, x_init ? 1 : 0, r_new,
                                                          Ar_new, op.geo.L0, op.geo.L1, (R)op.diag, ws.partials,
-                                                         sc_new, ws.ticket);
+                                                         sc_new, ws.ticket, op.shift);
     else
       mr_wilson_kernel<R, false><<<grid, threads, 0, s>>>(op.U, r_old, Ar_old, sc_old, omega, x, 0, r_new, Ar_new,
                                                           op.geo.L0, op.geo.L1, (R)op.diag, ws.partials, sc_new,
-                                                          ws.ticket);
+                                                          ws.ticket, op.shift);
+  } else if (op.N == 8) {
+    const dim3 grid(grid_for(op.geo.nsites * 32, threads), nvec);
+    if ((long long)grid.x * 3 * nvec > ws.capacity) fail(MG_ERR_STATE, "MR reduction workspace too small");
+    if (step)
+      mr_stencil8_kernel<R, true><<<grid, threads, 0, s>>>(op.Y, r_old, Ar_old, sc_old, omega, x, x_init ? 1 : 0,
+                                                           r_new, Ar_new, op.geo.L0, op.geo.L1, ws.partials, sc_new,
+                                                           ws.ticket, op.shift);
+    else
+      mr_stencil8_kernel<R, false><<<grid, threads, 0, s>>>(op.Y, r_old, Ar_old, sc_old, omega, x, 0, r_new, Ar_new,
+                                                            op.geo.L0, op.geo.L1, ws.partials, sc_new, ws.ticket,
+                                                            op.shift);
   } else {
     const dim3 grid(grid_for(op.geo.nsites * op.N, threads), nvec);
     if ((long long)grid.x * 3 * nvec > ws.capacity) fail(MG_ERR_STATE, "MR reduction workspace too small");
 #define MG_MR_STENCIL(STEPV, NTV)                                                                                    \
   mr_stencil_kernel<R, STEPV, NTV><<<grid, threads, 0, s>>>(op.Y, r_old, Ar_old, sc_old, omega, x, x_init ? 1 : 0,   \
                                                             r_new, Ar_new, op.geo.L0, op.geo.L1, op.N, ws.partials, \
-                                                            sc_new, ws.ticket)
-    if (op.N == 8) {
-      if (step) MG_MR_STENCIL(true, 8); else MG_MR_STENCIL(false, 8);
-    } else {
-      if (step) MG_MR_STENCIL(true, 0); else MG_MR_STENCIL(false, 0);
-    }
+                                                            sc_new, ws.ticket, op.shift)
+    if (step) MG_MR_STENCIL(true, 0); else MG_MR_STENCIL(false, 0);
 #undef MG_MR_STENCIL
   }
   MG_LAUNCHED();
@@ -228,11 +338,11 @@ void launch_mr_iteration(const OpDesc<R> &op, bool step, const Cx<R> *r_old, con
 
 template <typename R>
 void launch_mr_last(const Cx<R> *r_old, const double *sc_old, double omega, Cx<R> *x, bool x_init, long long n,
-                    cudaStream_t s, int nvec) {
+                    cudaStream_t s, int nvec, const Cx<R> *Ar_old, Cx<R> *r_out) {
   long long b = (n + 255) / 256;
   if (b > 152LL * 16) b = 152LL * 16;
-  mr_last_kernel<R><<<dim3((unsigned int)(b < 1 ? 1 : b), nvec), 256, 0, s>>>(r_old, sc_old, omega, x,
-                                                                              x_init ? 1 : 0, n);
+  mr_last_kernel<R><<<dim3((unsigned int)(b < 1 ? 1 : b), nvec), 256, 0, s>>>(r_old, Ar_old, sc_old, omega, x,
+                                                                              x_init ? 1 : 0, r_out, n);
   MG_LAUNCHED();
 }
 
@@ -243,8 +353,8 @@ template void launch_mr_iteration<float>(const OpDesc<float> &, bool, const Cx<f
                                          const double *, double, Cx<float> *, bool, Cx<float> *, Cx<float> *,
                                          double *, const ReduceWs &, cudaStream_t, int);
 template void launch_mr_last<double>(const Cx<double> *, const double *, double, Cx<double> *, bool, long long,
-                                     cudaStream_t, int);
+                                     cudaStream_t, int, const Cx<double> *, Cx<double> *);
 template void launch_mr_last<float>(const Cx<float> *, const double *, double, Cx<float> *, bool, long long,
-                                    cudaStream_t, int);
+                                    cudaStream_t, int, const Cx<float> *, Cx<float> *);
 
 }  // namespace mg

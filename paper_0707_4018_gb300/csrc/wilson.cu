@@ -15,8 +15,11 @@ namespace mg {
 template <typename R>
 __global__ void __launch_bounds__(256) dslash_kernel(const Cx<R> *__restrict__ U, const Cx<R> *__restrict__ in,
                                                      Cx<R> *__restrict__ out, int L0, int L1, R diag,
-                                                     const Cx<R> *__restrict__ b, R a, R c, long long ldv) {
-  // vector blockIdx.y of a batch stored with stride ldv (the links are shared)
+                                                     const Cx<R> *__restrict__ b, R a, R c, long long ldv,
+                                                     const double *__restrict__ shift) {
+  // vector blockIdx.y of a batch stored with stride ldv (the links are shared); its
+  // diagonal is diag + shift[blockIdx.y] when a shift array is given
+  if (shift != nullptr) diag += (R)shift[blockIdx.y];
   in += blockIdx.y * ldv;
   out += blockIdx.y * ldv;
   if (b != nullptr) b += blockIdx.y * ldv;
@@ -62,16 +65,18 @@ __global__ void __launch_bounds__(256) dslash_kernel(const Cx<R> *__restrict__ U
 
 template <typename R>
 void launch_dslash(const Cx<R> *U, const Cx<R> *in, Cx<R> *out, Geo2 g, double diag, const Cx<R> *b, double a,
-                   double c, cudaStream_t s, int nvec) {
+                   double c, cudaStream_t s, int nvec, const double *shift) {
   const int threads = 256;
   dslash_kernel<R><<<dim3(grid_for(g.nsites, threads), nvec), threads, 0, s>>>(U, in, out, g.L0, g.L1, (R)diag, b,
-                                                                              (R)a, (R)c, 2 * g.nsites);
+                                                                              (R)a, (R)c, 2 * g.nsites, shift);
   MG_LAUNCHED();
 }
 
 template void launch_dslash<double>(const Cx<double> *, const Cx<double> *, Cx<double> *, Geo2, double,
-                                    const Cx<double> *, double, double, cudaStream_t, int);
+                                    const Cx<double> *, double, double, cudaStream_t, int,
+                                    const double *);
 template void launch_dslash<float>(const Cx<float> *, const Cx<float> *, Cx<float> *, Geo2, double,
-                                   const Cx<float> *, double, double, cudaStream_t, int);
+                                   const Cx<float> *, double, double, cudaStream_t, int,
+                                   const double *);
 
 }  // namespace mg
