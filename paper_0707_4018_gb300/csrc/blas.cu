@@ -79,7 +79,7 @@ __global__ void mr_update_kernel(const double *__restrict__ sc, double omega, Cx
   }
 }
 
-// rows j < k: <W_j, w>; row k: <w, w>; row k + 1: <w, r>  (blockIdx.y = row)
+// rows j < k: <W_j, w>; row k: <w, w>; row k + 1: <w, r>; row k + 2: <r, r>  (blockIdx.y = row)
 __global__ void __launch_bounds__(kReduceThreads) gcr_dots_kernel(const Cx<double> *__restrict__ W,
                                                                   const Cx<double> *__restrict__ w,
                                                                   const Cx<double> *__restrict__ r, int k,
@@ -87,8 +87,8 @@ __global__ void __launch_bounds__(kReduceThreads) gcr_dots_kernel(const Cx<doubl
                                                                   unsigned int *ticket, int pstride) {
   __shared__ double sh[32 * 2];
   const int row = blockIdx.y;
-  const Cx<double> *a = row < k ? W + (long long)row * n : w;
-  const Cx<double> *b = row == k + 1 ? r : w;
+  const Cx<double> *a = row < k ? W + (long long)row * n : (row == k + 2 ? r : w);
+  const Cx<double> *b = row > k ? r : w;
   double v[2] = {0.0, 0.0};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const Cx<double> x = a[i], y = b[i];
@@ -126,7 +126,7 @@ __global__ void gcr_project_update_kernel(const Cx<double> *__restrict__ W, Cx<d
 
 void launch_gcr_dots(const Cx<double> *W, const Cx<double> *w, const Cx<double> *r, int k, long long n, double *out,
                      const ReduceWs &ws, cudaStream_t s) {
-  const int rows = k + 2;
+  const int rows = k + 3;
   if (rows > 128) fail(MG_ERR_UNSUPPORTED, "gcr_dots: too many basis vectors");
   int per = (int)(ws.capacity / (2 * rows));
   if (per > ws.max_blocks) per = ws.max_blocks;
@@ -173,17 +173,18 @@ __global__ void __launch_bounds__(kReduceThreads) norm2_batch_kernel(const Cx<do
   grid_finish<1>(v, partials + (long long)blockIdx.y * gridDim.x, out + blockIdx.y, ticket + blockIdx.y, sh);
 }
 
-// vector v = blockIdx.z, row = blockIdx.y: rows j < k <W_j, w>, row k |w|^2, row k + 1 <w, r>;
-// results at out[v * 2 (k + 2) + 2 row]
+// vector v = blockIdx.z, row = blockIdx.y: rows j < k <W_j, w>, row k |w|^2, row k + 1 <w, r>,
+// row k + 2 |r|^2; results at out[v * 2 (k + 3) + 2 row]
 __global__ void __launch_bounds__(kReduceThreads) gcr_dots_batch_kernel(const Cx<double> *__restrict__ W,
                                                                         const Cx<double> *__restrict__ r, int k,
                                                                         int nb, long long n, double *partials,
                                                                         double *out, unsigned int *ticket) {
   __shared__ double sh[32 * 2];
-  const int row = blockIdx.y, v = blockIdx.z, rows = k + 2;
+  const int row = blockIdx.y, v = blockIdx.z, rows = k + 3;
   const Cx<double> *w = W + ((long long)k * nb + v) * n;
-  const Cx<double> *a = row < k ? W + ((long long)row * nb + v) * n : w;
-  const Cx<double> *b = row == k + 1 ? r + (long long)v * n : w;
+  const Cx<double> *rv = r + (long long)v * n;
+  const Cx<double> *a = row < k ? W + ((long long)row * nb + v) * n : (row == k + 2 ? rv : w);
+  const Cx<double> *b = row > k ? rv : w;
   double acc[2] = {0.0, 0.0};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const Cx<double> x = a[i], y = b[i];
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(kReduceThreads) gcr_dots_batch_kernel(const Cx
 
 // per vector v (blockIdx.y), coef[4 v .. 4 v + 3] = (inv, alpha re, alpha im, mode):
 // mode 0 leaves the vector alone; mode 2 projects w_k, z_k against the basis with beta_j =
-// dots[v * 2 (k + 2) + 2 j]; mode 1 projects, scales both by inv and updates x += alpha z_k,
+// dots[v * 2 (k + 3) + 2 j]; mode 1 projects, scales both by inv and updates x += alpha z_k,
 // r -= alpha w_k
 __global__ void gcr_update_batch_kernel(Cx<double> *__restrict__ W, Cx<double> *__restrict__ Z, int k, int nb,
                                         const double *__restrict__ dots, const double *__restrict__ coef,
@@ -204,7 +205,7 @@ __global__ void gcr_update_batch_kernel(Cx<double> *__restrict__ W, Cx<double> *
   const int v = blockIdx.y;
   const int mode = (int)coef[4 * v + 3];
   if (mode == 0) return;
-  const double *beta = dots + (long long)v * 2 * (k + 2);
+  const double *beta = dots + (long long)v * 2 * (k + 3);
   const double inv = mode == 1 ? coef[4 * v] : 1.0;
   const Cx<double> alpha = mk(coef[4 * v + 1], coef[4 * v + 2]);
   Cx<double> *Wk = W + ((long long)k * nb + v) * n, *Zk = Z + ((long long)k * nb + v) * n;
@@ -246,7 +247,7 @@ void launch_norm2_batch(const Cx<double> *a, long long n, int nb, double *out, c
 
 void launch_gcr_dots_batch(const Cx<double> *W, const Cx<double> *r, int k, int nb, long long n, double *out,
                            const ReduceWs &ws, cudaStream_t s) {
-  const int rows = k + 2;
+  const int rows = k + 3;
   if ((long long)rows * nb > ws.tickets) fail(MG_ERR_UNSUPPORTED, "gcr_dots_batch: too many reductions");
   int per = (int)(ws.capacity / (2LL * rows * nb));
   if (per > ws.max_blocks) per = ws.max_blocks;

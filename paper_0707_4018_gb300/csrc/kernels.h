@@ -22,21 +22,23 @@ struct OpDesc {
 };
 
 // ---- fused MR smoothing (one launch per iteration) ----
-// step = false: Ar_new = A r_old and sc_new = (<Ar_new, r_old>, |Ar_new|^2).
-// step = true: alpha = omega <Ar_old, r_old>/|Ar_old|^2 from sc_old; x (+)= alpha r_old
-// (x_init: x = alpha r_old); r_new = r_old - alpha Ar_old; Ar_new = A r_new; sc_new as above.
-// r_new / Ar_new must differ from r_old / Ar_old, sc_new from sc_old.
-// Batched over nvec vectors stored with stride n (the level's dofs); vector v uses the
-// scalars sc[4 v .. 4 v + 2].
+// step = false: Ar_new = A r_old; the launch's block partials of (<Ar_new, r_old>, |Ar_new|^2)
+// go to part_out. step = true: alpha = omega <Ar_old, r_old>/|Ar_old|^2 from part_in (the
+// previous launch's partials); x (+)= alpha r_old (x_init: x = alpha r_old);
+// r_new = r_old - alpha Ar_old; Ar_new = A r_new; partials to part_out. r_new / Ar_new /
+// part_out must differ from r_old / Ar_old / part_in. Batched over nvec vectors stored with
+// stride n (the level's dofs); part_capacity: entries of type R in each partials buffer.
 template <typename R>
-void launch_mr_iteration(const OpDesc<R> &op, bool step, const Cx<R> *r_old, const Cx<R> *Ar_old, const double *sc_old,
-                         double omega, Cx<R> *x, bool x_init, Cx<R> *r_new, Cx<R> *Ar_new, double *sc_new,
-                         const ReduceWs &ws, cudaStream_t s, int nvec = 1);
-// x (+)= alpha r_old, alpha from sc_old (the last MR update); with r_out, also the final
-// residual r_out = r_old - alpha Ar_old (r_out may equal r_old)
+int mr_grid(const OpDesc<R> &op);  // blocks of one MR launch per vector
 template <typename R>
-void launch_mr_last(const Cx<R> *r_old, const double *sc_old, double omega, Cx<R> *x, bool x_init, long long n,
-                    cudaStream_t s, int nvec = 1, const Cx<R> *Ar_old = nullptr, Cx<R> *r_out = nullptr);
+void launch_mr_iteration(const OpDesc<R> &op, bool step, const Cx<R> *r_old, const Cx<R> *Ar_old, const R *part_in,
+                         double omega, Cx<R> *x, bool x_init, Cx<R> *r_new, Cx<R> *Ar_new, R *part_out,
+                         long long part_capacity, cudaStream_t s, int nvec = 1);
+// x (+)= alpha r_old with alpha from part_in (the last MR launch on `op`); with r_out, also
+// the final residual r_out = r_old - alpha Ar_old (r_out may equal r_old)
+template <typename R>
+void launch_mr_last(const OpDesc<R> &op, const Cx<R> *r_old, const Cx<R> *Ar_old, const R *part_in, double omega,
+                    Cx<R> *x, bool x_init, Cx<R> *r_out, long long n, cudaStream_t s, int nvec = 1);
 
 // ---- fine Wilson operator (2d, U(1), gamma_1 = sigma_1, gamma_2 = sigma_2) ----
 // out = a * D in + c * b   (b may be null when c == 0); D has diagonal `diag` = d + m,
@@ -74,7 +76,8 @@ template <typename R>
 void launch_mr_update(const double *sc, double omega, Cx<R> *x, Cx<R> *r, const Cx<R> *Ar, long long n,
                       cudaStream_t s);
 
-// outer GCR, FP64: out[2j..2j+1] = <W_j, w> (j < k), out[2k] = |w|^2, out[2k+2..2k+3] = <w, r>
+// outer GCR, FP64: out[2j..2j+1] = <W_j, w> (j < k), out[2k] = |w|^2, out[2k+2..2k+3] = <w, r>,
+// out[2k+4] = |r|^2
 void launch_gcr_dots(const Cx<double> *W, const Cx<double> *w, const Cx<double> *r, int k, long long n, double *out,
                      const ReduceWs &ws, cudaStream_t s);
 // w = (w - sum beta_j W_j) inv and z likewise (written to Wk / Zk); then, if update_xr,
@@ -88,7 +91,7 @@ void launch_gcr_project_update(const Cx<double> *W, Cx<double> *Wk, const Cx<dou
 void launch_copy_masked(const Cx<double> *x, Cx<double> *y, long long n, int nb, unsigned int mask, cudaStream_t s);
 // out[v] = |a_v|^2
 void launch_norm2_batch(const Cx<double> *a, long long n, int nb, double *out, const ReduceWs &ws, cudaStream_t s);
-// out[v * 2 (k + 2) + 2 j] = <W_j,v, W_k,v> (j < k), then |W_k,v|^2 and <W_k,v, r_v>
+// out[v * 2 (k + 3) + 2 j] = <W_j,v, W_k,v> (j < k), then |W_k,v|^2, <W_k,v, r_v> and |r_v|^2
 void launch_gcr_dots_batch(const Cx<double> *W, const Cx<double> *r, int k, int nb, long long n, double *out,
                            const ReduceWs &ws, cudaStream_t s);
 // per vector, coef[4 v .. 4 v + 3] = (inv, alpha, mode): mode 0 skip, 2 project W_k / Z_k

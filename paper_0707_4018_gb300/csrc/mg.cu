@@ -55,9 +55,8 @@ struct Level {
 
 // scalar slots on the device (FP64)
 enum : int {
-  kSlotMR = 0,          // per level: two alternating MR reductions of 4 doubles per batched vector
-  kSlotOuter = 1024,    // outer GCR reductions: 2 (restart + 2) doubles
-  kSlotCount = 2048
+  kSlotOuter = 0,   // outer GCR reductions: 2 (restart + 3) doubles
+  kSlotCount = 512
 };
 constexpr int kMaxBatch = 32;  // vectors per batched V-cycle (the setup batches the Nv near-null vectors)
 
@@ -121,6 +120,7 @@ struct mg_ctx {
   mg::DevBuf<mg::Cx<float>> z32;
   // reductions and scalars
   mg::DevBuf<double> partials, scal;
+  mg::DevBuf<double> mrpart[2];  // MR block partials (alternating), reused as float in FP32 cycles
   mg::DevBuf<unsigned int> tickets;
   mg::ReduceWs ws{};
   double *host = nullptr;  // pinned scalars
@@ -216,26 +216,28 @@ static void smooth(mg_ctx &c, int l, const Cx<R> *b, Cx<R> *x, int nu, bool accu
     if (r_out != nullptr && r_out != b) launch_copy<R>(b, r_out, L.n * nvec, c.s);
     return;
   }
-  double *sc[2] = {c.scal.p + kSlotMR + 8 * kMaxBatch * l, c.scal.p + kSlotMR + 8 * kMaxBatch * l + 4 * kMaxBatch};
+  // two alternating partials buffers in the vectors' precision
+  R *part[2] = {reinterpret_cast<R *>(c.mrpart[0].p), reinterpret_cast<R *>(c.mrpart[1].p)};
+  const long long cap = (long long)(c.mrpart[0].n * sizeof(double) / sizeof(R));
   const OpDesc<R> op = op_of<R>(c, l);
   Cx<R> *rbuf[2] = {w.r.p, w.r2.p};
   Cx<R> *Arbuf[2] = {w.Ar.p, w.Ar2.p};
-  launch_mr_iteration<R>(op, false, b, nullptr, nullptr, c.p.omega, nullptr, false, nullptr, Arbuf[0], sc[0], c.ws,
+  launch_mr_iteration<R>(op, false, b, nullptr, nullptr, c.p.omega, nullptr, false, nullptr, Arbuf[0], part[0], cap,
                          c.s, nvec);
   c.apps[l] += nvec;
   const Cx<R> *r_old = b;
-  int rsel = (b == rbuf[0]) ? 1 : 0, asel = 1, ssel = 1;
+  int rsel = (b == rbuf[0]) ? 1 : 0, asel = 1, psel = 1;
   for (int i = 1; i < nu; ++i) {
-    launch_mr_iteration<R>(op, true, r_old, Arbuf[asel ^ 1], sc[ssel ^ 1], c.p.omega, x, i == 1 && !accumulate,
-                           rbuf[rsel], Arbuf[asel], sc[ssel], c.ws, c.s, nvec);
+    launch_mr_iteration<R>(op, true, r_old, Arbuf[asel ^ 1], part[psel ^ 1], c.p.omega, x, i == 1 && !accumulate,
+                           rbuf[rsel], Arbuf[asel], part[psel], cap, c.s, nvec);
     c.apps[l] += nvec;
     r_old = rbuf[rsel];
     rsel ^= 1;
     asel ^= 1;
-    ssel ^= 1;
+    psel ^= 1;
   }
-  launch_mr_last<R>(r_old, sc[ssel ^ 1], c.p.omega, x, nu == 1 && !accumulate, L.n, c.s, nvec, Arbuf[asel ^ 1],
-                    r_out);
+  launch_mr_last<R>(op, r_old, Arbuf[asel ^ 1], part[psel ^ 1], c.p.omega, x, nu == 1 && !accumulate, r_out, L.n,
+                    c.s, nvec);
 }
 
 static void precondition(mg_ctx &c, const Cx<double> *r, Cx<double> *z);
@@ -247,18 +249,19 @@ struct GcrOut {
 };
 
 // Outer flexible GCR on D (FP64) with the V-cycle as right preconditioner.
-// Per iteration: z = V r, w = D z, one fused reduction of <W_j, w>, |w|^2, <w, r>;
+// Per iteration: z = V r, w = D z, one fused reduction of <W_j, w>, |w|^2, <w, r>, |r|^2;
 // the host forms the classical Gram-Schmidt coefficients, the Pythagorean norm
 // |w - W beta|^2 = |w|^2 - |beta|^2 and alpha = <w_hat, r>, and runs a second
 // projection only when that norm shows cancellation (< half of |w|^2); then one
-// fused kernel projects, normalises and updates x and r. The residual norm is
-// tracked as |r|^2 - |alpha|^2 and the true residual b - D x is recomputed at
-// every restart (defect correction).
+// fused kernel projects, normalises and updates x and r. The new residual norm is
+// |r|^2 - |alpha|^2 with |r|^2 freshly reduced (a running |b|^2 - sum |alpha|^2
+// cannot resolve residuals below about sqrt(eps) |b| = 1e-8 |b|), and the true
+// residual b - D x is recomputed at every restart (defect correction).
 static GcrOut outer_fgcr(mg_ctx &c, const Cx<double> *b, Cx<double> *x, double tol, int restart, int max_iter) {
   Level &F = c.lv[0];
   const long long n = F.n;
   Cx<double> *Z = c.oZ.p, *W = c.oW.p, *r = c.orr.p;
-  double *dots = c.scal.p + kSlotOuter;  // 2 (k + 2) doubles
+  double *dots = c.scal.p + kSlotOuter;  // 2 (k + 3) doubles
   double *h = c.host;
   GcrOut out;
   auto fetch = [&](int count) {
@@ -284,7 +287,8 @@ static GcrOut outer_fgcr(mg_ctx &c, const Cx<double> *b, Cx<double> *x, double t
       precondition(c, r, z);
       apply_op<double>(c, 0, z, w);
       launch_gcr_dots(W, w, r, k, n, dots, c.ws, c.s);
-      fetch(2 * (k + 2));
+      fetch(2 * (k + 3));
+      const double rr = h[2 * k + 4];  // |r|^2 before this update
       double nw0 = h[2 * k], nw2 = nw0;
       for (int j = 0; j < k; ++j) nw2 -= h[2 * j] * h[2 * j] + h[2 * j + 1] * h[2 * j + 1];
       double wr = h[2 * k + 2], wi = h[2 * k + 3];
@@ -292,7 +296,7 @@ static GcrOut outer_fgcr(mg_ctx &c, const Cx<double> *b, Cx<double> *x, double t
         // cancellation: project once, then take fresh coefficients for a second projection
         launch_gcr_project_update(W, w, Z, z, k, dots, 1.0, 0.0, 0.0, x, r, n, false, c.s);
         launch_gcr_dots(W, w, r, k, n, dots, c.ws, c.s);
-        fetch(2 * (k + 2));
+        fetch(2 * (k + 3));
         nw0 = h[2 * k];
         nw2 = nw0;
         for (int j = 0; j < k; ++j) nw2 -= h[2 * j] * h[2 * j] + h[2 * j + 1] * h[2 * j + 1];
@@ -303,7 +307,7 @@ static GcrOut outer_fgcr(mg_ctx &c, const Cx<double> *b, Cx<double> *x, double t
       const double inv = 1.0 / std::sqrt(nw2);
       const double are = wr * inv, aim = wi * inv;
       launch_gcr_project_update(W, w, Z, z, k, dots, inv, are, aim, x, r, n, true, c.s);
-      rn2 = std::max(rn2 - (are * are + aim * aim), 0.0);
+      rn2 = std::max(rr - (are * are + aim * aim), 0.0);
       ++out.iters;
       rel = std::sqrt(rn2 / bn2);
       if (rel <= tol) {
@@ -563,7 +567,7 @@ static void outer_fgcr_batch(mg_ctx &c, int nb, const Cx<double> *b, Cx<double> 
   const int restart = c.p.gcr_restart;
   Cx<double> *Z = c.bZ.p, *W = c.bW.p, *r = c.br.p;
   double *h = c.bhost;
-  double *hcoef = c.bhost + (size_t)c.p.max_rhs * 2 * (restart + 2);
+  double *hcoef = c.bhost + (size_t)c.p.max_rhs * 2 * (restart + 3);
   out.assign(nb, GcrOut{});
   auto fetch = [&](const double *dev, int count) {
     MG_CUDA(cudaMemcpyAsync(h, dev, count * sizeof(double), cudaMemcpyDeviceToHost, c.s));
@@ -585,7 +589,7 @@ static void outer_fgcr_batch(mg_ctx &c, int nb, const Cx<double> *b, Cx<double> 
   }
   const unsigned int all = nb == 32 ? 0xffffffffu : (1u << nb) - 1u;
   int iters = 0;
-  std::vector<double> nw0(nb), nw2(nb), wr(nb), wi(nb);
+  std::vector<double> nw0(nb), nw2(nb), wr(nb), wi(nb), rr(nb);
   while (done != all && iters < c.p.max_iter) {
     unsigned int act = all & ~done;
     int k = 0;
@@ -594,11 +598,12 @@ static void outer_fgcr_batch(mg_ctx &c, int nb, const Cx<double> *b, Cx<double> 
       precondition_batch(c, nb, r, act, Zk);
       apply_op<double>(c, 0, Zk, Wk, nullptr, 1.0, 0.0, nb);
       launch_gcr_dots_batch(W, r, k, nb, n, c.bdots.p, c.ws, c.s);
-      const int stride = 2 * (k + 2);
+      const int stride = 2 * (k + 3);
       fetch(c.bdots.p, nb * stride);
       unsigned int cancel = 0u;
       for (int v = 0; v < nb; ++v) {
         const double *hv = h + v * stride;
+        rr[v] = hv[2 * k + 4];  // |r_v|^2 before this update
         nw0[v] = hv[2 * k];
         nw2[v] = nw0[v];
         for (int j = 0; j < k; ++j) nw2[v] -= hv[2 * j] * hv[2 * j] + hv[2 * j + 1] * hv[2 * j + 1];
@@ -640,7 +645,7 @@ static void outer_fgcr_batch(mg_ctx &c, int nb, const Cx<double> *b, Cx<double> 
         hcoef[4 * v + 1] = are;
         hcoef[4 * v + 2] = aim;
         hcoef[4 * v + 3] = 1.0;
-        rn2[v] = std::max(rn2[v] - (are * are + aim * aim), 0.0);
+        rn2[v] = std::max(rr[v] - (are * are + aim * aim), 0.0);
         ++out[v].iters;
         if (std::sqrt(rn2[v] / bn2[v]) <= tol) act &= ~(1u << v);
       }
@@ -821,6 +826,34 @@ static void enter(mg_ctx &c) {
   MG_CUDA(cudaStreamWaitEvent(c.s, c.ev, 0));
 }
 
+// buffers of batched solves (allocated at setup when max_rhs > 1, else on the first
+// mg_solve_batch call, before any batched graph is captured)
+static void alloc_batch(mg_ctx &c) {
+  const Level &F = c.lv[0];
+  const Level &Cst = c.lv.back();
+  const bool f32 = c.p.precision == MG_FP32;
+  const size_t nr = (size_t)c.p.max_rhs;
+  const size_t m2 = (size_t)Cst.geo.nsites * Cst.nint * Cst.nint;
+  if (c.use_lu) {
+    c.bLU.resize(nr);
+    c.bipiv.resize(nr);
+  } else {
+    c.bMinv.alloc(nr * m2);
+    if (!c.cg_batch) c.bYt.alloc(nr * 5 * m2);
+  }
+  c.bZ.alloc((size_t)c.p.gcr_restart * nr * F.n);
+  c.bW.alloc((size_t)c.p.gcr_restart * nr * F.n);
+  c.br.alloc(nr * F.n);
+  c.brin.alloc(nr * F.n);
+  if (f32)
+    c.bz32.alloc(nr * F.n);
+  else
+    c.bz64.alloc(nr * F.n);
+  c.bdots.alloc(nr * 2 * (c.p.gcr_restart + 3));
+  c.bcoef.alloc(nr * 4);
+  MG_CUDA(cudaMallocHost(&c.bhost, (nr * 2 * (c.p.gcr_restart + 3) + nr * 4) * sizeof(double)));
+}
+
 static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_params *p, void *stream) {
   validate(g, p);
   auto c = std::make_unique<mg_ctx>();
@@ -938,28 +971,8 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
   c->slot_shift.assign(p->max_rhs, std::nan(""));
   c->preb[0].resize(p->max_rhs + 1);
   c->preb[1].resize(p->max_rhs + 1);
-  if (p->max_rhs > 1) {
-    const size_t nr = (size_t)p->max_rhs;
-    const size_t m2 = (size_t)Cst.geo.nsites * Cst.nint * Cst.nint;
-    if (c->use_lu) {
-      c->bLU.resize(nr);
-      c->bipiv.resize(nr);
-    } else {
-      c->bMinv.alloc(nr * m2);
-      if (!c->cg_batch) c->bYt.alloc(nr * 5 * m2);
-    }
-    c->bZ.alloc((size_t)p->gcr_restart * nr * F.n);
-    c->bW.alloc((size_t)p->gcr_restart * nr * F.n);
-    c->br.alloc(nr * F.n);
-    c->brin.alloc(nr * F.n);
-    if (f32)
-      c->bz32.alloc(nr * F.n);
-    else
-      c->bz64.alloc(nr * F.n);
-    c->bdots.alloc(nr * 2 * (p->gcr_restart + 2));
-    c->bcoef.alloc(nr * 4);
-    MG_CUDA(cudaMallocHost(&c->bhost, (nr * 2 * (p->gcr_restart + 2) + nr * 4) * sizeof(double)));
-  }
+  if (p->max_rhs > 1) alloc_batch(*c);
+
   // outer
   c->z64.alloc(F.n);
   c->oZ.alloc((size_t)p->gcr_restart * F.n);
@@ -974,10 +987,12 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
     const long long units = l == 0 ? c->lv[l].geo.nsites : (c->lv[l].nint == 8 ? 4 : 1) * c->lv[l].n;
     cap = std::max(cap, 3 * ((units + 255) / 256) * c->nbatch);
   }
-  cap = std::max(cap, 2LL * (p->gcr_restart + 2) * p->max_rhs * 64);
+  cap = std::max(cap, 2LL * (p->gcr_restart + 3) * p->max_rhs * 64);
   c->partials.alloc((size_t)cap + 16);
   c->ws.capacity = cap;
-  c->ws.tickets = std::max(128, (p->gcr_restart + 2) * p->max_rhs);
+  c->mrpart[0].alloc((size_t)cap);
+  c->mrpart[1].alloc((size_t)cap);
+  c->ws.tickets = std::max(160, (p->gcr_restart + 3) * p->max_rhs);
   c->tickets.alloc((size_t)c->ws.tickets);
   MG_CUDA(cudaMemsetAsync(c->tickets.p, 0, c->ws.tickets * sizeof(unsigned int), c->s));
   c->scal.alloc(kSlotCount);
@@ -1125,6 +1140,7 @@ int mg_solve_batch(mg_ctx *c, int nrhs, const void *chi, void *psi, const double
     need_ptr(psi);
     if (nrhs < 1 || nrhs > c->p.max_rhs) fail(MG_ERR_INVALID_ARG, "nrhs must be in [1, max_rhs]");
     check_fresh(*c);
+    if (c->bZ.p == nullptr) alloc_batch(*c);
     std::vector<double> sh(nrhs, 0.0);
     for (int v = 0; v < nrhs; ++v) {
       if (mass != nullptr) sh[v] = mass[v] - c->m;
@@ -1177,11 +1193,23 @@ int mg_solve_batch(mg_ctx *c, int nrhs, const void *chi, void *psi, const double
   return rc;
 }
 
+// Captured V-cycles hold the fine diagonal d + m as a kernel argument: a new mass
+// needs new graphs (every buffer they touch is unchanged, the coarse operators are
+// rebuilt in place).
+static void drop_graphs(mg_ctx &c) {
+  for (auto &g : c.pre) g.reset();
+  for (auto &g : c.setup_vc) g.reset();
+  for (auto &v : c.preb)
+    for (auto &g : v) g.reset();
+}
+
 int mg_update_mass(mg_ctx *c, double m) {
   return guarded([&] {
     need_ctx(c);
     check_fresh(*c);
     c->m = m;
+    MG_CUDA(cudaStreamSynchronize(c->s));  // no replay of the old graphs is still in flight
+    drop_graphs(*c);
     for (int l = 0; l + 1 < c->p.levels; ++l) {
       Level &L = c->lv[l];
       if (l == 0)

@@ -100,7 +100,7 @@ def test_batch_of_one_and_default_mass():
     import torch
     U = _field()
     chi = _sources(1, seed=9)
-    ctx = _ctx(U, 0.1, 0, 2)
+    ctx = _ctx(U, 0.1, 0, 1)  # max_rhs 1: the batch buffers are made on the first batched call
     psi = torch.empty((1, DIMS[0] * DIMS[1], 2), dtype=torch.complex128, device="cuda")
     st = ctx.solve_batch(to_dev(chi), psi, 1e-13)
     assert st[0]["converged"]

@@ -217,6 +217,10 @@ def test_update_mass_matches_oracle():
     dims = (32, 32)
     U, _, _ = inputs.schwinger_links(32, 6.0, sweeps=100, workload_id=5)
     hier, ctx, _ = make_pair(dims, 0.0, [(4, 4), (2, 2)], [8, 8], U, coarsest_lu_max=4096)
+    # a cycle at the old mass first: its captured graph must not survive the mass change
+    b0 = inputs.gaussian_source(*dims, seed=8)
+    x0 = torch.empty((1024, 2), dtype=torch.complex128, device="cuda")
+    ctx.vcycle(to_dev(b0), x0)
     ctx.update_mass(0.31)
     setup.update_mass(hier, 0.31)
     for l in (1, 2):
