@@ -388,6 +388,23 @@ def run_only(case: str):
     U, _, _ = inputs.schwinger_links(L, beta, sweeps=2000, workload_id=WORKLOAD_ID)
     mc = mcrit_table()[f"w{WORKLOAD_ID}_L{L}_b{beta:g}"]["m_crit"]
     seed = inputs.workload_seed(WORKLOAD_ID, L, beta)
+    if case == "vcycle":
+        # the preconditioner alone: 5 warm-up cycles, then 20 replays of the captured graph
+        ctx = mg.Context.setup(torch.from_numpy(U).cuda(), mc + DMS[0], (L, L), mg_params(mg.MG_FP32))
+        r = torch.from_numpy(inputs.gaussian_source(L, L, seed=seed)).cuda()
+        z = torch.empty_like(r)
+        for _ in range(5):
+            ctx.vcycle(r, z)
+        torch.cuda.synchronize()
+        n0 = mg.mg_kernel_launches()
+        t0 = time.perf_counter()
+        for _ in range(20):
+            ctx.vcycle(r, z)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": case, "us_per_cycle_host_clock": (time.perf_counter() - t0) / 20 * 1e6,
+                          "launches_per_cycle": (mg.mg_kernel_launches() - n0) / 20}))
+        ctx.close()
+        return
     fd = dict(beta=beta, m_c=mc, U_dev=torch.from_numpy(U).cuda(),
               chi_dev=[torch.from_numpy(inputs.gaussian_source(L, L, seed=seed, index=i)).cuda() for i in range(3)],
               psi_dev=[torch.empty((L * L, 2), dtype=torch.complex128, device="cuda") for _ in DMS])
@@ -405,8 +422,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--only", default=None, choices=["dslash-f32", "dslash-f64", "solve"],
-                    help="profiling cases: the Dslash timing loop alone, or one beta's setup + 3 solves")
+    ap.add_argument("--only", default=None, choices=["dslash-f32", "dslash-f64", "solve", "vcycle"],
+                    help="profiling cases: the Dslash timing loop alone, one beta's setup + 3 solves, or "
+                         "25 mixed-precision V-cycles after one beta's setup")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("warmup must be >= 3")

@@ -12,14 +12,16 @@
 
 namespace mg {
 
-template <typename R>
-__global__ void __launch_bounds__(256) dslash_kernel(const Cx<R> *__restrict__ U, const Cx<R> *__restrict__ in,
+// FP32: at most 32 registers, so that 8 blocks of 256 threads fit an SM (this kernel is
+// HBM-bound and needs the memory parallelism of full occupancy)
+template <typename R, bool SHIFT>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 8 : 4) dslash_kernel(const Cx<R> *__restrict__ U, const Cx<R> *__restrict__ in,
                                                      Cx<R> *__restrict__ out, int L0, int L1, R diag,
                                                      const Cx<R> *__restrict__ b, R a, R c, long long ldv,
                                                      const double *__restrict__ shift) {
   // vector blockIdx.y of a batch stored with stride ldv (the links are shared); its
   // diagonal is diag + shift[blockIdx.y] when a shift array is given
-  if (shift != nullptr) diag += (R)shift[blockIdx.y];
+  if (SHIFT) diag += (R)shift[blockIdx.y];
   in += blockIdx.y * ldv;
   out += blockIdx.y * ldv;
   if (b != nullptr) b += blockIdx.y * ldv;
@@ -67,8 +69,12 @@ template <typename R>
 void launch_dslash(const Cx<R> *U, const Cx<R> *in, Cx<R> *out, Geo2 g, double diag, const Cx<R> *b, double a,
                    double c, cudaStream_t s, int nvec, const double *shift) {
   const int threads = 256;
-  dslash_kernel<R><<<dim3(grid_for(g.nsites, threads), nvec), threads, 0, s>>>(U, in, out, g.L0, g.L1, (R)diag, b,
-                                                                              (R)a, (R)c, 2 * g.nsites, shift);
+  const dim3 grid(grid_for(g.nsites, threads), nvec);
+  if (shift != nullptr)
+    dslash_kernel<R, true><<<grid, threads, 0, s>>>(U, in, out, g.L0, g.L1, (R)diag, b, (R)a, (R)c, 2 * g.nsites, shift);
+  else
+    dslash_kernel<R, false><<<grid, threads, 0, s>>>(U, in, out, g.L0, g.L1, (R)diag, b, (R)a, (R)c, 2 * g.nsites,
+                                                     nullptr);
   MG_LAUNCHED();
 }
 
