@@ -32,7 +32,7 @@ _LIB = os.path.join(_HERE, "libmginputs.so")
 _lock = threading.Lock()
 _lib = None
 
-# Root seed of every workload; each workload adds its own id (see DESIGN).
+# Root seed of every workload; each workload adds its own id (workload_seed mixes in L and beta).
 ROOT_SEED = 20070704
 
 

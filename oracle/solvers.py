@@ -6,7 +6,7 @@ Paper, the five V-cycle steps (section after Eq. Galerkin) and Eq. vcycle:
   3. coarse V-cycle:               e_c = V^(l+1) r_c   (exact solve on the coarsest level)
   4. coarse-grid correction:       x = x + P e_c
   5. relax on the final residual:  x = x + R (b - A x)
-Readings (see the design notes): steps 1 and 5 are additive corrections (the
+Reading of the printed cycle: steps 1 and 5 are additive corrections (the
 printed "x = R(b - Ax)" means x += R(b - Ax)), and the operator form then reads
 V = R + R^dagger - R A R^dagger + (1 - R A) P V_c P^dagger (1 - A R^dagger);
 the printed "+RAR^dagger" cannot hold for the five steps. The cost is 2 nu + 2
