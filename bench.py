@@ -126,30 +126,64 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _one_field(f, precision, stats_out, host_io, contexts):
+    """One beta: setup at the lightest mass and the three solves (update_mass between them)."""
+    import paper_0707_4018_gb300 as mg
+    if host_io is not None:
+        U = f["U_host"].to("cuda", non_blocking=True)
+    else:
+        U = f["U_dev"]
+    ctx = mg.Context.setup(U, f["m_c"] + DMS[0], (L, L), mg_params(precision))
+    contexts.append(ctx)
+    n = 0
+    for i, dm in enumerate(DMS):
+        if i > 0:
+            ctx.update_mass(f["m_c"] + dm)
+        chi = f["chi_host"][i].to("cuda", non_blocking=True) if host_io is not None else f["chi_dev"][i]
+        psi = f["psi_dev"][i]
+        st = ctx.solve(chi, psi, TOL)
+        if host_io is not None:
+            host_io[f["beta"]][i].copy_(psi, non_blocking=True)
+        if stats_out is not None:
+            stats_out.append(dict(beta=f["beta"], dm=dm, **st))
+        n += 1
+    return n
+
+
+# The betas are independent problems with their own contexts (own streams): one host thread
+# each lets their small, latency-bound kernels overlap on the GPU. --serial runs them in turn.
+CONCURRENT = True
+
+
 def run_step(fields_dev, precision: int, stats_out=None, host_io=None):
     """One pass over the batch: per beta, setup at the lightest mass and three solves."""
     import torch
-    import paper_0707_4018_gb300 as mg
-    n_solves = 0
-    for f in fields_dev:
-        if host_io is not None:
-            U = f["U_host"].to("cuda", non_blocking=True)
-        else:
-            U = f["U_dev"]
-        ctx = mg.Context.setup(U, f["m_c"] + DMS[0], (L, L), mg_params(precision))
-        for i, dm in enumerate(DMS):
-            if i > 0:
-                ctx.update_mass(f["m_c"] + dm)
-            chi = f["chi_host"][i].to("cuda", non_blocking=True) if host_io is not None else f["chi_dev"][i]
-            psi = f["psi_dev"][i]
-            st = ctx.solve(chi, psi, TOL)
-            if host_io is not None:
-                host_io[f["beta"]][i].copy_(psi, non_blocking=True)
-            if stats_out is not None:
-                stats_out.append(dict(beta=f["beta"], dm=dm, **st))
-            n_solves += 1
-        ctx.close()
+    contexts = []
+    stats = [] if stats_out is not None else None
+    if CONCURRENT and len(fields_dev) > 1:
+        errors, counts = [], []
+
+        def work(f):
+            try:
+                counts.append(_one_field(f, precision, stats, host_io, contexts))
+            except BaseException as e:  # re-raised on the calling thread
+                errors.append(e)
+
+        threads = [threading.Thread(target=work, args=(f,)) for f in fields_dev]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        if errors:
+            raise errors[0]
+        n_solves = sum(counts)
+    else:
+        n_solves = sum(_one_field(f, precision, stats, host_io, contexts) for f in fields_dev)
     torch.cuda.current_stream().synchronize()
+    for ctx in contexts:  # freed after every beta finished (a free synchronises the device)
+        ctx.close()
+    if stats_out is not None:
+        stats_out.extend(sorted(stats, key=lambda d: (d["beta"], d["dm"])))
     return n_solves
 
 
@@ -420,12 +454,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--serial", action="store_true", help="run the betas of a step one after another")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--only", default=None, choices=["dslash-f32", "dslash-f64", "solve", "vcycle"],
                     help="profiling cases: the Dslash timing loop alone, one beta's setup + 3 solves, or "
                          "25 mixed-precision V-cycles after one beta's setup")
     args = ap.parse_args()
+    global CONCURRENT
+    CONCURRENT = not args.serial
     if args.warmup < 3:
         raise SystemExit("warmup must be >= 3")
     if args.only is not None:
@@ -494,6 +531,8 @@ def main():
         "config": {"workload": WORKLOAD, "lattice": f"{L}x{L}", "betas": list(BETAS), "m_minus_mc": list(DMS),
                    "solves_per_step": len(BETAS) * len(DMS), "precision": "FP64 outer GCR, FP32 V-cycle",
                    "l2": "flushed before every timed step (512 MiB write)", "tol": TOL,
+                   "betas_run": "concurrently (one host thread and context stream each)" if CONCURRENT
+                   else "one after another",
                    "gauge_digest_matches_table": all(f["digest_ok"] for f in fields) if rank == 0 else None},
         "solver": {"iters": iters, "worst_true_rel_residual": worst_res},
         "fp64_mg": fp64,
