@@ -517,27 +517,38 @@ __device__ __forceinline__ void grid_sync3(const Cg3Args &a, bool &ok) {
   ok = ok && s_ok;
 }
 
-// cpart[0..nv) holds this CTA's sums; publish, barrier, stage every CTA's
-// partials, sum each slot in CTA order into sres
-__device__ __forceinline__ void grid_sum3(const Cg3Args &a, int nv, const double *cpart, double *stage, double *sres,
-                                          bool &ok) {
+// cpart[0..nv) holds this CTA's sums; publish them slot-major (partials[s * G + cta]),
+// barrier, and sum each slot over the CTAs into sres: a warp takes four slots at a time,
+// each lane loads all its partials of them at once (lane l adds CTAs l, l + 32, ... in
+// that order, then the shuffle tree: a fixed order in every CTA)
+constexpr int kMaxGrid3 = 256;
+__device__ __forceinline__ void grid_sum3(const Cg3Args &a, int nv, const double *cpart, double *sres, bool &ok) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int G = (int)gridDim.x;
   __syncthreads();
-  for (int s = threadIdx.x; s < nv; s += blockDim.x) a.partials[(long long)blockIdx.x * kSmSlots + s] = cpart[s];
+  for (int q = threadIdx.x; q < nv; q += blockDim.x) a.partials[(long long)q * G + blockIdx.x] = cpart[q];
   __threadfence();
   grid_sync3(a, ok);
-  const int total = (int)gridDim.x * nv;
-  for (int q = threadIdx.x; q < total; q += blockDim.x) {
-    const int c = q / nv, s = q - c * nv;
-    stage[q] = __ldcg(a.partials + (long long)c * kSmSlots + s);
-  }
-  __syncthreads();
-  for (int s = wid; s < nv; s += nw) {
-    double t = 0.0;
-    for (unsigned int c = lane; c < gridDim.x; c += 32) t += stage[c * nv + s];
+  for (int q0 = wid * 4; q0 < nv; q0 += nw * 4) {
+    double vals[4][kMaxGrid3 / 32];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) sres[s] = t;
+    for (int u = 0; u < 4; ++u) {
+      const double *src = a.partials + (long long)(q0 + u) * G;
+#pragma unroll
+      for (int i = 0; i < kMaxGrid3 / 32; ++i) {
+        const int c = lane + 32 * i;
+        vals[u][i] = (q0 + u < nv && c < G) ? __ldcg(src + c) : 0.0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      double t = 0.0;
+#pragma unroll
+      for (int i = 0; i < kMaxGrid3 / 32; ++i) t += vals[u][i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0 && q0 + u < nv) sres[q0 + u] = t;
+    }
   }
   __syncthreads();
 }
@@ -610,7 +621,9 @@ __device__ __forceinline__ void cta_dots(int k, int nd, const Cx<double> *Ws, co
   }
 }
 
-__global__ void __launch_bounds__(256, 1) coarsest_gcr_smem_kernel(Cg3Args a) {
+// two CTAs per SM (at most 128 registers, about 86 KB of shared memory each), so that the
+// coarsest solves of two contexts running on different streams can share the GPU
+__global__ void __launch_bounds__(256, 2) coarsest_gcr_smem_kernel(Cg3Args a) {
   extern __shared__ double sm3[];
   Cx<double> *Ys = reinterpret_cast<Cx<double> *>(sm3);  // [64 rows][5][8]
   Cx<double> *Ms = Ys + kSmMaxDofs * 40;                  // [8 sites][64]
@@ -621,7 +634,6 @@ __global__ void __launch_bounds__(256, 1) coarsest_gcr_smem_kernel(Cg3Args a) {
   Cx<double> *Ws = Zs + kSmMaxRestart * kSmMaxDofs;       // [16][64]
   double *cpart = reinterpret_cast<double *>(Ws + kSmMaxRestart * kSmMaxDofs);  // [kSmSlots]
   double *sres = cpart + kSmSlots;
-  double *stage = sres + kSmSlots;                        // [G][kSmSlots]
   const int tid = threadIdx.x;
   const long long site0 = blockIdx.x * (long long)a.spc;
   long long ns = a.nsites - site0;
@@ -653,7 +665,7 @@ __global__ void __launch_bounds__(256, 1) coarsest_gcr_smem_kernel(Cg3Args a) {
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (tid == 0) cpart[0] = t;
   }
-  grid_sum3(a, 1, cpart, stage, sres, ok);
+  grid_sum3(a, 1, cpart, sres, ok);
   if (!ok) return;
   const double bn2 = sres[0];
   const double tol2 = a.tol * a.tol * bn2;
@@ -668,7 +680,7 @@ __global__ void __launch_bounds__(256, 1) coarsest_gcr_smem_kernel(Cg3Args a) {
       for (int d = tid; d < nd; d += blockDim.x) Zk[d] = rs[d];
       __syncthreads();
       cta_dots(k, nd, Ws, Wk, rs, cpart);
-      grid_sum3(a, 3 + 2 * k, cpart, stage, sres, ok);
+      grid_sum3(a, 3 + 2 * k, cpart, sres, ok);
       if (!ok) return;
       double nw0 = sres[0];
       double nw2 = nw0;
@@ -689,7 +701,7 @@ __global__ void __launch_bounds__(256, 1) coarsest_gcr_smem_kernel(Cg3Args a) {
         // cancellation: project once more against the basis (same branch in every CTA)
         __syncthreads();
         cta_dots(k, nd, Ws, Wk, rs, cpart);
-        grid_sum3(a, 3 + 2 * k, cpart, stage, sres, ok);
+        grid_sum3(a, 3 + 2 * k, cpart, sres, ok);
         if (!ok) return;
         nw2 = sres[0];
         for (int j = 0; j < k; ++j) nw2 -= sres[3 + 2 * j] * sres[3 + 2 * j] + sres[4 + 2 * j] * sres[4 + 2 * j];
@@ -746,7 +758,7 @@ __global__ void __launch_bounds__(256, 1) coarsest_gcr_smem_kernel(Cg3Args a) {
       if (tid == 0) cpart[0] = t;
     }
     __threadfence();
-    grid_sum3(a, 1, cpart, stage, sres, ok);
+    grid_sum3(a, 1, cpart, sres, ok);
     if (!ok) return;
     rn2 = sres[0];
     converged = rn2 <= tol2;
@@ -797,9 +809,10 @@ void launch_coarsest_gcr_smem(const Cx<double> *Yt, const Cx<double> *Minv, Geo2
   a.spin_limit = 1LL << 24;
   a.out = out;
   a.out_rel = out_rel;
+  if (grid > kMaxGrid3) fail(MG_ERR_UNSUPPORTED, "coarsest solve: more than 256 CTAs");
   const size_t smem = (size_t)(kSmMaxDofs * 40 + 8 * 64 + 3 * kSmMaxDofs + 2 * kSmMaxRestart * kSmMaxDofs) *
                           sizeof(Cx<double>) +
-                      (size_t)(2 + grid) * kSmSlots * sizeof(double);
+                      (size_t)2 * kSmSlots * sizeof(double);
   const void *fn = (const void *)coarsest_gcr_smem_kernel;
   MG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
@@ -856,6 +869,7 @@ int barrier_selftest(unsigned int expected, long long spin_limit, cudaStream_t s
   DevBuf<int> status;
   bar.alloc(2);
   status.alloc(1);
+  pool_ready();
   MG_CUDA(cudaMemsetAsync(bar.p, 0, 2 * sizeof(unsigned int), s));
   MG_CUDA(cudaMemsetAsync(status.p, 0, sizeof(int), s));
   void *args[] = {&bar.p, &expected, &spin_limit, &status.p};

@@ -97,8 +97,17 @@ template <typename To, typename From>
 __host__ __device__ __forceinline__ Cx<To> cvt(Cx<From> a) { return mk((To)a.re, (To)a.im); }
 
 // ---------------------------------------------------------------------------
-// device buffers
+// device buffers: stream-ordered allocations from the device's default memory
+// pool, ordered on the calling thread's per-thread stream. Contexts are made and
+// dropped often (one per configuration); the pool keeps freed memory, so that
+// costs neither driver allocations nor device-wide synchronisation (a plain
+// cudaFree synchronises the whole device, stalling every other context).
+// The owner must have finished all work on a buffer before it is released, and
+// must order its first use after the allocation (pool_ready below).
 // ---------------------------------------------------------------------------
+void pool_init();   // once per process and device: keep freed memory in the pool
+void pool_ready();  // allocations made by this thread so far are usable on any stream
+
 template <typename T>
 struct DevBuf {
   T *p = nullptr;
@@ -115,17 +124,18 @@ struct DevBuf {
   void alloc(size_t count) {
     release();
     if (count == 0) return;
+    pool_init();
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    cudaError_t e = cudaMallocAsync(&q, count * sizeof(T), cudaStreamPerThread);
     if (e != cudaSuccess) {
       (void)cudaGetLastError();
-      fail(MG_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes: " + cudaGetErrorString(e));
+      fail(MG_ERR_OOM, "cudaMallocAsync of " + std::to_string(count * sizeof(T)) + " bytes: " + cudaGetErrorString(e));
     }
     p = static_cast<T *>(q);
     n = count;
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, cudaStreamPerThread);
     p = nullptr;
     n = 0;
   }

@@ -15,6 +15,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <vector>
 
 #include "kernels.h"
@@ -22,6 +23,23 @@
 namespace mg {
 
 std::atomic<long long> g_launches{0};
+
+void pool_init() {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    unsigned long long keep = ~0ULL;  // never hand freed memory back to the driver
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  done[dev] = true;
+}
+
+void pool_ready() { MG_CUDA(cudaStreamSynchronize(cudaStreamPerThread)); }
 
 static thread_local std::string t_last_error;
 
@@ -132,6 +150,7 @@ struct mg_ctx {
   bool graphs_ok = true;
   mg::DevBuf<mg::Cx<double>> z64;
   ~mg_ctx() {
+    if (s) cudaStreamSynchronize(s);  // no work may still use the buffers released below
     for (auto &g : pre) g.reset();
     for (auto &v : preb)
       for (auto &g : v) g.reset();
@@ -517,6 +536,7 @@ static void prepare_slots(mg_ctx &c, int nb, const double *shift) {
       if (c.bLU[v].p == nullptr) {
         c.bLU[v].alloc((size_t)c.nc * c.nc);
         c.bipiv[v].alloc(c.nc);
+        pool_ready();
       }
       launch_dense_from_stencil(L.Y64.p, c.bLU[v].p, L.geo, L.nint, c.s, shift[v]);
       lu_factor(c.bLU[v].p, c.nc, c.bipiv[v].p, c.info.p, c.s);
@@ -852,6 +872,7 @@ static void alloc_batch(mg_ctx &c) {
   c.bdots.alloc(nr * 2 * (c.p.gcr_restart + 3));
   c.bcoef.alloc(nr * 4);
   MG_CUDA(cudaMallocHost(&c.bhost, (nr * 2 * (c.p.gcr_restart + 3) + nr * 4) * sizeof(double)));
+  pool_ready();
 }
 
 static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_params *p, void *stream) {
@@ -952,7 +973,6 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
     c->cg_work.alloc((size_t)Cst.geo.nsites * 2 * Cst.nint * Cst.nint);
     c->cg_y.alloc(Cst.n);
     c->cg_info.alloc(1);
-    MG_CUDA(cudaMemsetAsync(c->cg_out.p, 0, 3 * sizeof(int), c->s));
     c->cg_batch = c->cg_smem && coarsest_batch_fits(Cst.geo, Cst.nint, p->coarsest_restart, c->cg_grid) &&
                   std::getenv("MG_NO_BATCH_COARSEST") == nullptr;
     if (c->cg_batch) {
@@ -994,6 +1014,8 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
   c->mrpart[1].alloc((size_t)cap);
   c->ws.tickets = std::max(160, (p->gcr_restart + 3) * p->max_rhs);
   c->tickets.alloc((size_t)c->ws.tickets);
+  pool_ready();  // every buffer above is usable on the context stream from here
+  if (!c->use_lu) MG_CUDA(cudaMemsetAsync(c->cg_out.p, 0, 3 * sizeof(int), c->s));
   MG_CUDA(cudaMemsetAsync(c->tickets.p, 0, c->ws.tickets * sizeof(unsigned int), c->s));
   c->scal.alloc(kSlotCount);
   MG_CUDA(cudaMemsetAsync(c->scal.p, 0, kSlotCount * sizeof(double), c->s));
