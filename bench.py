@@ -418,6 +418,19 @@ def run_only(case: str):
         r = dslash_roofline(1 if case == "dslash-f32" else 0, iters=3)
         print(json.dumps({"case": case, **r}))
         return
+    if case == "transfer":
+        Lt = 1024
+        p = mg.mg_default_params(levels=3, blocks=[(4, 4), (2, 2)], Nv=[8, 8], precision=mg.MG_FP32, n_pass=1,
+                                 nu_setup=4, coarsest_tol=0.2)
+        ctx = mg.Context.setup(torch.from_numpy(inputs.hot_links(Lt, Lt, seed=3)).cuda(), 0.1, (Lt, Lt), p)
+        r = torch.from_numpy(inputs.gaussian_source(Lt, Lt, seed=4)).cuda()
+        z = torch.empty_like(r)
+        for _ in range(5):
+            ctx.vcycle(r, z)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": case, "lattice": f"{Lt}x{Lt}", "cycles": 5}))
+        ctx.close()
+        return
     beta = 6.0
     U, _, _ = inputs.schwinger_links(L, beta, sweeps=2000, workload_id=WORKLOAD_ID)
     mc = mcrit_table()[f"w{WORKLOAD_ID}_L{L}_b{beta:g}"]["m_crit"]
@@ -457,9 +470,10 @@ def main():
     ap.add_argument("--serial", action="store_true", help="run the betas of a step one after another")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--only", default=None, choices=["dslash-f32", "dslash-f64", "solve", "vcycle"],
-                    help="profiling cases: the Dslash timing loop alone, one beta's setup + 3 solves, or "
-                         "25 mixed-precision V-cycles after one beta's setup")
+    ap.add_argument("--only", default=None, choices=["dslash-f32", "dslash-f64", "solve", "vcycle", "transfer"],
+                    help="profiling cases: the Dslash timing loop alone, one beta's setup + 3 solves, "
+                         "25 mixed-precision V-cycles after one beta's setup, or 5 V-cycles on a 1024^2 "
+                         "hierarchy (fine level larger than L2, for the restriction and prolongation)")
     args = ap.parse_args()
     global CONCURRENT
     CONCURRENT = not args.serial

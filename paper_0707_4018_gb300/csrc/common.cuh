@@ -157,10 +157,13 @@ struct BlockGeo {
   long long nblocks;
 };
 
+// 32-bit index arithmetic (a 64-bit division costs about a hundred instructions; lattices
+// are limited to fewer than 2^31 sites at setup)
 __host__ __device__ __forceinline__ long long fine_site_of(const BlockGeo &g, long long b, int s) {
-  int cb0 = (int)(b % g.nb0), cb1 = (int)(b / g.nb0);
-  int x0 = cb0 * g.B0 + s % g.B0, x1 = cb1 * g.B1 + s / g.B0;
-  return (long long)x0 + (long long)g.L0 * x1;
+  const int bi = (int)b;
+  const int cb1 = bi / g.nb0, cb0 = bi - cb1 * g.nb0;
+  const int sy = s / g.B0, sx = s - sy * g.B0;
+  return (long long)(cb0 * g.B0 + sx) + (long long)g.L0 * (cb1 * g.B1 + sy);
 }
 
 // ---------------------------------------------------------------------------

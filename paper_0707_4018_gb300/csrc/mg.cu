@@ -817,6 +817,8 @@ static void validate(const mg_geom *g, const mg_params *p) {
   if (g->d != 2) fail(MG_ERR_UNSUPPORTED, "only d = 2 is built");
   if (g->Nc != 1) fail(MG_ERR_UNSUPPORTED, "only Nc = 1 (U(1)) is built");
   if (g->dims[0] < 2 || g->dims[1] < 2) fail(MG_ERR_INVALID_ARG, "lattice extents must be >= 2");
+  if ((long long)g->dims[0] * g->dims[1] * 8 >= (1LL << 31))
+    fail(MG_ERR_UNSUPPORTED, "lattices are limited to fewer than 2^28 sites (32-bit dof indexing)");
   if (p->levels < 2 || p->levels > MG_MAX_LEVELS) fail(MG_ERR_INVALID_ARG, "levels must be in [2, 4]");
   if (p->precision != MG_FP64 && p->precision != MG_FP32) fail(MG_ERR_INVALID_ARG, "unknown precision");
   if (p->n_pass < 1 || p->nu_pre < 0 || p->nu_post < 0 || p->nu_setup < 0) fail(MG_ERR_INVALID_ARG, "bad counts");

@@ -55,6 +55,96 @@ __global__ void __launch_bounds__(128) restrict_kernel(const Cx<R> *__restrict__
   if (lane < Nv) coarse[b * Nv + lane] = mine;
 }
 
+// Streaming restriction for Nv = 8 (the hot levels): a CTA of 256 threads takes BPC
+// consecutive blocks, whose prolongator rows V[b][k][0..Nb) form one contiguous tile
+// (16 KB in FP32), and reads it with 16-byte loads in order (four per thread): every
+// load instruction of a warp covers 512 contiguous bytes. A 16-byte vector holds CPV
+// complex numbers (2 in FP32, 1 in FP64) of one (block, k) row and of one site (n_int is
+// a multiple of CPV), so the matching residual entries are one 16-byte load too (served
+// from L1/L2 for the other seven k). The Nb / CPV vectors of a row belong to consecutive
+// lanes and are summed by a shuffle tree within that lane group.
+template <typename R>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using T = float4;
+  static constexpr int cpv = 2;
+};
+template <>
+struct Vec16<double> {
+  using T = double2;
+  static constexpr int cpv = 1;
+};
+
+template <typename R>
+__device__ __forceinline__ void cmac_conj_vec(Cx<R> &acc, typename Vec16<R>::T v, typename Vec16<R>::T r);
+template <>
+__device__ __forceinline__ void cmac_conj_vec<float>(Cx<float> &acc, float4 v, float4 r) {
+  cmac_conj(acc, mk(v.x, v.y), mk(r.x, r.y));
+  cmac_conj(acc, mk(v.z, v.w), mk(r.z, r.w));
+}
+template <>
+__device__ __forceinline__ void cmac_conj_vec<double>(Cx<double> &acc, double2 v, double2 r) {
+  cmac_conj(acc, mk(v.x, v.y), mk(r.x, r.y));
+}
+
+template <typename R, int BPC, int PER_ROW>
+__global__ void __launch_bounds__(256) restrict8_stream_kernel(const Cx<R> *__restrict__ V,
+                                                               const Cx<R> *__restrict__ fine,
+                                                               Cx<R> *__restrict__ coarse, BlockGeo g) {
+  using T = typename Vec16<R>::T;
+  constexpr int CPV = Vec16<R>::cpv;
+  constexpr int NV = 8;
+  constexpr int ITERS = BPC * NV * PER_ROW / 256;  // vectors per thread
+  static_assert(ITERS * 256 == BPC * NV * PER_ROW && PER_ROW <= 32 && (PER_ROW & (PER_ROW - 1)) == 0, "tile");
+  fine += blockIdx.y * (g.nblocks * (long long)g.Nb);
+  coarse += blockIdx.y * (g.nblocks * (long long)NV);
+  const long long b0 = (long long)blockIdx.x * BPC;
+  const T *tile = reinterpret_cast<const T *>(V + b0 * NV * g.Nb);
+  const int lane = threadIdx.x & 31;
+  // coarse coordinates of the CTA's first block, once (32-bit: index arithmetic, not
+  // bandwidth, bounded the first version of this kernel)
+  const int b0i = (int)b0;
+  const int c1_0 = b0i / g.nb0, c0_0 = b0i - c1_0 * g.nb0;
+  // all loads first: ITERS tile vectors and their residual vectors in flight together
+  T vv[ITERS], rr[ITERS];
+#pragma unroll
+  for (int u = 0; u < ITERS; ++u) {
+    const int f = threadIdx.x + 256 * u;
+    const int row = f / PER_ROW, j = f - row * PER_ROW;
+    const int bl = row / NV;
+    if (b0i + bl < g.nblocks) {
+      int c0 = c0_0 + bl, c1 = c1_0;
+      while (c0 >= g.nb0) {  // the CTA's blocks are consecutive in x, wrapping into the next row
+        c0 -= g.nb0;
+        ++c1;
+      }
+      const int i = j * CPV, st = i / g.nint, a = i - st * g.nint;
+      const int sy = st / g.B0, sx = st - sy * g.B0;
+      const long long site = (long long)(c0 * g.B0 + sx) + (long long)g.L0 * (c1 * g.B1 + sy);
+      vv[u] = tile[f];
+      rr[u] = *reinterpret_cast<const T *>(fine + site * g.nint + a);
+    } else {
+      vv[u] = T{};
+      rr[u] = T{};
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < ITERS; ++u) {
+    const int f = threadIdx.x + 256 * u;
+    const int row = f / PER_ROW;
+    const long long b = b0 + row / NV;
+    Cx<R> acc = mk((R)0, (R)0);
+    cmac_conj_vec<R>(acc, vv[u], rr[u]);
+#pragma unroll
+    for (int o = PER_ROW >> 1; o > 0; o >>= 1) {
+      acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
+      acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
+    }
+    if ((lane & (PER_ROW - 1)) == 0 && b < g.nblocks) coarse[b * NV + (row - (row / NV) * NV)] = acc;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // prolongation: fine[site(b, s)][a] += sum_k V[b][k][i] coarse[b][k]
 // ---------------------------------------------------------------------------
@@ -68,9 +158,11 @@ __global__ void __launch_bounds__(128) prolong_add_kernel(const Cx<R> *__restric
   if (b >= g.nblocks) return;
   const Cx<R> *Vb = V + b * (long long)Nv * g.Nb;
   const Cx<R> *e = coarse + b * Nv;
+  const int c1 = (int)(b / g.nb0), c0 = (int)(b - (long long)c1 * g.nb0);
   for (int i = lane; i < g.Nb; i += 32) {
     const int s = i / g.nint, a = i - s * g.nint;
-    const long long f = fine_site_of(g, b, s) * g.nint + a;
+    const int sy = s / g.B0, sx = s - sy * g.B0;
+    const long long f = ((long long)(c0 * g.B0 + sx) + (long long)g.L0 * (c1 * g.B1 + sy)) * g.nint + a;
     Cx<R> acc = fine[f];
     for (int k = 0; k < Nv; ++k) cmac(acc, Vb[(long long)k * g.Nb + i], e[k]);
     fine[f] = acc;
@@ -308,6 +400,15 @@ __global__ void gaussian_kernel(Cx<double> *out, long long n, unsigned long long
 template <typename R>
 void launch_restrict(const Cx<R> *V, const Cx<R> *fine, Cx<R> *coarse, BlockGeo bg, int Nv, cudaStream_t s,
                      int nvec) {
+  constexpr int CPV = Vec16<R>::cpv;
+  if (Nv == 8 && bg.nint % CPV == 0 && bg.Nb / CPV == 32 / CPV) {
+    // streaming form: 32 dofs per block (4 x 4 sites x 2 spins, or 2 x 2 sites x 8)
+    constexpr int BPC = 4 * CPV;  // 16 KB tiles in FP32, 32 KB in FP64
+    const dim3 grid((unsigned int)((bg.nblocks + BPC - 1) / BPC), nvec);
+    restrict8_stream_kernel<R, BPC, 32 / CPV><<<grid, 256, 0, s>>>(V, fine, coarse, bg);
+    MG_LAUNCHED();
+    return;
+  }
   const int threads = 128;
   const dim3 grid(grid_for(bg.nblocks * 32, threads), nvec);
   if (Nv <= 8)
