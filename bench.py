@@ -418,6 +418,35 @@ def run_only(case: str):
         r = dslash_roofline(1 if case == "dslash-f32" else 0, iters=3)
         print(json.dumps({"case": case, **r}))
         return
+    if case == "coarse-tc":
+        # level 1 of the 256^2 hierarchy (64^2 coarse sites x 8) applied to 16 vectors
+        U, _, _ = inputs.schwinger_links(L, 6.0, sweeps=2000, workload_id=WORKLOAD_ID)
+        ctx = mg.Context.setup(torch.from_numpy(U).cuda(), 0.1, (L, L), mg_params(mg.MG_FP32))
+        n_sites, n_int = ctx.level_size(1)
+        R = 16
+        g = torch.Generator(device="cuda").manual_seed(9)
+        x = torch.randn((R, n_sites, n_int), dtype=torch.complex64, device="cuda", generator=g)
+        y = torch.empty_like(x)
+        res = {}
+        stream = torch.cuda.current_stream()
+        for tc in (True, False):
+            for _ in range(3):
+                ctx.coarse_apply_mrhs(1, x, y, tc)
+            ms = []
+            for _ in range(20):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.coarse_apply_mrhs(1, x, y, tc)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            t = statistics.median(ms) * 1e-3
+            res["tensor" if tc else "cuda_core"] = {"us_per_call_incl_sync": t * 1e6,
+                                                    "gflops": 2560 * R * n_sites / t / 1e9}
+        print(json.dumps({"case": case, "coarse_sites": n_sites, "rhs": R, **res}))
+        ctx.close()
+        return
     if case == "transfer":
         Lt = 1024
         p = mg.mg_default_params(levels=3, blocks=[(4, 4), (2, 2)], Nv=[8, 8], precision=mg.MG_FP32, n_pass=1,
@@ -470,10 +499,11 @@ def main():
     ap.add_argument("--serial", action="store_true", help="run the betas of a step one after another")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--only", default=None, choices=["dslash-f32", "dslash-f64", "solve", "vcycle", "transfer"],
+    ap.add_argument("--only", default=None, choices=["dslash-f32", "dslash-f64", "solve", "vcycle", "transfer", "coarse-tc"],
                     help="profiling cases: the Dslash timing loop alone, one beta's setup + 3 solves, "
                          "25 mixed-precision V-cycles after one beta's setup, or 5 V-cycles on a 1024^2 "
-                         "hierarchy (fine level larger than L2, for the restriction and prolongation)")
+                         "hierarchy (fine level larger than L2, for the restriction and prolongation), or the "
+                         "level-1 coarse apply on 16 vectors, tensor cores and CUDA cores")
     args = ap.parse_args()
     global CONCURRENT
     CONCURRENT = not args.serial

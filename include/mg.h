@@ -232,6 +232,19 @@ int mg_level_size(mg_ctx *ctx, int level, long long *n_sites, int *n_int);
 int mg_smooth_fine_noalloc(const mg_geom *g, const void *U, double m, const void *b, void *x, int nu, double omega,
                            void *stream);
 
+/* Coarse stencil apply on tensor cores for many right-hand sides (paper: the coarse
+ * operator P^dagger D P of Eq. Galerkin applied to a block of vectors, the contraction of
+ * multi-RHS solves): out_n = A_l in_n for n < nrhs.
+ *   level    1..levels-1, with N = 8 dofs per coarse site
+ *   in, out  device complex64 [n][site][dof], nrhs level vectors back to back (caller-owned)
+ * Per site and direction the complex 8 x 8 block is applied as a real 16 x 16 matrix with
+ * mma.sync m16n8k16: the context's FP32 operator and the input are rounded to BF16, the
+ * products summed in FP32 (relative error about 2^-8 of sum |Y| |x|). tensor_cores = 0 runs
+ * the same product on CUDA cores in FP32 (the comparison path). Needs a context set up with
+ * precision MG_FP32. Errors: INVALID_ARG (level, nrhs < 1, null pointers), UNSUPPORTED (FP64
+ * context or N != 8). */
+int mg_coarse_apply_mrhs(mg_ctx *ctx, int level, int nrhs, const void *in, void *out, int tensor_cores);
+
 /* Self-test of the bounded device-side wait used by the persistent kernels (a
  * failure-detection check; the paper has no counterpart). Launches a 2-CTA
  * cooperative kernel whose grid barrier expects 2 + missing_arrivals arrivals

@@ -75,6 +75,7 @@ def load():
         "mg_setup": (I, [P(ctxp), P(mg_geom), VP, D, P(mg_params), VP]),
         "mg_solve": (I, [ctxp, VP, VP, D, P(mg_stats)]),
         "mg_solve_batch": (I, [ctxp, I, VP, VP, P(D), D, P(mg_stats)]),
+        "mg_coarse_apply_mrhs": (I, [ctxp, I, I, VP, VP, I]),
         "mg_update_mass": (I, [ctxp, D]),
         "mg_destroy": (None, [ctxp]),
         "mg_last_error": (ctypes.c_char_p, []),
@@ -107,7 +108,8 @@ def exported_symbols():
     return ["mg_default_params", "mg_setup", "mg_solve", "mg_update_mass", "mg_destroy", "mg_last_error",
             "mg_dslash", "mg_level_apply", "mg_restrict", "mg_prolong", "mg_vcycle", "mg_smooth", "mg_build_level",
             "mg_get_null_vectors", "mg_get_prolongator", "mg_get_coarse_op", "mg_level_size", "mg_kernel_launches",
-            "mg_smooth_fine_noalloc", "mg_coarsest_solve", "mg_selftest_barrier", "mg_solve_batch"]
+            "mg_smooth_fine_noalloc", "mg_coarsest_solve", "mg_selftest_barrier", "mg_solve_batch",
+            "mg_coarse_apply_mrhs"]
 
 
 def _check(code: int):
@@ -271,6 +273,14 @@ class Context:
         if code != 0 and (raise_on_fail or code != 4):
             _check(code)
         return [st[v].as_dict() for v in range(nrhs)]
+
+    def coarse_apply_mrhs(self, level: int, inp: torch.Tensor, out: torch.Tensor, tensor_cores: bool = True):
+        """mg_coarse_apply_mrhs: out[n] = A_level inp[n] (complex64) on tensor cores (BF16 operands,
+        FP32 sums) or, with tensor_cores=False, on CUDA cores in FP32."""
+        nrhs = int(inp.shape[0])
+        n = self._numel(level) * nrhs
+        _check(load().mg_coarse_apply_mrhs(self._need(), int(level), nrhs, _ptr(inp, torch.complex64, n),
+                                           _ptr(out, torch.complex64, n), 1 if tensor_cores else 0))
 
     def update_mass(self, m: float):
         _check(load().mg_update_mass(self._need(), float(m)))

@@ -53,6 +53,14 @@ template <typename R>
 void launch_coarse_apply(const Cx<R> *Y, const Cx<R> *in, Cx<R> *out, Geo2 g, int N, const Cx<R> *b, double a,
                          double c, cudaStream_t s, int nvec = 1, const double *shift = nullptr);
 
+// ---- coarse stencil apply on tensor cores (N = 8, many vectors, BF16 operands, FP32 sums) ----
+// Ypk: nsites * 5 * 32 words packed from the FP32 internal stencil Y (A-fragment order)
+void launch_pack_coarse_bf16(const Cx<float> *Y, uint2 *Ypk, long long nsites, cudaStream_t s);
+// out_n = a (A + shift_n) in_n + c b_n for nvec vectors stored with stride nsites * 8
+// (b and shift may be null)
+void launch_coarse_apply_tc(const uint2 *Ypk, const Cx<float> *in, Cx<float> *out, Geo2 g, int nvec,
+                            const Cx<float> *b, double a, double c, const double *shift, cudaStream_t s);
+
 // ---- BLAS-1 ----
 template <typename R>
 void launch_zero(Cx<R> *x, long long n, cudaStream_t s);

@@ -57,6 +57,7 @@ struct Level {
   // coarse operator of this level (level >= 1), internal layout
   DevBuf<Cx<double>> Y64;
   DevBuf<Cx<float>> Y32;
+  DevBuf<uint2> Ypk;  // BF16 A fragments of Y32 for the tensor-core apply (N = 8, FP32 mode)
   // transfer to the next level
   BlockGeo bg{};
   int Nv = 0;
@@ -193,6 +194,13 @@ template <>
 const Cx<double> *Vof<double>(const Level &L) { return L.V64.p; }
 template <>
 const Cx<float> *Vof<float>(const Level &L) { return L.V32.p; }
+
+// FP32 copy of a coarse level's operator (and its packed BF16 form where it exists)
+static void refresh_y32(mg_ctx &c, int l) {
+  Level &L = c.lv[l];
+  launch_convert<float, double>(L.Y64.p, L.Y32.p, L.Y64.n, c.s);
+  if (L.Ypk.p != nullptr) launch_pack_coarse_bf16(L.Y32.p, L.Ypk.p, L.geo.nsites, c.s);
+}
 
 // out = a * A_l in + c * b
 template <typename R>
@@ -792,7 +800,7 @@ static void setup_level(mg_ctx &c, int l, bool full) {
     if (f32) {
       launch_convert<float, double>(L.V64.p, L.V32.p, L.V64.n, c.s);
       Level &C = c.lv[l + 1];
-      launch_convert<float, double>(C.Y64.p, C.Y32.p, C.Y64.n, c.s);
+      refresh_y32(c, l + 1);
     }
     if (l + 1 == c.p.levels - 1)
       prepare_coarsest(c);
@@ -808,7 +816,7 @@ static void make_fp32_copies(mg_ctx &c) {
   for (size_t l = 0; l < c.lv.size(); ++l) {
     Level &L = c.lv[l];
     if (l + 1 < c.lv.size()) launch_convert<float, double>(L.V64.p, L.V32.p, L.V64.n, c.s);
-    if (l > 0) launch_convert<float, double>(L.Y64.p, L.Y32.p, L.Y64.n, c.s);
+    if (l > 0) refresh_y32(c, (int)l);
   }
 }
 
@@ -903,6 +911,7 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
     if (l > 0) {
       L.Y64.alloc(L.geo.nsites * 5 * (size_t)nint * nint);
       if (f32) L.Y32.alloc(L.Y64.n);
+      if (f32 && nint == 8) L.Ypk.alloc(L.geo.nsites * 5 * 32);
     }
     const size_t nb = (size_t)c->nbatch;
     L.w64.b.alloc(L.n * nb);
@@ -1318,6 +1327,26 @@ int mg_vcycle(mg_ctx *c, const void *b, void *x) {
     need_ptr(x);
     check_fresh(*c);
     precondition(*c, static_cast<const Cx<double> *>(b), static_cast<Cx<double> *>(x));
+    MG_CUDA(cudaStreamSynchronize(c->s));
+  });
+}
+
+int mg_coarse_apply_mrhs(mg_ctx *c, int level, int nrhs, const void *in, void *out, int tensor_cores) {
+  return guarded([&] {
+    need_level(c, level, false);
+    need_ptr(in);
+    need_ptr(out);
+    if (level < 1) fail(MG_ERR_INVALID_ARG, "the tensor-core apply is for coarse levels (level >= 1)");
+    if (nrhs < 1) fail(MG_ERR_INVALID_ARG, "nrhs must be >= 1");
+    check_fresh(*c);
+    Level &L = c->lv[level];
+    if (L.Ypk.p == nullptr) fail(MG_ERR_UNSUPPORTED, "needs an MG_FP32 context and N = 8 on that level");
+    if (tensor_cores)
+      launch_coarse_apply_tc(L.Ypk.p, static_cast<const Cx<float> *>(in), static_cast<Cx<float> *>(out), L.geo,
+                             nrhs, nullptr, 1.0, 0.0, nullptr, c->s);
+    else
+      launch_coarse_apply<float>(L.Y32.p, static_cast<const Cx<float> *>(in), static_cast<Cx<float> *>(out), L.geo,
+                                 L.nint, nullptr, 1.0, 0.0, c->s, nrhs);
     MG_CUDA(cudaStreamSynchronize(c->s));
   });
 }
