@@ -248,6 +248,38 @@ def dslash_roofline(precision: int, L_big: int = 4096, iters: int = 20):
                 ms=t * 1e3, gbs=bytes_alg / t / 1e9)
 
 
+def dslash4_roofline(precision: int, dims=(32, 32, 32, 64), iters: int = 20):
+    """4d SU(3) Wilson apply alone on a lattice far larger than L2 (32^3 x 64: 1 GB per FP32
+    apply): algorithmic bytes / time. Links are Gaussian 3 x 3 matrices (the timing does not
+    depend on the values; the parity tests use SU(3) fields)."""
+    import torch
+    import paper_0707_4018_gb300 as mg
+    dt = torch.complex128 if precision == 0 else torch.complex64
+    V = int(np.prod(dims))
+    g = torch.Generator(device="cuda").manual_seed(6)
+    U = torch.randn((V, 4, 3, 3), device="cuda", generator=g, dtype=dt) / 3.0
+    psi = torch.randn((V, 4, 3), device="cuda", generator=g, dtype=dt)
+    out = torch.empty_like(psi)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        mg.mg_dslash(U, psi, out, 0.01, dims, precision)
+    ms = []
+    for _ in range(iters):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mg.mg_dslash(U, psi, out, 0.01, dims, precision)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = statistics.median(ms) * 1e-3
+    cplx = 16 if precision == 0 else 8
+    per_site = (12 + 36 + 12) * cplx  # psi in, 4 links, psi out
+    return dict(lattice="x".join(str(v) for v in dims), dtype="f64" if precision == 0 else "f32",
+                bytes_per_site=per_site, flop_per_site=1368, ms=t * 1e3, gbs=V * per_site / t / 1e9,
+                tflops=V * 1368 / t / 1e12)
+
+
 def coarsest_flops(iters: int, restart: int, n: int) -> float:
     """Algorithmic FP64 flops of one GCR solve on the preconditioned coarsest stencil (N = 8).
 
@@ -414,6 +446,10 @@ def run_only(case: str):
     import torch
     import paper_0707_4018_gb300 as mg
     mg.load()
+    if case.startswith("dslash4"):
+        r = dslash4_roofline(1 if case == "dslash4-f32" else 0, iters=3)
+        print(json.dumps({"case": case, **r}))
+        return
     if case.startswith("dslash"):
         r = dslash_roofline(1 if case == "dslash-f32" else 0, iters=3)
         print(json.dumps({"case": case, **r}))
@@ -499,8 +535,9 @@ def main():
     ap.add_argument("--serial", action="store_true", help="run the betas of a step one after another")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--only", default=None, choices=["dslash-f32", "dslash-f64", "solve", "vcycle", "transfer", "coarse-tc"],
-                    help="profiling cases: the Dslash timing loop alone, one beta's setup + 3 solves, "
+    ap.add_argument("--only", default=None, choices=["dslash-f32", "dslash-f64", "dslash4-f32", "dslash4-f64", "solve", "vcycle",
+                                                      "transfer", "coarse-tc"],
+                    help="profiling cases: the Dslash timing loop alone (2d, or 4d SU(3)), one beta's setup + 3 solves, "
                          "25 mixed-precision V-cycles after one beta's setup, or 5 V-cycles on a 1024^2 "
                          "hierarchy (fine level larger than L2, for the restriction and prolongation), or the "
                          "level-1 coarse apply on 16 vectors, tensor cores and CUDA cores")
@@ -560,6 +597,7 @@ def main():
     peak, peak_kind = measured_peaks()
     ds32 = dslash_roofline(1)
     ds64 = dslash_roofline(0)
+    ds4 = dslash4_roofline(1)
     cr = coarsest_roofline(fields_dev)
 
     cpu = None
@@ -589,7 +627,8 @@ def main():
                      "peak_kind": "GB300 nominal FP64 (no FP64 figure in the measured peaks)"},
         "dslash_hbm": {"f32": ds32, "f64": ds64, "peak_gbs": peak, "peak_kind": peak_kind,
                        "frac_f32": ds32["gbs"] / peak,
-                       "traffic_f32": 780606208, "traffic_source": "profiles/dslash_f32_4096x4096.md"},
+                       "traffic_f32": 780606208, "traffic_source": "profiles/dslash_f32_4096x4096.md",
+                       "su3_4d_f32": {**ds4, "frac": ds4["gbs"] / peak}},
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

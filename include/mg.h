@@ -74,9 +74,9 @@ typedef enum {
 } mg_precision;
 
 typedef struct {
-  int d;       /* number of dimensions; 2 */
-  int dims[4]; /* lattice extents (dims[0] = L0, dims[1] = L1) */
-  int Nc;      /* colours; 1 (U(1)) */
+  int d;       /* number of dimensions: 2 (U(1)), or 4 (SU(3), where a call says so) */
+  int dims[4]; /* lattice extents (dims[0] = L0, dims[1] = L1, ...) */
+  int Nc;      /* colours: 1 (U(1), d = 2) or 3 (SU(3), d = 4) */
 } mg_geom;
 
 typedef struct {
@@ -173,7 +173,15 @@ const char *mg_last_error(void);
 
 /* Fine Wilson operator out = D(U) in without a context (paper, definition of D).
  * precision MG_FP64: U, in, out complex128; MG_FP32: complex64. in and out must
- * not alias. stream: cudaStream_t. Asynchronous on the stream (no sync). */
+ * not alias. stream: cudaStream_t. Asynchronous on the stream (no sync).
+ * Geometries: d = 2 with Nc = 1 (layouts above), or d = 4 with Nc = 3: the
+ * paper's four-dimensional SU(3) case (its outlook), in the DeGrand-Rossi basis
+ *   gamma_1 = [[0,0,0,i],[0,0,i,0],[0,-i,0,0],[-i,0,0,0]], gamma_2 = [[0,0,0,-1],[0,0,1,0],[0,1,0,0],[-1,0,0,0]],
+ *   gamma_3 = [[0,0,i,0],[0,0,0,-i],[-i,0,0,0],[0,i,0,0]], gamma_4 = [[0,0,1,0],[0,0,0,1],[1,0,0,0],[0,1,0,0]],
+ * site x = x0 + L0 (x1 + L1 (x2 + L2 x3)), psi[x][s][c] (s < 4, c < 3),
+ * U[x][mu][a][b] (SU(3) link from x to x + mu-hat, row a, column b), diagonal 4 + m.
+ * Errors: INVALID_ARG (extent < 2, volume >= 2^31, null or aliasing pointers,
+ * unknown precision), UNSUPPORTED (other d / Nc). */
 int mg_dslash(const mg_geom *g, const void *U, double m, const void *in, void *out, int precision, void *stream);
 
 /* Apply the level-l operator (l = 0: D; l >= 1: the Galerkin stencil) in FP64. */

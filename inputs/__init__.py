@@ -13,8 +13,15 @@ action, periodic, beta = 6 and 10):
   * sources: complex Gaussian, Re and Im independent N(0, 1) (Box-Muller);
   * gauge transforms: uniform U(1) phases.
 
-Layouts: site x = x0 + L0*x1; links U[x, mu] complex128; spinors psi[x, s]
-complex128 (2d: two spin components).
+4d SU(3) recipe (Wilson-Dirac in four dimensions):
+  * links: every U_x^mu the SU(3) projection of 1 + eps H (H Gaussian traceless
+    hermitian, eps = 0.4), then ``ape_steps`` APE smearing steps with alpha = 0.5;
+    the projection is row Gram-Schmidt with row 3 = conj(row 1 x row 2);
+  * sources: complex Gaussian, 12 components (4 spins x 3 colours) per site.
+
+Layouts: site x = x0 + L0*x1 (+ L0 L1 x2 + L0 L1 L2 x3 in 4d); links U[x, mu]
+complex128 (U[x, mu, a, b] for SU(3)); spinors psi[x, s] complex128 (psi[x, s, c]
+in 4d).
 """
 from __future__ import annotations
 
@@ -61,6 +68,9 @@ def _load():
             lib.links_from_angles.argtypes = [ctypes.c_int64, dp, dp]
             lib.gen_u1_phases.argtypes = [ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, dp]
             lib.gen_num_threads.restype = ctypes.c_int
+            lib.gen_su3_near_identity.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, dp]
+            lib.gen_su3_random.argtypes = [ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, dp]
+            lib.ape_smear_4d.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_double, dp, dp]
             _lib = lib
     return _lib
 
@@ -178,3 +188,44 @@ def free_links(L0: int, L1: int, phi=(0.0, 0.0)) -> np.ndarray:
 def hot_links(L0: int, L1: int, seed: int) -> np.ndarray:
     """Uniformly random U(1) links (infinite-temperature field)."""
     return u1_phases(L0 * L1 * 2, seed, 0x484F54).reshape(L0 * L1, 2)
+
+
+# ---------------------------------------------------------------------------
+# 4d SU(3)
+# ---------------------------------------------------------------------------
+
+def su3_near_identity(n: int, eps: float, seed: int, tag: int) -> np.ndarray:
+    """n SU(3) matrices (n, 3, 3): projection of 1 + eps H, H Gaussian traceless hermitian."""
+    out = np.empty(n * 18, dtype=np.float64)
+    _load().gen_su3_near_identity(int(n), float(eps), int(seed), int(tag), _dp(out))
+    return out.view(np.complex128).reshape(n, 3, 3)
+
+
+def su3_random(n: int, seed: int, tag: int) -> np.ndarray:
+    """n random SU(3) matrices (n, 3, 3): projection of complex Gaussian matrices."""
+    out = np.empty(n * 18, dtype=np.float64)
+    _load().gen_su3_random(int(n), int(seed), int(tag), _dp(out))
+    return out.view(np.complex128).reshape(n, 3, 3)
+
+
+def ape_smear(U: np.ndarray, dims, alpha: float = 0.5, steps: int = 1) -> np.ndarray:
+    """``steps`` APE smearing steps of a 4d SU(3) field U[x, mu, a, b] (returns a new array)."""
+    L = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    cur = np.ascontiguousarray(U, dtype=np.complex128).copy()
+    nxt = np.empty_like(cur)
+    for _ in range(int(steps)):
+        _load().ape_smear_4d(L, float(alpha), _dp(cur.view(np.float64)), _dp(nxt.view(np.float64)))
+        cur, nxt = nxt, cur
+    return cur
+
+
+def su3_links(dims, seed: int, eps: float = 0.4, ape_steps: int = 4, alpha: float = 0.5) -> np.ndarray:
+    """4d SU(3) gauge field U[x, mu, a, b] (complex128, (V, 4, 3, 3)) of the recipe above."""
+    V = int(np.prod(dims))
+    U = su3_near_identity(V * 4, eps, seed, 0x535533).reshape(V, 4, 3, 3)
+    return ape_smear(U, dims, alpha, ape_steps) if ape_steps > 0 else U
+
+
+def gaussian_spinor(nsites: int, n_int: int, seed: int, index: int = 0) -> np.ndarray:
+    """Gaussian complex field (nsites, n_int) for right-hand side ``index`` (any dimension)."""
+    return gaussian_complex(nsites * n_int, seed, 0x5352430000 + index).reshape(nsites, n_int)

@@ -226,3 +226,205 @@ int gen_num_threads(void) {
   return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* SU(3) gauge fields in 4d                                                  */
+/* ------------------------------------------------------------------------ */
+/*
+ * A 3 x 3 complex matrix is 18 doubles, row-major, (re, im) interleaved.
+ * Links: U[((x * 4 + mu) * 3 + a) * 3 + b], x = x0 + L0 (x1 + L1 (x2 + L2 x3)),
+ * U_x^mu the link from x to x + mu-hat.
+ */
+typedef struct { double re, im; } cplx;
+
+static inline cplx cx(double re, double im) { cplx z = {re, im}; return z; }
+static inline cplx cadd(cplx a, cplx b) { return cx(a.re + b.re, a.im + b.im); }
+static inline cplx csub(cplx a, cplx b) { return cx(a.re - b.re, a.im - b.im); }
+static inline cplx cmul(cplx a, cplx b) { return cx(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
+static inline cplx cconj(cplx a) { return cx(a.re, -a.im); }
+static inline cplx cscale(double s, cplx a) { return cx(s * a.re, s * a.im); }
+
+static inline cplx mget(const double *m, int a, int b) { return cx(m[(a * 3 + b) * 2], m[(a * 3 + b) * 2 + 1]); }
+static inline void mset(double *m, int a, int b, cplx z) {
+  m[(a * 3 + b) * 2] = z.re;
+  m[(a * 3 + b) * 2 + 1] = z.im;
+}
+
+/*
+ * Projection to SU(3): rows 1 and 2 made orthonormal by Gram-Schmidt (row 1
+ * normalised, row 2 orthogonalised against it and normalised), row 3 set to
+ * conj(row1 x row2), which gives det = 1.
+ */
+static void su3_project(double *m) {
+  cplx r0[3], r1[3];
+  double n0 = 0.0;
+  for (int b = 0; b < 3; ++b) {
+    r0[b] = mget(m, 0, b);
+    n0 += r0[b].re * r0[b].re + r0[b].im * r0[b].im;
+  }
+  n0 = 1.0 / sqrt(n0);
+  for (int b = 0; b < 3; ++b) r0[b] = cscale(n0, r0[b]);
+  cplx dot = cx(0.0, 0.0); /* <r0, r1> = sum conj(r0) r1 */
+  for (int b = 0; b < 3; ++b) {
+    r1[b] = mget(m, 1, b);
+    dot = cadd(dot, cmul(cconj(r0[b]), r1[b]));
+  }
+  double n1 = 0.0;
+  for (int b = 0; b < 3; ++b) {
+    r1[b] = csub(r1[b], cmul(dot, r0[b]));
+    n1 += r1[b].re * r1[b].re + r1[b].im * r1[b].im;
+  }
+  n1 = 1.0 / sqrt(n1);
+  for (int b = 0; b < 3; ++b) r1[b] = cscale(n1, r1[b]);
+  for (int b = 0; b < 3; ++b) {
+    mset(m, 0, b, r0[b]);
+    mset(m, 1, b, r1[b]);
+  }
+  mset(m, 2, 0, cconj(csub(cmul(r0[1], r1[2]), cmul(r0[2], r1[1]))));
+  mset(m, 2, 1, cconj(csub(cmul(r0[2], r1[0]), cmul(r0[0], r1[2]))));
+  mset(m, 2, 2, cconj(csub(cmul(r0[0], r1[1]), cmul(r0[1], r1[0]))));
+}
+
+/* Two independent standard normals for matrix i, pair j: Box-Muller on one Philox block */
+static inline void gauss2(uint32_t key[2], int64_t i, uint32_t j, uint64_t tag, double g[2]) {
+  const double two_pi = 6.283185307179586476925286766559;
+  uint32_t ctr[4] = {(uint32_t)i, ((uint32_t)((uint64_t)i >> 32) << 8) | j, (uint32_t)tag, (uint32_t)(tag >> 32)};
+  uint32_t w[4];
+  philox4x32_10(ctr, key, w);
+  double u1, u2;
+  two_uniforms(w, &u1, &u2);
+  const double rad = sqrt(-2.0 * log(u1));
+  g[0] = rad * cos(two_pi * u2);
+  g[1] = rad * sin(two_pi * u2);
+}
+
+/*
+ * n SU(3) matrices, each the projection (su3_project) of 1 + eps H with H
+ * traceless hermitian, H = (1/sqrt 2) sum_a c_a lambda_a over the Gell-Mann
+ * matrices, c_a independent N(0, 1): off-diagonal entries have Re, Im ~
+ * N(0, 1/2). Random numbers: key = seed, counter (i, pair j, tag).
+ */
+void gen_su3_near_identity(int64_t n, double eps, uint64_t seed, uint64_t tag, double *out) {
+  uint32_t key[2];
+  seed_key(seed, key);
+  const double s2 = 0.70710678118654752440, s3 = 0.57735026918962576451;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double c[8];
+    for (uint32_t j = 0; j < 4; ++j) gauss2(key, i, j, tag, c + 2 * j);
+    double *m = out + i * 18;
+    /* c[0..7] = c_1 .. c_8 */
+    const cplx h01 = cx(s2 * c[0], -s2 * c[1]);
+    const cplx h02 = cx(s2 * c[3], -s2 * c[4]);
+    const cplx h12 = cx(s2 * c[5], -s2 * c[6]);
+    const double h00 = s2 * (c[2] + s3 * c[7]);
+    const double h11 = s2 * (-c[2] + s3 * c[7]);
+    const double h22 = s2 * (-2.0 * s3 * c[7]);
+    mset(m, 0, 0, cx(1.0 + eps * h00, 0.0));
+    mset(m, 1, 1, cx(1.0 + eps * h11, 0.0));
+    mset(m, 2, 2, cx(1.0 + eps * h22, 0.0));
+    mset(m, 0, 1, cscale(eps, h01));
+    mset(m, 1, 0, cscale(eps, cconj(h01)));
+    mset(m, 0, 2, cscale(eps, h02));
+    mset(m, 2, 0, cscale(eps, cconj(h02)));
+    mset(m, 1, 2, cscale(eps, h12));
+    mset(m, 2, 1, cscale(eps, cconj(h12)));
+    su3_project(m);
+  }
+}
+
+/*
+ * n random SU(3) matrices: su3_project of a matrix with independent complex
+ * Gaussian entries (row Gram-Schmidt of a Gaussian matrix; used for random
+ * gauge transformations).
+ */
+void gen_su3_random(int64_t n, uint64_t seed, uint64_t tag, double *out) {
+  uint32_t key[2];
+  seed_key(seed, key);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double g[18];
+    for (uint32_t j = 0; j < 9; ++j) gauss2(key, i, j, tag, g + 2 * j);
+    double *m = out + i * 18;
+    for (int e = 0; e < 18; ++e) m[e] = g[e];
+    su3_project(m);
+  }
+}
+
+static inline void mmul(const double *a, const double *b, double *c) { /* c = a b */
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k) {
+      cplx s = cx(0.0, 0.0);
+      for (int j = 0; j < 3; ++j) s = cadd(s, cmul(mget(a, i, j), mget(b, j, k)));
+      mset(c, i, k, s);
+    }
+}
+static inline void mmul_dag_right(const double *a, const double *b, double *c) { /* c = a b^dagger */
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k) {
+      cplx s = cx(0.0, 0.0);
+      for (int j = 0; j < 3; ++j) s = cadd(s, cmul(mget(a, i, j), cconj(mget(b, k, j))));
+      mset(c, i, k, s);
+    }
+}
+static inline void mmul_dag_left(const double *a, const double *b, double *c) { /* c = a^dagger b */
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k) {
+      cplx s = cx(0.0, 0.0);
+      for (int j = 0; j < 3; ++j) s = cadd(s, cmul(cconj(mget(a, j, i)), mget(b, j, k)));
+      mset(c, i, k, s);
+    }
+}
+
+static inline int64_t site4(const int L[4], const int c[4]) {
+  return c[0] + (int64_t)L[0] * (c[1] + (int64_t)L[1] * (c[2] + (int64_t)L[2] * c[3]));
+}
+
+/*
+ * One APE smearing step on a periodic 4d lattice, all links from the old
+ * field (no ordering dependence): V = (1 - alpha) U_x^mu + (alpha / 6) S_x^mu,
+ *   S_x^mu = sum_{nu != mu} [ U_x^nu U_{x+nu}^mu U_{x+mu}^nu^dagger
+ *                           + U_{x-nu}^nu^dagger U_{x-nu}^mu U_{x-nu+mu}^nu ],
+ * then Uout_x^mu = su3_project(V).
+ */
+void ape_smear_4d(const int L[4], double alpha, const double *Uin, double *Uout) {
+  const int64_t V = (int64_t)L[0] * L[1] * L[2] * L[3];
+#pragma omp parallel for schedule(static)
+  for (int64_t q = 0; q < V * 4; ++q) {
+    const int64_t x = q / 4;
+    const int mu = (int)(q % 4);
+    int c[4];
+    int64_t r = x;
+    for (int k = 0; k < 4; ++k) {
+      c[k] = (int)(r % L[k]);
+      r /= L[k];
+    }
+    double S[18] = {0}, t1[18], t2[18];
+    for (int nu = 0; nu < 4; ++nu) {
+      if (nu == mu) continue;
+      int cp[4], cm[4], cpm[4], cmn[4];
+      for (int k = 0; k < 4; ++k) cp[k] = cm[k] = cpm[k] = cmn[k] = c[k];
+      cp[nu] = (c[nu] + 1) % L[nu];              /* x + nu */
+      cm[mu] = (c[mu] + 1) % L[mu];              /* x + mu */
+      cmn[nu] = (c[nu] - 1 + L[nu]) % L[nu];     /* x - nu */
+      cpm[nu] = cmn[nu];
+      cpm[mu] = (c[mu] + 1) % L[mu];             /* x - nu + mu */
+      const double *Uxn = Uin + (x * 4 + nu) * 18;
+      const double *Uxpn_mu = Uin + (site4(L, cp) * 4 + mu) * 18;
+      const double *Uxpm_nu = Uin + (site4(L, cm) * 4 + nu) * 18;
+      const double *Uxmn_nu = Uin + (site4(L, cmn) * 4 + nu) * 18;
+      const double *Uxmn_mu = Uin + (site4(L, cmn) * 4 + mu) * 18;
+      const double *Uxmnpm_nu = Uin + (site4(L, cpm) * 4 + nu) * 18;
+      mmul(Uxn, Uxpn_mu, t1);
+      mmul_dag_right(t1, Uxpm_nu, t2);
+      for (int e = 0; e < 18; ++e) S[e] += t2[e];
+      mmul_dag_left(Uxmn_nu, Uxmn_mu, t1);
+      mmul(t1, Uxmnpm_nu, t2);
+      for (int e = 0; e < 18; ++e) S[e] += t2[e];
+    }
+    double *o = Uout + q * 18;
+    const double *u = Uin + q * 18;
+    for (int e = 0; e < 18; ++e) o[e] = (1.0 - alpha) * u[e] + (alpha / 6.0) * S[e];
+    su3_project(o);
+  }
+}

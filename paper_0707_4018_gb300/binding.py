@@ -164,12 +164,17 @@ def mg_default_params(**overrides) -> mg_params:
 
 def mg_dslash(U: torch.Tensor, inp: torch.Tensor, out: torch.Tensor, m: float, dims, precision: int = MG_FP64,
               stream=None):
-    """out = D(U) inp on the fine lattice (asynchronous on the stream)."""
+    """out = D(U) inp on the fine lattice (asynchronous on the stream). ``dims`` of length 2:
+    U(1) in 2d (2 spins); of length 4: SU(3) in 4d (U[x][mu][3][3], psi[x][4][3])."""
     dt = torch.complex128 if precision == MG_FP64 else torch.complex64
-    V = int(dims[0]) * int(dims[1])
-    g = make_geom(dims)
-    _check(load().mg_dslash(ctypes.byref(g), _ptr(U, dt, 2 * V), float(m), _ptr(inp, dt, 2 * V),
-                            _ptr(out, dt, 2 * V), precision, _stream(stream)))
+    V = 1
+    for L in dims:
+        V *= int(L)
+    four = len(dims) == 4
+    g = make_geom(dims, Nc=3 if four else 1)
+    nu, npsi = (36 * V, 12 * V) if four else (2 * V, 2 * V)
+    _check(load().mg_dslash(ctypes.byref(g), _ptr(U, dt, nu), float(m), _ptr(inp, dt, npsi),
+                            _ptr(out, dt, npsi), precision, _stream(stream)))
 
 
 def mg_smooth_fine_noalloc(U: torch.Tensor, b: torch.Tensor, x: torch.Tensor, m: float, dims, nu: int,

@@ -149,6 +149,12 @@ struct Geo2 {
   long long nsites;
 };
 
+// periodic 4d lattice, x = x0 + L0 (x1 + L1 (x2 + L2 x3)); fewer than 2^31 sites
+struct Geo4 {
+  int L[4];
+  long long nsites;
+};
+
 // fine level (extents L0 x L1, nint dofs per site) blocked by B0 x B1 into a
 // coarse level of extents nb0 x nb1; a block holds bvol = B0*B1 sites and
 // Nb = bvol * nint dofs ordered (in-block site s, internal dof a) -> s*nint + a.

@@ -47,6 +47,12 @@ template <typename R>
 void launch_dslash(const Cx<R> *U, const Cx<R> *in, Cx<R> *out, Geo2 g, double diag, const Cx<R> *b, double a,
                    double c, cudaStream_t s, int nvec = 1, const double *shift = nullptr);
 
+// ---- fine Wilson operator (4d, SU(3), DeGrand-Rossi gammas) ----
+// out = a * D in + c * b on psi[x][4][3], U[x][4][3][3]; diagonal `diag` = 4 + m (+ shift[v])
+template <typename R>
+void launch_dslash4(const Cx<R> *U, const Cx<R> *in, Cx<R> *out, Geo4 g, double diag, const Cx<R> *b, double a,
+                    double c, cudaStream_t s, int nvec = 1, const double *shift = nullptr);
+
 // ---- coarse stencil operator, N x N blocks, internal layout Y[j][dir][col][row] ----
 // out = a * A in + c * b; with `shift`, vector v sees A + shift[v] * identity
 template <typename R>

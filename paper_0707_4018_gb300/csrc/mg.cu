@@ -1266,12 +1266,31 @@ void mg_destroy(mg_ctx *c) {
 int mg_dslash(const mg_geom *g, const void *U, double m, const void *in, void *out, int precision, void *stream) {
   return guarded([&] {
     if (!g) fail(MG_ERR_INVALID_ARG, "null geometry");
-    if (g->d != 2 || g->Nc != 1) fail(MG_ERR_UNSUPPORTED, "only d = 2, Nc = 1 is built");
-    if (g->dims[0] < 2 || g->dims[1] < 2) fail(MG_ERR_INVALID_ARG, "lattice extents must be >= 2");
+    if (!((g->d == 2 && g->Nc == 1) || (g->d == 4 && g->Nc == 3)))
+      fail(MG_ERR_UNSUPPORTED, "built: d = 2 with Nc = 1, d = 4 with Nc = 3");
+    long long vol = 1;
+    for (int mu = 0; mu < g->d; ++mu) {
+      if (g->dims[mu] < 2) fail(MG_ERR_INVALID_ARG, "lattice extents must be >= 2");
+      vol *= g->dims[mu];
+    }
+    if (vol >= (1LL << 31)) fail(MG_ERR_INVALID_ARG, "lattice volume must be below 2^31 sites");
     need_ptr(U);
     need_ptr(in);
     need_ptr(out);
     if (in == out) fail(MG_ERR_INVALID_ARG, "in and out must not alias");
+    if (g->d == 4) {
+      Geo4 g4{{g->dims[0], g->dims[1], g->dims[2], g->dims[3]}, vol};
+      cudaStream_t s4 = static_cast<cudaStream_t>(stream);
+      if (precision == MG_FP64)
+        launch_dslash4<double>(static_cast<const Cx<double> *>(U), static_cast<const Cx<double> *>(in),
+                               static_cast<Cx<double> *>(out), g4, 4.0 + m, nullptr, 1.0, 0.0, s4);
+      else if (precision == MG_FP32)
+        launch_dslash4<float>(static_cast<const Cx<float> *>(U), static_cast<const Cx<float> *>(in),
+                              static_cast<Cx<float> *>(out), g4, 4.0 + m, nullptr, 1.0, 0.0, s4);
+      else
+        fail(MG_ERR_INVALID_ARG, "unknown precision");
+      return;
+    }
     Geo2 geo{g->dims[0], g->dims[1], (long long)g->dims[0] * g->dims[1]};
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (precision == MG_FP64)

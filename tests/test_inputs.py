@@ -94,3 +94,66 @@ def test_cold_start_zero_sweeps():
     assert np.all(theta == 0)
     U = inputs.links_from_angles(theta)
     assert np.all(U == 1)
+
+
+def test_su3_fields_are_special_unitary():
+    for U in (inputs.su3_near_identity(500, 0.4, 3, 1), inputs.su3_random(500, 3, 2),
+              inputs.su3_links((4, 2, 2, 4), seed=8).reshape(-1, 3, 3)):
+        np.testing.assert_allclose(U @ np.conj(np.swapaxes(U, 1, 2)), np.broadcast_to(np.eye(3), U.shape), atol=1e-14)
+        np.testing.assert_allclose(np.linalg.det(U), 1.0, atol=1e-14)
+
+
+def test_su3_near_identity_distribution():
+    # projection of 1 + eps H: to first order U = 1 + eps (H_offdiag-antihermitian part); the
+    # off-diagonal entries have mean 0 and E|U_01|^2 = eps^2 E|H_01|^2 = eps^2 (1/2 + 1/2) to O(eps^4)
+    U = inputs.su3_near_identity(200000, 0.01, 5, 1)
+    assert abs(U[:, 0, 1].mean()) < 5 * 0.01 / np.sqrt(len(U))  # five standard errors
+    np.testing.assert_allclose(np.mean(np.abs(U[:, 0, 1]) ** 2) / 0.01 ** 2, 1.0, rtol=0.02)
+
+
+def _plaquette_4d(U, dims):
+    L0, L1, L2, L3 = dims
+    G = U.reshape(L3, L2, L1, L0, 4, 3, 3)
+    tot = []
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            Un = np.roll(G[..., nu, :, :], -1, axis=3 - mu)   # U_{x+mu}^nu
+            Um = np.roll(G[..., mu, :, :], -1, axis=3 - nu)   # U_{x+nu}^mu
+            P = G[..., mu, :, :] @ Un @ np.conj(np.swapaxes(Um, -1, -2)) @ np.conj(np.swapaxes(G[..., nu, :, :], -1, -2))
+            tot.append(np.trace(P, axis1=-2, axis2=-1).real.mean() / 3)
+    return float(np.mean(tot))
+
+
+def test_ape_leaves_pure_gauge_field_unchanged():
+    # U_x^mu = Omega_x Omega_{x+mu}^dagger: every staple equals the link, so V = U and the
+    # projection of a special unitary matrix returns it
+    dims = (4, 2, 4, 2)
+    V = int(np.prod(dims))
+    om = inputs.su3_random(V, 9, 3)
+    from oracle.lattice import Lattice
+    lat = Lattice(dims)
+    U = np.empty((V, 4, 3, 3), dtype=np.complex128)
+    for mu in range(4):
+        U[:, mu] = om @ np.conj(np.swapaxes(lat.shift(om, mu, +1), 1, 2))
+    np.testing.assert_allclose(inputs.ape_smear(U, dims, 0.5, 2), U, atol=1e-13)
+    assert abs(_plaquette_4d(U, dims) - 1.0) < 1e-13
+
+
+def test_ape_smoothing_raises_plaquette():
+    dims = (4, 4, 2, 4)
+    U0 = inputs.su3_links(dims, seed=2, ape_steps=0)
+    p = [_plaquette_4d(inputs.ape_smear(U0, dims, 0.5, k), dims) for k in range(4)]
+    assert all(b > a for a, b in zip(p, p[1:])), p
+
+
+def test_su3_generators_thread_count_independent():
+    code = ("import inputs, sys; U = inputs.su3_links((4, 4, 2, 6), seed=7); "
+            "sys.stdout.write(inputs.field_digest(U))")
+    env = dict(os.environ)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env["PYTHONPATH"] = root + os.pathsep + env.get("PYTHONPATH", "")
+    outs = []
+    for nt in ("1", "3"):
+        env["OMP_NUM_THREADS"] = nt
+        outs.append(subprocess.check_output([sys.executable, "-c", code], env=env, cwd=root).decode())
+    assert outs[0] == outs[1]

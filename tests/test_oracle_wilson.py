@@ -144,3 +144,39 @@ def test_sampled_apply_matches_whole_field_apply():
     sites = np.array([0, 5, 11, 12, 59, 119])
     np.testing.assert_allclose(wilson.apply_D_at(U, psi, 0.3, lat, sites),
                                wilson.apply_D(U, psi, 0.3, lat)[sites], atol=1e-14)
+
+
+def test_gamma5_hermiticity_4d_su3():
+    dims = (4, 2, 4, 6)
+    lat = Lattice(dims)
+    U = inputs.su3_random(lat.volume * 4, 4, 0x11).reshape(-1, 4, 3, 3)
+    m = -0.3
+    phi = inputs.gaussian_spinor(lat.volume, 12, 11, 1)
+    psi = inputs.gaussian_spinor(lat.volume, 12, 11, 2)
+    g5Dg5psi = wilson.apply_gamma5(wilson.apply_D(U, wilson.apply_gamma5(psi, lat, 3), m, lat), lat, 3)
+    lhs = np.vdot(phi, g5Dg5psi)
+    rhs = np.vdot(wilson.apply_D(U, phi, m, lat), psi)
+    assert abs(lhs - rhs) <= 1e-13 * abs(rhs)
+
+
+def test_gauge_covariance_4d_su3():
+    dims = (4, 4, 2, 4)
+    lat = Lattice(dims)
+    U = inputs.su3_links(dims, seed=6, ape_steps=1)
+    omega = inputs.su3_random(lat.volume, 5, 9)
+    Ug = wilson.gauge_transform(U, omega, lat)
+    psi = inputs.gaussian_spinor(lat.volume, 12, 12, 3)
+    lhs = wilson.apply_D(Ug, wilson.transform_spinor(psi, omega, lat, 3), 0.07, lat)
+    rhs = wilson.transform_spinor(wilson.apply_D(U, psi, 0.07, lat), omega, lat, 3)
+    np.testing.assert_allclose(lhs, rhs, atol=1e-13)
+
+
+def test_4d_projector_rank_two():
+    # every (1 -+ gamma_mu) of the DeGrand-Rossi basis is twice a rank-2 projector: the
+    # property that lets a 4d hop carry a half spinor
+    g, _ = wilson.gammas(4)
+    for gm in g:
+        for sgn in (+1, -1):
+            Pm = (np.eye(4) + sgn * gm) / 2
+            np.testing.assert_allclose(Pm @ Pm, Pm, atol=1e-15)
+            assert np.linalg.matrix_rank(Pm) == 2
