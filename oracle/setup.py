@@ -17,6 +17,9 @@ order of recursion):
     v - V(A v), one V-cycle error-propagation step on A x = 0 with the
     hierarchy of the previous pass, before block Gram-Schmidt and the
     Galerkin rebuild;
+  * chirality split (params.chiral_split, the 4d SU(3) hierarchy): before the
+    Gram-Schmidt of the fine level every vector v_k is replaced by the pair
+    (1 + gamma_5) v_k / 2, (1 - gamma_5) v_k / 2, giving 2 Nv coarse dofs per site;
   * recursion: after every pass on level l the next level is rebuilt from
     the new coarse operator; it receives only its first pass (relaxation,
     Gram-Schmidt, Galerkin) except after the last pass on level l, when it
@@ -29,7 +32,7 @@ import dataclasses
 
 import numpy as np
 
-from . import coarse, rng, transfer
+from . import coarse, rng, transfer, wilson
 from .lattice import Blocking, Lattice
 from .solvers import CoarsestSolver, OpCounter, mr, vcycle
 
@@ -51,6 +54,7 @@ class MGParams:
     coarsest_restart: int = 16
     coarsest_max_iter: int = 20000
     seed: int = 20070704
+    chiral_split: bool = False
 
 
 class Hierarchy:
@@ -70,7 +74,13 @@ class Hierarchy:
             lat = self.blk[l].coarse
 
     def n_int(self, level: int) -> int:
-        return self.ops[0].n_int if level == 0 else self.params.Nv[level - 1]
+        if level == 0:
+            return self.ops[0].n_int
+        return self.params.Nv[level - 1] * (2 if self.split(level - 1) else 1)
+
+    def split(self, level: int) -> bool:
+        """Chirality split of the vectors that build level + 1 (the fine level only)."""
+        return bool(self.params.chiral_split) and level == 0
 
     def restrict(self, level: int, r):
         return transfer.restrict(self.P[level], r, self.blk[level])
@@ -79,8 +89,11 @@ class Hierarchy:
         return transfer.prolong(self.P[level], e, self.blk[level], self.n_int(level))
 
     def build_level(self, level: int, vectors):
-        """Block Gram-Schmidt of ``vectors`` and Galerkin coarse operator of the next level."""
+        """Block Gram-Schmidt of ``vectors`` (after the chirality split where it applies) and
+        the Galerkin coarse operator of the next level."""
         self.vecs[level] = [np.array(v) for v in vectors]
+        if self.split(level):
+            vectors = chirality_split(vectors, self.ops[level].lat, self.ops[level].Nc)
         self.P[level], _ = transfer.block_gram_schmidt(np.stack(vectors), self.blk[level])
         Yc = coarse.galerkin(self.ops[level], self.P[level], self.blk[level])
         self.ops[level + 1] = coarse.StencilOperator(Yc, self.blk[level].coarse)
@@ -89,6 +102,23 @@ class Hierarchy:
         p = self.params
         self.coarsest = CoarsestSolver(self.ops[-1], p.coarsest_lu_max, p.coarsest_tol, p.coarsest_restart,
                                        p.coarsest_max_iter)
+
+
+def chirality_split(vectors, lat: Lattice, Nc: int):
+    """[P+ v_0, ..., P+ v_{Nv-1}, P- v_0, ..., P- v_{Nv-1}] with P+- = (1 +- gamma_5) / 2.
+
+    Applied to the fine near-null vectors before block Gram-Schmidt (a reading: the paper
+    has one vector set; the split doubles the coarse dofs, each coarse dof of one
+    chirality, so that the coarse operator inherits gamma_5-hermiticity with the coarse
+    gamma_5 = diag(1, ..., 1, -1, ..., -1)).
+    """
+    plus, minus = [], []
+    for v in vectors:
+        v = np.asarray(v, dtype=np.complex128)
+        g5v = wilson.apply_gamma5(v, lat, Nc).reshape(v.shape)
+        plus.append(0.5 * (v + g5v))
+        minus.append(0.5 * (v - g5v))
+    return plus + minus
 
 
 def initial_vectors(hier: Hierarchy, level: int):
