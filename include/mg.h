@@ -96,6 +96,9 @@ typedef struct {
   int precision;                    /* mg_precision */
   uint64_t seed;                    /* Philox4x32-10 key of the setup's random vectors */
   int max_rhs;                      /* right-hand sides one mg_solve_batch call may take (1..32) */
+  int chiral_split;                 /* 1: split every fine near-null vector into its two chirality
+                                       halves (1 +- gamma_5) / 2 before Gram-Schmidt, 2 Nv coarse dofs
+                                       per site; required (and only built) for d = 4 */
 } mg_params;
 
 typedef struct {

@@ -38,7 +38,7 @@ class mg_params(ctypes.Structure):
                 ("gcr_restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("coarsest_lu_max", ctypes.c_int),
                 ("coarsest_tol", ctypes.c_double), ("coarsest_restart", ctypes.c_int),
                 ("coarsest_max_iter", ctypes.c_int), ("precision", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("max_rhs", ctypes.c_int)]
+                ("max_rhs", ctypes.c_int), ("chiral_split", ctypes.c_int)]
 
 
 class mg_stats(ctypes.Structure):
@@ -204,19 +204,27 @@ class Context:
         self.dims = tuple(dims)
         self.params = params
         self.stream = stream
-        self.volume = int(dims[0]) * int(dims[1])
+        self.volume = 1
+        for L in dims:
+            self.volume *= int(L)
+        self.four = len(dims) == 4
+        self.n0 = self.volume * (12 if self.four else 2)  # fine-level dofs
 
     @classmethod
     def setup(cls, U: torch.Tensor, m: float, dims, params: mg_params | None = None, stream=None) -> "Context":
-        """mg_setup: adaptive setup of the hierarchy for D(U) with mass m."""
+        """mg_setup: adaptive setup of the hierarchy for D(U) with mass m (``dims`` of length 2:
+        U(1) links U[x][mu]; of length 4: SU(3) links U[x][mu][3][3], two levels, chiral_split = 1)."""
         lib = load()
         p = params if params is not None else mg_default_params()
-        g = make_geom(dims)
-        V = int(dims[0]) * int(dims[1])
+        four = len(dims) == 4
+        g = make_geom(dims, Nc=3 if four else 1)
+        V = 1
+        for L in dims:
+            V *= int(L)
         h = ctypes.c_void_p()
         s = _stream(stream)
-        _check(lib.mg_setup(ctypes.byref(h), ctypes.byref(g), _ptr(U, torch.complex128, 2 * V), float(m),
-                            ctypes.byref(p), s))
+        _check(lib.mg_setup(ctypes.byref(h), ctypes.byref(g), _ptr(U, torch.complex128, (36 if four else 2) * V),
+                            float(m), ctypes.byref(p), s))
         return cls(h, dims, p, s)
 
     def close(self):
@@ -254,7 +262,7 @@ class Context:
     def solve(self, chi: torch.Tensor, psi: torch.Tensor, tol: float, raise_on_fail: bool = True) -> dict:
         """mg_solve: psi = D^{-1} chi to relative true residual tol; returns the stats."""
         st = mg_stats()
-        n = 2 * self.volume
+        n = self.n0
         code = load().mg_solve(self._need(), _ptr(chi, torch.complex128, n), _ptr(psi, torch.complex128, n),
                                float(tol), ctypes.byref(st))
         if code != 0 and (raise_on_fail or code != 4):
@@ -266,7 +274,7 @@ class Context:
         """mg_solve_batch: psi[v] = D(m_v)^{-1} chi[v] for the nrhs = chi.shape[0] vectors
         (masses: one per vector, or None for the context mass); returns the stats per vector."""
         nrhs = int(chi.shape[0])
-        n = 2 * self.volume * nrhs
+        n = self.n0 * nrhs
         st = (mg_stats * nrhs)()
         mp = None
         if masses is not None:
@@ -333,7 +341,8 @@ class Context:
         return out
 
     def prolongator(self, level: int) -> torch.Tensor:
-        nv = self.params.Nv[level]
+        """The columns of P_level as level vectors (2 Nv of them with the chirality split)."""
+        nv = self.params.Nv[level] * (2 if self.four else 1)
         n, k = self.level_size(level)
         out = torch.empty((nv, n, k), dtype=torch.complex128, device="cuda")
         _check(load().mg_get_prolongator(self._need(), level, _ptr(out)))
@@ -341,6 +350,6 @@ class Context:
 
     def coarse_op(self, level: int) -> torch.Tensor:
         n, k = self.level_size(level)
-        out = torch.empty((n, 5, k, k), dtype=torch.complex128, device="cuda")
+        out = torch.empty((n, 9 if self.four else 5, k, k), dtype=torch.complex128, device="cuda")
         _check(load().mg_get_coarse_op(self._need(), level, _ptr(out)))
         return out

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "kernels.h"
+#include "mg4d.h"
 
 namespace mg {
 
@@ -150,8 +151,10 @@ struct mg_ctx {
   mg::GraphCache setup_vc[MG_MAX_LEVELS];
   bool graphs_ok = true;
   mg::DevBuf<mg::Cx<double>> z64;
+  mg::Engine4 *e4 = nullptr;  // the 4d SU(3) hierarchy (d = 4); the members above stay empty
   ~mg_ctx() {
     if (s) cudaStreamSynchronize(s);  // no work may still use the buffers released below
+    if (e4) mg::engine4_destroy(e4);
     for (auto &g : pre) g.reset();
     for (auto &v : preb)
       for (auto &g : v) g.reset();
@@ -1112,6 +1115,20 @@ int mg_setup(mg_ctx **ctx, const mg_geom *g, const void *U, double m, const mg_p
     if (!ctx) fail(MG_ERR_INVALID_ARG, "null context out-pointer");
     *ctx = nullptr;
     need_ptr(U);
+    if (g != nullptr && g->d == 4) {
+      validate4(g, p);
+      auto c = std::make_unique<mg_ctx>();
+      c->geom = *g;
+      c->p = *p;
+      c->m = m;
+      c->user = static_cast<cudaStream_t>(stream);
+      MG_CUDA(cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking));
+      MG_CUDA(cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming));
+      enter(*c);
+      c->e4 = engine4_create(g, U, m, p, c->s);
+      *ctx = c.release();
+      return;
+    }
     auto c = create(g, m, p, stream);
     MG_CUDA(cudaMemcpyAsync(c->U64.p, U, c->U64.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, c->s));
     if (c->p.precision == MG_FP32) launch_convert<float, double>(c->U64.p, c->U32.p, c->U64.n, c->s);
@@ -1129,6 +1146,20 @@ int mg_solve(mg_ctx *c, const void *chi, void *psi, double tol, mg_stats *st) {
     need_ctx(c);
     need_ptr(chi);
     need_ptr(psi);
+    if (c->e4) {
+      const Solve4 o = engine4_solve(*c->e4, chi, psi, tol);
+      if (st) {
+        st->iters = o.iters;
+        st->converged = o.converged ? 1 : 0;
+        st->true_rel_residual = o.rel;
+        for (int l = 0; l < MG_MAX_LEVELS; ++l) st->level_apps[l] = o.apps[l];
+        st->coarsest_iters = o.coarsest_iters;
+        st->ms = o.ms;
+        st->graphs = 0;
+      }
+      if (!o.converged) status = MG_ERR_NOT_CONVERGED;
+      return;
+    }
     check_fresh(*c);
     for (long long &a : c->apps) a = 0;
     collect_coarsest(*c);
@@ -1171,6 +1202,7 @@ int mg_solve_batch(mg_ctx *c, int nrhs, const void *chi, void *psi, const double
     need_ctx(c);
     need_ptr(chi);
     need_ptr(psi);
+    if (c->e4) fail(MG_ERR_UNSUPPORTED, "batched solves are built for d = 2");
     if (nrhs < 1 || nrhs > c->p.max_rhs) fail(MG_ERR_INVALID_ARG, "nrhs must be in [1, max_rhs]");
     check_fresh(*c);
     if (c->bZ.p == nullptr) alloc_batch(*c);
@@ -1239,6 +1271,11 @@ static void drop_graphs(mg_ctx &c) {
 int mg_update_mass(mg_ctx *c, double m) {
   return guarded([&] {
     need_ctx(c);
+    if (c->e4) {
+      c->m = m;
+      engine4_update_mass(*c->e4, m);
+      return;
+    }
     check_fresh(*c);
     c->m = m;
     MG_CUDA(cudaStreamSynchronize(c->s));  // no replay of the old graphs is still in flight
@@ -1309,6 +1346,10 @@ int mg_level_apply(mg_ctx *c, int level, const void *in, void *out) {
     need_level(c, level, false);
     need_ptr(in);
     need_ptr(out);
+    if (c->e4) {
+      engine4_level_apply(*c->e4, level, in, out);
+      return;
+    }
     apply_op<double>(*c, level, static_cast<const Cx<double> *>(in), static_cast<Cx<double> *>(out));
     MG_CUDA(cudaStreamSynchronize(c->s));
   });
@@ -1319,6 +1360,10 @@ int mg_restrict(mg_ctx *c, int level, const void *fine, void *coarse) {
     need_level(c, level, true);
     need_ptr(fine);
     need_ptr(coarse);
+    if (c->e4) {
+      engine4_restrict(*c->e4, fine, coarse);
+      return;
+    }
     Level &L = c->lv[level];
     launch_restrict<double>(L.V64.p, static_cast<const Cx<double> *>(fine), static_cast<Cx<double> *>(coarse), L.bg,
                             L.Nv, c->s);
@@ -1331,6 +1376,10 @@ int mg_prolong(mg_ctx *c, int level, const void *coarse, void *fine) {
     need_level(c, level, true);
     need_ptr(fine);
     need_ptr(coarse);
+    if (c->e4) {
+      engine4_prolong(*c->e4, coarse, fine);
+      return;
+    }
     Level &L = c->lv[level];
     launch_zero<double>(static_cast<Cx<double> *>(fine), L.n, c->s);
     launch_prolong_add<double>(L.V64.p, static_cast<const Cx<double> *>(coarse), static_cast<Cx<double> *>(fine),
@@ -1344,6 +1393,10 @@ int mg_vcycle(mg_ctx *c, const void *b, void *x) {
     need_ctx(c);
     need_ptr(b);
     need_ptr(x);
+    if (c->e4) {
+      engine4_vcycle(*c->e4, b, x);
+      return;
+    }
     check_fresh(*c);
     precondition(*c, static_cast<const Cx<double> *>(b), static_cast<Cx<double> *>(x));
     MG_CUDA(cudaStreamSynchronize(c->s));
@@ -1355,6 +1408,7 @@ int mg_coarse_apply_mrhs(mg_ctx *c, int level, int nrhs, const void *in, void *o
     need_level(c, level, false);
     need_ptr(in);
     need_ptr(out);
+    if (c->e4) fail(MG_ERR_UNSUPPORTED, "the tensor-core apply is built for d = 2 coarse levels");
     if (level < 1) fail(MG_ERR_INVALID_ARG, "the tensor-core apply is for coarse levels (level >= 1)");
     if (nrhs < 1) fail(MG_ERR_INVALID_ARG, "nrhs must be >= 1");
     check_fresh(*c);
@@ -1384,6 +1438,13 @@ int mg_coarsest_solve(mg_ctx *c, const void *b, void *x, long long *iters, doubl
     need_ctx(c);
     need_ptr(b);
     need_ptr(x);
+    if (c->e4) {
+      float t = 0.f;
+      const long long it = engine4_coarsest_solve(*c->e4, b, x, &t);
+      if (iters) *iters = it;
+      if (ms) *ms = t;
+      return;
+    }
     check_fresh(*c);
     collect_coarsest(*c);
     cudaEvent_t e0, e1;
@@ -1409,6 +1470,11 @@ int mg_smooth(mg_ctx *c, int level, const void *b, void *x, int nu) {
     need_ptr(b);
     need_ptr(x);
     if (nu < 0) fail(MG_ERR_INVALID_ARG, "nu must be >= 0");
+    if (c->e4) {
+      if (level != 0) fail(MG_ERR_UNSUPPORTED, "the 4d hierarchy smooths on level 0 only");
+      engine4_smooth(*c->e4, b, x, nu);
+      return;
+    }
     Level &L = c->lv[level];
     (void)L;
     smooth<double>(*c, level, static_cast<const Cx<double> *>(b), static_cast<Cx<double> *>(x), nu, false);
@@ -1420,6 +1486,10 @@ int mg_build_level(mg_ctx *c, int level, const void *vectors) {
   return guarded([&] {
     need_level(c, level, true);
     need_ptr(vectors);
+    if (c->e4) {
+      engine4_build_level(*c->e4, vectors);
+      return;
+    }
     Level &L = c->lv[level];
     MG_CUDA(cudaMemcpyAsync(L.nullv.p, vectors, L.nullv.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, c->s));
     build_level(*c, level);
@@ -1437,6 +1507,10 @@ int mg_get_null_vectors(mg_ctx *c, int level, void *out) {
   return guarded([&] {
     need_level(c, level, true);
     need_ptr(out);
+    if (c->e4) {
+      engine4_get_null_vectors(*c->e4, out);
+      return;
+    }
     Level &L = c->lv[level];
     MG_CUDA(cudaMemcpyAsync(out, L.nullv.p, L.nullv.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, c->s));
     MG_CUDA(cudaStreamSynchronize(c->s));
@@ -1447,6 +1521,10 @@ int mg_get_prolongator(mg_ctx *c, int level, void *out) {
   return guarded([&] {
     need_level(c, level, true);
     need_ptr(out);
+    if (c->e4) {
+      engine4_get_prolongator(*c->e4, out);
+      return;
+    }
     Level &L = c->lv[level];
     launch_prolongator_to_canonical(L.V64.p, static_cast<Cx<double> *>(out), L.bg, L.Nv, c->s);
     MG_CUDA(cudaStreamSynchronize(c->s));
@@ -1458,6 +1536,10 @@ int mg_get_coarse_op(mg_ctx *c, int level, void *out) {
     need_level(c, level, false);
     if (level < 1) fail(MG_ERR_INVALID_ARG, "level 0 has no stencil blocks");
     need_ptr(out);
+    if (c->e4) {
+      engine4_get_coarse_op(*c->e4, out);
+      return;
+    }
     Level &L = c->lv[level];
     launch_coarse_to_canonical(L.Y64.p, static_cast<Cx<double> *>(out), L.geo.nsites, L.nint, c->s);
     MG_CUDA(cudaStreamSynchronize(c->s));
@@ -1467,6 +1549,10 @@ int mg_get_coarse_op(mg_ctx *c, int level, void *out) {
 int mg_level_size(mg_ctx *c, int level, long long *n_sites, int *n_int) {
   return guarded([&] {
     need_level(c, level, false);
+    if (c->e4) {
+      engine4_level_size(*c->e4, level, n_sites, n_int);
+      return;
+    }
     if (n_sites) *n_sites = c->lv[level].geo.nsites;
     if (n_int) *n_int = c->lv[level].nint;
   });

@@ -1,0 +1,527 @@
+// Engine of the 4d SU(3) two-level adaptive multigrid (paper: the adaptive
+// setup with Eq. relax and Eq. P1, Eq. Galerkin, the five V-cycle steps with
+// an exact coarse solve; the four-dimensional case of its outlook).
+//
+//   setup: Nv Gaussian vectors (Philox, keyed by seed, vector, dof) relaxed by
+//          nu_setup MR iterations on D v = 0; split by chirality
+//          ((1 +- gamma_5) / 2, 2 Nv coarse dofs); block Gram-Schmidt (FP64);
+//          Galerkin P^dagger D P (FP64); passes 2..n_pass: v <- v - V(D v).
+//   V-cycle (FP64, or FP32 for MG_FP32): MR pre-smoothing from 0, residual,
+//          restriction, coarse solve (FP64 GCR to coarsest_tol), prolongation
+//          and correction, residual, MR post-smoothing.
+//   solve: FP64 flexible GCR with the V-cycle as right preconditioner and the
+//          true residual at every restart.
+#include <algorithm>
+#include <cmath>
+#include <memory>
+#include <vector>
+
+#include "mg4d.h"
+
+namespace mg {
+
+struct Engine4 {
+  mg_geom geom{};
+  mg_params p{};
+  double m = 0.0;
+  cudaStream_t s = nullptr;
+  bool f32 = false;
+  Geo4 fg{};
+  Block4 bg{};
+  Coarse4 cg{};
+  long long nf = 0, nc = 0;  // fine / coarse dofs
+  int N = 0;
+  DevBuf<Cx<double>> U64, nullv, V64, Y64;
+  DevBuf<Cx<float>> U32, V32, Y32;
+  // V-cycle work
+  DevBuf<Cx<double>> vr64, vAr64, vx64, vb64;
+  DevBuf<Cx<float>> vr32, vAr32, vx32, vb32;
+  DevBuf<Cx<double>> cb, cx;  // coarse right-hand side / solution (FP64)
+  DevBuf<Cx<float>> cb32, cx32;
+  DevBuf<Cx<double>> cZ, cW, cr;  // coarse GCR
+  DevBuf<Cx<double>> oZ, oW, orr, t64;  // outer GCR, setup scratch
+  DevBuf<double> partials, scal;
+  DevBuf<unsigned int> tickets;
+  ReduceWs ws{};
+  double *host = nullptr;  // pinned: [0, 256) outer, [256, 512) coarse
+  long long apps[MG_MAX_LEVELS] = {0, 0, 0, 0};
+  long long coarsest_iters = 0;
+  ~Engine4() {
+    if (s) cudaStreamSynchronize(s);
+    if (host) cudaFreeHost(host);
+  }
+};
+
+namespace {
+
+constexpr int kScalOuter = 0, kScalCoarse = 256, kScalMr = 512, kScalCount = 640;
+
+double diag4(const Engine4 &e) { return 4.0 + e.m; }
+
+template <typename R>
+const Cx<R> *U_of(const Engine4 &e);
+template <>
+const Cx<double> *U_of<double>(const Engine4 &e) { return e.U64.p; }
+template <>
+const Cx<float> *U_of<float>(const Engine4 &e) { return e.U32.p; }
+template <typename R>
+const Cx<R> *V_of(const Engine4 &e);
+template <>
+const Cx<double> *V_of<double>(const Engine4 &e) { return e.V64.p; }
+template <>
+const Cx<float> *V_of<float>(const Engine4 &e) { return e.V32.p; }
+
+// out = a D in + c b on the fine lattice
+template <typename R>
+void fine_apply(Engine4 &e, const Cx<R> *in, Cx<R> *out, const Cx<R> *b = nullptr, double a = 1.0, double c = 0.0) {
+  launch_dslash4<R>(U_of<R>(e), in, out, e.fg, diag4(e), b, a, c, e.s);
+  ++e.apps[0];
+}
+
+void coarse_apply64(Engine4 &e, const Cx<double> *in, Cx<double> *out, const Cx<double> *b = nullptr, double a = 1.0,
+                    double c = 0.0) {
+  launch_coarse4_apply<double>(e.Y64.p, in, out, e.cg, b, a, c, e.s);
+  ++e.apps[1];
+}
+
+struct Gcr {
+  int iters = 0;
+  bool converged = false;
+  double rel = 0.0;
+};
+
+// Flexible GCR (FP64) for A x = b with right preconditioner z = M r; x starts at 0.
+// Classical Gram-Schmidt coefficients from one fused reduction, a second projection
+// when |w - W beta|^2 shows cancellation, the residual norm |r|^2 - |alpha|^2 from a
+// fresh |r|^2, and the true residual b - A x at every restart.
+template <typename ApplyF, typename PrecF>
+Gcr fgcr(Engine4 &e, ApplyF &&apply, PrecF &&prec, const Cx<double> *b, Cx<double> *x, long long n, double tol,
+         int restart, int max_iter, Cx<double> *Z, Cx<double> *W, Cx<double> *r, int slot) {
+  double *dots = e.scal.p + slot;
+  double *h = e.host + slot;
+  Gcr out;
+  auto fetch = [&](int count) {
+    MG_CUDA(cudaMemcpyAsync(h, dots, count * sizeof(double), cudaMemcpyDeviceToHost, e.s));
+    MG_CUDA(cudaStreamSynchronize(e.s));
+    for (int i = 0; i < count; ++i)
+      if (std::isnan(h[i])) fail(MG_ERR_NAN, "GCR: NaN in a reduction");
+  };
+  launch_zero<double>(x, n, e.s);
+  launch_copy<double>(b, r, n, e.s);
+  launch_norm2<double>(b, n, dots, e.ws, e.s);
+  fetch(1);
+  const double bn2 = h[0];
+  if (!(bn2 > 0.0)) {
+    out.converged = true;
+    return out;
+  }
+  double rel = 1.0;
+  while (out.iters < max_iter) {
+    int k = 0;
+    for (; k < restart && out.iters < max_iter; ++k) {
+      Cx<double> *z = Z + (long long)k * n, *w = W + (long long)k * n;
+      prec(r, z);
+      apply(z, w);
+      launch_gcr_dots(W, w, r, k, n, dots, e.ws, e.s);
+      fetch(2 * (k + 3));
+      const double rr = h[2 * k + 4];
+      double nw0 = h[2 * k], nw2 = nw0;
+      for (int j = 0; j < k; ++j) nw2 -= h[2 * j] * h[2 * j] + h[2 * j + 1] * h[2 * j + 1];
+      double wr = h[2 * k + 2], wi = h[2 * k + 3];
+      if (k > 0 && !(nw2 > 0.5 * nw0)) {
+        launch_gcr_project_update(W, w, Z, z, k, dots, 1.0, 0.0, 0.0, x, r, n, false, e.s);
+        launch_gcr_dots(W, w, r, k, n, dots, e.ws, e.s);
+        fetch(2 * (k + 3));
+        nw0 = h[2 * k];
+        nw2 = nw0;
+        for (int j = 0; j < k; ++j) nw2 -= h[2 * j] * h[2 * j] + h[2 * j + 1] * h[2 * j + 1];
+        wr = h[2 * k + 2];
+        wi = h[2 * k + 3];
+      }
+      if (!(nw2 > 1e-28 * nw0)) break;
+      const double inv = 1.0 / std::sqrt(nw2);
+      const double are = wr * inv, aim = wi * inv;
+      launch_gcr_project_update(W, w, Z, z, k, dots, inv, are, aim, x, r, n, true, e.s);
+      ++out.iters;
+      rel = std::sqrt(std::max(rr - (are * are + aim * aim), 0.0) / bn2);
+      if (rel <= tol) {
+        ++k;
+        break;
+      }
+    }
+    apply(x, r, b);  // r = b - A x
+    launch_norm2<double>(r, n, dots, e.ws, e.s);
+    fetch(1);
+    rel = std::sqrt(h[0] / bn2);
+    if (rel <= tol) {
+      out.converged = true;
+      break;
+    }
+    if (k == 0) break;
+  }
+  out.rel = rel;
+  return out;
+}
+
+// coarse solve (FP64 GCR to coarsest_tol): cx = A_c^{-1} cb
+long long coarse_solve(Engine4 &e) {
+  auto apply = [&](const Cx<double> *in, Cx<double> *out, const Cx<double> *b = nullptr) {
+    if (b != nullptr)
+      coarse_apply64(e, in, out, b, -1.0, 1.0);
+    else
+      coarse_apply64(e, in, out);
+  };
+  auto prec = [&](const Cx<double> *r, Cx<double> *z) { launch_copy<double>(r, z, e.nc, e.s); };
+  Gcr g = fgcr(e, apply, prec, e.cb.p, e.cx.p, e.nc, e.p.coarsest_tol, e.p.coarsest_restart, e.p.coarsest_max_iter,
+               e.cZ.p, e.cW.p, e.cr.p, kScalCoarse);
+  e.coarsest_iters += g.iters;
+  return g.iters;
+}
+
+// x (+)= nu MR iterations on D e = r (r updated to the recurrence residual)
+template <typename R>
+void mr_fine(Engine4 &e, Cx<R> *x, Cx<R> *r, Cx<R> *Ar, int nu) {
+  double *sc = e.scal.p + kScalMr;
+  for (int it = 0; it < nu; ++it) {
+    fine_apply<R>(e, r, Ar);
+    launch_dot_norm<R>(Ar, r, e.nf, sc, e.ws, e.s);
+    launch_mr_update<R>(sc, e.p.omega, x, r, Ar, e.nf, e.s);
+  }
+}
+
+template <typename R>
+struct VWork;
+template <>
+struct VWork<double> {
+  static Cx<double> *r(Engine4 &e) { return e.vr64.p; }
+  static Cx<double> *Ar(Engine4 &e) { return e.vAr64.p; }
+  static Cx<double> *x(Engine4 &e) { return e.vx64.p; }
+  static Cx<double> *b(Engine4 &e) { return e.vb64.p; }
+};
+template <>
+struct VWork<float> {
+  static Cx<float> *r(Engine4 &e) { return e.vr32.p; }
+  static Cx<float> *Ar(Engine4 &e) { return e.vAr32.p; }
+  static Cx<float> *x(Engine4 &e) { return e.vx32.p; }
+  static Cx<float> *b(Engine4 &e) { return e.vb32.p; }
+};
+
+// FP64 <-> cycle precision
+template <typename R>
+void from64(Engine4 &e, const Cx<double> *src, Cx<R> *dst, long long n);
+template <>
+void from64<double>(Engine4 &e, const Cx<double> *src, Cx<double> *dst, long long n) {
+  launch_copy<double>(src, dst, n, e.s);
+}
+template <>
+void from64<float>(Engine4 &e, const Cx<double> *src, Cx<float> *dst, long long n) {
+  launch_convert<float, double>(src, dst, n, e.s);
+}
+template <typename R>
+void to64(Engine4 &e, const Cx<R> *src, Cx<double> *dst, long long n);
+template <>
+void to64<double>(Engine4 &e, const Cx<double> *src, Cx<double> *dst, long long n) {
+  launch_copy<double>(src, dst, n, e.s);
+}
+template <>
+void to64<float>(Engine4 &e, const Cx<float> *src, Cx<double> *dst, long long n) {
+  launch_convert<double, float>(src, dst, n, e.s);
+}
+
+// x = V b (b, x FP64; the cycle runs in R)
+template <typename R>
+void vcycle(Engine4 &e, const Cx<double> *b64, Cx<double> *x64) {
+  Cx<R> *r = VWork<R>::r(e), *Ar = VWork<R>::Ar(e), *x = VWork<R>::x(e), *b = VWork<R>::b(e);
+  from64<R>(e, b64, b, e.nf);
+  // 1. pre-smoothing from x = 0
+  launch_zero<R>(x, e.nf, e.s);
+  launch_copy<R>(b, r, e.nf, e.s);
+  mr_fine<R>(e, x, r, Ar, e.p.nu_pre);
+  // 2. residual and restriction
+  fine_apply<R>(e, x, r, b, -1.0, 1.0);
+  Cx<R> *rc = sizeof(R) == 8 ? reinterpret_cast<Cx<R> *>(e.cb.p) : reinterpret_cast<Cx<R> *>(e.cb32.p);
+  launch_restrict4<R>(V_of<R>(e), r, rc, e.bg, e.s);
+  if (sizeof(R) == 4) to64<R>(e, rc, e.cb.p, e.nc);
+  // 3. coarse solve
+  coarse_solve(e);
+  // 4. prolongation and correction
+  Cx<R> *ec = sizeof(R) == 8 ? reinterpret_cast<Cx<R> *>(e.cx.p) : reinterpret_cast<Cx<R> *>(e.cx32.p);
+  if (sizeof(R) == 4) from64<R>(e, e.cx.p, ec, e.nc);
+  launch_prolong4<R>(V_of<R>(e), ec, x, e.bg, e.s);
+  // 5. post-smoothing on the new residual
+  fine_apply<R>(e, x, r, b, -1.0, 1.0);
+  mr_fine<R>(e, x, r, Ar, e.p.nu_post);
+  to64<R>(e, x, x64, e.nf);
+}
+
+void precondition(Engine4 &e, const Cx<double> *r, Cx<double> *z) {
+  if (e.f32)
+    vcycle<float>(e, r, z);
+  else
+    vcycle<double>(e, r, z);
+}
+
+void make_fp32(Engine4 &e) {
+  if (!e.f32) return;
+  launch_convert<float, double>(e.V64.p, e.V32.p, e.V64.n, e.s);
+  launch_convert<float, double>(e.Y64.p, e.Y32.p, e.Y64.n, e.s);
+}
+
+// chirality split, block Gram-Schmidt and Galerkin operator from the current vectors
+void build(Engine4 &e) {
+  launch_gather_split4(e.nullv.p, e.nf, e.V64.p, e.bg, e.s);
+  launch_block_gs4(e.V64.p, e.bg, e.s);
+  launch_galerkin4(e.U64.p, diag4(e), e.V64.p, e.Y64.p, e.bg, e.s);
+  make_fp32(e);
+}
+
+void setup(Engine4 &e) {
+  const int Nv = e.bg.Nv;
+  double *sc = e.scal.p + kScalMr;
+  for (int k = 0; k < Nv; ++k) {
+    Cx<double> *v = e.nullv.p + (long long)k * e.nf;
+    launch_gaussian(v, e.nf, e.p.seed, k, 0, e.s);
+    // relaxation: MR on D x = 0 from x = v (r = -D v)
+    fine_apply<double>(e, v, e.vr64.p, nullptr, -1.0, 0.0);
+    for (int it = 0; it < e.p.nu_setup; ++it) {
+      fine_apply<double>(e, e.vr64.p, e.vAr64.p);
+      launch_dot_norm<double>(e.vAr64.p, e.vr64.p, e.nf, sc, e.ws, e.s);
+      launch_mr_update<double>(sc, e.p.omega, v, e.vr64.p, e.vAr64.p, e.nf, e.s);
+    }
+  }
+  build(e);
+  for (int pass = 2; pass <= e.p.n_pass; ++pass) {
+    for (int k = 0; k < Nv; ++k) {
+      Cx<double> *v = e.nullv.p + (long long)k * e.nf;
+      fine_apply<double>(e, v, e.t64.p);
+      precondition(e, e.t64.p, e.orr.p);        // orr = V (D v)
+      launch_xmy<double>(v, e.orr.p, e.nf, e.s);  // orr = v - V (D v)
+      launch_copy<double>(e.orr.p, v, e.nf, e.s);
+    }
+    build(e);
+  }
+}
+
+}  // namespace
+
+void validate4(const mg_geom *g, const mg_params *p) {
+  if (!g || !p) fail(MG_ERR_INVALID_ARG, "null geometry or parameters");
+  if (g->Nc != 3) fail(MG_ERR_UNSUPPORTED, "d = 4 needs Nc = 3 (SU(3))");
+  long long vol = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    if (g->dims[mu] < 2) fail(MG_ERR_INVALID_ARG, "lattice extents must be >= 2");
+    vol *= g->dims[mu];
+  }
+  if (vol * 12 >= (1LL << 31)) fail(MG_ERR_UNSUPPORTED, "4d lattices are limited to fewer than 2^31 / 12 sites");
+  if (p->levels != 2) fail(MG_ERR_UNSUPPORTED, "the 4d hierarchy is built with 2 levels");
+  if (p->chiral_split != 1) fail(MG_ERR_UNSUPPORTED, "the 4d hierarchy needs chiral_split = 1");
+  if (p->precision != MG_FP64 && p->precision != MG_FP32) fail(MG_ERR_INVALID_ARG, "unknown precision");
+  if (p->n_pass < 1 || p->nu_pre < 0 || p->nu_post < 0 || p->nu_setup < 0) fail(MG_ERR_INVALID_ARG, "bad counts");
+  if (p->gcr_restart < 1 || p->gcr_restart > 128) fail(MG_ERR_INVALID_ARG, "gcr_restart must be in [1, 128]");
+  if (p->coarsest_restart < 1 || p->coarsest_restart > 64)
+    fail(MG_ERR_INVALID_ARG, "coarsest_restart must be in [1, 64] for d = 4");
+  if (p->max_iter < 1 || p->coarsest_max_iter < 1) fail(MG_ERR_INVALID_ARG, "iteration limits must be >= 1");
+  int bvol = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    const int B = p->block[0][mu];
+    if (B < 1 || g->dims[mu] % B) fail(MG_ERR_INVALID_ARG, "level 0: extents not divisible by the block");
+    bvol *= B;
+  }
+  if (bvol > 512) fail(MG_ERR_UNSUPPORTED, "4d blocks are limited to 512 sites");
+  if (p->Nv[0] < 1 || p->Nv[0] > 32 || p->Nv[0] > 6 * bvol)
+    fail(MG_ERR_INVALID_ARG, "level 0: Nv must be in [1, min(6 x block sites, 32)]");
+}
+
+Engine4 *engine4_create(const mg_geom *g, const void *U, double m, const mg_params *p, cudaStream_t s) {
+  validate4(g, p);
+  auto e = std::make_unique<Engine4>();
+  e->geom = *g;
+  e->p = *p;
+  e->m = m;
+  e->s = s;
+  e->f32 = p->precision == MG_FP32;
+  long long vol = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    e->fg.L[mu] = g->dims[mu];
+    e->bg.L[mu] = g->dims[mu];
+    e->bg.B[mu] = p->block[0][mu];
+    e->bg.nb[mu] = g->dims[mu] / p->block[0][mu];
+    e->cg.nb[mu] = e->bg.nb[mu];
+    vol *= g->dims[mu];
+  }
+  e->fg.nsites = vol;
+  e->bg.bvol = p->block[0][0] * p->block[0][1] * p->block[0][2] * p->block[0][3];
+  e->bg.nblocks = (int)(vol / e->bg.bvol);
+  e->bg.Nv = p->Nv[0];
+  e->N = 2 * p->Nv[0];
+  e->cg.N = e->N;
+  e->cg.nsites = e->bg.nblocks;
+  e->nf = vol * 12;
+  e->nc = (long long)e->bg.nblocks * e->N;
+  MG_CUDA(cudaMallocHost(&e->host, kScalCount * sizeof(double)));
+  e->U64.alloc((size_t)vol * 36);
+  e->nullv.alloc((size_t)e->bg.Nv * e->nf);
+  e->V64.alloc((size_t)e->bg.nblocks * e->N * e->bg.bvol * 6);
+  e->Y64.alloc((size_t)e->bg.nblocks * 9 * e->N * e->N);
+  e->vr64.alloc(e->nf);
+  e->vAr64.alloc(e->nf);
+  e->vx64.alloc(e->nf);
+  e->vb64.alloc(e->nf);
+  if (e->f32) {
+    e->U32.alloc(e->U64.n);
+    e->V32.alloc(e->V64.n);
+    e->Y32.alloc(e->Y64.n);
+    e->vr32.alloc(e->nf);
+    e->vAr32.alloc(e->nf);
+    e->vx32.alloc(e->nf);
+    e->vb32.alloc(e->nf);
+    e->cb32.alloc(e->nc);
+    e->cx32.alloc(e->nc);
+  }
+  e->cb.alloc(e->nc);
+  e->cx.alloc(e->nc);
+  e->cZ.alloc((size_t)p->coarsest_restart * e->nc);
+  e->cW.alloc((size_t)p->coarsest_restart * e->nc);
+  e->cr.alloc(e->nc);
+  e->oZ.alloc((size_t)p->gcr_restart * e->nf);
+  e->oW.alloc((size_t)p->gcr_restart * e->nf);
+  e->orr.alloc(e->nf);
+  e->t64.alloc(e->nf);
+  e->ws.max_blocks = 152 * 8;
+  const long long cap = std::max<long long>((long long)e->ws.max_blocks * 4, 2LL * (std::max(p->gcr_restart, p->coarsest_restart) + 3) * 64);
+  e->partials.alloc((size_t)cap + 16);
+  e->ws.capacity = cap;
+  e->ws.tickets = 160;
+  e->tickets.alloc((size_t)e->ws.tickets);
+  e->scal.alloc(kScalCount);
+  pool_ready();
+  MG_CUDA(cudaMemsetAsync(e->tickets.p, 0, e->ws.tickets * sizeof(unsigned int), s));
+  MG_CUDA(cudaMemsetAsync(e->scal.p, 0, kScalCount * sizeof(double), s));
+  e->ws.partials = e->partials.p;
+  e->ws.ticket = e->tickets.p;
+  MG_CUDA(cudaMemcpyAsync(e->U64.p, U, e->U64.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, s));
+  if (e->f32) launch_convert<float, double>(e->U64.p, e->U32.p, e->U64.n, s);
+  setup(*e);
+  MG_CUDA(cudaStreamSynchronize(s));
+  return e.release();
+}
+
+void engine4_destroy(Engine4 *e) { delete e; }
+
+Solve4 engine4_solve(Engine4 &e, const void *chi, void *psi, double tol) {
+  for (long long &a : e.apps) a = 0;
+  e.coarsest_iters = 0;
+  cudaEvent_t e0, e1;
+  MG_CUDA(cudaEventCreate(&e0));
+  MG_CUDA(cudaEventCreate(&e1));
+  MG_CUDA(cudaEventRecord(e0, e.s));
+  auto apply = [&](const Cx<double> *in, Cx<double> *out, const Cx<double> *b = nullptr) {
+    if (b != nullptr)
+      fine_apply<double>(e, in, out, b, -1.0, 1.0);
+    else
+      fine_apply<double>(e, in, out);
+  };
+  auto prec = [&](const Cx<double> *r, Cx<double> *z) { precondition(e, r, z); };
+  Gcr g = fgcr(e, apply, prec, static_cast<const Cx<double> *>(chi), static_cast<Cx<double> *>(psi), e.nf, tol,
+               e.p.gcr_restart, e.p.max_iter, e.oZ.p, e.oW.p, e.orr.p, kScalOuter);
+  MG_CUDA(cudaEventRecord(e1, e.s));
+  MG_CUDA(cudaEventSynchronize(e1));
+  Solve4 out;
+  MG_CUDA(cudaEventElapsedTime(&out.ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  out.iters = g.iters;
+  out.converged = g.converged;
+  out.rel = g.rel;
+  for (int l = 0; l < MG_MAX_LEVELS; ++l) out.apps[l] = e.apps[l];
+  out.coarsest_iters = e.coarsest_iters;
+  return out;
+}
+
+void engine4_update_mass(Engine4 &e, double m) {
+  e.m = m;
+  launch_galerkin4(e.U64.p, diag4(e), e.V64.p, e.Y64.p, e.bg, e.s);
+  make_fp32(e);
+  MG_CUDA(cudaStreamSynchronize(e.s));
+}
+
+void engine4_level_size(const Engine4 &e, int level, long long *n_sites, int *n_int) {
+  if (n_sites) *n_sites = level == 0 ? e.fg.nsites : e.cg.nsites;
+  if (n_int) *n_int = level == 0 ? 12 : e.N;
+}
+
+void engine4_level_apply(Engine4 &e, int level, const void *in, void *out) {
+  if (level == 0)
+    fine_apply<double>(e, static_cast<const Cx<double> *>(in), static_cast<Cx<double> *>(out));
+  else
+    coarse_apply64(e, static_cast<const Cx<double> *>(in), static_cast<Cx<double> *>(out));
+  MG_CUDA(cudaStreamSynchronize(e.s));
+}
+
+void engine4_restrict(Engine4 &e, const void *fine, void *coarse) {
+  launch_restrict4<double>(e.V64.p, static_cast<const Cx<double> *>(fine), static_cast<Cx<double> *>(coarse), e.bg,
+                           e.s);
+  MG_CUDA(cudaStreamSynchronize(e.s));
+}
+
+void engine4_prolong(Engine4 &e, const void *coarse, void *fine) {
+  launch_zero<double>(static_cast<Cx<double> *>(fine), e.nf, e.s);
+  launch_prolong4<double>(e.V64.p, static_cast<const Cx<double> *>(coarse), static_cast<Cx<double> *>(fine), e.bg,
+                          e.s);
+  MG_CUDA(cudaStreamSynchronize(e.s));
+}
+
+void engine4_vcycle(Engine4 &e, const void *b, void *x) {
+  precondition(e, static_cast<const Cx<double> *>(b), static_cast<Cx<double> *>(x));
+  MG_CUDA(cudaStreamSynchronize(e.s));
+}
+
+void engine4_smooth(Engine4 &e, const void *b, void *x, int nu) {
+  Cx<double> *xx = static_cast<Cx<double> *>(x);
+  launch_zero<double>(xx, e.nf, e.s);
+  launch_copy<double>(static_cast<const Cx<double> *>(b), e.vr64.p, e.nf, e.s);
+  mr_fine<double>(e, xx, e.vr64.p, e.vAr64.p, nu);
+  MG_CUDA(cudaStreamSynchronize(e.s));
+}
+
+void engine4_build_level(Engine4 &e, const void *vectors) {
+  MG_CUDA(cudaMemcpyAsync(e.nullv.p, vectors, e.nullv.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, e.s));
+  build(e);
+  MG_CUDA(cudaStreamSynchronize(e.s));
+}
+
+void engine4_get_null_vectors(Engine4 &e, void *out) {
+  MG_CUDA(cudaMemcpyAsync(out, e.nullv.p, e.nullv.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, e.s));
+  MG_CUDA(cudaStreamSynchronize(e.s));
+}
+
+void engine4_get_prolongator(Engine4 &e, void *out) {
+  launch_prolongator4_to_canonical(e.V64.p, static_cast<Cx<double> *>(out), e.bg, e.s);
+  MG_CUDA(cudaStreamSynchronize(e.s));
+}
+
+void engine4_get_coarse_op(Engine4 &e, void *out) {
+  launch_coarse4_to_canonical(e.Y64.p, static_cast<Cx<double> *>(out), e.cg, e.s);
+  MG_CUDA(cudaStreamSynchronize(e.s));
+}
+
+long long engine4_coarsest_solve(Engine4 &e, const void *b, void *x, float *ms) {
+  cudaEvent_t e0, e1;
+  MG_CUDA(cudaEventCreate(&e0));
+  MG_CUDA(cudaEventCreate(&e1));
+  MG_CUDA(cudaMemcpyAsync(e.cb.p, b, e.nc * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, e.s));
+  MG_CUDA(cudaEventRecord(e0, e.s));
+  const long long it = coarse_solve(e);
+  MG_CUDA(cudaEventRecord(e1, e.s));
+  MG_CUDA(cudaMemcpyAsync(x, e.cx.p, e.nc * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, e.s));
+  MG_CUDA(cudaEventSynchronize(e1));
+  float t = 0.f;
+  MG_CUDA(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  MG_CUDA(cudaStreamSynchronize(e.s));
+  if (ms) *ms = t;
+  return it;
+}
+
+}  // namespace mg

@@ -1,0 +1,82 @@
+// Two-level adaptive multigrid for the 4d SU(3) Wilson operator (paper: the
+// adaptive setup, Eq. P1, Eq. Galerkin and the V-cycle, applied to the
+// four-dimensional case of its outlook). Internal interface between the C ABI
+// (mg.cu) and the 4d engine (mg4d.cu, mg4d_kernels.cu).
+#pragma once
+
+#include "kernels.h"
+
+namespace mg {
+
+// blocking of the fine 4d lattice: blocks of B[0] x .. x B[3] sites, coarse
+// lattice nb[mu] = L[mu] / B[mu]; Nv near-null vectors, each split by
+// chirality, so N = 2 Nv coarse dofs per site. Column c < N of a block's
+// prolongator is the chirality half chi = c / Nv of vector k = c % Nv: it lives
+// on the 6 dofs 6 chi .. 6 chi + 5 of each site (spins 2 chi, 2 chi + 1).
+struct Block4 {
+  int L[4], B[4], nb[4];
+  int bvol;     // sites per block
+  int nblocks;  // coarse sites
+  int Nv;       // vectors per chirality
+};
+
+struct Coarse4 {
+  int nb[4];
+  int N;
+  long long nsites;
+};
+
+// ---- kernels (mg4d_kernels.cu); V: [b][c][s][6] (block-major, Nh = bvol * 6 per column),
+// Y: [j][dir][col][row] with dir 0 = self, 1 + 2 mu = +mu (source j + mu), 2 + 2 mu = -mu ----
+template <typename R>
+void launch_restrict4(const Cx<R> *V, const Cx<R> *fine, Cx<R> *coarse, const Block4 &g, cudaStream_t s,
+                      int nvec = 1);
+// fine += P coarse
+template <typename R>
+void launch_prolong4(const Cx<R> *V, const Cx<R> *coarse, Cx<R> *fine, const Block4 &g, cudaStream_t s,
+                     int nvec = 1);
+// V[b][chi Nv + k] = chirality half chi of vector k (vectors [k][x][12], stride vstride)
+void launch_gather_split4(const Cx<double> *vecs, long long vstride, Cx<double> *V, const Block4 &g, cudaStream_t s);
+// modified Gram-Schmidt, twice, of the Nv columns of each (block, chirality), in place
+void launch_block_gs4(Cx<double> *V, const Block4 &g, cudaStream_t s);
+// Y = P^dagger D P (FP64) for the fine Wilson operator with diagonal `diag`
+void launch_galerkin4(const Cx<double> *U, double diag, const Cx<double> *V, Cx<double> *Y, const Block4 &g,
+                      cudaStream_t s);
+// out = a (A + shift_v) in + c b on the coarse lattice (nvec vectors, stride nsites * N)
+template <typename R>
+void launch_coarse4_apply(const Cx<R> *Y, const Cx<R> *in, Cx<R> *out, const Coarse4 &g, const Cx<R> *b, double a,
+                          double c, cudaStream_t s, int nvec = 1, const double *shift = nullptr);
+// exports: Y in [j][dir][row][col]; P as N fine vectors [c][x][12]
+void launch_coarse4_to_canonical(const Cx<double> *Yi, Cx<double> *Yc, const Coarse4 &g, cudaStream_t s);
+void launch_prolongator4_to_canonical(const Cx<double> *V, Cx<double> *out, const Block4 &g, cudaStream_t s);
+
+// ---- engine (mg4d.cu) ----
+struct Engine4;
+struct Solve4 {
+  int iters = 0;
+  bool converged = false;
+  double rel = 0.0;
+  long long apps[MG_MAX_LEVELS] = {0, 0, 0, 0};
+  long long coarsest_iters = 0;
+  float ms = 0.f;
+};
+
+void validate4(const mg_geom *g, const mg_params *p);
+// runs the full adaptive setup on stream s (U: device complex128 [x][4][3][3])
+Engine4 *engine4_create(const mg_geom *g, const void *U, double m, const mg_params *p, cudaStream_t s);
+void engine4_destroy(Engine4 *e);
+Solve4 engine4_solve(Engine4 &e, const void *chi, void *psi, double tol);
+void engine4_update_mass(Engine4 &e, double m);
+void engine4_level_size(const Engine4 &e, int level, long long *n_sites, int *n_int);
+void engine4_level_apply(Engine4 &e, int level, const void *in, void *out);
+void engine4_restrict(Engine4 &e, const void *fine, void *coarse);
+void engine4_prolong(Engine4 &e, const void *coarse, void *fine);
+void engine4_vcycle(Engine4 &e, const void *b, void *x);
+void engine4_smooth(Engine4 &e, const void *b, void *x, int nu);
+void engine4_build_level(Engine4 &e, const void *vectors);
+void engine4_get_null_vectors(Engine4 &e, void *out);
+void engine4_get_prolongator(Engine4 &e, void *out);
+void engine4_get_coarse_op(Engine4 &e, void *out);
+long long engine4_coarsest_solve(Engine4 &e, const void *b, void *x, float *ms);
+
+}  // namespace mg

@@ -1,0 +1,475 @@
+// Transfer, Gram-Schmidt, Galerkin and coarse-operator kernels of the 4d SU(3)
+// two-level multigrid (paper: Eq. P1 and the adaptive step for the block-local
+// prolongator, Eq. Galerkin for P^dagger D P, the V-cycle's restriction and
+// prolongation).
+//
+// The prolongator keeps only the nonzero chirality half of each column:
+// V[b][c][s][d6], c < N = 2 Nv, s < bvol, d6 < 6, is dof 6 chi + d6 (chi = c / Nv)
+// of site s of block b; per column Nh = 6 bvol complex, contiguous, so the block
+// reductions and the prolongation read V with unit stride.
+#include "mg4d.h"
+#include "wilson4d.cuh"
+
+namespace mg {
+
+namespace {
+
+__device__ __forceinline__ int fine_site4(const Block4 &g, int b, int s) {
+  int x = 0, stride = 1;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const int bc = b % g.nb[mu];
+    b /= g.nb[mu];
+    const int sc = s % g.B[mu];
+    s /= g.B[mu];
+    x += (bc * g.B[mu] + sc) * stride;
+    stride *= g.L[mu];
+  }
+  return x;
+}
+
+template <typename R>
+__device__ __forceinline__ void warp_sum2(R &a, R &b) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+}
+
+// sum of (a, b) over the CTA, returned to every thread (fixed order: deterministic)
+__device__ __forceinline__ void block_sum2(double &a, double &b, double (*red)[32]) {
+  warp_sum2(a, b);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) {
+    red[0][w] = a;
+    red[1][w] = b;
+  }
+  __syncthreads();
+  a = 0.0;
+  b = 0.0;
+  for (int i = 0; i < nw; ++i) {
+    a += red[0][i];
+    b += red[1][i];
+  }
+  __syncthreads();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// restriction r_c[b][c] = sum_{s, d6} conj(V[b][c][s][d6]) r[x(b, s)][6 chi + d6]:
+// the block's fine values are staged in shared memory, a warp reduces one column
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256) restrict4_kernel(const Cx<R> *__restrict__ V, const Cx<R> *__restrict__ fine,
+                                                        Cx<R> *__restrict__ coarse, Block4 g, long long fine_ld,
+                                                        long long coarse_ld) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  Cx<R> *sm = reinterpret_cast<Cx<R> *>(sm_raw);
+  const int b = blockIdx.x;
+  fine += blockIdx.y * fine_ld;
+  coarse += blockIdx.y * coarse_ld;
+  const int N = 2 * g.Nv, Nh = g.bvol * 6;
+  for (int e = threadIdx.x; e < g.bvol * 12; e += blockDim.x) {
+    const int s = e / 12, d = e - s * 12;
+    sm[e] = fine[(long long)fine_site4(g, b, s) * 12 + d];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = warp; c < N; c += nw) {
+    const int chi = c / g.Nv;
+    const Cx<R> *Vc = V + ((long long)b * N + c) * Nh;
+    R re = 0, im = 0;
+    for (int e = lane; e < Nh; e += 32) {
+      const int s = e / 6, d6 = e - s * 6;
+      const Cx<R> v = Vc[e], f = sm[s * 12 + 6 * chi + d6];
+      re += v.re * f.re + v.im * f.im;
+      im += v.re * f.im - v.im * f.re;
+    }
+    warp_sum2(re, im);
+    if (lane == 0) coarse[(long long)b * N + c] = mk(re, im);
+  }
+}
+
+// prolongation fine[x(b, s)][6 chi + d6] += sum_k V[b][chi Nv + k][s][d6] e[b][chi Nv + k]
+template <typename R>
+__global__ void __launch_bounds__(256) prolong4_kernel(const Cx<R> *__restrict__ V, const Cx<R> *__restrict__ coarse,
+                                                       Cx<R> *__restrict__ fine, Block4 g, long long fine_ld,
+                                                       long long coarse_ld) {
+  __shared__ Cx<R> es[128];
+  const int b = blockIdx.x;
+  fine += blockIdx.y * fine_ld;
+  coarse += blockIdx.y * coarse_ld;
+  const int N = 2 * g.Nv, Nh = g.bvol * 6;
+  for (int c = threadIdx.x; c < N; c += blockDim.x) es[c] = coarse[(long long)b * N + c];
+  __syncthreads();
+  for (int e = threadIdx.x; e < 2 * Nh; e += blockDim.x) {
+    const int chi = e / Nh, r = e - chi * Nh, s = r / 6, d6 = r - s * 6;
+    const Cx<R> *Vb = V + ((long long)b * N + chi * g.Nv) * Nh + r;
+    Cx<R> acc = mk((R)0, (R)0);
+    for (int k = 0; k < g.Nv; ++k) cmac(acc, Vb[(long long)k * Nh], es[chi * g.Nv + k]);
+    Cx<R> *f = fine + (long long)fine_site4(g, b, s) * 12 + 6 * chi + d6;
+    *f = *f + acc;
+  }
+}
+
+// V[b][chi Nv + k][s][d6] = vecs[k][x(b, s)][6 chi + d6]
+__global__ void gather_split4_kernel(const Cx<double> *__restrict__ vecs, long long vstride,
+                                     Cx<double> *__restrict__ V, Block4 g) {
+  const int N = 2 * g.Nv, Nh = g.bvol * 6;
+  const long long total = (long long)g.nblocks * N * Nh;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e % Nh);
+    const long long bc = e / Nh;
+    const int c = (int)(bc % N), b = (int)(bc / N);
+    const int chi = c / g.Nv, k = c - chi * g.Nv, s = r / 6, d6 = r - s * 6;
+    V[e] = vecs[k * vstride + (long long)fine_site4(g, b, s) * 12 + 6 * chi + d6];
+  }
+}
+
+// modified Gram-Schmidt in k order, run twice, on the Nv columns of one (block, chirality)
+__global__ void __launch_bounds__(256) block_gs4_kernel(Cx<double> *__restrict__ V, Block4 g) {
+  __shared__ double red[2][32];
+  const int b = blockIdx.x, chi = blockIdx.y, N = 2 * g.Nv, Nh = g.bvol * 6;
+  Cx<double> *base = V + ((long long)b * N + chi * g.Nv) * Nh;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int k = 0; k < g.Nv; ++k) {
+      Cx<double> *vk = base + (long long)k * Nh;
+      for (int j = 0; j < k; ++j) {
+        const Cx<double> *vj = base + (long long)j * Nh;
+        double re = 0.0, im = 0.0;  // <v_j, v_k>
+        for (int e = threadIdx.x; e < Nh; e += blockDim.x) {
+          const Cx<double> a = vj[e], c = vk[e];
+          re += a.re * c.re + a.im * c.im;
+          im += a.re * c.im - a.im * c.re;
+        }
+        block_sum2(re, im, red);
+        for (int e = threadIdx.x; e < Nh; e += blockDim.x) {
+          const Cx<double> a = vj[e];
+          Cx<double> c = vk[e];
+          c.re -= re * a.re - im * a.im;
+          c.im -= re * a.im + im * a.re;
+          vk[e] = c;
+        }
+      }
+      double n2 = 0.0, zero = 0.0;
+      for (int e = threadIdx.x; e < Nh; e += blockDim.x) n2 += norm2(vk[e]);
+      block_sum2(n2, zero, red);
+      const double inv = 1.0 / sqrt(n2);
+      for (int e = threadIdx.x; e < Nh; e += blockDim.x) vk[e] = inv * vk[e];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Galerkin operator: CTA (coarse site j, direction dir). For every fine site x of
+// block j that dir involves (all sites for dir 0; the forward / backward face in mu
+// for +mu / -mu) the N columns are moved through the part of D that dir denotes
+// (diagonal plus in-block hops; the hop from the neighbouring block), and the
+// rows of block j at x are contracted with them:
+//   Y[j][dir][col][row] += sum_d conj(V_row(x)_d) (D_dir V_col)(x)_d
+// ---------------------------------------------------------------------------
+constexpr int kGalPairs = 16;  // (row, col) pairs per thread: N <= 64
+
+__global__ void __launch_bounds__(256) galerkin4_kernel(const Cx<double> *__restrict__ U, double diag,
+                                                        const Cx<double> *__restrict__ V, Cx<double> *__restrict__ Y,
+                                                        Block4 g) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int N = 2 * g.Nv, Nh = g.bvol * 6;
+  Cx<double> *Hs = reinterpret_cast<Cx<double> *>(sm_raw);  // [N][12]
+  Cx<double> *Vs = Hs + N * 12;                              // [N][6]
+  const int j = blockIdx.x, dir = blockIdx.y, tid = threadIdx.x;
+  int jc[4];
+  {
+    int r = j;
+    for (int mu = 0; mu < 4; ++mu) {
+      jc[mu] = r % g.nb[mu];
+      r /= g.nb[mu];
+    }
+  }
+  const int mu = dir == 0 ? 0 : (dir - 1) >> 1;
+  const bool fwd = dir != 0 && ((dir - 1) & 1) == 0;
+  int jsrc = j;
+  if (dir != 0) {
+    int cc[4] = {jc[0], jc[1], jc[2], jc[3]};
+    cc[mu] = fwd ? (cc[mu] + 1) % g.nb[mu] : (cc[mu] + g.nb[mu] - 1) % g.nb[mu];
+    jsrc = cc[0] + g.nb[0] * (cc[1] + g.nb[1] * (cc[2] + g.nb[2] * cc[3]));
+  }
+  int bst[4], fst[4];  // in-block and fine strides
+  bst[0] = 1;
+  fst[0] = 1;
+  for (int m2 = 1; m2 < 4; ++m2) {
+    bst[m2] = bst[m2 - 1] * g.B[m2 - 1];
+    fst[m2] = fst[m2 - 1] * g.L[m2 - 1];
+  }
+  const int npairs = N * N;
+  Cx<double> acc[kGalPairs];
+#pragma unroll
+  for (int i = 0; i < kGalPairs; ++i) acc[i] = mk(0.0, 0.0);
+  const int nvisit = dir == 0 ? g.bvol : g.bvol / g.B[mu];
+  for (int q = 0; q < nvisit; ++q) {
+    // in-block position s of the q-th site (for a face: coordinate mu fixed)
+    int sc[4];
+    if (dir == 0) {
+      int r = q;
+      for (int m2 = 0; m2 < 4; ++m2) {
+        sc[m2] = r % g.B[m2];
+        r /= g.B[m2];
+      }
+    } else {
+      int r = q;
+      for (int m2 = 0; m2 < 4; ++m2) {
+        if (m2 == mu) {
+          sc[m2] = fwd ? g.B[mu] - 1 : 0;
+        } else {
+          sc[m2] = r % g.B[m2];
+          r /= g.B[m2];
+        }
+      }
+    }
+    const int s = sc[0] + bst[1] * sc[1] + bst[2] * sc[2] + bst[3] * sc[3];
+    const int x = fine_site4(g, j, s);
+    __syncthreads();  // the previous site's shared data is consumed
+    for (int e = tid; e < N * 6; e += blockDim.x) {
+      const int r = e / 6, d6 = e - r * 6;
+      Vs[e] = V[((long long)j * N + r) * Nh + s * 6 + d6];
+    }
+    if (tid < N) {
+      const int c = tid, chi = c / g.Nv;
+      Cx<double> hacc[12];
+#pragma unroll
+      for (int i = 0; i < 12; ++i) hacc[i] = mk(0.0, 0.0);
+      Cx<double> p[12];
+      auto load_col = [&](int blk, int spos) {
+#pragma unroll
+        for (int i = 0; i < 12; ++i) p[i] = mk(0.0, 0.0);
+        const Cx<double> *src = V + ((long long)blk * N + c) * Nh + spos * 6;
+#pragma unroll
+        for (int d6 = 0; d6 < 6; ++d6) p[6 * chi + d6] = src[d6];
+      };
+      Cx<double> h[12];
+      if (dir == 0) {
+        load_col(j, s);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) h[i] = diag * p[i];
+        for (int m2 = 0; m2 < 4; ++m2) {
+          if (sc[m2] + 1 < g.B[m2]) {  // x + m2 inside the block
+            load_col(j, s + bst[m2]);
+            hop_dispatch<double>(2 * m2, p, U + ((long long)x * 4 + m2) * 9, hacc);
+          }
+          if (sc[m2] > 0) {  // x - m2 inside the block
+            load_col(j, s - bst[m2]);
+            hop_dispatch<double>(2 * m2 + 1, p, U + ((long long)(x - fst[m2]) * 4 + m2) * 9, hacc);
+          }
+        }
+      } else {
+        int sn = s + (fwd ? -(g.B[mu] - 1) : (g.B[mu] - 1)) * bst[mu];  // mirror position in the source block
+        load_col(jsrc, sn);
+        const int xn = fine_site4(g, jsrc, sn);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) h[i] = mk(0.0, 0.0);
+        hop_dispatch<double>(fwd ? 2 * mu : 2 * mu + 1, p, U + ((long long)(fwd ? x : xn) * 4 + mu) * 9, hacc);
+      }
+#pragma unroll
+      for (int i = 0; i < 12; ++i) Hs[c * 12 + i] = mk(h[i].re - 0.5 * hacc[i].re, h[i].im - 0.5 * hacc[i].im);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kGalPairs; ++i) {
+      const int pr = tid + 256 * i;
+      if (pr < npairs) {
+        const int col = pr / N, row = pr - col * N, chr = row / g.Nv;
+        Cx<double> a = acc[i];
+#pragma unroll
+        for (int d6 = 0; d6 < 6; ++d6) cmac_conj(a, Vs[row * 6 + d6], Hs[col * 12 + 6 * chr + d6]);
+        acc[i] = a;
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kGalPairs; ++i) {
+    const int pr = tid + 256 * i;
+    if (pr < npairs) Y[((long long)j * 9 + dir) * npairs + pr] = acc[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// coarse apply: CTA (site j, vector v), 4 N threads: the 9 N source values in shared
+// memory, thread (q, row) sums the (dir, col) pairs p = q, q + 4, ... of its row
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void coarse4_apply_kernel(const Cx<R> *__restrict__ Y, const Cx<R> *__restrict__ in,
+                                     Cx<R> *__restrict__ out, Coarse4 g, const Cx<R> *__restrict__ b, R a, R c,
+                                     long long ldv, const double *__restrict__ shift) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int N = g.N;
+  Cx<R> *xs = reinterpret_cast<Cx<R> *>(sm_raw);  // [9][N]
+  Cx<R> *red = xs + 9 * N;                          // [4][N]
+  const int j = blockIdx.x, v = blockIdx.y;
+  in += v * ldv;
+  out += v * ldv;
+  if (b != nullptr) b += v * ldv;
+  int jc[4];
+  {
+    int r = j;
+    for (int mu = 0; mu < 4; ++mu) {
+      jc[mu] = r % g.nb[mu];
+      r /= g.nb[mu];
+    }
+  }
+  for (int e = threadIdx.x; e < 9 * N; e += blockDim.x) {
+    const int dir = e / N, col = e - dir * N;
+    int src = j;
+    if (dir != 0) {
+      const int mu = (dir - 1) >> 1;
+      int cc[4] = {jc[0], jc[1], jc[2], jc[3]};
+      cc[mu] = ((dir - 1) & 1) == 0 ? (cc[mu] + 1) % g.nb[mu] : (cc[mu] + g.nb[mu] - 1) % g.nb[mu];
+      src = cc[0] + g.nb[0] * (cc[1] + g.nb[1] * (cc[2] + g.nb[2] * cc[3]));
+    }
+    xs[e] = in[(long long)src * N + col];
+  }
+  __syncthreads();
+  const int row = threadIdx.x % N, q = threadIdx.x / N;
+  const Cx<R> *Yj = Y + (long long)j * 9 * N * N;
+  R re = 0, im = 0;
+  for (int p = q; p < 9 * N; p += 4) {
+    const Cx<R> y = Yj[(long long)p * N + row], xv = xs[p];
+    re += y.re * xv.re - y.im * xv.im;
+    im += y.re * xv.im + y.im * xv.re;
+  }
+  red[q * N + row] = mk(re, im);
+  __syncthreads();
+  if (q == 0) {
+    R sre = red[row].re + red[N + row].re + red[2 * N + row].re + red[3 * N + row].re;
+    R sim = red[row].im + red[N + row].im + red[2 * N + row].im + red[3 * N + row].im;
+    if (shift != nullptr) {
+      const R sv = (R)shift[v];
+      sre += sv * xs[row].re;
+      sim += sv * xs[row].im;
+    }
+    Cx<R> o = mk(a * sre, a * sim);
+    if (b != nullptr) {
+      const Cx<R> bb = b[(long long)j * N + row];
+      o = mk(o.re + c * bb.re, o.im + c * bb.im);
+    }
+    out[(long long)j * N + row] = o;
+  }
+}
+
+__global__ void coarse4_to_canonical_kernel(const Cx<double> *__restrict__ Yi, Cx<double> *__restrict__ Yc,
+                                            long long total, int N) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;  // canonical [j][dir][row][col]
+  if (e >= total) return;
+  const int col = (int)(e % N);
+  const long long t = e / N;
+  const int row = (int)(t % N);
+  const long long jd = t / N;
+  Yc[e] = Yi[(jd * N + col) * N + row];
+}
+
+__global__ void prolongator4_to_canonical_kernel(const Cx<double> *__restrict__ V, Cx<double> *__restrict__ out,
+                                                 Block4 g, long long nsites) {
+  const int N = 2 * g.Nv, Nh = g.bvol * 6;
+  const long long total = (long long)N * nsites * 12;
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;  // [c][x][12]
+  if (e >= total) return;
+  const int dof = (int)(e % 12);
+  const long long cx = e / 12;
+  const int x = (int)(cx % nsites), c = (int)(cx / nsites);
+  const int chi = c / g.Nv;
+  Cx<double> v = mk(0.0, 0.0);
+  if (dof / 6 == chi) {
+    int b = 0, s = 0, bstr = 1, sstr = 1, r = x;
+    for (int mu = 0; mu < 4; ++mu) {
+      const int xc = r % g.L[mu];
+      r /= g.L[mu];
+      b += (xc / g.B[mu]) * bstr;
+      s += (xc % g.B[mu]) * sstr;
+      bstr *= g.nb[mu];
+      sstr *= g.B[mu];
+    }
+    v = V[((long long)b * N + c) * Nh + s * 6 + (dof - 6 * chi)];
+  }
+  out[e] = v;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename R>
+void launch_restrict4(const Cx<R> *V, const Cx<R> *fine, Cx<R> *coarse, const Block4 &g, cudaStream_t s, int nvec) {
+  const size_t smem = (size_t)g.bvol * 12 * sizeof(Cx<R>);
+  static bool attr = false;  // one opt-in per process for more than 48 KB
+  if (!attr) {
+    MG_CUDA(cudaFuncSetAttribute(restrict4_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+    attr = true;
+  }
+  const long long nf = (long long)g.nblocks * g.bvol * 12;
+  restrict4_kernel<R><<<dim3(g.nblocks, nvec), 256, smem, s>>>(V, fine, coarse, g, nf, (long long)g.nblocks * 2 * g.Nv);
+  MG_LAUNCHED();
+}
+
+template <typename R>
+void launch_prolong4(const Cx<R> *V, const Cx<R> *coarse, Cx<R> *fine, const Block4 &g, cudaStream_t s, int nvec) {
+  const long long nf = (long long)g.nblocks * g.bvol * 12;
+  prolong4_kernel<R><<<dim3(g.nblocks, nvec), 256, 0, s>>>(V, coarse, fine, g, nf, (long long)g.nblocks * 2 * g.Nv);
+  MG_LAUNCHED();
+}
+
+void launch_gather_split4(const Cx<double> *vecs, long long vstride, Cx<double> *V, const Block4 &g, cudaStream_t s) {
+  const long long total = (long long)g.nblocks * 2 * g.Nv * g.bvol * 6;
+  const unsigned int grid = (unsigned int)std::min<long long>((total + 255) / 256, 152LL * 16);
+  gather_split4_kernel<<<grid, 256, 0, s>>>(vecs, vstride, V, g);
+  MG_LAUNCHED();
+}
+
+void launch_block_gs4(Cx<double> *V, const Block4 &g, cudaStream_t s) {
+  block_gs4_kernel<<<dim3(g.nblocks, 2), 256, 0, s>>>(V, g);
+  MG_LAUNCHED();
+}
+
+void launch_galerkin4(const Cx<double> *U, double diag, const Cx<double> *V, Cx<double> *Y, const Block4 &g,
+                      cudaStream_t s) {
+  const int N = 2 * g.Nv;
+  const size_t smem = (size_t)N * 18 * sizeof(Cx<double>);
+  galerkin4_kernel<<<dim3(g.nblocks, 9), 256, smem, s>>>(U, diag, V, Y, g);
+  MG_LAUNCHED();
+}
+
+template <typename R>
+void launch_coarse4_apply(const Cx<R> *Y, const Cx<R> *in, Cx<R> *out, const Coarse4 &g, const Cx<R> *b, double a,
+                          double c, cudaStream_t s, int nvec, const double *shift) {
+  const size_t smem = (size_t)13 * g.N * sizeof(Cx<R>);
+  coarse4_apply_kernel<R><<<dim3((unsigned int)g.nsites, nvec), 4 * g.N, smem, s>>>(
+      Y, in, out, g, b, (R)a, (R)c, g.nsites * g.N, shift);
+  MG_LAUNCHED();
+}
+
+void launch_coarse4_to_canonical(const Cx<double> *Yi, Cx<double> *Yc, const Coarse4 &g, cudaStream_t s) {
+  const long long total = g.nsites * 9 * g.N * g.N;
+  coarse4_to_canonical_kernel<<<grid_for(total, 256), 256, 0, s>>>(Yi, Yc, total, g.N);
+  MG_LAUNCHED();
+}
+
+void launch_prolongator4_to_canonical(const Cx<double> *V, Cx<double> *out, const Block4 &g, cudaStream_t s) {
+  const long long nsites = (long long)g.nblocks * g.bvol;
+  prolongator4_to_canonical_kernel<<<grid_for(2LL * g.Nv * nsites * 12, 256), 256, 0, s>>>(V, out, g, nsites);
+  MG_LAUNCHED();
+}
+
+template void launch_restrict4<double>(const Cx<double> *, const Cx<double> *, Cx<double> *, const Block4 &,
+                                       cudaStream_t, int);
+template void launch_restrict4<float>(const Cx<float> *, const Cx<float> *, Cx<float> *, const Block4 &, cudaStream_t,
+                                      int);
+template void launch_prolong4<double>(const Cx<double> *, const Cx<double> *, Cx<double> *, const Block4 &,
+                                      cudaStream_t, int);
+template void launch_prolong4<float>(const Cx<float> *, const Cx<float> *, Cx<float> *, const Block4 &, cudaStream_t,
+                                     int);
+template void launch_coarse4_apply<double>(const Cx<double> *, const Cx<double> *, Cx<double> *, const Coarse4 &,
+                                           const Cx<double> *, double, double, cudaStream_t, int, const double *);
+template void launch_coarse4_apply<float>(const Cx<float> *, const Cx<float> *, Cx<float> *, const Coarse4 &,
+                                          const Cx<float> *, double, double, cudaStream_t, int, const double *);
+
+}  // namespace mg

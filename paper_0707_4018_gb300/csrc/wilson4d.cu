@@ -24,28 +24,11 @@
 // spinors (8 per site) and links (2 reads each) come from L2, which makes the
 // on-chip traffic about 3x the HBM traffic.
 #include "kernels.h"
+#include "wilson4d.cuh"
 
 namespace mg {
 
 namespace {
-
-// A_mu psi_dn for the two lower spins (d0, d1) = (psi_2, psi_3) of one colour
-template <typename R, int MU>
-__device__ __forceinline__ void a_times(Cx<R> d0, Cx<R> d1, Cx<R> &o0, Cx<R> &o1) {
-  if (MU == 0) { o0 = times_i(d1); o1 = times_i(d0); }
-  if (MU == 1) { o0 = mk(-d1.re, -d1.im); o1 = d0; }
-  if (MU == 2) { o0 = times_i(d0); o1 = mk(d1.im, -d1.re); }
-  if (MU == 3) { o0 = d0; o1 = d1; }
-}
-
-// A_mu^dagger t for the two upper-spin components (t0, t1) of one colour
-template <typename R, int MU>
-__device__ __forceinline__ void adag_times(Cx<R> t0, Cx<R> t1, Cx<R> &o0, Cx<R> &o1) {
-  if (MU == 0) { o0 = mk(t1.im, -t1.re); o1 = mk(t0.im, -t0.re); }  // (-i t1, -i t0)
-  if (MU == 1) { o0 = t1; o1 = mk(-t0.re, -t0.im); }                // (t1, -t0)
-  if (MU == 2) { o0 = mk(t0.im, -t0.re); o1 = times_i(t1); }        // (-i t0, i t1)
-  if (MU == 3) { o0 = t0; o1 = t1; }
-}
 
 // ---------------------------------------------------------------------------
 // Warp-cooperative staging. A warp owns 32 consecutive sites. The 96-B spinors
@@ -117,70 +100,6 @@ __device__ __forceinline__ void read_spinor(const typename Stage<R>::V *sp, int 
   }
 }
 
-// One hop into the accumulators: FWD: (1 - gamma_mu) U psi_nbr; else
-// (1 + gamma_mu) U^dagger psi_nbr (the -1/2 is applied at the end).
-template <typename R, int MU, bool FWD>
-__device__ __forceinline__ void hop4(const Cx<R> (&p)[12], const Cx<R> *link, Cx<R> (&acc)[12]) {
-  Cx<R> h[2][3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    Cx<R> a0, a1;
-    a_times<R, MU>(p[6 + c], p[9 + c], a0, a1);
-    h[0][c] = FWD ? p[c] - a0 : p[c] + a0;
-    h[1][c] = FWD ? p[3 + c] - a1 : p[3 + c] + a1;
-  }
-  Cx<R> t[2][3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    t[0][a] = mk((R)0, (R)0);
-    t[1][a] = mk((R)0, (R)0);
-  }
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      if (FWD) {
-        const Cx<R> u = link[a * 3 + b];  // U_ab
-        cmac(t[0][a], u, h[0][b]);
-        cmac(t[1][a], u, h[1][b]);
-      } else {
-        const Cx<R> u = link[b * 3 + a];  // (U^dagger)_ab = conj(U_ba)
-        cmac_conj(t[0][a], u, h[0][b]);
-        cmac_conj(t[1][a], u, h[1][b]);
-      }
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    Cx<R> l0, l1;
-    adag_times<R, MU>(t[0][c], t[1][c], l0, l1);
-    acc[c] = acc[c] + t[0][c];
-    acc[3 + c] = acc[3 + c] + t[1][c];
-    if (FWD) {
-      acc[6 + c] = acc[6 + c] - l0;
-      acc[9 + c] = acc[9 + c] - l1;
-    } else {
-      acc[6 + c] = acc[6 + c] + l0;
-      acc[9 + c] = acc[9 + c] + l1;
-    }
-  }
-}
-
-// apply hop number `hop` (mu = hop / 2, forward for even hop) to the staged spinor
-template <typename R>
-__device__ __forceinline__ void hop_dispatch(int hop, const Cx<R> (&p)[12], const Cx<R> *link, Cx<R> (&acc)[12]) {
-  switch (hop) {
-    case 0: hop4<R, 0, true>(p, link, acc); break;
-    case 1: hop4<R, 0, false>(p, link, acc); break;
-    case 2: hop4<R, 1, true>(p, link, acc); break;
-    case 3: hop4<R, 1, false>(p, link, acc); break;
-    case 4: hop4<R, 2, true>(p, link, acc); break;
-    case 5: hop4<R, 2, false>(p, link, acc); break;
-    case 6: hop4<R, 3, true>(p, link, acc); break;
-    default: hop4<R, 3, false>(p, link, acc); break;
-  }
-}
-
 }  // namespace
 
 constexpr int DSLASH4_WARPS = 4;
@@ -188,7 +107,7 @@ constexpr int DSLASH4_WARPS = 4;
 // out = a (D in) + c b for vector blockIdx.y of a batch (stride ldv complex); with
 // SHIFT the diagonal of that vector is diag + shift[blockIdx.y]
 template <typename R, bool SHIFT>
-__global__ void __launch_bounds__(32 * DSLASH4_WARPS, 5) dslash4_kernel(const Cx<R> *__restrict__ U,
+__global__ void __launch_bounds__(32 * DSLASH4_WARPS, sizeof(R) == 4 ? 5 : 2) dslash4_kernel(const Cx<R> *__restrict__ U,
                                                                    const Cx<R> *__restrict__ in,
                                                                    Cx<R> *__restrict__ out, Geo4 g, R diag,
                                                                    const Cx<R> *__restrict__ b, R a, R c,

@@ -23,6 +23,12 @@ OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "mcrit.json")
 # (workload id, L, beta): 64^2 beta=6 (the small two-level case) and the 256^2 points
 # of the three-level sweep over beta in {3, 6, 10}
 FIELDS = [(0, 64, 6.0), (1, 256, 3.0), (1, 256, 6.0), (1, 256, 10.0)]
+# (workload id, dims) of the 4d SU(3) fields: projected 1 + 0.4 H links after 4 APE steps (alpha 0.5)
+FIELDS4 = [(3, (16, 16, 16, 32))]
+
+
+def key4(wid, dims):
+    return f"w{wid}_su3_" + "x".join(str(d) for d in dims)
 
 
 def key(wid, L, beta):
@@ -32,8 +38,23 @@ def key(wid, L, beta):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--only", default=None)
+    ap.add_argument("--su3", action="store_true", help="the 4d SU(3) fields only")
     args = ap.parse_args()
     table = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    if args.su3:
+        for wid, dims in FIELDS4:
+            t0 = time.time()
+            U = inputs.su3_links(dims, seed=inputs.workload_seed(wid, dims[0], 0.0))
+            t1 = time.time()
+            mc = spectrum.critical_mass(U, Lattice(dims), Nc=3)
+            t2 = time.time()
+            table[key4(wid, dims)] = dict(workload_id=wid, dims=list(dims), eps=0.4, ape_steps=4, ape_alpha=0.5,
+                                          seed=inputs.workload_seed(wid, dims[0], 0.0),
+                                          links_digest=inputs.field_digest(U), m_crit=mc,
+                                          gen_seconds=round(t1 - t0, 1), scan_seconds=round(t2 - t1, 1))
+            print(key4(wid, dims), table[key4(wid, dims)], flush=True)
+            json.dump(table, open(OUT, "w"), indent=1, sort_keys=True)
+        return
     for wid, L, beta in FIELDS:
         if args.only and args.only != f"{L},{beta:g}":
             continue

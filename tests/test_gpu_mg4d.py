@@ -1,0 +1,165 @@
+"""GPU parity of the 4d SU(3) two-level multigrid (chirality-split prolongator, 9-direction Galerkin
+operator, V-cycle, FP64 flexible-GCR solve) with the oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import inputs
+from oracle import coarse, setup, solvers, transfer, wilson
+from oracle.lattice import Lattice
+from tests._util import mcrit_table, rel_err, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def _params(block, nv, precision=0, **kw):
+    import paper_0707_4018_gb300 as mg
+    return mg.mg_default_params(levels=2, blocks=[block], Nv=[nv], precision=precision, chiral_split=1, **kw)
+
+
+def _oracle_hier(U, m, dims, block, nv, **kw):
+    p = setup.MGParams(levels=2, blocks=(block,), Nv=(nv,), chiral_split=True, **kw)
+    return setup.Hierarchy(coarse.WilsonOperator(U, m, Lattice(dims), 3), p)
+
+
+CASES = [((4, 4, 4, 8), (2, 2, 2, 2), 4), ((8, 8, 8, 8), (4, 4, 4, 4), 6), ((6, 4, 2, 4), (3, 2, 1, 2), 3)]
+
+
+@pytest.mark.parametrize("dims,block,nv", CASES)
+def test_build_level_matches_oracle(dims, block, nv):
+    import torch
+    import paper_0707_4018_gb300 as mg
+    lat = Lattice(dims)
+    U = inputs.su3_links(dims, seed=21)
+    m = 0.1
+    ctx = mg.Context.setup(to_dev(U), m, dims, _params(block, nv, n_pass=1, nu_setup=2))
+    vecs = np.stack([inputs.gaussian_spinor(lat.volume, 12, 40, k) for k in range(nv)])
+    ctx.build_level(0, to_dev(vecs))
+    hier = _oracle_hier(U, m, dims, block, nv)
+    hier.build_level(0, list(vecs))
+    # prolongator columns, as fine fields
+    P = to_host(ctx.prolongator(0))
+    want = np.stack([transfer.from_blocks(hier.P[0][:, :, c], hier.blk[0], 12) for c in range(2 * nv)])
+    assert np.abs(P - want).max() < 1e-12
+    # Galerkin stencil [j][dir][row][col]
+    Y = to_host(ctx.coarse_op(1))
+    assert Y.shape == hier.ops[1].Y.shape
+    assert np.abs(Y - hier.ops[1].Y).max() < 1e-12 * np.abs(hier.ops[1].Y).max()
+    # restriction, prolongation and the coarse apply
+    n_c, k_c = ctx.level_size(1)
+    assert (n_c, k_c) == (hier.blk[0].n_blocks, 2 * nv)
+    r = inputs.gaussian_spinor(lat.volume, 12, 41, 0)
+    rc = torch.empty((n_c, k_c), dtype=torch.complex128, device="cuda")
+    ctx.restrict(0, to_dev(r), rc)
+    assert rel_err(to_host(rc), hier.restrict(0, r)) < 1e-13
+    e = inputs.gaussian_spinor(n_c, k_c, 42, 0)
+    f = torch.empty((lat.volume, 12), dtype=torch.complex128, device="cuda")
+    ctx.prolong(0, to_dev(e), f)
+    assert rel_err(to_host(f), hier.prolong(0, e)) < 1e-13
+    y = torch.empty_like(rc)
+    ctx.level_apply(1, to_dev(e), y)
+    assert rel_err(to_host(y), hier.ops[1].apply(e)) < 1e-13
+    ctx.close()
+
+
+def test_first_pass_vectors_match_oracle():
+    # the relaxed vectors of pass 1 from the same Philox draws
+    import paper_0707_4018_gb300 as mg
+    dims, block, nv = (4, 4, 4, 8), (2, 2, 2, 2), 4
+    U = inputs.su3_links(dims, seed=22)
+    m = 0.05
+    p = _params(block, nv, n_pass=1)
+    ctx = mg.Context.setup(to_dev(U), m, dims, p)
+    got = to_host(ctx.null_vectors(0))
+    hier = _oracle_hier(U, m, dims, block, nv, seed=int(p.seed), n_pass=1)
+    want = [setup.relax_null(hier, 0, v) for v in setup.initial_vectors(hier, 0)]
+    for k in range(nv):
+        assert rel_err(got[k], want[k]) < 1e-11
+    # and the hierarchy built from them
+    hier.build_level(0, want)
+    Y = to_host(ctx.coarse_op(1))
+    assert np.abs(Y - hier.ops[1].Y).max() < 1e-10 * np.abs(hier.ops[1].Y).max()
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_vcycle_matches_oracle(precision):
+    import torch
+    import paper_0707_4018_gb300 as mg
+    dims, block, nv = (4, 4, 4, 4), (2, 2, 2, 2), 4
+    lat = Lattice(dims)
+    U = inputs.su3_links(dims, seed=23)
+    m = 0.08
+    ctx = mg.Context.setup(to_dev(U), m, dims, _params(block, nv, precision, n_pass=1, coarsest_tol=1e-13))
+    vecs = to_host(ctx.null_vectors(0))
+    hier = _oracle_hier(U, m, dims, block, nv, coarsest_tol=1e-13, coarsest_lu_max=0)
+    hier.build_level(0, list(vecs))
+    hier.prepare_coarsest()
+    b = inputs.gaussian_spinor(lat.volume, 12, 43, 0)
+    x = torch.empty((lat.volume, 12), dtype=torch.complex128, device="cuda")
+    ctx.vcycle(to_dev(b), x)
+    want = solvers.vcycle(hier, 0, b)
+    assert rel_err(to_host(x), want) < (1e-10 if precision == 0 else 1e-5)
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_matches_dense_lu(precision):
+    import torch
+    import paper_0707_4018_gb300 as mg
+    dims, block, nv = (4, 4, 4, 4), (2, 2, 2, 2), 4
+    lat = Lattice(dims)
+    U = inputs.su3_links(dims, seed=11)
+    m = 0.05
+    ctx = mg.Context.setup(to_dev(U), m, dims, _params(block, nv, precision, n_pass=2, coarsest_tol=0.05))
+    chi = inputs.gaussian_spinor(lat.volume, 12, 12, 0)
+    psi = torch.empty((lat.volume, 12), dtype=torch.complex128, device="cuda")
+    st = ctx.solve(to_dev(chi), psi, 1e-13)
+    got = to_host(psi)
+    assert st["converged"]
+    res = np.linalg.norm(chi - wilson.apply_D(U, got.reshape(-1, 4, 3), m, lat).reshape(chi.shape))
+    assert res <= 1e-13 * np.linalg.norm(chi) * 1.01
+    ref = np.linalg.solve(wilson.dense_D(U, m, lat, 3), chi.reshape(-1)).reshape(chi.shape)
+    assert rel_err(got, ref) <= 1e-8
+    ctx.close()
+
+
+def test_gauge_covariance_of_solution():
+    # psi[U^Omega, Omega chi] = Omega psi[U, chi], to the solve tolerance
+    import torch
+    import paper_0707_4018_gb300 as mg
+    dims, block, nv = (4, 4, 4, 4), (2, 2, 2, 2), 4
+    lat = Lattice(dims)
+    U = inputs.su3_links(dims, seed=12)
+    om = inputs.su3_random(lat.volume, 13, 0x47)
+    m = 0.1
+    chi = inputs.gaussian_spinor(lat.volume, 12, 14, 0)
+    out = []
+    for UU, cc in ((U, chi), (wilson.gauge_transform(U, om, lat), wilson.transform_spinor(chi, om, lat, 3))):
+        ctx = mg.Context.setup(to_dev(UU), m, dims, _params(block, nv, 1, n_pass=2, coarsest_tol=0.05))
+        psi = torch.empty((lat.volume, 12), dtype=torch.complex128, device="cuda")
+        assert ctx.solve(to_dev(cc), psi, 1e-12)["converged"]
+        out.append(to_host(psi))
+        ctx.close()
+    assert rel_err(out[1], wilson.transform_spinor(out[0], om, lat, 3)) < 1e-10
+
+
+def test_su3_workload_16x16x16x32_true_residual():
+    # the 4d workload: 16^3 x 32, APE-smeared SU(3) links, 4^4 blocks, Nv = 24 (48 coarse dofs),
+    # mixed precision; the oracle recomputes the FP64 true residual
+    import torch
+    import paper_0707_4018_gb300 as mg
+    dims = (16, 16, 16, 32)
+    lat = Lattice(dims)
+    U = inputs.su3_links(dims, seed=inputs.workload_seed(3, 16, 0.0))
+    row = mcrit_table().get("w3_su3_16x16x16x32")
+    # m_c + 0.005 (lowest |eigenvalue| about 5e-3) from the oracle's table, else m = 0 (above m_c)
+    m = row["m_crit"] + 0.005 if row and row["links_digest"] == inputs.field_digest(U) else 0.0
+    ctx = mg.Context.setup(to_dev(U), m, dims, _params((4, 4, 4, 4), 24, 1, n_pass=3, coarsest_tol=0.05,
+                                                       coarsest_restart=32))
+    chi = inputs.gaussian_spinor(lat.volume, 12, 15, 0)
+    psi = torch.empty((lat.volume, 12), dtype=torch.complex128, device="cuda")
+    st = ctx.solve(to_dev(chi), psi, 1e-10)
+    got = to_host(psi)
+    res = np.linalg.norm(chi - wilson.apply_D(U, got.reshape(-1, 4, 3), m, lat).reshape(chi.shape))
+    assert st["converged"] and res <= 1e-10 * np.linalg.norm(chi) * 1.01, (st, res / np.linalg.norm(chi))
+    ctx.close()
