@@ -280,6 +280,55 @@ def dslash4_roofline(precision: int, dims=(32, 32, 32, 64), iters: int = 20):
                 tflops=V * 1368 / t / 1e12)
 
 
+SU3_DIMS = (16, 16, 16, 32)
+SU3_RHS = 12
+
+
+def su3_params(precision: int):
+    """4d SU(3) hierarchy: two levels, 4^4 blocks, Nv = 24 split by chirality (48 coarse dofs),
+    one relaxation pass of 200 MR iterations (deeper relaxation in place of adaptive passes,
+    which lowered the quality of the 4d vectors), MR 4 + 4, coarse GCR(64) to 0.05 with block
+    Jacobi."""
+    import paper_0707_4018_gb300 as mg
+    return mg.mg_default_params(levels=2, blocks=[(4, 4, 4, 4)], Nv=[24], precision=precision, chiral_split=1,
+                                n_pass=1, nu_setup=200, coarsest_tol=0.05, coarsest_restart=64, max_iter=300)
+
+
+def su3_workload(precisions=(1, 0)):
+    """Solves/s including setup on the 4d SU(3) workload: APE-smeared links on 16^3 x 32, m = m_c + 0.005
+    (m_c from the oracle's table when present, else m = 0), 12 Gaussian sources to 1e-10, one setup."""
+    import torch
+    import paper_0707_4018_gb300 as mg
+    import inputs
+    U = inputs.su3_links(SU3_DIMS, seed=inputs.workload_seed(3, SU3_DIMS[0], 0.0))
+    row = mcrit_table().get("w3_su3_" + "x".join(str(v) for v in SU3_DIMS))
+    m_ok = row is not None and row.get("links_digest") == inputs.field_digest(U)
+    m = row["m_crit"] + 0.005 if m_ok else 0.0
+    V = int(np.prod(SU3_DIMS))
+    Ud = torch.from_numpy(U).cuda()
+    chis = [torch.from_numpy(inputs.gaussian_spinor(V, 12, 15, k)).cuda() for k in range(SU3_RHS)]
+    psi = torch.empty((V, 12), dtype=torch.complex128, device="cuda")
+    out = {"workload": "4d SU(3) Wilson-Dirac 16^3x32, DeGrand-Rossi, APE-smeared links (4 steps, alpha 0.5); "
+                       "2-level MG 4^4 blocks, Nv=24 chirality-split (48x48 coarse blocks), 12 Gaussian sources, tol 1e-10",
+           "m": m, "m_from": "m_c + 0.005 (oracle table)" if m_ok else "0.0 (no m_c in the table)"}
+    for prec in precisions:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx = mg.Context.setup(Ud, m, SU3_DIMS, su3_params(prec))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        sts = [ctx.solve(c, psi, TOL, raise_on_fail=False) for c in chis]
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        ctx.close()
+        out["mixed" if prec == 1 else "fp64"] = {
+            "solves_per_s_incl_setup": SU3_RHS / (t2 - t0), "solves_per_s_excl_setup": SU3_RHS / (t2 - t1),
+            "setup_s": t1 - t0, "ms_per_solve": (t2 - t1) / SU3_RHS * 1e3, "iters": [st["iters"] for st in sts],
+            "coarse_iters": [st["coarsest_iters"] for st in sts], "converged": all(st["converged"] for st in sts),
+            "worst_true_rel_residual": max(st["true_rel_residual"] for st in sts)}
+    return out
+
+
 def coarsest_flops(iters: int, restart: int, n: int) -> float:
     """Algorithmic FP64 flops of one GCR solve on the preconditioned coarsest stencil (N = 8).
 
@@ -446,6 +495,9 @@ def run_only(case: str):
     import torch
     import paper_0707_4018_gb300 as mg
     mg.load()
+    if case == "su3":
+        print(json.dumps({"case": case, **su3_workload()}))
+        return
     if case.startswith("dslash4"):
         r = dslash4_roofline(1 if case == "dslash4-f32" else 0, iters=3)
         print(json.dumps({"case": case, **r}))
@@ -536,7 +588,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--only", default=None, choices=["dslash-f32", "dslash-f64", "dslash4-f32", "dslash4-f64", "solve", "vcycle",
-                                                      "transfer", "coarse-tc"],
+                                                      "transfer", "coarse-tc", "su3"],
                     help="profiling cases: the Dslash timing loop alone (2d, or 4d SU(3)), one beta's setup + 3 solves, "
                          "25 mixed-precision V-cycles after one beta's setup, or 5 V-cycles on a 1024^2 "
                          "hierarchy (fine level larger than L2, for the restriction and prolongation), or the "
@@ -598,6 +650,7 @@ def main():
     ds32 = dslash_roofline(1)
     ds64 = dslash_roofline(0)
     ds4 = dslash4_roofline(1)
+    su3 = su3_workload() if world_of(d) == 1 or rank == 0 else None
     cr = coarsest_roofline(fields_dev)
 
     cpu = None
@@ -630,6 +683,7 @@ def main():
                        "traffic_f32": 780606208, "traffic_source": "profiles/dslash_f32_4096x4096.md",
                        "su3_4d_f32": {**ds4, "frac": ds4["gbs"] / peak}},
         "cpu_baseline": cpu,
+        "su3_4d": su3,
     }
     print(json.dumps(line), flush=True)
 

@@ -7,8 +7,11 @@
 //          ((1 +- gamma_5) / 2, 2 Nv coarse dofs); block Gram-Schmidt (FP64);
 //          Galerkin P^dagger D P (FP64); passes 2..n_pass: v <- v - V(D v).
 //   V-cycle (FP64, or FP32 for MG_FP32): MR pre-smoothing from 0, residual,
-//          restriction, coarse solve (FP64 GCR to coarsest_tol), prolongation
-//          and correction, residual, MR post-smoothing.
+//          restriction, coarse solve (FP64 GCR to coarsest_tol, right-
+//          preconditioned by the inverses of the coarse self blocks; the
+//          operator applied in FP32 for MG_FP32), prolongation and correction,
+//          residual, MR post-smoothing. MG_FP32 also relaxes the setup vectors
+//          in FP32.
 //   solve: FP64 flexible GCR with the V-cycle as right preconditioner and the
 //          true residual at every restart.
 #include <algorithm>
@@ -31,8 +34,9 @@ struct Engine4 {
   Coarse4 cg{};
   long long nf = 0, nc = 0;  // fine / coarse dofs
   int N = 0;
-  DevBuf<Cx<double>> U64, nullv, V64, Y64;
-  DevBuf<Cx<float>> U32, V32, Y32;
+  DevBuf<Cx<double>> U64, nullv, V64, Y64, Minv64;
+  DevBuf<Cx<float>> U32, V32, Y32, Minv32;
+  DevBuf<int> info;  // set by the block inversion when a self block is singular
   // V-cycle work
   DevBuf<Cx<double>> vr64, vAr64, vx64, vb64;
   DevBuf<Cx<float>> vr32, vAr32, vx32, vb32;
@@ -78,9 +82,13 @@ void fine_apply(Engine4 &e, const Cx<R> *in, Cx<R> *out, const Cx<R> *b = nullpt
   ++e.apps[0];
 }
 
+// out = a A_c in + c b on FP64 vectors; `fast`: the FP32 copy of the operator (FP32 sums)
 void coarse_apply64(Engine4 &e, const Cx<double> *in, Cx<double> *out, const Cx<double> *b = nullptr, double a = 1.0,
-                    double c = 0.0) {
-  launch_coarse4_apply<double>(e.Y64.p, in, out, e.cg, b, a, c, e.s);
+                    double c = 0.0, bool fast = false) {
+  if (fast)
+    launch_coarse4_apply<float, double>(e.Y32.p, in, out, e.cg, b, a, c, e.s);
+  else
+    launch_coarse4_apply<double, double>(e.Y64.p, in, out, e.cg, b, a, c, e.s);
   ++e.apps[1];
 }
 
@@ -163,19 +171,67 @@ Gcr fgcr(Engine4 &e, ApplyF &&apply, PrecF &&prec, const Cx<double> *b, Cx<doubl
   return out;
 }
 
-// coarse solve (FP64 GCR to coarsest_tol): cx = A_c^{-1} cb
+// coarse solve: cx = A_c^{-1} cb by FP64 GCR to coarsest_tol, right-preconditioned by
+// block Jacobi (the inverses of the self blocks). With MG_FP32 and a tolerance that
+// FP32 arithmetic can reach (>= 1e-5), the operator and the preconditioner are applied
+// from their FP32 copies; the Krylov vectors stay FP64.
 long long coarse_solve(Engine4 &e) {
+  const bool fast = e.f32 && e.p.coarsest_tol >= 1e-5;
   auto apply = [&](const Cx<double> *in, Cx<double> *out, const Cx<double> *b = nullptr) {
     if (b != nullptr)
-      coarse_apply64(e, in, out, b, -1.0, 1.0);
+      coarse_apply64(e, in, out, b, -1.0, 1.0, fast);
     else
-      coarse_apply64(e, in, out);
+      coarse_apply64(e, in, out, nullptr, 1.0, 0.0, fast);
   };
-  auto prec = [&](const Cx<double> *r, Cx<double> *z) { launch_copy<double>(r, z, e.nc, e.s); };
-  Gcr g = fgcr(e, apply, prec, e.cb.p, e.cx.p, e.nc, e.p.coarsest_tol, e.p.coarsest_restart, e.p.coarsest_max_iter,
-               e.cZ.p, e.cW.p, e.cr.p, kScalCoarse);
-  e.coarsest_iters += g.iters;
-  return g.iters;
+  auto prec = [&](const Cx<double> *r, Cx<double> *z) {
+    if (fast)
+      launch_block_apply4<float>(e.Minv32.p, r, z, e.cg, e.s);
+    else
+      launch_block_apply4<double>(e.Minv64.p, r, z, e.cg, e.s);
+  };
+  const long long n = e.nc;
+  Cx<double> *x = e.cx.p, *r = e.cr.p, *Z = e.cZ.p, *W = e.cW.p;
+  const Cx<double> *b = e.cb.p;
+  double *dots = e.scal.p + kScalCoarse, *coef = dots + 200, *state = dots + 204;
+  double *h = e.host + kScalCoarse;
+  auto fetch = [&](const double *src) {
+    MG_CUDA(cudaMemcpyAsync(h, src, sizeof(double), cudaMemcpyDeviceToHost, e.s));
+    MG_CUDA(cudaStreamSynchronize(e.s));
+    if (std::isnan(h[0])) fail(MG_ERR_NAN, "coarse GCR: NaN in a reduction");
+    return h[0];
+  };
+  launch_zero<double>(x, n, e.s);
+  launch_copy<double>(b, r, n, e.s);
+  launch_norm2<double>(b, n, dots, e.ws, e.s);
+  const double bn2 = fetch(dots);
+  if (!(bn2 > 0.0)) return 0;
+  const double tol2 = e.p.coarsest_tol * e.p.coarsest_tol * bn2;
+  const int restart = e.p.coarsest_restart, max_iter = e.p.coarsest_max_iter;
+  constexpr int kCheck = 4;  // iterations between host reads of the residual estimate
+  long long iters = 0;
+  while (iters < max_iter) {
+    int k = 0;
+    bool done = false;
+    for (; k < restart && iters < max_iter; ++k) {
+      Cx<double> *z = Z + (long long)k * n, *w = W + (long long)k * n;
+      prec(r, z);
+      apply(z, w);
+      launch_gcr_dots(W, w, r, k, n, dots, e.ws, e.s);
+      launch_gcr_coef(dots, k, coef, state, e.s);
+      launch_gcr_update_dev(W, w, Z, z, k, dots, coef, x, r, n, e.s);
+      ++iters;
+      if ((k + 1) % kCheck == 0 && fetch(state) <= tol2) {
+        done = true;
+        ++k;
+        break;
+      }
+    }
+    apply(x, r, b);  // true residual
+    launch_norm2<double>(r, n, dots, e.ws, e.s);
+    if (fetch(dots) <= tol2 || (done && k == 0)) break;
+  }
+  e.coarsest_iters += iters;
+  return iters;
 }
 
 // x (+)= nu MR iterations on D e = r (r updated to the recurrence residual)
@@ -261,10 +317,13 @@ void precondition(Engine4 &e, const Cx<double> *r, Cx<double> *z) {
     vcycle<double>(e, r, z);
 }
 
-void make_fp32(Engine4 &e) {
+// block-Jacobi inverses of the coarse self blocks, then the FP32 copies (MG_FP32)
+void prepare_coarse(Engine4 &e) {
+  launch_block_invert4(e.Y64.p, e.Minv64.p, e.cg, e.info.p, e.s);
   if (!e.f32) return;
   launch_convert<float, double>(e.V64.p, e.V32.p, e.V64.n, e.s);
   launch_convert<float, double>(e.Y64.p, e.Y32.p, e.Y64.n, e.s);
+  launch_convert<float, double>(e.Minv64.p, e.Minv32.p, e.Minv64.n, e.s);
 }
 
 // chirality split, block Gram-Schmidt and Galerkin operator from the current vectors
@@ -272,7 +331,7 @@ void build(Engine4 &e) {
   launch_gather_split4(e.nullv.p, e.nf, e.V64.p, e.bg, e.s);
   launch_block_gs4(e.V64.p, e.bg, e.s);
   launch_galerkin4(e.U64.p, diag4(e), e.V64.p, e.Y64.p, e.bg, e.s);
-  make_fp32(e);
+  prepare_coarse(e);
 }
 
 void setup(Engine4 &e) {
@@ -281,7 +340,18 @@ void setup(Engine4 &e) {
   for (int k = 0; k < Nv; ++k) {
     Cx<double> *v = e.nullv.p + (long long)k * e.nf;
     launch_gaussian(v, e.nf, e.p.seed, k, 0, e.s);
-    // relaxation: MR on D x = 0 from x = v (r = -D v)
+    // relaxation: MR on D x = 0 from x = v (r = -D v); FP32 on an FP32 copy in mixed mode
+    if (e.f32) {
+      launch_convert<float, double>(v, e.vx32.p, e.nf, e.s);
+      fine_apply<float>(e, e.vx32.p, e.vr32.p, nullptr, -1.0, 0.0);
+      for (int it = 0; it < e.p.nu_setup; ++it) {
+        fine_apply<float>(e, e.vr32.p, e.vAr32.p);
+        launch_dot_norm<float>(e.vAr32.p, e.vr32.p, e.nf, sc, e.ws, e.s);
+        launch_mr_update<float>(sc, e.p.omega, e.vx32.p, e.vr32.p, e.vAr32.p, e.nf, e.s);
+      }
+      launch_convert<double, float>(e.vx32.p, v, e.nf, e.s);
+      continue;
+    }
     fine_apply<double>(e, v, e.vr64.p, nullptr, -1.0, 0.0);
     for (int it = 0; it < e.p.nu_setup; ++it) {
       fine_apply<double>(e, e.vr64.p, e.vAr64.p);
@@ -363,6 +433,8 @@ Engine4 *engine4_create(const mg_geom *g, const void *U, double m, const mg_para
   e->nullv.alloc((size_t)e->bg.Nv * e->nf);
   e->V64.alloc((size_t)e->bg.nblocks * e->N * e->bg.bvol * 6);
   e->Y64.alloc((size_t)e->bg.nblocks * 9 * e->N * e->N);
+  e->Minv64.alloc((size_t)e->bg.nblocks * e->N * e->N);
+  e->info.alloc(1);
   e->vr64.alloc(e->nf);
   e->vAr64.alloc(e->nf);
   e->vx64.alloc(e->nf);
@@ -371,6 +443,7 @@ Engine4 *engine4_create(const mg_geom *g, const void *U, double m, const mg_para
     e->U32.alloc(e->U64.n);
     e->V32.alloc(e->V64.n);
     e->Y32.alloc(e->Y64.n);
+    e->Minv32.alloc(e->Minv64.n);
     e->vr32.alloc(e->nf);
     e->vAr32.alloc(e->nf);
     e->vx32.alloc(e->nf);
@@ -397,6 +470,7 @@ Engine4 *engine4_create(const mg_geom *g, const void *U, double m, const mg_para
   pool_ready();
   MG_CUDA(cudaMemsetAsync(e->tickets.p, 0, e->ws.tickets * sizeof(unsigned int), s));
   MG_CUDA(cudaMemsetAsync(e->scal.p, 0, kScalCount * sizeof(double), s));
+  MG_CUDA(cudaMemsetAsync(e->info.p, 0, sizeof(int), s));
   e->ws.partials = e->partials.p;
   e->ws.ticket = e->tickets.p;
   MG_CUDA(cudaMemcpyAsync(e->U64.p, U, e->U64.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, s));
@@ -441,7 +515,7 @@ Solve4 engine4_solve(Engine4 &e, const void *chi, void *psi, double tol) {
 void engine4_update_mass(Engine4 &e, double m) {
   e.m = m;
   launch_galerkin4(e.U64.p, diag4(e), e.V64.p, e.Y64.p, e.bg, e.s);
-  make_fp32(e);
+  prepare_coarse(e);
   MG_CUDA(cudaStreamSynchronize(e.s));
 }
 

@@ -42,10 +42,24 @@ void launch_block_gs4(Cx<double> *V, const Block4 &g, cudaStream_t s);
 // Y = P^dagger D P (FP64) for the fine Wilson operator with diagonal `diag`
 void launch_galerkin4(const Cx<double> *U, double diag, const Cx<double> *V, Cx<double> *Y, const Block4 &g,
                       cudaStream_t s);
-// out = a (A + shift_v) in + c b on the coarse lattice (nvec vectors, stride nsites * N)
+// out = a (A + shift_v) in + c b on the coarse lattice (nvec vectors, stride nsites * N);
+// the operator's precision RY may be below the vectors' RV (float / double: FP32 sums)
+template <typename RY, typename RV>
+void launch_coarse4_apply(const Cx<RY> *Y, const Cx<RV> *in, Cx<RV> *out, const Coarse4 &g, const Cx<RV> *b,
+                          double a, double c, cudaStream_t s, int nvec = 1, const double *shift = nullptr);
+// Minv[j] = inverse of the self block Y[j][0] (FP64 Gauss-Jordan, partial pivoting); *info
+// set to 1 if a block is singular
+void launch_block_invert4(const Cx<double> *Y, Cx<double> *Minv, const Coarse4 &g, int *info, cudaStream_t s);
+// z_j = Minv_j r_j (vectors FP64, Minv in R)
 template <typename R>
-void launch_coarse4_apply(const Cx<R> *Y, const Cx<R> *in, Cx<R> *out, const Coarse4 &g, const Cx<R> *b, double a,
-                          double c, cudaStream_t s, int nvec = 1, const double *shift = nullptr);
+void launch_block_apply4(const Cx<R> *Minv, const Cx<double> *r, Cx<double> *z, const Coarse4 &g, cudaStream_t s);
+// GCR step with device-side coefficients: coef = (inv, Re alpha, Im alpha) and
+// state[0] = |r|^2 - |alpha|^2 from the reduction of launch_gcr_dots; then the fused
+// projection / normalisation / x, r update reading them
+void launch_gcr_coef(const double *dots, int k, double *coef, double *state, cudaStream_t s);
+void launch_gcr_update_dev(const Cx<double> *W, Cx<double> *Wk, const Cx<double> *Z, Cx<double> *Zk, int k,
+                           const double *beta, const double *coef, Cx<double> *x, Cx<double> *r, long long n,
+                           cudaStream_t s);
 // exports: Y in [j][dir][row][col]; P as N fine vectors [c][x][12]
 void launch_coarse4_to_canonical(const Cx<double> *Yi, Cx<double> *Yc, const Coarse4 &g, cudaStream_t s);
 void launch_prolongator4_to_canonical(const Cx<double> *V, Cx<double> *out, const Block4 &g, cudaStream_t s);

@@ -7,6 +7,8 @@
 // V[b][c][s][d6], c < N = 2 Nv, s < bvol, d6 < 6, is dof 6 chi + d6 (chi = c / Nv)
 // of site s of block b; per column Nh = 6 bvol complex, contiguous, so the block
 // reductions and the prolongation read V with unit stride.
+#include <algorithm>
+
 #include "mg4d.h"
 #include "wilson4d.cuh"
 
@@ -296,17 +298,21 @@ __global__ void __launch_bounds__(256) galerkin4_kernel(const Cx<double> *__rest
 }
 
 // ---------------------------------------------------------------------------
-// coarse apply: CTA (site j, vector v), 4 N threads: the 9 N source values in shared
-// memory, thread (q, row) sums the (dir, col) pairs p = q, q + 4, ... of its row
+// coarse apply: CTA (site j, vector v), QP N threads (QP = min(8, 512 / N) partial sums
+// per row): the 9 N source values in shared memory, thread (q, row) sums the (dir, col)
+// pairs p = q, q + QP, ... of its row.
+// The operator may be stored in lower precision than the vectors (RY = float with
+// RV = double: the sums run in FP32, inputs rounded once, the result widened).
 // ---------------------------------------------------------------------------
-template <typename R>
-__global__ void coarse4_apply_kernel(const Cx<R> *__restrict__ Y, const Cx<R> *__restrict__ in,
-                                     Cx<R> *__restrict__ out, Coarse4 g, const Cx<R> *__restrict__ b, R a, R c,
+template <typename RY, typename RV>
+__global__ void coarse4_apply_kernel(const Cx<RY> *__restrict__ Y, const Cx<RV> *__restrict__ in,
+                                     Cx<RV> *__restrict__ out, Coarse4 g, const Cx<RV> *__restrict__ b, RV a, RV c,
                                      long long ldv, const double *__restrict__ shift) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int N = g.N;
-  Cx<R> *xs = reinterpret_cast<Cx<R> *>(sm_raw);  // [9][N]
-  Cx<R> *red = xs + 9 * N;                          // [4][N]
+  const int QP = blockDim.x / N;                     // partial sums per row
+  Cx<RY> *xs = reinterpret_cast<Cx<RY> *>(sm_raw);  // [9][N]
+  Cx<RY> *red = xs + 9 * N;                          // [QP][N]
   const int j = blockIdx.x, v = blockIdx.y;
   in += v * ldv;
   out += v * ldv;
@@ -328,33 +334,180 @@ __global__ void coarse4_apply_kernel(const Cx<R> *__restrict__ Y, const Cx<R> *_
       cc[mu] = ((dir - 1) & 1) == 0 ? (cc[mu] + 1) % g.nb[mu] : (cc[mu] + g.nb[mu] - 1) % g.nb[mu];
       src = cc[0] + g.nb[0] * (cc[1] + g.nb[1] * (cc[2] + g.nb[2] * cc[3]));
     }
-    xs[e] = in[(long long)src * N + col];
+    xs[e] = cvt<RY, RV>(in[(long long)src * N + col]);
   }
   __syncthreads();
   const int row = threadIdx.x % N, q = threadIdx.x / N;
-  const Cx<R> *Yj = Y + (long long)j * 9 * N * N;
-  R re = 0, im = 0;
-  for (int p = q; p < 9 * N; p += 4) {
-    const Cx<R> y = Yj[(long long)p * N + row], xv = xs[p];
+  const Cx<RY> *Yj = Y + (long long)j * 9 * N * N;
+  RY re = 0, im = 0;
+#pragma unroll 4
+  for (int p = q; p < 9 * N; p += QP) {  // independent loads: unrolled for memory parallelism
+    const Cx<RY> y = Yj[(long long)p * N + row], xv = xs[p];
     re += y.re * xv.re - y.im * xv.im;
     im += y.re * xv.im + y.im * xv.re;
   }
   red[q * N + row] = mk(re, im);
   __syncthreads();
   if (q == 0) {
-    R sre = red[row].re + red[N + row].re + red[2 * N + row].re + red[3 * N + row].re;
-    R sim = red[row].im + red[N + row].im + red[2 * N + row].im + red[3 * N + row].im;
-    if (shift != nullptr) {
-      const R sv = (R)shift[v];
-      sre += sv * xs[row].re;
-      sim += sv * xs[row].im;
+    RV sre = 0, sim = 0;
+    for (int i = 0; i < QP; ++i) {
+      sre += (RV)red[i * N + row].re;
+      sim += (RV)red[i * N + row].im;
     }
-    Cx<R> o = mk(a * sre, a * sim);
+    if (shift != nullptr) {
+      const Cx<RV> xv = in[(long long)j * N + row];
+      sre += (RV)shift[v] * xv.re;
+      sim += (RV)shift[v] * xv.im;
+    }
+    Cx<RV> o = mk(a * sre, a * sim);
     if (b != nullptr) {
-      const Cx<R> bb = b[(long long)j * N + row];
+      const Cx<RV> bb = b[(long long)j * N + row];
       o = mk(o.re + c * bb.re, o.im + c * bb.im);
     }
     out[(long long)j * N + row] = o;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// block-Jacobi preconditioner of the coarse solve: Minv[j] = X_j^{-1}, X_j the self
+// block Y[j][0], by Gauss-Jordan elimination with partial pivoting (FP64, one CTA per
+// site, the N x 2N tableau in shared memory); stored column-major like Y
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) block_invert4_kernel(const Cx<double> *__restrict__ Y,
+                                                            Cx<double> *__restrict__ Minv, int N, int *info) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  Cx<double> *T = reinterpret_cast<Cx<double> *>(sm_raw);  // T[row][0..2N)
+  __shared__ int piv;
+  __shared__ double pscale[2];
+  const int j = blockIdx.x, W = 2 * N;
+  const Cx<double> *X = Y + (long long)j * 9 * N * N;  // dir 0, [col][row]
+  for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
+    const int r = e / W, cc = e - r * W;
+    T[e] = cc < N ? X[(long long)cc * N + r] : mk(cc - N == r ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  for (int k = 0; k < N; ++k) {
+    if (threadIdx.x < 32) {  // pivot: largest |T[i][k]| for i >= k, lowest index on ties
+      double best = -1.0;
+      int bi = k;
+      for (int i = k + threadIdx.x; i < N; i += 32) {
+        const double v = norm2(T[i * W + k]);
+        if (v > best) {
+          best = v;
+          bi = i;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (threadIdx.x == 0) {
+        piv = bi;
+        if (!(best > 0.0)) atomicExch(info, 1);
+      }
+    }
+    __syncthreads();
+    if (piv != k)
+      for (int cc = threadIdx.x; cc < W; cc += blockDim.x) {
+        const Cx<double> t = T[k * W + cc];
+        T[k * W + cc] = T[piv * W + cc];
+        T[piv * W + cc] = t;
+      }
+    __syncthreads();
+    if (threadIdx.x == 0) {  // 1 / pivot
+      const Cx<double> p = T[k * W + k];
+      const double d = norm2(p);
+      pscale[0] = p.re / d;
+      pscale[1] = -p.im / d;
+    }
+    __syncthreads();
+    const Cx<double> ip = mk(pscale[0], pscale[1]);
+    for (int cc = threadIdx.x; cc < W; cc += blockDim.x) T[k * W + cc] = T[k * W + cc] * ip;
+    __syncthreads();
+    for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
+      const int r = e / W, cc = e - r * W;
+      if (r == k || cc == k) continue;
+      const Cx<double> f = T[r * W + k];
+      T[e] = T[e] - f * T[k * W + cc];
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < N; r += blockDim.x)
+      if (r != k) T[r * W + k] = mk(0.0, 0.0);
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int cc = e / N, r = e - cc * N;
+    Minv[(long long)j * N * N + e] = T[r * W + N + cc];
+  }
+}
+
+// z_j = Minv_j r_j (one CTA per site, one thread per row)
+template <typename R>
+__global__ void block_apply4_kernel(const Cx<R> *__restrict__ Minv, const Cx<double> *__restrict__ r,
+                                    Cx<double> *__restrict__ z, int N) {
+  __shared__ Cx<R> rs[64];
+  const int j = blockIdx.x, row = threadIdx.x;
+  if (row < N) rs[row] = cvt<R, double>(r[(long long)j * N + row]);
+  __syncthreads();
+  if (row >= N) return;
+  const Cx<R> *M = Minv + (long long)j * N * N;
+  Cx<R> acc = mk((R)0, (R)0);
+#pragma unroll 8
+  for (int cc = 0; cc < N; ++cc) cmac(acc, M[(long long)cc * N + row], rs[cc]);
+  z[(long long)j * N + row] = cvt<double, R>(acc);
+}
+
+// ---------------------------------------------------------------------------
+// GCR coefficients on the device (no host round trip per iteration): from the fused
+// reduction dots = (<W_j, w>_j<k, |w|^2, <w, r>, |r|^2) form the classical Gram-Schmidt
+// norm |w - W beta|^2 = |w|^2 - |beta|^2, inv = 1 / that norm, alpha = <w, r> inv, and
+// the residual estimate |r|^2 - |alpha|^2 (state[0]). A breakdown (no new direction)
+// gives inv = alpha = 0: the step then changes nothing.
+// ---------------------------------------------------------------------------
+__global__ void gcr_coef_kernel(const double *__restrict__ dots, int k, double *__restrict__ coef,
+                                double *__restrict__ state) {
+  const double nw0 = dots[2 * k];
+  double nw2 = nw0;
+  for (int j = 0; j < k; ++j) nw2 -= dots[2 * j] * dots[2 * j] + dots[2 * j + 1] * dots[2 * j + 1];
+  double inv = 0.0, are = 0.0, aim = 0.0;
+  if (nw2 > 1e-28 * nw0) {
+    inv = 1.0 / sqrt(nw2);
+    are = dots[2 * k + 2] * inv;
+    aim = dots[2 * k + 3] * inv;
+  }
+  coef[0] = inv;
+  coef[1] = are;
+  coef[2] = aim;
+  state[0] = fmax(dots[2 * k + 4] - (are * are + aim * aim), 0.0);
+}
+
+// w <- (w - sum_j beta_j W_j) inv, z likewise; W_k = w, Z_k = z; x += alpha z; r -= alpha w,
+// with beta (dots) and (inv, alpha) (coef) read from device memory
+__global__ void gcr_update_dev_kernel(const Cx<double> *__restrict__ W, Cx<double> *__restrict__ Wk,
+                                      const Cx<double> *__restrict__ Z, Cx<double> *__restrict__ Zk, int k,
+                                      const double *__restrict__ beta, const double *__restrict__ coef,
+                                      Cx<double> *__restrict__ x, Cx<double> *__restrict__ r, long long n) {
+  const double inv = coef[0];
+  const Cx<double> alpha = mk(coef[1], coef[2]), malpha = mk(-coef[1], -coef[2]);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    Cx<double> w = Wk[i], z = Zk[i];
+    for (int j = 0; j < k; ++j) {
+      const Cx<double> bj = mk(-beta[2 * j], -beta[2 * j + 1]);
+      cmac(w, bj, W[(long long)j * n + i]);
+      cmac(z, bj, Z[(long long)j * n + i]);
+    }
+    w = inv * w;
+    z = inv * z;
+    Wk[i] = w;
+    Zk[i] = z;
+    cmac(x[i], alpha, z);
+    Cx<double> ri = r[i];
+    cmac(ri, malpha, w);
+    r[i] = ri;
   }
 }
 
@@ -438,12 +591,44 @@ void launch_galerkin4(const Cx<double> *U, double diag, const Cx<double> *V, Cx<
   MG_LAUNCHED();
 }
 
+template <typename RY, typename RV>
+void launch_coarse4_apply(const Cx<RY> *Y, const Cx<RV> *in, Cx<RV> *out, const Coarse4 &g, const Cx<RV> *b,
+                          double a, double c, cudaStream_t s, int nvec, const double *shift) {
+  const int qp = std::max(1, std::min(8, 512 / g.N));
+  const size_t smem = (size_t)(9 + qp) * g.N * sizeof(Cx<RY>);
+  coarse4_apply_kernel<RY, RV><<<dim3((unsigned int)g.nsites, nvec), qp * g.N, smem, s>>>(
+      Y, in, out, g, b, (RV)a, (RV)c, g.nsites * g.N, shift);
+  MG_LAUNCHED();
+}
+
+void launch_block_invert4(const Cx<double> *Y, Cx<double> *Minv, const Coarse4 &g, int *info, cudaStream_t s) {
+  const size_t smem = (size_t)g.N * 2 * g.N * sizeof(Cx<double>);
+  static bool attr = false;
+  if (!attr) {
+    MG_CUDA(cudaFuncSetAttribute(block_invert4_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+    attr = true;
+  }
+  block_invert4_kernel<<<(unsigned int)g.nsites, 256, smem, s>>>(Y, Minv, g.N, info);
+  MG_LAUNCHED();
+}
+
 template <typename R>
-void launch_coarse4_apply(const Cx<R> *Y, const Cx<R> *in, Cx<R> *out, const Coarse4 &g, const Cx<R> *b, double a,
-                          double c, cudaStream_t s, int nvec, const double *shift) {
-  const size_t smem = (size_t)13 * g.N * sizeof(Cx<R>);
-  coarse4_apply_kernel<R><<<dim3((unsigned int)g.nsites, nvec), 4 * g.N, smem, s>>>(
-      Y, in, out, g, b, (R)a, (R)c, g.nsites * g.N, shift);
+void launch_block_apply4(const Cx<R> *Minv, const Cx<double> *r, Cx<double> *z, const Coarse4 &g, cudaStream_t s) {
+  block_apply4_kernel<R><<<(unsigned int)g.nsites, 64, 0, s>>>(Minv, r, z, g.N);
+  MG_LAUNCHED();
+}
+
+void launch_gcr_coef(const double *dots, int k, double *coef, double *state, cudaStream_t s) {
+  gcr_coef_kernel<<<1, 1, 0, s>>>(dots, k, coef, state);
+  MG_LAUNCHED();
+}
+
+void launch_gcr_update_dev(const Cx<double> *W, Cx<double> *Wk, const Cx<double> *Z, Cx<double> *Zk, int k,
+                           const double *beta, const double *coef, Cx<double> *x, Cx<double> *r, long long n,
+                           cudaStream_t s) {
+  long long b = (n + 255) / 256;
+  if (b > 152LL * 16) b = 152LL * 16;
+  gcr_update_dev_kernel<<<(unsigned int)(b < 1 ? 1 : b), 256, 0, s>>>(W, Wk, Z, Zk, k, beta, coef, x, r, n);
   MG_LAUNCHED();
 }
 
@@ -467,9 +652,17 @@ template void launch_prolong4<double>(const Cx<double> *, const Cx<double> *, Cx
                                       cudaStream_t, int);
 template void launch_prolong4<float>(const Cx<float> *, const Cx<float> *, Cx<float> *, const Block4 &, cudaStream_t,
                                      int);
-template void launch_coarse4_apply<double>(const Cx<double> *, const Cx<double> *, Cx<double> *, const Coarse4 &,
-                                           const Cx<double> *, double, double, cudaStream_t, int, const double *);
-template void launch_coarse4_apply<float>(const Cx<float> *, const Cx<float> *, Cx<float> *, const Coarse4 &,
-                                          const Cx<float> *, double, double, cudaStream_t, int, const double *);
+template void launch_coarse4_apply<double, double>(const Cx<double> *, const Cx<double> *, Cx<double> *,
+                                                   const Coarse4 &, const Cx<double> *, double, double, cudaStream_t,
+                                                   int, const double *);
+template void launch_coarse4_apply<float, float>(const Cx<float> *, const Cx<float> *, Cx<float> *, const Coarse4 &,
+                                                 const Cx<float> *, double, double, cudaStream_t, int, const double *);
+template void launch_coarse4_apply<float, double>(const Cx<float> *, const Cx<double> *, Cx<double> *,
+                                                  const Coarse4 &, const Cx<double> *, double, double, cudaStream_t,
+                                                  int, const double *);
+template void launch_block_apply4<double>(const Cx<double> *, const Cx<double> *, Cx<double> *, const Coarse4 &,
+                                          cudaStream_t);
+template void launch_block_apply4<float>(const Cx<float> *, const Cx<double> *, Cx<double> *, const Coarse4 &,
+                                         cudaStream_t);
 
 }  // namespace mg
