@@ -46,6 +46,12 @@ struct Engine4 {
   DevBuf<Cx<double>> oZ, oW, orr, t64;  // outer GCR, setup scratch
   DevBuf<double> partials, scal;
   DevBuf<unsigned int> tickets;
+  // batched MR reductions (setup relaxation of the Nv vectors, V-cycle MR): per-vector
+  // partials, tickets and (<Ar, r>, |Ar|^2) sums
+  DevBuf<double> bpart, bsc;
+  DevBuf<unsigned int> btickets;
+  DevBuf<Cx<float>> sx32, sr32, sAr32;  // setup relaxation batch (MG_FP32)
+  DevBuf<Cx<double>> sr64, sAr64;       // setup relaxation batch (MG_FP64; x is the vector set itself)
   ReduceWs ws{};
   double *host = nullptr;  // pinned: [0, 256) outer, [256, 512) coarse
   long long apps[MG_MAX_LEVELS] = {0, 0, 0, 0};
@@ -234,14 +240,17 @@ long long coarse_solve(Engine4 &e) {
   return iters;
 }
 
-// x (+)= nu MR iterations on D e = r (r updated to the recurrence residual)
+constexpr int kMrBlocks = 152 * 4;  // grid cap of the batched MR reductions
+
+// x (+)= nu MR iterations on D e = r for nvec vectors (stride nf; r updated to the
+// recurrence residual); the reductions are summed in the vectors' precision
 template <typename R>
-void mr_fine(Engine4 &e, Cx<R> *x, Cx<R> *r, Cx<R> *Ar, int nu) {
-  double *sc = e.scal.p + kScalMr;
+void mr_fine(Engine4 &e, Cx<R> *x, Cx<R> *r, Cx<R> *Ar, int nu, int nvec = 1) {
   for (int it = 0; it < nu; ++it) {
-    fine_apply<R>(e, r, Ar);
-    launch_dot_norm<R>(Ar, r, e.nf, sc, e.ws, e.s);
-    launch_mr_update<R>(sc, e.p.omega, x, r, Ar, e.nf, e.s);
+    launch_dslash4<R>(U_of<R>(e), r, Ar, e.fg, diag4(e), nullptr, 1.0, 0.0, e.s, nvec);
+    e.apps[0] += nvec;
+    launch_dot_norm_batch<R>(Ar, r, e.nf, nvec, e.bsc.p, e.bpart.p, e.btickets.p, kMrBlocks, e.s);
+    launch_mr_update_batch<R>(e.bsc.p, e.p.omega, x, r, Ar, e.nf, nvec, e.s);
   }
 }
 
@@ -336,28 +345,18 @@ void build(Engine4 &e) {
 
 void setup(Engine4 &e) {
   const int Nv = e.bg.Nv;
-  double *sc = e.scal.p + kScalMr;
-  for (int k = 0; k < Nv; ++k) {
-    Cx<double> *v = e.nullv.p + (long long)k * e.nf;
-    launch_gaussian(v, e.nf, e.p.seed, k, 0, e.s);
-    // relaxation: MR on D x = 0 from x = v (r = -D v); FP32 on an FP32 copy in mixed mode
-    if (e.f32) {
-      launch_convert<float, double>(v, e.vx32.p, e.nf, e.s);
-      fine_apply<float>(e, e.vx32.p, e.vr32.p, nullptr, -1.0, 0.0);
-      for (int it = 0; it < e.p.nu_setup; ++it) {
-        fine_apply<float>(e, e.vr32.p, e.vAr32.p);
-        launch_dot_norm<float>(e.vAr32.p, e.vr32.p, e.nf, sc, e.ws, e.s);
-        launch_mr_update<float>(sc, e.p.omega, e.vx32.p, e.vr32.p, e.vAr32.p, e.nf, e.s);
-      }
-      launch_convert<double, float>(e.vx32.p, v, e.nf, e.s);
-      continue;
-    }
-    fine_apply<double>(e, v, e.vr64.p, nullptr, -1.0, 0.0);
-    for (int it = 0; it < e.p.nu_setup; ++it) {
-      fine_apply<double>(e, e.vr64.p, e.vAr64.p);
-      launch_dot_norm<double>(e.vAr64.p, e.vr64.p, e.nf, sc, e.ws, e.s);
-      launch_mr_update<double>(sc, e.p.omega, v, e.vr64.p, e.vAr64.p, e.nf, e.s);
-    }
+  for (int k = 0; k < Nv; ++k) launch_gaussian(e.nullv.p + (long long)k * e.nf, e.nf, e.p.seed, k, 0, e.s);
+  // relaxation of all Nv vectors as one batch: MR on D x = 0 from x = v (r = -D v); in FP32
+  // on FP32 copies in mixed mode
+  const long long nall = (long long)Nv * e.nf;
+  if (e.f32) {
+    launch_convert<float, double>(e.nullv.p, e.sx32.p, nall, e.s);
+    launch_dslash4<float>(e.U32.p, e.sx32.p, e.sr32.p, e.fg, diag4(e), nullptr, -1.0, 0.0, e.s, Nv);
+    mr_fine<float>(e, e.sx32.p, e.sr32.p, e.sAr32.p, e.p.nu_setup, Nv);
+    launch_convert<double, float>(e.sx32.p, e.nullv.p, nall, e.s);
+  } else {
+    launch_dslash4<double>(e.U64.p, e.nullv.p, e.sr64.p, e.fg, diag4(e), nullptr, -1.0, 0.0, e.s, Nv);
+    mr_fine<double>(e, e.nullv.p, e.sr64.p, e.sAr64.p, e.p.nu_setup, Nv);
   }
   build(e);
   for (int pass = 2; pass <= e.p.n_pass; ++pass) {
@@ -467,7 +466,19 @@ Engine4 *engine4_create(const mg_geom *g, const void *U, double m, const mg_para
   e->ws.tickets = 160;
   e->tickets.alloc((size_t)e->ws.tickets);
   e->scal.alloc(kScalCount);
+  e->bpart.alloc((size_t)e->bg.Nv * kMrBlocks * 3 + 16);
+  e->bsc.alloc((size_t)e->bg.Nv * 3);
+  e->btickets.alloc((size_t)e->bg.Nv);
+  if (e->f32) {
+    e->sx32.alloc((size_t)e->bg.Nv * e->nf);
+    e->sr32.alloc((size_t)e->bg.Nv * e->nf);
+    e->sAr32.alloc((size_t)e->bg.Nv * e->nf);
+  } else {
+    e->sr64.alloc((size_t)e->bg.Nv * e->nf);
+    e->sAr64.alloc((size_t)e->bg.Nv * e->nf);
+  }
   pool_ready();
+  MG_CUDA(cudaMemsetAsync(e->btickets.p, 0, e->bg.Nv * sizeof(unsigned int), s));
   MG_CUDA(cudaMemsetAsync(e->tickets.p, 0, e->ws.tickets * sizeof(unsigned int), s));
   MG_CUDA(cudaMemsetAsync(e->scal.p, 0, kScalCount * sizeof(double), s));
   MG_CUDA(cudaMemsetAsync(e->info.p, 0, sizeof(int), s));

@@ -60,6 +60,15 @@ void launch_gcr_coef(const double *dots, int k, double *coef, double *state, cud
 void launch_gcr_update_dev(const Cx<double> *W, Cx<double> *Wk, const Cx<double> *Z, Cx<double> *Zk, int k,
                            const double *beta, const double *coef, Cx<double> *x, Cx<double> *r, long long n,
                            cudaStream_t s);
+// batched MR: out[3 v .. 3 v + 2] = (<a_v, b_v>, |a_v|^2) summed in R (partials: nvec x
+// max_blocks x 3 doubles, tickets: nvec zeroed counters), then x_v += alpha_v r_v,
+// r_v -= alpha_v Ar_v with alpha_v = omega <Ar_v, r_v> / |Ar_v|^2 from those sums
+template <typename R>
+void launch_dot_norm_batch(const Cx<R> *a, const Cx<R> *b, long long n, int nvec, double *out, double *partials,
+                           unsigned int *tickets, int max_blocks, cudaStream_t s);
+template <typename R>
+void launch_mr_update_batch(const double *sc, double omega, Cx<R> *x, Cx<R> *r, const Cx<R> *Ar, long long n,
+                            int nvec, cudaStream_t s);
 // exports: Y in [j][dir][row][col]; P as N fine vectors [c][x][12]
 void launch_coarse4_to_canonical(const Cx<double> *Yi, Cx<double> *Yc, const Coarse4 &g, cudaStream_t s);
 void launch_prolongator4_to_canonical(const Cx<double> *V, Cx<double> *out, const Block4 &g, cudaStream_t s);

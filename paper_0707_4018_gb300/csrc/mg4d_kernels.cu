@@ -511,6 +511,48 @@ __global__ void gcr_update_dev_kernel(const Cx<double> *__restrict__ W, Cx<doubl
   }
 }
 
+// ---------------------------------------------------------------------------
+// batched MR pieces for nvec vectors of n complex each (vector v = blockIdx.y):
+// sc[3 v .. 3 v + 2] = (<Ar_v, r_v>, |Ar_v|^2), summed per thread and per block in R
+// (FP32 for FP32 vectors: GB300's FP64 unit is far slower), partials and the final
+// sum in FP64; then x_v += alpha_v r_v, r_v -= alpha_v Ar_v with
+// alpha_v = omega <Ar_v, r_v> / |Ar_v|^2
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kReduceThreads) dot_norm_batch_kernel(const Cx<R> *__restrict__ a,
+                                                                        const Cx<R> *__restrict__ b, long long n,
+                                                                        double *partials, double *out,
+                                                                        unsigned int *ticket) {
+  __shared__ R sh[32 * 3];
+  const long long off = blockIdx.y * n;
+  R v[3] = {(R)0, (R)0, (R)0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const Cx<R> x = a[off + i], y = b[off + i];
+    v[0] += x.re * y.re + x.im * y.im;
+    v[1] += x.re * y.im - x.im * y.re;
+    v[2] += x.re * x.re + x.im * x.im;
+  }
+  grid_finish_t<3, R>(v, partials + (long long)blockIdx.y * gridDim.x * 3, out + 3 * blockIdx.y,
+                      ticket + blockIdx.y, sh);
+}
+
+template <typename R>
+__global__ void mr_update_batch_kernel(const double *__restrict__ sc, double omega, Cx<R> *__restrict__ x,
+                                       Cx<R> *__restrict__ r, const Cx<R> *__restrict__ Ar, long long n) {
+  const int v = blockIdx.y;
+  const double den = sc[3 * v + 2];
+  const R are = den > 0.0 ? (R)(omega * sc[3 * v] / den) : (R)0, aim = den > 0.0 ? (R)(omega * sc[3 * v + 1] / den) : (R)0;
+  const long long off = v * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const Cx<R> ri = r[off + i], ai = Ar[off + i];
+    Cx<R> xi = x[off + i];
+    xi.re += are * ri.re - aim * ri.im;
+    xi.im += are * ri.im + aim * ri.re;
+    x[off + i] = xi;
+    r[off + i] = mk(ri.re - (are * ai.re - aim * ai.im), ri.im - (are * ai.im + aim * ai.re));
+  }
+}
+
 __global__ void coarse4_to_canonical_kernel(const Cx<double> *__restrict__ Yi, Cx<double> *__restrict__ Yc,
                                             long long total, int N) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;  // canonical [j][dir][row][col]
@@ -632,6 +674,23 @@ void launch_gcr_update_dev(const Cx<double> *W, Cx<double> *Wk, const Cx<double>
   MG_LAUNCHED();
 }
 
+template <typename R>
+void launch_dot_norm_batch(const Cx<R> *a, const Cx<R> *b, long long n, int nvec, double *out, double *partials,
+                           unsigned int *tickets, int max_blocks, cudaStream_t s) {
+  dot_norm_batch_kernel<R><<<dim3(reduce_blocks(n, max_blocks), nvec), kReduceThreads, 0, s>>>(a, b, n, partials, out,
+                                                                                                tickets);
+  MG_LAUNCHED();
+}
+
+template <typename R>
+void launch_mr_update_batch(const double *sc, double omega, Cx<R> *x, Cx<R> *r, const Cx<R> *Ar, long long n,
+                            int nvec, cudaStream_t s) {
+  long long b = (n + 255) / 256;
+  if (b > 152LL * 8) b = 152LL * 8;
+  mr_update_batch_kernel<R><<<dim3((unsigned int)b, nvec), 256, 0, s>>>(sc, omega, x, r, Ar, n);
+  MG_LAUNCHED();
+}
+
 void launch_coarse4_to_canonical(const Cx<double> *Yi, Cx<double> *Yc, const Coarse4 &g, cudaStream_t s) {
   const long long total = g.nsites * 9 * g.N * g.N;
   coarse4_to_canonical_kernel<<<grid_for(total, 256), 256, 0, s>>>(Yi, Yc, total, g.N);
@@ -660,6 +719,14 @@ template void launch_coarse4_apply<float, float>(const Cx<float> *, const Cx<flo
 template void launch_coarse4_apply<float, double>(const Cx<float> *, const Cx<double> *, Cx<double> *,
                                                   const Coarse4 &, const Cx<double> *, double, double, cudaStream_t,
                                                   int, const double *);
+template void launch_dot_norm_batch<float>(const Cx<float> *, const Cx<float> *, long long, int, double *, double *,
+                                           unsigned int *, int, cudaStream_t);
+template void launch_dot_norm_batch<double>(const Cx<double> *, const Cx<double> *, long long, int, double *,
+                                            double *, unsigned int *, int, cudaStream_t);
+template void launch_mr_update_batch<float>(const double *, double, Cx<float> *, Cx<float> *, const Cx<float> *,
+                                            long long, int, cudaStream_t);
+template void launch_mr_update_batch<double>(const double *, double, Cx<double> *, Cx<double> *, const Cx<double> *,
+                                             long long, int, cudaStream_t);
 template void launch_block_apply4<double>(const Cx<double> *, const Cx<double> *, Cx<double> *, const Coarse4 &,
                                           cudaStream_t);
 template void launch_block_apply4<float>(const Cx<float> *, const Cx<double> *, Cx<double> *, const Coarse4 &,
