@@ -294,7 +294,7 @@ def su3_params(precision: int):
                                 n_pass=1, nu_setup=200, coarsest_tol=0.05, coarsest_restart=64, max_iter=300)
 
 
-def su3_workload(precisions=(1, 0)):
+def su3_workload(precisions=(1, 0), nrhs: int = SU3_RHS):
     """Solves/s including setup on the 4d SU(3) workload: APE-smeared links on 16^3 x 32, m = m_c + 0.005
     (m_c from the oracle's table when present, else m = 0), 12 Gaussian sources to 1e-10, one setup."""
     import torch
@@ -306,7 +306,7 @@ def su3_workload(precisions=(1, 0)):
     m = row["m_crit"] + 0.005 if m_ok else 0.0
     V = int(np.prod(SU3_DIMS))
     Ud = torch.from_numpy(U).cuda()
-    chis = [torch.from_numpy(inputs.gaussian_spinor(V, 12, 15, k)).cuda() for k in range(SU3_RHS)]
+    chis = [torch.from_numpy(inputs.gaussian_spinor(V, 12, 15, k)).cuda() for k in range(nrhs)]
     psi = torch.empty((V, 12), dtype=torch.complex128, device="cuda")
     out = {"workload": "4d SU(3) Wilson-Dirac 16^3x32, DeGrand-Rossi, APE-smeared links (4 steps, alpha 0.5); "
                        "2-level MG 4^4 blocks, Nv=24 chirality-split (48x48 coarse blocks), 12 Gaussian sources, tol 1e-10",
@@ -322,8 +322,8 @@ def su3_workload(precisions=(1, 0)):
         t2 = time.perf_counter()
         ctx.close()
         out["mixed" if prec == 1 else "fp64"] = {
-            "solves_per_s_incl_setup": SU3_RHS / (t2 - t0), "solves_per_s_excl_setup": SU3_RHS / (t2 - t1),
-            "setup_s": t1 - t0, "ms_per_solve": (t2 - t1) / SU3_RHS * 1e3, "iters": [st["iters"] for st in sts],
+            "solves_per_s_incl_setup": nrhs / (t2 - t0), "solves_per_s_excl_setup": nrhs / (t2 - t1),
+            "setup_s": t1 - t0, "ms_per_solve": (t2 - t1) / nrhs * 1e3, "iters": [st["iters"] for st in sts],
             "coarse_iters": [st["coarsest_iters"] for st in sts], "converged": all(st["converged"] for st in sts),
             "worst_true_rel_residual": max(st["true_rel_residual"] for st in sts)}
     return out
@@ -498,6 +498,9 @@ def run_only(case: str):
     if case == "su3":
         print(json.dumps({"case": case, **su3_workload()}))
         return
+    if case == "su3-prof":  # mixed precision, setup and 2 solves (launch-list profiling)
+        print(json.dumps({"case": case, **su3_workload((1,), 2)}))
+        return
     if case.startswith("dslash4"):
         r = dslash4_roofline(1 if case == "dslash4-f32" else 0, iters=3)
         print(json.dumps({"case": case, **r}))
@@ -588,7 +591,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--only", default=None, choices=["dslash-f32", "dslash-f64", "dslash4-f32", "dslash4-f64", "solve", "vcycle",
-                                                      "transfer", "coarse-tc", "su3"],
+                                                      "transfer", "coarse-tc", "su3", "su3-prof"],
                     help="profiling cases: the Dslash timing loop alone (2d, or 4d SU(3)), one beta's setup + 3 solves, "
                          "25 mixed-precision V-cycles after one beta's setup, or 5 V-cycles on a 1024^2 "
                          "hierarchy (fine level larger than L2, for the restriction and prolongation), or the "
