@@ -34,13 +34,13 @@ struct Engine4 {
   Coarse4 cg{};
   long long nf = 0, nc = 0;  // fine / coarse dofs
   int N = 0;
-  DevBuf<Cx<double>> U64, nullv, V64, Y64, Minv64;
-  DevBuf<Cx<float>> U32, V32, Y32, Minv32;
+  DevBuf<Cx<double>> U64, nullv, V64, Y64, Minv64, Yt64;  // Yt: A M, the preconditioned stencil
+  DevBuf<Cx<float>> U32, V32, Yt32, Minv32;
   DevBuf<int> info;  // set by the block inversion when a self block is singular
   // V-cycle work
   DevBuf<Cx<double>> vr64, vAr64, vx64, vb64;
   DevBuf<Cx<float>> vr32, vAr32, vx32, vb32;
-  DevBuf<Cx<double>> cb, cx;  // coarse right-hand side / solution (FP64)
+  DevBuf<Cx<double>> cb, cx, cy;  // coarse right-hand side / solution / preconditioned solution (FP64)
   DevBuf<Cx<float>> cb32, cx32;
   DevBuf<Cx<double>> cZ, cW, cr;  // coarse GCR
   DevBuf<Cx<double>> oZ, oW, orr, t64;  // outer GCR, setup scratch
@@ -53,6 +53,7 @@ struct Engine4 {
   DevBuf<Cx<float>> sx32, sr32, sAr32;  // setup relaxation batch (MG_FP32)
   DevBuf<Cx<double>> sr64, sAr64;       // setup relaxation batch (MG_FP64; x is the vector set itself)
   ReduceWs ws{};
+  ReduceWs wsc{};  // the same workspace with fewer blocks per reduction (coarse vectors are short)
   double *host = nullptr;  // pinned: [0, 256) outer, [256, 512) coarse
   long long apps[MG_MAX_LEVELS] = {0, 0, 0, 0};
   long long coarsest_iters = 0;
@@ -88,13 +89,10 @@ void fine_apply(Engine4 &e, const Cx<R> *in, Cx<R> *out, const Cx<R> *b = nullpt
   ++e.apps[0];
 }
 
-// out = a A_c in + c b on FP64 vectors; `fast`: the FP32 copy of the operator (FP32 sums)
+// out = a A_c in + c b on FP64 vectors
 void coarse_apply64(Engine4 &e, const Cx<double> *in, Cx<double> *out, const Cx<double> *b = nullptr, double a = 1.0,
-                    double c = 0.0, bool fast = false) {
-  if (fast)
-    launch_coarse4_apply<float, double>(e.Y32.p, in, out, e.cg, b, a, c, e.s);
-  else
-    launch_coarse4_apply<double, double>(e.Y64.p, in, out, e.cg, b, a, c, e.s);
+                    double c = 0.0) {
+  launch_coarse4_apply<double, double>(e.Y64.p, in, out, e.cg, b, a, c, e.s);
   ++e.apps[1];
 }
 
@@ -177,28 +175,25 @@ Gcr fgcr(Engine4 &e, ApplyF &&apply, PrecF &&prec, const Cx<double> *b, Cx<doubl
   return out;
 }
 
-// coarse solve: cx = A_c^{-1} cb by FP64 GCR to coarsest_tol, right-preconditioned by
-// block Jacobi (the inverses of the self blocks). With MG_FP32 and a tolerance that
-// FP32 arithmetic can reach (>= 1e-5), the operator and the preconditioner are applied
-// from their FP32 copies; the Krylov vectors stay FP64.
+// coarse solve: cx = A_c^{-1} cb by GCR to coarsest_tol on A M y = b, x = M y, with M the
+// inverses of the coarse self blocks (block Jacobi) folded into the stencil A M. The
+// Gram-Schmidt coefficients are formed on the device, so the host reads the residual
+// estimate only every 4 iterations. With MG_FP32 and a tolerance FP32 arithmetic can reach
+// (>= 1e-5), the stencil and M are applied from their FP32 copies; the Krylov vectors
+// and reductions stay FP64.
 long long coarse_solve(Engine4 &e) {
   const bool fast = e.f32 && e.p.coarsest_tol >= 1e-5;
   auto apply = [&](const Cx<double> *in, Cx<double> *out, const Cx<double> *b = nullptr) {
-    if (b != nullptr)
-      coarse_apply64(e, in, out, b, -1.0, 1.0, fast);
-    else
-      coarse_apply64(e, in, out, nullptr, 1.0, 0.0, fast);
-  };
-  auto prec = [&](const Cx<double> *r, Cx<double> *z) {
     if (fast)
-      launch_block_apply4<float>(e.Minv32.p, r, z, e.cg, e.s);
+      launch_coarse4_apply<float, double>(e.Yt32.p, in, out, e.cg, b, b ? -1.0 : 1.0, b ? 1.0 : 0.0, e.s);
     else
-      launch_block_apply4<double>(e.Minv64.p, r, z, e.cg, e.s);
+      launch_coarse4_apply<double, double>(e.Yt64.p, in, out, e.cg, b, b ? -1.0 : 1.0, b ? 1.0 : 0.0, e.s);
+    ++e.apps[1];
   };
   const long long n = e.nc;
-  Cx<double> *x = e.cx.p, *r = e.cr.p, *Z = e.cZ.p, *W = e.cW.p;
+  Cx<double> *x = e.cy.p, *r = e.cr.p, *Z = e.cZ.p, *W = e.cW.p;
   const Cx<double> *b = e.cb.p;
-  double *dots = e.scal.p + kScalCoarse, *coef = dots + 200, *state = dots + 204;
+  double *dots = e.scal.p + kScalCoarse, *state = dots + 204;
   double *h = e.host + kScalCoarse;
   auto fetch = [&](const double *src) {
     MG_CUDA(cudaMemcpyAsync(h, src, sizeof(double), cudaMemcpyDeviceToHost, e.s));
@@ -208,34 +203,37 @@ long long coarse_solve(Engine4 &e) {
   };
   launch_zero<double>(x, n, e.s);
   launch_copy<double>(b, r, n, e.s);
-  launch_norm2<double>(b, n, dots, e.ws, e.s);
+  launch_norm2<double>(b, n, dots, e.wsc, e.s);
   const double bn2 = fetch(dots);
-  if (!(bn2 > 0.0)) return 0;
-  const double tol2 = e.p.coarsest_tol * e.p.coarsest_tol * bn2;
-  const int restart = e.p.coarsest_restart, max_iter = e.p.coarsest_max_iter;
-  constexpr int kCheck = 4;  // iterations between host reads of the residual estimate
   long long iters = 0;
-  while (iters < max_iter) {
-    int k = 0;
-    bool done = false;
-    for (; k < restart && iters < max_iter; ++k) {
-      Cx<double> *z = Z + (long long)k * n, *w = W + (long long)k * n;
-      prec(r, z);
-      apply(z, w);
-      launch_gcr_dots(W, w, r, k, n, dots, e.ws, e.s);
-      launch_gcr_coef(dots, k, coef, state, e.s);
-      launch_gcr_update_dev(W, w, Z, z, k, dots, coef, x, r, n, e.s);
-      ++iters;
-      if ((k + 1) % kCheck == 0 && fetch(state) <= tol2) {
-        done = true;
-        ++k;
-        break;
+  if (bn2 > 0.0) {
+    const double tol2 = e.p.coarsest_tol * e.p.coarsest_tol * bn2;
+    const int restart = e.p.coarsest_restart, max_iter = e.p.coarsest_max_iter;
+    constexpr int kCheck = 4;  // iterations between host reads of the residual estimate
+    while (iters < max_iter) {
+      int k = 0;
+      for (; k < restart && iters < max_iter; ++k) {
+        Cx<double> *z = Z + (long long)k * n, *w = W + (long long)k * n;
+        launch_copy<double>(r, z, n, e.s);
+        apply(z, w);
+        launch_gcr_dots(W, w, r, k, n, dots, e.wsc, e.s);
+        launch_gcr_update_dev(W, w, Z, z, k, dots, state, x, r, n, e.s);
+        ++iters;
+        if ((k + 1) % kCheck == 0 && fetch(state) <= tol2) {
+          ++k;
+          break;
+        }
       }
+      apply(x, r, b);  // true residual
+      launch_norm2<double>(r, n, dots, e.wsc, e.s);
+      if (fetch(dots) <= tol2) break;
     }
-    apply(x, r, b);  // true residual
-    launch_norm2<double>(r, n, dots, e.ws, e.s);
-    if (fetch(dots) <= tol2 || (done && k == 0)) break;
   }
+  // x = M y
+  if (fast)
+    launch_block_apply4<float>(e.Minv32.p, x, e.cx.p, e.cg, e.s);
+  else
+    launch_block_apply4<double>(e.Minv64.p, x, e.cx.p, e.cg, e.s);
   e.coarsest_iters += iters;
   return iters;
 }
@@ -326,12 +324,14 @@ void precondition(Engine4 &e, const Cx<double> *r, Cx<double> *z) {
     vcycle<double>(e, r, z);
 }
 
-// block-Jacobi inverses of the coarse self blocks, then the FP32 copies (MG_FP32)
+// block-Jacobi inverses of the coarse self blocks and the preconditioned stencil A M, then
+// the FP32 copies (MG_FP32)
 void prepare_coarse(Engine4 &e) {
   launch_block_invert4(e.Y64.p, e.Minv64.p, e.cg, e.info.p, e.s);
+  launch_precondition4(e.Y64.p, e.Minv64.p, e.Yt64.p, e.cg, e.s);
   if (!e.f32) return;
   launch_convert<float, double>(e.V64.p, e.V32.p, e.V64.n, e.s);
-  launch_convert<float, double>(e.Y64.p, e.Y32.p, e.Y64.n, e.s);
+  launch_convert<float, double>(e.Yt64.p, e.Yt32.p, e.Yt64.n, e.s);
   launch_convert<float, double>(e.Minv64.p, e.Minv32.p, e.Minv64.n, e.s);
 }
 
@@ -433,6 +433,7 @@ Engine4 *engine4_create(const mg_geom *g, const void *U, double m, const mg_para
   e->V64.alloc((size_t)e->bg.nblocks * e->N * e->bg.bvol * 6);
   e->Y64.alloc((size_t)e->bg.nblocks * 9 * e->N * e->N);
   e->Minv64.alloc((size_t)e->bg.nblocks * e->N * e->N);
+  e->Yt64.alloc(e->Y64.n);
   e->info.alloc(1);
   e->vr64.alloc(e->nf);
   e->vAr64.alloc(e->nf);
@@ -441,7 +442,7 @@ Engine4 *engine4_create(const mg_geom *g, const void *U, double m, const mg_para
   if (e->f32) {
     e->U32.alloc(e->U64.n);
     e->V32.alloc(e->V64.n);
-    e->Y32.alloc(e->Y64.n);
+    e->Yt32.alloc(e->Y64.n);
     e->Minv32.alloc(e->Minv64.n);
     e->vr32.alloc(e->nf);
     e->vAr32.alloc(e->nf);
@@ -452,6 +453,7 @@ Engine4 *engine4_create(const mg_geom *g, const void *U, double m, const mg_para
   }
   e->cb.alloc(e->nc);
   e->cx.alloc(e->nc);
+  e->cy.alloc(e->nc);
   e->cZ.alloc((size_t)p->coarsest_restart * e->nc);
   e->cW.alloc((size_t)p->coarsest_restart * e->nc);
   e->cr.alloc(e->nc);
@@ -484,6 +486,8 @@ Engine4 *engine4_create(const mg_geom *g, const void *U, double m, const mg_para
   MG_CUDA(cudaMemsetAsync(e->info.p, 0, sizeof(int), s));
   e->ws.partials = e->partials.p;
   e->ws.ticket = e->tickets.p;
+  e->wsc = e->ws;
+  e->wsc.max_blocks = 8;
   MG_CUDA(cudaMemcpyAsync(e->U64.p, U, e->U64.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, s));
   if (e->f32) launch_convert<float, double>(e->U64.p, e->U32.p, e->U64.n, s);
   setup(*e);

@@ -53,13 +53,14 @@ void launch_block_invert4(const Cx<double> *Y, Cx<double> *Minv, const Coarse4 &
 // z_j = Minv_j r_j (vectors FP64, Minv in R)
 template <typename R>
 void launch_block_apply4(const Cx<R> *Minv, const Cx<double> *r, Cx<double> *z, const Coarse4 &g, cudaStream_t s);
-// GCR step with device-side coefficients: coef = (inv, Re alpha, Im alpha) and
-// state[0] = |r|^2 - |alpha|^2 from the reduction of launch_gcr_dots; then the fused
-// projection / normalisation / x, r update reading them
-void launch_gcr_coef(const double *dots, int k, double *coef, double *state, cudaStream_t s);
+// GCR step with device-side coefficients formed from the reduction of launch_gcr_dots:
+// projection, normalisation and the x, r update; state[0] = |r|^2 - |alpha|^2
 void launch_gcr_update_dev(const Cx<double> *W, Cx<double> *Wk, const Cx<double> *Z, Cx<double> *Zk, int k,
-                           const double *beta, const double *coef, Cx<double> *x, Cx<double> *r, long long n,
+                           const double *dots, double *state, Cx<double> *x, Cx<double> *r, long long n,
                            cudaStream_t s);
+// Yt[j][dir] = Y[j][dir] Minv[src(j, dir)]: the block-Jacobi right-preconditioned stencil A M
+void launch_precondition4(const Cx<double> *Y, const Cx<double> *Minv, Cx<double> *Yt, const Coarse4 &g,
+                          cudaStream_t s);
 // batched MR: out[3 v .. 3 v + 2] = (<a_v, b_v>, |a_v|^2) summed in R (partials: nvec x
 // max_blocks x 3 doubles, tickets: nvec zeroed counters), then x_v += alpha_v r_v,
 // r_v -= alpha_v Ar_v with alpha_v = omega <Ar_v, r_v> / |Ar_v|^2 from those sums

@@ -462,41 +462,41 @@ __global__ void block_apply4_kernel(const Cx<R> *__restrict__ Minv, const Cx<dou
 }
 
 // ---------------------------------------------------------------------------
-// GCR coefficients on the device (no host round trip per iteration): from the fused
-// reduction dots = (<W_j, w>_j<k, |w|^2, <w, r>, |r|^2) form the classical Gram-Schmidt
-// norm |w - W beta|^2 = |w|^2 - |beta|^2, inv = 1 / that norm, alpha = <w, r> inv, and
-// the residual estimate |r|^2 - |alpha|^2 (state[0]). A breakdown (no new direction)
-// gives inv = alpha = 0: the step then changes nothing.
+// GCR step with the coefficients formed on the device (no host round trip per
+// iteration): from the fused reduction dots = (<W_j, w>_j<k, |w|^2, <w, r>, |r|^2) each
+// CTA forms the classical Gram-Schmidt norm |w - W beta|^2 = |w|^2 - |beta|^2,
+// inv = 1 / that norm and alpha = <w, r> inv (a breakdown gives inv = alpha = 0: the
+// step changes nothing); CTA 0 also stores the residual estimate |r|^2 - |alpha|^2 in
+// state[0]. Then w <- (w - sum_j beta_j W_j) inv, z likewise; W_k = w, Z_k = z;
+// x += alpha z; r -= alpha w.
 // ---------------------------------------------------------------------------
-__global__ void gcr_coef_kernel(const double *__restrict__ dots, int k, double *__restrict__ coef,
-                                double *__restrict__ state) {
-  const double nw0 = dots[2 * k];
-  double nw2 = nw0;
-  for (int j = 0; j < k; ++j) nw2 -= dots[2 * j] * dots[2 * j] + dots[2 * j + 1] * dots[2 * j + 1];
-  double inv = 0.0, are = 0.0, aim = 0.0;
-  if (nw2 > 1e-28 * nw0) {
-    inv = 1.0 / sqrt(nw2);
-    are = dots[2 * k + 2] * inv;
-    aim = dots[2 * k + 3] * inv;
-  }
-  coef[0] = inv;
-  coef[1] = are;
-  coef[2] = aim;
-  state[0] = fmax(dots[2 * k + 4] - (are * are + aim * aim), 0.0);
-}
-
-// w <- (w - sum_j beta_j W_j) inv, z likewise; W_k = w, Z_k = z; x += alpha z; r -= alpha w,
-// with beta (dots) and (inv, alpha) (coef) read from device memory
 __global__ void gcr_update_dev_kernel(const Cx<double> *__restrict__ W, Cx<double> *__restrict__ Wk,
                                       const Cx<double> *__restrict__ Z, Cx<double> *__restrict__ Zk, int k,
-                                      const double *__restrict__ beta, const double *__restrict__ coef,
+                                      const double *__restrict__ dots, double *__restrict__ state,
                                       Cx<double> *__restrict__ x, Cx<double> *__restrict__ r, long long n) {
+  __shared__ double coef[3];
+  if (threadIdx.x == 0) {
+    const double nw0 = dots[2 * k];
+    double nw2 = nw0;
+    for (int j = 0; j < k; ++j) nw2 -= dots[2 * j] * dots[2 * j] + dots[2 * j + 1] * dots[2 * j + 1];
+    double inv = 0.0, are = 0.0, aim = 0.0;
+    if (nw2 > 1e-28 * nw0) {
+      inv = 1.0 / sqrt(nw2);
+      are = dots[2 * k + 2] * inv;
+      aim = dots[2 * k + 3] * inv;
+    }
+    coef[0] = inv;
+    coef[1] = are;
+    coef[2] = aim;
+    if (blockIdx.x == 0) state[0] = fmax(dots[2 * k + 4] - (are * are + aim * aim), 0.0);
+  }
+  __syncthreads();
   const double inv = coef[0];
   const Cx<double> alpha = mk(coef[1], coef[2]), malpha = mk(-coef[1], -coef[2]);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     Cx<double> w = Wk[i], z = Zk[i];
     for (int j = 0; j < k; ++j) {
-      const Cx<double> bj = mk(-beta[2 * j], -beta[2 * j + 1]);
+      const Cx<double> bj = mk(-dots[2 * j], -dots[2 * j + 1]);
       cmac(w, bj, W[(long long)j * n + i]);
       cmac(z, bj, Z[(long long)j * n + i]);
     }
@@ -509,6 +509,35 @@ __global__ void gcr_update_dev_kernel(const Cx<double> *__restrict__ W, Cx<doubl
     cmac(ri, malpha, w);
     r[i] = ri;
   }
+}
+
+// Yt[j][dir] = Y[j][dir] Minv[src(j, dir)] (column-major blocks): the block-Jacobi
+// right-preconditioned stencil A M, one thread per entry
+__global__ void precondition4_kernel(const Cx<double> *__restrict__ Y, const Cx<double> *__restrict__ Minv,
+                                     Cx<double> *__restrict__ Yt, Coarse4 g) {
+  const int N = g.N;
+  const long long per = 9LL * N * N;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= g.nsites * per) return;
+  const long long j = t / per;
+  const int rem = (int)(t - j * per), dir = rem / (N * N), cr = rem - dir * N * N, col = cr / N, row = cr - col * N;
+  long long src = j;
+  if (dir != 0) {
+    int jc[4];
+    long long q = j;
+    for (int mu = 0; mu < 4; ++mu) {
+      jc[mu] = (int)(q % g.nb[mu]);
+      q /= g.nb[mu];
+    }
+    const int mu = (dir - 1) >> 1;
+    jc[mu] = ((dir - 1) & 1) == 0 ? (jc[mu] + 1) % g.nb[mu] : (jc[mu] + g.nb[mu] - 1) % g.nb[mu];
+    src = jc[0] + (long long)g.nb[0] * (jc[1] + (long long)g.nb[1] * (jc[2] + (long long)g.nb[2] * jc[3]));
+  }
+  const Cx<double> *Yd = Y + (j * 9 + dir) * (long long)N * N;
+  const Cx<double> *Ms = Minv + src * (long long)N * N;
+  Cx<double> acc = mk(0.0, 0.0);
+  for (int q = 0; q < N; ++q) cmac(acc, Yd[(long long)q * N + row], Ms[(long long)col * N + q]);
+  Yt[t] = acc;
 }
 
 // ---------------------------------------------------------------------------
@@ -660,17 +689,19 @@ void launch_block_apply4(const Cx<R> *Minv, const Cx<double> *r, Cx<double> *z, 
   MG_LAUNCHED();
 }
 
-void launch_gcr_coef(const double *dots, int k, double *coef, double *state, cudaStream_t s) {
-  gcr_coef_kernel<<<1, 1, 0, s>>>(dots, k, coef, state);
-  MG_LAUNCHED();
-}
-
 void launch_gcr_update_dev(const Cx<double> *W, Cx<double> *Wk, const Cx<double> *Z, Cx<double> *Zk, int k,
-                           const double *beta, const double *coef, Cx<double> *x, Cx<double> *r, long long n,
+                           const double *dots, double *state, Cx<double> *x, Cx<double> *r, long long n,
                            cudaStream_t s) {
   long long b = (n + 255) / 256;
   if (b > 152LL * 16) b = 152LL * 16;
-  gcr_update_dev_kernel<<<(unsigned int)(b < 1 ? 1 : b), 256, 0, s>>>(W, Wk, Z, Zk, k, beta, coef, x, r, n);
+  gcr_update_dev_kernel<<<(unsigned int)(b < 1 ? 1 : b), 256, 0, s>>>(W, Wk, Z, Zk, k, dots, state, x, r, n);
+  MG_LAUNCHED();
+}
+
+void launch_precondition4(const Cx<double> *Y, const Cx<double> *Minv, Cx<double> *Yt, const Coarse4 &g,
+                          cudaStream_t s) {
+  const long long total = g.nsites * 9LL * g.N * g.N;
+  precondition4_kernel<<<grid_for(total, 256), 256, 0, s>>>(Y, Minv, Yt, g);
   MG_LAUNCHED();
 }
 
