@@ -256,6 +256,13 @@ int mg_smooth_fine_noalloc(const mg_geom *g, const void *U, double m, const void
  * context or N != 8). */
 int mg_coarse_apply_mrhs(mg_ctx *ctx, int level, int nrhs, const void *in, void *out, int tensor_cores);
 
+/* Launch shapes picked by the library's autotuner so far (the tensor-core coarse apply
+ * times its six tile shapes -- warps per CTA x vector tiles per warp -- on first use for
+ * each lattice and vector count, and keeps the fastest; all shapes give bitwise the same
+ * result). Writes "key=variant;..." into buf (NUL-terminated, truncated to len - 1
+ * characters) and returns the full length. buf may be NULL when len is 0. */
+size_t mg_autotune_report(char *buf, size_t len);
+
 /* Self-test of the bounded device-side wait used by the persistent kernels (a
  * failure-detection check; the paper has no counterpart). Launches a 2-CTA
  * cooperative kernel whose grid barrier expects 2 + missing_arrivals arrivals

@@ -94,6 +94,7 @@ def load():
         "mg_smooth_fine_noalloc": (I, [P(mg_geom), VP, D, VP, VP, I, D, VP]),
         "mg_coarsest_solve": (I, [ctxp, VP, VP, P(ctypes.c_longlong), P(D)]),
         "mg_selftest_barrier": (I, [I, VP]),
+        "mg_autotune_report": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -109,7 +110,21 @@ def exported_symbols():
             "mg_dslash", "mg_level_apply", "mg_restrict", "mg_prolong", "mg_vcycle", "mg_smooth", "mg_build_level",
             "mg_get_null_vectors", "mg_get_prolongator", "mg_get_coarse_op", "mg_level_size", "mg_kernel_launches",
             "mg_smooth_fine_noalloc", "mg_coarsest_solve", "mg_selftest_barrier", "mg_solve_batch",
-            "mg_coarse_apply_mrhs"]
+            "mg_coarse_apply_mrhs", "mg_autotune_report"]
+
+
+def autotune_report() -> dict:
+    """mg_autotune_report: {kernel/shape key: chosen launch variant} of the library's autotuner."""
+    lib = load()
+    n = lib.mg_autotune_report(None, 0)
+    buf = ctypes.create_string_buffer(n + 1)
+    lib.mg_autotune_report(buf, n + 1)
+    out = {}
+    for item in buf.value.decode().split(";"):
+        if item:
+            k, v = item.rsplit("=", 1)
+            out[k] = int(v)
+    return out
 
 
 def _check(code: int):

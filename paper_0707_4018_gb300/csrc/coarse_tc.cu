@@ -19,6 +19,8 @@
 // direction), the size of the complex block in 16-bit storage.
 #include <cuda_bf16.h>
 
+#include <string>
+
 #include "kernels.h"
 
 namespace mg {
@@ -48,18 +50,13 @@ __device__ __forceinline__ void mma_bf16_16816(float (&c)[4], unsigned int a0, u
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-// out_n = a (A + shift_n) in_n + c b_n for the nvec vectors (stride ldv); one warp per
-// (site, group of 8 vectors)
-__global__ void __launch_bounds__(256) coarse_apply_tc_kernel(const uint2 *__restrict__ Ypk,
-                                                              const Cx<float> *__restrict__ in,
-                                                              Cx<float> *__restrict__ out, int L0, int L1,
-                                                              long long ldv, int nvec, const Cx<float> *b,
-                                                              float a, float c, const double *shift) {
-  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const long long V = (long long)L0 * L1;
-  const int tiles = (nvec + 7) >> 3;
-  if (w >= V * tiles) return;  // whole warps
+// out_n = a (A + shift_n) in_n + c b_n for the nvec vectors (stride ldv), item w = (site j,
+// group of 8 vectors), j = w / tiles
+__device__ __forceinline__ void tc_item(long long w, int lane, const uint2 *__restrict__ Ypk,
+                                        const Cx<float> *__restrict__ in, Cx<float> *__restrict__ out, int L0, int L1,
+                                        long long ldv, int nvec, int tiles, const Cx<float> *b, float a, float c,
+                                        const double *shift) {
+  const int g = lane >> 2, t = lane & 3;
   const long long j = w / tiles;
   const int n0 = (int)(w - j * tiles) * 8;
   const int x1 = (int)(j / L0), x0 = (int)(j - (long long)x1 * L0);
@@ -101,18 +98,55 @@ __global__ void __launch_bounds__(256) coarse_apply_tc_kernel(const uint2 *__res
   }
 }
 
+// one warp per SPW consecutive items; the launch shape (warps per CTA, SPW) changes
+// neither the arithmetic nor its order
+template <int SPW>
+__global__ void __launch_bounds__(256) coarse_apply_tc_kernel(const uint2 *__restrict__ Ypk,
+                                                              const Cx<float> *__restrict__ in,
+                                                              Cx<float> *__restrict__ out, int L0, int L1,
+                                                              long long ldv, int nvec, const Cx<float> *b,
+                                                              float a, float c, const double *shift) {
+  const long long w0 = ((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5) * SPW;
+  const int lane = threadIdx.x & 31;
+  const int tiles = (nvec + 7) >> 3;
+  const long long items = (long long)L0 * L1 * tiles;
+#pragma unroll
+  for (int q = 0; q < SPW; ++q)
+    if (w0 + q < items) tc_item(w0 + q, lane, Ypk, in, out, L0, L1, ldv, nvec, tiles, b, a, c, shift);
+}
+
 void launch_pack_coarse_bf16(const Cx<float> *Y, uint2 *Ypk, long long nsites, cudaStream_t s) {
   pack_coarse_bf16_kernel<<<grid_for(nsites * 5 * 32, 256), 256, 0, s>>>(Y, Ypk, nsites);
+  MG_LAUNCHED();
+}
+
+// launch shapes: (warps per CTA, items per warp)
+static const int kTcShapes[6][2] = {{8, 1}, {4, 1}, {2, 1}, {8, 2}, {4, 2}, {2, 2}};
+
+static void tc_launch(int shape, const uint2 *Ypk, const Cx<float> *in, Cx<float> *out, Geo2 g, int nvec,
+                      const Cx<float> *b, double a, double c, const double *shift, cudaStream_t s) {
+  const int wpc = kTcShapes[shape][0], spw = kTcShapes[shape][1];
+  const long long items = g.nsites * ((nvec + 7) / 8);
+  const long long warps = (items + spw - 1) / spw;
+  const unsigned int grid = grid_for(warps, wpc);
+  if (spw == 1)
+    coarse_apply_tc_kernel<1><<<grid, 32 * wpc, 0, s>>>(Ypk, in, out, g.L0, g.L1, g.nsites * 8, nvec, b, (float)a,
+                                                        (float)c, shift);
+  else
+    coarse_apply_tc_kernel<2><<<grid, 32 * wpc, 0, s>>>(Ypk, in, out, g.L0, g.L1, g.nsites * 8, nvec, b, (float)a,
+                                                        (float)c, shift);
   MG_LAUNCHED();
 }
 
 void launch_coarse_apply_tc(const uint2 *Ypk, const Cx<float> *in, Cx<float> *out, Geo2 g, int nvec,
                             const Cx<float> *b, double a, double c, const double *shift, cudaStream_t s) {
   if (nvec < 1) return;
-  const long long warps = g.nsites * ((nvec + 7) / 8);
-  coarse_apply_tc_kernel<<<grid_for(warps * 32, 256), 256, 0, s>>>(Ypk, in, out, g.L0, g.L1, g.nsites * 8, nvec, b,
-                                                                   (float)a, (float)c, shift);
-  MG_LAUNCHED();
+  // the launch shape is picked once per problem shape by timing all six (the result does not
+  // depend on it)
+  const std::string key = "coarse_apply_tc/" + std::to_string(g.L0) + "x" + std::to_string(g.L1) + "/nvec" +
+                          std::to_string(nvec);
+  const int shape = autotune_choose(key, 6, [&](int v) { tc_launch(v, Ypk, in, out, g, nvec, b, a, c, shift, s); }, s);
+  tc_launch(shape, Ypk, in, out, g, nvec, b, a, c, shift, s);
 }
 
 }  // namespace mg

@@ -2,6 +2,9 @@
 // on the given stream). R is double or float; complex fields are Cx<R>.
 #pragma once
 
+#include <functional>
+#include <string>
+
 #include "common.cuh"
 
 namespace mg {
@@ -66,6 +69,16 @@ void launch_pack_coarse_bf16(const Cx<float> *Y, uint2 *Ypk, long long nsites, c
 // (b and shift may be null)
 void launch_coarse_apply_tc(const uint2 *Ypk, const Cx<float> *in, Cx<float> *out, Geo2 g, int nvec,
                             const Cx<float> *b, double a, double c, const double *shift, cudaStream_t s);
+
+// ---- autotuner of launch shapes (autotune.cu) ----
+// Index of the fastest of `count` launch variants of one kernel for one problem shape, by
+// timing each on stream s (one untimed launch, then three timed with CUDA events); cached
+// under `key` for the process. Every variant must compute the same result: only the launch
+// shape may differ. While s is being captured into a graph an unknown key is not timed and
+// variant 0 is returned (uncached).
+int autotune_choose(const std::string &key, int count, const std::function<void(int)> &launch, cudaStream_t s);
+// "key=variant;..." for every cached choice
+std::string autotune_report();
 
 // ---- BLAS-1 ----
 template <typename R>

@@ -1424,6 +1424,16 @@ int mg_coarse_apply_mrhs(mg_ctx *c, int level, int nrhs, const void *in, void *o
   });
 }
 
+size_t mg_autotune_report(char *buf, size_t len) {
+  const std::string r = autotune_report();
+  if (buf != nullptr && len > 0) {
+    const size_t m = std::min(len - 1, r.size());
+    std::memcpy(buf, r.data(), m);
+    buf[m] = '\0';
+  }
+  return r.size();
+}
+
 int mg_selftest_barrier(int missing_arrivals, void *stream) {
   return guarded([&] {
     if (missing_arrivals < 0 || missing_arrivals > 1) fail(MG_ERR_INVALID_ARG, "missing_arrivals must be 0 or 1");
