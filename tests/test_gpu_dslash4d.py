@@ -29,7 +29,8 @@ def _field(dims, seed, smooth=True):
 
 
 @pytest.mark.parametrize("dims,smooth", [((2, 2, 2, 2), False), ((4, 4, 4, 4), True), ((6, 4, 2, 8), False),
-                                         ((5, 3, 7, 2), True), ((8, 8, 8, 16), True)])
+                                         ((5, 3, 7, 2), True), ((8, 8, 8, 16), True), ((8, 4, 4, 2), False),
+                                         ((16, 8, 4, 6), False)])
 def test_dslash4d_fp64_matches_oracle(dims, smooth):
     lat = Lattice(dims)
     U = _field(dims, 31, smooth)
@@ -58,7 +59,7 @@ def test_dslash4d_free_plane_wave_closed_form():
     np.testing.assert_allclose(got, ph[:, None, None] * (Dp @ u)[None], atol=1e-13)
 
 
-@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (16, 16, 16, 32), (6, 10, 4, 2)])
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (16, 16, 16, 32), (6, 10, 4, 2), (8, 4, 4, 2)])
 def test_dslash4d_fp32_per_site_error_below_1e6(dims):
     # reference: FP64 D on the same FP32-rounded inputs; per-site error relative to
     # |diag psi_x| + 1/2 sum |hop terms_x| (bounds the cancellation at that site)
