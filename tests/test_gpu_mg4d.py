@@ -163,3 +163,52 @@ def test_su3_workload_16x16x16x32_true_residual():
     res = np.linalg.norm(chi - wilson.apply_D(U, got.reshape(-1, 4, 3), m, lat).reshape(chi.shape))
     assert st["converged"] and res <= 1e-10 * np.linalg.norm(chi) * 1.01, (st, res / np.linalg.norm(chi))
     ctx.close()
+
+
+def test_update_mass_rebuilds_galerkin_like_oracle():
+    import paper_0707_4018_gb300 as mg
+    dims, block, nv = (4, 4, 4, 8), (2, 2, 2, 2), 4
+    U = inputs.su3_links(dims, seed=24)
+    ctx = mg.Context.setup(to_dev(U), 0.1, dims, _params(block, nv, n_pass=1, nu_setup=4))
+    vecs = to_host(ctx.null_vectors(0))
+    ctx.update_mass(0.35)
+    hier = _oracle_hier(U, 0.35, dims, block, nv)
+    hier.build_level(0, list(vecs))
+    Y = to_host(ctx.coarse_op(1))
+    assert np.abs(Y - hier.ops[1].Y).max() < 1e-12 * np.abs(hier.ops[1].Y).max()
+    ctx.close()
+
+
+def test_smooth_matches_oracle_mr():
+    import torch
+    import paper_0707_4018_gb300 as mg
+    dims = (4, 4, 4, 8)
+    lat = Lattice(dims)
+    U = inputs.su3_links(dims, seed=25)
+    m = 0.2
+    ctx = mg.Context.setup(to_dev(U), m, dims, _params((2, 2, 2, 2), 4, n_pass=1, nu_setup=2))
+    b = inputs.gaussian_spinor(lat.volume, 12, 44, 0)
+    x = torch.empty((lat.volume, 12), dtype=torch.complex128, device="cuda")
+    ctx.smooth(0, to_dev(b), x, 6)
+    want, _ = solvers.mr(lambda v: wilson.apply_D(U, v.reshape(-1, 4, 3), m, lat).reshape(v.shape), b, 6,
+                         ctx.params.omega)
+    assert rel_err(to_host(x), want) < 1e-12
+    ctx.close()
+
+
+def test_solves_are_bitwise_reproducible():
+    import torch
+    import paper_0707_4018_gb300 as mg
+    dims = (8, 8, 8, 8)
+    lat = Lattice(dims)
+    U = inputs.su3_links(dims, seed=26)
+    chi = to_dev(inputs.gaussian_spinor(lat.volume, 12, 45, 0))
+    outs = []
+    for _ in range(2):
+        ctx = mg.Context.setup(to_dev(U), 0.05, dims, _params((4, 4, 4, 4), 6, 1, n_pass=1, nu_setup=20,
+                                                              coarsest_tol=0.05))
+        psi = torch.empty((lat.volume, 12), dtype=torch.complex128, device="cuda")
+        assert ctx.solve(chi, psi, 1e-10)["converged"]
+        outs.append(psi)
+        ctx.close()
+    assert torch.equal(outs[0], outs[1])
