@@ -127,7 +127,10 @@ class ClockSampler:
 
 
 def _one_field(f, precision, stats_out, host_io, contexts):
-    """One beta: setup at the lightest mass and the three solves (update_mass between them)."""
+    """One beta: setup at the lightest mass and the three solves. Concurrent mode: the setup is
+    cloned for the two heavier masses (mg_clone rebuilds the Galerkin operators) and the three
+    solves run at once, one host thread and context stream each; serial mode: update_mass
+    between the solves."""
     import paper_0707_4018_gb300 as mg
     if host_io is not None:
         U = f["U_host"].to("cuda", non_blocking=True)
@@ -135,23 +138,45 @@ def _one_field(f, precision, stats_out, host_io, contexts):
         U = f["U_dev"]
     ctx = mg.Context.setup(U, f["m_c"] + DMS[0], (L, L), mg_params(precision))
     contexts.append(ctx)
-    n = 0
-    for i, dm in enumerate(DMS):
-        if i > 0:
-            ctx.update_mass(f["m_c"] + dm)
+
+    def solve(c, i, dm):
         chi = f["chi_host"][i].to("cuda", non_blocking=True) if host_io is not None else f["chi_dev"][i]
         psi = f["psi_dev"][i]
-        st = ctx.solve(chi, psi, TOL)
+        st = c.solve(chi, psi, TOL)
         if host_io is not None:
             host_io[f["beta"]][i].copy_(psi, non_blocking=True)
         if stats_out is not None:
             stats_out.append(dict(beta=f["beta"], dm=dm, **st))
-        n += 1
-    return n
+
+    if not CONCURRENT:
+        for i, dm in enumerate(DMS):
+            if i > 0:
+                ctx.update_mass(f["m_c"] + dm)
+            solve(ctx, i, dm)
+        return len(DMS)
+    ctxs = [ctx] + [ctx.clone(f["m_c"] + dm) for dm in DMS[1:]]
+    contexts.extend(ctxs[1:])
+    errors = []
+
+    def work(i):
+        try:
+            solve(ctxs[i], i, DMS[i])
+        except BaseException as e:  # re-raised on the calling thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(len(DMS))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    if errors:
+        raise errors[0]
+    return len(DMS)
 
 
-# The betas are independent problems with their own contexts (own streams): one host thread
-# each lets their small, latency-bound kernels overlap on the GPU. --serial runs them in turn.
+# The betas (and, through clones of a beta's setup, its masses) are independent problems with
+# their own contexts (own streams): one host thread each lets their small, latency-bound
+# kernels overlap on the GPU. --serial runs them in turn.
 CONCURRENT = True
 
 
@@ -671,7 +696,8 @@ def main():
         "config": {"workload": WORKLOAD, "lattice": f"{L}x{L}", "betas": list(BETAS), "m_minus_mc": list(DMS),
                    "solves_per_step": len(BETAS) * len(DMS), "precision": "FP64 outer GCR, FP32 V-cycle",
                    "l2": "flushed before every timed step (512 MiB write)", "tol": TOL,
-                   "betas_run": "concurrently (one host thread and context stream each)" if CONCURRENT
+                   "betas_run": "concurrently: one host thread and context stream per beta and, through clones of "
+                                "the beta's setup (Galerkin rebuilt per mass), per mass" if CONCURRENT
                    else "one after another",
                    "gauge_digest_matches_table": all(f["digest_ok"] for f in fields) if rank == 0 else None},
         "solver": {"iters": iters, "worst_true_rel_residual": worst_res},

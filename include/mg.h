@@ -166,6 +166,18 @@ int mg_solve_batch(mg_ctx *ctx, int nrhs, const void *chi, void *psi, const doub
  * the kept prolongators and re-prepares the coarsest solve. */
 int mg_update_mass(mg_ctx *ctx, double m);
 
+/* A second context for another mass that reuses the setup of src (paper: the setup made
+ * at the lightest mass serves the heavier ones): copies src's links and near-null vectors
+ * / prolongators, builds every Galerkin operator at mass m and prepares the coarsest
+ * solve, with no relaxation or adaptive pass. The result equals mg_update_mass(src, m)
+ * applied to a copy of src; both contexts stay usable and independent (own stream,
+ * own buffers), so solves at several masses can run concurrently.
+ *   out     new context (NULL on error); free with mg_destroy
+ *   stream  cudaStream_t the new context orders its work after
+ * Errors: INVALID_ARG (null pointers), STATE (src has a stale level), UNSUPPORTED (d = 4),
+ * OOM, CUDA. */
+int mg_clone(mg_ctx *src, double m, void *stream, mg_ctx **out);
+
 /* Frees every device buffer of the context. NULL is a no-op. */
 void mg_destroy(mg_ctx *ctx);
 

@@ -77,6 +77,7 @@ def load():
         "mg_solve_batch": (I, [ctxp, I, VP, VP, P(D), D, P(mg_stats)]),
         "mg_coarse_apply_mrhs": (I, [ctxp, I, I, VP, VP, I]),
         "mg_update_mass": (I, [ctxp, D]),
+        "mg_clone": (I, [ctxp, D, VP, P(ctxp)]),
         "mg_destroy": (None, [ctxp]),
         "mg_last_error": (ctypes.c_char_p, []),
         "mg_dslash": (I, [P(mg_geom), VP, D, VP, VP, I, VP]),
@@ -110,7 +111,7 @@ def exported_symbols():
             "mg_dslash", "mg_level_apply", "mg_restrict", "mg_prolong", "mg_vcycle", "mg_smooth", "mg_build_level",
             "mg_get_null_vectors", "mg_get_prolongator", "mg_get_coarse_op", "mg_level_size", "mg_kernel_launches",
             "mg_smooth_fine_noalloc", "mg_coarsest_solve", "mg_selftest_barrier", "mg_solve_batch",
-            "mg_coarse_apply_mrhs", "mg_autotune_report"]
+            "mg_coarse_apply_mrhs", "mg_autotune_report", "mg_clone"]
 
 
 def autotune_report() -> dict:
@@ -312,6 +313,13 @@ class Context:
 
     def update_mass(self, m: float):
         _check(load().mg_update_mass(self._need(), float(m)))
+
+    def clone(self, m: float, stream=None) -> "Context":
+        """mg_clone: a new context at mass m reusing this context's setup (Galerkin rebuilt)."""
+        h = ctypes.c_void_p()
+        s = _stream(stream)
+        _check(load().mg_clone(self._need(), float(m), s, ctypes.byref(h)))
+        return Context(h, self.dims, self.params, s)
 
     def level_apply(self, level: int, inp: torch.Tensor, out: torch.Tensor):
         n = self._numel(level)

@@ -1293,6 +1293,36 @@ int mg_update_mass(mg_ctx *c, double m) {
   });
 }
 
+int mg_clone(mg_ctx *src, double m, void *stream, mg_ctx **out) {
+  return guarded([&] {
+    if (!out) fail(MG_ERR_INVALID_ARG, "null context out-pointer");
+    *out = nullptr;
+    need_ctx(src);
+    if (src->e4) fail(MG_ERR_UNSUPPORTED, "clones are built for d = 2");
+    check_fresh(*src);
+    MG_CUDA(cudaStreamSynchronize(src->s));  // the source's buffers are final
+    auto c = create(&src->geom, m, &src->p, stream);
+    MG_CUDA(cudaMemcpyAsync(c->U64.p, src->U64.p, c->U64.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, c->s));
+    if (c->p.precision == MG_FP32) launch_convert<float, double>(c->U64.p, c->U32.p, c->U64.n, c->s);
+    for (int l = 0; l + 1 < c->p.levels; ++l) {
+      Level &L = c->lv[l];
+      const Level &S = src->lv[l];
+      MG_CUDA(cudaMemcpyAsync(L.nullv.p, S.nullv.p, L.nullv.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, c->s));
+      MG_CUDA(cudaMemcpyAsync(L.V64.p, S.V64.p, L.V64.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, c->s));
+      // Galerkin operators at the clone's mass, level by level (level l + 1 needs Y of level l)
+      if (l == 0)
+        launch_galerkin_wilson(c->U64.p, diag_of(*c), L.V64.p, c->lv[1].Y64.p, L.bg, L.Nv, c->s);
+      else
+        launch_galerkin_stencil(L.Y64.p, L.V64.p, c->lv[l + 1].Y64.p, L.bg, L.Nv, c->s);
+    }
+    prepare_coarsest(*c);
+    make_fp32_copies(*c);
+    collect_coarsest(*c);
+    MG_CUDA(cudaStreamSynchronize(c->s));
+    *out = c.release();
+  });
+}
+
 void mg_destroy(mg_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->s);
