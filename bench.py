@@ -565,6 +565,38 @@ def run_only(case: str):
         print(json.dumps({"case": case, "coarse_sites": n_sites, "rhs": R, **res, "autotune": mg.autotune_report()}))
         ctx.close()
         return
+    if case == "coarse-tc4":
+        # the 4d coarse level of the 16^3 x 32 hierarchy (512 sites x 48) on 12 and 16 vectors
+        import inputs as inp
+        U4 = inp.su3_links(SU3_DIMS, seed=inp.workload_seed(3, SU3_DIMS[0], 0.0))
+        p4 = su3_params(mg.MG_FP32)
+        p4.nu_setup = 20
+        ctx = mg.Context.setup(torch.from_numpy(U4).cuda(), 0.0, SU3_DIMS, p4)
+        n_sites, n_int = ctx.level_size(1)
+        stream = torch.cuda.current_stream()
+        out = {"case": case, "coarse_sites": n_sites, "n_int": n_int}
+        for R in (12, 16):
+            g = torch.Generator(device="cuda").manual_seed(9)
+            x = torch.randn((R, n_sites, n_int), dtype=torch.complex64, device="cuda", generator=g)
+            y = torch.empty_like(x)
+            for tc in (True, False):
+                for _ in range(3):
+                    ctx.coarse_apply_mrhs(1, x, y, tc)
+                ms = []
+                for _ in range(20):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ctx.coarse_apply_mrhs(1, x, y, tc)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                t = statistics.median(ms) * 1e-3
+                out[f"{'tensor' if tc else 'cuda_core'}_rhs{R}"] = {
+                    "us_per_call_incl_sync": t * 1e6, "gflops": 9 * 48 * 48 * 8 * R * n_sites / t / 1e9}
+        print(json.dumps(out))
+        ctx.close()
+        return
     if case == "transfer":
         Lt = 1024
         p = mg.mg_default_params(levels=3, blocks=[(4, 4), (2, 2)], Nv=[8, 8], precision=mg.MG_FP32, n_pass=1,
@@ -618,7 +650,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--only", default=None, choices=["dslash-f32", "dslash-f64", "dslash4-f32", "dslash4-f64", "solve", "vcycle",
-                                                      "transfer", "coarse-tc", "su3", "su3-prof"],
+                                                      "transfer", "coarse-tc", "coarse-tc4", "su3", "su3-prof"],
                     help="profiling cases: the Dslash timing loop alone (2d, or 4d SU(3)), one beta's setup + 3 solves, "
                          "25 mixed-precision V-cycles after one beta's setup, or 5 V-cycles on a 1024^2 "
                          "hierarchy (fine level larger than L2, for the restriction and prolongation), or the "

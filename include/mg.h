@@ -258,14 +258,19 @@ int mg_smooth_fine_noalloc(const mg_geom *g, const void *U, double m, const void
 /* Coarse stencil apply on tensor cores for many right-hand sides (paper: the coarse
  * operator P^dagger D P of Eq. Galerkin applied to a block of vectors, the contraction of
  * multi-RHS solves): out_n = A_l in_n for n < nrhs.
- *   level    1..levels-1, with N = 8 dofs per coarse site
+ *   d = 2: level 1..levels-1 with N = 8 dofs per coarse site. Per site and direction the
+ *          complex 8 x 8 block is the real 16 x 16 matrix [[Re, -Im], [Im, Re]], applied with
+ *          mma.sync m16n8k16; the tile shape is chosen by the autotuner (mg_autotune_report).
+ *          Needs a context set up with precision MG_FP32 (its FP32 operator is rounded to BF16).
+ *   d = 4: level 1 with N = 48 (Nv = 24): the 48 x 48 complex block is the real 96 x 96
+ *          matrix [[A, -B], [B, A]] (A = Re Y, B = Im Y), applied as 16 x 16 tiles of A and
+ *          B (-B by a sign flip): 108 mma.sync per warp of 16 rows x 8 vectors; the FP64
+ *          operator is rounded to BF16 (either precision).
  *   in, out  device complex64 [n][site][dof], nrhs level vectors back to back (caller-owned)
- * Per site and direction the complex 8 x 8 block is applied as a real 16 x 16 matrix with
- * mma.sync m16n8k16: the context's FP32 operator and the input are rounded to BF16, the
- * products summed in FP32 (relative error about 2^-8 of sum |Y| |x|). tensor_cores = 0 runs
- * the same product on CUDA cores in FP32 (the comparison path). Needs a context set up with
- * precision MG_FP32. Errors: INVALID_ARG (level, nrhs < 1, null pointers), UNSUPPORTED (FP64
- * context or N != 8). */
+ * Operands are rounded to BF16 and the products summed in FP32 (relative error about 2^-8 of
+ * sum |Y| |x|). tensor_cores = 0 runs the same product on CUDA cores in FP32 (the comparison
+ * path). Errors: INVALID_ARG (level, nrhs < 1, null pointers), UNSUPPORTED (d = 2 with an
+ * FP64 context or N != 8; d = 4 with N != 48). */
 int mg_coarse_apply_mrhs(mg_ctx *ctx, int level, int nrhs, const void *in, void *out, int tensor_cores);
 
 /* Launch shapes picked by the library's autotuner so far (the tensor-core coarse apply

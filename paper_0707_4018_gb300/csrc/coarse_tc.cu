@@ -149,4 +149,119 @@ void launch_coarse_apply_tc(const uint2 *Ypk, const Cx<float> *in, Cx<float> *ou
   tc_launch(shape, Ypk, in, out, g, nvec, b, a, c, shift, s);
 }
 
+// ===========================================================================
+// 4d coarse level (N = 48, 9 directions). The complex block Y = A + i B (48 x 48)
+// acts on x = xr + i xi as the real product [[A, -B], [B, A]] [xr; xi]; with 16 x 16
+// tiles (48 = 3 x 16) every tile of that real matrix is a tile of A, of B or of -B.
+// Only the A and B tiles are packed (BF16, A-fragment order, 512 B per tile); -B is
+// B with the sign bits flipped. A warp takes one site, 16 complex output rows (row
+// tile tm) and 8 vectors: for every direction and column tile tk it loads the A and
+// B fragments once and issues 4 mma.sync.m16n8k16 (A xr, -B xi into the real rows;
+// B xr, A xi into the imaginary rows): 108 per warp, FP32 accumulation.
+// ===========================================================================
+
+// Ypk4[((j * 9 + dir) * 2 + q) * 9 + tm * 3 + tk][lane] (uint4), q = 0: A = Re Y, 1: B = Im Y,
+// from the FP64 internal stencil Y[j][dir][col][row]
+__global__ void pack_coarse4_bf16_kernel(const Cx<double> *__restrict__ Y, uint4 *__restrict__ Ypk, long long nsites) {
+  const long long qi = blockIdx.x * (long long)blockDim.x + threadIdx.x;  // (j, dir, q, tile, lane)
+  if (qi >= nsites * 9 * 2 * 9 * 32) return;
+  const int lane = (int)(qi & 31);
+  long long r = qi >> 5;
+  const int tile = (int)(r % 9);
+  r /= 9;
+  const int q = (int)(r & 1);
+  const long long jd = r >> 1;  // j * 9 + dir
+  const int tm = tile / 3, tk = tile - tm * 3, g = lane >> 2, t = lane & 3;
+  const Cx<double> *Yb = Y + jd * 48 * 48;
+  auto el = [&](int row, int col) {  // element (row, col) of A or B
+    const Cx<double> y = Yb[(long long)(16 * tk + col) * 48 + 16 * tm + row];
+    return (float)(q == 0 ? y.re : y.im);
+  };
+  uint4 out;
+  out.x = pack_bf16x2(el(g, 2 * t), el(g, 2 * t + 1));
+  out.y = pack_bf16x2(el(g + 8, 2 * t), el(g + 8, 2 * t + 1));
+  out.z = pack_bf16x2(el(g, 2 * t + 8), el(g, 2 * t + 9));
+  out.w = pack_bf16x2(el(g + 8, 2 * t + 8), el(g + 8, 2 * t + 9));
+  Ypk[qi] = out;
+}
+
+// out_n = A_c in_n for nvec vectors (stride ldv = nsites * 48); one warp per (site, row tile,
+// group of 8 vectors)
+__global__ void __launch_bounds__(256) coarse4_apply_tc_kernel(const uint4 *__restrict__ Ypk,
+                                                               const Cx<float> *__restrict__ in,
+                                                               Cx<float> *__restrict__ out, int nb0, int nb1, int nb2,
+                                                               int nb3, long long ldv, int nvec) {
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const long long nsites = (long long)nb0 * nb1 * nb2 * nb3;
+  const int tiles = (nvec + 7) >> 3;
+  if (w >= nsites * 3 * tiles) return;  // whole warps
+  const long long j = w / (3 * tiles);
+  const int rem = (int)(w - j * 3 * tiles), tm = rem / tiles, n0 = (rem - tm * tiles) * 8;
+  const int nb[4] = {nb0, nb1, nb2, nb3};
+  int jc[4];
+  {
+    long long q = j;
+    for (int mu = 0; mu < 4; ++mu) {
+      jc[mu] = (int)(q % nb[mu]);
+      q /= nb[mu];
+    }
+  }
+  const int nv = n0 + g;  // this lane's vector in the B fragments
+  const bool bcol = nv < nvec;
+  float cre[4] = {0.f, 0.f, 0.f, 0.f}, cim[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int dir = 0; dir < 9; ++dir) {
+    long long src = j;
+    if (dir != 0) {
+      const int mu = (dir - 1) >> 1;
+      int cc[4] = {jc[0], jc[1], jc[2], jc[3]};
+      cc[mu] = ((dir - 1) & 1) == 0 ? (cc[mu] + 1) % nb[mu] : (cc[mu] + nb[mu] - 1) % nb[mu];
+      src = cc[0] + (long long)nb[0] * (cc[1] + (long long)nb[1] * (cc[2] + (long long)nb[2] * cc[3]));
+    }
+    const Cx<float> *xs = in + nv * ldv + src * 48;
+    const uint4 *Yd = Ypk + (j * 9 + dir) * 2 * 9 * 32;
+#pragma unroll
+    for (int tk = 0; tk < 3; ++tk) {
+      float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;  // x[16 tk + 2t .. +1], x[16 tk + 2t + 8 .. +9]
+      if (bcol) {
+        lo = *reinterpret_cast<const float4 *>(xs + 16 * tk + 2 * t);
+        hi = *reinterpret_cast<const float4 *>(xs + 16 * tk + 2 * t + 8);
+      }
+      const unsigned int r0 = pack_bf16x2(lo.x, lo.z), r1 = pack_bf16x2(hi.x, hi.z);  // xr fragment
+      const unsigned int i0 = pack_bf16x2(lo.y, lo.w), i1 = pack_bf16x2(hi.y, hi.w);  // xi fragment
+      const uint4 fa = Yd[(0 * 9 + tm * 3 + tk) * 32 + lane];
+      const uint4 fb = Yd[(1 * 9 + tm * 3 + tk) * 32 + lane];
+      const unsigned int s = 0x80008000u;
+      mma_bf16_16816(cre, fa.x, fa.y, fa.z, fa.w, r0, r1);                  // + A xr
+      mma_bf16_16816(cre, fb.x ^ s, fb.y ^ s, fb.z ^ s, fb.w ^ s, i0, i1);  // - B xi
+      mma_bf16_16816(cim, fb.x, fb.y, fb.z, fb.w, r0, r1);                  // + B xr
+      mma_bf16_16816(cim, fa.x, fa.y, fa.z, fa.w, i0, i1);                  // + A xi
+    }
+  }
+  // C fragment: rows g, g + 8 of the tile (complex rows 16 tm + g, + 8), vectors n0 + 2t, + 1
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int n = n0 + 2 * t + h;
+    if (n >= nvec) continue;
+    Cx<float> *o = out + n * ldv + j * 48 + 16 * tm;
+    o[g] = mk(cre[h], cim[h]);
+    o[g + 8] = mk(cre[2 + h], cim[2 + h]);
+  }
+}
+
+void launch_pack_coarse4_bf16(const Cx<double> *Y, uint4 *Ypk, long long nsites, cudaStream_t s) {
+  pack_coarse4_bf16_kernel<<<grid_for(nsites * 9 * 2 * 9 * 32, 256), 256, 0, s>>>(Y, Ypk, nsites);
+  MG_LAUNCHED();
+}
+
+void launch_coarse4_apply_tc(const uint4 *Ypk, const Cx<float> *in, Cx<float> *out, const int nb[4], int nvec,
+                             cudaStream_t s) {
+  if (nvec < 1) return;
+  const long long nsites = (long long)nb[0] * nb[1] * nb[2] * nb[3];
+  const long long warps = nsites * 3 * ((nvec + 7) / 8);
+  coarse4_apply_tc_kernel<<<grid_for(warps * 32, 256), 256, 0, s>>>(Ypk, in, out, nb[0], nb[1], nb[2], nb[3],
+                                                                    nsites * 48, nvec);
+  MG_LAUNCHED();
+}
+
 }  // namespace mg

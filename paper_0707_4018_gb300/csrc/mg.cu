@@ -1438,7 +1438,12 @@ int mg_coarse_apply_mrhs(mg_ctx *c, int level, int nrhs, const void *in, void *o
     need_level(c, level, false);
     need_ptr(in);
     need_ptr(out);
-    if (c->e4) fail(MG_ERR_UNSUPPORTED, "the tensor-core apply is built for d = 2 coarse levels");
+    if (c->e4) {
+      if (level != 1) fail(MG_ERR_INVALID_ARG, "the 4d hierarchy has one coarse level (level 1)");
+      if (nrhs < 1) fail(MG_ERR_INVALID_ARG, "nrhs must be >= 1");
+      engine4_coarse_apply_mrhs(*c->e4, nrhs, in, out, tensor_cores != 0);
+      return;
+    }
     if (level < 1) fail(MG_ERR_INVALID_ARG, "the tensor-core apply is for coarse levels (level >= 1)");
     if (nrhs < 1) fail(MG_ERR_INVALID_ARG, "nrhs must be >= 1");
     check_fresh(*c);

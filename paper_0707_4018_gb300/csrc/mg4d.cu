@@ -37,6 +37,11 @@ struct Engine4 {
   DevBuf<Cx<double>> U64, nullv, V64, Y64, Minv64, Yt64;  // Yt: A M, the preconditioned stencil
   DevBuf<Cx<float>> U32, V32, Yt32, Minv32;
   DevBuf<int> info;  // set by the block inversion when a self block is singular
+  // multi-vector coarse apply (made on first use after each Galerkin build): BF16 tensor-core
+  // fragments and an FP32 copy of Y
+  DevBuf<uint4> Ypk4;
+  DevBuf<Cx<float>> Y32;
+  bool mrhs_ready = false;
   // V-cycle work
   DevBuf<Cx<double>> vr64, vAr64, vx64, vb64;
   DevBuf<Cx<float>> vr32, vAr32, vx32, vb32;
@@ -327,6 +332,7 @@ void precondition(Engine4 &e, const Cx<double> *r, Cx<double> *z) {
 // block-Jacobi inverses of the coarse self blocks and the preconditioned stencil A M, then
 // the FP32 copies (MG_FP32)
 void prepare_coarse(Engine4 &e) {
+  e.mrhs_ready = false;
   launch_block_invert4(e.Y64.p, e.Minv64.p, e.cg, e.info.p, e.s);
   launch_precondition4(e.Y64.p, e.Minv64.p, e.Yt64.p, e.cg, e.s);
   if (!e.f32) return;
@@ -591,6 +597,27 @@ void engine4_get_prolongator(Engine4 &e, void *out) {
 
 void engine4_get_coarse_op(Engine4 &e, void *out) {
   launch_coarse4_to_canonical(e.Y64.p, static_cast<Cx<double> *>(out), e.cg, e.s);
+  MG_CUDA(cudaStreamSynchronize(e.s));
+}
+
+void engine4_coarse_apply_mrhs(Engine4 &e, int nrhs, const void *in, void *out, bool tensor_cores) {
+  if (e.N != 48) fail(MG_ERR_UNSUPPORTED, "the 4d multi-vector coarse apply is built for N = 48 (Nv = 24)");
+  if (!e.mrhs_ready) {
+    if (e.Ypk4.p == nullptr) {
+      e.Ypk4.alloc((size_t)e.cg.nsites * 9 * 2 * 9 * 32);
+      e.Y32.alloc(e.Y64.n);
+      pool_ready();
+    }
+    launch_pack_coarse4_bf16(e.Y64.p, e.Ypk4.p, e.cg.nsites, e.s);
+    launch_convert<float, double>(e.Y64.p, e.Y32.p, e.Y64.n, e.s);
+    e.mrhs_ready = true;
+  }
+  const Cx<float> *x = static_cast<const Cx<float> *>(in);
+  Cx<float> *y = static_cast<Cx<float> *>(out);
+  if (tensor_cores)
+    launch_coarse4_apply_tc(e.Ypk4.p, x, y, e.cg.nb, nrhs, e.s);
+  else
+    launch_coarse4_apply<float, float>(e.Y32.p, x, y, e.cg, nullptr, 1.0, 0.0, e.s, nrhs);
   MG_CUDA(cudaStreamSynchronize(e.s));
 }
 

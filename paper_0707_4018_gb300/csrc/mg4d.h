@@ -70,6 +70,12 @@ void launch_dot_norm_batch(const Cx<R> *a, const Cx<R> *b, long long n, int nvec
 template <typename R>
 void launch_mr_update_batch(const double *sc, double omega, Cx<R> *x, Cx<R> *r, const Cx<R> *Ar, long long n,
                             int nvec, cudaStream_t s);
+// tensor-core coarse apply (coarse_tc.cu), N = 48: BF16 A-fragments of Re Y and Im Y
+// (nsites x 9 x 2 x 9 x 32 uint4) from the FP64 stencil, then out_n = A_c in_n for nvec
+// complex64 vectors [n][site][48]
+void launch_pack_coarse4_bf16(const Cx<double> *Y, uint4 *Ypk, long long nsites, cudaStream_t s);
+void launch_coarse4_apply_tc(const uint4 *Ypk, const Cx<float> *in, Cx<float> *out, const int nb[4], int nvec,
+                             cudaStream_t s);
 // exports: Y in [j][dir][row][col]; P as N fine vectors [c][x][12]
 void launch_coarse4_to_canonical(const Cx<double> *Yi, Cx<double> *Yc, const Coarse4 &g, cudaStream_t s);
 void launch_prolongator4_to_canonical(const Cx<double> *V, Cx<double> *out, const Block4 &g, cudaStream_t s);
@@ -102,5 +108,8 @@ void engine4_get_null_vectors(Engine4 &e, void *out);
 void engine4_get_prolongator(Engine4 &e, void *out);
 void engine4_get_coarse_op(Engine4 &e, void *out);
 long long engine4_coarsest_solve(Engine4 &e, const void *b, void *x, float *ms);
+// out_n = A_c in_n for nrhs complex64 coarse vectors: tensor cores (BF16 operands, FP32 sums)
+// or, with tensor_cores = 0, CUDA cores in FP32 (the comparison path)
+void engine4_coarse_apply_mrhs(Engine4 &e, int nrhs, const void *in, void *out, bool tensor_cores);
 
 }  // namespace mg

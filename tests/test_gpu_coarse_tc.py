@@ -95,3 +95,39 @@ def test_autotuner_picks_a_tile_shape_and_keeps_results():
     key = "coarse_apply_tc/8x8/nvec11"
     assert key in rep and 0 <= rep[key] < 6, rep
     assert torch.equal(y1, y2)
+
+
+@pytest.mark.parametrize("nrhs", [1, 8, 12, 16])
+def test_tensor_core_apply_4d_matches_bf16_reference(nrhs):
+    import torch
+    import paper_0707_4018_gb300 as mg
+    dims = (8, 8, 8, 16)
+    U = inputs.su3_links(dims, seed=31)
+    p = mg.mg_default_params(levels=2, blocks=[(4, 4, 4, 4)], Nv=[24], precision=1, chiral_split=1, n_pass=1,
+                             nu_setup=4)
+    ctx = mg.Context.setup(to_dev(U), 0.1, dims, p)
+    n_sites, n_int = ctx.level_size(1)
+    lat = Lattice((2, 2, 2, 4))
+    assert lat.volume == n_sites and n_int == 48
+    Y = to_host(ctx.coarse_op(1))  # [j][dir][row][col]
+    x = np.stack([inputs.gaussian_complex(n_sites * 48, 80, 900 + k).reshape(n_sites, 48)
+                  for k in range(nrhs)]).astype(np.complex64)
+    out_tc = torch.empty((nrhs, n_sites, 48), dtype=torch.complex64, device="cuda")
+    out_cc = torch.empty_like(out_tc)
+    ctx.coarse_apply_mrhs(1, to_dev(x), out_tc, True)
+    ctx.coarse_apply_mrhs(1, to_dev(x), out_cc, False)
+    got, cc = to_host(out_tc).astype(np.complex128), to_host(out_cc).astype(np.complex128)
+    Yb = bf16c(Y.astype(np.complex64))
+    op_b, op_abs, op_exact = StencilOperator(Yb, lat), StencilOperator(np.abs(Yb), lat), StencilOperator(Y, lat)
+    worst_emul = worst_exact = worst_cc = 0.0
+    for k in range(nrhs):
+        xb = bf16c(x[k])
+        bound = op_abs.apply(np.abs(xb))
+        exact = op_exact.apply(x[k].astype(np.complex128))
+        worst_emul = max(worst_emul, float(np.max(np.abs(got[k] - op_b.apply(xb)) / bound)))
+        worst_exact = max(worst_exact, float(np.max(np.abs(got[k] - exact) / bound)))
+        worst_cc = max(worst_cc, float(np.max(np.abs(cc[k] - exact) / bound)))
+    assert worst_emul <= 1e-5, worst_emul       # only the FP32 summation of 432 products differs
+    assert worst_exact <= 1e-2, worst_exact     # the BF16 rounding of both operands
+    assert worst_cc <= 1e-5, worst_cc           # the FP32 CUDA-core path
+    ctx.close()
