@@ -157,7 +157,11 @@ int mg_solve(mg_ctx *ctx, const void *chi, void *psi, double tol, mg_stats *st);
  * A vector stops when its tracked residual meets tol and is confirmed by the
  * true residual at the next restart. Returns NOT_CONVERGED if any vector
  * missed tol within max_iter (outer iterations of the batch), INVALID_ARG for
- * nrhs outside 1..max_rhs or a non-finite mass. */
+ * nrhs outside 1..max_rhs or a non-finite mass.
+ * d = 4 (the 4d SU(3) hierarchy): chi, psi complex128 [v][x][s][c]; every vector
+ * solves at the context mass (mass NULL, else UNSUPPORTED); the batched
+ * V-cycle's coarse solve is a lockstep GCR whose operator applications run on
+ * tensor cores for all vectors at once (N = 48; BF16 operands, FP32 sums). */
 int mg_solve_batch(mg_ctx *ctx, int nrhs, const void *chi, void *psi, const double *mass, double tol,
                    mg_stats *st);
 

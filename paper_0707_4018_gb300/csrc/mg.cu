@@ -1202,7 +1202,24 @@ int mg_solve_batch(mg_ctx *c, int nrhs, const void *chi, void *psi, const double
     need_ctx(c);
     need_ptr(chi);
     need_ptr(psi);
-    if (c->e4) fail(MG_ERR_UNSUPPORTED, "batched solves are built for d = 2");
+    if (c->e4) {
+      if (mass != nullptr)
+        for (int v = 0; v < nrhs; ++v)
+          if (mass[v] != c->m) fail(MG_ERR_UNSUPPORTED, "4d batched solves take the context mass (mass = NULL)");
+      const std::vector<Solve4> o = engine4_solve_batch(*c->e4, nrhs, chi, psi, tol);
+      for (int v = 0; v < nrhs; ++v) {
+        if (!o[v].converged) status = MG_ERR_NOT_CONVERGED;
+        if (!st) continue;
+        st[v].iters = o[v].iters;
+        st[v].converged = o[v].converged ? 1 : 0;
+        st[v].true_rel_residual = o[v].rel;
+        for (int l = 0; l < MG_MAX_LEVELS; ++l) st[v].level_apps[l] = o[v].apps[l];
+        st[v].coarsest_iters = o[v].coarsest_iters;
+        st[v].ms = o[v].ms;
+        st[v].graphs = 0;
+      }
+      return;
+    }
     if (nrhs < 1 || nrhs > c->p.max_rhs) fail(MG_ERR_INVALID_ARG, "nrhs must be in [1, max_rhs]");
     check_fresh(*c);
     if (c->bZ.p == nullptr) alloc_batch(*c);

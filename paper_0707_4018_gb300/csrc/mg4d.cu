@@ -62,9 +62,26 @@ struct Engine4 {
   double *host = nullptr;  // pinned: [0, 256) outer, [256, 512) coarse
   long long apps[MG_MAX_LEVELS] = {0, 0, 0, 0};
   long long coarsest_iters = 0;
+  // batched solves (made on the first batched call, for max_rhs vectors): outer Krylov bases
+  // [k][v][nf] and residuals, V-cycle vectors [v][nf], coarse GCR vectors [v][nc] and bases
+  // [k][v][nc], FP32 operands of the tensor-core coarse apply, reductions and coefficients
+  struct Batch {
+    int cap = 0;
+    DevBuf<Cx<double>> Z, W, r, rin, z64;
+    DevBuf<Cx<float>> r32, Ar32, x32, b32;
+    DevBuf<Cx<double>> r64, Ar64, x64, b64;
+    DevBuf<Cx<double>> cb, cx, cr, crin, cZ, cW;
+    DevBuf<Cx<float>> cin32, cout32;
+    DevBuf<double> dots, coef, cdots, ccoef, part;
+    DevBuf<unsigned int> tickets;
+    ReduceWs ws{};
+    double *host = nullptr, *chost = nullptr;  // pinned: dots, then coefficients (outer / coarse)
+  } bt;
   ~Engine4() {
     if (s) cudaStreamSynchronize(s);
     if (host) cudaFreeHost(host);
+    if (bt.host) cudaFreeHost(bt.host);
+    if (bt.chost) cudaFreeHost(bt.chost);
   }
 };
 
@@ -243,6 +260,118 @@ long long coarse_solve(Engine4 &e) {
   return iters;
 }
 
+// Flexible GCR over nb systems in lockstep (FP64, vectors [v][n], bases [k][v][n]): one
+// batched preconditioner, one batched operator apply and one batched reduction per
+// iteration; the host forms every vector's coefficients from one fetch, with a second
+// projection where |w - W beta|^2 shows cancellation. A vector whose tracked residual meets
+// tol (or whose basis breaks down) rests until the next restart, where the true residuals
+// decide which vectors go on; a resting vector's preconditioner input is zero.
+struct GcrB {
+  int iters = 0;
+  bool converged = false;
+  double rel = 0.0;
+};
+
+template <typename ApplyF, typename PrecF>
+void fgcr_batch(Engine4 &e, int nb, ApplyF &&apply, PrecF &&prec, const Cx<double> *b, Cx<double> *x, long long n,
+                double tol, int restart, int max_iter, Cx<double> *Z, Cx<double> *W, Cx<double> *r,
+                Cx<double> *rin, double *dots, double *coef, double *h, const ReduceWs &ws,
+                std::vector<GcrB> &out) {
+  double *hcoef = h + (size_t)nb * 2 * (restart + 3);
+  out.assign(nb, GcrB{});
+  auto fetch = [&](int count) {
+    MG_CUDA(cudaMemcpyAsync(h, dots, count * sizeof(double), cudaMemcpyDeviceToHost, e.s));
+    MG_CUDA(cudaStreamSynchronize(e.s));
+    for (int i = 0; i < count; ++i)
+      if (std::isnan(h[i])) fail(MG_ERR_NAN, "GCR (batched): NaN in a reduction");
+  };
+  launch_zero<double>(x, n * nb, e.s);
+  launch_copy<double>(b, r, n * nb, e.s);
+  launch_norm2_batch(b, n, nb, dots, ws, e.s);
+  fetch(nb);
+  std::vector<double> bn2(h, h + nb), rn2(bn2), nw0(nb), nw2(nb), wr(nb), wi(nb), rr(nb);
+  const unsigned int all = nb == 32 ? 0xffffffffu : (1u << nb) - 1u;
+  unsigned int done = 0u;
+  for (int v = 0; v < nb; ++v)
+    if (!(bn2[v] > 0.0)) {
+      done |= 1u << v;
+      out[v].converged = true;
+    }
+  int iters = 0;
+  while (done != all && iters < max_iter) {
+    unsigned int act = all & ~done;
+    int k = 0;
+    for (; k < restart && iters < max_iter && act != 0u; ++k) {
+      Cx<double> *Zk = Z + (long long)k * nb * n, *Wk = W + (long long)k * nb * n;
+      launch_copy_masked(r, rin, n, nb, act, e.s);
+      prec(rin, Zk);
+      apply(Zk, Wk, nullptr);
+      launch_gcr_dots_batch(W, r, k, nb, n, dots, ws, e.s);
+      const int stride = 2 * (k + 3);
+      fetch(nb * stride);
+      unsigned int cancel = 0u;
+      for (int v = 0; v < nb; ++v) {
+        const double *hv = h + v * stride;
+        rr[v] = hv[2 * k + 4];
+        nw0[v] = nw2[v] = hv[2 * k];
+        for (int j = 0; j < k; ++j) nw2[v] -= hv[2 * j] * hv[2 * j] + hv[2 * j + 1] * hv[2 * j + 1];
+        wr[v] = hv[2 * k + 2];
+        wi[v] = hv[2 * k + 3];
+        if (((act >> v) & 1u) && k > 0 && !(nw2[v] > 0.5 * nw0[v])) cancel |= 1u << v;
+      }
+      if (cancel != 0u) {  // project those vectors once, then take fresh coefficients for them
+        for (int v = 0; v < nb; ++v) {
+          hcoef[4 * v] = 1.0;
+          hcoef[4 * v + 1] = hcoef[4 * v + 2] = 0.0;
+          hcoef[4 * v + 3] = ((cancel >> v) & 1u) ? 2.0 : 0.0;
+        }
+        MG_CUDA(cudaMemcpyAsync(coef, hcoef, 4 * nb * sizeof(double), cudaMemcpyHostToDevice, e.s));
+        launch_gcr_update_batch(W, Z, k, nb, dots, coef, x, r, n, e.s);
+        launch_gcr_dots_batch(W, r, k, nb, n, dots, ws, e.s);
+        fetch(nb * stride);
+        for (int v = 0; v < nb; ++v) {
+          if (!((cancel >> v) & 1u)) continue;
+          const double *hv = h + v * stride;
+          nw0[v] = nw2[v] = hv[2 * k];
+          for (int j = 0; j < k; ++j) nw2[v] -= hv[2 * j] * hv[2 * j] + hv[2 * j + 1] * hv[2 * j + 1];
+        }
+      }
+      for (int v = 0; v < nb; ++v) {
+        hcoef[4 * v + 3] = 0.0;
+        if (!((act >> v) & 1u)) continue;
+        if (!(nw2[v] > 1e-28 * nw0[v])) {
+          act &= ~(1u << v);  // breakdown: this vector waits for the restart
+          continue;
+        }
+        const double inv = 1.0 / std::sqrt(nw2[v]);
+        const double are = wr[v] * inv, aim = wi[v] * inv;
+        hcoef[4 * v] = inv;
+        hcoef[4 * v + 1] = are;
+        hcoef[4 * v + 2] = aim;
+        hcoef[4 * v + 3] = 1.0;
+        rn2[v] = std::max(rr[v] - (are * are + aim * aim), 0.0);
+        ++out[v].iters;
+        if (std::sqrt(rn2[v] / bn2[v]) <= tol) act &= ~(1u << v);
+      }
+      MG_CUDA(cudaMemcpyAsync(coef, hcoef, 4 * nb * sizeof(double), cudaMemcpyHostToDevice, e.s));
+      launch_gcr_update_batch(W, Z, k, nb, dots, coef, x, r, n, e.s);
+      ++iters;
+    }
+    apply(x, r, b);  // true residuals r = b - A x
+    launch_norm2_batch(r, n, nb, dots, ws, e.s);
+    fetch(nb);
+    for (int v = 0; v < nb; ++v) {
+      if ((done >> v) & 1u) continue;
+      out[v].rel = std::sqrt(h[v] / bn2[v]);
+      if (out[v].rel <= tol) {
+        done |= 1u << v;
+        out[v].converged = true;
+      }
+    }
+    if (k == 0) break;
+  }
+}
+
 constexpr int kMrBlocks = 152 * 4;  // grid cap of the batched MR reductions
 
 // x (+)= nu MR iterations on D e = r for nvec vectors (stride nf; r updated to the
@@ -396,6 +525,7 @@ void validate4(const mg_geom *g, const mg_params *p) {
   if (p->coarsest_restart < 1 || p->coarsest_restart > 64)
     fail(MG_ERR_INVALID_ARG, "coarsest_restart must be in [1, 64] for d = 4");
   if (p->max_iter < 1 || p->coarsest_max_iter < 1) fail(MG_ERR_INVALID_ARG, "iteration limits must be >= 1");
+  if (p->max_rhs < 1 || p->max_rhs > 32) fail(MG_ERR_INVALID_ARG, "max_rhs must be in [1, 32]");
   int bvol = 1;
   for (int mu = 0; mu < 4; ++mu) {
     const int B = p->block[0][mu];
@@ -474,9 +604,10 @@ Engine4 *engine4_create(const mg_geom *g, const void *U, double m, const mg_para
   e->ws.tickets = 160;
   e->tickets.alloc((size_t)e->ws.tickets);
   e->scal.alloc(kScalCount);
-  e->bpart.alloc((size_t)e->bg.Nv * kMrBlocks * 3 + 16);
-  e->bsc.alloc((size_t)e->bg.Nv * 3);
-  e->btickets.alloc((size_t)e->bg.Nv);
+  const int nbat = std::max(e->bg.Nv, std::max(1, p->max_rhs));  // vectors of a batched MR
+  e->bpart.alloc((size_t)nbat * kMrBlocks * 3 + 16);
+  e->bsc.alloc((size_t)nbat * 3);
+  e->btickets.alloc((size_t)nbat);
   if (e->f32) {
     e->sx32.alloc((size_t)e->bg.Nv * e->nf);
     e->sr32.alloc((size_t)e->bg.Nv * e->nf);
@@ -486,7 +617,7 @@ Engine4 *engine4_create(const mg_geom *g, const void *U, double m, const mg_para
     e->sAr64.alloc((size_t)e->bg.Nv * e->nf);
   }
   pool_ready();
-  MG_CUDA(cudaMemsetAsync(e->btickets.p, 0, e->bg.Nv * sizeof(unsigned int), s));
+  MG_CUDA(cudaMemsetAsync(e->btickets.p, 0, e->btickets.n * sizeof(unsigned int), s));
   MG_CUDA(cudaMemsetAsync(e->tickets.p, 0, e->ws.tickets * sizeof(unsigned int), s));
   MG_CUDA(cudaMemsetAsync(e->scal.p, 0, kScalCount * sizeof(double), s));
   MG_CUDA(cudaMemsetAsync(e->info.p, 0, sizeof(int), s));
@@ -598,6 +729,182 @@ void engine4_get_prolongator(Engine4 &e, void *out) {
 void engine4_get_coarse_op(Engine4 &e, void *out) {
   launch_coarse4_to_canonical(e.Y64.p, static_cast<Cx<double> *>(out), e.cg, e.s);
   MG_CUDA(cudaStreamSynchronize(e.s));
+}
+
+namespace {
+
+// buffers of batched solves, for max_rhs vectors
+void alloc_batch(Engine4 &e) {
+  auto &b = e.bt;
+  const int nb = std::max(1, e.p.max_rhs), ro = e.p.gcr_restart, rc = e.p.coarsest_restart;
+  b.cap = nb;
+  b.Z.alloc((size_t)ro * nb * e.nf);
+  b.W.alloc((size_t)ro * nb * e.nf);
+  b.r.alloc((size_t)nb * e.nf);
+  b.rin.alloc((size_t)nb * e.nf);
+  b.z64.alloc((size_t)nb * e.nf);
+  if (e.f32) {
+    b.r32.alloc((size_t)nb * e.nf);
+    b.Ar32.alloc((size_t)nb * e.nf);
+    b.x32.alloc((size_t)nb * e.nf);
+    b.b32.alloc((size_t)nb * e.nf);
+  } else {
+    b.r64.alloc((size_t)nb * e.nf);
+    b.Ar64.alloc((size_t)nb * e.nf);
+    b.x64.alloc((size_t)nb * e.nf);
+    b.b64.alloc((size_t)nb * e.nf);
+  }
+  b.cb.alloc((size_t)nb * e.nc);
+  b.cx.alloc((size_t)nb * e.nc);
+  b.cr.alloc((size_t)nb * e.nc);
+  b.crin.alloc((size_t)nb * e.nc);
+  b.cZ.alloc((size_t)rc * nb * e.nc);
+  b.cW.alloc((size_t)rc * nb * e.nc);
+  b.cin32.alloc((size_t)nb * e.nc);
+  b.cout32.alloc((size_t)nb * e.nc);
+  const int rows = std::max(ro, rc) + 3;
+  b.dots.alloc((size_t)nb * 2 * (ro + 3));
+  b.coef.alloc((size_t)nb * 4);
+  b.cdots.alloc((size_t)nb * 2 * (rc + 3));
+  b.ccoef.alloc((size_t)nb * 4);
+  b.ws.max_blocks = 64;
+  b.ws.tickets = (long long)rows * nb;
+  b.ws.capacity = 2LL * rows * nb * 64;
+  b.part.alloc((size_t)b.ws.capacity + 16);
+  b.tickets.alloc((size_t)b.ws.tickets);
+  MG_CUDA(cudaMallocHost(&b.host, ((size_t)nb * 2 * (ro + 3) + nb * 4) * sizeof(double)));
+  MG_CUDA(cudaMallocHost(&b.chost, ((size_t)nb * 2 * (rc + 3) + nb * 4) * sizeof(double)));
+  pool_ready();
+  MG_CUDA(cudaMemsetAsync(b.tickets.p, 0, b.ws.tickets * sizeof(unsigned int), e.s));
+  b.ws.partials = b.part.p;
+  b.ws.ticket = b.tickets.p;
+}
+
+// batched coarse solve of nb vectors: cx_v = A_c^{-1} cb_v by lockstep GCR to coarsest_tol,
+// right-preconditioned by block Jacobi; the operator applied to all vectors at once on
+// tensor cores (N = 48; BF16 operands, FP32 sums) or, otherwise, in FP64
+void coarse_solve_batch(Engine4 &e, int nb) {
+  auto &b = e.bt;
+  const bool tc = e.N == 48;
+  if (tc && !e.mrhs_ready) {
+    if (e.Ypk4.p == nullptr) {
+      e.Ypk4.alloc((size_t)e.cg.nsites * 9 * 2 * 9 * 32);
+      e.Y32.alloc(e.Y64.n);
+      pool_ready();
+    }
+    launch_pack_coarse4_bf16(e.Y64.p, e.Ypk4.p, e.cg.nsites, e.s);
+    launch_convert<float, double>(e.Y64.p, e.Y32.p, e.Y64.n, e.s);
+    e.mrhs_ready = true;
+  }
+  auto apply = [&](const Cx<double> *in, Cx<double> *out, const Cx<double> *rhs) {
+    if (tc) {
+      launch_convert<float, double>(in, b.cin32.p, (long long)nb * e.nc, e.s);
+      launch_coarse4_apply_tc(e.Ypk4.p, b.cin32.p, b.cout32.p, e.cg.nb, nb, e.s);
+      launch_convert<double, float>(b.cout32.p, out, (long long)nb * e.nc, e.s);
+      if (rhs != nullptr) launch_xmy<double>(rhs, out, (long long)nb * e.nc, e.s);  // out = rhs - A in
+    } else {
+      launch_coarse4_apply<double, double>(e.Y64.p, in, out, e.cg, rhs, rhs ? -1.0 : 1.0, rhs ? 1.0 : 0.0, e.s,
+                                           nb);
+    }
+    e.apps[1] += nb;
+  };
+  auto prec = [&](const Cx<double> *r, Cx<double> *z) {
+    if (e.f32)
+      launch_block_apply4<float>(e.Minv32.p, r, z, e.cg, e.s, nb);
+    else
+      launch_block_apply4<double>(e.Minv64.p, r, z, e.cg, e.s, nb);
+  };
+  std::vector<GcrB> out;
+  fgcr_batch(e, nb, apply, prec, b.cb.p, b.cx.p, e.nc, e.p.coarsest_tol, e.p.coarsest_restart,
+             e.p.coarsest_max_iter, b.cZ.p, b.cW.p, b.cr.p, b.crin.p, b.cdots.p, b.ccoef.p, b.chost, b.ws, out);
+  int mx = 0;
+  for (const auto &o : out) mx = std::max(mx, o.iters);
+  e.coarsest_iters += mx;
+}
+
+// batched V-cycle x_v = V b_v (FP64 in and out, the cycle in R)
+template <typename R>
+struct BWork;
+template <>
+struct BWork<double> {
+  static Cx<double> *r(Engine4 &e) { return e.bt.r64.p; }
+  static Cx<double> *Ar(Engine4 &e) { return e.bt.Ar64.p; }
+  static Cx<double> *x(Engine4 &e) { return e.bt.x64.p; }
+  static Cx<double> *b(Engine4 &e) { return e.bt.b64.p; }
+};
+template <>
+struct BWork<float> {
+  static Cx<float> *r(Engine4 &e) { return e.bt.r32.p; }
+  static Cx<float> *Ar(Engine4 &e) { return e.bt.Ar32.p; }
+  static Cx<float> *x(Engine4 &e) { return e.bt.x32.p; }
+  static Cx<float> *b(Engine4 &e) { return e.bt.b32.p; }
+};
+
+template <typename R>
+void vcycle_batch(Engine4 &e, int nb, const Cx<double> *b64, Cx<double> *x64) {
+  Cx<R> *r = BWork<R>::r(e), *Ar = BWork<R>::Ar(e), *x = BWork<R>::x(e), *b = BWork<R>::b(e);
+  const long long nall = (long long)nb * e.nf;
+  from64<R>(e, b64, b, nall);
+  launch_zero<R>(x, nall, e.s);
+  launch_copy<R>(b, r, nall, e.s);
+  mr_fine<R>(e, x, r, Ar, e.p.nu_pre, nb);
+  launch_dslash4<R>(U_of<R>(e), x, r, e.fg, diag4(e), b, -1.0, 1.0, e.s, nb);
+  e.apps[0] += nb;
+  // restriction in R, coarse solve in FP64
+  Cx<R> *rc = sizeof(R) == 8 ? reinterpret_cast<Cx<R> *>(e.bt.cb.p) : reinterpret_cast<Cx<R> *>(e.bt.cin32.p);
+  launch_restrict4<R>(V_of<R>(e), r, rc, e.bg, e.s, nb);
+  if (sizeof(R) == 4) to64<R>(e, rc, e.bt.cb.p, (long long)nb * e.nc);
+  coarse_solve_batch(e, nb);
+  Cx<R> *ec = sizeof(R) == 8 ? reinterpret_cast<Cx<R> *>(e.bt.cx.p) : reinterpret_cast<Cx<R> *>(e.bt.cin32.p);
+  if (sizeof(R) == 4) from64<R>(e, e.bt.cx.p, ec, (long long)nb * e.nc);
+  launch_prolong4<R>(V_of<R>(e), ec, x, e.bg, e.s, nb);
+  launch_dslash4<R>(U_of<R>(e), x, r, e.fg, diag4(e), b, -1.0, 1.0, e.s, nb);
+  e.apps[0] += nb;
+  mr_fine<R>(e, x, r, Ar, e.p.nu_post, nb);
+  to64<R>(e, x, x64, nall);
+}
+
+}  // namespace
+
+std::vector<Solve4> engine4_solve_batch(Engine4 &e, int nrhs, const void *chi, void *psi, double tol) {
+  if (e.bt.cap == 0) alloc_batch(e);
+  if (nrhs < 1 || nrhs > e.bt.cap) fail(MG_ERR_INVALID_ARG, "nrhs must be in [1, max_rhs]");
+  for (long long &a : e.apps) a = 0;
+  e.coarsest_iters = 0;
+  cudaEvent_t e0, e1;
+  MG_CUDA(cudaEventCreate(&e0));
+  MG_CUDA(cudaEventCreate(&e1));
+  MG_CUDA(cudaEventRecord(e0, e.s));
+  auto apply = [&](const Cx<double> *in, Cx<double> *out, const Cx<double> *rhs) {
+    launch_dslash4<double>(e.U64.p, in, out, e.fg, diag4(e), rhs, rhs ? -1.0 : 1.0, rhs ? 1.0 : 0.0, e.s, nrhs);
+    e.apps[0] += nrhs;
+  };
+  auto prec = [&](const Cx<double> *r, Cx<double> *z) {
+    if (e.f32)
+      vcycle_batch<float>(e, nrhs, r, z);
+    else
+      vcycle_batch<double>(e, nrhs, r, z);
+  };
+  std::vector<GcrB> g;
+  fgcr_batch(e, nrhs, apply, prec, static_cast<const Cx<double> *>(chi), static_cast<Cx<double> *>(psi), e.nf, tol,
+             e.p.gcr_restart, e.p.max_iter, e.bt.Z.p, e.bt.W.p, e.bt.r.p, e.bt.rin.p, e.bt.dots.p, e.bt.coef.p,
+             e.bt.host, e.bt.ws, g);
+  MG_CUDA(cudaEventRecord(e1, e.s));
+  MG_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  MG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::vector<Solve4> out(nrhs);
+  for (int v = 0; v < nrhs; ++v) {
+    out[v].iters = g[v].iters;
+    out[v].converged = g[v].converged;
+    out[v].rel = g[v].rel;
+    for (int l = 0; l < MG_MAX_LEVELS; ++l) out[v].apps[l] = e.apps[l];
+    out[v].coarsest_iters = e.coarsest_iters;
+    out[v].ms = ms;
+  }
+  return out;
 }
 
 void engine4_coarse_apply_mrhs(Engine4 &e, int nrhs, const void *in, void *out, bool tensor_cores) {

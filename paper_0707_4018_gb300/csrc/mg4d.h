@@ -4,6 +4,8 @@
 // (mg.cu) and the 4d engine (mg4d.cu, mg4d_kernels.cu).
 #pragma once
 
+#include <vector>
+
 #include "kernels.h"
 
 namespace mg {
@@ -50,9 +52,10 @@ void launch_coarse4_apply(const Cx<RY> *Y, const Cx<RV> *in, Cx<RV> *out, const 
 // Minv[j] = inverse of the self block Y[j][0] (FP64 Gauss-Jordan, partial pivoting); *info
 // set to 1 if a block is singular
 void launch_block_invert4(const Cx<double> *Y, Cx<double> *Minv, const Coarse4 &g, int *info, cudaStream_t s);
-// z_j = Minv_j r_j (vectors FP64, Minv in R)
+// z_j = Minv_j r_j for nvec vectors (FP64, stride nsites N; Minv in R)
 template <typename R>
-void launch_block_apply4(const Cx<R> *Minv, const Cx<double> *r, Cx<double> *z, const Coarse4 &g, cudaStream_t s);
+void launch_block_apply4(const Cx<R> *Minv, const Cx<double> *r, Cx<double> *z, const Coarse4 &g, cudaStream_t s,
+                         int nvec = 1);
 // GCR step with device-side coefficients formed from the reduction of launch_gcr_dots:
 // projection, normalisation and the x, r update; state[0] = |r|^2 - |alpha|^2
 void launch_gcr_update_dev(const Cx<double> *W, Cx<double> *Wk, const Cx<double> *Z, Cx<double> *Zk, int k,
@@ -108,6 +111,10 @@ void engine4_get_null_vectors(Engine4 &e, void *out);
 void engine4_get_prolongator(Engine4 &e, void *out);
 void engine4_get_coarse_op(Engine4 &e, void *out);
 long long engine4_coarsest_solve(Engine4 &e, const void *b, void *x, float *ms);
+// nrhs systems D psi_v = chi_v (at the context mass) in lockstep through one hierarchy
+// (FP64 flexible GCR over the batch, batched V-cycles whose coarse solve applies the
+// coarse operator to all vectors on tensor cores); nrhs <= max_rhs
+std::vector<Solve4> engine4_solve_batch(Engine4 &e, int nrhs, const void *chi, void *psi, double tol);
 // out_n = A_c in_n for nrhs complex64 coarse vectors: tensor cores (BF16 operands, FP32 sums)
 // or, with tensor_cores = 0, CUDA cores in FP32 (the comparison path)
 void engine4_coarse_apply_mrhs(Engine4 &e, int nrhs, const void *in, void *out, bool tensor_cores);

@@ -445,11 +445,14 @@ __global__ void __launch_bounds__(256) block_invert4_kernel(const Cx<double> *__
   }
 }
 
-// z_j = Minv_j r_j (one CTA per site, one thread per row)
+// z_j = Minv_j r_j (one CTA per site and vector blockIdx.y, one thread per row; vectors at
+// stride ld)
 template <typename R>
 __global__ void block_apply4_kernel(const Cx<R> *__restrict__ Minv, const Cx<double> *__restrict__ r,
-                                    Cx<double> *__restrict__ z, int N) {
+                                    Cx<double> *__restrict__ z, int N, long long ld) {
   __shared__ Cx<R> rs[64];
+  r += blockIdx.y * ld;
+  z += blockIdx.y * ld;
   const int j = blockIdx.x, row = threadIdx.x;
   if (row < N) rs[row] = cvt<R, double>(r[(long long)j * N + row]);
   __syncthreads();
@@ -684,8 +687,9 @@ void launch_block_invert4(const Cx<double> *Y, Cx<double> *Minv, const Coarse4 &
 }
 
 template <typename R>
-void launch_block_apply4(const Cx<R> *Minv, const Cx<double> *r, Cx<double> *z, const Coarse4 &g, cudaStream_t s) {
-  block_apply4_kernel<R><<<(unsigned int)g.nsites, 64, 0, s>>>(Minv, r, z, g.N);
+void launch_block_apply4(const Cx<R> *Minv, const Cx<double> *r, Cx<double> *z, const Coarse4 &g, cudaStream_t s,
+                         int nvec) {
+  block_apply4_kernel<R><<<dim3((unsigned int)g.nsites, nvec), 64, 0, s>>>(Minv, r, z, g.N, g.nsites * g.N);
   MG_LAUNCHED();
 }
 
@@ -759,8 +763,8 @@ template void launch_mr_update_batch<float>(const double *, double, Cx<float> *,
 template void launch_mr_update_batch<double>(const double *, double, Cx<double> *, Cx<double> *, const Cx<double> *,
                                              long long, int, cudaStream_t);
 template void launch_block_apply4<double>(const Cx<double> *, const Cx<double> *, Cx<double> *, const Coarse4 &,
-                                          cudaStream_t);
+                                          cudaStream_t, int);
 template void launch_block_apply4<float>(const Cx<float> *, const Cx<double> *, Cx<double> *, const Coarse4 &,
-                                         cudaStream_t);
+                                         cudaStream_t, int);
 
 }  // namespace mg
