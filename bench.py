@@ -321,7 +321,7 @@ def su3_params(precision: int):
                                 coarsest_max_iter=128, max_iter=300, max_rhs=SU3_RHS)
 
 
-def su3_workload(precisions=(1, 0), nrhs: int = SU3_RHS, batched: bool = True):
+def su3_workload(precisions=(1, 0), nrhs: int = SU3_RHS, batched: bool = True, singles: bool = True):
     """Solves/s including setup on the 4d SU(3) workload: APE-smeared links on 16^3 x 32, m = m_c + 0.005
     (m_c from the oracle's table when present, else m = 0), 12 Gaussian sources to 1e-10, one setup."""
     import torch
@@ -339,6 +339,8 @@ def su3_workload(precisions=(1, 0), nrhs: int = SU3_RHS, batched: bool = True):
                        "2-level MG 4^4 blocks, Nv=24 chirality-split (48x48 coarse blocks), 12 Gaussian sources, tol 1e-10",
            "m": m, "m_from": "m_c + 0.005 (oracle table)" if m_ok else "0.0 (no m_c in the table)"}
     for prec in precisions:
+        if not singles:
+            break
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx = mg.Context.setup(Ud, m, SU3_DIMS, su3_params(prec))
@@ -353,9 +355,9 @@ def su3_workload(precisions=(1, 0), nrhs: int = SU3_RHS, batched: bool = True):
             "setup_s": t1 - t0, "ms_per_solve": (t2 - t1) / nrhs * 1e3, "iters": [st["iters"] for st in sts],
             "coarse_iters": [st["coarsest_iters"] for st in sts], "converged": all(st["converged"] for st in sts),
             "worst_true_rel_residual": max(st["true_rel_residual"] for st in sts)}
-        if prec != 1 or batched is False:
-            continue
+    if batched and 1 in precisions:
         # the same sources as one batch: lockstep solve, coarse operator on tensor cores
+        prec = 1
         chi_b = torch.stack(chis)
         psi_b = torch.empty_like(chi_b)
         torch.cuda.synchronize()
@@ -544,6 +546,10 @@ def run_only(case: str):
     if case == "su3":
         print(json.dumps({"case": case, **su3_workload()}))
         return
+    if case == "su3-batch-prof":  # mixed precision, setup and one batch of 12 sources (launch-list profiling)
+        r = su3_workload((1,), SU3_RHS, batched=True, singles=False)
+        print(json.dumps({"case": case, **r}))
+        return
     if case == "su3-prof":  # mixed precision, setup and 2 solves (launch-list profiling)
         print(json.dumps({"case": case, **su3_workload((1,), 2, batched=False)}))
         return
@@ -669,7 +675,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--only", default=None, choices=["dslash-f32", "dslash-f64", "dslash4-f32", "dslash4-f64", "solve", "vcycle",
-                                                      "transfer", "coarse-tc", "coarse-tc4", "su3", "su3-prof"],
+                                                      "transfer", "coarse-tc", "coarse-tc4", "su3", "su3-prof",
+                                                      "su3-batch-prof"],
                     help="profiling cases: the Dslash timing loop alone (2d, or 4d SU(3)), one beta's setup + 3 solves, "
                          "25 mixed-precision V-cycles after one beta's setup, or 5 V-cycles on a 1024^2 "
                          "hierarchy (fine level larger than L2, for the restriction and prolongation), or the "

@@ -458,6 +458,17 @@ void precondition(Engine4 &e, const Cx<double> *r, Cx<double> *z) {
     vcycle<double>(e, r, z);
 }
 
+// MG_ERR_NAN if the last block inversion met a singular (or NaN) coarse self block
+void check_info(Engine4 &e) {
+  int info = 0;
+  MG_CUDA(cudaMemcpyAsync(&info, e.info.p, sizeof(int), cudaMemcpyDeviceToHost, e.s));
+  MG_CUDA(cudaStreamSynchronize(e.s));
+  if (info != 0) {
+    MG_CUDA(cudaMemsetAsync(e.info.p, 0, sizeof(int), e.s));
+    fail(MG_ERR_NAN, "coarse level: a self block is singular or not finite");
+  }
+}
+
 // block-Jacobi inverses of the coarse self blocks and the preconditioned stencil A M, then
 // the FP32 copies (MG_FP32)
 void prepare_coarse(Engine4 &e) {
@@ -628,7 +639,7 @@ Engine4 *engine4_create(const mg_geom *g, const void *U, double m, const mg_para
   MG_CUDA(cudaMemcpyAsync(e->U64.p, U, e->U64.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, s));
   if (e->f32) launch_convert<float, double>(e->U64.p, e->U32.p, e->U64.n, s);
   setup(*e);
-  MG_CUDA(cudaStreamSynchronize(s));
+  check_info(*e);
   return e.release();
 }
 
@@ -668,7 +679,7 @@ void engine4_update_mass(Engine4 &e, double m) {
   e.m = m;
   launch_galerkin4(e.U64.p, diag4(e), e.V64.p, e.Y64.p, e.bg, e.s);
   prepare_coarse(e);
-  MG_CUDA(cudaStreamSynchronize(e.s));
+  check_info(e);
 }
 
 void engine4_level_size(const Engine4 &e, int level, long long *n_sites, int *n_int) {

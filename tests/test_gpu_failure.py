@@ -55,3 +55,26 @@ def test_nan_links_are_reported_by_setup():
     with pytest.raises(mg.MGError) as e:
         mg.Context.setup(to_dev(U), 0.2, (L, L), mg.mg_default_params(n_pass=2))
     assert e.value.code in (5,)
+
+
+def test_4d_nan_source_and_links_are_reported():
+    import torch
+    import paper_0707_4018_gb300 as mg
+    dims = (4, 4, 4, 4)
+    V = 256
+    U = inputs.su3_links(dims, seed=2)
+    p = mg.mg_default_params(levels=2, blocks=[(2, 2, 2, 2)], Nv=[4], chiral_split=1, n_pass=1)
+    ctx = mg.Context.setup(to_dev(U), 0.1, dims, p)
+    chi = inputs.gaussian_spinor(V, 12, 3, 0)
+    chi[9, 4] = np.nan
+    psi = torch.empty((V, 12), dtype=torch.complex128, device="cuda")
+    with pytest.raises(mg.MGError) as e:
+        ctx.solve(to_dev(chi), psi, 1e-10)
+    assert e.value.code == 5
+    assert ctx.solve(to_dev(inputs.gaussian_spinor(V, 12, 3, 1)), psi, 1e-10)["converged"]
+    ctx.close()
+    Ubad = U.copy()
+    Ubad[17, 2, 1, 1] = np.nan
+    with pytest.raises(mg.MGError) as e:
+        mg.Context.setup(to_dev(Ubad), 0.1, dims, p)
+    assert e.value.code == 5
