@@ -305,6 +305,73 @@ def dslash4_roofline(precision: int, dims=(32, 32, 32, 64), iters: int = 20):
                 tflops=V * 1368 / t / 1e12)
 
 
+# several gauge configurations of uneven sizes, 16 sources each (workload id, L, beta)
+MIX_FIELDS = ((0, 64, 6.0), (2, 128, 6.0), (1, 256, 6.0), (1, 256, 10.0))
+MIX_RHS = 16
+MIX_DM = 0.02
+
+
+def mixed_sizes(precision: int = 1, reps: int = 2):
+    """Solves/s including setup for a set of gauge configurations of uneven lattice sizes, each with
+    MIX_RHS Gaussian sources at m = m_c + 0.02: per configuration one setup and one batched solve
+    (mg_solve_batch, all sources in lockstep), the configurations concurrently (one host thread and
+    context stream each). Fields without a stored m_c are skipped (and listed)."""
+    import torch
+    import paper_0707_4018_gb300 as mg
+    table = mcrit_table()
+    cfgs, skipped = [], []
+    for wid, Lm, beta in MIX_FIELDS:
+        row = table.get(f"w{wid}_L{Lm}_b{beta:g}")
+        U, theta, _ = inputs.schwinger_links(Lm, beta, sweeps=2000, workload_id=wid)
+        if row is None or row["theta_digest"] != inputs.field_digest(theta):
+            skipped.append(f"{Lm}x{Lm} beta {beta:g}")
+            continue
+        seed = inputs.workload_seed(wid, Lm, beta)
+        chi = np.stack([inputs.gaussian_source(Lm, Lm, seed=seed, index=10 + i) for i in range(MIX_RHS)])
+        cfgs.append(dict(L=Lm, beta=beta, m=row["m_crit"] + MIX_DM, U=torch.from_numpy(U).cuda(),
+                         chi=torch.from_numpy(chi).cuda(),
+                         psi=torch.empty((MIX_RHS, Lm * Lm, 2), dtype=torch.complex128, device="cuda")))
+    if not cfgs:
+        return {"skipped": skipped}
+
+    def params():
+        p = mg_params(precision)
+        p.max_rhs = MIX_RHS
+        return p
+
+    def one(cf, res):
+        ctx = mg.Context.setup(cf["U"], cf["m"], (cf["L"], cf["L"]), params())
+        st = ctx.solve_batch(cf["chi"], cf["psi"], TOL, raise_on_fail=False)
+        ctx.close()
+        res.append((cf["L"], cf["beta"], st))
+
+    best = None
+    for _ in range(reps):  # the first repetition also warms up (graph capture, pool)
+        res = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        threads = [threading.Thread(target=one, args=(cf, res)) for cf in cfgs]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if len(res) != len(cfgs):
+            raise RuntimeError("a configuration of the mixed-size batch failed")
+        if best is None or dt < best[0]:
+            best = (dt, res)
+    dt, res = best
+    n = MIX_RHS * len(cfgs)
+    return {"workload": "2d U(1) configurations of uneven sizes " + ", ".join(f"{c['L']}^2 beta {c['beta']:g}" for c in cfgs)
+                        + f"; {MIX_RHS} Gaussian sources each at m_c + {MIX_DM}, 3-level MG, one batched solve per "
+                        "configuration, the configurations concurrently",
+            "solves": n, "seconds": dt, "solves_per_s_incl_setup": n / dt, "skipped": skipped,
+            "iters_max": {f"{Lm}^2 b{beta:g}": max(s["iters"] for s in st) for Lm, beta, st in res},
+            "converged": all(s["converged"] for _, _, st in res for s in st),
+            "worst_true_rel_residual": max(s["true_rel_residual"] for _, _, st in res for s in st)}
+
+
 SU3_DIMS = (16, 16, 16, 32)
 SU3_RHS = 12
 
@@ -546,6 +613,9 @@ def run_only(case: str):
     if case == "su3":
         print(json.dumps({"case": case, **su3_workload()}))
         return
+    if case == "mixed-sizes":
+        print(json.dumps({"case": case, **mixed_sizes()}))
+        return
     if case == "su3-batch-prof":  # mixed precision, setup and one batch of 12 sources (launch-list profiling)
         r = su3_workload((1,), SU3_RHS, batched=True, singles=False)
         print(json.dumps({"case": case, **r}))
@@ -676,7 +746,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--only", default=None, choices=["dslash-f32", "dslash-f64", "dslash4-f32", "dslash4-f64", "solve", "vcycle",
                                                       "transfer", "coarse-tc", "coarse-tc4", "su3", "su3-prof",
-                                                      "su3-batch-prof"],
+                                                      "su3-batch-prof", "mixed-sizes"],
                     help="profiling cases: the Dslash timing loop alone (2d, or 4d SU(3)), one beta's setup + 3 solves, "
                          "25 mixed-precision V-cycles after one beta's setup, or 5 V-cycles on a 1024^2 "
                          "hierarchy (fine level larger than L2, for the restriction and prolongation), or the "
@@ -739,6 +809,7 @@ def main():
     ds64 = dslash_roofline(0)
     ds4 = dslash4_roofline(1)
     su3 = su3_workload() if world_of(d) == 1 or rank == 0 else None
+    mix = mixed_sizes() if world_of(d) == 1 or rank == 0 else None
     cr = coarsest_roofline(fields_dev)
 
     cpu = None
@@ -773,6 +844,7 @@ def main():
                        "su3_4d_f32": {**ds4, "frac": ds4["gbs"] / peak}},
         "cpu_baseline": cpu,
         "su3_4d": su3,
+        "mixed_sizes": mix,
     }
     print(json.dumps(line), flush=True)
 

@@ -20,9 +20,10 @@ from oracle.lattice import Lattice  # noqa: E402
 
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "mcrit.json")
 
-# (workload id, L, beta): 64^2 beta=6 (the small two-level case) and the 256^2 points
-# of the three-level sweep over beta in {3, 6, 10}
-FIELDS = [(0, 64, 6.0), (1, 256, 3.0), (1, 256, 6.0), (1, 256, 10.0)]
+# (workload id, L, beta): 64^2 beta=6 (the small two-level case), the 256^2 points
+# of the three-level sweep over beta in {3, 6, 10}, and a 128^2 beta=6 field
+FIELDS = [(0, 64, 6.0), (1, 256, 3.0), (1, 256, 6.0), (1, 256, 10.0),
+          (2, 128, 6.0)]  # the mixed-size batch (64^2, 128^2 and 256^2 fields)
 # (workload id, dims) of the 4d SU(3) fields: projected 1 + 0.4 H links after 4 APE steps (alpha 0.5)
 FIELDS4 = [(3, (16, 16, 16, 32))]
 
@@ -33,6 +34,13 @@ def key4(wid, dims):
 
 def key(wid, L, beta):
     return f"w{wid}_L{L}_b{beta:g}"
+
+
+def save(k, row):
+    """Merge one entry into the stored table (re-read first: several scans may run at once)."""
+    table = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    table[k] = row
+    json.dump(table, open(OUT, "w"), indent=1, sort_keys=True)
 
 
 def main():
@@ -54,7 +62,7 @@ def main():
                                           links_digest=inputs.field_digest(U), m_crit=mc,
                                           gen_seconds=round(t1 - t0, 1), scan_seconds=round(t2 - t1, 1))
             print(key4(wid, dims), table[key4(wid, dims)], flush=True)
-            json.dump(table, open(OUT, "w"), indent=1, sort_keys=True)
+            save(key4(wid, dims), table[key4(wid, dims)])
         return
     for wid, L, beta in FIELDS:
         if args.only and args.only != f"{L},{beta:g}":
@@ -71,7 +79,7 @@ def main():
                                         theta_digest=inputs.field_digest(theta), m_crit=mc,
                                         gen_seconds=round(t1 - t0, 1), scan_seconds=round(t2 - t1, 1))
         print(key(wid, L, beta), table[key(wid, L, beta)], flush=True)
-        json.dump(table, open(OUT, "w"), indent=1, sort_keys=True)
+        save(key(wid, L, beta), table[key(wid, L, beta)])
 
 
 if __name__ == "__main__":
