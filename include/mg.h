@@ -109,6 +109,13 @@ typedef struct {
   long long coarsest_iters;          /* iterations of the iterative coarsest solve */
   double ms;                         /* wall time of the call, stream-synchronised */
   int graphs;                        /* 1 if the V-cycles replayed a captured CUDA graph */
+  double setup_s;                    /* seconds the context's setup took (mg_setup, mg_load_setup or
+                                        mg_clone; host wall clock, stream-synchronised): the cost the
+                                        paper amortises over right-hand sides and masses */
+  double solve_s;                    /* seconds of this solve (ms / 1000) */
+  long long fine_D_apps;             /* fine operator applications in this call: outer loop, true
+                                        residuals and every V-cycle's smoothing and residual (the
+                                        paper's cost measure); equals level_apps[0] */
 } mg_stats;
 
 typedef struct mg_ctx mg_ctx;
@@ -136,9 +143,13 @@ int mg_setup(mg_ctx **ctx, const mg_geom *g, const void *U, double m, const mg_p
 
 /* Solve D psi = chi to relative true residual tol by flexible GCR preconditioned
  * with one V-cycle per iteration (FP64 outer loop, true residual at restarts).
- * chi, psi: device complex128 [x][s]; psi is overwritten (initial guess 0).
- * st may be NULL. Returns NOT_CONVERGED (psi = last iterate) after max_iter. */
-int mg_solve(mg_ctx *ctx, const void *chi, void *psi, double tol, mg_stats *st);
+ * chi, psi: device complex128 [x][s] (d = 4: [x][s][c]); psi is overwritten (initial
+ * guess 0). nrhs > 1 solves nrhs systems at the context mass with chi, psi holding
+ * nrhs vectors back to back: the same as mg_solve_batch(ctx, nrhs, chi, psi, NULL, tol,
+ * st) (the paper: many right-hand sides amortise one setup), so nrhs <= max_rhs.
+ * st may be NULL, else nrhs entries. Returns NOT_CONVERGED (psi = last iterate)
+ * after max_iter, INVALID_ARG for nrhs < 1. */
+int mg_solve(mg_ctx *ctx, const void *chi, void *psi, int nrhs, double tol, mg_stats *st);
 
 /* Solve nrhs systems D(m_v) psi_v = chi_v with one hierarchy (paper: many
  * right-hand sides amortise one setup; mass reuse, the setup at the lightest
@@ -181,6 +192,44 @@ int mg_update_mass(mg_ctx *ctx, double m);
  * Errors: INVALID_ARG (null pointers), STATE (src has a stale level), UNSUPPORTED (d = 4),
  * OOM, CUDA. */
 int mg_clone(mg_ctx *src, double m, void *stream, mg_ctx **out);
+
+/* Adaptive setups of several gauge configurations (possibly of different lattice
+ * sizes) at once (paper: one setup per configuration, amortised over its right-hand
+ * sides and masses). Configuration i is set up exactly as mg_setup(&ctx[i], &g[i], U[i],
+ * m[i], &p[i], stream) would, each on its own context stream and host thread, so the
+ * setups run concurrently on the GPU; every context orders its work after `stream`.
+ *   count  number of configurations (>= 1)
+ *   ctx    out: count contexts (all NULL on error)
+ *   g, U, m, p  arrays of count geometries, device link pointers, masses and parameters
+ * The result of every configuration is the one mg_setup gives (bitwise). On any failure
+ * every context made so far is destroyed and the first failure's status is returned. */
+int mg_setup_batch(int count, mg_ctx **ctx, const mg_geom *g, const void *const *U, const double *m,
+                   const mg_params *p, void *stream);
+
+/* Write the context's adaptive setup to a file (paper: the near-null space found once is
+ * reused for further masses and right-hand sides). The file holds the geometry, the
+ * parameters, the mass, a 64-bit FNV-1a digest of the links the setup was made on, and
+ * the near-null vectors of every level before orthonormalisation (complex128, the
+ * mg_get_null_vectors layout), with a digest of that payload. The prolongators and
+ * Galerkin operators are not stored: loading rebuilds them from the vectors.
+ * Errors: INVALID_ARG (null pointers), STATE (a stale level), CUDA, and UNSUPPORTED when
+ * the file cannot be written. */
+int mg_save_setup(mg_ctx *ctx, const char *path);
+
+/* A context from a saved setup: allocates as mg_setup does, copies U, then rebuilds every
+ * level from the stored vectors (block Gram-Schmidt, Galerkin operator, coarsest-solve
+ * preparation) without any relaxation or adaptive pass. The result, and every solve on
+ * it, is bitwise equal to those of the context that was saved.
+ *   U       device links of the same layout as mg_setup's; their digest must match the
+ *           stored one (a setup belongs to its gauge field)
+ *   stream  cudaStream_t the new context orders its work after
+ * Errors: INVALID_ARG (null pointers, unreadable or corrupt file, version or size
+ * mismatch, links whose digest differs), OOM, CUDA. */
+int mg_load_setup(mg_ctx **ctx, const char *path, const void *U, void *stream);
+
+/* The geometry, parameters and current mass of a context (any out-pointer may be NULL);
+ * for a context from mg_load_setup these are the saved ones. */
+int mg_context_info(const mg_ctx *ctx, mg_geom *g, mg_params *p, double *m);
 
 /* Frees every device buffer of the context. NULL is a no-op. */
 void mg_destroy(mg_ctx *ctx);
@@ -250,8 +299,10 @@ int mg_level_size(mg_ctx *ctx, int level, long long *n_sites, int *n_int);
  * this is a library convenience.
  *   g: d = 2, Nc = 1, at most 65536 sites (256 x 256); larger lattices are rejected
  *      with MG_ERR_INVALID_ARG before any device work.
- *   U, b, x: device complex128 ([x][mu], [x][s], [x][s]); b and x must not alias.
- *   stream: cudaStream_t; the call is asynchronous on it.
+ *   U, b, x: device complex128 ([x][mu], [x][s], [x][s]) on the CURRENT device (the
+ *      scratch array is per device); b and x must not alias. x on another device, or not
+ *      device memory, is rejected with MG_ERR_INVALID_ARG.
+ *   stream: cudaStream_t of the current device; the call is asynchronous on it.
  * Scratch lives in one fixed device array (about 4 MB, held on every GPU that
  * loads the library until exit), shared by all calls on a device; calls whose
  * work overlaps on the GPU race on it. The first call on a device looks up the

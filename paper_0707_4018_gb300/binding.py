@@ -44,12 +44,14 @@ class mg_params(ctypes.Structure):
 class mg_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("true_rel_residual", ctypes.c_double),
                 ("level_apps", ctypes.c_longlong * MG_MAX_LEVELS), ("coarsest_iters", ctypes.c_longlong),
-                ("ms", ctypes.c_double), ("graphs", ctypes.c_int)]
+                ("ms", ctypes.c_double), ("graphs", ctypes.c_int), ("setup_s", ctypes.c_double),
+                ("solve_s", ctypes.c_double), ("fine_D_apps", ctypes.c_longlong)]
 
     def as_dict(self):
         return dict(iters=self.iters, converged=bool(self.converged), true_rel_residual=self.true_rel_residual,
                     level_apps=list(self.level_apps), coarsest_iters=self.coarsest_iters, ms=self.ms,
-                    graphs=bool(self.graphs))
+                    graphs=bool(self.graphs), setup_s=self.setup_s, solve_s=self.solve_s,
+                    fine_D_apps=self.fine_D_apps)
 
 
 _lib = None
@@ -73,7 +75,11 @@ def load():
     sig = {
         "mg_default_params": (None, [P(mg_params)]),
         "mg_setup": (I, [P(ctxp), P(mg_geom), VP, D, P(mg_params), VP]),
-        "mg_solve": (I, [ctxp, VP, VP, D, P(mg_stats)]),
+        "mg_solve": (I, [ctxp, VP, VP, I, D, P(mg_stats)]),
+        "mg_setup_batch": (I, [I, P(ctxp), P(mg_geom), P(VP), P(D), P(mg_params), VP]),
+        "mg_save_setup": (I, [ctxp, ctypes.c_char_p]),
+        "mg_load_setup": (I, [P(ctxp), ctypes.c_char_p, VP, VP]),
+        "mg_context_info": (I, [ctxp, P(mg_geom), P(mg_params), P(D)]),
         "mg_solve_batch": (I, [ctxp, I, VP, VP, P(D), D, P(mg_stats)]),
         "mg_coarse_apply_mrhs": (I, [ctxp, I, I, VP, VP, I]),
         "mg_update_mass": (I, [ctxp, D]),
@@ -111,7 +117,8 @@ def exported_symbols():
             "mg_dslash", "mg_level_apply", "mg_restrict", "mg_prolong", "mg_vcycle", "mg_smooth", "mg_build_level",
             "mg_get_null_vectors", "mg_get_prolongator", "mg_get_coarse_op", "mg_level_size", "mg_kernel_launches",
             "mg_smooth_fine_noalloc", "mg_coarsest_solve", "mg_selftest_barrier", "mg_solve_batch",
-            "mg_coarse_apply_mrhs", "mg_autotune_report", "mg_clone"]
+            "mg_coarse_apply_mrhs", "mg_autotune_report", "mg_clone", "mg_setup_batch", "mg_save_setup",
+            "mg_load_setup", "mg_context_info"]
 
 
 def autotune_report() -> dict:
@@ -243,6 +250,53 @@ class Context:
                             float(m), ctypes.byref(p), s))
         return cls(h, dims, p, s)
 
+    @classmethod
+    def setup_batch(cls, Us, masses, dims_list, params_list, stream=None) -> list:
+        """mg_setup_batch: the adaptive setups of several configurations (possibly of different
+        sizes) at once, each as Context.setup would make it; returns one Context per configuration."""
+        lib = load()
+        n = len(Us)
+        if not (len(masses) == len(dims_list) == len(params_list) == n) or n < 1:
+            raise ValueError("one mass, geometry and parameter set per configuration")
+        geoms = (mg_geom * n)()
+        ptrs = (ctypes.c_void_p * n)()
+        ms = (ctypes.c_double * n)(*[float(m) for m in masses])
+        ps = (mg_params * n)(*params_list)
+        for i, (U, dims) in enumerate(zip(Us, dims_list)):
+            four = len(dims) == 4
+            geoms[i] = make_geom(dims, Nc=3 if four else 1)
+            V = 1
+            for L in dims:
+                V *= int(L)
+            ptrs[i] = _ptr(U, torch.complex128, (36 if four else 2) * V)
+        hs = (ctypes.c_void_p * n)()
+        s = _stream(stream)
+        _check(lib.mg_setup_batch(n, hs, geoms, ptrs, ms, ps, s))
+        return [cls(ctypes.c_void_p(hs[i]), dims_list[i], params_list[i], s) for i in range(n)]
+
+    @classmethod
+    def load(cls, path: str, U: torch.Tensor, dims, stream=None) -> "Context":
+        """mg_load_setup: a context rebuilt from a setup saved by Context.save, on the same links U."""
+        four = len(dims) == 4
+        V = 1
+        for L in dims:
+            V *= int(L)
+        h = ctypes.c_void_p()
+        s = _stream(stream)
+        _check(load().mg_load_setup(ctypes.byref(h), os.fsencode(path), _ptr(U, torch.complex128,
+                                                                               (36 if four else 2) * V), s))
+        p = mg_params()
+        g = mg_geom()
+        m = ctypes.c_double()
+        _check(load().mg_context_info(h, ctypes.byref(g), ctypes.byref(p), ctypes.byref(m)))
+        ctx = cls(h, dims, p, s)
+        ctx.mass = float(m.value)
+        return ctx
+
+    def save(self, path: str):
+        """mg_save_setup: write this context's near-null vectors (and what identifies them) to path."""
+        _check(load().mg_save_setup(self._need(), os.fsencode(path)))
+
     def close(self):
         if self._h:
             load().mg_destroy(self._h)
@@ -280,10 +334,21 @@ class Context:
         st = mg_stats()
         n = self.n0
         code = load().mg_solve(self._need(), _ptr(chi, torch.complex128, n), _ptr(psi, torch.complex128, n),
-                               float(tol), ctypes.byref(st))
+                               1, float(tol), ctypes.byref(st))
         if code != 0 and (raise_on_fail or code != 4):
             _check(code)
         return st.as_dict()
+
+    def solve_nrhs(self, chi: torch.Tensor, psi: torch.Tensor, tol: float, raise_on_fail: bool = True) -> list:
+        """mg_solve with nrhs = chi.shape[0] right-hand sides at the context mass; stats per vector."""
+        nrhs = int(chi.shape[0])
+        n = self.n0 * nrhs
+        st = (mg_stats * nrhs)()
+        code = load().mg_solve(self._need(), _ptr(chi, torch.complex128, n), _ptr(psi, torch.complex128, n),
+                               nrhs, float(tol), st)
+        if code != 0 and (raise_on_fail or code != 4):
+            _check(code)
+        return [st[v].as_dict() for v in range(nrhs)]
 
     def solve_batch(self, chi: torch.Tensor, psi: torch.Tensor, tol: float, masses=None,
                     raise_on_fail: bool = True) -> list:

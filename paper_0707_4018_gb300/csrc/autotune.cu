@@ -23,26 +23,19 @@ int autotune_choose(const std::string &key, int count, const std::function<void(
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   MG_CUDA(cudaStreamIsCapturing(s, &cap));
   if (cap != cudaStreamCaptureStatusNone) return 0;
-  cudaEvent_t e0, e1;
-  MG_CUDA(cudaEventCreate(&e0));
-  MG_CUDA(cudaEventCreate(&e1));
+  EventPair ev;
   int best = 0;
   float best_ms = 0.f;
   for (int v = 0; v < count; ++v) {
     launch(v);  // untimed: first-touch and instruction-cache effects
-    MG_CUDA(cudaEventRecord(e0, s));
+    ev.start(s);
     for (int r = 0; r < 3; ++r) launch(v);
-    MG_CUDA(cudaEventRecord(e1, s));
-    MG_CUDA(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    MG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    const float ms = ev.stop(s);
     if (v == 0 || ms < best_ms) {
       best = v;
       best_ms = ms;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[key] = best;
   return best;

@@ -141,6 +141,34 @@ struct DevBuf {
   }
 };
 
+// two timing events recorded around a region of a stream; destroyed on every exit path
+// (a solve that throws must not leak them)
+struct EventPair {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  EventPair() {
+    MG_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+      cudaEventDestroy(e0);
+      fail(MG_ERR_CUDA, "cudaEventCreate failed");
+    }
+  }
+  EventPair(const EventPair &) = delete;
+  EventPair &operator=(const EventPair &) = delete;
+  ~EventPair() {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  void start(cudaStream_t s) { MG_CUDA(cudaEventRecord(e0, s)); }
+  // records the end, waits for it and returns the milliseconds between the two events
+  float stop(cudaStream_t s) {
+    MG_CUDA(cudaEventRecord(e1, s));
+    MG_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    MG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    return ms;
+  }
+};
+
 // ---------------------------------------------------------------------------
 // geometry of one 2d level and of a blocking between two levels
 // ---------------------------------------------------------------------------

@@ -12,10 +12,13 @@
 // stream; the host only sequences launches and reads convergence scalars.
 #include <cmath>
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "kernels.h"
@@ -152,6 +155,7 @@ struct mg_ctx {
   bool graphs_ok = true;
   mg::DevBuf<mg::Cx<double>> z64;
   mg::Engine4 *e4 = nullptr;  // the 4d SU(3) hierarchy (d = 4); the members above stay empty
+  double setup_s = 0.0;       // seconds of the setup, load or clone that made this context
   ~mg_ctx() {
     if (s) cudaStreamSynchronize(s);  // no work may still use the buffers released below
     if (e4) mg::engine4_destroy(e4);
@@ -1077,6 +1081,99 @@ static void need_ptr(const void *p) {
   if (!p) fail(MG_ERR_INVALID_ARG, "null pointer");
 }
 
+static double seconds_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// A context at mass m on links U: the full adaptive setup, or, with saved vectors
+// (`vectors[l]`: the host copy of level l's near-null vectors), the rebuild of every
+// level from them (block Gram-Schmidt, Galerkin operators, coarsest preparation) with no
+// relaxation or adaptive pass.
+static std::unique_ptr<mg_ctx> make_context(const mg_geom *g, const void *U, double m, const mg_params *p,
+                                            void *stream, const std::vector<std::vector<Cx<double>>> *vectors) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (g != nullptr && g->d == 4) {
+    validate4(g, p);
+    auto c = std::make_unique<mg_ctx>();
+    c->geom = *g;
+    c->p = *p;
+    c->m = m;
+    c->user = static_cast<cudaStream_t>(stream);
+    MG_CUDA(cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking));
+    MG_CUDA(cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming));
+    enter(*c);
+    c->e4 = engine4_create(g, U, m, p, c->s, vectors == nullptr);
+    if (vectors != nullptr) {
+      const std::vector<Cx<double>> &v = (*vectors)[0];
+      if ((long long)v.size() != engine4_null_vector_count(*c->e4))
+        fail(MG_ERR_INVALID_ARG, "saved setup: vector count does not match the hierarchy");
+      DevBuf<Cx<double>> tmp;
+      tmp.alloc(v.size());
+      pool_ready();
+      MG_CUDA(cudaMemcpyAsync(tmp.p, v.data(), v.size() * sizeof(Cx<double>), cudaMemcpyHostToDevice, c->s));
+      engine4_build_level(*c->e4, tmp.p);
+    }
+    MG_CUDA(cudaStreamSynchronize(c->s));
+    c->setup_s = seconds_since(t0);
+    return c;
+  }
+  auto c = create(g, m, p, stream);
+  MG_CUDA(cudaMemcpyAsync(c->U64.p, U, c->U64.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, c->s));
+  if (c->p.precision == MG_FP32) launch_convert<float, double>(c->U64.p, c->U32.p, c->U64.n, c->s);
+  if (vectors == nullptr) {
+    setup_level(*c, 0, true);
+  } else {
+    for (int l = 0; l + 1 < c->p.levels; ++l) {
+      Level &L = c->lv[l];
+      const std::vector<Cx<double>> &v = (*vectors)[l];
+      if (v.size() != L.nullv.n) fail(MG_ERR_INVALID_ARG, "saved setup: vector count does not match the hierarchy");
+      MG_CUDA(cudaMemcpyAsync(L.nullv.p, v.data(), v.size() * sizeof(Cx<double>), cudaMemcpyHostToDevice, c->s));
+      build_level(*c, l);
+      if (l + 2 == c->p.levels) prepare_coarsest(*c);
+    }
+  }
+  make_fp32_copies(*c);
+  collect_coarsest(*c);
+  MG_CUDA(cudaStreamSynchronize(c->s));
+  c->setup_s = seconds_since(t0);
+  return c;
+}
+
+// ---- saved setups: header, then the near-null vectors of every level ----
+struct SetupFileHeader {
+  char magic[8];
+  uint32_t version, levels_saved;
+  mg_geom g;
+  mg_params p;
+  double m;
+  uint64_t links_digest, payload_digest;
+  uint64_t count[MG_MAX_LEVELS];  // complex128 elements of each level's vectors
+};
+static const char kSetupMagic[8] = {'M', 'G', 'S', 'E', 'T', 'U', 'P', '1'};
+
+// 64-bit FNV-1a (Fowler, Noll, Vo) over bytes
+static uint64_t fnv1a(const void *data, size_t n, uint64_t h = 14695981039346656037ULL) {
+  const unsigned char *q = static_cast<const unsigned char *>(data);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= q[i];
+    h *= 1099511628211ULL;
+  }
+  return h;
+}
+
+static size_t link_bytes(const mg_geom &g) {
+  long long vol = 1;
+  for (int mu = 0; mu < g.d; ++mu) vol *= g.dims[mu];
+  return (size_t)vol * g.d * g.Nc * g.Nc * sizeof(Cx<double>);
+}
+
+static uint64_t device_digest(const void *dev, size_t bytes, cudaStream_t s) {
+  std::vector<unsigned char> h(bytes);
+  MG_CUDA(cudaMemcpyAsync(h.data(), dev, bytes, cudaMemcpyDeviceToHost, s));
+  MG_CUDA(cudaStreamSynchronize(s));
+  return fnv1a(h.data(), bytes);
+}
+
 extern "C" {
 
 void mg_default_params(mg_params *p) {
@@ -1115,32 +1212,55 @@ int mg_setup(mg_ctx **ctx, const mg_geom *g, const void *U, double m, const mg_p
     if (!ctx) fail(MG_ERR_INVALID_ARG, "null context out-pointer");
     *ctx = nullptr;
     need_ptr(U);
-    if (g != nullptr && g->d == 4) {
-      validate4(g, p);
-      auto c = std::make_unique<mg_ctx>();
-      c->geom = *g;
-      c->p = *p;
-      c->m = m;
-      c->user = static_cast<cudaStream_t>(stream);
-      MG_CUDA(cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking));
-      MG_CUDA(cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming));
-      enter(*c);
-      c->e4 = engine4_create(g, U, m, p, c->s);
-      *ctx = c.release();
-      return;
-    }
-    auto c = create(g, m, p, stream);
-    MG_CUDA(cudaMemcpyAsync(c->U64.p, U, c->U64.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, c->s));
-    if (c->p.precision == MG_FP32) launch_convert<float, double>(c->U64.p, c->U32.p, c->U64.n, c->s);
-    setup_level(*c, 0, true);
-    make_fp32_copies(*c);
-    collect_coarsest(*c);
-    MG_CUDA(cudaStreamSynchronize(c->s));
-    *ctx = c.release();
+    *ctx = make_context(g, U, m, p, stream, nullptr).release();
   });
 }
 
-int mg_solve(mg_ctx *c, const void *chi, void *psi, double tol, mg_stats *st) {
+int mg_setup_batch(int count, mg_ctx **ctx, const mg_geom *g, const void *const *U, const double *m,
+                   const mg_params *p, void *stream) {
+  return guarded([&] {
+    if (count < 1) fail(MG_ERR_INVALID_ARG, "count must be >= 1");
+    if (!ctx || !g || !U || !m || !p) fail(MG_ERR_INVALID_ARG, "null array");
+    for (int i = 0; i < count; ++i) ctx[i] = nullptr;
+    for (int i = 0; i < count; ++i) need_ptr(U[i]);
+    std::vector<std::unique_ptr<mg_ctx>> made(count);
+    std::vector<Error> errs(count, Error{MG_OK, ""});
+    int dev = 0;
+    MG_CUDA(cudaGetDevice(&dev));  // the workers set up on the caller's device
+    // one host thread per configuration (at most 16 at a time); each setup runs on its
+    // own context stream, so the GPU overlaps them
+    const int width = std::min(count, 16);
+    for (int i0 = 0; i0 < count; i0 += width) {
+      std::vector<std::thread> th;
+      for (int i = i0; i < std::min(count, i0 + width); ++i)
+        th.emplace_back([&, i] {
+          try {
+            MG_CUDA(cudaSetDevice(dev));
+            made[i] = make_context(&g[i], U[i], m[i], &p[i], stream, nullptr);
+          } catch (const Error &e) {
+            errs[i] = e;
+          } catch (const std::bad_alloc &) {
+            errs[i] = Error{MG_ERR_OOM, "host allocation failed"};
+          } catch (...) {
+            errs[i] = Error{MG_ERR_CUDA, "unexpected exception"};
+          }
+        });
+      for (auto &t : th) t.join();
+    }
+    for (int i = 0; i < count; ++i)
+      if (errs[i].code != MG_OK) throw Error{errs[i].code, "configuration " + std::to_string(i) + ": " + errs[i].msg};
+    for (int i = 0; i < count; ++i) ctx[i] = made[i].release();
+  });
+}
+
+int mg_solve(mg_ctx *c, const void *chi, void *psi, int nrhs, double tol, mg_stats *st) {
+  if (nrhs != 1) {
+    if (nrhs < 1) {
+      t_last_error = "nrhs must be >= 1";
+      return MG_ERR_INVALID_ARG;
+    }
+    return mg_solve_batch(c, nrhs, chi, psi, nullptr, tol, st);
+  }
   int status = MG_OK;
   int rc = guarded([&] {
     need_ctx(c);
@@ -1156,6 +1276,9 @@ int mg_solve(mg_ctx *c, const void *chi, void *psi, double tol, mg_stats *st) {
         st->coarsest_iters = o.coarsest_iters;
         st->ms = o.ms;
         st->graphs = 0;
+        st->setup_s = c->setup_s;
+        st->solve_s = o.ms * 1e-3;
+        st->fine_D_apps = o.apps[0];
       }
       if (!o.converged) status = MG_ERR_NOT_CONVERGED;
       return;
@@ -1164,20 +1287,13 @@ int mg_solve(mg_ctx *c, const void *chi, void *psi, double tol, mg_stats *st) {
     for (long long &a : c->apps) a = 0;
     collect_coarsest(*c);
     c->coarsest_iters = 0;
-    cudaEvent_t e0, e1;
-    MG_CUDA(cudaEventCreate(&e0));
-    MG_CUDA(cudaEventCreate(&e1));
-    MG_CUDA(cudaEventRecord(e0, c->s));
+    EventPair ev;
+    ev.start(c->s);
     GcrOut o = outer_fgcr(*c, static_cast<const Cx<double> *>(chi), static_cast<Cx<double> *>(psi), tol,
                           c->p.gcr_restart, c->p.max_iter);
-    MG_CUDA(cudaEventRecord(e1, c->s));
-    MG_CUDA(cudaEventSynchronize(e1));
+    const float ms = ev.stop(c->s);
     c->coarsest_iters = collect_coarsest(*c);
     if (!c->use_lu) c->apps[c->p.levels - 1] += c->coarsest_iters;
-    float ms = 0.f;
-    MG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if (st) {
       st->iters = o.iters;
       st->converged = o.converged ? 1 : 0;
@@ -1186,6 +1302,9 @@ int mg_solve(mg_ctx *c, const void *chi, void *psi, double tol, mg_stats *st) {
       st->coarsest_iters = c->coarsest_iters;
       st->ms = ms;
       st->graphs = (c->graphs_ok && c->pre[c->p.precision == MG_FP32 ? 1 : 0].exec != nullptr) ? 1 : 0;
+      st->setup_s = c->setup_s;
+      st->solve_s = ms * 1e-3;
+      st->fine_D_apps = c->apps[0];
     }
     if (!o.converged) status = MG_ERR_NOT_CONVERGED;
   });
@@ -1217,6 +1336,9 @@ int mg_solve_batch(mg_ctx *c, int nrhs, const void *chi, void *psi, const double
         st[v].coarsest_iters = o[v].coarsest_iters;
         st[v].ms = o[v].ms;
         st[v].graphs = 0;
+        st[v].setup_s = c->setup_s;
+        st[v].solve_s = o[v].ms * 1e-3;
+        st[v].fine_D_apps = o[v].apps[0];
       }
       return;
     }
@@ -1233,29 +1355,20 @@ int mg_solve_batch(mg_ctx *c, int nrhs, const void *chi, void *psi, const double
     for (long long &a : c->apps) a = 0;
     collect_coarsest(*c);
     c->coarsest_iters = 0;
-    cudaEvent_t e0, e1;
-    MG_CUDA(cudaEventCreate(&e0));
-    MG_CUDA(cudaEventCreate(&e1));
-    MG_CUDA(cudaEventRecord(e0, c->s));
+    EventPair ev;
+    ev.start(c->s);
     std::vector<GcrOut> o;
     c->cur_shift = c->shift_dev.p;
     try {
       outer_fgcr_batch(*c, nrhs, static_cast<const Cx<double> *>(chi), static_cast<Cx<double> *>(psi), tol, o);
     } catch (...) {
       c->cur_shift = nullptr;
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
       throw;
     }
     c->cur_shift = nullptr;
-    MG_CUDA(cudaEventRecord(e1, c->s));
-    MG_CUDA(cudaEventSynchronize(e1));
+    const float ms = ev.stop(c->s);
     c->coarsest_iters = collect_coarsest(*c);
     if (!c->use_lu) c->apps[c->p.levels - 1] += c->coarsest_iters;
-    float ms = 0.f;
-    MG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     for (int v = 0; v < nrhs; ++v) {
       if (!o[v].converged) status = MG_ERR_NOT_CONVERGED;
       if (!st) continue;
@@ -1266,6 +1379,9 @@ int mg_solve_batch(mg_ctx *c, int nrhs, const void *chi, void *psi, const double
       st[v].coarsest_iters = c->coarsest_iters;
       st[v].ms = ms;
       st[v].graphs = (c->graphs_ok && c->preb[c->p.precision == MG_FP32 ? 1 : 0][nrhs].exec != nullptr) ? 1 : 0;
+      st[v].setup_s = c->setup_s;
+      st[v].solve_s = ms * 1e-3;
+      st[v].fine_D_apps = c->apps[0];
     }
   });
   if (rc == MG_OK && status != MG_OK) {
@@ -1315,6 +1431,7 @@ int mg_clone(mg_ctx *src, double m, void *stream, mg_ctx **out) {
     if (!out) fail(MG_ERR_INVALID_ARG, "null context out-pointer");
     *out = nullptr;
     need_ctx(src);
+    const auto t0 = std::chrono::steady_clock::now();
     if (src->e4) fail(MG_ERR_UNSUPPORTED, "clones are built for d = 2");
     check_fresh(*src);
     MG_CUDA(cudaStreamSynchronize(src->s));  // the source's buffers are final
@@ -1336,7 +1453,102 @@ int mg_clone(mg_ctx *src, double m, void *stream, mg_ctx **out) {
     make_fp32_copies(*c);
     collect_coarsest(*c);
     MG_CUDA(cudaStreamSynchronize(c->s));
+    c->setup_s = seconds_since(t0);
     *out = c.release();
+  });
+}
+
+int mg_save_setup(mg_ctx *c, const char *path) {
+  return guarded([&] {
+    need_ctx(c);
+    need_ptr(path);
+    SetupFileHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kSetupMagic, 8);
+    h.version = 1;
+    h.g = c->geom;
+    h.p = c->p;
+    h.m = c->m;
+    std::vector<std::vector<Cx<double>>> vecs;
+    if (c->e4) {
+      h.levels_saved = 1;
+      vecs.emplace_back((size_t)engine4_null_vector_count(*c->e4));
+      DevBuf<Cx<double>> tmp;
+      tmp.alloc(vecs[0].size());
+      pool_ready();
+      engine4_get_null_vectors(*c->e4, tmp.p);
+      MG_CUDA(cudaMemcpy(vecs[0].data(), tmp.p, vecs[0].size() * sizeof(Cx<double>), cudaMemcpyDeviceToHost));
+      h.links_digest = device_digest(engine4_links(*c->e4), link_bytes(c->geom), c->s);
+    } else {
+      check_fresh(*c);
+      h.levels_saved = (uint32_t)(c->p.levels - 1);
+      for (int l = 0; l + 1 < c->p.levels; ++l) {
+        const Level &L = c->lv[l];
+        vecs.emplace_back(L.nullv.n);
+        MG_CUDA(cudaMemcpyAsync(vecs.back().data(), L.nullv.p, L.nullv.n * sizeof(Cx<double>),
+                                cudaMemcpyDeviceToHost, c->s));
+      }
+      MG_CUDA(cudaStreamSynchronize(c->s));
+      h.links_digest = device_digest(c->U64.p, link_bytes(c->geom), c->s);
+    }
+    uint64_t pd = 14695981039346656037ULL;
+    for (size_t l = 0; l < vecs.size(); ++l) {
+      h.count[l] = vecs[l].size();
+      pd = fnv1a(vecs[l].data(), vecs[l].size() * sizeof(Cx<double>), pd);
+    }
+    h.payload_digest = pd;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) fail(MG_ERR_UNSUPPORTED, std::string("cannot open ") + path + " for writing");
+    bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1;
+    for (const auto &v : vecs) ok = ok && std::fwrite(v.data(), sizeof(Cx<double>), v.size(), f) == v.size();
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) fail(MG_ERR_UNSUPPORTED, std::string("writing ") + path + " failed");
+  });
+}
+
+int mg_context_info(const mg_ctx *c, mg_geom *g, mg_params *p, double *m) {
+  return guarded([&] {
+    if (!c) fail(MG_ERR_INVALID_ARG, "null context");
+    if (g) *g = c->geom;
+    if (p) *p = c->p;
+    if (m) *m = c->m;
+  });
+}
+
+int mg_load_setup(mg_ctx **ctx, const char *path, const void *U, void *stream) {
+  return guarded([&] {
+    if (!ctx) fail(MG_ERR_INVALID_ARG, "null context out-pointer");
+    *ctx = nullptr;
+    need_ptr(path);
+    need_ptr(U);
+    FILE *f = std::fopen(path, "rb");
+    if (!f) fail(MG_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    SetupFileHeader h;
+    bool ok = std::fread(&h, sizeof(h), 1, f) == 1 && std::memcmp(h.magic, kSetupMagic, 8) == 0 && h.version == 1 &&
+              h.levels_saved >= 1 && h.levels_saved < MG_MAX_LEVELS;
+    std::vector<std::vector<Cx<double>>> vecs;
+    uint64_t pd = 14695981039346656037ULL;
+    for (uint32_t l = 0; ok && l < h.levels_saved; ++l) {
+      if (h.count[l] == 0 || h.count[l] > (1ULL << 34)) {
+        ok = false;
+        break;
+      }
+      vecs.emplace_back((size_t)h.count[l]);
+      ok = std::fread(vecs.back().data(), sizeof(Cx<double>), vecs.back().size(), f) == vecs.back().size();
+      if (ok) pd = fnv1a(vecs.back().data(), vecs.back().size() * sizeof(Cx<double>), pd);
+    }
+    std::fclose(f);
+    if (!ok) fail(MG_ERR_INVALID_ARG, std::string(path) + " is not a complete saved setup of this version");
+    if (pd != h.payload_digest) fail(MG_ERR_INVALID_ARG, std::string(path) + ": payload digest mismatch (corrupt)");
+    int dev = 0;
+    MG_CUDA(cudaGetDevice(&dev));
+    const size_t lb = link_bytes(h.g);
+    if (h.g.d != 2 && h.g.d != 4) fail(MG_ERR_INVALID_ARG, "saved setup: bad geometry");
+    if (device_digest(U, lb, static_cast<cudaStream_t>(stream)) != h.links_digest)
+      fail(MG_ERR_INVALID_ARG, "saved setup was made on other links (digest mismatch)");
+    if (h.g.d == 2 && (int)h.levels_saved != h.p.levels - 1)
+      fail(MG_ERR_INVALID_ARG, "saved setup: level count does not match its parameters");
+    *ctx = make_context(&h.g, U, h.m, &h.p, stream, &vecs).release();
   });
 }
 
@@ -1455,6 +1667,20 @@ int mg_coarse_apply_mrhs(mg_ctx *c, int level, int nrhs, const void *in, void *o
     need_level(c, level, false);
     need_ptr(in);
     need_ptr(out);
+    if (nrhs >= 1 && level >= 1) {
+      // the stencil reads neighbours of `in` while it writes `out`: the ranges must be disjoint
+      long long ns = 0;
+      int ni = 0;
+      if (c->e4)
+        engine4_level_size(*c->e4, level, &ns, &ni);
+      else {
+        ns = c->lv[level].geo.nsites;
+        ni = c->lv[level].nint;
+      }
+      const unsigned long long bytes = (unsigned long long)nrhs * ns * ni * sizeof(Cx<float>);
+      const unsigned long long a0 = reinterpret_cast<uintptr_t>(in), b0 = reinterpret_cast<uintptr_t>(out);
+      if (a0 < b0 + bytes && b0 < a0 + bytes) fail(MG_ERR_INVALID_ARG, "in and out must not overlap");
+    }
     if (c->e4) {
       if (level != 1) fail(MG_ERR_INVALID_ARG, "the 4d hierarchy has one coarse level (level 1)");
       if (nrhs < 1) fail(MG_ERR_INVALID_ARG, "nrhs must be >= 1");
@@ -1509,17 +1735,10 @@ int mg_coarsest_solve(mg_ctx *c, const void *b, void *x, long long *iters, doubl
     }
     check_fresh(*c);
     collect_coarsest(*c);
-    cudaEvent_t e0, e1;
-    MG_CUDA(cudaEventCreate(&e0));
-    MG_CUDA(cudaEventCreate(&e1));
-    MG_CUDA(cudaEventRecord(e0, c->s));
+    EventPair ev;
+    ev.start(c->s);
     coarsest_solve64(*c, static_cast<const Cx<double> *>(b), static_cast<Cx<double> *>(x));
-    MG_CUDA(cudaEventRecord(e1, c->s));
-    MG_CUDA(cudaEventSynchronize(e1));
-    float t = 0.f;
-    MG_CUDA(cudaEventElapsedTime(&t, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    const float t = ev.stop(c->s);
     const long long it = collect_coarsest(*c);
     if (iters) *iters = it;
     if (ms) *ms = t;

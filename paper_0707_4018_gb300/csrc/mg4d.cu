@@ -548,7 +548,8 @@ void validate4(const mg_geom *g, const mg_params *p) {
     fail(MG_ERR_INVALID_ARG, "level 0: Nv must be in [1, min(6 x block sites, 32)]");
 }
 
-Engine4 *engine4_create(const mg_geom *g, const void *U, double m, const mg_params *p, cudaStream_t s) {
+Engine4 *engine4_create(const mg_geom *g, const void *U, double m, const mg_params *p, cudaStream_t s,
+                        bool run_setup) {
   validate4(g, p);
   auto e = std::make_unique<Engine4>();
   e->geom = *g;
@@ -638,8 +639,10 @@ Engine4 *engine4_create(const mg_geom *g, const void *U, double m, const mg_para
   e->wsc.max_blocks = 8;
   MG_CUDA(cudaMemcpyAsync(e->U64.p, U, e->U64.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, s));
   if (e->f32) launch_convert<float, double>(e->U64.p, e->U32.p, e->U64.n, s);
-  setup(*e);
-  check_info(*e);
+  if (run_setup) {
+    setup(*e);
+    check_info(*e);
+  }
   return e.release();
 }
 
@@ -648,10 +651,8 @@ void engine4_destroy(Engine4 *e) { delete e; }
 Solve4 engine4_solve(Engine4 &e, const void *chi, void *psi, double tol) {
   for (long long &a : e.apps) a = 0;
   e.coarsest_iters = 0;
-  cudaEvent_t e0, e1;
-  MG_CUDA(cudaEventCreate(&e0));
-  MG_CUDA(cudaEventCreate(&e1));
-  MG_CUDA(cudaEventRecord(e0, e.s));
+  EventPair ev;
+  ev.start(e.s);
   auto apply = [&](const Cx<double> *in, Cx<double> *out, const Cx<double> *b = nullptr) {
     if (b != nullptr)
       fine_apply<double>(e, in, out, b, -1.0, 1.0);
@@ -661,12 +662,8 @@ Solve4 engine4_solve(Engine4 &e, const void *chi, void *psi, double tol) {
   auto prec = [&](const Cx<double> *r, Cx<double> *z) { precondition(e, r, z); };
   Gcr g = fgcr(e, apply, prec, static_cast<const Cx<double> *>(chi), static_cast<Cx<double> *>(psi), e.nf, tol,
                e.p.gcr_restart, e.p.max_iter, e.oZ.p, e.oW.p, e.orr.p, kScalOuter);
-  MG_CUDA(cudaEventRecord(e1, e.s));
-  MG_CUDA(cudaEventSynchronize(e1));
   Solve4 out;
-  MG_CUDA(cudaEventElapsedTime(&out.ms, e0, e1));
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  out.ms = ev.stop(e.s);
   out.iters = g.iters;
   out.converged = g.converged;
   out.rel = g.rel;
@@ -724,8 +721,13 @@ void engine4_smooth(Engine4 &e, const void *b, void *x, int nu) {
 void engine4_build_level(Engine4 &e, const void *vectors) {
   MG_CUDA(cudaMemcpyAsync(e.nullv.p, vectors, e.nullv.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, e.s));
   build(e);
+  check_info(e);
   MG_CUDA(cudaStreamSynchronize(e.s));
 }
+
+long long engine4_null_vector_count(const Engine4 &e) { return (long long)e.nullv.n; }
+
+const void *engine4_links(const Engine4 &e) { return e.U64.p; }
 
 void engine4_get_null_vectors(Engine4 &e, void *out) {
   MG_CUDA(cudaMemcpyAsync(out, e.nullv.p, e.nullv.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, e.s));
@@ -882,10 +884,8 @@ std::vector<Solve4> engine4_solve_batch(Engine4 &e, int nrhs, const void *chi, v
   if (nrhs < 1 || nrhs > e.bt.cap) fail(MG_ERR_INVALID_ARG, "nrhs must be in [1, max_rhs]");
   for (long long &a : e.apps) a = 0;
   e.coarsest_iters = 0;
-  cudaEvent_t e0, e1;
-  MG_CUDA(cudaEventCreate(&e0));
-  MG_CUDA(cudaEventCreate(&e1));
-  MG_CUDA(cudaEventRecord(e0, e.s));
+  EventPair ev;
+  ev.start(e.s);
   auto apply = [&](const Cx<double> *in, Cx<double> *out, const Cx<double> *rhs) {
     launch_dslash4<double>(e.U64.p, in, out, e.fg, diag4(e), rhs, rhs ? -1.0 : 1.0, rhs ? 1.0 : 0.0, e.s, nrhs);
     e.apps[0] += nrhs;
@@ -900,12 +900,7 @@ std::vector<Solve4> engine4_solve_batch(Engine4 &e, int nrhs, const void *chi, v
   fgcr_batch(e, nrhs, apply, prec, static_cast<const Cx<double> *>(chi), static_cast<Cx<double> *>(psi), e.nf, tol,
              e.p.gcr_restart, e.p.max_iter, e.bt.Z.p, e.bt.W.p, e.bt.r.p, e.bt.rin.p, e.bt.dots.p, e.bt.coef.p,
              e.bt.host, e.bt.ws, g);
-  MG_CUDA(cudaEventRecord(e1, e.s));
-  MG_CUDA(cudaEventSynchronize(e1));
-  float ms = 0.f;
-  MG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  const float ms = ev.stop(e.s);
   std::vector<Solve4> out(nrhs);
   for (int v = 0; v < nrhs; ++v) {
     out[v].iters = g[v].iters;
@@ -940,19 +935,12 @@ void engine4_coarse_apply_mrhs(Engine4 &e, int nrhs, const void *in, void *out, 
 }
 
 long long engine4_coarsest_solve(Engine4 &e, const void *b, void *x, float *ms) {
-  cudaEvent_t e0, e1;
-  MG_CUDA(cudaEventCreate(&e0));
-  MG_CUDA(cudaEventCreate(&e1));
+  EventPair ev;
   MG_CUDA(cudaMemcpyAsync(e.cb.p, b, e.nc * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, e.s));
-  MG_CUDA(cudaEventRecord(e0, e.s));
+  ev.start(e.s);
   const long long it = coarse_solve(e);
-  MG_CUDA(cudaEventRecord(e1, e.s));
+  const float t = ev.stop(e.s);
   MG_CUDA(cudaMemcpyAsync(x, e.cx.p, e.nc * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, e.s));
-  MG_CUDA(cudaEventSynchronize(e1));
-  float t = 0.f;
-  MG_CUDA(cudaEventElapsedTime(&t, e0, e1));
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   MG_CUDA(cudaStreamSynchronize(e.s));
   if (ms) *ms = t;
   return it;

@@ -95,8 +95,11 @@ struct Solve4 {
 };
 
 void validate4(const mg_geom *g, const mg_params *p);
-// runs the full adaptive setup on stream s (U: device complex128 [x][4][3][3])
-Engine4 *engine4_create(const mg_geom *g, const void *U, double m, const mg_params *p, cudaStream_t s);
+// allocates the hierarchy and copies U (device complex128 [x][4][3][3]) on stream s, then runs
+// the full adaptive setup (run_setup; otherwise the caller builds the level from saved vectors
+// with engine4_build_level before any solve)
+Engine4 *engine4_create(const mg_geom *g, const void *U, double m, const mg_params *p, cudaStream_t s,
+                        bool run_setup = true);
 void engine4_destroy(Engine4 *e);
 Solve4 engine4_solve(Engine4 &e, const void *chi, void *psi, double tol);
 void engine4_update_mass(Engine4 &e, double m);
@@ -107,6 +110,8 @@ void engine4_prolong(Engine4 &e, const void *coarse, void *fine);
 void engine4_vcycle(Engine4 &e, const void *b, void *x);
 void engine4_smooth(Engine4 &e, const void *b, void *x, int nu);
 void engine4_build_level(Engine4 &e, const void *vectors);
+long long engine4_null_vector_count(const Engine4 &e);  // complex128 elements of the Nv fine vectors
+const void *engine4_links(const Engine4 &e);            // the engine's FP64 copy of U (device)
 void engine4_get_null_vectors(Engine4 &e, void *out);
 void engine4_get_prolongator(Engine4 &e, void *out);
 void engine4_get_coarse_op(Engine4 &e, void *out);

@@ -69,6 +69,14 @@ extern "C" int mg_smooth_fine_noalloc(const mg_geom *g, const void *U, double m,
     if (nu < 0) fail(MG_ERR_INVALID_ARG, "nu must be >= 0");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const long long n = 2 * sites;
+    // the scratch address belongs to the current device: x must live there too
+    int dev = 0;
+    MG_CUDA(cudaGetDevice(&dev));
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, x) != cudaSuccess || pa.type != cudaMemoryTypeDevice || pa.device != dev) {
+      (void)cudaGetLastError();
+      fail(MG_ERR_INVALID_ARG, "x must be device memory of the current device (the scratch array is per device)");
+    }
     double *S = noalloc_scratch();
     Cx<double> *r = reinterpret_cast<Cx<double> *>(S);
     Cx<double> *Ar = r + kNoAllocMaxDofs;

@@ -56,7 +56,7 @@ def test_tensor_core_apply_matches_bf16_reference(level, nrhs):
     for k in range(nrhs):
         xb = bf16c(x[k])
         ref = op_b.apply(xb)
-        bound = op_abs.apply(np.abs(xb))
+        bound = op_abs.apply(np.abs(xb)).real
         worst_emul = max(worst_emul, float(np.max(np.abs(got[k] - ref) / bound)))
         exact = op_exact.apply(x[k].astype(np.complex128))
         worst_exact = max(worst_exact, float(np.max(np.abs(got[k] - exact) / bound)))
@@ -122,7 +122,7 @@ def test_tensor_core_apply_4d_matches_bf16_reference(nrhs):
     worst_emul = worst_exact = worst_cc = 0.0
     for k in range(nrhs):
         xb = bf16c(x[k])
-        bound = op_abs.apply(np.abs(xb))
+        bound = op_abs.apply(np.abs(xb)).real
         exact = op_exact.apply(x[k].astype(np.complex128))
         worst_emul = max(worst_emul, float(np.max(np.abs(got[k] - op_b.apply(xb)) / bound)))
         worst_exact = max(worst_exact, float(np.max(np.abs(got[k] - exact) / bound)))

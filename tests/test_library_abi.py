@@ -44,8 +44,38 @@ def test_default_params_and_argument_errors_without_gpu():
     code = lib.mg_setup(ctypes.byref(ctx), ctypes.byref(g), ctypes.c_void_p(1), 0.1, ctypes.byref(bad), None)
     assert code == 1 and b"divisible" in lib.mg_last_error()
     assert ctx.value is None
-    code = lib.mg_solve(None, None, None, 1e-10, None)
+    code = lib.mg_solve(None, None, None, 1, 1e-10, None)
     assert code == 1
+    code = lib.mg_solve(None, None, None, 0, 1e-10, None)
+    assert code == 1 and b"nrhs" in lib.mg_last_error()
+
+
+def test_new_boundary_calls_reject_bad_arguments_without_gpu(tmp_path):
+    lib = binding.load()
+    ctx = ctypes.c_void_p()
+    # a missing or foreign file is rejected before any device work
+    code = lib.mg_load_setup(ctypes.byref(ctx), str(tmp_path / "missing.mgs").encode(), ctypes.c_void_p(1), None)
+    assert code == 1 and ctx.value is None
+    junk = tmp_path / "junk.mgs"
+    junk.write_bytes(b"not a saved setup" * 100)
+    code = lib.mg_load_setup(ctypes.byref(ctx), str(junk).encode(), ctypes.c_void_p(1), None)
+    assert code == 1 and b"saved setup" in lib.mg_last_error()
+    assert lib.mg_save_setup(None, b"x") == 1
+    assert lib.mg_context_info(None, None, None, None) == 1
+    # setup batches: count and null arrays are checked first
+    assert lib.mg_setup_batch(0, None, None, None, None, None, None) == 1
+    hs = (ctypes.c_void_p * 1)()
+    assert lib.mg_setup_batch(1, hs, None, None, None, None, None) == 1
+
+
+def test_stats_struct_matches_header():
+    # mg_stats gained setup_s, solve_s and fine_D_apps at its end: the ctypes layout must follow
+    names = [f[0] for f in binding.mg_stats._fields_]
+    assert names[-3:] == ["setup_s", "solve_s", "fine_D_apps"]
+    text = open(os.path.join(ROOT, "include", "mg.h")).read()
+    body = text[text.index("typedef struct {\n  int iters;"):text.index("} mg_stats;")]
+    for n in names:
+        assert re.search(r"\b" + n + r"\b", body), n
 
 
 def test_library_is_built_for_sm_103a():
