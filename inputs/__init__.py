@@ -53,6 +53,64 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+_GPU_SRC = os.path.join(_HERE, "metropolis_gpu.cu")
+_GPU_LIB = os.path.join(_HERE, "libmginputs_gpu.so")
+_gpu_lib = None
+
+
+def build_gpu(force: bool = False) -> str:
+    """Compile the GPU twin of the Metropolis generator (metropolis_gpu.cu) for sm_103a with nvcc."""
+    if force or not os.path.exists(_GPU_LIB) or os.path.getmtime(_GPU_LIB) < os.path.getmtime(_GPU_SRC):
+        import shutil
+        nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+        tmp = _GPU_LIB + f".tmp{os.getpid()}"
+        cmd = [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-shared", "-Xcompiler",
+               "-fPIC", "-o", tmp, _GPU_SRC]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _GPU_LIB)
+    return _GPU_LIB
+
+
+def _load_gpu():
+    global _gpu_lib
+    with _lock:
+        if _gpu_lib is None:
+            lib = ctypes.CDLL(build_gpu())
+            vp = ctypes.c_void_p
+            lib.gen_metropolis_u1_2d_gpu.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                     ctypes.c_int, ctypes.c_double, vp, vp, vp, vp, vp]
+            lib.gen_metropolis_u1_2d_gpu.restype = ctypes.c_int
+            _gpu_lib = lib
+    return _gpu_lib
+
+
+def metropolis_u1_2d_gpu(L0: int, L1: int, betas, seeds, sweeps: int, hits: int = 10, step: float = 0.5):
+    """The Markov chain of metropolis_u1_2d from a cold start, run on the current CUDA device for
+    len(seeds) fields of L0 x L1 at once (beta and seed per field). Returns (theta[f, x, mu] on the
+    host, acceptance per field). Check the result's digest against the CPU generator's where a
+    stored digest exists: the two agree bit for bit unless an accept decision falls within the
+    hosts' cos / sin / exp rounding difference."""
+    import torch
+    if L0 % 2 or L1 % 2:
+        raise ValueError("Metropolis checkerboard needs even extents")
+    nf = len(seeds)
+    if len(betas) != nf:
+        raise ValueError("one beta per seed")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    theta = torch.zeros((nf, L0 * L1, 2), dtype=torch.float64, device=dev)
+    b = torch.tensor([float(x) for x in betas], dtype=torch.float64, device=dev)
+    sd = torch.tensor(np.array([int(x) for x in seeds], dtype=np.uint64).view(np.int64), device=dev)
+    acc = torch.zeros(nf, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    rc = _load_gpu().gen_metropolis_u1_2d_gpu(L0, L1, nf, int(sweeps), int(hits), float(step), b.data_ptr(),
+                                              sd.data_ptr(), theta.data_ptr(), acc.data_ptr(), stream.cuda_stream)
+    if rc != 0:
+        raise RuntimeError(f"GPU Metropolis generator: CUDA error {rc}")
+    stream.synchronize()
+    tot = max(1, sweeps * hits * 2 * L0 * L1)
+    return theta.cpu().numpy(), (acc.cpu().numpy() / tot)
+
+
 def _load():
     global _lib
     with _lock:
@@ -162,6 +220,21 @@ def field_digest(a: np.ndarray) -> str:
 def workload_seed(workload_id: int, L: int, beta: float) -> int:
     """Seed of one gauge ensemble member: root seed + workload id, with L and beta mixed in."""
     return (ROOT_SEED + workload_id) * 1000003 + L * 101 + int(round(beta * 1000))
+
+
+def member_seed(workload_id: int, L: int, beta: float, index: int) -> int:
+    """Seed of member `index` of an ensemble of many fields (index 0 is workload_seed's field)."""
+    return workload_seed(workload_id, L, beta) + (index << 40)
+
+
+def schwinger_links_gpu(L: int, beta: float, sweeps: int = 2000, workload_id: int = 0, hits: int = 10,
+                        step: float = 0.5, indices=(0,)):
+    """Fields of the 2d U(1) ensemble recipe made by the GPU twin of the Metropolis chain:
+    members `indices` (seed member_seed), links computed on the host from the angles exactly as
+    schwinger_links does. Returns [(U, theta, acceptance)] per member."""
+    seeds = [member_seed(workload_id, L, beta, i) for i in indices]
+    th, acc = metropolis_u1_2d_gpu(L, L, [beta] * len(seeds), seeds, sweeps, hits=hits, step=step)
+    return [(links_from_angles(th[k]), th[k], float(acc[k])) for k in range(len(seeds))]
 
 
 def schwinger_links(L: int, beta: float, sweeps: int = 2000, workload_id: int = 0, hits: int = 10,

@@ -24,6 +24,11 @@ OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "mcrit.json")
 # of the three-level sweep over beta in {3, 6, 10}, and a 128^2 beta=6 field
 FIELDS = [(0, 64, 6.0), (1, 256, 3.0), (1, 256, 6.0), (1, 256, 10.0),
           (2, 128, 6.0)]  # the mixed-size batch (64^2, 128^2 and 256^2 fields)
+# (workload id, L, beta) of fields too large for the Arnoldi scan (the 1024^2 points of the
+# three-level sweep): m_c is taken from the 256^2 field of the same beta and recipe (a calibration
+# on the smaller lattice), and the row records the 1024^2 field's own digest
+CALIBRATED = [(1, 1024, 3.0), (1, 1024, 6.0), (1, 1024, 10.0)]
+CALIBRATION_L = 256
 # (workload id, dims) of the 4d SU(3) fields: projected 1 + 0.4 H links after 4 APE steps (alpha 0.5)
 FIELDS4 = [(3, (16, 16, 16, 32))]
 
@@ -47,8 +52,26 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--only", default=None)
     ap.add_argument("--su3", action="store_true", help="the 4d SU(3) fields only")
+    ap.add_argument("--calibrated", action="store_true", help="the 1024^2 fields (m_c from 256^2)")
     args = ap.parse_args()
     table = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    if args.calibrated:
+        for wid, L, beta in CALIBRATED:
+            if args.only and args.only != f"{L},{beta:g}":
+                continue
+            src = key(wid, CALIBRATION_L, beta)
+            if src not in table:
+                raise SystemExit(f"{src} must be computed first")
+            t0 = time.time()
+            U, theta, acc = inputs.schwinger_links(L, beta, sweeps=2000, workload_id=wid)
+            t1 = time.time()
+            row = dict(workload_id=wid, L=L, beta=beta, sweeps=2000, hits=10, step=0.5,
+                       seed=inputs.workload_seed(wid, L, beta), acceptance=acc,
+                       Q=round(inputs.topological_charge(theta, L, L)), theta_digest=inputs.field_digest(theta),
+                       m_crit=table[src]["m_crit"], m_crit_from=src, gen_seconds=round(t1 - t0, 1))
+            print(key(wid, L, beta), row, flush=True)
+            save(key(wid, L, beta), row)
+        return
     if args.su3:
         for wid, dims in FIELDS4:
             t0 = time.time()
