@@ -55,20 +55,37 @@ def mcrit_table():
     return json.load(open(os.path.join(ROOT, "tests", "golden", "mcrit.json")))
 
 
-def make_inputs(rank: int):
-    """Links, critical masses and sources of the workload (host numpy)."""
+def make_inputs(rank: int, Lf: int = L):
+    """Links, critical masses and sources of the workload (host numpy). The links come from the
+    GPU twin of the Metropolis generator (the CPU chain, step for step); the digest of every
+    field is compared with the one the CPU generator stored next to its critical mass."""
     table = mcrit_table()
     fields = []
+    wid = WORKLOAD_ID + 100 * rank
     for beta in BETAS:
-        U, theta, _ = inputs.schwinger_links(L, beta, sweeps=2000, workload_id=WORKLOAD_ID + 100 * rank)
-        row = table.get(f"w{WORKLOAD_ID}_L{L}_b{beta:g}")
+        (U, theta, _), = inputs.schwinger_links_gpu(Lf, beta, sweeps=2000, workload_id=wid)
+        row = table.get(f"w{WORKLOAD_ID}_L{Lf}_b{beta:g}")
         if row is None:
-            raise RuntimeError(f"no critical mass stored for L={L} beta={beta}")
+            raise RuntimeError(f"no critical mass stored for L={Lf} beta={beta}")
         digest_ok = rank == 0 and row["theta_digest"] == inputs.field_digest(theta)
-        seed = inputs.workload_seed(WORKLOAD_ID + 100 * rank, L, beta)
-        chis = [inputs.gaussian_source(L, L, seed=seed, index=i) for i in range(len(DMS))]
-        fields.append(dict(beta=beta, U=U, m_c=row["m_crit"], digest_ok=digest_ok, chis=chis))
+        seed = inputs.workload_seed(wid, Lf, beta)
+        chis = [inputs.gaussian_source(Lf, Lf, seed=seed, index=i) for i in range(len(DMS))]
+        fields.append(dict(beta=beta, L=Lf, U=U, m_c=row["m_crit"], m_c_from=row.get("m_crit_from"),
+                           digest_ok=digest_ok, chis=chis))
     return fields
+
+
+def device_fields(fields):
+    import torch
+    out = []
+    for f in fields:
+        Lf = f["L"]
+        out.append(dict(beta=f["beta"], L=Lf, m_c=f["m_c"], U_dev=torch.from_numpy(f["U"]).cuda(),
+                        chi_dev=[torch.from_numpy(c).cuda() for c in f["chis"]],
+                        psi_dev=[torch.empty((Lf * Lf, 2), dtype=torch.complex128, device="cuda") for _ in DMS],
+                        U_host=torch.from_numpy(f["U"]).pin_memory(),
+                        chi_host=[torch.from_numpy(c).pin_memory() for c in f["chis"]]))
+    return out
 
 
 class ClockSampler:
@@ -136,7 +153,8 @@ def _one_field(f, precision, stats_out, host_io, contexts):
         U = f["U_host"].to("cuda", non_blocking=True)
     else:
         U = f["U_dev"]
-    ctx = mg.Context.setup(U, f["m_c"] + DMS[0], (L, L), mg_params(precision))
+    Lf = f.get("L", L)
+    ctx = mg.Context.setup(U, f["m_c"] + DMS[0], (Lf, Lf), mg_params(precision))
     contexts.append(ctx)
 
     def solve(c, i, dm):
@@ -241,6 +259,39 @@ def timed_steps(fields_dev, precision, steps, warmup, flush, dist_ctx, host_io=N
     barrier(dist_ctx)
     total_ms = max_over_ranks(total_ms, dist_ctx)
     return dict(ms=total_ms, solves=solves, stats=stats, launches=launches, clocks=clocks)
+
+
+LARGE_L = 1024
+
+
+def config1_large(flush, precisions=(1, 0)):
+    """The 1024^2 points of the three-level sweep (beta in {3, 6, 10}, m - m_c in {0.005, 0.02,
+    0.1}): one step (3 setups + 9 solves, betas and masses concurrently as in the headline) after
+    one untimed step, per precision. m_c is the 256^2 calibration of the same beta (the 1024^2
+    spectrum is beyond the oracle's Arnoldi scan)."""
+    import torch
+    fields = make_inputs(0, LARGE_L)
+    fdev = device_fields(fields)
+    out = {"lattice": f"{LARGE_L}x{LARGE_L}", "m_c_from": [f["m_c_from"] for f in fields],
+           "gauge_digest_matches_table": all(f["digest_ok"] for f in fields)}
+    stream = torch.cuda.current_stream()
+    for prec in precisions:
+        run_step(fdev, prec)
+        flush.zero_()
+        stats = []
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        n = run_step(fdev, prec, stats_out=stats)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        out["mixed" if prec == 1 else "fp64"] = dict(
+            value=n / (ms * 1e-3), unit="solves/s (incl. setup)", ms_per_step=ms, solves=n,
+            iters=[s["iters"] for s in stats], converged=all(s["converged"] for s in stats),
+            worst_true_rel_residual=max(s["true_rel_residual"] for s in stats),
+            setup_s=sorted({round(s["setup_s"], 4) for s in stats}))
+    return out
 
 
 def dslash_roofline(precision: int, L_big: int = 4096, iters: int = 20):
@@ -744,6 +795,7 @@ def main():
     ap.add_argument("--serial", action="store_true", help="run the betas of a step one after another")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the 1024^2 sweep points")
     ap.add_argument("--only", default=None, choices=["dslash-f32", "dslash-f64", "dslash4-f32", "dslash4-f64", "solve", "vcycle",
                                                       "transfer", "coarse-tc", "coarse-tc4", "su3", "su3-prof",
                                                       "su3-batch-prof", "mixed-sizes"],
@@ -770,14 +822,7 @@ def main():
     torch.cuda.set_device(local)
     mg.load()
     fields = make_inputs(rank)
-    fields_dev = []
-    for f in fields:
-        fd = dict(beta=f["beta"], m_c=f["m_c"], U_dev=torch.from_numpy(f["U"]).cuda(),
-                  chi_dev=[torch.from_numpy(c).cuda() for c in f["chis"]],
-                  psi_dev=[torch.empty((L * L, 2), dtype=torch.complex128, device="cuda") for _ in DMS],
-                  U_host=torch.from_numpy(f["U"]).pin_memory(),
-                  chi_host=[torch.from_numpy(c).pin_memory() for c in f["chis"]])
-        fields_dev.append(fd)
+    fields_dev = device_fields(fields)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     sampler = ClockSampler(local)
@@ -811,6 +856,7 @@ def main():
     su3 = su3_workload() if world_of(d) == 1 or rank == 0 else None
     mix = mixed_sizes() if world_of(d) == 1 or rank == 0 else None
     cr = coarsest_roofline(fields_dev)
+    large = config1_large(flush) if (world_of(d) == 1 or rank == 0) and not args.no_large else None
 
     cpu = None
     if rank == 0 and world_of(d) == 1 and not args.no_cpu:
@@ -845,6 +891,7 @@ def main():
         "cpu_baseline": cpu,
         "su3_4d": su3,
         "mixed_sizes": mix,
+        "config1_1024": large,
     }
     print(json.dumps(line), flush=True)
 

@@ -328,6 +328,74 @@ int mg_smooth_fine_noalloc(const mg_geom *g, const void *U, double m, const void
  * FP64 context or N != 8; d = 4 with N != 48). */
 int mg_coarse_apply_mrhs(mg_ctx *ctx, int level, int nrhs, const void *in, void *out, int tensor_cores);
 
+/* ---- learned near-null setup --------------------------------------------------------
+ * The paper finds the near-null vectors by relaxation on the homogeneous problem
+ * (Eq. relax) refined by the adaptive passes, and notes that this setup is the cost to be
+ * amortised. The learned setup predicts them instead with a gauge-covariant network and
+ * keeps the plain setup as its fallback and its judge (the measured MG convergence rate).
+ *
+ * Network: 4 parallel-transport convolution layers, cin -> channels -> channels ->
+ * channels -> nv (each channel a 2-spin field); per site x and channel-spin index
+ * l = 2 c + s,
+ *     a_x = sum_dir W_dir T_dir(h)_x,  dir = self, +0, -0, +1, -1,
+ *     T_self h_x = h_x,  T_{+mu} h_x = U_x^mu h_{x+mu},  T_{-mu} h_x = conj(U_{x-mu}^mu) h_{x-mu};
+ * hidden layers h = a / sqrt(1 + |a_c|^2) per channel c (both spins), the last layer is
+ * linear and its channel k is the predicted vector v_k. The weights W_dir[l_out][l_in]
+ * (complex, FP32) act on channel and spin only, so the network commutes with gauge
+ * transformations. Activations are stored in bfloat16, arithmetic is FP32. The input is
+ * cin complex Gaussian fields: channel c, dof (x, s) is the setup's Philox4x32-10 draw
+ * with key noise_seed, counter (2 x + s, 0, c, 0x4E4E), Box-Muller as in mg_setup.
+ * Loss (rotation invariant, per block b of the blocking, rows (site in block, spin)):
+ *     L_b = sum_k |(1 - Q_b Q_b^dagger) V_b e_k|^2,  loss = mean_b L_b / nv in [0, 1],
+ * Q_b an orthonormal basis of the predicted vectors on b, V_b the target block-orthonormal
+ * prolongator columns (mg_get_prolongator of a plain setup).
+ * Weights are exchanged as complex64, layers packed [l][5][2 co][2 ci]. */
+typedef struct mg_nullnet mg_nullnet;
+
+/* New network with weights drawn from a seeded Gaussian (variance 1 / (10 ci) per
+ * component). cin, channels in [1, 16], nv in [1, 8]. */
+int mg_nullnet_create(mg_nullnet **net, int cin, int channels, int nv, uint64_t seed);
+void mg_nullnet_destroy(mg_nullnet *net);
+long long mg_nullnet_weight_count(const mg_nullnet *net); /* complex weights, all layers */
+int mg_nullnet_get_weights(mg_nullnet *net, void *host_out);  /* complex64 [count] */
+int mg_nullnet_set_weights(mg_nullnet *net, const void *host_in); /* resets the Adam state */
+
+/* Forward pass on nfields fields of geometry g (d = 2, Nc = 1): U device complex128
+ * [f][x][mu]; noise_seeds host [nfields]; out device complex64 [f][x][2 nv] (channel k,
+ * spin s at 2 k + s). Synchronous. */
+int mg_nullnet_forward(mg_nullnet *net, const mg_geom *g, int nfields, const void *U, const uint64_t *noise_seeds,
+                       void *out, void *stream);
+
+/* Loss and its conjugate cogradient dloss/dW^* (host complex64 [count], may be NULL) for
+ * nfields fields against targets (device complex128 [f][k][x][s], block-orthonormal on the
+ * blocks block[0] x block[1], at most 16 sites). The real-parameter gradient is 2 (Re, Im). */
+int mg_nullnet_gradient(mg_nullnet *net, const mg_geom *g, int nfields, const void *U, const uint64_t *noise_seeds,
+                        const void *target, const int *block, double *loss, void *grad, void *stream);
+
+/* `steps` Adam steps (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on batches of `batch`
+ * fields taken cyclically from the nfields (U, target as for mg_nullnet_gradient), each
+ * draw with fresh noise (seed + (draw << 20)). losses: host [steps] or NULL. */
+int mg_nullnet_train(mg_nullnet *net, const mg_geom *g, int nfields, const void *U, const void *target,
+                     const int *block, int steps, int batch, double lr, uint64_t seed, double *losses,
+                     void *stream);
+
+/* Setup with learned near-null vectors (d = 2): the network predicts the level-0 vectors
+ * from noise_seed (it needs nv == p->Nv[0]), nu_refine MR iterations on D v = 0 refine
+ * them (0: none), then block Gram-Schmidt and the Galerkin operator build level 1; deeper
+ * levels get the plain adaptive setup. The judge: the asymptotic convergence factor of the
+ * V-cycle iteration e <- (1 - V D) e on a random vector over rate_steps steps (as
+ * mg_convergence_rate). If it exceeds max_rate, the plain adaptive setup replaces the
+ * learned one (the fallback) and *used_learned is 0. rate (may be NULL): the factor of the
+ * hierarchy kept. stats of later solves report the whole call's time as setup_s. */
+int mg_setup_learned(mg_ctx **ctx, const mg_geom *g, const void *U, double m, const mg_params *p, mg_nullnet *net,
+                     uint64_t noise_seed, int nu_refine, double max_rate, int rate_steps, int *used_learned,
+                     double *rate, void *stream);
+
+/* Asymptotic convergence factor of the multigrid iteration: e_0 a Philox Gaussian vector
+ * (seed), e_{i+1} = e_i - V(D e_i) with the context's V-cycle, rate = (|e_steps| / |e_1|)^(1
+ * / (steps - 1)) (steps >= 2). d = 2. */
+int mg_convergence_rate(mg_ctx *ctx, int steps, uint64_t seed, double *rate);
+
 /* Launch shapes picked by the library's autotuner so far (the tensor-core coarse apply
  * times its six tile shapes -- warps per CTA x vector tiles per warp -- on first use for
  * each lattice and vector count, and keeps the fastest; all shapes give bitwise the same

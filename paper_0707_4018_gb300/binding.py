@@ -80,6 +80,17 @@ def load():
         "mg_save_setup": (I, [ctxp, ctypes.c_char_p]),
         "mg_load_setup": (I, [P(ctxp), ctypes.c_char_p, VP, VP]),
         "mg_context_info": (I, [ctxp, P(mg_geom), P(mg_params), P(D)]),
+        "mg_nullnet_create": (I, [P(ctxp), I, I, I, ctypes.c_uint64]),
+        "mg_nullnet_destroy": (None, [ctxp]),
+        "mg_nullnet_weight_count": (ctypes.c_longlong, [ctxp]),
+        "mg_nullnet_get_weights": (I, [ctxp, VP]),
+        "mg_nullnet_set_weights": (I, [ctxp, VP]),
+        "mg_nullnet_forward": (I, [ctxp, P(mg_geom), I, VP, P(ctypes.c_uint64), VP, VP]),
+        "mg_nullnet_gradient": (I, [ctxp, P(mg_geom), I, VP, P(ctypes.c_uint64), VP, P(I), P(D), VP, VP]),
+        "mg_nullnet_train": (I, [ctxp, P(mg_geom), I, VP, VP, P(I), I, I, D, ctypes.c_uint64, P(D), VP]),
+        "mg_setup_learned": (I, [P(ctxp), P(mg_geom), VP, D, P(mg_params), ctxp, ctypes.c_uint64, I, D, I, P(I),
+                                 P(D), VP]),
+        "mg_convergence_rate": (I, [ctxp, I, ctypes.c_uint64, P(D)]),
         "mg_solve_batch": (I, [ctxp, I, VP, VP, P(D), D, P(mg_stats)]),
         "mg_coarse_apply_mrhs": (I, [ctxp, I, I, VP, VP, I]),
         "mg_update_mass": (I, [ctxp, D]),
@@ -118,7 +129,9 @@ def exported_symbols():
             "mg_get_null_vectors", "mg_get_prolongator", "mg_get_coarse_op", "mg_level_size", "mg_kernel_launches",
             "mg_smooth_fine_noalloc", "mg_coarsest_solve", "mg_selftest_barrier", "mg_solve_batch",
             "mg_coarse_apply_mrhs", "mg_autotune_report", "mg_clone", "mg_setup_batch", "mg_save_setup",
-            "mg_load_setup", "mg_context_info"]
+            "mg_load_setup", "mg_context_info", "mg_nullnet_create", "mg_nullnet_destroy", "mg_nullnet_weight_count",
+            "mg_nullnet_get_weights", "mg_nullnet_set_weights", "mg_nullnet_forward", "mg_nullnet_gradient",
+            "mg_nullnet_train", "mg_setup_learned", "mg_convergence_rate"]
 
 
 def autotune_report() -> dict:
@@ -293,6 +306,29 @@ class Context:
         ctx.mass = float(m.value)
         return ctx
 
+    @classmethod
+    def setup_learned(cls, U: torch.Tensor, m: float, dims, params, net: "NullNet", noise_seed: int = 1,
+                      nu_refine: int = 0, max_rate: float = 1.0, rate_steps: int = 4, stream=None):
+        """mg_setup_learned: a hierarchy whose level-0 vectors the network predicts (optionally refined
+        by nu_refine MR iterations), judged by the measured convergence rate, with the plain setup as
+        fallback. Returns (context, used_learned, rate)."""
+        g = make_geom(dims)
+        V = int(dims[0]) * int(dims[1])
+        h = ctypes.c_void_p()
+        used = ctypes.c_int(0)
+        rate = ctypes.c_double(0.0)
+        s = _stream(stream)
+        _check(load().mg_setup_learned(ctypes.byref(h), ctypes.byref(g), _ptr(U, torch.complex128, 2 * V), float(m),
+                                       ctypes.byref(params), net._need(), int(noise_seed), int(nu_refine),
+                                       float(max_rate), int(rate_steps), ctypes.byref(used), ctypes.byref(rate), s))
+        return cls(h, dims, params, s), bool(used.value), float(rate.value)
+
+    def convergence_rate(self, steps: int = 4, seed: int = 1) -> float:
+        """mg_convergence_rate: asymptotic factor of e <- e - V(D e)."""
+        r = ctypes.c_double(0.0)
+        _check(load().mg_convergence_rate(self._need(), int(steps), int(seed), ctypes.byref(r)))
+        return float(r.value)
+
     def save(self, path: str):
         """mg_save_setup: write this context's near-null vectors (and what identifies them) to path."""
         _check(load().mg_save_setup(self._need(), os.fsencode(path)))
@@ -441,3 +477,88 @@ class Context:
         out = torch.empty((n, 9 if self.four else 5, k, k), dtype=torch.complex128, device="cuda")
         _check(load().mg_get_coarse_op(self._need(), level, _ptr(out)))
         return out
+
+
+class NullNet:
+    """The learned near-null network (wraps mg_nullnet*): 4 parallel-transport layers
+    cin -> channels -> channels -> channels -> nv, complex FP32 weights, bf16 activations."""
+
+    def __init__(self, cin: int = 8, channels: int = 16, nv: int = 8, seed: int = 20070704):
+        h = ctypes.c_void_p()
+        _check(load().mg_nullnet_create(ctypes.byref(h), int(cin), int(channels), int(nv), int(seed)))
+        self._h = h
+        self.cin, self.channels, self.nv = cin, channels, nv
+
+    def _need(self):
+        if not self._h:
+            raise RuntimeError("network is destroyed")
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().mg_nullnet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def weight_count(self) -> int:
+        return int(load().mg_nullnet_weight_count(self._need()))
+
+    def get_weights(self):
+        import numpy as np
+        out = np.empty(self.weight_count(), dtype=np.complex64)
+        _check(load().mg_nullnet_get_weights(self._need(), out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def set_weights(self, w):
+        import numpy as np
+        w = np.ascontiguousarray(w, dtype=np.complex64)
+        if w.size != self.weight_count():
+            raise ValueError("wrong number of weights")
+        _check(load().mg_nullnet_set_weights(self._need(), w.ctypes.data_as(ctypes.c_void_p)))
+
+    @staticmethod
+    def _seeds(seeds):
+        return (ctypes.c_uint64 * len(seeds))(*[int(x) for x in seeds])
+
+    def forward(self, U: torch.Tensor, dims, seeds, stream=None) -> torch.Tensor:
+        """Network output complex64 [f][x][2 nv] for the fields U (complex128 [f][x][2])."""
+        nf = len(seeds)
+        V = int(dims[0]) * int(dims[1])
+        g = make_geom(dims)
+        out = torch.empty((nf, V, 2 * self.nv), dtype=torch.complex64, device=U.device)
+        _check(load().mg_nullnet_forward(self._need(), ctypes.byref(g), nf, _ptr(U, torch.complex128, nf * 2 * V),
+                                         self._seeds(seeds), _ptr(out), _stream(stream)))
+        return out
+
+    def gradient(self, U: torch.Tensor, dims, seeds, target: torch.Tensor, block, stream=None):
+        """(loss, dloss/dW^* as complex64 [count]) against target complex128 [f][k][x][2]."""
+        import numpy as np
+        nf = len(seeds)
+        V = int(dims[0]) * int(dims[1])
+        g = make_geom(dims)
+        blk = (ctypes.c_int * 2)(int(block[0]), int(block[1]))
+        loss = ctypes.c_double(0.0)
+        grad = np.empty(self.weight_count(), dtype=np.complex64)
+        _check(load().mg_nullnet_gradient(self._need(), ctypes.byref(g), nf, _ptr(U, torch.complex128, nf * 2 * V),
+                                          self._seeds(seeds), _ptr(target, torch.complex128, nf * self.nv * 2 * V),
+                                          blk, ctypes.byref(loss), grad.ctypes.data_as(ctypes.c_void_p),
+                                          _stream(stream)))
+        return float(loss.value), grad
+
+    def train(self, U: torch.Tensor, dims, target: torch.Tensor, block, steps: int, batch: int, lr: float,
+              seed: int = 1, stream=None):
+        """Adam steps on batches of fields; returns the loss of every step."""
+        nf = int(U.shape[0])
+        V = int(dims[0]) * int(dims[1])
+        g = make_geom(dims)
+        blk = (ctypes.c_int * 2)(int(block[0]), int(block[1]))
+        losses = (ctypes.c_double * max(1, steps))()
+        _check(load().mg_nullnet_train(self._need(), ctypes.byref(g), nf, _ptr(U, torch.complex128, nf * 2 * V),
+                                       _ptr(target, torch.complex128, nf * self.nv * 2 * V), blk, int(steps),
+                                       int(batch), float(lr), int(seed), losses, _stream(stream)))
+        return [losses[i] for i in range(steps)]

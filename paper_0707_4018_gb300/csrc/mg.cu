@@ -23,6 +23,7 @@
 
 #include "kernels.h"
 #include "mg4d.h"
+#include "nullnet.h"
 
 namespace mg {
 
@@ -1085,6 +1086,35 @@ static double seconds_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
+// Asymptotic convergence factor of the stationary multigrid iteration on the homogeneous
+// problem, e <- e - V(D e) (the error propagator the adaptive passes apply): from a Philox
+// Gaussian e_0, (|e_steps| / |e_1|)^(1 / (steps - 1)). Uses the level-0 setup temporaries.
+static double convergence_rate(mg_ctx &c, int steps, uint64_t seed) {
+  Level &F = c.lv[0];
+  const long long n = F.n;
+  if ((long long)F.tA.n < 2 * n) fail(MG_ERR_STATE, "rate measurement needs Nv >= 2 on level 0");
+  Cx<double> *e = F.tA.p, *t = F.tB.p, *z = F.tA.p + n;
+  double *dots = c.scal.p + kSlotOuter;
+  auto norm = [&](const Cx<double> *v) {
+    launch_norm2<double>(v, n, dots, c.ws, c.s);
+    MG_CUDA(cudaMemcpyAsync(c.host, dots, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+    MG_CUDA(cudaStreamSynchronize(c.s));
+    return std::sqrt(c.host[0]);
+  };
+  launch_gaussian(e, n, seed, 0, 0x5241, c.s);
+  double n1 = 0.0, nl = 0.0;
+  for (int i = 1; i <= steps; ++i) {
+    apply_op<double>(c, 0, e, t);
+    precondition(c, t, z);
+    launch_xmy<double>(e, z, n, c.s);  // z = e - V(D e)
+    launch_copy<double>(z, e, n, c.s);
+    if (i == 1) n1 = norm(e);
+    if (i == steps) nl = norm(e);
+  }
+  if (!(n1 > 0.0) || !std::isfinite(nl)) fail(MG_ERR_NAN, "rate measurement: degenerate error vector");
+  return std::pow(nl / n1, 1.0 / (steps - 1));
+}
+
 // A context at mass m on links U: the full adaptive setup, or, with saved vectors
 // (`vectors[l]`: the host copy of level l's near-null vectors), the rebuild of every
 // level from them (block Gram-Schmidt, Galerkin operators, coarsest preparation) with no
@@ -1503,6 +1533,78 @@ int mg_save_setup(mg_ctx *c, const char *path) {
     for (const auto &v : vecs) ok = ok && std::fwrite(v.data(), sizeof(Cx<double>), v.size(), f) == v.size();
     ok = (std::fclose(f) == 0) && ok;
     if (!ok) fail(MG_ERR_UNSUPPORTED, std::string("writing ") + path + " failed");
+  });
+}
+
+int mg_convergence_rate(mg_ctx *c, int steps, uint64_t seed, double *rate) {
+  return guarded([&] {
+    need_ctx(c);
+    if (c->e4) fail(MG_ERR_UNSUPPORTED, "the convergence-rate measurement is built for d = 2");
+    if (steps < 2) fail(MG_ERR_INVALID_ARG, "steps must be >= 2");
+    check_fresh(*c);
+    const double r = convergence_rate(*c, steps, seed);
+    if (rate) *rate = r;
+  });
+}
+
+int mg_setup_learned(mg_ctx **ctx, const mg_geom *g, const void *U, double m, const mg_params *p, mg_nullnet *net,
+                     uint64_t noise_seed, int nu_refine, double max_rate, int rate_steps, int *used_learned,
+                     double *rate, void *stream) {
+  return guarded([&] {
+    if (!ctx) fail(MG_ERR_INVALID_ARG, "null context out-pointer");
+    *ctx = nullptr;
+    need_ptr(U);
+    need_ptr(net);
+    if (!g || g->d != 2) fail(MG_ERR_UNSUPPORTED, "the learned setup is built for d = 2");
+    if (!p) fail(MG_ERR_INVALID_ARG, "null parameters");
+    if (nullnet_nv(*net) != p->Nv[0]) fail(MG_ERR_INVALID_ARG, "the network predicts nv != Nv[0] vectors");
+    if (nu_refine < 0 || rate_steps < 2) fail(MG_ERR_INVALID_ARG, "need nu_refine >= 0 and rate_steps >= 2");
+    const auto t0 = std::chrono::steady_clock::now();
+    auto c = create(g, m, p, stream);
+    MG_CUDA(cudaMemcpyAsync(c->U64.p, U, c->U64.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, c->s));
+    const bool f32 = c->p.precision == MG_FP32;
+    if (f32) launch_convert<float, double>(c->U64.p, c->U32.p, c->U64.n, c->s);
+    Level &F = c->lv[0];
+    nullnet_predict(*net, *g, c->U64.p, noise_seed, F.nullv.p, c->s);
+    if (nu_refine > 0) {
+      // the predicted vectors start the relaxation of Eq. relax in place of random ones
+      const int keep = c->p.nu_setup;
+      c->p.nu_setup = nu_refine;
+      if (f32)
+        relax_and_adapt<float>(*c, 0, 1);
+      else
+        relax_and_adapt<double>(*c, 0, 1);
+      c->p.nu_setup = keep;
+    }
+    build_level(*c, 0);
+    if (f32) {
+      launch_convert<float, double>(F.V64.p, F.V32.p, F.V64.n, c->s);
+      refresh_y32(*c, 1);
+    }
+    if (c->p.levels > 2)
+      setup_level(*c, 1, true);
+    else
+      prepare_coarsest(*c);
+    F.stale = false;
+    make_fp32_copies(*c);
+    collect_coarsest(*c);
+    double r = convergence_rate(*c, rate_steps, noise_seed ^ 0x5241544552ULL);
+    int used = 1;
+    if (!(r <= max_rate)) {
+      // the judge rejects the learned vectors: the plain adaptive setup takes over
+      MG_CUDA(cudaStreamSynchronize(c->s));
+      drop_graphs(*c);
+      setup_level(*c, 0, true);
+      make_fp32_copies(*c);
+      collect_coarsest(*c);
+      r = convergence_rate(*c, rate_steps, noise_seed ^ 0x5241544552ULL);
+      used = 0;
+    }
+    MG_CUDA(cudaStreamSynchronize(c->s));
+    c->setup_s = seconds_since(t0);
+    if (used_learned) *used_learned = used;
+    if (rate) *rate = r;
+    *ctx = c.release();
   });
 }
 
