@@ -380,9 +380,11 @@ int mg_nullnet_train(mg_nullnet *net, const mg_geom *g, int nfields, const void 
                      void *stream);
 
 /* Setup with learned near-null vectors (d = 2): the network predicts the level-0 vectors
- * from noise_seed (it needs nv == p->Nv[0]), nu_refine MR iterations on D v = 0 refine
- * them (0: none), then block Gram-Schmidt and the Galerkin operator build level 1; deeper
- * levels get the plain adaptive setup. The judge: the asymptotic convergence factor of the
+ * from noise_seed (it needs nv == p->Nv[0]) in place of the random start and relaxation of
+ * the first pass (Eq. relax); nu_refine MR iterations on D v = 0 refine them (0: none), then
+ * block Gram-Schmidt and the Galerkin operator build level 1. Passes 2..p->n_pass follow as
+ * in the plain setup (p->n_pass = 1: none), and deeper levels get the plain adaptive setup
+ * after each pass. The judge: the asymptotic convergence factor of the
  * V-cycle iteration e <- (1 - V D) e on a random vector over rate_steps steps (as
  * mg_convergence_rate). If it exceeds max_rate, the plain adaptive setup replaces the
  * learned one (the fallback) and *used_learned is 0. rate (may be NULL): the factor of the

@@ -469,14 +469,19 @@ constexpr int kSmMaxDofs = 64;
 constexpr int kSmMaxRestart = 16;
 constexpr int kSmSlots = 2 * kSmMaxRestart + 4;  // |w|^2, <w, r>, then 2 per basis vector
 
+// RS: precision in which A M is stored and applied (double; float in mixed-precision cycles,
+// where the Krylov vectors, Gram-Schmidt and updates stay FP64); rpub / ypub, the copies of r
+// and y that neighbouring CTAs read for the stencil, are kept in RS too.
+template <typename RS>
 struct Cg3Args {
-  const Cx<double> *Yt;    // A M, internal layout [j][dir][col][row], N = 8
+  const Cx<RS> *Yt;        // A M, internal layout [j][dir][col][row], N = 8
   const Cx<double> *Minv;  // [j][col][row]
   int L0, L1;
   long long nsites;
   int spc;  // sites per CTA
   const Cx<double> *b;
-  Cx<double> *x, *rpub, *ypub;
+  Cx<double> *x;
+  Cx<RS> *rpub, *ypub;
   double *partials;
   unsigned int *bar;
   double tol;
@@ -486,7 +491,8 @@ struct Cg3Args {
   double *out_rel;
 };
 
-__device__ __forceinline__ void grid_sync3(const Cg3Args &a, bool &ok) {
+template <typename A>
+__device__ __forceinline__ void grid_sync3(const A &a, bool &ok) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -522,7 +528,8 @@ __device__ __forceinline__ void grid_sync3(const Cg3Args &a, bool &ok) {
 // each lane loads all its partials of them at once (lane l adds CTAs l, l + 32, ... in
 // that order, then the shuffle tree: a fixed order in every CTA)
 constexpr int kMaxGrid3 = 256;
-__device__ __forceinline__ void grid_sum3(const Cg3Args &a, int nv, const double *cpart, double *sres, bool &ok) {
+template <typename A>
+__device__ __forceinline__ void grid_sum3(const A &a, int nv, const double *cpart, double *sres, bool &ok) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int G = (int)gridDim.x;
   __syncthreads();
@@ -555,10 +562,20 @@ __device__ __forceinline__ void grid_sum3(const Cg3Args &a, int nv, const double
 
 // out[d] = (A M v)_d for the CTA's rows, v read from global (published) memory;
 // 4 threads per row, 10 of the 40 (dir, col) terms each, combined by shuffles
-__device__ __forceinline__ void stencil_rows(const Cg3Args &a, const Cx<double> *Ys, const Cx<double> *v,
+__device__ __forceinline__ Cx<double> ldcg_cx(const Cx<double> *p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+  return mk(v.x, v.y);
+}
+__device__ __forceinline__ Cx<float> ldcg_cx(const Cx<float> *p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+  return mk(v.x, v.y);
+}
+
+template <typename RS>
+__device__ __forceinline__ void stencil_rows(const Cg3Args<RS> &a, const Cx<RS> *Ys, const Cx<RS> *v,
                                              long long site0, int nd, Cx<double> *outs) {
   const int t = threadIdx.x, d = t >> 2, q = t & 3;
-  Cx<double> acc = mk(0.0, 0.0);
+  Cx<RS> acc = mk<RS>(0, 0);
   if (d < nd) {
     const long long j = site0 + (d >> 3);
     const int x1 = (int)(j / a.L0), x0 = (int)(j - (long long)x1 * a.L0);
@@ -572,8 +589,7 @@ __device__ __forceinline__ void stencil_rows(const Cg3Args &a, const Cx<double> 
 #pragma unroll
     for (int u = 0; u < 10; ++u) {
       const int term = q * 10 + u, dir = term >> 3, col = term & 7;
-      const double2 vv = __ldcg(reinterpret_cast<const double2 *>(v + src[dir] * 8 + col));
-      cmac(acc, Ys[(d * 5 + dir) * 8 + col], mk(vv.x, vv.y));
+      cmac(acc, Ys[(d * 5 + dir) * 8 + col], ldcg_cx(v + src[dir] * 8 + col));
     }
   }
 #pragma unroll
@@ -581,7 +597,7 @@ __device__ __forceinline__ void stencil_rows(const Cg3Args &a, const Cx<double> 
     acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
     acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
   }
-  if (d < nd && q == 0) outs[d] = acc;
+  if (d < nd && q == 0) outs[d] = cvt<double, RS>(acc);
 }
 
 // CTA-local sums: slot 0 |w|^2, slots 1, 2 <w, r>, slots 3 + 2j, 4 + 2j <W_j, w> (j < k);
@@ -623,10 +639,11 @@ __device__ __forceinline__ void cta_dots(int k, int nd, const Cx<double> *Ws, co
 
 // two CTAs per SM (at most 128 registers, about 86 KB of shared memory each), so that the
 // coarsest solves of two contexts running on different streams can share the GPU
-__global__ void __launch_bounds__(256, 2) coarsest_gcr_smem_kernel(Cg3Args a) {
+template <typename RS>
+__global__ void __launch_bounds__(256, 2) coarsest_gcr_smem_kernel(Cg3Args<RS> a) {
   extern __shared__ double sm3[];
-  Cx<double> *Ys = reinterpret_cast<Cx<double> *>(sm3);  // [64 rows][5][8]
-  Cx<double> *Ms = Ys + kSmMaxDofs * 40;                  // [8 sites][64]
+  Cx<RS> *Ys = reinterpret_cast<Cx<RS> *>(sm3);                         // [64 rows][5][8]
+  Cx<double> *Ms = reinterpret_cast<Cx<double> *>(Ys + kSmMaxDofs * 40);  // [8 sites][64]
   Cx<double> *bs = Ms + 8 * 64;
   Cx<double> *rs = bs + kSmMaxDofs;
   Cx<double> *ys = rs + kSmMaxDofs;
@@ -654,7 +671,7 @@ __global__ void __launch_bounds__(256, 2) coarsest_gcr_smem_kernel(Cg3Args a) {
     bs[d] = bd;
     rs[d] = bd;
     ys[d] = mk(0.0, 0.0);
-    a.rpub[dof0 + d] = bd;
+    a.rpub[dof0 + d] = cvt<RS, double>(bd);
   }
   __syncthreads();
   // |b|^2
@@ -728,7 +745,7 @@ __global__ void __launch_bounds__(256, 2) coarsest_gcr_smem_kernel(Cg3Args a) {
         Cx<double> rd = rs[d];
         cmac(rd, mk(-alpha.re, -alpha.im), w);
         rs[d] = rd;
-        a.rpub[dof0 + d] = rd;
+        a.rpub[dof0 + d] = cvt<RS, double>(rd);
       }
       rn2 = fmax(rn2 - norm2(alpha), 0.0);
       ++it;
@@ -738,7 +755,7 @@ __global__ void __launch_bounds__(256, 2) coarsest_gcr_smem_kernel(Cg3Args a) {
       if (rn2 <= tol2 || breakdown) break;
     }
     // true residual r = b - (A M) y with the published y
-    for (int d = tid; d < nd; d += blockDim.x) a.ypub[dof0 + d] = ys[d];
+    for (int d = tid; d < nd; d += blockDim.x) a.ypub[dof0 + d] = cvt<RS, double>(ys[d]);
     __threadfence();
     grid_sync3(a, ok);
     if (!ok) return;
@@ -747,7 +764,7 @@ __global__ void __launch_bounds__(256, 2) coarsest_gcr_smem_kernel(Cg3Args a) {
     for (int d = tid; d < nd; d += blockDim.x) {
       const Cx<double> rd = bs[d] - rs[d];
       rs[d] = rd;
-      a.rpub[dof0 + d] = rd;
+      a.rpub[dof0 + d] = cvt<RS, double>(rd);
     }
     __syncthreads();
     if (tid < 32) {
@@ -785,11 +802,11 @@ bool coarsest_smem_fits(Geo2 g, int N, int restart, int sms) {
   return spc * 8 <= kSmMaxDofs;
 }
 
-void launch_coarsest_gcr_smem(const Cx<double> *Yt, const Cx<double> *Minv, Geo2 g, const Cx<double> *b,
-                              Cx<double> *x, Cx<double> *rpub, Cx<double> *ypub, double *partials, unsigned int *bar,
-                              double tol, int restart, int max_iter, int *out, double *out_rel, int sms,
-                              cudaStream_t s) {
-  Cg3Args a;
+template <typename RS>
+static void coarsest_smem_go(const Cx<RS> *Yt, const Cx<double> *Minv, Geo2 g, const Cx<double> *b, Cx<double> *x,
+                             Cx<double> *rpub, Cx<double> *ypub, double *partials, unsigned int *bar, double tol,
+                             int restart, int max_iter, int *out, double *out_rel, int sms, cudaStream_t s) {
+  Cg3Args<RS> a;
   a.Yt = Yt;
   a.Minv = Minv;
   a.L0 = g.L0;
@@ -799,8 +816,9 @@ void launch_coarsest_gcr_smem(const Cx<double> *Yt, const Cx<double> *Minv, Geo2
   const int grid = (int)((g.nsites + a.spc - 1) / a.spc);
   a.b = b;
   a.x = x;
-  a.rpub = rpub;
-  a.ypub = ypub;
+  // the published copies fit in the FP64 buffers whatever RS is
+  a.rpub = reinterpret_cast<Cx<RS> *>(rpub);
+  a.ypub = reinterpret_cast<Cx<RS> *>(ypub);
   a.partials = partials;
   a.bar = bar;
   a.tol = tol;
@@ -810,10 +828,10 @@ void launch_coarsest_gcr_smem(const Cx<double> *Yt, const Cx<double> *Minv, Geo2
   a.out = out;
   a.out_rel = out_rel;
   if (grid > kMaxGrid3) fail(MG_ERR_UNSUPPORTED, "coarsest solve: more than 256 CTAs");
-  const size_t smem = (size_t)(kSmMaxDofs * 40 + 8 * 64 + 3 * kSmMaxDofs + 2 * kSmMaxRestart * kSmMaxDofs) *
-                          sizeof(Cx<double>) +
+  const size_t smem = (size_t)kSmMaxDofs * 40 * sizeof(Cx<RS>) +
+                      (size_t)(8 * 64 + 3 * kSmMaxDofs + 2 * kSmMaxRestart * kSmMaxDofs) * sizeof(Cx<double>) +
                       (size_t)2 * kSmSlots * sizeof(double);
-  const void *fn = (const void *)coarsest_gcr_smem_kernel;
+  const void *fn = (const void *)coarsest_gcr_smem_kernel<RS>;
   MG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessorWithFlags(&per_sm, fn, 256, smem, 0));
@@ -822,6 +840,18 @@ void launch_coarsest_gcr_smem(const Cx<double> *Yt, const Cx<double> *Minv, Geo2
   void *args[] = {&a};
   MG_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, smem, s));
   MG_LAUNCHED();
+}
+
+void launch_coarsest_gcr_smem(const Cx<double> *Yt, const Cx<float> *Yt32, const Cx<double> *Minv, Geo2 g,
+                              const Cx<double> *b, Cx<double> *x, Cx<double> *rpub, Cx<double> *ypub,
+                              double *partials, unsigned int *bar, double tol, int restart, int max_iter, int *out,
+                              double *out_rel, int sms, cudaStream_t s) {
+  if (Yt32 != nullptr)
+    coarsest_smem_go<float>(Yt32, Minv, g, b, x, rpub, ypub, partials, bar, tol, restart, max_iter, out, out_rel, sms,
+                            s);
+  else
+    coarsest_smem_go<double>(Yt, Minv, g, b, x, rpub, ypub, partials, bar, tol, restart, max_iter, out, out_rel, sms,
+                             s);
 }
 
 }  // namespace mg

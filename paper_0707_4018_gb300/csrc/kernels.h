@@ -182,11 +182,13 @@ constexpr int kCoarsestSlots = 68;
 // Same solve with each CTA's rows, vectors and Krylov basis resident in shared memory
 // (N = 8, restart <= 16, at most 64 dofs per CTA when spread over `sms` CTAs): rpub, ypub
 // are n-entry publication buffers for the neighbours' reads; 2 grid barriers per iteration.
+// With Yt32 (an FP32 copy of A M) the stencil is stored and applied in FP32 while the Krylov
+// vectors, Gram-Schmidt, residuals and updates stay FP64.
 bool coarsest_smem_fits(Geo2 g, int N, int restart, int sms);
-void launch_coarsest_gcr_smem(const Cx<double> *Yt, const Cx<double> *Minv, Geo2 g, const Cx<double> *b,
-                              Cx<double> *x, Cx<double> *rpub, Cx<double> *ypub, double *partials, unsigned int *bar,
-                              double tol, int restart, int max_iter, int *out, double *out_rel, int sms,
-                              cudaStream_t s);
+void launch_coarsest_gcr_smem(const Cx<double> *Yt, const Cx<float> *Yt32, const Cx<double> *Minv, Geo2 g,
+                              const Cx<double> *b, Cx<double> *x, Cx<double> *rpub, Cx<double> *ypub,
+                              double *partials, unsigned int *bar, double tol, int restart, int max_iter, int *out,
+                              double *out_rel, int sms, cudaStream_t s);
 
 // Batched variant: nb <= 4 right-hand sides in one launch, vector v solving
 // (Y + shift[v]) x_v = b_v (shift: device, null for none) with M_v = Minv + v * minv_stride

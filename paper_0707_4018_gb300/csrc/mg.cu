@@ -116,6 +116,7 @@ struct mg_ctx {
   mg::DevBuf<mg::Cx<double>> cZ, cW, cr, cb, cx;
   mg::DevBuf<double> cg_partials, cg_rel;
   mg::DevBuf<mg::Cx<double>> cg_Minv, cg_Yt, cg_work, cg_y;
+  mg::DevBuf<mg::Cx<float>> cg_Yt32;  // FP32 copy of A M for mixed-precision cycles (shared-memory kernel)
   mg::DevBuf<int> cg_info;
   mg::DevBuf<unsigned int> cg_bar;
   mg::DevBuf<int> cg_out;  // [0] iterations, [1] timeout flag, [2] solves above tolerance
@@ -381,7 +382,8 @@ static void coarsest_solve64(mg_ctx &c, const Cx<double> *b, Cx<double> *x, int 
   const Cx<double> *Minv = slot == 0 ? c.cg_Minv.p : c.bMinv.p + (slot - 1) * m2;
   const Cx<double> *Yt = slot == 0 ? c.cg_Yt.p : c.bYt.p + (slot - 1) * 5 * m2;
   if (c.cg_smem)
-    launch_coarsest_gcr_smem(Yt, Minv, L.geo, b, x, c.cr.p, c.cg_y.p, c.cg_partials.p, c.cg_bar.p,
+    launch_coarsest_gcr_smem(Yt, slot == 0 ? c.cg_Yt32.p : nullptr, Minv, L.geo, b, x, c.cr.p, c.cg_y.p,
+                             c.cg_partials.p, c.cg_bar.p,
                              c.p.coarsest_tol, c.p.coarsest_restart, c.p.coarsest_max_iter, c.cg_out.p, c.cg_rel.p,
                              c.cg_grid, c.s);
   else
@@ -716,6 +718,7 @@ static void prepare_coarsest(mg_ctx &c) {
   std::fill(c.slot_shift.begin(), c.slot_shift.end(), std::nan(""));  // batched slots are stale
   if (!c.use_lu) {
     prepare_coarsest_gcr(L.Y64.p, L.geo, L.nint, c.cg_Minv.p, c.cg_Yt.p, c.cg_work.p, c.cg_info.p, c.s);
+    if (c.cg_Yt32.p != nullptr) launch_convert<float, double>(c.cg_Yt.p, c.cg_Yt32.p, c.cg_Yt.n, c.s);
     int info = 0;
     MG_CUDA(cudaMemcpyAsync(&info, c.cg_info.p, sizeof(int), cudaMemcpyDeviceToHost, c.s));
     MG_CUDA(cudaStreamSynchronize(c.s));
@@ -989,6 +992,10 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
     c->cg_rel.alloc(1);
     c->cg_Minv.alloc((size_t)Cst.geo.nsites * Cst.nint * Cst.nint);
     c->cg_Yt.alloc((size_t)Cst.geo.nsites * 5 * Cst.nint * Cst.nint);
+    // mixed precision: store and apply A M in FP32 when the requested coarsest accuracy is far
+    // above FP32 rounding (the Krylov vectors and reductions stay FP64)
+    if (f32 && c->cg_smem && p->coarsest_tol >= 1e-5 && std::getenv("MG_FP64_COARSEST_STENCIL") == nullptr)
+      c->cg_Yt32.alloc(c->cg_Yt.n);
     c->cg_work.alloc((size_t)Cst.geo.nsites * 2 * Cst.nint * Cst.nint);
     c->cg_y.alloc(Cst.n);
     c->cg_info.alloc(1);
@@ -1576,15 +1583,24 @@ int mg_setup_learned(mg_ctx **ctx, const mg_geom *g, const void *U, double m, co
         relax_and_adapt<double>(*c, 0, 1);
       c->p.nu_setup = keep;
     }
-    build_level(*c, 0);
-    if (f32) {
-      launch_convert<float, double>(F.V64.p, F.V32.p, F.V64.n, c->s);
-      refresh_y32(*c, 1);
+    // the adaptive passes 2..n_pass follow as in the plain setup, from the learned start
+    for (int pass = 1; pass <= c->p.n_pass; ++pass) {
+      if (pass > 1) {
+        if (f32)
+          relax_and_adapt<float>(*c, 0, pass);
+        else
+          relax_and_adapt<double>(*c, 0, pass);
+      }
+      build_level(*c, 0);
+      if (f32) {
+        launch_convert<float, double>(F.V64.p, F.V32.p, F.V64.n, c->s);
+        refresh_y32(*c, 1);
+      }
+      if (c->p.levels > 2)
+        setup_level(*c, 1, pass == c->p.n_pass);
+      else
+        prepare_coarsest(*c);
     }
-    if (c->p.levels > 2)
-      setup_level(*c, 1, true);
-    else
-      prepare_coarsest(*c);
     F.stale = false;
     make_fp32_copies(*c);
     collect_coarsest(*c);

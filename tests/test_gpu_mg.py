@@ -249,3 +249,21 @@ def test_solve_is_bitwise_reproducible(precision):
         outs.append(to_host(psi))
         ctx.close()
     assert np.array_equal(outs[0].view(np.uint64), outs[1].view(np.uint64))
+
+
+def test_fp32_stencil_coarsest_solve_meets_its_tolerance():
+    # mixed precision with a loose coarsest tolerance: A M is stored and applied in FP32 inside the
+    # FP64 GCR; the solution still meets the tolerance against the oracle's FP64 coarse operator
+    import torch
+    dims = (64, 64)
+    U, _, _ = inputs.schwinger_links(64, 6.0, sweeps=100, workload_id=5)
+    hier, ctx, _ = make_pair(dims, 0.02, [(4, 4), (2, 2)], [8, 8], U, precision=1, coarsest_lu_max=0,
+                             coarsest_tol=1e-4)
+    n, k = ctx.level_size(2)
+    A = solvers.stencil_matrix(hier.ops[2])
+    for seed in (8, 9):
+        b = inputs.gaussian_complex(n * k, seed, 80).reshape(n, k)
+        x = torch.empty((n, k), dtype=torch.complex128, device="cuda")
+        iters, _ = ctx.coarsest_solve(to_dev(b), x)
+        res = np.linalg.norm(b.reshape(-1) - A @ to_host(x).reshape(-1)) / np.linalg.norm(b)
+        assert 0 < iters < 200 and res <= 1.5e-4, (iters, res)
