@@ -294,6 +294,99 @@ def config1_large(flush, precisions=(1, 0)):
     return out
 
 
+LEARN_L, LEARN_TRAIN, LEARN_EVAL, LEARN_BIG_L, LEARN_BIG_EVAL = 128, 256, 64, 512, 8
+LEARN_WID = 4
+
+
+def learned_setup_eval(n_train: int = LEARN_TRAIN, n_eval: int = LEARN_EVAL, n_big: int = LEARN_BIG_EVAL,
+                       steps: int = 300, nu_refine: int = 16, max_rate: float = 0.6):
+    """Learned near-null setup (2 levels, 4x4 blocks, Nv 8, beta 6): the network is trained on the
+    plain adaptive setup's prolongators of n_train fields at 128^2, then held-out fields at 128^2
+    and 512^2 are set up both ways (plain: 5 passes; learned: the network's vectors, nu_refine MR
+    iterations, the convergence-rate judge with the plain setup as fallback) and solved once each
+    to 1e-10 at m = m_c + 0.02 (m_c: the stored 128^2 field, and the 256^2 calibration for 512^2)."""
+    import torch
+    import paper_0707_4018_gb300 as mg
+    table = mcrit_table()
+    t0 = time.time()
+    seeds = [inputs.member_seed(LEARN_WID, LEARN_L, 6.0, i) for i in range(n_train + n_eval)]
+    th, _ = inputs.metropolis_u1_2d_gpu(LEARN_L, LEARN_L, [6.0] * len(seeds), seeds, 2000)
+    big_seeds = [inputs.member_seed(LEARN_WID, LEARN_BIG_L, 6.0, i) for i in range(n_big)]
+    thb, _ = inputs.metropolis_u1_2d_gpu(LEARN_BIG_L, LEARN_BIG_L, [6.0] * n_big, big_seeds, 2000)
+    gen_s = time.time() - t0
+    U = torch.from_numpy(np.stack([inputs.links_from_angles(t) for t in th])).cuda()
+    Ub = torch.from_numpy(np.stack([inputs.links_from_angles(t) for t in thb])).cuda()
+    m = table["w2_L128_b6"]["m_crit"] + 0.02
+    mb = table["w1_L256_b6"]["m_crit"] + 0.02
+    plain_p = mg.mg_default_params(levels=2, blocks=[(4, 4)], Nv=[8], n_pass=5, precision=1, coarsest_tol=0.2)
+    learn_p = mg.mg_default_params(levels=2, blocks=[(4, 4)], Nv=[8], n_pass=1, precision=1, coarsest_tol=0.2)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    targets = []
+    for i0 in range(0, n_train, 64):
+        cs = mg.Context.setup_batch([U[i] for i in range(i0, min(n_train, i0 + 64))], [m] * min(64, n_train - i0),
+                                    [(LEARN_L, LEARN_L)] * min(64, n_train - i0), [plain_p] * min(64, n_train - i0))
+        targets += [c.prolongator(0) for c in cs]
+        for c in cs:
+            c.close()
+    T = torch.stack(targets)
+    torch.cuda.synchronize()
+    target_s = time.time() - t0
+    net = mg.NullNet(8, 16, 8, seed=ROOT_NET_SEED)
+    t0 = time.time()
+    losses = net.train(U[:n_train], (LEARN_L, LEARN_L), T, (4, 4), steps=steps, batch=16, lr=3e-3, seed=5)
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    del T
+
+    def compare(Us, Lf, mass, count, tag):
+        chi = torch.from_numpy(inputs.gaussian_source(Lf, Lf, seed=11)).cuda()
+        psi = torch.empty_like(chi)
+        rows = {"plain": [], "learned": [], "plain_fp64": []}
+        fallbacks = 0
+        for i in range(count):
+            for kind in ("plain", "learned", "plain_fp64"):
+                torch.cuda.synchronize()
+                t = time.time()
+                if kind == "learned":
+                    ctx, used, rate = mg.Context.setup_learned(Us[i], mass, (Lf, Lf), learn_p, net,
+                                                               noise_seed=1000 + i, nu_refine=nu_refine,
+                                                               max_rate=max_rate)
+                    fallbacks += 0 if used else 1
+                else:
+                    q = plain_p if kind == "plain" else mg.mg_default_params(levels=2, blocks=[(4, 4)], Nv=[8],
+                                                                             n_pass=5, precision=0,
+                                                                             coarsest_tol=0.2)
+                    ctx = mg.Context.setup(Us[i], mass, (Lf, Lf), q)
+                st = ctx.solve(chi, psi, TOL)
+                torch.cuda.synchronize()
+                rows[kind].append(dict(iters=st["iters"], setup_s=st["setup_s"], solve_s=st["solve_s"],
+                                       wall_s=time.time() - t, res=st["true_rel_residual"],
+                                       conv=st["converged"]))
+                ctx.close()
+        out = {"lattice": f"{Lf}x{Lf}", "held_out_fields": count, "learned_fallbacks": fallbacks}
+        for kind, r in rows.items():
+            out[kind] = dict(mean_iters=float(np.mean([x["iters"] for x in r])),
+                             mean_setup_ms=1e3 * float(np.mean([x["setup_s"] for x in r])),
+                             mean_solve_ms=1e3 * float(np.mean([x["solve_s"] for x in r])),
+                             solves_per_s_incl_setup=len(r) / sum(x["wall_s"] for x in r),
+                             all_converged=all(x["conv"] for x in r),
+                             worst_true_rel_residual=max(x["res"] for x in r))
+        return out
+
+    small = compare([U[n_train + i] for i in range(n_eval)], LEARN_L, m, n_eval, "128")
+    big = compare([Ub[i] for i in range(n_big)], LEARN_BIG_L, mb, n_big, "512")
+    return {"train": {"fields": n_train, "lattice": f"{LEARN_L}x{LEARN_L}", "steps": steps, "batch": 16,
+                      "loss_first10": float(np.mean(losses[:10])), "loss_last10": float(np.mean(losses[-10:])),
+                      "gen_s": gen_s, "plain_setups_s": target_s, "train_s": train_s},
+            "learned": {"nu_refine": nu_refine, "n_pass": 1, "judge_max_rate": max_rate},
+            "eval_128": small, "eval_512": big,
+            "mass": "m_c + 0.02 (m_c of the stored 128^2 beta 6 field; 256^2 calibration for 512^2)"}
+
+
+ROOT_NET_SEED = 20070704
+
+
 def dslash_roofline(precision: int, L_big: int = 4096, iters: int = 20):
     """Fine Wilson apply alone on a lattice far larger than L2: algorithmic bytes / time."""
     import torch
@@ -667,6 +760,13 @@ def run_only(case: str):
     if case == "mixed-sizes":
         print(json.dumps({"case": case, **mixed_sizes()}))
         return
+    if case == "learned":
+        print(json.dumps({"case": case, **learned_setup_eval()}))
+        return
+    if case == "large":
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        print(json.dumps({"case": case, **config1_large(flush)}))
+        return
     if case == "su3-batch-prof":  # mixed precision, setup and one batch of 12 sources (launch-list profiling)
         r = su3_workload((1,), SU3_RHS, batched=True, singles=False)
         print(json.dumps({"case": case, **r}))
@@ -796,9 +896,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 1024^2 sweep points")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned near-null setup evaluation")
     ap.add_argument("--only", default=None, choices=["dslash-f32", "dslash-f64", "dslash4-f32", "dslash4-f64", "solve", "vcycle",
                                                       "transfer", "coarse-tc", "coarse-tc4", "su3", "su3-prof",
-                                                      "su3-batch-prof", "mixed-sizes"],
+                                                      "su3-batch-prof", "mixed-sizes", "learned", "large"],
                     help="profiling cases: the Dslash timing loop alone (2d, or 4d SU(3)), one beta's setup + 3 solves, "
                          "25 mixed-precision V-cycles after one beta's setup, or 5 V-cycles on a 1024^2 "
                          "hierarchy (fine level larger than L2, for the restriction and prolongation), or the "
@@ -857,6 +958,7 @@ def main():
     mix = mixed_sizes() if world_of(d) == 1 or rank == 0 else None
     cr = coarsest_roofline(fields_dev)
     large = config1_large(flush) if (world_of(d) == 1 or rank == 0) and not args.no_large else None
+    learned = learned_setup_eval() if (world_of(d) == 1 or rank == 0) and not args.no_learned else None
 
     cpu = None
     if rank == 0 and world_of(d) == 1 and not args.no_cpu:
@@ -892,6 +994,7 @@ def main():
         "su3_4d": su3,
         "mixed_sizes": mix,
         "config1_1024": large,
+        "learned_setup": learned,
     }
     print(json.dumps(line), flush=True)
 

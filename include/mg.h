@@ -414,6 +414,12 @@ size_t mg_autotune_report(char *buf, size_t len);
  * With 0 the barrier completes and the call returns MG_OK. */
 int mg_selftest_barrier(int missing_arrivals, void *stream);
 
+/* Measured fused-multiply-add throughput of the current GPU in TFLOP/s (2 flops per FMA),
+ * precision MG_FP64 or MG_FP32: a grid of 8 CTAs per SM, each thread running 8 independent
+ * FMA chains, timed with CUDA events on `stream` after a warm-up launch. The roofline
+ * denominator of the ALU-bound kernels (the paper has no counterpart; a measurement aid). */
+int mg_alu_peak(int precision, double *tflops, void *stream);
+
 /* Number of kernels this library has launched since the process started. */
 long long mg_kernel_launches(void);
 

@@ -91,6 +91,7 @@ def load():
         "mg_setup_learned": (I, [P(ctxp), P(mg_geom), VP, D, P(mg_params), ctxp, ctypes.c_uint64, I, D, I, P(I),
                                  P(D), VP]),
         "mg_convergence_rate": (I, [ctxp, I, ctypes.c_uint64, P(D)]),
+        "mg_alu_peak": (I, [I, P(D), VP]),
         "mg_solve_batch": (I, [ctxp, I, VP, VP, P(D), D, P(mg_stats)]),
         "mg_coarse_apply_mrhs": (I, [ctxp, I, I, VP, VP, I]),
         "mg_update_mass": (I, [ctxp, D]),
@@ -131,7 +132,7 @@ def exported_symbols():
             "mg_coarse_apply_mrhs", "mg_autotune_report", "mg_clone", "mg_setup_batch", "mg_save_setup",
             "mg_load_setup", "mg_context_info", "mg_nullnet_create", "mg_nullnet_destroy", "mg_nullnet_weight_count",
             "mg_nullnet_get_weights", "mg_nullnet_set_weights", "mg_nullnet_forward", "mg_nullnet_gradient",
-            "mg_nullnet_train", "mg_setup_learned", "mg_convergence_rate"]
+            "mg_nullnet_train", "mg_setup_learned", "mg_convergence_rate", "mg_alu_peak"]
 
 
 def autotune_report() -> dict:
@@ -226,6 +227,13 @@ def mg_smooth_fine_noalloc(U: torch.Tensor, b: torch.Tensor, x: torch.Tensor, m:
 def mg_selftest_barrier(missing_arrivals: int, stream=None):
     """Bounded grid-barrier self-test: raises MGError(MG_ERR_TIMEOUT) when an arrival is missing."""
     _check(load().mg_selftest_barrier(int(missing_arrivals), _stream(stream)))
+
+
+def mg_alu_peak(precision: int, stream=None) -> float:
+    """Measured FMA throughput (TFLOP/s) of the current GPU in FP64 (0) or FP32 (1)."""
+    t = ctypes.c_double(0.0)
+    _check(load().mg_alu_peak(int(precision), ctypes.byref(t), _stream(stream)))
+    return float(t.value)
 
 
 def mg_kernel_launches() -> int:

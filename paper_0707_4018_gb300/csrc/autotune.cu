@@ -49,3 +49,72 @@ std::string autotune_report() {
 }
 
 }  // namespace mg
+
+// ---------------------------------------------------------------------------
+// Arithmetic peak probe: the FP64 / FP32 fused multiply-add rate this GPU sustains, the
+// denominator of the roofline of ALU-bound kernels (GB300's FP64 rate is a small fraction of
+// its FP32 rate). Every thread runs 8 independent FMA chains; the result is stored only when
+// it equals a value it never takes, so the chains cannot be optimised away.
+// ---------------------------------------------------------------------------
+namespace mg {
+namespace {
+
+template <typename R>
+__global__ void __launch_bounds__(256) fma_probe_kernel(int iters, R b, R c, R *sink) {
+  R a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = (R)(threadIdx.x + k);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+  }
+  R s = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  if (s == (R)-12345.678) sink[threadIdx.x] = s;
+}
+
+template <typename R>
+double fma_probe(cudaStream_t s) {
+  int dev = 0, sms = 0;
+  MG_CUDA(cudaGetDevice(&dev));
+  MG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  DevBuf<R> sink;
+  sink.alloc(256);
+  pool_ready();
+  const int blocks = sms * 8, iters = sizeof(R) == 8 ? 2048 : 16384;
+  const R b = (R)0.999999, c = (R)1e-7;
+  fma_probe_kernel<R><<<blocks, 256, 0, s>>>(64, b, c, sink.p);  // warm-up
+  MG_LAUNCHED();
+  EventPair ev;
+  ev.start(s);
+  fma_probe_kernel<R><<<blocks, 256, 0, s>>>(iters, b, c, sink.p);
+  MG_LAUNCHED();
+  const float ms = ev.stop(s);
+  const double flops = 2.0 * 8.0 * iters * (double)blocks * 256.0;
+  return flops / (ms * 1e-3) * 1e-12;
+}
+
+}  // namespace
+}  // namespace mg
+
+extern "C" int mg_alu_peak(int precision, double *tflops, void *stream) {
+  try {
+    if (!tflops) mg::fail(MG_ERR_INVALID_ARG, "null output");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision == MG_FP64)
+      *tflops = mg::fma_probe<double>(s);
+    else if (precision == MG_FP32)
+      *tflops = mg::fma_probe<float>(s);
+    else
+      mg::fail(MG_ERR_INVALID_ARG, "precision must be MG_FP64 or MG_FP32");
+    mg::set_last_error("");
+    return MG_OK;
+  } catch (const mg::Error &e) {
+    mg::set_last_error(e.msg);
+    return e.code;
+  } catch (...) {
+    mg::set_last_error("unexpected exception");
+    return MG_ERR_CUDA;
+  }
+}
