@@ -643,9 +643,22 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def cpu_baseline(budget_s: float = 25.0):
+def cpu_baseline(budget_s: float | None = 25.0, threads: int | None = None):
     """The FP64 oracle, as it stands, on a bounded sample of the workload: beta = 6 only,
-    adaptive setup at the lightest mass then solves at the three masses until the budget."""
+    adaptive setup at the lightest mass then solves at the three masses (the GPU step's
+    amortisation: 3 solves per setup) until the budget (None: all three). threads: BLAS
+    threads (None: all host cores; numpy's elementwise work is single-threaded either way)."""
+    import contextlib
+    try:
+        import threadpoolctl
+        limit = threadpoolctl.threadpool_limits(threads) if threads else contextlib.nullcontext()
+    except ImportError:
+        limit = contextlib.nullcontext()
+    with limit:
+        return _cpu_baseline(budget_s, threads)
+
+
+def _cpu_baseline(budget_s, threads):
     from oracle import setup as osetup, solvers as osolvers
     from oracle.lattice import Lattice
     table = mcrit_table()
@@ -665,15 +678,18 @@ def cpu_baseline(budget_s: float = 25.0):
         chi = inputs.gaussian_source(L, L, seed=seed, index=i)
         osolvers.mg_solve(hier, chi, TOL)
         solves += 1
-        if time.perf_counter() - t0 > budget_s:
+        if budget_s is not None and time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    try:
-        import threadpoolctl
-        cores = max(info.get("num_threads", 1) for info in threadpoolctl.threadpool_info()) or 1
-    except Exception:
-        cores = os.cpu_count() or 1
-    return dict(value=solves / dt, unit="solves/s", cores=cores, kind="oracle", seconds=dt,
+    if threads:
+        cores = threads
+    else:
+        try:
+            import threadpoolctl
+            cores = max(info.get("num_threads", 1) for info in threadpoolctl.threadpool_info()) or 1
+        except Exception:
+            cores = os.cpu_count() or 1
+    return dict(value=solves / dt, unit="solves/s", cores=cores, kind="oracle", seconds=dt, solves=solves,
                 sample=f"beta=6 only: oracle setup at m_c+0.005 then {solves} solve(s) "
                        f"(of the 9-solve step), 256x256, tol 1e-10")
 
@@ -732,19 +748,26 @@ def run_reference(args, d):
     """The oracle arm: the FP64 CPU oracle timed on the host cores (rank 0 only)."""
     if rank_of(d) != 0:
         return
+    # each step: one oracle setup and its three solves (the GPU step's amortisation of 3 solves per
+    # setup, for beta = 6); steps run until about 150 s have passed (at least one), so the arm
+    # ends within a few minutes whatever --steps is
     per_step = []
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        pass
+    t0 = time.perf_counter()
     for _ in range(max(1, args.steps)):
-        cb = cpu_baseline(budget_s=min(25.0, 60.0 / max(1, args.steps)))
-        per_step.append(cb)
-    v = float(np.mean([c["value"] for c in per_step]))
+        per_step.append(cpu_baseline(budget_s=None))
+        if time.perf_counter() - t0 > 150.0:
+            break
+    solves = sum(c["solves"] for c in per_step)
+    secs = sum(c["seconds"] for c in per_step)
+    v = solves / secs
+    sample = (f"{len(per_step)} of {args.steps} step(s) timed; each: " + per_step[0]["sample"])
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": per_step[0]["sample"]},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(per_step),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": f"{L}x{L}", "betas": list(BETAS), "m_minus_mc": list(DMS),
+                       "tol": TOL},
             "cpu_baseline": {"value": v, "unit": "solves/s", "cores": per_step[0]["cores"], "kind": "oracle",
-                             "sample": per_step[0]["sample"]},
+                             "sample": sample},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -963,6 +986,8 @@ def main():
     cpu = None
     if rank == 0 and world_of(d) == 1 and not args.no_cpu:
         cpu = cpu_baseline()
+        one = cpu_baseline(budget_s=10.0, threads=1)
+        cpu["single_thread"] = {k: one[k] for k in ("value", "unit", "cores", "seconds", "sample")}
 
     if rank != 0:
         return

@@ -190,6 +190,15 @@ void launch_coarsest_gcr_smem(const Cx<double> *Yt, const Cx<float> *Yt32, const
                               double *partials, unsigned int *bar, double tol, int restart, int max_iter, int *out,
                               double *out_rel, int sms, cudaStream_t s);
 
+// One-cluster variant (coarsest_cluster.cu) for mixed-precision cycles with a loose tolerance:
+// FP32 GCR on A M (Yt32) with FP64 cross-warp / cross-CTA sums, 16 CTAs of one thread-block
+// cluster per vector (nvec clusters in one launch, vector v at offset v n of b, x and of the
+// FP32 publication buffers rpub, ypub of nvec n entries each); N = 8, at most 8192 dofs.
+bool coarsest_cluster_fits(Geo2 g, int N, int restart);
+void launch_coarsest_gcr_cluster(const Cx<float> *Yt32, const Cx<double> *Minv, Geo2 g, int nvec,
+                                 const Cx<double> *b, Cx<double> *x, Cx<float> *rpub, Cx<float> *ypub, double tol,
+                                 int restart, int max_iter, int *out, double *out_rel, cudaStream_t s);
+
 // Batched variant: nb <= 4 right-hand sides in one launch, vector v solving
 // (Y + shift[v]) x_v = b_v (shift: device, null for none) with M_v = Minv + v * minv_stride
 // (minv_stride 0: one preconditioner for all); Y is the raw stencil. b, x, upub, xpub hold

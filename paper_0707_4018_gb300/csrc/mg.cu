@@ -117,6 +117,8 @@ struct mg_ctx {
   mg::DevBuf<double> cg_partials, cg_rel;
   mg::DevBuf<mg::Cx<double>> cg_Minv, cg_Yt, cg_work, cg_y;
   mg::DevBuf<mg::Cx<float>> cg_Yt32;  // FP32 copy of A M for mixed-precision cycles (shared-memory kernel)
+  bool cg_cluster = false;            // one-cluster FP32 coarsest GCR (mixed precision, loose tolerance)
+  mg::DevBuf<mg::Cx<float>> cl_rpub, cl_ypub;  // its publication buffers (nbatch vectors)
   mg::DevBuf<int> cg_info;
   mg::DevBuf<unsigned int> cg_bar;
   mg::DevBuf<int> cg_out;  // [0] iterations, [1] timeout flag, [2] solves above tolerance
@@ -381,7 +383,10 @@ static void coarsest_solve64(mg_ctx &c, const Cx<double> *b, Cx<double> *x, int 
   const long long m2 = L.geo.nsites * (long long)L.nint * L.nint;
   const Cx<double> *Minv = slot == 0 ? c.cg_Minv.p : c.bMinv.p + (slot - 1) * m2;
   const Cx<double> *Yt = slot == 0 ? c.cg_Yt.p : c.bYt.p + (slot - 1) * 5 * m2;
-  if (c.cg_smem)
+  if (c.cg_cluster && slot == 0)
+    launch_coarsest_gcr_cluster(c.cg_Yt32.p, Minv, L.geo, 1, b, x, c.cl_rpub.p, c.cl_ypub.p, c.p.coarsest_tol,
+                                c.p.coarsest_restart, c.p.coarsest_max_iter, c.cg_out.p, c.cg_rel.p, c.s);
+  else if (c.cg_smem)
     launch_coarsest_gcr_smem(Yt, slot == 0 ? c.cg_Yt32.p : nullptr, Minv, L.geo, b, x, c.cr.p, c.cg_y.p,
                              c.cg_partials.p, c.cg_bar.p,
                              c.p.coarsest_tol, c.p.coarsest_restart, c.p.coarsest_max_iter, c.cg_out.p, c.cg_rel.p,
@@ -400,6 +405,13 @@ static void coarsest_vectors64(mg_ctx &c, const Cx<double> *b, Cx<double> *x, in
   const Level &L = c.lv[l];
   const long long n = L.n;
   const bool batch = c.cur_shift != nullptr;
+  if (c.cg_cluster && nvec > 1 && !batch) {
+    // every vector at the context mass: one cluster per vector, all in one launch
+    launch_coarsest_gcr_cluster(c.cg_Yt32.p, c.cg_Minv.p, L.geo, nvec, b, x, c.cl_rpub.p, c.cl_ypub.p,
+                                c.p.coarsest_tol, c.p.coarsest_restart, c.p.coarsest_max_iter, c.cg_out.p, c.cg_rel.p,
+                                c.s);
+    return;
+  }
   if (c.cg_batch && (nvec > 1 || batch)) {
     const long long m2 = L.geo.nsites * 64LL;
     for (int v0 = 0; v0 < nvec; v0 += kCoarsestBatchVecs) {
@@ -994,8 +1006,15 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
     c->cg_Yt.alloc((size_t)Cst.geo.nsites * 5 * Cst.nint * Cst.nint);
     // mixed precision: store and apply A M in FP32 when the requested coarsest accuracy is far
     // above FP32 rounding (the Krylov vectors and reductions stay FP64)
-    if (f32 && c->cg_smem && p->coarsest_tol >= 1e-5 && std::getenv("MG_FP64_COARSEST_STENCIL") == nullptr)
+    c->cg_cluster = f32 && p->coarsest_tol >= 1e-5 && std::getenv("MG_NO_CLUSTER_COARSEST") == nullptr &&
+                    coarsest_cluster_fits(Cst.geo, Cst.nint, p->coarsest_restart);
+    if ((f32 && c->cg_smem && p->coarsest_tol >= 1e-5 && std::getenv("MG_FP64_COARSEST_STENCIL") == nullptr) ||
+        c->cg_cluster)
       c->cg_Yt32.alloc(c->cg_Yt.n);
+    if (c->cg_cluster) {
+      c->cl_rpub.alloc((size_t)c->nbatch * Cst.n);
+      c->cl_ypub.alloc((size_t)c->nbatch * Cst.n);
+    }
     c->cg_work.alloc((size_t)Cst.geo.nsites * 2 * Cst.nint * Cst.nint);
     c->cg_y.alloc(Cst.n);
     c->cg_info.alloc(1);

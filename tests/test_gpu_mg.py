@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import inputs
-from oracle import coarse, setup, solvers, transfer
+from oracle import coarse, setup, solvers, transfer, wilson
 from oracle.lattice import Lattice
 from tests._util import rel_err, to_dev, to_host
 
@@ -251,10 +251,14 @@ def test_solve_is_bitwise_reproducible(precision):
     assert np.array_equal(outs[0].view(np.uint64), outs[1].view(np.uint64))
 
 
-def test_fp32_stencil_coarsest_solve_meets_its_tolerance():
-    # mixed precision with a loose coarsest tolerance: A M is stored and applied in FP32 inside the
-    # FP64 GCR; the solution still meets the tolerance against the oracle's FP64 coarse operator
+@pytest.mark.parametrize("kernel", ["cluster", "smem_fp32_stencil"])
+def test_fp32_stencil_coarsest_solve_meets_its_tolerance(kernel, monkeypatch):
+    # mixed precision with a loose coarsest tolerance: the one-cluster FP32 GCR, or (cluster kernel
+    # switched off) A M stored and applied in FP32 inside the whole-chip FP64 GCR; the solution
+    # meets the tolerance against the oracle's FP64 coarse operator
     import torch
+    if kernel != "cluster":
+        monkeypatch.setenv("MG_NO_CLUSTER_COARSEST", "1")
     dims = (64, 64)
     U, _, _ = inputs.schwinger_links(64, 6.0, sweeps=100, workload_id=5)
     hier, ctx, _ = make_pair(dims, 0.02, [(4, 4), (2, 2)], [8, 8], U, precision=1, coarsest_lu_max=0,
@@ -267,3 +271,24 @@ def test_fp32_stencil_coarsest_solve_meets_its_tolerance():
         iters, _ = ctx.coarsest_solve(to_dev(b), x)
         res = np.linalg.norm(b.reshape(-1) - A @ to_host(x).reshape(-1)) / np.linalg.norm(b)
         assert 0 < iters < 200 and res <= 1.5e-4, (iters, res)
+
+
+@pytest.mark.parametrize("kernel", ["cluster", "smem"])
+def test_mixed_solve_with_loose_coarsest_reaches_true_residual(kernel, monkeypatch):
+    # the bench's configuration (3 levels, coarsest tolerance 0.2): the setup's batched V-cycles
+    # (one cluster per vector) and the solve's cycles; the FP64 outer loop reaches 1e-10
+    import torch
+    import paper_0707_4018_gb300 as mg
+    if kernel != "cluster":
+        monkeypatch.setenv("MG_NO_CLUSTER_COARSEST", "1")
+    L = 128
+    U, _, _ = inputs.schwinger_links(L, 6.0, sweeps=200, workload_id=5)
+    p = mg.mg_default_params(levels=3, blocks=[(4, 4), (2, 2)], Nv=[8, 8], precision=1, coarsest_tol=0.2,
+                             coarsest_lu_max=0)
+    ctx = mg.Context.setup(to_dev(U), 0.02, (L, L), p)
+    chi = inputs.gaussian_source(L, L, seed=12)
+    psi = torch.empty((L * L, 2), dtype=torch.complex128, device="cuda")
+    st = ctx.solve(to_dev(chi), psi, 1e-10)
+    res = np.linalg.norm(chi - wilson.apply_D(U, to_host(psi), 0.02, Lattice((L, L)))) / np.linalg.norm(chi)
+    assert st["converged"] and res <= 1e-10 and st["coarsest_iters"] > 0
+    ctx.close()
