@@ -198,9 +198,63 @@ def _one_field(f, precision, stats_out, host_io, contexts):
 CONCURRENT = True
 
 
+def run_step_graph(fields_dev, precision: int, stats_out=None, host_io=None):
+    """One pass over the batch with every solve in one graph launch: the betas' setups and the clones
+    of each setup for the heavier masses (one host thread per beta), then mg_solve_multi on all nine
+    contexts (each outer loop a conditional WHILE node on the device)."""
+    import torch
+    import paper_0707_4018_gb300 as mg
+    per_beta, errors = {}, []
+
+    def prepare(f):  # one host thread per beta: its setup, then the clones for the heavier masses
+        try:
+            U = f["U_host"].to("cuda", non_blocking=True) if host_io is not None else f["U_dev"]
+            Lf = f.get("L", L)
+            c = mg.Context.setup(U, f["m_c"] + DMS[0], (Lf, Lf), mg_params(precision))
+            per_beta[f["beta"]] = [c] + [c.clone(f["m_c"] + dm) for dm in DMS[1:]]
+        except BaseException as e:  # re-raised on the calling thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=prepare, args=(f,)) for f in fields_dev]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    if errors:
+        for cs in per_beta.values():
+            for c in cs:
+                c.close()
+        raise errors[0]
+    ctxs, chis, psis, tags = [], [], [], []
+    for f in fields_dev:
+        for i, dm in enumerate(DMS):
+            ctxs.append(per_beta[f["beta"]][i])
+            chis.append(f["chi_host"][i].to("cuda", non_blocking=True) if host_io is not None else f["chi_dev"][i])
+            psis.append(f["psi_dev"][i])
+            tags.append((f["beta"], dm, i))
+    st = mg.solve_multi(ctxs, chis, psis, TOL)
+    if host_io is not None:
+        for (beta, dm, i), psi in zip(tags, psis):
+            host_io[beta][i].copy_(psi, non_blocking=True)
+    torch.cuda.current_stream().synchronize()
+    for c in ctxs:
+        c.close()
+    if stats_out is not None:
+        stats_out.extend(sorted([dict(beta=t[0], dm=t[1], **s) for t, s in zip(tags, st)],
+                                key=lambda d: (d["beta"], d["dm"])))
+    return len(ctxs)
+
+
+# how a step runs its solves: "graph" (one mg_solve_multi launch for all of them) or "threads"
+# (one host thread and host-driven loop per solve)
+STEP_MODE = "graph"
+
+
 def run_step(fields_dev, precision: int, stats_out=None, host_io=None):
     """One pass over the batch: per beta, setup at the lightest mass and three solves."""
     import torch
+    if STEP_MODE == "graph" and CONCURRENT:
+        return run_step_graph(fields_dev, precision, stats_out, host_io)
     contexts = []
     stats = [] if stats_out is not None else None
     if CONCURRENT and len(fields_dev) > 1:
@@ -919,6 +973,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 1024^2 sweep points")
+    ap.add_argument("--threads", action="store_true",
+                    help="solve with one host thread and host-driven loop per solve instead of one graph launch")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned near-null setup evaluation")
     ap.add_argument("--only", default=None, choices=["dslash-f32", "dslash-f64", "dslash4-f32", "dslash4-f64", "solve", "vcycle",
                                                       "transfer", "coarse-tc", "coarse-tc4", "su3", "su3-prof",
@@ -928,8 +984,9 @@ def main():
                          "hierarchy (fine level larger than L2, for the restriction and prolongation), or the "
                          "level-1 coarse apply on 16 vectors, tensor cores and CUDA cores")
     args = ap.parse_args()
-    global CONCURRENT
+    global CONCURRENT, STEP_MODE
     CONCURRENT = not args.serial
+    STEP_MODE = "threads" if args.threads else "graph"
     if args.warmup < 3:
         raise SystemExit("warmup must be >= 3")
     if args.only is not None:

@@ -92,6 +92,7 @@ def load():
                                  P(D), VP]),
         "mg_convergence_rate": (I, [ctxp, I, ctypes.c_uint64, P(D)]),
         "mg_alu_peak": (I, [I, P(D), VP]),
+        "mg_solve_multi": (I, [I, P(ctxp), P(VP), P(VP), D, P(mg_stats)]),
         "mg_solve_batch": (I, [ctxp, I, VP, VP, P(D), D, P(mg_stats)]),
         "mg_coarse_apply_mrhs": (I, [ctxp, I, I, VP, VP, I]),
         "mg_update_mass": (I, [ctxp, D]),
@@ -132,7 +133,7 @@ def exported_symbols():
             "mg_coarse_apply_mrhs", "mg_autotune_report", "mg_clone", "mg_setup_batch", "mg_save_setup",
             "mg_load_setup", "mg_context_info", "mg_nullnet_create", "mg_nullnet_destroy", "mg_nullnet_weight_count",
             "mg_nullnet_get_weights", "mg_nullnet_set_weights", "mg_nullnet_forward", "mg_nullnet_gradient",
-            "mg_nullnet_train", "mg_setup_learned", "mg_convergence_rate", "mg_alu_peak"]
+            "mg_nullnet_train", "mg_setup_learned", "mg_convergence_rate", "mg_alu_peak", "mg_solve_multi"]
 
 
 def autotune_report() -> dict:
@@ -227,6 +228,21 @@ def mg_smooth_fine_noalloc(U: torch.Tensor, b: torch.Tensor, x: torch.Tensor, m:
 def mg_selftest_barrier(missing_arrivals: int, stream=None):
     """Bounded grid-barrier self-test: raises MGError(MG_ERR_TIMEOUT) when an arrival is missing."""
     _check(load().mg_selftest_barrier(int(missing_arrivals), _stream(stream)))
+
+
+def solve_multi(contexts, chis, psis, tol: float, raise_on_fail: bool = True) -> list:
+    """mg_solve_multi: psis[i] = D_i^{-1} chis[i] for every context, all loops in one graph launch."""
+    n = len(contexts)
+    if not (len(chis) == len(psis) == n) or n < 1:
+        raise ValueError("one source and one solution per context")
+    hs = (ctypes.c_void_p * n)(*[c._need().value if hasattr(c._need(), "value") else c._need() for c in contexts])
+    cp = (ctypes.c_void_p * n)(*[_ptr(chis[i], torch.complex128, contexts[i].n0).value for i in range(n)])
+    pp = (ctypes.c_void_p * n)(*[_ptr(psis[i], torch.complex128, contexts[i].n0).value for i in range(n)])
+    st = (mg_stats * n)()
+    code = load().mg_solve_multi(n, hs, cp, pp, float(tol), st)
+    if code != 0 and (raise_on_fail or code != 4):
+        _check(code)
+    return [st[i].as_dict() for i in range(n)]
 
 
 def mg_alu_peak(precision: int, stream=None) -> float:

@@ -323,3 +323,132 @@ template void launch_convert<float, double>(const Cx<double> *, Cx<float> *, lon
 template void launch_convert<double, float>(const Cx<float> *, Cx<double> *, long long, cudaStream_t);
 
 }  // namespace mg
+
+// ---------------------------------------------------------------------------
+// Outer flexible GCR with the loop on the device (a conditional WHILE node of a CUDA graph
+// replays one iteration until the control kernel clears the condition). The basis index k
+// and the counters live in device memory: ctl[0] iterations, ctl[1] k, ctl[2] stop reason
+// (1 converged by the estimate, 2 iteration limit, 3 breakdown); st[0] the running |r|^2
+// estimate, st[1] tol^2 |b|^2. Gram-Schmidt is classical with one pass.
+// ---------------------------------------------------------------------------
+namespace mg {
+
+// rows j < k: <W_j, w>; row k: |w|^2; row k + 1: <w, r>; row k + 2: |r|^2, with k = ctl[1];
+// the grid has restart + 3 rows, the rows above k + 2 only finish their (empty) reduction
+__global__ void __launch_bounds__(kReduceThreads) gcr_dots_devk_kernel(const Cx<double> *__restrict__ W,
+                                                                       const Cx<double> *__restrict__ w,
+                                                                       const Cx<double> *__restrict__ r,
+                                                                       const int *__restrict__ ctl, long long n,
+                                                                       double *partials, double *out,
+                                                                       unsigned int *ticket, int pstride) {
+  __shared__ double sh[32 * 2];
+  const int row = blockIdx.y, k = ctl[1];
+  double v[2] = {0.0, 0.0};
+  if (row <= k + 2) {
+    const Cx<double> *a = row < k ? W + (long long)row * n : (row == k + 2 ? r : w);
+    const Cx<double> *b = row > k ? r : w;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+      const Cx<double> x = a[i], y = b[i];
+      v[0] += x.re * y.re + x.im * y.im;
+      v[1] += x.re * y.im - x.im * y.re;
+    }
+  }
+  grid_finish<2>(v, partials + (long long)row * pstride, out + 2 * row, ticket + row, sh);
+}
+
+// W_k = (w - sum_j beta_j W_j) / |.|, Z_k likewise from z; x += alpha Z_k; r -= alpha W_k;
+// st[2] = |r|^2 - |alpha|^2 (the new residual estimate), st[3] = 1 on breakdown
+__global__ void gcr_update_devk_kernel(Cx<double> *__restrict__ W, Cx<double> *__restrict__ Z,
+                                       const Cx<double> *__restrict__ w, const Cx<double> *__restrict__ z,
+                                       const int *__restrict__ ctl, const double *__restrict__ dots,
+                                       double *__restrict__ st, Cx<double> *__restrict__ x,
+                                       Cx<double> *__restrict__ r, long long n) {
+  __shared__ double coef[3];
+  const int k = ctl[1];
+  if (threadIdx.x == 0) {
+    const double nw0 = dots[2 * k];
+    double nw2 = nw0;
+    for (int j = 0; j < k; ++j) nw2 -= dots[2 * j] * dots[2 * j] + dots[2 * j + 1] * dots[2 * j + 1];
+    double inv = 0.0, are = 0.0, aim = 0.0;
+    const bool ok = nw2 > 1e-28 * nw0;
+    if (ok) {
+      inv = 1.0 / sqrt(nw2);
+      are = dots[2 * k + 2] * inv;
+      aim = dots[2 * k + 3] * inv;
+    }
+    coef[0] = inv;
+    coef[1] = are;
+    coef[2] = aim;
+    if (blockIdx.x == 0) {
+      st[2] = fmax(dots[2 * k + 4] - (are * are + aim * aim), 0.0);
+      st[3] = ok ? 0.0 : 1.0;
+    }
+  }
+  __syncthreads();
+  const double inv = coef[0];
+  const Cx<double> alpha = mk(coef[1], coef[2]), malpha = mk(-coef[1], -coef[2]);
+  Cx<double> *Wk = W + (long long)k * n, *Zk = Z + (long long)k * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    Cx<double> wi = w[i], zi = z[i];
+    for (int j = 0; j < k; ++j) {
+      const Cx<double> bj = mk(-dots[2 * j], -dots[2 * j + 1]);
+      cmac(wi, bj, W[(long long)j * n + i]);
+      cmac(zi, bj, Z[(long long)j * n + i]);
+    }
+    wi = inv * wi;
+    zi = inv * zi;
+    Wk[i] = wi;
+    Zk[i] = zi;
+    cmac(x[i], alpha, zi);
+    Cx<double> ri = r[i];
+    cmac(ri, malpha, wi);
+    r[i] = ri;
+  }
+}
+
+// one thread: counts the iteration, advances k (a restart starts a new basis from the
+// recurrence residual), decides whether the loop goes on, and sets the WHILE condition
+__global__ void gcr_control_kernel(int *ctl, double *st, int restart, int max_iter,
+                                   cudaGraphConditionalHandle handle) {
+  const int it = ctl[0] + 1;
+  int k = ctl[1] + 1;
+  if (k == restart) k = 0;
+  ctl[0] = it;
+  ctl[1] = k;
+  st[0] = st[2];
+  int reason = 0;
+  if (!(st[0] > st[1])) reason = 1;
+  else if (it >= max_iter) reason = 2;
+  else if (st[3] != 0.0) reason = 3;
+  ctl[2] = reason;
+  cudaGraphSetConditional(handle, reason == 0 ? 1u : 0u);
+}
+
+void launch_gcr_dots_devk(const Cx<double> *W, const Cx<double> *w, const Cx<double> *r, const int *ctl, int restart,
+                          long long n, double *out, const ReduceWs &ws, cudaStream_t s) {
+  const int rows = restart + 3;
+  int per = (int)(ws.capacity / (2 * rows));
+  if (per > ws.max_blocks) per = ws.max_blocks;
+  if (per < 1) per = 1;
+  dim3 grid(reduce_blocks(n, per), rows);
+  gcr_dots_devk_kernel<<<grid, kReduceThreads, 0, s>>>(W, w, r, ctl, n, ws.partials, out, ws.ticket, 2 * (int)grid.x);
+  MG_LAUNCHED();
+}
+
+void launch_gcr_update_devk(Cx<double> *W, Cx<double> *Z, const Cx<double> *w, const Cx<double> *z, const int *ctl,
+                            const double *dots, double *st, Cx<double> *x, Cx<double> *r, long long n,
+                            cudaStream_t s) {
+  long long b = (n + 255) / 256;
+  if (b > 152LL * 16) b = 152LL * 16;
+  gcr_update_devk_kernel<<<(unsigned int)(b < 1 ? 1 : b), 256, 0, s>>>(W, Z, w, z, ctl, dots, st, x, r, n);
+  MG_LAUNCHED();
+}
+
+void launch_gcr_control(int *ctl, double *st, int restart, int max_iter, cudaGraphConditionalHandle handle,
+                        cudaStream_t s) {
+  gcr_control_kernel<<<1, 1, 0, s>>>(ctl, st, restart, max_iter, handle);
+  MG_LAUNCHED();
+}
+
+}  // namespace mg

@@ -70,6 +70,17 @@ void launch_pack_coarse_bf16(const Cx<float> *Y, uint2 *Ypk, long long nsites, c
 void launch_coarse_apply_tc(const uint2 *Ypk, const Cx<float> *in, Cx<float> *out, Geo2 g, int nvec,
                             const Cx<float> *b, double a, double c, const double *shift, cudaStream_t s);
 
+// ---- outer GCR driven on the device (blas.cu): ctl = {iterations, k, stop reason}, st = {|r|^2
+// estimate, tol^2 |b|^2, new estimate, breakdown flag}; the control kernel sets the condition
+// of the WHILE graph node that replays one iteration ----
+void launch_gcr_dots_devk(const Cx<double> *W, const Cx<double> *w, const Cx<double> *r, const int *ctl, int restart,
+                          long long n, double *out, const ReduceWs &ws, cudaStream_t s);
+void launch_gcr_update_devk(Cx<double> *W, Cx<double> *Z, const Cx<double> *w, const Cx<double> *z, const int *ctl,
+                            const double *dots, double *st, Cx<double> *x, Cx<double> *r, long long n,
+                            cudaStream_t s);
+void launch_gcr_control(int *ctl, double *st, int restart, int max_iter, cudaGraphConditionalHandle handle,
+                        cudaStream_t s);
+
 // ---- autotuner of launch shapes (autotune.cu) ----
 // Index of the fastest of `count` launch variants of one kernel for one problem shape, by
 // timing each on stream s (one untimed launch, then three timed with CUDA events); cached
@@ -191,10 +202,12 @@ void launch_coarsest_gcr_smem(const Cx<double> *Yt, const Cx<float> *Yt32, const
                               double *out_rel, int sms, cudaStream_t s);
 
 // One-cluster variant (coarsest_cluster.cu) for mixed-precision cycles with a loose tolerance:
-// FP32 GCR on A M (Yt32) with FP64 cross-warp / cross-CTA sums, 16 CTAs of one thread-block
+// FP32 GCR on A M (Yt32, row-major blocks) with FP64 cross-warp / cross-CTA sums, 16 CTAs of one thread-block
 // cluster per vector (nvec clusters in one launch, vector v at offset v n of b, x and of the
 // FP32 publication buffers rpub, ypub of nvec n entries each); N = 8, at most 8192 dofs.
 bool coarsest_cluster_fits(Geo2 g, int N, int restart);
+// the cluster kernel reads A M as row-major 8 x 8 blocks: [j][dir][col][row] -> [j][dir][row][col]
+void launch_transpose_blocks8(const Cx<float> *in, Cx<float> *out, long long nblocks, cudaStream_t s);
 void launch_coarsest_gcr_cluster(const Cx<float> *Yt32, const Cx<double> *Minv, Geo2 g, int nvec,
                                  const Cx<double> *b, Cx<double> *x, Cx<float> *rpub, Cx<float> *ypub, double tol,
                                  int restart, int max_iter, int *out, double *out_rel, cudaStream_t s);

@@ -119,6 +119,10 @@ struct mg_ctx {
   mg::DevBuf<mg::Cx<float>> cg_Yt32;  // FP32 copy of A M for mixed-precision cycles (shared-memory kernel)
   bool cg_cluster = false;            // one-cluster FP32 coarsest GCR (mixed precision, loose tolerance)
   mg::DevBuf<mg::Cx<float>> cl_rpub, cl_ypub;  // its publication buffers (nbatch vectors)
+  mg::DevBuf<mg::Cx<float>> cl_Yr;             // A M in FP32 as row-major blocks
+  mg::DevBuf<int> dl_ctl;                      // device-driven outer loop: counters, residual state, w
+  mg::DevBuf<double> dl_st;
+  mg::DevBuf<mg::Cx<double>> dl_w;
   mg::DevBuf<int> cg_info;
   mg::DevBuf<unsigned int> cg_bar;
   mg::DevBuf<int> cg_out;  // [0] iterations, [1] timeout flag, [2] solves above tolerance
@@ -384,7 +388,7 @@ static void coarsest_solve64(mg_ctx &c, const Cx<double> *b, Cx<double> *x, int 
   const Cx<double> *Minv = slot == 0 ? c.cg_Minv.p : c.bMinv.p + (slot - 1) * m2;
   const Cx<double> *Yt = slot == 0 ? c.cg_Yt.p : c.bYt.p + (slot - 1) * 5 * m2;
   if (c.cg_cluster && slot == 0)
-    launch_coarsest_gcr_cluster(c.cg_Yt32.p, Minv, L.geo, 1, b, x, c.cl_rpub.p, c.cl_ypub.p, c.p.coarsest_tol,
+    launch_coarsest_gcr_cluster(c.cl_Yr.p, Minv, L.geo, 1, b, x, c.cl_rpub.p, c.cl_ypub.p, c.p.coarsest_tol,
                                 c.p.coarsest_restart, c.p.coarsest_max_iter, c.cg_out.p, c.cg_rel.p, c.s);
   else if (c.cg_smem)
     launch_coarsest_gcr_smem(Yt, slot == 0 ? c.cg_Yt32.p : nullptr, Minv, L.geo, b, x, c.cr.p, c.cg_y.p,
@@ -407,7 +411,7 @@ static void coarsest_vectors64(mg_ctx &c, const Cx<double> *b, Cx<double> *x, in
   const bool batch = c.cur_shift != nullptr;
   if (c.cg_cluster && nvec > 1 && !batch) {
     // every vector at the context mass: one cluster per vector, all in one launch
-    launch_coarsest_gcr_cluster(c.cg_Yt32.p, c.cg_Minv.p, L.geo, nvec, b, x, c.cl_rpub.p, c.cl_ypub.p,
+    launch_coarsest_gcr_cluster(c.cl_Yr.p, c.cg_Minv.p, L.geo, nvec, b, x, c.cl_rpub.p, c.cl_ypub.p,
                                 c.p.coarsest_tol, c.p.coarsest_restart, c.p.coarsest_max_iter, c.cg_out.p, c.cg_rel.p,
                                 c.s);
     return;
@@ -723,6 +727,177 @@ static void outer_fgcr_batch(mg_ctx &c, int nb, const Cx<double> *b, Cx<double> 
 }
 
 // ---------------------------------------------------------------------------
+// Outer flexible GCR driven on the device: one iteration (V-cycle, D apply, Gram-Schmidt
+// reduction, update, control) is captured into the body of a conditional WHILE graph node,
+// which the GPU replays until the control kernel clears the condition; the loops of several
+// contexts sit side by side in one graph, so one launch runs all their solves with no host
+// round trip per iteration. Gram-Schmidt is classical, one pass (the host-driven loop adds a
+// second pass on cancellation); a restart starts a new basis from the recurrence residual,
+// and the true residual b - D x is recomputed after the launch (relaunching if it misses tol).
+// ---------------------------------------------------------------------------
+struct DevSolve {
+  mg_ctx *c = nullptr;
+  const Cx<double> *b = nullptr;
+  Cx<double> *x = nullptr;
+  double bn2 = 0.0;
+  GcrOut out;
+  long long kernels_per_it = 0, apps_per_it[MG_MAX_LEVELS] = {0, 0, 0, 0};
+};
+
+static void devloop_buffers(mg_ctx &c) {
+  if (c.dl_ctl.p != nullptr) return;
+  c.dl_ctl.alloc(4);
+  c.dl_st.alloc(4);
+  c.dl_w.alloc(c.lv[0].n);
+  pool_ready();
+}
+
+// counters and residual state for a (re)start from the residual now in c.orr (|r|^2 = rn2)
+static void devloop_arm(mg_ctx &c, double rn2, double tol2, int iters_done) {
+  const int ctl[4] = {iters_done, 0, 0, 0};
+  const double st[4] = {rn2, tol2, rn2, 0.0};
+  MG_CUDA(cudaMemcpyAsync(c.dl_ctl.p, ctl, sizeof(ctl), cudaMemcpyHostToDevice, c.s));
+  MG_CUDA(cudaMemcpyAsync(c.dl_st.p, st, sizeof(st), cudaMemcpyHostToDevice, c.s));
+  MG_CUDA(cudaStreamSynchronize(c.s));  // the host arrays are stack memory
+}
+
+// |v|^2 of a fine FP64 vector, read back
+static double fine_norm2(mg_ctx &c, const Cx<double> *v) {
+  double *dots = c.scal.p + kSlotOuter;
+  launch_norm2<double>(v, c.lv[0].n, dots, c.ws, c.s);
+  MG_CUDA(cudaMemcpyAsync(c.host, dots, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+  MG_CUDA(cudaStreamSynchronize(c.s));
+  return c.host[0];
+}
+
+static void devloop_capture(DevSolve &d, cudaGraph_t body, cudaGraphConditionalHandle h) {
+  mg_ctx &c = *d.c;
+  Level &F = c.lv[0];
+  const long long n = F.n;
+  const long long l0 = g_launches.load();
+  long long a0[MG_MAX_LEVELS];
+  for (int l = 0; l < MG_MAX_LEVELS; ++l) a0[l] = c.apps[l];
+  MG_CUDA(cudaStreamBeginCaptureToGraph(c.s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  bool ok = true;
+  try {
+    if (c.p.precision == MG_FP32) {
+      launch_convert<float, double>(c.orr.p, F.w32.b.p, n, c.s);
+      vcycle<float>(c, 0, F.w32.b.p, c.z32.p);
+      launch_convert<double, float>(c.z32.p, c.z64.p, n, c.s);
+    } else {
+      vcycle<double>(c, 0, c.orr.p, c.z64.p);
+    }
+    apply_op<double>(c, 0, c.z64.p, c.dl_w.p);
+    double *dots = c.scal.p + kSlotOuter;
+    launch_gcr_dots_devk(c.oW.p, c.dl_w.p, c.orr.p, c.dl_ctl.p, c.p.gcr_restart, n, dots, c.ws, c.s);
+    launch_gcr_update_devk(c.oW.p, c.oZ.p, c.dl_w.p, c.z64.p, c.dl_ctl.p, dots, c.dl_st.p, d.x, c.orr.p, n, c.s);
+    launch_gcr_control(c.dl_ctl.p, c.dl_st.p, c.p.gcr_restart, c.p.max_iter, h, c.s);
+  } catch (const Error &) {
+    ok = false;
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c.s, &g);
+  d.kernels_per_it = g_launches.load() - l0;
+  g_launches.store(l0);
+  for (int l = 0; l < MG_MAX_LEVELS; ++l) {
+    d.apps_per_it[l] = c.apps[l] - a0[l];
+    c.apps[l] = a0[l];
+  }
+  if (!ok || e != cudaSuccess) {
+    (void)cudaGetLastError();
+    fail(MG_ERR_CUDA, std::string("capture of the device-driven GCR iteration failed: ") + cudaGetErrorString(e));
+  }
+}
+
+// one graph with a WHILE loop per unfinished solve, launched once on stream ls
+static void devloop_launch(std::vector<DevSolve *> &act, cudaStream_t ls) {
+  cudaGraph_t top = nullptr;
+  MG_CUDA(cudaGraphCreate(&top, 0));
+  cudaGraphExec_t exec = nullptr;
+  try {
+    for (DevSolve *d : act) {
+      cudaGraphConditionalHandle h;
+      MG_CUDA(cudaGraphConditionalHandleCreate(&h, top, 1, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams np = {};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      cudaGraphNode_t node;
+      MG_CUDA(cudaGraphAddNode(&node, top, nullptr, nullptr, 0, &np));
+      devloop_capture(*d, np.conditional.phGraph_out[0], h);
+    }
+    MG_CUDA(cudaGraphInstantiate(&exec, top, 0));
+    for (DevSolve *d : act) {  // the launch stream waits for every context's queued work
+      MG_CUDA(cudaEventRecord(d->c->ev, d->c->s));
+      MG_CUDA(cudaStreamWaitEvent(ls, d->c->ev, 0));
+    }
+    MG_CUDA(cudaGraphLaunch(exec, ls));
+    MG_CUDA(cudaStreamSynchronize(ls));
+  } catch (...) {
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(top);
+    throw;
+  }
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(top);
+}
+
+static void devloop_solve(std::vector<DevSolve> &v, double tol) {
+  for (DevSolve &d : v) {
+    mg_ctx &c = *d.c;
+    check_fresh(c);
+    devloop_buffers(c);
+    for (long long &a : c.apps) a = 0;
+    collect_coarsest(c);
+    const long long n = c.lv[0].n;
+    launch_zero<double>(d.x, n, c.s);
+    launch_copy<double>(d.b, c.orr.p, n, c.s);
+    d.bn2 = fine_norm2(c, d.b);
+    d.out = GcrOut{};
+    if (!(d.bn2 > 0.0)) {
+      d.out.converged = true;
+      continue;
+    }
+    devloop_arm(c, d.bn2, tol * tol * d.bn2, 0);
+  }
+  for (int round = 0; round < 8; ++round) {
+    std::vector<DevSolve *> act;
+    for (DevSolve &d : v)
+      if (!d.out.converged && d.out.iters < d.c->p.max_iter) act.push_back(&d);
+    if (act.empty()) break;
+    devloop_launch(act, act[0]->c->s);
+    for (DevSolve *d : act) {
+      mg_ctx &c = *d->c;
+      MG_CUDA(cudaEventRecord(act[0]->c->ev, act[0]->c->s));
+      MG_CUDA(cudaStreamWaitEvent(c.s, act[0]->c->ev, 0));
+      int ctl[4];
+      MG_CUDA(cudaMemcpyAsync(ctl, c.dl_ctl.p, sizeof(ctl), cudaMemcpyDeviceToHost, c.s));
+      MG_CUDA(cudaStreamSynchronize(c.s));
+      const long long done = ctl[0] - d->out.iters;
+      d->out.iters = ctl[0];
+      g_launches.fetch_add(done * d->kernels_per_it);
+      for (int l = 0; l < MG_MAX_LEVELS; ++l) c.apps[l] += done * d->apps_per_it[l];
+      // true residual (defect correction)
+      apply_op<double>(c, 0, d->x, c.orr.p, d->b, -1.0, 1.0);
+      const double rn2 = fine_norm2(c, c.orr.p);
+      if (!std::isfinite(rn2)) fail(MG_ERR_NAN, "outer GCR (device loop): NaN in the true residual");
+      d->out.rel = std::sqrt(rn2 / d->bn2);
+      d->out.converged = d->out.rel <= tol;
+      if (!d->out.converged) {
+        if (ctl[2] == 3 && done <= 1) d->out.iters = c.p.max_iter;  // no progress possible: give up
+        else devloop_arm(c, rn2, tol * tol * d->bn2, ctl[0]);
+      }
+    }
+  }
+  for (DevSolve &d : v) {
+    mg_ctx &c = *d.c;
+    c.coarsest_iters = collect_coarsest(c);
+    if (!c.use_lu) c.apps[c.p.levels - 1] += c.coarsest_iters;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // setup
 // ---------------------------------------------------------------------------
 static void prepare_coarsest(mg_ctx &c) {
@@ -731,6 +906,7 @@ static void prepare_coarsest(mg_ctx &c) {
   if (!c.use_lu) {
     prepare_coarsest_gcr(L.Y64.p, L.geo, L.nint, c.cg_Minv.p, c.cg_Yt.p, c.cg_work.p, c.cg_info.p, c.s);
     if (c.cg_Yt32.p != nullptr) launch_convert<float, double>(c.cg_Yt.p, c.cg_Yt32.p, c.cg_Yt.n, c.s);
+    if (c.cl_Yr.p != nullptr) launch_transpose_blocks8(c.cg_Yt32.p, c.cl_Yr.p, (long long)c.cg_Yt.n / 64, c.s);
     int info = 0;
     MG_CUDA(cudaMemcpyAsync(&info, c.cg_info.p, sizeof(int), cudaMemcpyDeviceToHost, c.s));
     MG_CUDA(cudaStreamSynchronize(c.s));
@@ -1012,6 +1188,7 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
         c->cg_cluster)
       c->cg_Yt32.alloc(c->cg_Yt.n);
     if (c->cg_cluster) {
+      c->cl_Yr.alloc(c->cg_Yt.n);
       c->cl_rpub.alloc((size_t)c->nbatch * Cst.n);
       c->cl_ypub.alloc((size_t)c->nbatch * Cst.n);
     }
@@ -1560,6 +1737,58 @@ int mg_save_setup(mg_ctx *c, const char *path) {
     ok = (std::fclose(f) == 0) && ok;
     if (!ok) fail(MG_ERR_UNSUPPORTED, std::string("writing ") + path + " failed");
   });
+}
+
+int mg_solve_multi(int count, mg_ctx *const *ctx, const void *const *chi, void *const *psi, double tol,
+                   mg_stats *st) {
+  int status = MG_OK;
+  int rc = guarded([&] {
+    if (count < 1 || !ctx || !chi || !psi) fail(MG_ERR_INVALID_ARG, "need count >= 1 and non-null arrays");
+    int dev0 = -1;
+    std::vector<DevSolve> v(count);
+    for (int i = 0; i < count; ++i) {
+      need_ctx(ctx[i]);
+      need_ptr(chi[i]);
+      need_ptr(psi[i]);
+      if (ctx[i]->e4) fail(MG_ERR_UNSUPPORTED, "the device-driven multi-solve is built for d = 2");
+      for (int j = 0; j < i; ++j)
+        if (ctx[j] == ctx[i]) fail(MG_ERR_INVALID_ARG, "a context appears twice (its buffers would be shared)");
+      cudaPointerAttributes pa{};
+      if (cudaPointerGetAttributes(&pa, psi[i]) != cudaSuccess || pa.type != cudaMemoryTypeDevice) {
+        (void)cudaGetLastError();
+        fail(MG_ERR_INVALID_ARG, "psi must be device memory");
+      }
+      if (dev0 < 0) dev0 = pa.device;
+      if (pa.device != dev0) fail(MG_ERR_INVALID_ARG, "all contexts must be on one device");
+      v[i].c = ctx[i];
+      v[i].b = static_cast<const Cx<double> *>(chi[i]);
+      v[i].x = static_cast<Cx<double> *>(psi[i]);
+    }
+    EventPair ev;
+    ev.start(v[0].c->s);
+    devloop_solve(v, tol);
+    const float ms = ev.stop(v[0].c->s);
+    for (int i = 0; i < count; ++i) {
+      mg_ctx &c = *v[i].c;
+      if (!v[i].out.converged) status = MG_ERR_NOT_CONVERGED;
+      if (!st) continue;
+      st[i].iters = v[i].out.iters;
+      st[i].converged = v[i].out.converged ? 1 : 0;
+      st[i].true_rel_residual = v[i].out.rel;
+      for (int l = 0; l < MG_MAX_LEVELS; ++l) st[i].level_apps[l] = c.apps[l];
+      st[i].coarsest_iters = c.coarsest_iters;
+      st[i].ms = ms;
+      st[i].graphs = 1;
+      st[i].setup_s = c.setup_s;
+      st[i].solve_s = ms * 1e-3;
+      st[i].fine_D_apps = c.apps[0];
+    }
+  });
+  if (rc == MG_OK && status != MG_OK) {
+    t_last_error = "a system did not converge within max_iter";
+    return status;
+  }
+  return rc;
 }
 
 int mg_convergence_rate(mg_ctx *c, int steps, uint64_t seed, double *rate) {

@@ -1,0 +1,65 @@
+"""mg_solve_multi: the solves of several contexts (different lattices, configurations, masses and
+precisions) in one graph launch, each outer flexible GCR running as a conditional WHILE loop on the
+device. Every solution meets the tolerance by the oracle's FP64 true residual, with outer iteration
+counts close to the host-driven loop's."""
+import numpy as np
+import pytest
+
+import inputs
+from oracle import wilson
+from oracle.lattice import Lattice
+from tests._util import to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(L0, L1, beta, seed):
+    th, _ = inputs.metropolis_u1_2d(L0, L1, beta, 200, seed=seed)
+    return inputs.links_from_angles(th)
+
+
+def test_multi_solve_several_configurations():
+    import torch
+    import paper_0707_4018_gb300 as mg
+    specs = [((64, 64), 6.0, 0.03, 1, 3), ((32, 64), 3.0, 0.05, 0, 2), ((128, 128), 10.0, 0.02, 1, 3),
+             ((64, 64), 6.0, 0.1, 1, 2)]
+    ctxs, Us, chis, psis, single = [], [], [], [], []
+    for i, (dims, beta, m, prec, levels) in enumerate(specs):
+        U = _case(dims[0], dims[1], beta, 100 + i)
+        blocks = [(4, 4), (2, 2)][: levels - 1]
+        p = mg.mg_default_params(levels=levels, blocks=blocks, Nv=[8] * (levels - 1), precision=prec, n_pass=3,
+                                 coarsest_tol=0.2, coarsest_lu_max=0 if levels == 3 else 2048)
+        ctx = mg.Context.setup(to_dev(U), m, dims, p)
+        chi = to_dev(inputs.gaussian_source(dims[0], dims[1], seed=7 + i))
+        ref = torch.empty_like(chi)
+        single.append(ctx.solve(chi, ref, 1e-10))
+        ctxs.append(ctx)
+        Us.append(U)
+        chis.append(chi)
+        psis.append(torch.empty_like(chi))
+    st = mg.solve_multi(ctxs, chis, psis, 1e-10)
+    for i, (dims, beta, m, prec, levels) in enumerate(specs):
+        res = np.linalg.norm(to_host(chis[i]) - wilson.apply_D(Us[i], to_host(psis[i]), m, Lattice(dims)))
+        assert st[i]["converged"] and res / np.linalg.norm(to_host(chis[i])) <= 1e-10, (i, st[i])
+        assert st[i]["fine_D_apps"] > 0 and st[i]["graphs"]
+        assert abs(st[i]["iters"] - single[i]["iters"]) <= max(3, single[i]["iters"] // 5), (st[i]["iters"],
+                                                                                            single[i]["iters"])
+    # a second call on the same contexts gives the same iterates (deterministic loop)
+    psis2 = [torch.empty_like(c) for c in chis]
+    st2 = mg.solve_multi(ctxs, chis, psis2, 1e-10)
+    for i in range(len(specs)):
+        assert st2[i]["iters"] == st[i]["iters"] and torch.equal(psis2[i], psis[i])
+    for c in ctxs:
+        c.close()
+
+
+def test_multi_solve_rejects_repeated_context():
+    import torch
+    import paper_0707_4018_gb300 as mg
+    U = _case(32, 32, 6.0, 5)
+    ctx = mg.Context.setup(to_dev(U), 0.05, (32, 32), mg.mg_default_params(n_pass=2))
+    chi = to_dev(inputs.gaussian_source(32, 32, seed=1))
+    with pytest.raises(mg.MGError) as e:
+        mg.solve_multi([ctx, ctx], [chi, chi], [torch.empty_like(chi), torch.empty_like(chi)], 1e-10)
+    assert e.value.code == 1
+    ctx.close()
