@@ -440,6 +440,81 @@ def learned_setup_eval(n_train: int = LEARN_TRAIN, n_eval: int = LEARN_EVAL, n_b
 
 ROOT_NET_SEED = 20070704
 
+C2_FIELDS, C2_RHS, C2_SIZES, C2_WID = 32, 16, (128, 256, 512, 1024), 2
+C2_WAVE_SITES = 4 * 1024 * 1024  # sites set up and solved together (device memory of the batched bases)
+
+
+def config2_sizes(n_fields: int = C2_FIELDS):
+    """Lattice sizes of the many-configuration batch: uniform draws from {128, 256, 512, 1024}
+    (the inputs module's counter-based uniforms, key root seed + 2)."""
+    u = inputs.uniform(n_fields, inputs.ROOT_SEED + C2_WID, 0xC2)
+    return [C2_SIZES[min(3, int(x * 4))] for x in u]
+
+
+def config2_batch(n_fields: int = C2_FIELDS, nrhs: int = C2_RHS, precision: int = 1):
+    """Many configurations x many right-hand sides: n_fields beta 6 fields with sizes from
+    config2_sizes, nrhs Gaussian sources each, m = m_c + 0.02 (m_c of the stored 128^2 field for
+    128^2 and the 256^2 calibration above). Fields are processed in waves of at most 4 M sites: the
+    wave's setups run at once (mg_setup_batch), then every solve of the wave (fields x sources) runs
+    from one graph launch (mg_solve_multi; each context's nrhs vectors in lockstep inside its WHILE
+    loop, the coarse residual applies on tensor cores). Timed end to end including setup."""
+    import torch
+    import paper_0707_4018_gb300 as mg
+    table = mcrit_table()
+    sizes = config2_sizes(n_fields)
+    mc = {128: table["w2_L128_b6"]["m_crit"]}
+    for Lf in C2_SIZES[1:]:
+        mc[Lf] = table["w1_L256_b6"]["m_crit"]
+    fields = []
+    t0 = time.time()
+    for Lf in sorted(set(sizes)):
+        idx = [i for i, s in enumerate(sizes) if s == Lf]
+        seeds = [inputs.member_seed(C2_WID, Lf, 6.0, i) for i in idx]
+        th, _ = inputs.metropolis_u1_2d_gpu(Lf, Lf, [6.0] * len(idx), seeds, 2000)
+        for k, i in enumerate(idx):
+            U = torch.from_numpy(inputs.links_from_angles(th[k])).cuda()
+            chi = torch.stack([torch.from_numpy(inputs.gaussian_source(Lf, Lf, seed=seeds[k], index=v))
+                               for v in range(nrhs)]).cuda()
+            fields.append(dict(i=i, L=Lf, U=U, chi=chi, psi=torch.empty_like(chi)))
+    gen_s = time.time() - t0
+    fields.sort(key=lambda f: -f["L"])
+    waves, cur, sites = [], [], 0
+    for f in fields:
+        if cur and sites + f["L"] ** 2 > C2_WAVE_SITES:
+            waves.append(cur)
+            cur, sites = [], 0
+        cur.append(f)
+        sites += f["L"] ** 2
+    waves.append(cur)
+    p = mg.mg_default_params(levels=3, blocks=[(4, 4), (2, 2)], Nv=[8, 8], precision=precision, coarsest_tol=0.2,
+                             max_rhs=nrhs, gcr_restart=8)
+    stats = []
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for wave in waves:
+        ctxs = mg.Context.setup_batch([f["U"] for f in wave], [mc[f["L"]] + 0.02 for f in wave],
+                                      [(f["L"], f["L"]) for f in wave], [p] * len(wave))
+        st = mg.solve_multi(ctxs, [f["chi"] for f in wave], [f["psi"] for f in wave], TOL,
+                            nrhs=[nrhs] * len(wave), raise_on_fail=False)
+        stats += st
+        for c in ctxs:
+            c.close()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    n_solves = n_fields * nrhs
+    return {"fields": n_fields, "sources_per_field": nrhs, "sizes": {str(Lf): sizes.count(Lf) for Lf in C2_SIZES},
+            "waves": len(waves), "solves": n_solves, "value": n_solves / (ms * 1e-3),
+            "unit": "solves/s (incl. setup)", "ms": ms, "gen_s": gen_s,
+            "all_converged": all(s["converged"] for s in stats),
+            "worst_true_rel_residual": max(s["true_rel_residual"] for s in stats),
+            "mean_iters": float(np.mean([s["iters"] for s in stats])),
+            "precision": "FP64 outer GCR (device-driven, gcr_restart 8), FP32 cycles, coarse residual applies "
+                         "on tensor cores (BF16 operands, FP32 sums)"}
+
 
 def dslash_roofline(precision: int, L_big: int = 4096, iters: int = 20):
     """Fine Wilson apply alone on a lattice far larger than L2: algorithmic bytes / time."""
@@ -837,6 +912,9 @@ def run_only(case: str):
     if case == "mixed-sizes":
         print(json.dumps({"case": case, **mixed_sizes()}))
         return
+    if case == "config2":
+        print(json.dumps({"case": case, **config2_batch()}))
+        return
     if case == "learned":
         print(json.dumps({"case": case, **learned_setup_eval()}))
         return
@@ -976,9 +1054,11 @@ def main():
     ap.add_argument("--threads", action="store_true",
                     help="solve with one host thread and host-driven loop per solve instead of one graph launch")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned near-null setup evaluation")
+    ap.add_argument("--no-config2", action="store_true", help="skip the many-configuration x many-source batch")
     ap.add_argument("--only", default=None, choices=["dslash-f32", "dslash-f64", "dslash4-f32", "dslash4-f64", "solve", "vcycle",
                                                       "transfer", "coarse-tc", "coarse-tc4", "su3", "su3-prof",
-                                                      "su3-batch-prof", "mixed-sizes", "learned", "large"],
+                                                      "su3-batch-prof", "mixed-sizes", "learned", "large",
+                                                      "config2"],
                     help="profiling cases: the Dslash timing loop alone (2d, or 4d SU(3)), one beta's setup + 3 solves, "
                          "25 mixed-precision V-cycles after one beta's setup, or 5 V-cycles on a 1024^2 "
                          "hierarchy (fine level larger than L2, for the restriction and prolongation), or the "
@@ -1039,6 +1119,7 @@ def main():
     cr = coarsest_roofline(fields_dev)
     large = config1_large(flush) if (world_of(d) == 1 or rank == 0) and not args.no_large else None
     learned = learned_setup_eval() if (world_of(d) == 1 or rank == 0) and not args.no_learned else None
+    many = config2_batch() if (world_of(d) == 1 or rank == 0) and not args.no_config2 else None
 
     cpu = None
     if rank == 0 and world_of(d) == 1 and not args.no_cpu:
@@ -1077,6 +1158,7 @@ def main():
         "mixed_sizes": mix,
         "config1_1024": large,
         "learned_setup": learned,
+        "config2_many_configs": many,
     }
     print(json.dumps(line), flush=True)
 

@@ -176,22 +176,26 @@ int mg_solve(mg_ctx *ctx, const void *chi, void *psi, int nrhs, double tol, mg_s
 int mg_solve_batch(mg_ctx *ctx, int nrhs, const void *chi, void *psi, const double *mass, double tol,
                    mg_stats *st);
 
-/* One system D_i psi_i = chi_i per context (2d contexts of any sizes, configurations and
- * masses; the paper: many gauge configurations, each with its own setup), all solved by ONE
- * launch of one CUDA graph: each context's outer flexible GCR runs as a conditional WHILE
- * node on the device (V-cycle, D apply, Gram-Schmidt reduction, update and a control kernel
- * that decides whether the loop goes on), the loops of all contexts side by side, with no
- * host round trip per iteration. Gram-Schmidt is classical with one pass; a restart starts a
- * new basis from the recurrence residual. After the launch the true residual b - D x of
- * every system is recomputed in FP64; a system that misses tol (rounding of the recurrence)
- * is relaunched from its true residual.
- *   count      number of systems (>= 1); every ctx[i] distinct, all on one device
- *   chi, psi   arrays of device complex128 [x][s] pointers (psi overwritten, guess 0)
- *   st         NULL or count entries (ms / solve_s: the whole call)
+/* nrhs[i] systems D_i psi = chi per context (2d contexts of any sizes, configurations and
+ * masses; the paper: many gauge configurations, each with its own setup, and many right-hand
+ * sides per setup), all solved by ONE launch of one CUDA graph: each context's outer flexible
+ * GCR runs as a conditional WHILE node on the device (batched V-cycle, D apply, Gram-Schmidt
+ * reduction, update and a control kernel that decides whether the loop goes on; the nrhs[i]
+ * vectors of a context in lockstep, each stopping on its own residual), the loops of all
+ * contexts side by side, with no host round trip per iteration. Gram-Schmidt is classical
+ * with one pass; a restart starts a new basis from the recurrence residual. After the launch
+ * the true residual b - D x of every system is recomputed in FP64; a system that misses tol
+ * (rounding of the recurrence) is relaunched from its true residual.
+ *   count      number of contexts (>= 1); every ctx[i] distinct, all on one device
+ *   nrhs       NULL (one system each) or count entries in [1, max_rhs of the context]; all
+ *              vectors of a context are solved at its mass
+ *   chi, psi   arrays of device complex128 pointers, context i: nrhs[i] vectors [v][x][s]
+ *              back to back (psi overwritten, initial guess 0)
+ *   st         NULL or sum(nrhs) entries, context by context (ms / solve_s: the whole call)
  * Returns NOT_CONVERGED if any system missed tol within its max_iter, UNSUPPORTED for
  * d = 4 contexts. */
-int mg_solve_multi(int count, mg_ctx *const *ctx, const void *const *chi, void *const *psi, double tol,
-                   mg_stats *st);
+int mg_solve_multi(int count, mg_ctx *const *ctx, const int *nrhs, const void *const *chi, void *const *psi,
+                   double tol, mg_stats *st);
 
 /* Reuse the near-null vectors for another mass (paper: setup at the lightest
  * mass only, reused for heavier ones): rebuilds every Galerkin operator with

@@ -92,7 +92,7 @@ def load():
                                  P(D), VP]),
         "mg_convergence_rate": (I, [ctxp, I, ctypes.c_uint64, P(D)]),
         "mg_alu_peak": (I, [I, P(D), VP]),
-        "mg_solve_multi": (I, [I, P(ctxp), P(VP), P(VP), D, P(mg_stats)]),
+        "mg_solve_multi": (I, [I, P(ctxp), P(I), P(VP), P(VP), D, P(mg_stats)]),
         "mg_solve_batch": (I, [ctxp, I, VP, VP, P(D), D, P(mg_stats)]),
         "mg_coarse_apply_mrhs": (I, [ctxp, I, I, VP, VP, I]),
         "mg_update_mass": (I, [ctxp, D]),
@@ -230,19 +230,22 @@ def mg_selftest_barrier(missing_arrivals: int, stream=None):
     _check(load().mg_selftest_barrier(int(missing_arrivals), _stream(stream)))
 
 
-def solve_multi(contexts, chis, psis, tol: float, raise_on_fail: bool = True) -> list:
-    """mg_solve_multi: psis[i] = D_i^{-1} chis[i] for every context, all loops in one graph launch."""
+def solve_multi(contexts, chis, psis, tol: float, nrhs=None, raise_on_fail: bool = True) -> list:
+    """mg_solve_multi: psis[i] = D_i^{-1} chis[i] for every context (nrhs[i] vectors each, default 1),
+    all outer loops in one graph launch; returns the stats of every vector, context by context."""
     n = len(contexts)
     if not (len(chis) == len(psis) == n) or n < 1:
-        raise ValueError("one source and one solution per context")
+        raise ValueError("one source and one solution array per context")
+    nr = [1] * n if nrhs is None else [int(k) for k in nrhs]
     hs = (ctypes.c_void_p * n)(*[c._need().value if hasattr(c._need(), "value") else c._need() for c in contexts])
-    cp = (ctypes.c_void_p * n)(*[_ptr(chis[i], torch.complex128, contexts[i].n0).value for i in range(n)])
-    pp = (ctypes.c_void_p * n)(*[_ptr(psis[i], torch.complex128, contexts[i].n0).value for i in range(n)])
-    st = (mg_stats * n)()
-    code = load().mg_solve_multi(n, hs, cp, pp, float(tol), st)
+    cp = (ctypes.c_void_p * n)(*[_ptr(chis[i], torch.complex128, contexts[i].n0 * nr[i]).value for i in range(n)])
+    pp = (ctypes.c_void_p * n)(*[_ptr(psis[i], torch.complex128, contexts[i].n0 * nr[i]).value for i in range(n)])
+    na = (ctypes.c_int * n)(*nr)
+    st = (mg_stats * sum(nr))()
+    code = load().mg_solve_multi(n, hs, na, cp, pp, float(tol), st)
     if code != 0 and (raise_on_fail or code != 4):
         _check(code)
-    return [st[i].as_dict() for i in range(n)]
+    return [st[i].as_dict() for i in range(sum(nr))]
 
 
 def mg_alu_peak(precision: int, stream=None) -> float:

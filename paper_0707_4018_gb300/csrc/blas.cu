@@ -452,3 +452,160 @@ void launch_gcr_control(int *ctl, double *st, int restart, int max_iter, cudaGra
 }
 
 }  // namespace mg
+
+// ---------------------------------------------------------------------------
+// Device-driven outer GCR over a batch of nb vectors in lockstep (one WHILE loop per context):
+// act[v] says whether vector v still iterates (it stops on its residual estimate or on a
+// breakdown); stv[2 v] its |r|^2 estimate, stv[2 v + 1] its tol^2 |b_v|^2; coef[4 v ..] the
+// update coefficients (inv, alpha re, alpha im, mode: 1 update, 0 leave alone). Dots are laid out
+// per vector with stride 2 (restart + 3), as the host-driven batched loop's.
+// ---------------------------------------------------------------------------
+namespace mg {
+
+__global__ void copy_active_kernel(const Cx<double> *__restrict__ x, Cx<double> *__restrict__ y, long long n,
+                                   const int *__restrict__ act) {
+  const long long off = blockIdx.y * n;
+  const bool on = act[blockIdx.y] != 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[off + i] = on ? x[off + i] : mk(0.0, 0.0);
+}
+
+// vector v = blockIdx.z, row = blockIdx.y < restart + 3 (rows above k + 2 empty), k = ctl[1]
+__global__ void __launch_bounds__(kReduceThreads) gcr_dots_batch_devk_kernel(
+    const Cx<double> *__restrict__ W, const Cx<double> *__restrict__ w, const Cx<double> *__restrict__ r,
+    const int *__restrict__ ctl, int nb, int restart, long long n, double *partials, double *out,
+    unsigned int *ticket) {
+  __shared__ double sh[32 * 2];
+  const int row = blockIdx.y, v = blockIdx.z, rows = restart + 3, k = ctl[1];
+  double acc[2] = {0.0, 0.0};
+  if (row <= k + 2) {
+    const Cx<double> *wv = w + (long long)v * n;
+    const Cx<double> *rv = r + (long long)v * n;
+    const Cx<double> *a = row < k ? W + ((long long)row * nb + v) * n : (row == k + 2 ? rv : wv);
+    const Cx<double> *b = row > k ? rv : wv;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+      const Cx<double> x = a[i], y = b[i];
+      acc[0] += x.re * y.re + x.im * y.im;
+      acc[1] += x.re * y.im - x.im * y.re;
+    }
+  }
+  const long long slot = (long long)v * rows + row;
+  grid_finish<2>(acc, partials + slot * 2 * gridDim.x, out + 2 * slot, ticket + slot, sh);
+}
+
+// one thread per vector: classical Gram-Schmidt coefficients, breakdown and convergence
+__global__ void gcr_coef_batch_kernel(const double *__restrict__ dots, const int *__restrict__ ctl, int nb,
+                                      int restart, int *__restrict__ act, double *__restrict__ stv,
+                                      double *__restrict__ coef) {
+  const int v = threadIdx.x;
+  if (v >= nb) return;
+  const int k = ctl[1];
+  const double *d = dots + (long long)v * 2 * (restart + 3);
+  double inv = 0.0, are = 0.0, aim = 0.0, mode = 0.0;
+  if (act[v]) {
+    const double nw0 = d[2 * k];
+    double nw2 = nw0;
+    for (int j = 0; j < k; ++j) nw2 -= d[2 * j] * d[2 * j] + d[2 * j + 1] * d[2 * j + 1];
+    if (nw2 > 1e-28 * nw0) {
+      inv = 1.0 / sqrt(nw2);
+      are = d[2 * k + 2] * inv;
+      aim = d[2 * k + 3] * inv;
+      mode = 1.0;
+      const double rn2 = fmax(d[2 * k + 4] - (are * are + aim * aim), 0.0);
+      stv[2 * v] = rn2;
+      if (rn2 <= stv[2 * v + 1]) act[v] = 0;
+    } else {
+      act[v] = 0;  // breakdown: this vector waits for the true residual after the launch
+    }
+  }
+  coef[4 * v] = inv;
+  coef[4 * v + 1] = are;
+  coef[4 * v + 2] = aim;
+  coef[4 * v + 3] = mode;
+}
+
+// W_{k,v} = (w_v - sum_j beta_j W_{j,v}) inv, Z likewise from z_v; x_v += alpha Z_{k,v}; r_v -= alpha W_{k,v}
+__global__ void gcr_update_batch_devk_kernel(Cx<double> *__restrict__ W, Cx<double> *__restrict__ Z,
+                                             const Cx<double> *__restrict__ w, const Cx<double> *__restrict__ z,
+                                             const int *__restrict__ ctl, int nb, int restart,
+                                             const double *__restrict__ dots, const double *__restrict__ coef,
+                                             Cx<double> *__restrict__ x, Cx<double> *__restrict__ r, long long n) {
+  const int v = blockIdx.y, k = ctl[1];
+  if (coef[4 * v + 3] == 0.0) return;
+  const double *beta = dots + (long long)v * 2 * (restart + 3);
+  const double inv = coef[4 * v];
+  const Cx<double> alpha = mk(coef[4 * v + 1], coef[4 * v + 2]);
+  Cx<double> *Wk = W + ((long long)k * nb + v) * n, *Zk = Z + ((long long)k * nb + v) * n;
+  const Cx<double> *wv = w + (long long)v * n, *zv = z + (long long)v * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    Cx<double> wi = wv[i], zi = zv[i];
+    for (int j = 0; j < k; ++j) {
+      const Cx<double> bj = mk(-beta[2 * j], -beta[2 * j + 1]);
+      const long long o = ((long long)j * nb + v) * n + i;
+      cmac(wi, bj, W[o]);
+      cmac(zi, bj, Z[o]);
+    }
+    wi = inv * wi;
+    zi = inv * zi;
+    Wk[i] = wi;
+    Zk[i] = zi;
+    cmac(x[(long long)v * n + i], alpha, zi);
+    Cx<double> ri = r[(long long)v * n + i];
+    cmac(ri, mk(-alpha.re, -alpha.im), wi);
+    r[(long long)v * n + i] = ri;
+  }
+}
+
+__global__ void gcr_control_batch_kernel(int *ctl, const int *act, int nb, int restart, int max_iter,
+                                         cudaGraphConditionalHandle handle) {
+  const int it = ctl[0] + 1;
+  int k = ctl[1] + 1;
+  if (k == restart) k = 0;
+  ctl[0] = it;
+  ctl[1] = k;
+  int any = 0;
+  for (int v = 0; v < nb; ++v) any |= act[v];
+  const int reason = !any ? 1 : (it >= max_iter ? 2 : 0);
+  ctl[2] = reason;
+  cudaGraphSetConditional(handle, reason == 0 ? 1u : 0u);
+}
+
+void launch_copy_active(const Cx<double> *x, Cx<double> *y, long long n, int nb, const int *act, cudaStream_t s) {
+  copy_active_kernel<<<dim3(stream_grid(n), nb), 256, 0, s>>>(x, y, n, act);
+  MG_LAUNCHED();
+}
+
+void launch_gcr_dots_batch_devk(const Cx<double> *W, const Cx<double> *w, const Cx<double> *r, const int *ctl,
+                                int nb, int restart, long long n, double *out, const ReduceWs &ws, cudaStream_t s) {
+  const int rows = restart + 3;
+  int per = (int)(ws.capacity / (2LL * rows * nb));
+  if (per > ws.max_blocks) per = ws.max_blocks;
+  if (per < 1) per = 1;
+  if ((long long)rows * nb > ws.tickets) fail(MG_ERR_UNSUPPORTED, "gcr_dots_batch: too many reduction slots");
+  gcr_dots_batch_devk_kernel<<<dim3(reduce_blocks(n, per), rows, nb), kReduceThreads, 0, s>>>(
+      W, w, r, ctl, nb, restart, n, ws.partials, out, ws.ticket);
+  MG_LAUNCHED();
+}
+
+void launch_gcr_coef_batch(const double *dots, const int *ctl, int nb, int restart, int *act, double *stv,
+                           double *coef, cudaStream_t s) {
+  gcr_coef_batch_kernel<<<1, 32, 0, s>>>(dots, ctl, nb, restart, act, stv, coef);
+  MG_LAUNCHED();
+}
+
+void launch_gcr_update_batch_devk(Cx<double> *W, Cx<double> *Z, const Cx<double> *w, const Cx<double> *z,
+                                  const int *ctl, int nb, int restart, const double *dots, const double *coef,
+                                  Cx<double> *x, Cx<double> *r, long long n, cudaStream_t s) {
+  gcr_update_batch_devk_kernel<<<dim3(stream_grid(n), nb), 256, 0, s>>>(W, Z, w, z, ctl, nb, restart, dots, coef, x,
+                                                                          r, n);
+  MG_LAUNCHED();
+}
+
+void launch_gcr_control_batch(int *ctl, const int *act, int nb, int restart, int max_iter,
+                              cudaGraphConditionalHandle handle, cudaStream_t s) {
+  gcr_control_batch_kernel<<<1, 1, 0, s>>>(ctl, act, nb, restart, max_iter, handle);
+  MG_LAUNCHED();
+}
+
+}  // namespace mg

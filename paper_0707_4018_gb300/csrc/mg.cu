@@ -123,6 +123,10 @@ struct mg_ctx {
   mg::DevBuf<int> dl_ctl;                      // device-driven outer loop: counters, residual state, w
   mg::DevBuf<double> dl_st;
   mg::DevBuf<mg::Cx<double>> dl_w;
+  bool tc_batch = false;                       // coarse residual applies of batched cycles on tensor cores
+  mg::DevBuf<mg::Cx<double>> dl_wb;            // batched device loop: w, flags, state, coefficients
+  mg::DevBuf<int> dl_act;
+  mg::DevBuf<double> dl_stv, dl_coef;
   mg::DevBuf<int> cg_info;
   mg::DevBuf<unsigned int> cg_bar;
   mg::DevBuf<int> cg_out;  // [0] iterations, [1] timeout flag, [2] solves above tolerance
@@ -224,6 +228,11 @@ static void apply_op(mg_ctx &c, int l, const Cx<R> *in, Cx<R> *out, const Cx<R> 
   Level &L = c.lv[l];
   if (l == 0)
     launch_dslash<R>(Uof<R>(c), in, out, L.geo, diag_of(c), b, a, cc, c.s, nvec, c.cur_shift);
+  else if (sizeof(R) == 4 && c.tc_batch && nvec >= 8 && L.Ypk.p != nullptr)
+    // batched solves: the coarse operator on tensor cores for all vectors at once (BF16
+    // operands, FP32 sums; an N-tile of the MMA is 8 vectors)
+    launch_coarse_apply_tc(L.Ypk.p, reinterpret_cast<const Cx<float> *>(in), reinterpret_cast<Cx<float> *>(out),
+                           L.geo, nvec, reinterpret_cast<const Cx<float> *>(b), a, cc, c.cur_shift, c.s);
   else
     launch_coarse_apply<R>(Yof<R>(L), in, out, L.geo, L.nint, b, a, cc, c.s, nvec, c.cur_shift);
   c.apps[l] += nvec;
@@ -739,17 +748,44 @@ struct DevSolve {
   mg_ctx *c = nullptr;
   const Cx<double> *b = nullptr;
   Cx<double> *x = nullptr;
-  double bn2 = 0.0;
-  GcrOut out;
+  int nb = 1;                 // right-hand sides of this context (lockstep batch when > 1)
+  std::vector<double> bn2;    // |b_v|^2
+  std::vector<GcrOut> out;    // per vector
+  int iters = 0;              // outer iterations of the context's loop
   long long kernels_per_it = 0, apps_per_it[MG_MAX_LEVELS] = {0, 0, 0, 0};
 };
 
-static void devloop_buffers(mg_ctx &c) {
-  if (c.dl_ctl.p != nullptr) return;
-  c.dl_ctl.alloc(4);
-  c.dl_st.alloc(4);
-  c.dl_w.alloc(c.lv[0].n);
+static void alloc_batch(mg_ctx &c);
+
+static void devloop_buffers(mg_ctx &c, int nb) {
+  if (c.dl_ctl.p == nullptr) {
+    c.dl_ctl.alloc(4);
+    c.dl_st.alloc(4);
+    c.dl_w.alloc(c.lv[0].n);
+  }
+  if (nb > 1 && (long long)c.dl_wb.n < nb * c.lv[0].n) {
+    if (c.bZ.p == nullptr) alloc_batch(c);
+    c.dl_wb.alloc((size_t)c.p.max_rhs * c.lv[0].n);
+    c.dl_act.alloc((size_t)c.p.max_rhs);
+    c.dl_stv.alloc((size_t)2 * c.p.max_rhs);
+    c.dl_coef.alloc((size_t)4 * c.p.max_rhs);
+  }
   pool_ready();
+}
+
+// batch: per-vector flags and residual state for a (re)start from the residuals now in c.br
+static void devloop_arm_batch(mg_ctx &c, int nb, const std::vector<int> &act, const std::vector<double> &rn2,
+                              const std::vector<double> &tol2, int iters_done) {
+  const int ctl[4] = {iters_done, 0, 0, 0};
+  std::vector<double> stv(2 * nb);
+  for (int v = 0; v < nb; ++v) {
+    stv[2 * v] = rn2[v];
+    stv[2 * v + 1] = tol2[v];
+  }
+  MG_CUDA(cudaMemcpyAsync(c.dl_ctl.p, ctl, sizeof(ctl), cudaMemcpyHostToDevice, c.s));
+  MG_CUDA(cudaMemcpyAsync(c.dl_act.p, act.data(), nb * sizeof(int), cudaMemcpyHostToDevice, c.s));
+  MG_CUDA(cudaMemcpyAsync(c.dl_stv.p, stv.data(), 2 * nb * sizeof(double), cudaMemcpyHostToDevice, c.s));
+  MG_CUDA(cudaStreamSynchronize(c.s));
 }
 
 // counters and residual state for a (re)start from the residual now in c.orr (|r|^2 = rn2)
@@ -779,7 +815,34 @@ static void devloop_capture(DevSolve &d, cudaGraph_t body, cudaGraphConditionalH
   for (int l = 0; l < MG_MAX_LEVELS; ++l) a0[l] = c.apps[l];
   MG_CUDA(cudaStreamBeginCaptureToGraph(c.s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   bool ok = true;
-  try {
+  if (d.nb > 1) {
+    // one lockstep iteration of the batch: z_v = V r_v for the iterating vectors (0 for the
+    // others), w_v = D z_v, the reductions, the per-vector coefficients, the update, the control
+    const int nb = d.nb, R = c.p.gcr_restart;
+    c.tc_batch = c.p.precision == MG_FP32 && nb >= 8 && std::getenv("MG_NO_TC_BATCH") == nullptr;
+    try {  // every vector at the context mass (no shift)
+      launch_copy_active(c.br.p, c.brin.p, n, nb, c.dl_act.p, c.s);
+      Cx<double> *z = c.bz64.p;
+      if (c.p.precision == MG_FP32) {
+        launch_convert<float, double>(c.brin.p, F.w32.b.p, n * nb, c.s);
+        vcycle<float>(c, 0, F.w32.b.p, c.bz32.p, nb);
+        launch_convert<double, float>(c.bz32.p, c.brin.p, n * nb, c.s);  // z in brin (r was copied already)
+        z = c.brin.p;
+      } else {
+        vcycle<double>(c, 0, c.brin.p, c.bz64.p, nb);
+      }
+      apply_op<double>(c, 0, z, c.dl_wb.p, nullptr, 1.0, 0.0, nb);
+      double *dots = c.bdots.p;
+      launch_gcr_dots_batch_devk(c.bW.p, c.dl_wb.p, c.br.p, c.dl_ctl.p, nb, R, n, dots, c.ws, c.s);
+      launch_gcr_coef_batch(dots, c.dl_ctl.p, nb, R, c.dl_act.p, c.dl_stv.p, c.dl_coef.p, c.s);
+      launch_gcr_update_batch_devk(c.bW.p, c.bZ.p, c.dl_wb.p, z, c.dl_ctl.p, nb, R, dots, c.dl_coef.p, d.x, c.br.p, n,
+                                   c.s);
+      launch_gcr_control_batch(c.dl_ctl.p, c.dl_act.p, nb, R, c.p.max_iter, h, c.s);
+    } catch (const Error &) {
+      ok = false;
+    }
+    c.tc_batch = false;
+  } else try {
     if (c.p.precision == MG_FP32) {
       launch_convert<float, double>(c.orr.p, F.w32.b.p, n, c.s);
       vcycle<float>(c, 0, F.w32.b.p, c.z32.p);
@@ -816,6 +879,15 @@ static void devloop_launch(std::vector<DevSolve *> &act, cudaStream_t ls) {
   cudaGraphExec_t exec = nullptr;
   try {
     for (DevSolve *d : act) {
+      // tensor-core coarse applies of batched cycles: tune their launch shape outside the capture
+      mg_ctx &c = *d->c;
+      if (c.p.precision == MG_FP32 && d->nb >= 8 && std::getenv("MG_NO_TC_BATCH") == nullptr)
+        for (int l = 1; l < c.p.levels; ++l)
+          if (c.lv[l].Ypk.p != nullptr)
+            launch_coarse_apply_tc(c.lv[l].Ypk.p, c.lv[l].w32.r.p, c.lv[l].w32.Ar.p, c.lv[l].geo, d->nb, nullptr, 1.0,
+                                   0.0, nullptr, c.s);
+    }
+    for (DevSolve *d : act) {
       cudaGraphConditionalHandle h;
       MG_CUDA(cudaGraphConditionalHandleCreate(&h, top, 1, cudaGraphCondAssignDefault));
       cudaGraphNodeParams np = {};
@@ -844,49 +916,100 @@ static void devloop_launch(std::vector<DevSolve *> &act, cudaStream_t ls) {
 }
 
 static void devloop_solve(std::vector<DevSolve> &v, double tol) {
+  const double tol2 = tol * tol;
   for (DevSolve &d : v) {
     mg_ctx &c = *d.c;
     check_fresh(c);
-    devloop_buffers(c);
+    devloop_buffers(c, d.nb);
     for (long long &a : c.apps) a = 0;
     collect_coarsest(c);
     const long long n = c.lv[0].n;
-    launch_zero<double>(d.x, n, c.s);
-    launch_copy<double>(d.b, c.orr.p, n, c.s);
-    d.bn2 = fine_norm2(c, d.b);
-    d.out = GcrOut{};
-    if (!(d.bn2 > 0.0)) {
-      d.out.converged = true;
-      continue;
+    d.out.assign(d.nb, GcrOut{});
+    d.bn2.assign(d.nb, 0.0);
+    d.iters = 0;
+    launch_zero<double>(d.x, n * d.nb, c.s);
+    if (d.nb == 1) {
+      launch_copy<double>(d.b, c.orr.p, n, c.s);
+      d.bn2[0] = fine_norm2(c, d.b);
+      if (!(d.bn2[0] > 0.0)) {
+        d.out[0].converged = true;
+        continue;
+      }
+      devloop_arm(c, d.bn2[0], tol2 * d.bn2[0], 0);
+    } else {
+      launch_copy<double>(d.b, c.br.p, n * d.nb, c.s);
+      launch_norm2_batch(d.b, n, d.nb, c.bdots.p, c.ws, c.s);
+      MG_CUDA(cudaMemcpyAsync(d.bn2.data(), c.bdots.p, d.nb * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+      MG_CUDA(cudaStreamSynchronize(c.s));
+      std::vector<int> act(d.nb);
+      std::vector<double> t2(d.nb);
+      for (int q = 0; q < d.nb; ++q) {
+        act[q] = d.bn2[q] > 0.0 ? 1 : 0;
+        d.out[q].converged = !act[q];
+        t2[q] = tol2 * d.bn2[q];
+      }
+      devloop_arm_batch(c, d.nb, act, d.bn2, t2, 0);
     }
-    devloop_arm(c, d.bn2, tol * tol * d.bn2, 0);
   }
+  auto open = [](const DevSolve &d) {
+    for (const GcrOut &o : d.out)
+      if (!o.converged) return d.iters < d.c->p.max_iter;
+    return false;
+  };
   for (int round = 0; round < 8; ++round) {
     std::vector<DevSolve *> act;
     for (DevSolve &d : v)
-      if (!d.out.converged && d.out.iters < d.c->p.max_iter) act.push_back(&d);
+      if (open(d)) act.push_back(&d);
     if (act.empty()) break;
     devloop_launch(act, act[0]->c->s);
+    MG_CUDA(cudaEventRecord(act[0]->c->ev, act[0]->c->s));
     for (DevSolve *d : act) {
       mg_ctx &c = *d->c;
-      MG_CUDA(cudaEventRecord(act[0]->c->ev, act[0]->c->s));
+      const long long n = c.lv[0].n;
       MG_CUDA(cudaStreamWaitEvent(c.s, act[0]->c->ev, 0));
       int ctl[4];
       MG_CUDA(cudaMemcpyAsync(ctl, c.dl_ctl.p, sizeof(ctl), cudaMemcpyDeviceToHost, c.s));
       MG_CUDA(cudaStreamSynchronize(c.s));
-      const long long done = ctl[0] - d->out.iters;
-      d->out.iters = ctl[0];
+      const long long done = ctl[0] - d->iters;
+      d->iters = ctl[0];
       g_launches.fetch_add(done * d->kernels_per_it);
       for (int l = 0; l < MG_MAX_LEVELS; ++l) c.apps[l] += done * d->apps_per_it[l];
-      // true residual (defect correction)
-      apply_op<double>(c, 0, d->x, c.orr.p, d->b, -1.0, 1.0);
-      const double rn2 = fine_norm2(c, c.orr.p);
-      if (!std::isfinite(rn2)) fail(MG_ERR_NAN, "outer GCR (device loop): NaN in the true residual");
-      d->out.rel = std::sqrt(rn2 / d->bn2);
-      d->out.converged = d->out.rel <= tol;
-      if (!d->out.converged) {
-        if (ctl[2] == 3 && done <= 1) d->out.iters = c.p.max_iter;  // no progress possible: give up
-        else devloop_arm(c, rn2, tol * tol * d->bn2, ctl[0]);
+      // true residuals (defect correction)
+      if (d->nb == 1) {
+        GcrOut &o = d->out[0];
+        o.iters = d->iters;
+        apply_op<double>(c, 0, d->x, c.orr.p, d->b, -1.0, 1.0);
+        const double rn2 = fine_norm2(c, c.orr.p);
+        if (!std::isfinite(rn2)) fail(MG_ERR_NAN, "outer GCR (device loop): NaN in the true residual");
+        o.rel = std::sqrt(rn2 / d->bn2[0]);
+        o.converged = o.rel <= tol;
+        if (!o.converged) {
+          if (ctl[2] == 3 && done <= 1) d->iters = c.p.max_iter;  // no progress possible: give up
+          else devloop_arm(c, rn2, tol2 * d->bn2[0], ctl[0]);
+        }
+      } else {
+        apply_op<double>(c, 0, d->x, c.br.p, d->b, -1.0, 1.0, d->nb);
+        launch_norm2_batch(c.br.p, n, d->nb, c.bdots.p, c.ws, c.s);
+        std::vector<double> rn2(d->nb), t2(d->nb);
+        MG_CUDA(cudaMemcpyAsync(rn2.data(), c.bdots.p, d->nb * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+        MG_CUDA(cudaStreamSynchronize(c.s));
+        std::vector<int> more(d->nb, 0);
+        bool any = false;
+        for (int q = 0; q < d->nb; ++q) {
+          GcrOut &o = d->out[q];
+          t2[q] = tol2 * d->bn2[q];
+          if (o.converged && d->bn2[q] == 0.0) continue;
+          if (!std::isfinite(rn2[q])) fail(MG_ERR_NAN, "outer GCR (device loop, batch): NaN in a true residual");
+          o.iters = d->iters;
+          o.rel = std::sqrt(rn2[q] / d->bn2[q]);
+          o.converged = o.rel <= tol;
+          more[q] = o.converged ? 0 : 1;
+          any = any || more[q];
+        }
+        if (any) {
+          if (done <= 0) d->iters = c.p.max_iter;  // no progress possible: give up
+          else devloop_arm_batch(c, d->nb, more, rn2, t2, ctl[0]);
+        }
       }
     }
   }
@@ -1739,8 +1862,8 @@ int mg_save_setup(mg_ctx *c, const char *path) {
   });
 }
 
-int mg_solve_multi(int count, mg_ctx *const *ctx, const void *const *chi, void *const *psi, double tol,
-                   mg_stats *st) {
+int mg_solve_multi(int count, mg_ctx *const *ctx, const int *nrhs, const void *const *chi, void *const *psi,
+                   double tol, mg_stats *st) {
   int status = MG_OK;
   int rc = guarded([&] {
     if (count < 1 || !ctx || !chi || !psi) fail(MG_ERR_INVALID_ARG, "need count >= 1 and non-null arrays");
@@ -1763,25 +1886,32 @@ int mg_solve_multi(int count, mg_ctx *const *ctx, const void *const *chi, void *
       v[i].c = ctx[i];
       v[i].b = static_cast<const Cx<double> *>(chi[i]);
       v[i].x = static_cast<Cx<double> *>(psi[i]);
+      v[i].nb = nrhs ? nrhs[i] : 1;
+      if (v[i].nb < 1 || v[i].nb > ctx[i]->p.max_rhs)
+        fail(MG_ERR_INVALID_ARG, "nrhs[i] must be in [1, max_rhs of context i]");
     }
     EventPair ev;
     ev.start(v[0].c->s);
     devloop_solve(v, tol);
     const float ms = ev.stop(v[0].c->s);
+    int e = 0;
     for (int i = 0; i < count; ++i) {
       mg_ctx &c = *v[i].c;
-      if (!v[i].out.converged) status = MG_ERR_NOT_CONVERGED;
-      if (!st) continue;
-      st[i].iters = v[i].out.iters;
-      st[i].converged = v[i].out.converged ? 1 : 0;
-      st[i].true_rel_residual = v[i].out.rel;
-      for (int l = 0; l < MG_MAX_LEVELS; ++l) st[i].level_apps[l] = c.apps[l];
-      st[i].coarsest_iters = c.coarsest_iters;
-      st[i].ms = ms;
-      st[i].graphs = 1;
-      st[i].setup_s = c.setup_s;
-      st[i].solve_s = ms * 1e-3;
-      st[i].fine_D_apps = c.apps[0];
+      for (int q = 0; q < v[i].nb; ++q, ++e) {
+        const GcrOut &o = v[i].out[q];
+        if (!o.converged) status = MG_ERR_NOT_CONVERGED;
+        if (!st) continue;
+        st[e].iters = o.iters;
+        st[e].converged = o.converged ? 1 : 0;
+        st[e].true_rel_residual = o.rel;
+        for (int l = 0; l < MG_MAX_LEVELS; ++l) st[e].level_apps[l] = c.apps[l];
+        st[e].coarsest_iters = c.coarsest_iters;
+        st[e].ms = ms;
+        st[e].graphs = 1;
+        st[e].setup_s = c.setup_s;
+        st[e].solve_s = ms * 1e-3;
+        st[e].fine_D_apps = c.apps[0];
+      }
     }
   });
   if (rc == MG_OK && status != MG_OK) {

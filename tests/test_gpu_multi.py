@@ -63,3 +63,38 @@ def test_multi_solve_rejects_repeated_context():
         mg.solve_multi([ctx, ctx], [chi, chi], [torch.empty_like(chi), torch.empty_like(chi)], 1e-10)
     assert e.value.code == 1
     ctx.close()
+
+
+def test_multi_solve_batches_of_right_hand_sides():
+    # contexts with several right-hand sides each, solved in lockstep inside their WHILE loops;
+    # with 8 or more vectors in FP32 cycles the coarse residual applies run on tensor cores
+    import torch
+    import paper_0707_4018_gb300 as mg
+    specs = [((64, 64), 6.0, 0.03, 1, 8), ((32, 64), 3.0, 0.05, 1, 3), ((64, 32), 10.0, 0.04, 0, 2)]
+    ctxs, Us, chis, psis, nrhs = [], [], [], [], []
+    for i, (dims, beta, m, prec, nr) in enumerate(specs):
+        U = _case(dims[0], dims[1], beta, 200 + i)
+        p = mg.mg_default_params(levels=3, blocks=[(4, 4), (2, 2)], Nv=[8, 8], precision=prec, n_pass=3,
+                                 coarsest_tol=0.2, coarsest_lu_max=0, max_rhs=8)
+        ctx = mg.Context.setup(to_dev(U), m, dims, p)
+        chi = torch.stack([to_dev(inputs.gaussian_source(dims[0], dims[1], seed=30 + 10 * i + v)) for v in range(nr)])
+        ctxs.append(ctx)
+        Us.append(U)
+        chis.append(chi)
+        psis.append(torch.empty_like(chi))
+        nrhs.append(nr)
+    st = mg.solve_multi(ctxs, chis, psis, 1e-10, nrhs=nrhs)
+    assert len(st) == sum(nrhs)
+    e = 0
+    for i, (dims, beta, m, prec, nr) in enumerate(specs):
+        ref = torch.empty_like(chis[i])
+        sb = ctxs[i].solve_batch(chis[i], ref, 1e-10)
+        for v in range(nr):
+            x = to_host(psis[i][v])
+            b = to_host(chis[i][v])
+            res = np.linalg.norm(b - wilson.apply_D(Us[i], x, m, Lattice(dims))) / np.linalg.norm(b)
+            assert st[e]["converged"] and res <= 1e-10, (i, v, st[e], res)
+            assert st[e]["iters"] <= sb[v]["iters"] + max(4, sb[v]["iters"] // 4), (st[e]["iters"], sb[v]["iters"])
+            e += 1
+    for c in ctxs:
+        c.close()
