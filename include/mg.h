@@ -70,7 +70,13 @@ typedef enum {
 
 typedef enum {
   MG_FP64 = 0, /* every level in FP64 */
-  MG_FP32 = 1  /* FP64 outer flexible GCR; V-cycle (smoother, transfer, coarse ops) in FP32 */
+  MG_FP32 = 1, /* FP64 outer flexible GCR; V-cycle (smoother, transfer, coarse ops) in FP32 */
+  MG_FP16 = 2  /* half-precision storage with per-site FP32 norms, FP32 arithmetic. As a context
+                  precision (d = 2): MG_FP32, except that the fine level of the solve's V-cycles
+                  stores its links and the MR smoother's r and A r in half (12 bytes per site and
+                  vector; the smoother's iterate, the cycle's input and the residual handed to the
+                  restriction stay FP32); the setup runs as in MG_FP32. For mg_dslash: the half
+                  layouts of mg_half_convert. */
 } mg_precision;
 
 typedef struct {
@@ -261,7 +267,8 @@ const char *mg_last_error(void);
 /* ---- step-level entry points (one step of the hot path each) ------------- */
 
 /* Fine Wilson operator out = D(U) in without a context (paper, definition of D).
- * precision MG_FP64: U, in, out complex128; MG_FP32: complex64. in and out must
+ * precision MG_FP64: U, in, out complex128; MG_FP32: complex64; MG_FP16 (d = 2): the half
+ * layouts of mg_half_convert. in and out must
  * not alias. stream: cudaStream_t. Asynchronous on the stream (no sync).
  * Geometries: d = 2 with Nc = 1 (layouts above), or d = 4 with Nc = 3: the
  * paper's four-dimensional SU(3) case (its outlook), in the DeGrand-Rossi basis
@@ -272,6 +279,18 @@ const char *mg_last_error(void);
  * Errors: INVALID_ARG (extent < 2, volume >= 2^31, null or aliasing pointers,
  * unknown precision), UNSUPPORTED (other d / Nc). */
 int mg_dslash(const mg_geom *g, const void *U, double m, const void *in, void *out, int precision, void *stream);
+
+/* Half-precision storage of 2d fields (the FP16 storage of the mixed-precision scheme): a spinor
+ * field of nsites sites is [nsites][2] IEEE half pairs (re, im), scaled by a per-site FP32 norm
+ * (the site's largest |Re| or |Im|), followed by [nsites] float norms: 12 bytes per site, value =
+ * norm x half. Links are [nsites][2] half pairs (cos, sin), unscaled (|U| = 1): 8 bytes per site.
+ * mg_dslash with MG_FP16 takes U, in and out in these layouts (FP32 arithmetic; the output is
+ * rescaled by its own per-site norm before it is rounded). Conversions:
+ *   what 0: complex spinor (precision MG_FP64 / MG_FP32, [x][s]) -> half spinor
+ *   what 1: half spinor -> complex spinor
+ *   what 2: complex links [x][mu] -> half links
+ * Asynchronous on stream. Errors: INVALID_ARG (null or aliasing pointers, bad what / precision). */
+int mg_half_convert(int what, int precision, const void *in, void *out, long long nsites, void *stream);
 
 /* Apply the level-l operator (l = 0: D; l >= 1: the Galerkin stencil) in FP64. */
 int mg_level_apply(mg_ctx *ctx, int level, const void *in, void *out);

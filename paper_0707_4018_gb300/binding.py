@@ -15,7 +15,7 @@ import torch
 from . import build as _build
 
 MG_MAX_LEVELS = 4
-MG_FP64, MG_FP32 = 0, 1
+MG_FP64, MG_FP32, MG_FP16 = 0, 1, 2
 
 STATUS = {0: "MG_OK", 1: "MG_ERR_INVALID_ARG", 2: "MG_ERR_CUDA", 3: "MG_ERR_OOM", 4: "MG_ERR_NOT_CONVERGED",
           5: "MG_ERR_NAN", 6: "MG_ERR_UNSUPPORTED", 7: "MG_ERR_STATE", 8: "MG_ERR_TIMEOUT"}
@@ -93,6 +93,7 @@ def load():
         "mg_convergence_rate": (I, [ctxp, I, ctypes.c_uint64, P(D)]),
         "mg_alu_peak": (I, [I, P(D), VP]),
         "mg_solve_multi": (I, [I, P(ctxp), P(I), P(VP), P(VP), D, P(mg_stats)]),
+        "mg_half_convert": (I, [I, I, VP, VP, ctypes.c_longlong, VP]),
         "mg_solve_batch": (I, [ctxp, I, VP, VP, P(D), D, P(mg_stats)]),
         "mg_coarse_apply_mrhs": (I, [ctxp, I, I, VP, VP, I]),
         "mg_update_mass": (I, [ctxp, D]),
@@ -133,7 +134,8 @@ def exported_symbols():
             "mg_coarse_apply_mrhs", "mg_autotune_report", "mg_clone", "mg_setup_batch", "mg_save_setup",
             "mg_load_setup", "mg_context_info", "mg_nullnet_create", "mg_nullnet_destroy", "mg_nullnet_weight_count",
             "mg_nullnet_get_weights", "mg_nullnet_set_weights", "mg_nullnet_forward", "mg_nullnet_gradient",
-            "mg_nullnet_train", "mg_setup_learned", "mg_convergence_rate", "mg_alu_peak", "mg_solve_multi"]
+            "mg_nullnet_train", "mg_setup_learned", "mg_convergence_rate", "mg_alu_peak", "mg_solve_multi",
+            "mg_half_convert"]
 
 
 def autotune_report() -> dict:
@@ -213,6 +215,34 @@ def mg_dslash(U: torch.Tensor, inp: torch.Tensor, out: torch.Tensor, m: float, d
     nu, npsi = (36 * V, 12 * V) if four else (2 * V, 2 * V)
     _check(load().mg_dslash(ctypes.byref(g), _ptr(U, dt, nu), float(m), _ptr(inp, dt, npsi),
                             _ptr(out, dt, npsi), precision, _stream(stream)))
+
+
+def half_spinor(nsites: int, device="cuda") -> torch.Tensor:
+    """Buffer of a half-precision spinor field with per-site norms (12 bytes per site)."""
+    return torch.empty(12 * nsites, dtype=torch.uint8, device=device)
+
+
+def half_links(nsites: int, device="cuda") -> torch.Tensor:
+    """Buffer of half-precision 2d links (8 bytes per site)."""
+    return torch.empty(8 * nsites, dtype=torch.uint8, device=device)
+
+
+def mg_half_convert(what: int, src: torch.Tensor, dst: torch.Tensor, nsites: int, stream=None):
+    """mg_half_convert: 0 complex spinor -> half, 1 half -> complex spinor, 2 complex links -> half
+    (the complex side complex128 or complex64)."""
+    cplx = src if what in (0, 2) else dst
+    prec = MG_FP64 if cplx.dtype == torch.complex128 else MG_FP32
+    _check(load().mg_half_convert(int(what), prec, _ptr(src), _ptr(dst), int(nsites), _stream(stream)))
+
+
+def mg_dslash_half(U_h: torch.Tensor, in_h: torch.Tensor, out_h: torch.Tensor, m: float, dims, stream=None):
+    """out = D(U) in on half-precision fields (layouts of mg_half_convert), FP32 arithmetic."""
+    V = int(dims[0]) * int(dims[1])
+    if U_h.numel() != 8 * V or in_h.numel() != 12 * V or out_h.numel() != 12 * V:
+        raise ValueError("half buffers of the wrong size")
+    g = make_geom(dims)
+    _check(load().mg_dslash(ctypes.byref(g), _ptr(U_h), float(m), _ptr(in_h), _ptr(out_h), MG_FP16,
+                            _stream(stream)))
 
 
 def mg_smooth_fine_noalloc(U: torch.Tensor, b: torch.Tensor, x: torch.Tensor, m: float, dims, nu: int,
@@ -438,6 +468,14 @@ class Context:
         n = self._numel(level) * nrhs
         _check(load().mg_coarse_apply_mrhs(self._need(), int(level), nrhs, _ptr(inp, torch.complex64, n),
                                            _ptr(out, torch.complex64, n), 1 if tensor_cores else 0))
+
+    def info(self) -> dict:
+        """mg_context_info: the parameters as given at setup (precision included) and the mass."""
+        p = mg_params()
+        g = mg_geom()
+        m = ctypes.c_double()
+        _check(load().mg_context_info(self._need(), ctypes.byref(g), ctypes.byref(p), ctypes.byref(m)))
+        return {"precision": int(p.precision), "levels": int(p.levels), "mass": float(m.value), "params": p}
 
     def update_mass(self, m: float):
         _check(load().mg_update_mass(self._need(), float(m)))

@@ -20,21 +20,78 @@
 //    reduction with |w|^2 and <w, r> (|w - W b|^2 = |w|^2 - |b|^2 for the
 //    orthonormal W), so an iteration costs 3 grid synchronisations.
 // Arithmetic: FP64 throughout (the coarsest solve stays in FP64 in every mode).
+#include <mutex>
+
 #include "kernels.h"
 
 namespace mg {
+
+// Cooperative kernels wait on one another's CTAs at grid barriers, so all their CTAs must be
+// resident at once. Two of them in flight on different streams (concurrent setups, solves
+// from several host threads, parallel branches of one graph) can each hold part of the GPU
+// and wait for the rest. Every cooperative launch outside a capture therefore passes through
+// one lane per device: it waits on the lane's event (the previous cooperative launch, from
+// any stream) and records the event after itself. A launch captured into a graph marks the
+// capturing thread instead; the graph's launch then takes the lane as a whole.
+namespace {
+struct CoopLane {
+  std::mutex mu;
+  cudaEvent_t ev = nullptr;
+};
+constexpr int kMaxLaneDevices = 64;
+CoopLane g_lanes[kMaxLaneDevices];
+thread_local bool t_coop_captured = false;
+
+template <typename F>
+void through_lane(cudaStream_t s, F &&launch) {
+  int dev = 0;
+  MG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxLaneDevices) fail(MG_ERR_UNSUPPORTED, "device ordinal beyond the cooperative lanes");
+  CoopLane &L = g_lanes[dev];
+  std::lock_guard<std::mutex> lk(L.mu);
+  if (L.ev == nullptr) MG_CUDA(cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming));
+  MG_CUDA(cudaStreamWaitEvent(s, L.ev, 0));
+  launch();
+  MG_CUDA(cudaEventRecord(L.ev, s));
+}
+}  // namespace
+
+void coop_launch(const void *fn, dim3 grid, dim3 block, void **args, size_t smem, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  MG_CUDA(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone) {
+    t_coop_captured = true;
+    MG_CUDA(cudaLaunchCooperativeKernel(fn, grid, block, args, smem, s));
+    return;
+  }
+  through_lane(s, [&] { MG_CUDA(cudaLaunchCooperativeKernel(fn, grid, block, args, smem, s)); });
+}
+
+bool coop_captured_take() {
+  const bool v = t_coop_captured;
+  t_coop_captured = false;
+  return v;
+}
+
+void coop_graph_launch(cudaGraphExec_t g, cudaStream_t s) {
+  through_lane(s, [&] { MG_CUDA(cudaGraphLaunch(g, s)); });
+}
 
 constexpr int kMaxRestart = 32;
 constexpr int kSlots = 2 * kMaxRestart + 4;
 static_assert(kSlots == kCoarsestSlots, "slot count shared with the host");
 
+// VT: precision of the stencil A M and of the Krylov vectors (double; float in mixed-precision
+// cycles with a loose coarsest tolerance, where every reduction still sums in FP64)
+template <typename VT>
 struct CgArgs {
-  const Cx<double> *Y;     // preconditioned stencil A M, internal layout
+  const Cx<VT> *Y;         // preconditioned stencil A M, internal layout
   const Cx<double> *Minv;  // X_j^{-1}, [j][col][row]
   int L0, L1, N;
   long long n;
   const Cx<double> *b;
-  Cx<double> *x, *y, *r, *Z, *W;
+  Cx<double> *x;
+  Cx<VT> *y, *r, *Z, *W;
   double *partials;   // [G][kSlots]
   unsigned int *bar;  // [0] count, [1] generation
   double tol;
@@ -46,7 +103,8 @@ struct CgArgs {
 };
 
 // bounded grid barrier; clears `ok` (and sets the status) when the wait gave up
-__device__ __forceinline__ void grid_sync(const CgArgs &a, bool &ok) {
+template <typename A>
+__device__ __forceinline__ void grid_sync(const A &a, bool &ok) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -87,7 +145,8 @@ __device__ __forceinline__ void warp_put(double t, int s, double *swarp) {
 // Sum slots [0, nv) of every warp across the grid. Block tree -> per-CTA
 // partials -> barrier -> every CTA stages all partials in shared memory with
 // independent loads -> one warp per slot sums them in CTA order.
-__device__ __forceinline__ void grid_sum(const CgArgs &a, int nv, double *swarp, double *stage, double *sres,
+template <typename A>
+__device__ __forceinline__ void grid_sum(const A &a, int nv, double *swarp, double *stage, double *sres,
                                          bool &ok) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __syncthreads();
@@ -114,8 +173,17 @@ __device__ __forceinline__ void grid_sum(const CgArgs &a, int nv, double *swarp,
   __syncthreads();
 }
 
-template <int NT>
-__device__ __forceinline__ Cx<double> apply_row(const CgArgs &a, long long i, const Cx<double> *v) {
+__device__ __forceinline__ Cx<double> ldcg2(const Cx<double> *p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+  return mk(v.x, v.y);
+}
+__device__ __forceinline__ Cx<float> ldcg2(const Cx<float> *p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+  return mk(v.x, v.y);
+}
+
+template <int NT, typename VT>
+__device__ __forceinline__ Cx<VT> apply_row(const CgArgs<VT> &a, long long i, const Cx<VT> *v) {
   const int N = NT > 0 ? NT : a.N;
   const long long j = i / N;
   const int row = (int)(i - j * N);
@@ -127,38 +195,38 @@ __device__ __forceinline__ Cx<double> apply_row(const CgArgs &a, long long i, co
   src[2] = rowo + (x0 == 0 ? a.L0 - 1 : x0 - 1);
   src[3] = (x1 + 1 == a.L1 ? 0 : rowo + a.L0) + x0;
   src[4] = (x1 == 0 ? (long long)(a.L1 - 1) * a.L0 : rowo - a.L0) + x0;
-  Cx<double> acc = mk(0.0, 0.0);
+  Cx<VT> acc = mk<VT>(0, 0);
 #pragma unroll
   for (int dir = 0; dir < 5; ++dir) {
-    const Cx<double> *Yd = a.Y + (j * 5 + dir) * (long long)N * N + row;
-    const Cx<double> *xs = v + src[dir] * N;
+    const Cx<VT> *Yd = a.Y + (j * 5 + dir) * (long long)N * N + row;
+    const Cx<VT> *xs = v + src[dir] * N;
 #pragma unroll(NT > 0 ? NT : 1)
     for (int c = 0; c < N; ++c) {
       // neighbour values were written by other CTAs: read through L2 (no stale L1 lines)
-      const double2 xv = __ldcg(reinterpret_cast<const double2 *>(xs + c));
-      cmac(acc, Yd[(long long)c * N], mk(xv.x, xv.y));
+      cmac(acc, Yd[(long long)c * N], ldcg2(xs + c));
     }
   }
   return acc;
 }
 
 // sum over own dofs of conj(W_j) * Wk for j < k, into warp slots off + 2j, off + 2j + 1
-__device__ __forceinline__ void gs_dots(const CgArgs &a, int k, const Cx<double> *Wk, long long gid, long long gs,
+template <typename VT>
+__device__ __forceinline__ void gs_dots(const CgArgs<VT> &a, int k, const Cx<VT> *Wk, long long gid, long long gs,
                                         double *swarp, int off) {
   for (int j = 0; j < k; ++j) {
     double re = 0.0, im = 0.0;
     for (long long i = gid; i < a.n; i += gs) {
-      const Cx<double> wj = a.W[(long long)j * a.n + i], w = Wk[i];
-      re += wj.re * w.re + wj.im * w.im;
-      im += wj.re * w.im - wj.im * w.re;
+      const Cx<VT> wj = a.W[(long long)j * a.n + i], w = Wk[i];
+      re += (double)(wj.re * w.re + wj.im * w.im);
+      im += (double)(wj.re * w.im - wj.im * w.re);
     }
     warp_put(re, off + 2 * j, swarp);
     warp_put(im, off + 2 * j + 1, swarp);
   }
 }
 
-template <int NT>
-__global__ void __launch_bounds__(256) coarsest_gcr_kernel(CgArgs a) {
+template <int NT, typename VT>
+__global__ void __launch_bounds__(256) coarsest_gcr_kernel(CgArgs<VT> a) {
   extern __shared__ double sdyn[];
   double *swarp = sdyn;               // 8 warps x kSlots
   double *sres = sdyn + 8 * kSlots;   // kSlots
@@ -173,8 +241,8 @@ __global__ void __launch_bounds__(256) coarsest_gcr_kernel(CgArgs a) {
   double t0 = 0.0;
   for (long long i = gid; i < n; i += gs) {
     const Cx<double> bi = a.b[i];
-    a.y[i] = mk(0.0, 0.0);
-    a.r[i] = bi;
+    a.y[i] = mk<VT>(0, 0);
+    a.r[i] = cvt<VT, double>(bi);
     t0 += norm2(bi);
   }
   warp_put(t0, 0, swarp);
@@ -187,10 +255,10 @@ __global__ void __launch_bounds__(256) coarsest_gcr_kernel(CgArgs a) {
   double rn2 = bn2;
   while (!converged && it < a.max_iter) {
     for (int k = 0; k < a.restart && it < a.max_iter; ++k) {
-      Cx<double> *Zk = a.Z + (long long)k * n, *Wk = a.W + (long long)k * n;
+      Cx<VT> *Zk = a.Z + (long long)k * n, *Wk = a.W + (long long)k * n;
       // z_k = r, w_k = (A M) r
       for (long long i = gid; i < n; i += gs) {
-        Wk[i] = apply_row<NT>(a, i, a.r);
+        Wk[i] = apply_row<NT, VT>(a, i, a.r);
         Zk[i] = a.r[i];
       }
       if (k > 0) {
@@ -199,9 +267,9 @@ __global__ void __launch_bounds__(256) coarsest_gcr_kernel(CgArgs a) {
         grid_sum(a, 2 * k, swarp, stage, sres, ok);
         if (!ok) return;
         for (long long i = gid; i < n; i += gs) {
-          Cx<double> w = Wk[i], z = Zk[i];
+          Cx<VT> w = Wk[i], z = Zk[i];
           for (int j = 0; j < k; ++j) {
-            const Cx<double> bj = mk(-sres[2 * j], -sres[2 * j + 1]);
+            const Cx<VT> bj = mk((VT)-sres[2 * j], (VT)-sres[2 * j + 1]);
             cmac(w, bj, a.W[(long long)j * n + i]);
             cmac(z, bj, a.Z[(long long)j * n + i]);
           }
@@ -213,10 +281,10 @@ __global__ void __launch_bounds__(256) coarsest_gcr_kernel(CgArgs a) {
       }
       double nn = 0.0, wr = 0.0, wi = 0.0;
       for (long long i = gid; i < n; i += gs) {
-        const Cx<double> w = Wk[i], ri = a.r[i];
-        nn += norm2(w);
-        wr += w.re * ri.re + w.im * ri.im;
-        wi += w.re * ri.im - w.im * ri.re;
+        const Cx<VT> w = Wk[i], ri = a.r[i];
+        nn += (double)norm2(w);
+        wr += (double)(w.re * ri.re + w.im * ri.im);
+        wi += (double)(w.re * ri.im - w.im * ri.re);
       }
       warp_put(nn, 0, swarp);
       warp_put(wr, 1, swarp);
@@ -228,24 +296,26 @@ __global__ void __launch_bounds__(256) coarsest_gcr_kernel(CgArgs a) {
       for (int j = 0; j < k; ++j) nw2 -= sres[3 + 2 * j] * sres[3 + 2 * j] + sres[4 + 2 * j] * sres[4 + 2 * j];
       const bool breakdown = !(nw2 > 1e-28 * sres[0]);
       const double inv = breakdown ? 0.0 : 1.0 / sqrt(nw2);
-      const Cx<double> alpha = mk(sres[1] * inv, sres[2] * inv);  // <w_hat, r>
+      const double ar = sres[1] * inv, ai = sres[2] * inv;  // <w_hat, r>
+      const Cx<VT> alpha = mk((VT)ar, (VT)ai);
+      const VT vinv = (VT)inv;
       for (long long i = gid; i < n; i += gs) {
-        Cx<double> w = Wk[i], z = Zk[i];
+        Cx<VT> w = Wk[i], z = Zk[i];
         for (int j = 0; j < k; ++j) {
-          const Cx<double> bj = mk(-sres[3 + 2 * j], -sres[4 + 2 * j]);
+          const Cx<VT> bj = mk((VT)-sres[3 + 2 * j], (VT)-sres[4 + 2 * j]);
           cmac(w, bj, a.W[(long long)j * n + i]);
           cmac(z, bj, a.Z[(long long)j * n + i]);
         }
-        w = inv * w;
-        z = inv * z;
+        w = vinv * w;
+        z = vinv * z;
         Wk[i] = w;
         Zk[i] = z;
         cmac(a.y[i], alpha, z);
-        Cx<double> ri = a.r[i];
+        Cx<VT> ri = a.r[i];
         cmac(ri, mk(-alpha.re, -alpha.im), w);
         a.r[i] = ri;
       }
-      rn2 = fmax(rn2 - norm2(alpha), 0.0);
+      rn2 = fmax(rn2 - (ar * ar + ai * ai), 0.0);
       ++it;
       grid_sync(a, ok);
       if (!ok) return;
@@ -254,9 +324,9 @@ __global__ void __launch_bounds__(256) coarsest_gcr_kernel(CgArgs a) {
     // true residual r = b - (A M) y
     double tr = 0.0;
     for (long long i = gid; i < n; i += gs) {
-      const Cx<double> ri = a.b[i] - apply_row<NT>(a, i, a.y);
+      const Cx<VT> ri = cvt<VT, double>(a.b[i]) - apply_row<NT, VT>(a, i, a.y);
       a.r[i] = ri;
-      tr += norm2(ri);
+      tr += (double)norm2(ri);
     }
     warp_put(tr, 0, swarp);
     grid_sum(a, 1, swarp, stage, sres, ok);
@@ -271,10 +341,7 @@ __global__ void __launch_bounds__(256) coarsest_gcr_kernel(CgArgs a) {
     const int row = (int)(i - j * N);
     const Cx<double> *Mj = a.Minv + j * (long long)N * N + row;
     Cx<double> acc = mk(0.0, 0.0);
-    for (int c = 0; c < N; ++c) {
-      const double2 yv = __ldcg(reinterpret_cast<const double2 *>(a.y + j * N + c));
-      cmac(acc, Mj[(long long)c * N], mk(yv.x, yv.y));
-    }
+    for (int c = 0; c < N; ++c) cmac(acc, Mj[(long long)c * N], cvt<double, VT>(ldcg2(a.y + j * N + c)));
     a.x[i] = acc;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -408,12 +475,13 @@ int coarsest_gcr_grid(int device) {
   return sms;
 }
 
-void launch_coarsest_gcr(const Cx<double> *Yt, const Cx<double> *Minv, Geo2 g, int N, const Cx<double> *b,
-                         Cx<double> *x, Cx<double> *y, Cx<double> *r, Cx<double> *Z, Cx<double> *W, double *partials,
-                         unsigned int *bar, double tol, int restart, int max_iter, int *out, double *out_rel, int grid,
-                         cudaStream_t s) {
+template <typename VT>
+static void coarsest_gcr_go(const Cx<VT> *Yt, const Cx<double> *Minv, Geo2 g, int N, const Cx<double> *b,
+                            Cx<double> *x, Cx<VT> *y, Cx<VT> *r, Cx<VT> *Z, Cx<VT> *W, double *partials,
+                            unsigned int *bar, double tol, int restart, int max_iter, int *out, double *out_rel,
+                            int grid, cudaStream_t s) {
   if (restart > kMaxRestart) fail(MG_ERR_INVALID_ARG, "coarsest restart exceeds 32");
-  CgArgs a;
+  CgArgs<VT> a;
   a.Y = Yt;
   a.Minv = Minv;
   a.L0 = g.L0;
@@ -439,15 +507,31 @@ void launch_coarsest_gcr(const Cx<double> *Yt, const Cx<double> *Minv, Geo2 g, i
   if (threads < 64) threads = 64;
   if (threads > 256) threads = 256;
   const size_t smem = (size_t)(9 + grid) * kSlots * sizeof(double);
-  const void *fn = (N == 8) ? (const void *)coarsest_gcr_kernel<8> : (const void *)coarsest_gcr_kernel<0>;
+  const void *fn = (N == 8) ? (const void *)coarsest_gcr_kernel<8, VT> : (const void *)coarsest_gcr_kernel<0, VT>;
   MG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessorWithFlags(&per_sm, fn, threads, smem, 0));
   if (per_sm < 1) fail(MG_ERR_CUDA, "coarsest solve kernel cannot be resident");
   MG_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s));
   void *args[] = {&a};
-  MG_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, smem, s));
+  coop_launch(fn, dim3(grid), dim3(threads), args, smem, s);
   MG_LAUNCHED();
+}
+
+void launch_coarsest_gcr(const Cx<double> *Yt, const Cx<double> *Minv, Geo2 g, int N, const Cx<double> *b,
+                         Cx<double> *x, Cx<double> *y, Cx<double> *r, Cx<double> *Z, Cx<double> *W, double *partials,
+                         unsigned int *bar, double tol, int restart, int max_iter, int *out, double *out_rel, int grid,
+                         cudaStream_t s) {
+  coarsest_gcr_go<double>(Yt, Minv, g, N, b, x, y, r, Z, W, partials, bar, tol, restart, max_iter, out, out_rel, grid,
+                          s);
+}
+
+void launch_coarsest_gcr32(const Cx<float> *Yt, const Cx<double> *Minv, Geo2 g, int N, const Cx<double> *b,
+                           Cx<double> *x, Cx<float> *y, Cx<float> *r, Cx<float> *Z, Cx<float> *W, double *partials,
+                           unsigned int *bar, double tol, int restart, int max_iter, int *out, double *out_rel,
+                           int grid, cudaStream_t s) {
+  coarsest_gcr_go<float>(Yt, Minv, g, N, b, x, y, r, Z, W, partials, bar, tol, restart, max_iter, out, out_rel, grid,
+                         s);
 }
 
 }  // namespace mg
@@ -838,7 +922,7 @@ static void coarsest_smem_go(const Cx<RS> *Yt, const Cx<double> *Minv, Geo2 g, c
   if (per_sm < 1) fail(MG_ERR_CUDA, "coarsest solve kernel (shared-memory variant) cannot be resident");
   MG_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s));
   void *args[] = {&a};
-  MG_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, smem, s));
+  coop_launch(fn, dim3(grid), dim3(256), args, smem, s);
   MG_LAUNCHED();
 }
 
@@ -903,7 +987,7 @@ int barrier_selftest(unsigned int expected, long long spin_limit, cudaStream_t s
   MG_CUDA(cudaMemsetAsync(bar.p, 0, 2 * sizeof(unsigned int), s));
   MG_CUDA(cudaMemsetAsync(status.p, 0, sizeof(int), s));
   void *args[] = {&bar.p, &expected, &spin_limit, &status.p};
-  MG_CUDA(cudaLaunchCooperativeKernel((const void *)barrier_selftest_kernel, dim3(2), dim3(32), args, 0, s));
+  coop_launch((const void *)barrier_selftest_kernel, dim3(2), dim3(32), args, 0, s);
   MG_LAUNCHED();
   int h = 0;
   MG_CUDA(cudaMemcpyAsync(&h, status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1454,7 +1538,7 @@ void launch_coarsest_gcr_batch(const Cx<double> *Y, const Cx<double> *Minv, long
   if (per_sm < 1) fail(MG_ERR_CUDA, "batched coarsest solve kernel cannot be resident");
   MG_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s));
   void *args[] = {&a};
-  MG_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, smem, s));
+  coop_launch(fn, dim3(grid), dim3(256), args, smem, s);
   MG_LAUNCHED();
 }
 

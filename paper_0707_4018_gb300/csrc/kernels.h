@@ -70,6 +70,22 @@ void launch_pack_coarse_bf16(const Cx<float> *Y, uint2 *Ypk, long long nsites, c
 void launch_coarse_apply_tc(const uint2 *Ypk, const Cx<float> *in, Cx<float> *out, Geo2 g, int nvec,
                             const Cx<float> *b, double a, double c, const double *shift, cudaStream_t s);
 
+// ---- half-precision storage with per-site norms (wilson_half.cu) ----
+void launch_dslash_half(const void *U, const void *in, void *out, Geo2 g, double diag, cudaStream_t s);
+// fine level of FP32 V-cycles with half storage (MG_FP16 contexts; wilson_half.cu): the fused MR
+// iteration and its last step on half r / A r fields (12 V bytes per field of a batch), the
+// residual apply on FP32 vectors with half links
+int mr_half_grid(Geo2 g);
+void launch_mr_iteration_half(const void *U16, Geo2 g, double diag, const double *shift, bool step,
+                              const Cx<float> *b, void *r_old, void *Ar_old, const float *part_in, double omega,
+                              Cx<float> *x, bool x_init, void *r_new, void *Ar_new, float *part_out,
+                              long long part_capacity, cudaStream_t s, int nvec);
+void launch_mr_last_half(void *r_old, void *Ar_old, const float *part_in, double omega, Cx<float> *x, bool x_init,
+                         Cx<float> *r_out, Geo2 g, cudaStream_t s, int nvec);
+void launch_dslash_hl(const void *U16, const Cx<float> *in, Cx<float> *out, Geo2 g, double diag, const Cx<float> *b,
+                      double a, double c, cudaStream_t s, int nvec, const double *shift);
+void launch_half_convert(int what, int precision, const void *in, void *out, long long nsites, cudaStream_t s);
+
 // ---- outer GCR driven on the device (blas.cu): ctl = {iterations, k, stop reason}, st = {|r|^2
 // estimate, tol^2 |b|^2, new estimate, breakdown flag}; the control kernel sets the condition
 // of the WHILE graph node that replays one iteration ----
@@ -201,6 +217,10 @@ void launch_coarsest_gcr(const Cx<double> *Yt, const Cx<double> *Minv, Geo2 g, i
                          cudaStream_t s);
 int coarsest_gcr_grid(int device);
 // bounded-barrier self-test (2 CTAs, `expected` arrivals); returns 1 if a wait gave up
+// cooperative launches and graphs holding them: serialised per device (see coarsest.cu)
+void coop_launch(const void *fn, dim3 grid, dim3 block, void **args, size_t smem, cudaStream_t s);
+bool coop_captured_take();  // a cooperative kernel was captured on this thread since the last call
+void coop_graph_launch(cudaGraphExec_t g, cudaStream_t s);
 int barrier_selftest(unsigned int expected, long long spin_limit, cudaStream_t s);
 constexpr int kCoarsestSlots = 68;
 // Same solve with each CTA's rows, vectors and Krylov basis resident in shared memory
@@ -208,6 +228,12 @@ constexpr int kCoarsestSlots = 68;
 // are n-entry publication buffers for the neighbours' reads; 2 grid barriers per iteration.
 // With Yt32 (an FP32 copy of A M) the stencil is stored and applied in FP32 while the Krylov
 // vectors, Gram-Schmidt, residuals and updates stay FP64.
+// FP32 variant of launch_coarsest_gcr (stencil A M and Krylov vectors in FP32, every reduction
+// summed in FP64) for mixed-precision cycles with a loose coarsest tolerance
+void launch_coarsest_gcr32(const Cx<float> *Yt, const Cx<double> *Minv, Geo2 g, int N, const Cx<double> *b,
+                           Cx<double> *x, Cx<float> *y, Cx<float> *r, Cx<float> *Z, Cx<float> *W, double *partials,
+                           unsigned int *bar, double tol, int restart, int max_iter, int *out, double *out_rel,
+                           int grid, cudaStream_t s);
 bool coarsest_smem_fits(Geo2 g, int N, int restart, int sms);
 void launch_coarsest_gcr_smem(const Cx<double> *Yt, const Cx<float> *Yt32, const Cx<double> *Minv, Geo2 g,
                               const Cx<double> *b, Cx<double> *x, Cx<double> *rpub, Cx<double> *ypub,

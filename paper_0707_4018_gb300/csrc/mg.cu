@@ -90,6 +90,7 @@ struct GraphCache {
   cudaGraphExec_t exec = nullptr;
   long long kernels = 0;
   long long apps[MG_MAX_LEVELS] = {0, 0, 0, 0};
+  bool coop = false;  // holds a cooperative kernel: launched through the cooperative lane
   void reset() {
     if (exec) cudaGraphExecDestroy(exec);
     exec = nullptr;
@@ -108,6 +109,11 @@ struct mg_ctx {
   std::vector<mg::Level> lv;
   mg::DevBuf<mg::Cx<double>> U64;
   mg::DevBuf<mg::Cx<float>> U32;
+  // MG_FP16: the fine level of the solve's FP32 cycles keeps its links and the smoother's r and
+  // A r in half with per-site norms (12 V bytes per field); half_now while such a cycle is built
+  bool half_fine = false, half_now = false;
+  mg::DevBuf<float> U16;             // 2 V floats: V x (U^0, U^1) half2 pairs
+  mg::DevBuf<float> hr[2], hA[2];    // 3 V floats per field, max_rhs fields
   // coarsest
   bool use_lu = false;
   int nc = 0;
@@ -118,6 +124,8 @@ struct mg_ctx {
   mg::DevBuf<mg::Cx<double>> cg_Minv, cg_Yt, cg_work, cg_y;
   mg::DevBuf<mg::Cx<float>> cg_Yt32;  // FP32 copy of A M for mixed-precision cycles (shared-memory kernel)
   bool cg_cluster = false;            // one-cluster FP32 coarsest GCR (mixed precision, loose tolerance)
+  bool cg_large32 = false;            // whole-chip FP32 coarsest GCR for large coarsest levels (same regime)
+  mg::DevBuf<mg::Cx<float>> cZ32, cW32, cr32, cy32;
   mg::DevBuf<mg::Cx<float>> cl_rpub, cl_ypub;  // its publication buffers (nbatch vectors)
   mg::DevBuf<mg::Cx<float>> cl_Yr;             // A M in FP32 as row-major blocks
   mg::DevBuf<int> dl_ctl;                      // device-driven outer loop: counters, residual state, w
@@ -226,7 +234,10 @@ template <typename R>
 static void apply_op(mg_ctx &c, int l, const Cx<R> *in, Cx<R> *out, const Cx<R> *b = nullptr, double a = 1.0,
                      double cc = 0.0, int nvec = 1) {
   Level &L = c.lv[l];
-  if (l == 0)
+  if (l == 0 && sizeof(R) == 4 && c.half_now)  // FP16 fine level: half links, FP32 vectors
+    launch_dslash_hl(c.U16.p, reinterpret_cast<const Cx<float> *>(in), reinterpret_cast<Cx<float> *>(out), L.geo,
+                     diag_of(c), reinterpret_cast<const Cx<float> *>(b), a, cc, c.s, nvec, c.cur_shift);
+  else if (l == 0)
     launch_dslash<R>(Uof<R>(c), in, out, L.geo, diag_of(c), b, a, cc, c.s, nvec, c.cur_shift);
   else if (sizeof(R) == 4 && c.tc_batch && nvec >= 8 && L.Ypk.p != nullptr)
     // batched solves: the coarse operator on tensor cores for all vectors at once (BF16
@@ -265,6 +276,28 @@ static void smooth(mg_ctx &c, int l, const Cx<R> *b, Cx<R> *x, int nu, bool accu
   if (nu <= 0) {
     if (!accumulate) launch_zero<R>(x, L.n * nvec, c.s);
     if (r_out != nullptr && r_out != b) launch_copy<R>(b, r_out, L.n * nvec, c.s);
+    return;
+  }
+  if (l == 0 && sizeof(R) == 4 && c.half_now) {
+    // FP16 fine level: r and A r alternate between two half fields; x, b and r_out stay FP32
+    if (nvec > c.p.max_rhs) fail(MG_ERR_STATE, "half-storage smoother: batch larger than max_rhs");
+    float *hp[2] = {reinterpret_cast<float *>(c.mrpart[0].p), reinterpret_cast<float *>(c.mrpart[1].p)};
+    const long long hcap = (long long)(c.mrpart[0].n * sizeof(double) / sizeof(float));
+    Cx<float> *xf = reinterpret_cast<Cx<float> *>(x);
+    launch_mr_iteration_half(c.U16.p, L.geo, diag_of(c), c.cur_shift, false, reinterpret_cast<const Cx<float> *>(b),
+                             nullptr, nullptr, nullptr, c.p.omega, nullptr, false, c.hr[0].p, c.hA[0].p, hp[0], hcap,
+                             c.s, nvec);
+    c.apps[l] += nvec;
+    int cur = 0;
+    for (int i = 1; i < nu; ++i) {
+      launch_mr_iteration_half(c.U16.p, L.geo, diag_of(c), c.cur_shift, true, nullptr, c.hr[cur].p, c.hA[cur].p,
+                               hp[cur], c.p.omega, xf, i == 1 && !accumulate, c.hr[cur ^ 1].p, c.hA[cur ^ 1].p,
+                               hp[cur ^ 1], hcap, c.s, nvec);
+      c.apps[l] += nvec;
+      cur ^= 1;
+    }
+    launch_mr_last_half(c.hr[cur].p, c.hA[cur].p, hp[cur], c.p.omega, xf, nu == 1 && !accumulate,
+                        reinterpret_cast<Cx<float> *>(r_out), L.geo, c.s, nvec);
     return;
   }
   // two alternating partials buffers in the vectors' precision
@@ -404,6 +437,12 @@ static void coarsest_solve64(mg_ctx &c, const Cx<double> *b, Cx<double> *x, int 
                              c.cg_partials.p, c.cg_bar.p,
                              c.p.coarsest_tol, c.p.coarsest_restart, c.p.coarsest_max_iter, c.cg_out.p, c.cg_rel.p,
                              c.cg_grid, c.s);
+  else if (c.cg_large32 && slot == 0)
+    // a quarter of the SMs: the FP32 solve is latency-bound (grid barriers over fewer CTAs are
+    // cheaper), and the other SMs stay free for the non-cooperative work of concurrent streams
+    launch_coarsest_gcr32(c.cg_Yt32.p, Minv, L.geo, L.nint, b, x, c.cy32.p, c.cr32.p, c.cZ32.p, c.cW32.p,
+                          c.cg_partials.p, c.cg_bar.p, c.p.coarsest_tol, c.p.coarsest_restart, c.p.coarsest_max_iter,
+                          c.cg_out.p, c.cg_rel.p, std::max(1, c.cg_grid / 4), c.s);
   else
     launch_coarsest_gcr(Yt, Minv, L.geo, L.nint, b, x, c.cg_y.p, c.cr.p, c.cZ.p, c.cW.p,
                         c.cg_partials.p, c.cg_bar.p, c.p.coarsest_tol, c.p.coarsest_restart, c.p.coarsest_max_iter,
@@ -505,11 +544,13 @@ static void graph_run(mg_ctx &c, GraphCache &g, F &&body) {
     for (int l = 0; l < MG_MAX_LEVELS; ++l) a0[l] = c.apps[l];
     bool ok = cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
+      (void)coop_captured_take();
       try {
         body();
       } catch (const Error &) {
         ok = false;
       }
+      g.coop = coop_captured_take();
       cudaGraph_t graph = nullptr;
       const cudaError_t e = cudaStreamEndCapture(c.s, &graph);
       ok = ok && e == cudaSuccess && graph != nullptr;
@@ -538,7 +579,10 @@ static void graph_run(mg_ctx &c, GraphCache &g, F &&body) {
     }
   }
   if (g.exec != nullptr) {
-    MG_CUDA(cudaGraphLaunch(g.exec, c.s));
+    if (g.coop)
+      coop_graph_launch(g.exec, c.s);
+    else
+      MG_CUDA(cudaGraphLaunch(g.exec, c.s));
     g_launches.fetch_add(g.kernels);
     for (int l = 0; l < MG_MAX_LEVELS; ++l) c.apps[l] += g.apps[l];
   } else {
@@ -549,10 +593,19 @@ static void graph_run(mg_ctx &c, GraphCache &g, F &&body) {
 // z = V r on the finest level in the context precision (r, z FP64). The cycle
 // reads r from the fixed buffer `rfix` (the outer residual) and leaves its result
 // in a fixed buffer, so one captured graph serves every call.
+// the solve's cycles of an MG_FP16 context run their fine level in half storage
+struct HalfCycles {
+  mg_ctx &c;
+  bool old;
+  explicit HalfCycles(mg_ctx &cc) : c(cc), old(cc.half_now) { c.half_now = c.half_fine; }
+  ~HalfCycles() { c.half_now = old; }
+};
+
 static void precondition(mg_ctx &c, const Cx<double> *r, Cx<double> *z) {
   Level &F = c.lv[0];
   const Cx<double> *rfix = c.orr.p;
   if (r != rfix) launch_copy<double>(r, c.orr.p, F.n, c.s);
+  HalfCycles hc(c);
   if (c.p.precision == MG_FP32) {
     graph_run(c, c.pre[1], [&] {
       launch_convert<float, double>(rfix, F.w32.b.p, F.n, c.s);
@@ -606,6 +659,7 @@ static void precondition_batch(mg_ctx &c, int nb, const Cx<double> *r, unsigned 
   Level &F = c.lv[0];
   const long long n = F.n;
   launch_copy_masked(r, c.brin.p, n, nb, mask, c.s);
+  HalfCycles hc(c);
   if (c.p.precision == MG_FP32) {
     graph_run(c, c.preb[1][nb], [&] {
       launch_convert<float, double>(c.brin.p, F.w32.b.p, n * nb, c.s);
@@ -753,6 +807,7 @@ struct DevSolve {
   std::vector<GcrOut> out;    // per vector
   int iters = 0;              // outer iterations of the context's loop
   long long kernels_per_it = 0, apps_per_it[MG_MAX_LEVELS] = {0, 0, 0, 0};
+  bool coop = false;          // the loop body holds a cooperative kernel
 };
 
 static void alloc_batch(mg_ctx &c);
@@ -814,6 +869,8 @@ static void devloop_capture(DevSolve &d, cudaGraph_t body, cudaGraphConditionalH
   long long a0[MG_MAX_LEVELS];
   for (int l = 0; l < MG_MAX_LEVELS; ++l) a0[l] = c.apps[l];
   MG_CUDA(cudaStreamBeginCaptureToGraph(c.s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  (void)coop_captured_take();
+  HalfCycles hc(c);
   bool ok = true;
   if (d.nb > 1) {
     // one lockstep iteration of the batch: z_v = V r_v for the iterating vectors (0 for the
@@ -858,6 +915,7 @@ static void devloop_capture(DevSolve &d, cudaGraph_t body, cudaGraphConditionalH
   } catch (const Error &) {
     ok = false;
   }
+  d.coop = coop_captured_take();
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(c.s, &g);
   d.kernels_per_it = g_launches.load() - l0;
@@ -887,6 +945,10 @@ static void devloop_launch(std::vector<DevSolve *> &act, cudaStream_t ls) {
             launch_coarse_apply_tc(c.lv[l].Ypk.p, c.lv[l].w32.r.p, c.lv[l].w32.Ar.p, c.lv[l].geo, d->nb, nullptr, 1.0,
                                    0.0, nullptr, c.s);
     }
+    // loops that hold cooperative kernels run one after another (their grid barriers need the
+    // whole GPU); the others run beside them
+    cudaGraphNode_t last_coop = nullptr;
+    bool any_coop = false;
     for (DevSolve *d : act) {
       cudaGraphConditionalHandle h;
       MG_CUDA(cudaGraphConditionalHandleCreate(&h, top, 1, cudaGraphCondAssignDefault));
@@ -898,13 +960,21 @@ static void devloop_launch(std::vector<DevSolve *> &act, cudaStream_t ls) {
       cudaGraphNode_t node;
       MG_CUDA(cudaGraphAddNode(&node, top, nullptr, nullptr, 0, &np));
       devloop_capture(*d, np.conditional.phGraph_out[0], h);
+      if (d->coop) {
+        if (last_coop != nullptr) MG_CUDA(cudaGraphAddDependencies(top, &last_coop, &node, nullptr, 1));
+        last_coop = node;
+        any_coop = true;
+      }
     }
     MG_CUDA(cudaGraphInstantiate(&exec, top, 0));
     for (DevSolve *d : act) {  // the launch stream waits for every context's queued work
       MG_CUDA(cudaEventRecord(d->c->ev, d->c->s));
       MG_CUDA(cudaStreamWaitEvent(ls, d->c->ev, 0));
     }
-    MG_CUDA(cudaGraphLaunch(exec, ls));
+    if (any_coop)
+      coop_graph_launch(exec, ls);
+    else
+      MG_CUDA(cudaGraphLaunch(exec, ls));
     MG_CUDA(cudaStreamSynchronize(ls));
   } catch (...) {
     if (exec) cudaGraphExecDestroy(exec);
@@ -1150,7 +1220,8 @@ static void validate(const mg_geom *g, const mg_params *p) {
   if ((long long)g->dims[0] * g->dims[1] * 8 >= (1LL << 31))
     fail(MG_ERR_UNSUPPORTED, "lattices are limited to fewer than 2^28 sites (32-bit dof indexing)");
   if (p->levels < 2 || p->levels > MG_MAX_LEVELS) fail(MG_ERR_INVALID_ARG, "levels must be in [2, 4]");
-  if (p->precision != MG_FP64 && p->precision != MG_FP32) fail(MG_ERR_INVALID_ARG, "unknown precision");
+  if (p->precision != MG_FP64 && p->precision != MG_FP32 && p->precision != MG_FP16)
+    fail(MG_ERR_INVALID_ARG, "unknown precision");
   if (p->n_pass < 1 || p->nu_pre < 0 || p->nu_post < 0 || p->nu_setup < 0) fail(MG_ERR_INVALID_ARG, "bad counts");
   if (p->gcr_restart < 1 || p->gcr_restart > 128) fail(MG_ERR_INVALID_ARG, "gcr_restart must be in [1, 128]");
   if (p->coarsest_restart < 1 || p->coarsest_restart > 32)
@@ -1207,11 +1278,27 @@ static void alloc_batch(mg_ctx &c) {
   pool_ready();
 }
 
+// the parameters as the caller gave them (an MG_FP16 context runs as FP32 internally)
+static mg_params user_params(const mg_ctx &c) {
+  mg_params p = c.p;
+  if (c.half_fine) p.precision = MG_FP16;
+  return p;
+}
+
+// FP32 and half copies of the fine links for the cycles
+static void make_link_copies(mg_ctx &c) {
+  if (c.p.precision == MG_FP32) launch_convert<float, double>(c.U64.p, c.U32.p, c.U64.n, c.s);
+  if (c.half_fine) launch_half_convert(2, MG_FP64, c.U64.p, c.U16.p, c.lv[0].geo.nsites, c.s);
+}
+
 static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_params *p, void *stream) {
   validate(g, p);
   auto c = std::make_unique<mg_ctx>();
   c->geom = *g;
   c->p = *p;
+  // MG_FP16 is an FP32 context whose solve cycles keep the fine level in half storage
+  c->half_fine = p->precision == MG_FP16;
+  if (c->half_fine) c->p.precision = MG_FP32;
   c->m = m;
   c->user = static_cast<cudaStream_t>(stream);
   MG_CUDA(cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking));
@@ -1224,7 +1311,7 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
   for (int l = 0; l + 1 < p->levels; ++l) c->nbatch = std::max(c->nbatch, p->Nv[l]);
   c->nbatch = std::max(c->nbatch, p->max_rhs);
   int L0 = g->dims[0], L1 = g->dims[1], nint = 2;
-  const bool f32 = p->precision == MG_FP32;
+  const bool f32 = c->p.precision == MG_FP32;
   for (int l = 0; l < p->levels; ++l) {
     Level &L = c->lv[l];
     L.geo = Geo2{L0, L1, (long long)L0 * L1};
@@ -1279,6 +1366,13 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
   }
   c->U64.alloc(F.geo.nsites * 2);
   if (f32) c->U32.alloc(F.geo.nsites * 2);
+  if (c->half_fine) {
+    c->U16.alloc(F.geo.nsites * 2);
+    for (int i = 0; i < 2; ++i) {
+      c->hr[i].alloc(F.geo.nsites * 3 * (size_t)p->max_rhs);
+      c->hA[i].alloc(F.geo.nsites * 3 * (size_t)p->max_rhs);
+    }
+  }
   // coarsest
   const Level &Cst = c->lv.back();
   c->nc = (int)Cst.n;
@@ -1307,9 +1401,17 @@ static std::unique_ptr<mg_ctx> create(const mg_geom *g, double m, const mg_param
     // above FP32 rounding (the Krylov vectors and reductions stay FP64)
     c->cg_cluster = f32 && p->coarsest_tol >= 1e-5 && std::getenv("MG_NO_CLUSTER_COARSEST") == nullptr &&
                     coarsest_cluster_fits(Cst.geo, Cst.nint, p->coarsest_restart);
+    c->cg_large32 = f32 && !c->cg_smem && !c->cg_cluster && p->coarsest_tol >= 1e-5 &&
+                    std::getenv("MG_FP64_COARSEST_STENCIL") == nullptr;
     if ((f32 && c->cg_smem && p->coarsest_tol >= 1e-5 && std::getenv("MG_FP64_COARSEST_STENCIL") == nullptr) ||
-        c->cg_cluster)
+        c->cg_cluster || c->cg_large32)
       c->cg_Yt32.alloc(c->cg_Yt.n);
+    if (c->cg_large32) {
+      c->cZ32.alloc((size_t)p->coarsest_restart * Cst.n);
+      c->cW32.alloc((size_t)p->coarsest_restart * Cst.n);
+      c->cr32.alloc(Cst.n);
+      c->cy32.alloc(Cst.n);
+    }
     if (c->cg_cluster) {
       c->cl_Yr.alloc(c->cg_Yt.n);
       c->cl_rpub.alloc((size_t)c->nbatch * Cst.n);
@@ -1475,7 +1577,7 @@ static std::unique_ptr<mg_ctx> make_context(const mg_geom *g, const void *U, dou
   }
   auto c = create(g, m, p, stream);
   MG_CUDA(cudaMemcpyAsync(c->U64.p, U, c->U64.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, c->s));
-  if (c->p.precision == MG_FP32) launch_convert<float, double>(c->U64.p, c->U32.p, c->U64.n, c->s);
+  make_link_copies(*c);
   if (vectors == nullptr) {
     setup_level(*c, 0, true);
   } else {
@@ -1791,9 +1893,10 @@ int mg_clone(mg_ctx *src, double m, void *stream, mg_ctx **out) {
     if (src->e4) fail(MG_ERR_UNSUPPORTED, "clones are built for d = 2");
     check_fresh(*src);
     MG_CUDA(cudaStreamSynchronize(src->s));  // the source's buffers are final
-    auto c = create(&src->geom, m, &src->p, stream);
+    const mg_params sp = user_params(*src);
+    auto c = create(&src->geom, m, &sp, stream);
     MG_CUDA(cudaMemcpyAsync(c->U64.p, src->U64.p, c->U64.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, c->s));
-    if (c->p.precision == MG_FP32) launch_convert<float, double>(c->U64.p, c->U32.p, c->U64.n, c->s);
+    make_link_copies(*c);
     for (int l = 0; l + 1 < c->p.levels; ++l) {
       Level &L = c->lv[l];
       const Level &S = src->lv[l];
@@ -1823,7 +1926,7 @@ int mg_save_setup(mg_ctx *c, const char *path) {
     std::memcpy(h.magic, kSetupMagic, 8);
     h.version = 1;
     h.g = c->geom;
-    h.p = c->p;
+    h.p = user_params(*c);
     h.m = c->m;
     std::vector<std::vector<Cx<double>>> vecs;
     if (c->e4) {
@@ -1948,7 +2051,7 @@ int mg_setup_learned(mg_ctx **ctx, const mg_geom *g, const void *U, double m, co
     auto c = create(g, m, p, stream);
     MG_CUDA(cudaMemcpyAsync(c->U64.p, U, c->U64.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, c->s));
     const bool f32 = c->p.precision == MG_FP32;
-    if (f32) launch_convert<float, double>(c->U64.p, c->U32.p, c->U64.n, c->s);
+    make_link_copies(*c);
     Level &F = c->lv[0];
     nullnet_predict(*net, *g, c->U64.p, noise_seed, F.nullv.p, c->s);
     if (nu_refine > 0) {
@@ -2006,7 +2109,7 @@ int mg_context_info(const mg_ctx *c, mg_geom *g, mg_params *p, double *m) {
   return guarded([&] {
     if (!c) fail(MG_ERR_INVALID_ARG, "null context");
     if (g) *g = c->geom;
-    if (p) *p = c->p;
+    if (p) *p = c->e4 ? c->p : user_params(*c);
     if (m) *m = c->m;
   });
 }
@@ -2091,8 +2194,22 @@ int mg_dslash(const mg_geom *g, const void *U, double m, const void *in, void *o
     else if (precision == MG_FP32)
       launch_dslash<float>(static_cast<const Cx<float> *>(U), static_cast<const Cx<float> *>(in),
                            static_cast<Cx<float> *>(out), geo, 2.0 + m, nullptr, 1.0, 0.0, s);
+    else if (precision == MG_FP16)
+      launch_dslash_half(U, in, out, geo, 2.0 + m, s);
     else
       fail(MG_ERR_INVALID_ARG, "unknown precision");
+  });
+}
+
+int mg_half_convert(int what, int precision, const void *in, void *out, long long nsites, void *stream) {
+  return guarded([&] {
+    need_ptr(in);
+    need_ptr(out);
+    if (in == out) fail(MG_ERR_INVALID_ARG, "in and out must not alias");
+    if (what < 0 || what > 2) fail(MG_ERR_INVALID_ARG, "what must be 0, 1 or 2");
+    if (precision != MG_FP64 && precision != MG_FP32) fail(MG_ERR_INVALID_ARG, "precision must be MG_FP64 or MG_FP32");
+    if (nsites < 1 || nsites >= (1LL << 31)) fail(MG_ERR_INVALID_ARG, "nsites out of range");
+    launch_half_convert(what, precision, in, out, nsites, static_cast<cudaStream_t>(stream));
   });
 }
 

@@ -31,6 +31,9 @@ CALIBRATED = [(1, 1024, 3.0), (1, 1024, 6.0), (1, 1024, 10.0)]
 CALIBRATION_L = 256
 # (workload id, dims) of the 4d SU(3) fields: projected 1 + 0.4 H links after 4 APE steps (alpha 0.5)
 FIELDS4 = [(3, (16, 16, 16, 32))]
+# a smaller lattice of the same 4d recipe: when the Arnoldi scan of the 16^3 x 32 field is too slow,
+# its m_c is taken from this calibration (as the 1024^2 fields take theirs from 256^2)
+CALIBRATION4 = (8, 8, 8, 16)
 
 
 def key4(wid, dims):
@@ -53,6 +56,8 @@ def main():
     ap.add_argument("--only", default=None)
     ap.add_argument("--su3", action="store_true", help="the 4d SU(3) fields only")
     ap.add_argument("--calibrated", action="store_true", help="the 1024^2 fields (m_c from 256^2)")
+    ap.add_argument("--su3-calibrated", action="store_true",
+                    help="the 4d fields with m_c from the 8^3 x 16 field of the same recipe")
     args = ap.parse_args()
     table = json.load(open(OUT)) if os.path.exists(OUT) else {}
     if args.calibrated:
@@ -71,6 +76,23 @@ def main():
                        m_crit=table[src]["m_crit"], m_crit_from=src, gen_seconds=round(t1 - t0, 1))
             print(key(wid, L, beta), row, flush=True)
             save(key(wid, L, beta), row)
+        return
+    if args.su3_calibrated:
+        for wid, dims in FIELDS4:
+            t0 = time.time()
+            Uc = inputs.su3_links(CALIBRATION4, seed=inputs.workload_seed(wid, CALIBRATION4[0], 0.0))
+            mc = spectrum.critical_mass_arnoldi(Uc, Lattice(CALIBRATION4), Nc=3, k=4, ncv=40, tol=1e-6)
+            t1 = time.time()
+            src = key4(wid, CALIBRATION4)
+            save(src, dict(workload_id=wid, dims=list(CALIBRATION4), eps=0.4, ape_steps=4, ape_alpha=0.5,
+                           seed=inputs.workload_seed(wid, CALIBRATION4[0], 0.0),
+                           links_digest=inputs.field_digest(Uc), m_crit=mc, scan_seconds=round(t1 - t0, 1)))
+            U = inputs.su3_links(dims, seed=inputs.workload_seed(wid, dims[0], 0.0))
+            row = dict(workload_id=wid, dims=list(dims), eps=0.4, ape_steps=4, ape_alpha=0.5,
+                       seed=inputs.workload_seed(wid, dims[0], 0.0), links_digest=inputs.field_digest(U),
+                       m_crit=mc, m_crit_from=src)
+            print(src, mc, key4(wid, dims), row, flush=True)
+            save(key4(wid, dims), row)
         return
     if args.su3:
         for wid, dims in FIELDS4:

@@ -251,14 +251,17 @@ def test_solve_is_bitwise_reproducible(precision):
     assert np.array_equal(outs[0].view(np.uint64), outs[1].view(np.uint64))
 
 
-@pytest.mark.parametrize("kernel", ["cluster", "smem_fp32_stencil"])
+@pytest.mark.parametrize("kernel", ["cluster", "smem_fp32_stencil", "large32"])
 def test_fp32_stencil_coarsest_solve_meets_its_tolerance(kernel, monkeypatch):
-    # mixed precision with a loose coarsest tolerance: the one-cluster FP32 GCR, or (cluster kernel
-    # switched off) A M stored and applied in FP32 inside the whole-chip FP64 GCR; the solution
-    # meets the tolerance against the oracle's FP64 coarse operator
+    # mixed precision with a loose coarsest tolerance: the one-cluster FP32 GCR, (cluster kernel
+    # switched off) A M stored and applied in FP32 inside the whole-chip FP64 GCR, or (both
+    # switched off, the path of large coarsest levels) the whole-chip FP32 GCR with FP64 sums;
+    # the solution meets the tolerance against the oracle's FP64 coarse operator
     import torch
     if kernel != "cluster":
         monkeypatch.setenv("MG_NO_CLUSTER_COARSEST", "1")
+    if kernel == "large32":
+        monkeypatch.setenv("MG_NO_SMEM_COARSEST", "1")
     dims = (64, 64)
     U, _, _ = inputs.schwinger_links(64, 6.0, sweeps=100, workload_id=5)
     hier, ctx, _ = make_pair(dims, 0.02, [(4, 4), (2, 2)], [8, 8], U, precision=1, coarsest_lu_max=0,

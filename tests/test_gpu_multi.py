@@ -98,3 +98,58 @@ def test_multi_solve_batches_of_right_hand_sides():
             e += 1
     for c in ctxs:
         c.close()
+
+
+@pytest.mark.parametrize("kernel", ["smem", "large32", "large64"])
+def test_concurrent_cooperative_coarsest_solves(kernel, monkeypatch):
+    # Contexts whose coarsest solve is a cooperative kernel (grid barriers over many CTAs): their
+    # setups run at once (mg_setup_batch, one stream each), their solves run from several host
+    # threads and from one multi-context graph. Cooperative launches pass through one lane per
+    # device, so none of them waits on CTAs that another one keeps off the GPU: every call
+    # succeeds, and the results equal those of the same contexts run one at a time.
+    import threading
+    import torch
+    import paper_0707_4018_gb300 as mg
+    monkeypatch.setenv("MG_NO_CLUSTER_COARSEST", "1")
+    if kernel != "smem":
+        monkeypatch.setenv("MG_NO_SMEM_COARSEST", "1")
+    tol_c = 1e-8 if kernel == "large64" else 0.2
+    n = 6
+    dims = (64, 64)
+    Us = [_case(64, 64, 6.0, 300 + i) for i in range(n)]
+    ms = [0.03 + 0.01 * i for i in range(n)]
+    p = mg.mg_default_params(levels=3, blocks=[(4, 4), (2, 2)], Nv=[8, 8], precision=1, n_pass=2,
+                             coarsest_tol=tol_c, coarsest_lu_max=0)
+    together = mg.Context.setup_batch([to_dev(U) for U in Us], ms, [dims] * n, [p] * n)
+    alone = [mg.Context.setup(to_dev(U), m, dims, p) for U, m in zip(Us, ms)]
+    chis = [to_dev(inputs.gaussian_source(64, 64, seed=40 + i)) for i in range(n)]
+    ref = [torch.empty_like(c) for c in chis]
+    st_ref = [alone[i].solve(chis[i], ref[i], 1e-10) for i in range(n)]
+    # host threads, one solve each, all at once
+    out = [torch.empty_like(c) for c in chis]
+    st_thr = [None] * n
+    err = []
+
+    def run(i):
+        try:
+            st_thr[i] = together[i].solve(chis[i], out[i], 1e-10)
+        except Exception as e:  # noqa: BLE001 - reported below
+            err.append(e)
+    th = [threading.Thread(target=run, args=(i,)) for i in range(n)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not err, err
+    torch.cuda.synchronize()
+    for i in range(n):
+        assert st_thr[i]["converged"] and st_thr[i]["iters"] == st_ref[i]["iters"], (i, st_thr[i], st_ref[i])
+        assert torch.equal(out[i], ref[i])
+    # one graph launch for all of them
+    outm = [torch.empty_like(c) for c in chis]
+    st_m = mg.solve_multi(together, chis, outm, 1e-10)
+    for i in range(n):
+        res = np.linalg.norm(to_host(chis[i]) - wilson.apply_D(Us[i], to_host(outm[i]), ms[i], Lattice(dims)))
+        assert st_m[i]["converged"] and res / np.linalg.norm(to_host(chis[i])) <= 1e-10, (i, st_m[i])
+    for c in together + alone:
+        c.close()
