@@ -603,7 +603,7 @@ def dslash_half_roofline(L_big: int = 4096, iters: int = 20):
                 gbs=V * 32 / t / 1e9, sites_per_s=V / t)
 
 
-def dslash4_roofline(precision: int, dims=(32, 32, 32, 64), iters: int = 20):
+def dslash4_roofline(precision: int, dims=(32, 32, 32, 64), iters: int = 20, compare_gather: bool = True):
     """4d SU(3) Wilson apply alone on a lattice far larger than L2 (32^3 x 64: 1 GB per FP32
     apply): algorithmic bytes / time. Links are Gaussian 3 x 3 matrices (the timing does not
     depend on the values; the parity tests use SU(3) fields)."""
@@ -616,23 +616,37 @@ def dslash4_roofline(precision: int, dims=(32, 32, 32, 64), iters: int = 20):
     psi = torch.randn((V, 4, 3), device="cuda", generator=g, dtype=dt)
     out = torch.empty_like(psi)
     stream = torch.cuda.current_stream()
-    for _ in range(3):
-        mg.mg_dslash(U, psi, out, 0.01, dims, precision)
-    ms = []
-    for _ in range(iters):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        mg.mg_dslash(U, psi, out, 0.01, dims, precision)
-        e1.record(stream)
-        e1.synchronize()
-        ms.append(e0.elapsed_time(e1))
-    t = statistics.median(ms) * 1e-3
     cplx = 16 if precision == 0 else 8
     per_site = (12 + 36 + 12) * cplx  # psi in, 4 links, psi out
-    return dict(lattice="x".join(str(v) for v in dims), dtype="f64" if precision == 0 else "f32",
-                bytes_per_site=per_site, flop_per_site=1368, ms=t * 1e3, gbs=V * per_site / t / 1e9,
-                tflops=V * 1368 / t / 1e12)
+
+    def timed():
+        for _ in range(3):
+            mg.mg_dslash(U, psi, out, 0.01, dims, precision)
+        ms = []
+        for _ in range(iters):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mg.mg_dslash(U, psi, out, 0.01, dims, precision)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms) * 1e-3
+
+    t = timed()
+    res = dict(lattice="x".join(str(v) for v in dims), dtype="f64" if precision == 0 else "f32",
+               bytes_per_site=per_site, flop_per_site=1368, ms=t * 1e3, gbs=V * per_site / t / 1e9,
+               tflops=V * 1368 / t / 1e12,
+               kernel="dslash4_tile_kernel (8x4x4x2 tiles)" if precision == 1 else "dslash4_kernel<double>")
+    if precision == 1 and compare_gather:
+        # the warp-gather kernel on the same inputs
+        os.environ["MG_DSLASH4_GATHER"] = "1"
+        try:
+            tg = timed()
+        finally:
+            del os.environ["MG_DSLASH4_GATHER"]
+        res["warp_gather_kernel"] = dict(ms=tg * 1e3, gbs=V * per_site / tg / 1e9)
+    return res
 
 
 # several gauge configurations of uneven sizes, 16 sources each (workload id, L, beta)
@@ -795,6 +809,8 @@ def coarsest_flops(iters: int, restart: int, n: int) -> float:
 
 CLUSTER_CTAS = 16   # CTAs (one per SM) of the coarsest solve's thread-block cluster
 GPU_SMS = 152
+# DRAM bytes per launch of coarsest_gcr_cluster_kernel (ncu, profiles/coarsest_gcr_cluster_256x256.md)
+CLUSTER_DRAM_BYTES = 3873536
 
 
 def coarsest_roofline(fields, iters_rep: int = 20):
@@ -997,8 +1013,26 @@ def run_only(case: str):
         print(json.dumps({"case": case, **su3_workload((1,), 2, batched=False)}))
         return
     if case.startswith("dslash4"):
-        r = dslash4_roofline(1 if case == "dslash4-f32" else 0, iters=3)
+        r = dslash4_roofline(1 if case == "dslash4-f32" else 0, iters=3, compare_gather=False)
         print(json.dumps({"case": case, **r}))
+        return
+    if case == "dslash4-sweep":
+        # the FP32 4d apply on 32^3 x 64 with each kernel variant (tile shapes, warp gather)
+        res = {}
+        for name, env in (("gather", ("MG_DSLASH4_GATHER", "1")), ("tileA_8x4x4x4", ("MG_DSLASH4_TILE", "0")),
+                          ("tileB_8x4x4x2", ("MG_DSLASH4_TILE", "1")), ("tileC_4x4x4x2", ("MG_DSLASH4_TILE", "2")),
+                          ("tileD_8x4x2x2", ("MG_DSLASH4_TILE", "3")), ("tileB_3cta", ("MG_DSLASH4_TILE", "4")),
+                          ("tileC_6cta", ("MG_DSLASH4_TILE", "5"))):
+            os.environ[env[0]] = env[1]
+            try:
+                r = dslash4_roofline(1, iters=10, compare_gather=False)
+            finally:
+                del os.environ[env[0]]
+            res[name] = {"ms": r["ms"], "gbs": r["gbs"]}
+        print(json.dumps({"case": case, **res}))
+        return
+    if case == "dslash-f16":
+        print(json.dumps({"case": case, **dslash_half_roofline(iters=3)}))
         return
     if case.startswith("dslash"):
         r = dslash_roofline(1 if case == "dslash-f32" else 0, iters=3)
@@ -1131,7 +1165,7 @@ def main():
                     help="solve with one host thread and host-driven loop per solve instead of one graph launch")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned near-null setup evaluation")
     ap.add_argument("--no-config2", action="store_true", help="skip the many-configuration x many-source batch")
-    ap.add_argument("--only", default=None, choices=["step", "dslash-f32", "dslash-f64", "dslash4-f32", "dslash4-f64", "solve", "vcycle",
+    ap.add_argument("--only", default=None, choices=["step", "dslash4-sweep", "dslash-f16", "dslash-f32", "dslash-f64", "dslash4-f32", "dslash4-f64", "solve", "vcycle",
                                                       "transfer", "coarse-tc", "coarse-tc4", "su3", "su3-prof",
                                                       "su3-batch-prof", "mixed-sizes", "learned", "large",
                                                       "config2"],
@@ -1248,7 +1282,8 @@ def main():
         "gpu_launches": mixed["launches"],
         "clocks": mixed["clocks"],
         "roofline": {"bound": "alu", "kernel": cr["kernel"], "achieved": cr["tflops"], "peak": cr["peak_fp32"],
-                     "unit": "TFLOP/s", "frac": cr["tflops"] / cr["peak_fp32"], "traffic": None,
+                     "unit": "TFLOP/s", "frac": cr["tflops"] / cr["peak_fp32"], "traffic": CLUSTER_DRAM_BYTES,
+                     "traffic_source": "profiles/coarsest_gcr_cluster_256x256.md",
                      "ms_per_launch": cr["ms"], "iters_per_launch": cr["iters"],
                      "peak_kind": "measured in this run (mg_alu_peak: FP32 FMA loop over all SMs)",
                      "sms_used": CLUSTER_CTAS,

@@ -23,6 +23,8 @@
 // once: 60 complex per site = 480 B (FP32) / 960 B (FP64). The neighbour
 // spinors (8 per site) and links (2 reads each) come from L2, which makes the
 // on-chip traffic about 3x the HBM traffic.
+#include <cstdlib>
+
 #include "kernels.h"
 #include "wilson4d.cuh"
 
@@ -207,9 +209,269 @@ __global__ void __launch_bounds__(32 * DSLASH4_WARPS, sizeof(R) == 4 ? 5 : 2) ds
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tiled FP32 apply, for extents divisible by the tile: one CTA per tile of the lattice, one site
+// per thread. Each site reads its spinor and its four forward links once and uses every link
+// twice: U_x^mu for its own forward hop (applied to the projected spinor of x + mu) and
+// U_x^mu^dagger for the backward hop of x + mu (applied to its own projected spinor here and
+// handed over). Per direction the tile exchanges these two half spinors (2 spins x 3 colours)
+// through shared memory; a site on a face of the tile forms the missing one itself from the
+// outside neighbour (its spinor, and for a backward hop its link, read through L2). On-chip
+// traffic per site: the 480 algorithmic bytes plus the faces' share, instead of 8 neighbour
+// spinors and 8 links per site.
+// ---------------------------------------------------------------------------
+
+// tile extents (powers of two) and the thread-id step of one hop in each direction
+template <int A0, int A1, int A2, int A3>
+struct Tile4 {
+  static constexpr int sites = A0 * A1 * A2 * A3;
+  template <int MU>
+  __host__ __device__ static constexpr int n() {
+    return MU == 0 ? A0 : MU == 1 ? A1 : MU == 2 ? A2 : A3;
+  }
+  template <int MU>
+  __host__ __device__ static constexpr int d() {
+    return MU == 0 ? 1 : MU == 1 ? A0 : MU == 2 ? A0 * A1 : A0 * A1 * A2;
+  }
+};
+
+__device__ __forceinline__ void load_spinor32(const Cx<float> *__restrict__ f, int x, Cx<float> (&p)[12]) {
+  const float4 *q = reinterpret_cast<const float4 *>(f) + (long long)x * 6;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const float4 w = __ldg(q + i);
+    p[2 * i] = mk(w.x, w.y);
+    p[2 * i + 1] = mk(w.z, w.w);
+  }
+}
+
+__device__ __forceinline__ void load_link32(const Cx<float> *__restrict__ U, int x, int mu, Cx<float> (&u)[9]) {
+  const float2 *q = reinterpret_cast<const float2 *>(U) + ((long long)x * 4 + mu) * 9;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const float2 w = __ldg(q + i);
+    u[i] = mk(w.x, w.y);
+  }
+}
+
+// h = psi_up - A_mu psi_dn (MINUS, the forward hop's (1 - gamma_mu)) or psi_up + A_mu psi_dn
+template <int MU, bool MINUS>
+__device__ __forceinline__ void project4(const Cx<float> (&p)[12], Cx<float> (&h)[6]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    Cx<float> a0, a1;
+    a_times<float, MU>(p[6 + c], p[9 + c], a0, a1);
+    h[c] = MINUS ? p[c] - a0 : p[c] + a0;
+    h[3 + c] = MINUS ? p[3 + c] - a1 : p[3 + c] + a1;
+  }
+}
+
+// t = U h (DAG false) or U^dagger h, for both spin rows of h
+template <bool DAG>
+__device__ __forceinline__ void link_times4(const Cx<float> (&u)[9], const Cx<float> (&h)[6], Cx<float> (&t)[6]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    Cx<float> t0 = mk(0.f, 0.f), t1 = mk(0.f, 0.f);
+#pragma unroll
+    for (int bb = 0; bb < 3; ++bb) {
+      if (DAG) {
+        cmac_conj(t0, u[bb * 3 + a], h[bb]);
+        cmac_conj(t1, u[bb * 3 + a], h[3 + bb]);
+      } else {
+        cmac(t0, u[a * 3 + bb], h[bb]);
+        cmac(t1, u[a * 3 + bb], h[3 + bb]);
+      }
+    }
+    t[a] = t0;
+    t[3 + a] = t1;
+  }
+}
+
+// acc_up += t, acc_dn -= A_mu^dagger t (forward hop) or += (backward hop)
+template <int MU, bool FWD>
+__device__ __forceinline__ void reconstruct4(const Cx<float> (&t)[6], Cx<float> (&acc)[12]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    Cx<float> l0, l1;
+    adag_times<float, MU>(t[c], t[3 + c], l0, l1);
+    acc[c] = acc[c] + t[c];
+    acc[3 + c] = acc[3 + c] + t[3 + c];
+    if (FWD) {
+      acc[6 + c] = acc[6 + c] - l0;
+      acc[9 + c] = acc[9 + c] - l1;
+    } else {
+      acc[6 + c] = acc[6 + c] + l0;
+      acc[9 + c] = acc[9 + c] + l1;
+    }
+  }
+}
+
+// the two hops of direction MU for the site of thread t (tile coordinate lm, lattice coordinate
+// cm, extent Lm, site stride sm); sF / sM: [6][sites] half spinors in flight
+template <class T, int MU>
+__device__ __forceinline__ void tile_hops(const Cx<float> *__restrict__ U, const Cx<float> *__restrict__ in,
+                                          const Cx<float> (&p)[12], int x, int t, int lm, int cm, int Lm, int sm,
+                                          float2 (*sF)[T::sites], float2 (*sM)[T::sites], Cx<float> (&acc)[12]) {
+  constexpr int n = T::template n<MU>(), d = T::template d<MU>();
+  Cx<float> u[9];
+  load_link32(U, x, MU, u);
+  Cx<float> h[6], m[6];
+  if (lm > 0) {  // the forward hop of x - mu needs (1 - gamma_mu) psi_x
+    project4<MU, true>(p, h);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sF[k][t - d] = make_float2(h[k].re, h[k].im);
+  }
+  if (lm < n - 1) {  // the backward hop of x + mu needs U_x^mu^dagger (1 + gamma_mu) psi_x
+    project4<MU, false>(p, h);
+    link_times4<true>(u, h, m);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sM[k][t + d] = make_float2(m[k].re, m[k].im);
+  }
+  __syncthreads();
+  if (lm < n - 1) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const float2 w = sF[k][t];
+      h[k] = mk(w.x, w.y);
+    }
+  } else {
+    Cx<float> q[12];
+    load_spinor32(in, cm + 1 == Lm ? x - cm * sm : x + sm, q);
+    project4<MU, true>(q, h);
+  }
+  link_times4<false>(u, h, m);
+  reconstruct4<MU, true>(m, acc);
+  if (lm > 0) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const float2 w = sM[k][t];
+      m[k] = mk(w.x, w.y);
+    }
+  } else {
+    const int y = cm == 0 ? x + (Lm - 1) * sm : x - sm;
+    Cx<float> q[12];
+    load_spinor32(in, y, q);
+    load_link32(U, y, MU, u);
+    project4<MU, false>(q, h);
+    link_times4<true>(u, h, m);
+  }
+  reconstruct4<MU, false>(m, acc);
+  __syncthreads();
+}
+
+template <class T, int MINB, bool SHIFT>
+__global__ void __launch_bounds__(T::sites, MINB) dslash4_tile_kernel(const Cx<float> *__restrict__ U,
+                                                                      const Cx<float> *__restrict__ in,
+                                                                      Cx<float> *__restrict__ out, Geo4 g,
+                                                                      float diag, const Cx<float> *__restrict__ b,
+                                                                      float a, float c, long long ldv,
+                                                                      const double *__restrict__ shift) {
+  constexpr int A0 = T::template n<0>(), A1 = T::template n<1>(), A2 = T::template n<2>();
+  __shared__ float2 sF[6][T::sites], sM[6][T::sites];
+  if (SHIFT) diag += (float)shift[blockIdx.y];
+  in += blockIdx.y * ldv;
+  out += blockIdx.y * ldv;
+  if (b != nullptr) b += blockIdx.y * ldv;
+  const int t = threadIdx.x;
+  const int l0 = t % A0, l1 = (t / A0) % A1, l2 = (t / (A0 * A1)) % A2, l3 = t / (A0 * A1 * A2);
+  const int n0 = g.L[0] / A0, n1 = g.L[1] / A1, n2 = g.L[2] / A2;
+  int tb = blockIdx.x;
+  const int b0 = tb % n0;
+  tb /= n0;
+  const int b1 = tb % n1;
+  tb /= n1;
+  const int b2 = tb % n2;
+  const int b3 = tb / n2;
+  const int c0 = b0 * A0 + l0, c1 = b1 * A1 + l1, c2 = b2 * A2 + l2, c3 = b3 * T::template n<3>() + l3;
+  const int s1 = g.L[0], s2 = g.L[0] * g.L[1], s3 = s2 * g.L[2];
+  const int x = c0 + c1 * s1 + c2 * s2 + c3 * s3;
+  Cx<float> p[12], acc[12];
+  load_spinor32(in, x, p);
+#pragma unroll
+  for (int i = 0; i < 12; ++i) acc[i] = mk(0.f, 0.f);
+  tile_hops<T, 0>(U, in, p, x, t, l0, c0, g.L[0], 1, sF, sM, acc);
+  tile_hops<T, 1>(U, in, p, x, t, l1, c1, g.L[1], s1, sF, sM, acc);
+  tile_hops<T, 2>(U, in, p, x, t, l2, c2, g.L[2], s2, sF, sM, acc);
+  tile_hops<T, 3>(U, in, p, x, t, l3, c3, g.L[3], s3, sF, sM, acc);
+#pragma unroll
+  for (int i = 0; i < 12; ++i)
+    p[i] = mk(a * (diag * p[i].re - 0.5f * acc[i].re), a * (diag * p[i].im - 0.5f * acc[i].im));
+  if (b != nullptr) {
+    Cx<float> q[12];
+    load_spinor32(b, x, q);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) p[i] = mk(p[i].re + c * q[i].re, p[i].im + c * q[i].im);
+  }
+  float4 *o = reinterpret_cast<float4 *>(out) + (long long)x * 6;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) o[i] = make_float4(p[2 * i].re, p[2 * i].im, p[2 * i + 1].re, p[2 * i + 1].im);
+}
+
+// tile shapes of the tiled kernel; MG_DSLASH4_TILE picks one (default 1), MG_DSLASH4_GATHER the
+// warp-gather kernel
+using TileA = Tile4<8, 4, 4, 4>;  // 512 threads, 1 CTA per SM
+using TileB = Tile4<8, 4, 4, 2>;  // 256 threads, 2 CTAs per SM
+using TileC = Tile4<4, 4, 4, 2>;  // 128 threads, 4 CTAs per SM
+using TileD = Tile4<8, 4, 2, 2>;  // 128 threads, 4 CTAs per SM
+
+template <class T>
+static bool tile_divides(const Geo4 &g) {
+  return g.L[0] % T::template n<0>() == 0 && g.L[1] % T::template n<1>() == 0 && g.L[2] % T::template n<2>() == 0 &&
+         g.L[3] % T::template n<3>() == 0;
+}
+
+template <class T, int MINB>
+static void launch_tile4(const Cx<float> *U, const Cx<float> *in, Cx<float> *out, Geo4 g, double diag,
+                         const Cx<float> *b, double a, double c, cudaStream_t s, int nvec, const double *shift) {
+  const dim3 grid((unsigned int)(g.nsites / T::sites), nvec);
+  if (shift != nullptr)
+    dslash4_tile_kernel<T, MINB, true><<<grid, T::sites, 0, s>>>(U, in, out, g, (float)diag, b, (float)a, (float)c,
+                                                                  12 * g.nsites, shift);
+  else
+    dslash4_tile_kernel<T, MINB, false><<<grid, T::sites, 0, s>>>(U, in, out, g, (float)diag, b, (float)a,
+                                                                   (float)c, 12 * g.nsites, nullptr);
+  MG_LAUNCHED();
+}
+
+// true when a tiled kernel took the apply
+static bool try_tile4(const Cx<float> *U, const Cx<float> *in, Cx<float> *out, Geo4 g, double diag,
+                      const Cx<float> *b, double a, double c, cudaStream_t s, int nvec, const double *shift) {
+  if (std::getenv("MG_DSLASH4_GATHER") != nullptr) return false;
+  const char *v = std::getenv("MG_DSLASH4_TILE");
+  const int which = v != nullptr ? std::atoi(v) : 1;
+  if (which == 0 && tile_divides<TileA>(g)) {
+    launch_tile4<TileA, 1>(U, in, out, g, diag, b, a, c, s, nvec, shift);
+    return true;
+  }
+  if (which == 2 && tile_divides<TileC>(g)) {
+    launch_tile4<TileC, 4>(U, in, out, g, diag, b, a, c, s, nvec, shift);
+    return true;
+  }
+  if (which == 3 && tile_divides<TileD>(g)) {
+    launch_tile4<TileD, 4>(U, in, out, g, diag, b, a, c, s, nvec, shift);
+    return true;
+  }
+  if (which == 4 && tile_divides<TileB>(g)) {  // 3 CTAs per SM: at most 85 registers
+    launch_tile4<TileB, 3>(U, in, out, g, diag, b, a, c, s, nvec, shift);
+    return true;
+  }
+  if (which == 5 && tile_divides<TileC>(g)) {  // 6 CTAs per SM
+    launch_tile4<TileC, 6>(U, in, out, g, diag, b, a, c, s, nvec, shift);
+    return true;
+  }
+  if (tile_divides<TileB>(g)) {
+    launch_tile4<TileB, 2>(U, in, out, g, diag, b, a, c, s, nvec, shift);
+    return true;
+  }
+  return false;
+}
+
 template <typename R>
 void launch_dslash4(const Cx<R> *U, const Cx<R> *in, Cx<R> *out, Geo4 g, double diag, const Cx<R> *b, double a,
                     double c, cudaStream_t s, int nvec, const double *shift) {
+  if constexpr (sizeof(R) == 4) {
+    if (try_tile4(U, in, out, g, diag, b, a, c, s, nvec, shift)) return;
+  }
   const int threads = 32 * DSLASH4_WARPS;
   const dim3 grid(grid_for(g.nsites, threads), nvec);
   if (shift != nullptr)

@@ -107,6 +107,81 @@ __global__ void __launch_bounds__(256, 8) dslash_half_kernel(const __half2 *__re
   store_site(out, out_nrm, x, o.a, o.b);
 }
 
+// two sites (x0, x0 + 1) of a row per thread, L0 even: the pair's own values, its neighbours in
+// rows x1 +- 1 and its forward links are one 16-byte load each (8-byte norm pairs), the two
+// sites are each other's x0 neighbours, and only x0 - 1 and x0 + 2 are single loads; the
+// per-thread instruction count, which bounds the one-site kernel, is about halved
+__device__ __forceinline__ void load_pair2(const __half2 *d, const float *nrm, long long x, Pair<float> &p,
+                                           Pair<float> &q) {
+  const uint4 raw = reinterpret_cast<const uint4 *>(d)[x >> 1];  // sites x, x + 1 (x even)
+  const float2 nu = reinterpret_cast<const float2 *>(nrm)[x >> 1];
+  __half2 h[4];
+  memcpy(&h[0], &raw.x, 4);
+  memcpy(&h[1], &raw.y, 4);
+  memcpy(&h[2], &raw.z, 4);
+  memcpy(&h[3], &raw.w, 4);
+  p.a = h2c(h[0], nu.x);
+  p.b = h2c(h[1], nu.x);
+  q.a = h2c(h[2], nu.y);
+  q.b = h2c(h[3], nu.y);
+}
+
+__device__ __forceinline__ void store_pair2(__half2 *d, float *nrm, long long x, const Pair<float> &p,
+                                            const Pair<float> &q) {
+  const float np = fmaxf(fmaxf(fabsf(p.a.re), fabsf(p.a.im)), fmaxf(fabsf(p.b.re), fabsf(p.b.im)));
+  const float nq = fmaxf(fmaxf(fabsf(q.a.re), fabsf(q.a.im)), fmaxf(fabsf(q.b.re), fabsf(q.b.im)));
+  const float ip = np > 1e-30f ? __frcp_rn(np) : 0.f, iq = nq > 1e-30f ? __frcp_rn(nq) : 0.f;
+  const __half2 h0 = __floats2half2_rn(p.a.re * ip, p.a.im * ip), h1 = __floats2half2_rn(p.b.re * ip, p.b.im * ip);
+  const __half2 h2 = __floats2half2_rn(q.a.re * iq, q.a.im * iq), h3 = __floats2half2_rn(q.b.re * iq, q.b.im * iq);
+  uint4 raw;
+  memcpy(&raw.x, &h0, 4);
+  memcpy(&raw.y, &h1, 4);
+  memcpy(&raw.z, &h2, 4);
+  memcpy(&raw.w, &h3, 4);
+  reinterpret_cast<uint4 *>(d)[x >> 1] = raw;
+  reinterpret_cast<float2 *>(nrm)[x >> 1] = make_float2(ip > 0.f ? np : 0.f, iq > 0.f ? nq : 0.f);
+}
+
+__global__ void __launch_bounds__(256, 6) dslash_half2_kernel(const __half2 *__restrict__ U,
+                                                              const __half2 *__restrict__ in,
+                                                              const float *__restrict__ in_nrm,
+                                                              __half2 *__restrict__ out, float *__restrict__ out_nrm,
+                                                              int L0, int L1, float diag) {
+  const unsigned int pr = blockIdx.x * blockDim.x + threadIdx.x;  // pair index
+  const unsigned int h0 = (unsigned int)L0 >> 1;
+  if (pr >= h0 * (unsigned int)L1) return;
+  const unsigned int x1 = pr / h0, x0 = 2 * (pr - x1 * h0);
+  const unsigned int row = x1 * (unsigned int)L0;
+  const long long xa = row + x0;  // even: sites xa (a) and xa + 1 (b)
+  const long long up = (x1 + 1 == (unsigned int)L1 ? 0u : row + L0) + x0;
+  const long long dn = (x1 == 0 ? ((unsigned int)L1 - 1) * L0 : row - L0) + x0;
+  const long long am = row + (x0 == 0 ? L0 - 1 : x0 - 1);                 // a - 0
+  const long long bp = row + (x0 + 2 == (unsigned int)L0 ? 0u : x0 + 2);  // b + 0
+  Pair<float> sa, sb, ua, ub, da, db;
+  load_pair2(in, in_nrm, xa, sa, sb);
+  load_pair2(in, in_nrm, up, ua, ub);
+  load_pair2(in, in_nrm, dn, da, db);
+  const Pair<float> am_v = load_site(in, in_nrm, am), bp_v = load_site(in, in_nrm, bp);
+  // links: forward of a and b (one 16-byte load), U^1 of dn and dn + 1 (one 16-byte load), U^0 of a - 0
+  const uint4 lf = reinterpret_cast<const uint4 *>(U)[xa >> 1];
+  const uint4 ld = reinterpret_cast<const uint4 *>(U)[dn >> 1];
+  __half2 f[4], g1, g3;
+  memcpy(&f[0], &lf.x, 4);
+  memcpy(&f[1], &lf.y, 4);
+  memcpy(&f[2], &lf.z, 4);
+  memcpy(&f[3], &lf.w, 4);
+  memcpy(&g1, &ld.y, 4);
+  memcpy(&g3, &ld.w, 4);
+  const Cx<float> ua0 = h2c(f[0], 1.f), ua1 = h2c(f[1], 1.f), ub0 = h2c(f[2], 1.f), ub1 = h2c(f[3], 1.f);
+  const Cx<float> dna1 = h2c(g1, 1.f), dnb1 = h2c(g3, 1.f);
+  const Cx<float> am0 = h2c(U[2 * am], 1.f);
+  // a: +0 = b, +1 = ua, -0 = am, -1 = da; backward links U_{a-0}^0 = am0, U_{a-1}^1 = dna1
+  const Pair<float> oa = wilson_at(sa, sb, ua, am_v, da, ua0, ua1, am0, dna1, diag);
+  // b: +0 = bp, +1 = ub, -0 = a, -1 = db; backward links U_{b-0}^0 = U_a^0, U_{b-1}^1 = dnb1
+  const Pair<float> ob = wilson_at(sb, bp_v, ub, sa, db, ub0, ub1, ua0, dnb1, diag);
+  store_pair2(out, out_nrm, xa, oa, ob);
+}
+
 // complex (FP64 / FP32) spinor field -> half storage with per-site norms, and back
 template <typename R>
 __global__ void spinor_to_half_kernel(const Cx<R> *__restrict__ in, __half2 *__restrict__ out,
@@ -289,6 +364,14 @@ void launch_dslash_half(const void *U, const void *in, void *out, Geo2 g, double
   const long long V = g.nsites;
   const __half2 *ih = static_cast<const __half2 *>(in);
   __half2 *oh = static_cast<__half2 *>(out);
+  if ((g.L0 & 1) == 0) {
+    dslash_half2_kernel<<<grid_for(V / 2, 256), 256, 0, s>>>(static_cast<const __half2 *>(U), ih,
+                                                             reinterpret_cast<const float *>(ih + 2 * V), oh,
+                                                             reinterpret_cast<float *>(oh + 2 * V), g.L0, g.L1,
+                                                             (float)diag);
+    MG_LAUNCHED();
+    return;
+  }
   dslash_half_kernel<<<grid_for(V, 256), 256, 0, s>>>(static_cast<const __half2 *>(U), ih,
                                                       reinterpret_cast<const float *>(ih + 2 * V), oh,
                                                       reinterpret_cast<float *>(oh + 2 * V), g.L0, g.L1, (float)diag);

@@ -59,7 +59,9 @@ def test_dslash4d_free_plane_wave_closed_form():
     np.testing.assert_allclose(got, ph[:, None, None] * (Dp @ u)[None], atol=1e-13)
 
 
-@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (16, 16, 16, 32), (6, 10, 4, 2), (8, 4, 4, 2)])
+# (8, 4, 4, 2): one tile of the tiled FP32 kernel (every face wraps onto the tile itself);
+# (16, 8, 4, 8), (16, 16, 16, 32): several tiles; (4, 4, 4, 4), (6, 10, 4, 2): the warp-gather kernel
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (16, 16, 16, 32), (6, 10, 4, 2), (8, 4, 4, 2), (16, 8, 4, 8)])
 def test_dslash4d_fp32_per_site_error_below_1e6(dims):
     # reference: FP64 D on the same FP32-rounded inputs; per-site error relative to
     # |diag psi_x| + 1/2 sum |hop terms_x| (bounds the cancellation at that site)
@@ -107,3 +109,19 @@ def test_dslash4d_large_sampled_fp32():
     want = wilson.apply_D_at(U32.astype(np.complex128), p32.astype(np.complex128).reshape(lat.volume, 4, 3), 0.01,
                              lat, sites).reshape(len(sites), 12)
     assert np.abs(got[sites] - want).max() / np.abs(want).max() < 1e-6
+
+
+@pytest.mark.parametrize("variant", ["0", "1", "2", "3", "4", "5"])
+def test_dslash4d_fp32_tiled_and_gather_kernels_agree(variant, monkeypatch):
+    # the FP32 kernels (every tile shape, and the warp-gather kernel) form the same hop sums in the
+    # same order: they agree to rounding
+    dims = (16, 8, 8, 8)
+    lat = Lattice(dims)
+    U = _field(dims, 17)
+    psi = inputs.gaussian_spinor(lat.volume, 12, 19, 0)
+    U32, p32 = U.astype(np.complex64), psi.astype(np.complex64)
+    monkeypatch.setenv("MG_DSLASH4_TILE", variant)
+    tiled = _gpu_D(U32, p32, 0.05, dims, precision=1)
+    monkeypatch.setenv("MG_DSLASH4_GATHER", "1")
+    gather = _gpu_D(U32, p32, 0.05, dims, precision=1)
+    assert np.abs(tiled - gather).max() <= 1e-6 * np.abs(gather).max()

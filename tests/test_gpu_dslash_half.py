@@ -37,7 +37,8 @@ def encode_links(U):
     return h.view(np.uint8).reshape(-1), (h[:, 0].astype(np.float64) + 1j * h[:, 1].astype(np.float64)).reshape(U.shape)
 
 
-@pytest.mark.parametrize("dims", [(2, 2), (16, 12), (130, 66), (256, 256)])
+# even L0: two sites per thread; odd L0 (15, 3): one site per thread
+@pytest.mark.parametrize("dims", [(2, 2), (16, 12), (130, 66), (256, 256), (15, 12), (3, 2)])
 def test_half_dslash_matches_oracle(dims):
     import torch
     import paper_0707_4018_gb300 as mg

@@ -154,8 +154,11 @@ def test_su3_workload_16x16x16x32_true_residual():
     row = mcrit_table().get("w3_su3_16x16x16x32")
     # m_c + 0.005 (lowest |eigenvalue| about 5e-3) from the oracle's table, else m = 0 (above m_c)
     m = row["m_crit"] + 0.005 if row and row["links_digest"] == inputs.field_digest(U) else 0.0
-    ctx = mg.Context.setup(to_dev(U), m, dims, _params((4, 4, 4, 4), 24, 1, n_pass=3, coarsest_tol=0.05,
-                                                       coarsest_restart=32))
+    # the bench's 4d parameters: one deep relaxation pass (the adaptive passes lower the quality of
+    # well-relaxed 4d vectors, in the oracle too), inexact coarse GCR(64) to 0.05
+    ctx = mg.Context.setup(to_dev(U), m, dims, _params((4, 4, 4, 4), 24, 1, n_pass=1, nu_setup=200,
+                                                       coarsest_tol=0.05, coarsest_restart=64,
+                                                       coarsest_max_iter=128, max_iter=300))
     chi = inputs.gaussian_spinor(lat.volume, 12, 15, 0)
     psi = torch.empty((lat.volume, 12), dtype=torch.complex128, device="cuda")
     st = ctx.solve(to_dev(chi), psi, 1e-10)
