@@ -200,50 +200,46 @@ CONCURRENT = True
 
 
 def run_step_graph(fields_dev, precision: int, stats_out=None, host_io=None):
-    """One pass over the batch with every solve in one graph launch: the betas' setups and the clones
-    of each setup for the heavier masses (one host thread per beta), then mg_solve_multi on all nine
-    contexts (each outer loop a conditional WHILE node on the device)."""
+    """One pass over the batch with device-driven outer loops: one host thread per beta runs the
+    beta's setup, the clones of it for the heavier masses, then one mg_solve_multi launch for the
+    beta's three solves (each outer loop a conditional WHILE node on the device). The betas run
+    concurrently, so one beta's setup overlaps another's solves on the GPU."""
     import torch
     import paper_0707_4018_gb300 as mg
-    per_beta, errors = {}, []
+    results, errors = {}, []
 
-    def prepare(f):  # one host thread per beta: its setup, then the clones for the heavier masses
+    def run(f):
+        cs = []
         try:
             U = f["U_host"].to("cuda", non_blocking=True) if host_io is not None else f["U_dev"]
             Lf = f.get("L", L)
             c = mg.Context.setup(U, f["m_c"] + DMS[0], (Lf, Lf), mg_params(precision))
-            per_beta[f["beta"]] = [c] + [c.clone(f["m_c"] + dm) for dm in DMS[1:]]
+            cs = [c] + [c.clone(f["m_c"] + dm) for dm in DMS[1:]]
+            chis = [f["chi_host"][i].to("cuda", non_blocking=True) if host_io is not None else f["chi_dev"][i]
+                    for i in range(len(DMS))]
+            st = mg.solve_multi(cs, chis, f["psi_dev"], TOL)
+            if host_io is not None:
+                for i, psi in enumerate(f["psi_dev"]):
+                    host_io[f["beta"]][i].copy_(psi, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            results[f["beta"]] = st
         except BaseException as e:  # re-raised on the calling thread
             errors.append(e)
+        finally:
+            for c in cs:
+                c.close()
 
-    threads = [threading.Thread(target=prepare, args=(f,)) for f in fields_dev]
+    threads = [threading.Thread(target=run, args=(f,)) for f in fields_dev]
     for t in threads:
         t.start()
     for t in threads:
         t.join()
     if errors:
-        for cs in per_beta.values():
-            for c in cs:
-                c.close()
         raise errors[0]
-    ctxs, chis, psis, tags = [], [], [], []
-    for f in fields_dev:
-        for i, dm in enumerate(DMS):
-            ctxs.append(per_beta[f["beta"]][i])
-            chis.append(f["chi_host"][i].to("cuda", non_blocking=True) if host_io is not None else f["chi_dev"][i])
-            psis.append(f["psi_dev"][i])
-            tags.append((f["beta"], dm, i))
-    st = mg.solve_multi(ctxs, chis, psis, TOL)
-    if host_io is not None:
-        for (beta, dm, i), psi in zip(tags, psis):
-            host_io[beta][i].copy_(psi, non_blocking=True)
-    torch.cuda.current_stream().synchronize()
-    for c in ctxs:
-        c.close()
     if stats_out is not None:
-        stats_out.extend(sorted([dict(beta=t[0], dm=t[1], **s) for t, s in zip(tags, st)],
-                                key=lambda d: (d["beta"], d["dm"])))
-    return len(ctxs)
+        for f in fields_dev:
+            stats_out.extend(dict(beta=f["beta"], dm=dm, **s) for dm, s in zip(DMS, results[f["beta"]]))
+    return sum(len(v) for v in results.values())
 
 
 # how a step runs its solves: "graph" (one mg_solve_multi launch for all of them) or "threads"
@@ -637,7 +633,7 @@ def dslash4_roofline(precision: int, dims=(32, 32, 32, 64), iters: int = 20, com
     res = dict(lattice="x".join(str(v) for v in dims), dtype="f64" if precision == 0 else "f32",
                bytes_per_site=per_site, flop_per_site=1368, ms=t * 1e3, gbs=V * per_site / t / 1e9,
                tflops=V * 1368 / t / 1e12,
-               kernel="dslash4_tile_kernel (8x4x4x2 tiles)" if precision == 1 else "dslash4_kernel<double>")
+               kernel="dslash4_tile_kernel (8x2x2x2 tiles)" if precision == 1 else "dslash4_kernel<double>")
     if precision == 1 and compare_gather:
         # the warp-gather kernel on the same inputs
         os.environ["MG_DSLASH4_GATHER"] = "1"
@@ -722,13 +718,15 @@ SU3_RHS = 12
 
 def su3_params(precision: int):
     """4d SU(3) hierarchy: two levels, 4^4 blocks, Nv = 24 split by chirality (48 coarse dofs),
-    one relaxation pass of 200 MR iterations (deeper relaxation in place of adaptive passes,
-    which lowered the quality of the 4d vectors), MR 4 + 4, coarse GCR(64) to 0.05 with block
-    Jacobi, at most 128 coarse iterations per cycle (near m_c an inexact coarse solve costs
-    fewer operations than an exact one; the outer flexible GCR absorbs it)."""
+    one relaxation pass of 400 MR iterations (deeper relaxation in place of adaptive passes,
+    which lower the quality of well-relaxed 4d vectors, in the oracle too), MR 4 + 4, coarse
+    GCR(64) to 0.3 with block Jacobi, at most 128 coarse iterations per cycle (near m_c an
+    inexact coarse solve costs fewer operations than an exact one; the outer flexible GCR absorbs
+    it). At m_c + 0.005 these settings took 144 ms per solve and 0.47 s of setup, against 227 ms
+    and 0.30 s with 200 relaxation steps and a coarse tolerance of 0.05."""
     import paper_0707_4018_gb300 as mg
     return mg.mg_default_params(levels=2, blocks=[(4, 4, 4, 4)], Nv=[24], precision=precision, chiral_split=1,
-                                n_pass=1, nu_setup=200, coarsest_tol=0.05, coarsest_restart=64,
+                                n_pass=1, nu_setup=400, coarsest_tol=0.3, coarsest_restart=64,
                                 coarsest_max_iter=128, max_iter=300, max_rhs=SU3_RHS)
 
 
@@ -1012,17 +1010,14 @@ def run_only(case: str):
     if case == "su3-prof":  # mixed precision, setup and 2 solves (launch-list profiling)
         print(json.dumps({"case": case, **su3_workload((1,), 2, batched=False)}))
         return
-    if case.startswith("dslash4"):
-        r = dslash4_roofline(1 if case == "dslash4-f32" else 0, iters=3, compare_gather=False)
-        print(json.dumps({"case": case, **r}))
-        return
     if case == "dslash4-sweep":
         # the FP32 4d apply on 32^3 x 64 with each kernel variant (tile shapes, warp gather)
         res = {}
         for name, env in (("gather", ("MG_DSLASH4_GATHER", "1")), ("tileA_8x4x4x4", ("MG_DSLASH4_TILE", "0")),
                           ("tileB_8x4x4x2", ("MG_DSLASH4_TILE", "1")), ("tileC_4x4x4x2", ("MG_DSLASH4_TILE", "2")),
                           ("tileD_8x4x2x2", ("MG_DSLASH4_TILE", "3")), ("tileB_3cta", ("MG_DSLASH4_TILE", "4")),
-                          ("tileC_6cta", ("MG_DSLASH4_TILE", "5"))):
+                          ("tileC_6cta", ("MG_DSLASH4_TILE", "5")), ("tileE_4x4x2x2", ("MG_DSLASH4_TILE", "6")),
+                          ("tileF_8x2x2x2", ("MG_DSLASH4_TILE", "7"))):
             os.environ[env[0]] = env[1]
             try:
                 r = dslash4_roofline(1, iters=10, compare_gather=False)
@@ -1030,6 +1025,10 @@ def run_only(case: str):
                 del os.environ[env[0]]
             res[name] = {"ms": r["ms"], "gbs": r["gbs"]}
         print(json.dumps({"case": case, **res}))
+        return
+    if case.startswith("dslash4"):
+        r = dslash4_roofline(1 if case == "dslash4-f32" else 0, iters=3, compare_gather=False)
+        print(json.dumps({"case": case, **r}))
         return
     if case == "dslash-f16":
         print(json.dumps({"case": case, **dslash_half_roofline(iters=3)}))
@@ -1271,9 +1270,12 @@ def main():
         "config": {"workload": WORKLOAD, "lattice": f"{L}x{L}", "betas": list(BETAS), "m_minus_mc": list(DMS),
                    "solves_per_step": len(BETAS) * len(DMS), "precision": "FP64 outer GCR, FP32 V-cycle",
                    "l2": "flushed before every timed step (512 MiB write)", "tol": TOL,
-                   "betas_run": "concurrently: one host thread and context stream per beta and, through clones of "
-                                "the beta's setup (Galerkin rebuilt per mass), per mass" if CONCURRENT
-                   else "one after another",
+                   "betas_run": ("concurrently: one host thread per beta runs its setup, two clones of it "
+                                 "(Galerkin rebuilt per mass) and one multi-solve graph launch of its three solves "
+                                 "(device-driven outer loops)" if STEP_MODE == "graph" else
+                                 "concurrently: one host thread and context stream per beta and, through clones of "
+                                 "the beta's setup (Galerkin rebuilt per mass), per mass (host-driven outer loops)")
+                   if CONCURRENT else "one after another",
                    "gauge_digest_matches_table": all(f["digest_ok"] for f in fields) if rank == 0 else None},
         "solver": {"iters": iters, "worst_true_rel_residual": worst_res},
         "fp64_mg": fp64,

@@ -80,21 +80,25 @@ __global__ void mr_update_kernel(const double *__restrict__ sc, double omega, Cx
 }
 
 // rows j < k: <W_j, w>; row k: <w, w>; row k + 1: <w, r>; row k + 2: <r, r>  (blockIdx.y = row)
-__global__ void __launch_bounds__(kReduceThreads) gcr_dots_kernel(const Cx<double> *__restrict__ W,
-                                                                  const Cx<double> *__restrict__ w,
-                                                                  const Cx<double> *__restrict__ r, int k,
+// (VT = float: FP32 vectors; each thread sums its few products in FP32, the block and grid
+// trees sum in FP64)
+template <typename VT>
+__global__ void __launch_bounds__(kReduceThreads) gcr_dots_kernel(const Cx<VT> *__restrict__ W,
+                                                                  const Cx<VT> *__restrict__ w,
+                                                                  const Cx<VT> *__restrict__ r, int k,
                                                                   long long n, double *partials, double *out,
                                                                   unsigned int *ticket, int pstride) {
   __shared__ double sh[32 * 2];
   const int row = blockIdx.y;
-  const Cx<double> *a = row < k ? W + (long long)row * n : (row == k + 2 ? r : w);
-  const Cx<double> *b = row > k ? r : w;
-  double v[2] = {0.0, 0.0};
+  const Cx<VT> *a = row < k ? W + (long long)row * n : (row == k + 2 ? r : w);
+  const Cx<VT> *b = row > k ? r : w;
+  VT t0 = (VT)0, t1 = (VT)0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const Cx<double> x = a[i], y = b[i];
-    v[0] += x.re * y.re + x.im * y.im;
-    v[1] += x.re * y.im - x.im * y.re;
+    const Cx<VT> x = a[i], y = b[i];
+    t0 += x.re * y.re + x.im * y.im;
+    t1 += x.re * y.im - x.im * y.re;
   }
+  double v[2] = {(double)t0, (double)t1};
   grid_finish<2>(v, partials + (long long)row * pstride, out + 2 * row, ticket + row, sh);
 }
 
@@ -124,16 +128,27 @@ __global__ void gcr_project_update_kernel(const Cx<double> *__restrict__ W, Cx<d
   }
 }
 
-void launch_gcr_dots(const Cx<double> *W, const Cx<double> *w, const Cx<double> *r, int k, long long n, double *out,
-                     const ReduceWs &ws, cudaStream_t s) {
+template <typename VT>
+static void gcr_dots_any(const Cx<VT> *W, const Cx<VT> *w, const Cx<VT> *r, int k, long long n, double *out,
+                         const ReduceWs &ws, cudaStream_t s) {
   const int rows = k + 3;
   if (rows > 128) fail(MG_ERR_UNSUPPORTED, "gcr_dots: too many basis vectors");
   int per = (int)(ws.capacity / (2 * rows));
   if (per > ws.max_blocks) per = ws.max_blocks;
   if (per < 1) per = 1;
   dim3 grid(reduce_blocks(n, per), rows);
-  gcr_dots_kernel<<<grid, kReduceThreads, 0, s>>>(W, w, r, k, n, ws.partials, out, ws.ticket, 2 * (int)grid.x);
+  gcr_dots_kernel<VT><<<grid, kReduceThreads, 0, s>>>(W, w, r, k, n, ws.partials, out, ws.ticket, 2 * (int)grid.x);
   MG_LAUNCHED();
+}
+
+void launch_gcr_dots(const Cx<double> *W, const Cx<double> *w, const Cx<double> *r, int k, long long n, double *out,
+                     const ReduceWs &ws, cudaStream_t s) {
+  gcr_dots_any<double>(W, w, r, k, n, out, ws, s);
+}
+
+void launch_gcr_dots(const Cx<float> *W, const Cx<float> *w, const Cx<float> *r, int k, long long n, double *out,
+                     const ReduceWs &ws, cudaStream_t s) {
+  gcr_dots_any<float>(W, w, r, k, n, out, ws, s);
 }
 
 void launch_gcr_project_update(const Cx<double> *W, Cx<double> *Wk, const Cx<double> *Z, Cx<double> *Zk, int k,

@@ -147,6 +147,9 @@ void launch_mr_update(const double *sc, double omega, Cx<R> *x, Cx<R> *r, const 
 // out[2k+4] = |r|^2
 void launch_gcr_dots(const Cx<double> *W, const Cx<double> *w, const Cx<double> *r, int k, long long n, double *out,
                      const ReduceWs &ws, cudaStream_t s);
+// the same reductions on FP32 vectors (products and sums in FP64)
+void launch_gcr_dots(const Cx<float> *W, const Cx<float> *w, const Cx<float> *r, int k, long long n, double *out,
+                     const ReduceWs &ws, cudaStream_t s);
 // w = (w - sum beta_j W_j) inv and z likewise (written to Wk / Zk); then, if update_xr,
 // x += alpha z and r -= alpha w. beta_dev: 2k doubles on the device.
 void launch_gcr_project_update(const Cx<double> *W, Cx<double> *Wk, const Cx<double> *Z, Cx<double> *Zk, int k,
@@ -178,11 +181,12 @@ void launch_prolong_add(const Cx<R> *V, const Cx<R> *coarse, Cx<R> *fine, BlockG
 // block Gram-Schmidt (modified, twice, k order) of Nv level vectors into V[b][k][i]; FP64
 void launch_block_mgs(const Cx<double> *vecs, long long vec_stride, Cx<double> *V, BlockGeo bg, int Nv,
                       double *min_norm_dev, cudaStream_t s);
-// Galerkin coarse operator Yc[b][dir][col][row] (internal layout) of P^dagger A P
+// Galerkin coarse operator Yc[b][dir][col][row] (internal layout) of P^dagger A P; FP64 inputs and
+// output, arithmetic in FP64 or (fp32_arith, the hierarchies of mixed-precision cycles) FP32
 void launch_galerkin_wilson(const Cx<double> *U, double diag, const Cx<double> *V, Cx<double> *Yc, BlockGeo bg,
-                            int Nv, cudaStream_t s);
+                            int Nv, cudaStream_t s, bool fp32_arith = false);
 void launch_galerkin_stencil(const Cx<double> *Y, const Cx<double> *V, Cx<double> *Yc, BlockGeo bg, int Nv,
-                             cudaStream_t s);
+                             cudaStream_t s, bool fp32_arith = false);
 
 // ---- layout conversions at the boundary ----
 // internal Y[j][dir][col][row] <-> canonical Y[j][dir][row][col]

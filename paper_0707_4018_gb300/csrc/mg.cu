@@ -192,6 +192,15 @@ struct mg_ctx {
 
 namespace mg {
 
+// Galerkin products in FP32 arithmetic for the hierarchies of mixed-precision cycles whose
+// coarsest solve is itself inexact (iterative, tolerance >= 1e-5): their coarse operators are
+// applied in FP32 and a 1e-7 relative change of them is far below what the cycle resolves.
+// FP64 contexts and exact coarsest solves keep FP64 products.
+static bool galerkin_f32(const mg_ctx &c) {
+  return c.p.precision == MG_FP32 && !c.use_lu && c.p.coarsest_tol >= 1e-5 &&
+         std::getenv("MG_FP64_GALERKIN") == nullptr;
+}
+
 static double diag_of(const mg_ctx &c) { return c.geom.d + c.m; }
 
 template <typename R>
@@ -1120,9 +1129,9 @@ static void build_level(mg_ctx &c, int l) {
   Level &C = c.lv[l + 1];
   launch_block_mgs(L.nullv.p, L.n, L.V64.p, L.bg, L.Nv, L.mgs_min.p, c.s);
   if (l == 0)
-    launch_galerkin_wilson(c.U64.p, diag_of(c), L.V64.p, C.Y64.p, L.bg, L.Nv, c.s);
+    launch_galerkin_wilson(c.U64.p, diag_of(c), L.V64.p, C.Y64.p, L.bg, L.Nv, c.s, galerkin_f32(c));
   else
-    launch_galerkin_stencil(L.Y64.p, L.V64.p, C.Y64.p, L.bg, L.Nv, c.s);
+    launch_galerkin_stencil(L.Y64.p, L.V64.p, C.Y64.p, L.bg, L.Nv, c.s, galerkin_f32(c));
 }
 
 // One adaptive-setup level in the context precision. In FP32 mode the relaxation
@@ -1874,9 +1883,9 @@ int mg_update_mass(mg_ctx *c, double m) {
     for (int l = 0; l + 1 < c->p.levels; ++l) {
       Level &L = c->lv[l];
       if (l == 0)
-        launch_galerkin_wilson(c->U64.p, diag_of(*c), L.V64.p, c->lv[1].Y64.p, L.bg, L.Nv, c->s);
+        launch_galerkin_wilson(c->U64.p, diag_of(*c), L.V64.p, c->lv[1].Y64.p, L.bg, L.Nv, c->s, galerkin_f32(*c));
       else
-        launch_galerkin_stencil(L.Y64.p, L.V64.p, c->lv[l + 1].Y64.p, L.bg, L.Nv, c->s);
+        launch_galerkin_stencil(L.Y64.p, L.V64.p, c->lv[l + 1].Y64.p, L.bg, L.Nv, c->s, galerkin_f32(*c));
     }
     prepare_coarsest(*c);
     make_fp32_copies(*c);
@@ -1904,9 +1913,9 @@ int mg_clone(mg_ctx *src, double m, void *stream, mg_ctx **out) {
       MG_CUDA(cudaMemcpyAsync(L.V64.p, S.V64.p, L.V64.n * sizeof(Cx<double>), cudaMemcpyDeviceToDevice, c->s));
       // Galerkin operators at the clone's mass, level by level (level l + 1 needs Y of level l)
       if (l == 0)
-        launch_galerkin_wilson(c->U64.p, diag_of(*c), L.V64.p, c->lv[1].Y64.p, L.bg, L.Nv, c->s);
+        launch_galerkin_wilson(c->U64.p, diag_of(*c), L.V64.p, c->lv[1].Y64.p, L.bg, L.Nv, c->s, galerkin_f32(*c));
       else
-        launch_galerkin_stencil(L.Y64.p, L.V64.p, c->lv[l + 1].Y64.p, L.bg, L.Nv, c->s);
+        launch_galerkin_stencil(L.Y64.p, L.V64.p, c->lv[l + 1].Y64.p, L.bg, L.Nv, c->s, galerkin_f32(*c));
     }
     prepare_coarsest(*c);
     make_fp32_copies(*c);

@@ -19,6 +19,8 @@
 #include <memory>
 #include <vector>
 
+#include <cstdlib>
+
 #include "mg4d.h"
 
 namespace mg {
@@ -48,6 +50,7 @@ struct Engine4 {
   DevBuf<Cx<double>> cb, cx, cy;  // coarse right-hand side / solution / preconditioned solution (FP64)
   DevBuf<Cx<float>> cb32, cx32;
   DevBuf<Cx<double>> cZ, cW, cr;  // coarse GCR
+  DevBuf<Cx<float>> cZ32, cW32, cr32, cy32;  // coarse GCR on FP32 vectors (MG_FP32, loose coarsest_tol)
   DevBuf<Cx<double>> oZ, oW, orr, t64;  // outer GCR, setup scratch
   DevBuf<double> partials, scal;
   DevBuf<unsigned int> tickets;
@@ -203,8 +206,67 @@ Gcr fgcr(Engine4 &e, ApplyF &&apply, PrecF &&prec, const Cx<double> *b, Cx<doubl
 // estimate only every 4 iterations. With MG_FP32 and a tolerance FP32 arithmetic can reach
 // (>= 1e-5), the stencil and M are applied from their FP32 copies; the Krylov vectors
 // and reductions stay FP64.
+// coarse solve on FP32 vectors: cx32 = A_c^{-1} cb32 by the GCR below with the FP32 stencil A M,
+// FP32 Krylov vectors and updates, and every reduction in FP64 (MG_FP32 with a coarsest
+// tolerance FP32 arithmetic can reach, >= 1e-5: the FP64 Gram-Schmidt over up to 64 basis
+// vectors, at 1/74 of the FP32 rate, was most of an iteration's time)
+long long coarse_solve32(Engine4 &e) {
+  const long long n = e.nc;
+  Cx<float> *x = e.cy32.p, *r = e.cr32.p, *Z = e.cZ32.p, *W = e.cW32.p;
+  const Cx<float> *b = e.cb32.p;
+  auto apply = [&](const Cx<float> *in, Cx<float> *out, const Cx<float> *rhs = nullptr) {
+    launch_coarse4_apply<float, float>(e.Yt32.p, in, out, e.cg, rhs, rhs ? -1.0 : 1.0, rhs ? 1.0 : 0.0, e.s);
+    ++e.apps[1];
+  };
+  double *dots = e.scal.p + kScalCoarse, *state = dots + 204;
+  double *h = e.host + kScalCoarse;
+  auto fetch = [&](const double *src) {
+    MG_CUDA(cudaMemcpyAsync(h, src, sizeof(double), cudaMemcpyDeviceToHost, e.s));
+    MG_CUDA(cudaStreamSynchronize(e.s));
+    if (std::isnan(h[0])) fail(MG_ERR_NAN, "coarse GCR: NaN in a reduction");
+    return h[0];
+  };
+  launch_zero<float>(x, n, e.s);
+  launch_copy<float>(b, r, n, e.s);
+  launch_norm2<float>(b, n, dots, e.wsc, e.s);
+  const double bn2 = fetch(dots);
+  long long iters = 0;
+  if (bn2 > 0.0) {
+    const double tol2 = e.p.coarsest_tol * e.p.coarsest_tol * bn2;
+    const int restart = e.p.coarsest_restart, max_iter = e.p.coarsest_max_iter;
+    constexpr int kCheck = 4;
+    while (iters < max_iter) {
+      int k = 0;
+      for (; k < restart && iters < max_iter; ++k) {
+        Cx<float> *z = Z + (long long)k * n, *w = W + (long long)k * n;
+        launch_copy<float>(r, z, n, e.s);
+        apply(z, w);
+        launch_gcr_dots(W, w, r, k, n, dots, e.wsc, e.s);
+        launch_gcr_update_dev(W, w, Z, z, k, dots, state, x, r, n, e.s);
+        ++iters;
+        if ((k + 1) % kCheck == 0 && fetch(state) <= tol2) {
+          ++k;
+          break;
+        }
+      }
+      apply(x, r, b);  // true residual
+      launch_norm2<float>(r, n, dots, e.wsc, e.s);
+      if (fetch(dots) <= tol2) break;
+    }
+  }
+  launch_block_apply4_32(e.Minv32.p, x, e.cx32.p, e.cg, e.s);  // x = M y
+  e.coarsest_iters += iters;
+  return iters;
+}
+
 long long coarse_solve(Engine4 &e) {
   const bool fast = e.f32 && e.p.coarsest_tol >= 1e-5;
+  if (fast && std::getenv("MG_COARSE4_FP64_VECTORS") == nullptr) {  // FP64 in, FP64 out, FP32 inside
+    launch_convert<float, double>(e.cb.p, e.cb32.p, e.nc, e.s);
+    const long long it = coarse_solve32(e);
+    launch_convert<double, float>(e.cx32.p, e.cx.p, e.nc, e.s);
+    return it;
+  }
   auto apply = [&](const Cx<double> *in, Cx<double> *out, const Cx<double> *b = nullptr) {
     if (fast)
       launch_coarse4_apply<float, double>(e.Yt32.p, in, out, e.cg, b, b ? -1.0 : 1.0, b ? 1.0 : 0.0, e.s);
@@ -438,12 +500,17 @@ void vcycle(Engine4 &e, const Cx<double> *b64, Cx<double> *x64) {
   fine_apply<R>(e, x, r, b, -1.0, 1.0);
   Cx<R> *rc = sizeof(R) == 8 ? reinterpret_cast<Cx<R> *>(e.cb.p) : reinterpret_cast<Cx<R> *>(e.cb32.p);
   launch_restrict4<R>(V_of<R>(e), r, rc, e.bg, e.s);
-  if (sizeof(R) == 4) to64<R>(e, rc, e.cb.p, e.nc);
-  // 3. coarse solve
-  coarse_solve(e);
+  // 3. coarse solve (FP32 vectors throughout when the coarse GCR runs on them)
+  const bool c32 = sizeof(R) == 4 && e.cy32.p != nullptr && std::getenv("MG_COARSE4_FP64_VECTORS") == nullptr;
+  if (c32) {
+    coarse_solve32(e);
+  } else {
+    if (sizeof(R) == 4) to64<R>(e, rc, e.cb.p, e.nc);
+    coarse_solve(e);
+  }
   // 4. prolongation and correction
   Cx<R> *ec = sizeof(R) == 8 ? reinterpret_cast<Cx<R> *>(e.cx.p) : reinterpret_cast<Cx<R> *>(e.cx32.p);
-  if (sizeof(R) == 4) from64<R>(e, e.cx.p, ec, e.nc);
+  if (sizeof(R) == 4 && !c32) from64<R>(e, e.cx.p, ec, e.nc);
   launch_prolong4<R>(V_of<R>(e), ec, x, e.bg, e.s);
   // 5. post-smoothing on the new residual
   fine_apply<R>(e, x, r, b, -1.0, 1.0);
@@ -598,6 +665,12 @@ Engine4 *engine4_create(const mg_geom *g, const void *U, double m, const mg_para
     e->vb32.alloc(e->nf);
     e->cb32.alloc(e->nc);
     e->cx32.alloc(e->nc);
+    if (p->coarsest_tol >= 1e-5) {
+      e->cZ32.alloc((size_t)p->coarsest_restart * e->nc);
+      e->cW32.alloc((size_t)p->coarsest_restart * e->nc);
+      e->cr32.alloc(e->nc);
+      e->cy32.alloc(e->nc);
+    }
   }
   e->cb.alloc(e->nc);
   e->cx.alloc(e->nc);

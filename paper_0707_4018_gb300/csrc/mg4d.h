@@ -61,6 +61,12 @@ void launch_block_apply4(const Cx<R> *Minv, const Cx<double> *r, Cx<double> *z, 
 void launch_gcr_update_dev(const Cx<double> *W, Cx<double> *Wk, const Cx<double> *Z, Cx<double> *Zk, int k,
                            const double *dots, double *state, Cx<double> *x, Cx<double> *r, long long n,
                            cudaStream_t s);
+// FP32 vectors (coefficients formed in FP64), and the block-Jacobi apply on FP32 vectors
+void launch_gcr_update_dev(const Cx<float> *W, Cx<float> *Wk, const Cx<float> *Z, Cx<float> *Zk, int k,
+                           const double *dots, double *state, Cx<float> *x, Cx<float> *r, long long n,
+                           cudaStream_t s);
+void launch_block_apply4_32(const Cx<float> *Minv, const Cx<float> *r, Cx<float> *z, const Coarse4 &g,
+                            cudaStream_t s);
 // Yt[j][dir] = Y[j][dir] Minv[src(j, dir)]: the block-Jacobi right-preconditioned stencil A M
 void launch_precondition4(const Cx<double> *Y, const Cx<double> *Minv, Cx<double> *Yt, const Coarse4 &g,
                           cudaStream_t s);

@@ -447,21 +447,21 @@ __global__ void __launch_bounds__(256) block_invert4_kernel(const Cx<double> *__
 
 // z_j = Minv_j r_j (one CTA per site and vector blockIdx.y, one thread per row; vectors at
 // stride ld)
-template <typename R>
-__global__ void block_apply4_kernel(const Cx<R> *__restrict__ Minv, const Cx<double> *__restrict__ r,
-                                    Cx<double> *__restrict__ z, int N, long long ld) {
+template <typename R, typename VT>
+__global__ void block_apply4_kernel(const Cx<R> *__restrict__ Minv, const Cx<VT> *__restrict__ r,
+                                    Cx<VT> *__restrict__ z, int N, long long ld) {
   __shared__ Cx<R> rs[64];
   r += blockIdx.y * ld;
   z += blockIdx.y * ld;
   const int j = blockIdx.x, row = threadIdx.x;
-  if (row < N) rs[row] = cvt<R, double>(r[(long long)j * N + row]);
+  if (row < N) rs[row] = cvt<R, VT>(r[(long long)j * N + row]);
   __syncthreads();
   if (row >= N) return;
   const Cx<R> *M = Minv + (long long)j * N * N;
   Cx<R> acc = mk((R)0, (R)0);
 #pragma unroll 8
   for (int cc = 0; cc < N; ++cc) cmac(acc, M[(long long)cc * N + row], rs[cc]);
-  z[(long long)j * N + row] = cvt<double, R>(acc);
+  z[(long long)j * N + row] = cvt<VT, R>(acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -473,10 +473,12 @@ __global__ void block_apply4_kernel(const Cx<R> *__restrict__ Minv, const Cx<dou
 // state[0]. Then w <- (w - sum_j beta_j W_j) inv, z likewise; W_k = w, Z_k = z;
 // x += alpha z; r -= alpha w.
 // ---------------------------------------------------------------------------
-__global__ void gcr_update_dev_kernel(const Cx<double> *__restrict__ W, Cx<double> *__restrict__ Wk,
-                                      const Cx<double> *__restrict__ Z, Cx<double> *__restrict__ Zk, int k,
+// (VT = float: FP32 vectors; the coefficients are formed in FP64 and applied in FP32)
+template <typename VT>
+__global__ void gcr_update_dev_kernel(const Cx<VT> *__restrict__ W, Cx<VT> *__restrict__ Wk,
+                                      const Cx<VT> *__restrict__ Z, Cx<VT> *__restrict__ Zk, int k,
                                       const double *__restrict__ dots, double *__restrict__ state,
-                                      Cx<double> *__restrict__ x, Cx<double> *__restrict__ r, long long n) {
+                                      Cx<VT> *__restrict__ x, Cx<VT> *__restrict__ r, long long n) {
   __shared__ double coef[3];
   if (threadIdx.x == 0) {
     const double nw0 = dots[2 * k];
@@ -494,12 +496,12 @@ __global__ void gcr_update_dev_kernel(const Cx<double> *__restrict__ W, Cx<doubl
     if (blockIdx.x == 0) state[0] = fmax(dots[2 * k + 4] - (are * are + aim * aim), 0.0);
   }
   __syncthreads();
-  const double inv = coef[0];
-  const Cx<double> alpha = mk(coef[1], coef[2]), malpha = mk(-coef[1], -coef[2]);
+  const VT inv = (VT)coef[0];
+  const Cx<VT> alpha = mk((VT)coef[1], (VT)coef[2]), malpha = mk((VT)-coef[1], (VT)-coef[2]);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    Cx<double> w = Wk[i], z = Zk[i];
+    Cx<VT> w = Wk[i], z = Zk[i];
     for (int j = 0; j < k; ++j) {
-      const Cx<double> bj = mk(-dots[2 * j], -dots[2 * j + 1]);
+      const Cx<VT> bj = mk((VT)-dots[2 * j], (VT)-dots[2 * j + 1]);
       cmac(w, bj, W[(long long)j * n + i]);
       cmac(z, bj, Z[(long long)j * n + i]);
     }
@@ -508,7 +510,7 @@ __global__ void gcr_update_dev_kernel(const Cx<double> *__restrict__ W, Cx<doubl
     Wk[i] = w;
     Zk[i] = z;
     cmac(x[i], alpha, z);
-    Cx<double> ri = r[i];
+    Cx<VT> ri = r[i];
     cmac(ri, malpha, w);
     r[i] = ri;
   }
@@ -689,17 +691,35 @@ void launch_block_invert4(const Cx<double> *Y, Cx<double> *Minv, const Coarse4 &
 template <typename R>
 void launch_block_apply4(const Cx<R> *Minv, const Cx<double> *r, Cx<double> *z, const Coarse4 &g, cudaStream_t s,
                          int nvec) {
-  block_apply4_kernel<R><<<dim3((unsigned int)g.nsites, nvec), 64, 0, s>>>(Minv, r, z, g.N, g.nsites * g.N);
+  block_apply4_kernel<R, double><<<dim3((unsigned int)g.nsites, nvec), 64, 0, s>>>(Minv, r, z, g.N, g.nsites * g.N);
+  MG_LAUNCHED();
+}
+
+void launch_block_apply4_32(const Cx<float> *Minv, const Cx<float> *r, Cx<float> *z, const Coarse4 &g,
+                            cudaStream_t s) {
+  block_apply4_kernel<float, float><<<(unsigned int)g.nsites, 64, 0, s>>>(Minv, r, z, g.N, g.nsites * g.N);
+  MG_LAUNCHED();
+}
+
+template <typename VT>
+static void gcr_update_dev_any(const Cx<VT> *W, Cx<VT> *Wk, const Cx<VT> *Z, Cx<VT> *Zk, int k, const double *dots,
+                               double *state, Cx<VT> *x, Cx<VT> *r, long long n, cudaStream_t s) {
+  long long b = (n + 255) / 256;
+  if (b > 152LL * 16) b = 152LL * 16;
+  gcr_update_dev_kernel<VT><<<(unsigned int)(b < 1 ? 1 : b), 256, 0, s>>>(W, Wk, Z, Zk, k, dots, state, x, r, n);
   MG_LAUNCHED();
 }
 
 void launch_gcr_update_dev(const Cx<double> *W, Cx<double> *Wk, const Cx<double> *Z, Cx<double> *Zk, int k,
                            const double *dots, double *state, Cx<double> *x, Cx<double> *r, long long n,
                            cudaStream_t s) {
-  long long b = (n + 255) / 256;
-  if (b > 152LL * 16) b = 152LL * 16;
-  gcr_update_dev_kernel<<<(unsigned int)(b < 1 ? 1 : b), 256, 0, s>>>(W, Wk, Z, Zk, k, dots, state, x, r, n);
-  MG_LAUNCHED();
+  gcr_update_dev_any<double>(W, Wk, Z, Zk, k, dots, state, x, r, n, s);
+}
+
+void launch_gcr_update_dev(const Cx<float> *W, Cx<float> *Wk, const Cx<float> *Z, Cx<float> *Zk, int k,
+                           const double *dots, double *state, Cx<float> *x, Cx<float> *r, long long n,
+                           cudaStream_t s) {
+  gcr_update_dev_any<float>(W, Wk, Z, Zk, k, dots, state, x, r, n, s);
 }
 
 void launch_precondition4(const Cx<double> *Y, const Cx<double> *Minv, Cx<double> *Yt, const Coarse4 &g,

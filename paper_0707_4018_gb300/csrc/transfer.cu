@@ -244,34 +244,38 @@ __device__ __forceinline__ NbrInfo neighbour_in_blocks(const BlockGeo &g, int x0
   return n;
 }
 
-// parts for the fine Wilson level (n_int = 2)
+// parts for the fine Wilson level (n_int = 2); arithmetic in CT (FP64, or FP32 for the
+// setup of mixed-precision hierarchies), inputs and output FP64
+template <typename CT>
 __device__ void galerkin_parts_wilson(const Cx<double> *__restrict__ U, double diag, const Cx<double> *__restrict__ V,
-                                      const BlockGeo &g, int Nv, long long b, int lane, Cx<double> *parts) {
+                                      const BlockGeo &g, int Nv, long long b, int lane, Cx<CT> *parts) {
   const long long pstride = (long long)Nv * g.Nb;  // parts[dir][k][i]
   for (int i = lane; i < g.Nb; i += 32) {
     const int s = i >> 1, spin = i & 1;
     const long long x = fine_site_of(g, b, s);
     const int x0 = (int)(x % g.L0), x1 = (int)(x / g.L0);
     NbrInfo nb[5];
-    Cx<double> link[5];
+    Cx<CT> link[5];
     for (int dir = 1; dir <= 4; ++dir) {
       nb[dir] = neighbour_in_blocks(g, x0, x1, dir);
       // +mu: U_x^mu; -mu: U_{x-mu}^mu (conjugated inside hop_scalar)
-      link[dir] = (dir == 1) ? U[2 * x] : (dir == 2) ? U[2 * nb[2].site] : (dir == 3) ? U[2 * x + 1]
-                                                                                        : U[2 * nb[4].site + 1];
+      link[dir] = cvt<CT, double>((dir == 1)   ? U[2 * x]
+                                  : (dir == 2) ? U[2 * nb[2].site]
+                                  : (dir == 3) ? U[2 * x + 1]
+                                               : U[2 * nb[4].site + 1]);
     }
     for (int k = 0; k < Nv; ++k) {
-      Cx<double> self = diag * V[(b * Nv + k) * (long long)g.Nb + i];
+      Cx<CT> self = (CT)diag * cvt<CT, double>(V[(b * Nv + k) * (long long)g.Nb + i]);
       for (int dir = 1; dir <= 4; ++dir) {
         const Cx<double> *Vs = V + (nb[dir].src_b * Nv + k) * (long long)g.Nb + 2 * nb[dir].src_s;
-        const Cx<double> t = hop_scalar<double>(dir, link[dir], Vs[0], Vs[1]);
-        Cx<double> comp = spin == 0 ? t : hop_lower<double>(dir, t);
-        comp = -0.5 * comp;
+        const Cx<CT> t = hop_scalar<CT>(dir, link[dir], cvt<CT, double>(Vs[0]), cvt<CT, double>(Vs[1]));
+        Cx<CT> comp = spin == 0 ? t : hop_lower<CT>(dir, t);
+        comp = (CT)-0.5 * comp;
         if (nb[dir].face) {
           parts[dir * pstride + (long long)k * g.Nb + i] = comp;
         } else {
           self = self + comp;
-          parts[dir * pstride + (long long)k * g.Nb + i] = mk(0.0, 0.0);
+          parts[dir * pstride + (long long)k * g.Nb + i] = mk((CT)0, (CT)0);
         }
       }
       parts[(long long)k * g.Nb + i] = self;
@@ -279,9 +283,10 @@ __device__ void galerkin_parts_wilson(const Cx<double> *__restrict__ U, double d
   }
 }
 
-// parts for a coarse stencil level (n_int = N, Y internal [j][dir][col][row])
+// parts for a coarse stencil level (n_int = N, Y internal [j][dir][col][row]); arithmetic in CT
+template <typename CT>
 __device__ void galerkin_parts_stencil(const Cx<double> *__restrict__ Y, const Cx<double> *__restrict__ V,
-                                       const BlockGeo &g, int Nv, long long b, int lane, Cx<double> *parts) {
+                                       const BlockGeo &g, int Nv, long long b, int lane, Cx<CT> *parts) {
   const int N = g.nint;
   const long long pstride = (long long)Nv * g.Nb;
   for (int i = lane; i < g.Nb; i += 32) {
@@ -290,23 +295,23 @@ __device__ void galerkin_parts_stencil(const Cx<double> *__restrict__ Y, const C
     const int x0 = (int)(x % g.L0), x1 = (int)(x / g.L0);
     for (int k = 0; k < Nv; ++k) {
       // self term: X(arow, c) W_k(x, c)
-      Cx<double> self = mk(0.0, 0.0);
+      Cx<CT> self = mk((CT)0, (CT)0);
       {
         const Cx<double> *Yd = Y + (x * 5 + 0) * (long long)N * N;
         const Cx<double> *Ws = V + (b * Nv + k) * (long long)g.Nb + (long long)s * N;
-        for (int c = 0; c < N; ++c) cmac(self, Yd[(long long)c * N + arow], Ws[c]);
+        for (int c = 0; c < N; ++c) cmac(self, cvt<CT, double>(Yd[(long long)c * N + arow]), cvt<CT, double>(Ws[c]));
       }
       for (int dir = 1; dir <= 4; ++dir) {
         const NbrInfo nb = neighbour_in_blocks(g, x0, x1, dir);
         const Cx<double> *Yd = Y + (x * 5 + dir) * (long long)N * N;
         const Cx<double> *Ws = V + (nb.src_b * Nv + k) * (long long)g.Nb + (long long)nb.src_s * N;
-        Cx<double> comp = mk(0.0, 0.0);
-        for (int c = 0; c < N; ++c) cmac(comp, Yd[(long long)c * N + arow], Ws[c]);
+        Cx<CT> comp = mk((CT)0, (CT)0);
+        for (int c = 0; c < N; ++c) cmac(comp, cvt<CT, double>(Yd[(long long)c * N + arow]), cvt<CT, double>(Ws[c]));
         if (nb.face) {
           parts[dir * pstride + (long long)k * g.Nb + i] = comp;
         } else {
           self = self + comp;
-          parts[dir * pstride + (long long)k * g.Nb + i] = mk(0.0, 0.0);
+          parts[dir * pstride + (long long)k * g.Nb + i] = mk((CT)0, (CT)0);
         }
       }
       parts[(long long)k * g.Nb + i] = self;
@@ -314,29 +319,30 @@ __device__ void galerkin_parts_stencil(const Cx<double> *__restrict__ Y, const C
   }
 }
 
-template <bool WILSON>
+template <bool WILSON, typename CT>
 __global__ void galerkin_kernel(const Cx<double> *__restrict__ U_or_Y, double diag, const Cx<double> *__restrict__ V,
                                 Cx<double> *__restrict__ Yc, BlockGeo g, int Nv) {
-  extern __shared__ Cx<double> smem_gal[];
+  extern __shared__ __align__(16) unsigned char smem_gal_raw[];
+  Cx<CT> *smem_gal = reinterpret_cast<Cx<CT> *>(smem_gal_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long b = blockIdx.x * (long long)(blockDim.x >> 5) + warp;
   if (b >= g.nblocks) return;
-  Cx<double> *parts = smem_gal + (long long)warp * 5 * Nv * g.Nb;
+  Cx<CT> *parts = smem_gal + (long long)warp * 5 * Nv * g.Nb;
   if (WILSON)
-    galerkin_parts_wilson(U_or_Y, diag, V, g, Nv, b, lane, parts);
+    galerkin_parts_wilson<CT>(U_or_Y, diag, V, g, Nv, b, lane, parts);
   else
-    galerkin_parts_stencil(U_or_Y, V, g, Nv, b, lane, parts);
+    galerkin_parts_stencil<CT>(U_or_Y, V, g, Nv, b, lane, parts);
   __syncwarp();
   const long long pstride = (long long)Nv * g.Nb;
   const Cx<double> *Vb = V + b * (long long)Nv * g.Nb;
   for (int o = lane; o < 5 * Nv * Nv; o += 32) {
     const int dir = o / (Nv * Nv), rem = o - dir * Nv * Nv, k = rem / Nv, kp = rem - k * Nv;
-    Cx<double> acc = mk(0.0, 0.0);
-    const Cx<double> *p = parts + dir * pstride + (long long)k * g.Nb;
+    Cx<CT> acc = mk((CT)0, (CT)0);
+    const Cx<CT> *p = parts + dir * pstride + (long long)k * g.Nb;
     const Cx<double> *vk = Vb + (long long)kp * g.Nb;
-    for (int i = 0; i < g.Nb; ++i) cmac_conj(acc, vk[i], p[i]);
+    for (int i = 0; i < g.Nb; ++i) cmac_conj(acc, cvt<CT, double>(vk[i]), p[i]);
     // internal layout [b][dir][col = k][row = kp]
-    Yc[((b * 5 + dir) * Nv + k) * (long long)Nv + kp] = acc;
+    Yc[((b * 5 + dir) * Nv + k) * (long long)Nv + kp] = cvt<double, CT>(acc);
   }
 }
 
@@ -449,28 +455,34 @@ void launch_block_mgs(const Cx<double> *vecs, long long vec_stride, Cx<double> *
   MG_LAUNCHED();
 }
 
-template <bool WILSON>
+template <bool WILSON, typename CT>
 static void launch_galerkin_impl(const Cx<double> *UY, double diag, const Cx<double> *V, Cx<double> *Yc, BlockGeo bg,
                                  int Nv, cudaStream_t s) {
-  const size_t per_warp = (size_t)5 * Nv * bg.Nb * sizeof(Cx<double>);
+  const size_t per_warp = (size_t)5 * Nv * bg.Nb * sizeof(Cx<CT>);
   const int warps = warps_for_smem(per_warp, 200 * 1024);
   if (warps < 1) fail(MG_ERR_UNSUPPORTED, "Galerkin build: block too large for shared memory");
   const size_t smem = per_warp * warps;
-  MG_CUDA(cudaFuncSetAttribute(galerkin_kernel<WILSON>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  MG_CUDA(cudaFuncSetAttribute(galerkin_kernel<WILSON, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const unsigned int grid = (unsigned int)((bg.nblocks + warps - 1) / warps);
-  galerkin_kernel<WILSON><<<grid, 32 * warps, smem, s>>>(UY, diag, V, Yc, bg, Nv);
+  galerkin_kernel<WILSON, CT><<<grid, 32 * warps, smem, s>>>(UY, diag, V, Yc, bg, Nv);
   MG_LAUNCHED();
 }
 
 void launch_galerkin_wilson(const Cx<double> *U, double diag, const Cx<double> *V, Cx<double> *Yc, BlockGeo bg,
-                            int Nv, cudaStream_t s) {
+                            int Nv, cudaStream_t s, bool fp32_arith) {
   if (bg.nint != 2) fail(MG_ERR_INVALID_ARG, "Galerkin (Wilson): n_int must be 2");
-  launch_galerkin_impl<true>(U, diag, V, Yc, bg, Nv, s);
+  if (fp32_arith)
+    launch_galerkin_impl<true, float>(U, diag, V, Yc, bg, Nv, s);
+  else
+    launch_galerkin_impl<true, double>(U, diag, V, Yc, bg, Nv, s);
 }
 
 void launch_galerkin_stencil(const Cx<double> *Y, const Cx<double> *V, Cx<double> *Yc, BlockGeo bg, int Nv,
-                             cudaStream_t s) {
-  launch_galerkin_impl<false>(Y, 0.0, V, Yc, bg, Nv, s);
+                             cudaStream_t s, bool fp32_arith) {
+  if (fp32_arith)
+    launch_galerkin_impl<false, float>(Y, 0.0, V, Yc, bg, Nv, s);
+  else
+    launch_galerkin_impl<false, double>(Y, 0.0, V, Yc, bg, Nv, s);
 }
 
 void launch_coarse_to_canonical(const Cx<double> *Yi, Cx<double> *Yc, long long nsites, int N, cudaStream_t s) {

@@ -407,12 +407,15 @@ __global__ void __launch_bounds__(T::sites, MINB) dslash4_tile_kernel(const Cx<f
   for (int i = 0; i < 6; ++i) o[i] = make_float4(p[2 * i].re, p[2 * i].im, p[2 * i + 1].re, p[2 * i + 1].im);
 }
 
-// tile shapes of the tiled kernel; MG_DSLASH4_TILE picks one (default 1), MG_DSLASH4_GATHER the
-// warp-gather kernel
+// tile shapes of the tiled kernel; MG_DSLASH4_TILE picks one (default 7, the fastest at 32^3 x 64:
+// 0.365 ms against 0.373 to 0.426 for the other shapes and 0.429 for the warp-gather kernel),
+// MG_DSLASH4_GATHER the warp-gather kernel
 using TileA = Tile4<8, 4, 4, 4>;  // 512 threads, 1 CTA per SM
 using TileB = Tile4<8, 4, 4, 2>;  // 256 threads, 2 CTAs per SM
 using TileC = Tile4<4, 4, 4, 2>;  // 128 threads, 4 CTAs per SM
 using TileD = Tile4<8, 4, 2, 2>;  // 128 threads, 4 CTAs per SM
+using TileE = Tile4<4, 4, 2, 2>;  // 64 threads, 8 CTAs per SM
+using TileF = Tile4<8, 2, 2, 2>;  // 64 threads, 8 CTAs per SM
 
 template <class T>
 static bool tile_divides(const Geo4 &g) {
@@ -438,13 +441,21 @@ static bool try_tile4(const Cx<float> *U, const Cx<float> *in, Cx<float> *out, G
                       const Cx<float> *b, double a, double c, cudaStream_t s, int nvec, const double *shift) {
   if (std::getenv("MG_DSLASH4_GATHER") != nullptr) return false;
   const char *v = std::getenv("MG_DSLASH4_TILE");
-  const int which = v != nullptr ? std::atoi(v) : 1;
+  const int which = v != nullptr ? std::atoi(v) : 7;
   if (which == 0 && tile_divides<TileA>(g)) {
     launch_tile4<TileA, 1>(U, in, out, g, diag, b, a, c, s, nvec, shift);
     return true;
   }
   if (which == 2 && tile_divides<TileC>(g)) {
     launch_tile4<TileC, 4>(U, in, out, g, diag, b, a, c, s, nvec, shift);
+    return true;
+  }
+  if (which == 6 && tile_divides<TileE>(g)) {
+    launch_tile4<TileE, 8>(U, in, out, g, diag, b, a, c, s, nvec, shift);
+    return true;
+  }
+  if (which == 7 && tile_divides<TileF>(g)) {
+    launch_tile4<TileF, 8>(U, in, out, g, diag, b, a, c, s, nvec, shift);
     return true;
   }
   if (which == 3 && tile_divides<TileD>(g)) {
@@ -457,6 +468,14 @@ static bool try_tile4(const Cx<float> *U, const Cx<float> *in, Cx<float> *out, G
   }
   if (which == 5 && tile_divides<TileC>(g)) {  // 6 CTAs per SM
     launch_tile4<TileC, 6>(U, in, out, g, diag, b, a, c, s, nvec, shift);
+    return true;
+  }
+  if (which == 1 && tile_divides<TileB>(g)) {
+    launch_tile4<TileB, 2>(U, in, out, g, diag, b, a, c, s, nvec, shift);
+    return true;
+  }
+  if (tile_divides<TileF>(g)) {
+    launch_tile4<TileF, 8>(U, in, out, g, diag, b, a, c, s, nvec, shift);
     return true;
   }
   if (tile_divides<TileB>(g)) {

@@ -59,9 +59,11 @@ def test_dslash4d_free_plane_wave_closed_form():
     np.testing.assert_allclose(got, ph[:, None, None] * (Dp @ u)[None], atol=1e-13)
 
 
-# (8, 4, 4, 2): one tile of the tiled FP32 kernel (every face wraps onto the tile itself);
-# (16, 8, 4, 8), (16, 16, 16, 32): several tiles; (4, 4, 4, 4), (6, 10, 4, 2): the warp-gather kernel
-@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (16, 16, 16, 32), (6, 10, 4, 2), (8, 4, 4, 2), (16, 8, 4, 8)])
+# (8, 2, 2, 2): one 8x2x2x2 tile of the tiled FP32 kernel (every face wraps onto the tile itself);
+# (8, 4, 4, 2), (16, 8, 4, 8), (16, 16, 16, 32): several tiles; (4, 4, 4, 4), (6, 10, 4, 2): the
+# warp-gather kernel
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (16, 16, 16, 32), (6, 10, 4, 2), (8, 4, 4, 2), (16, 8, 4, 8),
+                                  (8, 2, 2, 2)])
 def test_dslash4d_fp32_per_site_error_below_1e6(dims):
     # reference: FP64 D on the same FP32-rounded inputs; per-site error relative to
     # |diag psi_x| + 1/2 sum |hop terms_x| (bounds the cancellation at that site)
@@ -111,7 +113,7 @@ def test_dslash4d_large_sampled_fp32():
     assert np.abs(got[sites] - want).max() / np.abs(want).max() < 1e-6
 
 
-@pytest.mark.parametrize("variant", ["0", "1", "2", "3", "4", "5"])
+@pytest.mark.parametrize("variant", ["0", "1", "2", "3", "4", "5", "6", "7"])
 def test_dslash4d_fp32_tiled_and_gather_kernels_agree(variant, monkeypatch):
     # the FP32 kernels (every tile shape, and the warp-gather kernel) form the same hop sums in the
     # same order: they agree to rounding
