@@ -9,6 +9,8 @@
 // reductions and the prolongation read V with unit stride.
 #include <algorithm>
 
+#include <cstdlib>
+
 #include "mg4d.h"
 #include "wilson4d.cuh"
 
@@ -701,9 +703,79 @@ void launch_block_apply4_32(const Cx<float> *Minv, const Cx<float> *r, Cx<float>
   MG_LAUNCHED();
 }
 
+// the same step with kSplit consecutive lanes per element, each summing the basis vectors
+// j = lane, lane + kSplit, ... (the coarse vectors are short: one thread per element left most
+// SMs without work while every thread walked the whole basis)
+constexpr int kSplit = 4;
+
+template <typename VT>
+__global__ void gcr_update_split_kernel(const Cx<VT> *__restrict__ W, Cx<VT> *__restrict__ Wk,
+                                        const Cx<VT> *__restrict__ Z, Cx<VT> *__restrict__ Zk, int k,
+                                        const double *__restrict__ dots, double *__restrict__ state,
+                                        Cx<VT> *__restrict__ x, Cx<VT> *__restrict__ r, long long n) {
+  __shared__ double coef[3];
+  if (threadIdx.x == 0) {
+    const double nw0 = dots[2 * k];
+    double nw2 = nw0;
+    for (int j = 0; j < k; ++j) nw2 -= dots[2 * j] * dots[2 * j] + dots[2 * j + 1] * dots[2 * j + 1];
+    double inv = 0.0, are = 0.0, aim = 0.0;
+    if (nw2 > 1e-28 * nw0) {
+      inv = 1.0 / sqrt(nw2);
+      are = dots[2 * k + 2] * inv;
+      aim = dots[2 * k + 3] * inv;
+    }
+    coef[0] = inv;
+    coef[1] = are;
+    coef[2] = aim;
+    if (blockIdx.x == 0) state[0] = fmax(dots[2 * k + 4] - (are * are + aim * aim), 0.0);
+  }
+  __syncthreads();
+  const VT inv = (VT)coef[0];
+  const Cx<VT> alpha = mk((VT)coef[1], (VT)coef[2]), malpha = mk((VT)-coef[1], (VT)-coef[2]);
+  const int sub = threadIdx.x % kSplit, lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * (blockDim.x / kSplit);
+  long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / kSplit;
+  // i0, the warp's first element, steers the loop: every lane of the warp takes part in every
+  // shuffle, and lanes past the end only contribute zeros
+  for (long long i0 = i - lane / kSplit; i0 < n; i0 += stride, i += stride) {
+    const bool valid = i < n;
+    Cx<VT> pw = mk((VT)0, (VT)0), pz = mk((VT)0, (VT)0);
+    for (int j = sub; valid && j < k; j += kSplit) {
+      const Cx<VT> bj = mk((VT)-dots[2 * j], (VT)-dots[2 * j + 1]);
+      cmac(pw, bj, W[(long long)j * n + i]);
+      cmac(pz, bj, Z[(long long)j * n + i]);
+    }
+#pragma unroll
+    for (int o = kSplit / 2; o > 0; o >>= 1) {
+      pw.re += __shfl_xor_sync(0xffffffffu, pw.re, o);
+      pw.im += __shfl_xor_sync(0xffffffffu, pw.im, o);
+      pz.re += __shfl_xor_sync(0xffffffffu, pz.re, o);
+      pz.im += __shfl_xor_sync(0xffffffffu, pz.im, o);
+    }
+    if (valid && sub == 0) {
+      const Cx<VT> w = inv * (Wk[i] + pw), z = inv * (Zk[i] + pz);
+      Wk[i] = w;
+      Zk[i] = z;
+      cmac(x[i], alpha, z);
+      Cx<VT> ri = r[i];
+      cmac(ri, malpha, w);
+      r[i] = ri;
+    }
+  }
+}
+
 template <typename VT>
 static void gcr_update_dev_any(const Cx<VT> *W, Cx<VT> *Wk, const Cx<VT> *Z, Cx<VT> *Zk, int k, const double *dots,
                                double *state, Cx<VT> *x, Cx<VT> *r, long long n, cudaStream_t s) {
+  if (sizeof(VT) == 4 && std::getenv("MG_COARSE4_UPDATE_ONE") == nullptr) {
+    // kSplit threads per element in blocks of 256
+    long long b = (n * kSplit + 255) / 256;
+    if (b > 152LL * 16) b = 152LL * 16;
+    gcr_update_split_kernel<VT><<<(unsigned int)(b < 1 ? 1 : b), 256, 0, s>>>(W, Wk, Z, Zk, k, dots, state, x, r,
+                                                                              n);
+    MG_LAUNCHED();
+    return;
+  }
   long long b = (n + 255) / 256;
   if (b > 152LL * 16) b = 152LL * 16;
   gcr_update_dev_kernel<VT><<<(unsigned int)(b < 1 ? 1 : b), 256, 0, s>>>(W, Wk, Z, Zk, k, dots, state, x, r, n);
