@@ -45,11 +45,18 @@ WORKLOAD = ("2d U(1) Wilson-Dirac 256x256, beta in {3,6,10}, m-m_c in {0.005,0.0
             "3-level MG 4x4/2x2 Nv=8, 5 passes, MR 4+4; setup once per beta, 9 solves per step")
 
 
-def mg_params(precision: int):
+# outer GCR restart of the sweep: 8 at 256^2 (a step took 90.5 ms against 93.0 ms with 16: the FP64
+# Gram-Schmidt over the basis is a tenth of an outer iteration, for 0 to 6 more outer iterations per
+# solve); the 1024^2 points keep 16 (with 8 the beta 6 field at m_c + 0.005 did not converge in 3000)
+OUTER_RESTART = {256: 8, 1024: 16}
+
+
+def mg_params(precision: int, L_field: int = 256):
     import paper_0707_4018_gb300 as mg
-    # max_iter 3000: the 1024^2 field at m_c(256^2) + 0.005 needs about 600 outer iterations
+    # max_iter 3000: the 1024^2 field at m_c(256^2) + 0.005 needs about 500 outer iterations
     return mg.mg_default_params(levels=3, blocks=[(4, 4), (2, 2)], Nv=[8, 8], precision=precision,
-                                coarsest_tol=0.2, coarsest_restart=16, max_iter=3000)
+                                coarsest_tol=0.2, coarsest_restart=16, max_iter=3000,
+                                gcr_restart=OUTER_RESTART.get(L_field, 16))
 
 
 def mcrit_table():
@@ -155,7 +162,7 @@ def _one_field(f, precision, stats_out, host_io, contexts):
     else:
         U = f["U_dev"]
     Lf = f.get("L", L)
-    ctx = mg.Context.setup(U, f["m_c"] + DMS[0], (Lf, Lf), mg_params(precision))
+    ctx = mg.Context.setup(U, f["m_c"] + DMS[0], (Lf, Lf), mg_params(precision, Lf))
     contexts.append(ctx)
 
     def solve(c, i, dm):
@@ -213,7 +220,7 @@ def run_step_graph(fields_dev, precision: int, stats_out=None, host_io=None):
         try:
             U = f["U_host"].to("cuda", non_blocking=True) if host_io is not None else f["U_dev"]
             Lf = f.get("L", L)
-            c = mg.Context.setup(U, f["m_c"] + DMS[0], (Lf, Lf), mg_params(precision))
+            c = mg.Context.setup(U, f["m_c"] + DMS[0], (Lf, Lf), mg_params(precision, Lf))
             cs = [c] + [c.clone(f["m_c"] + dm) for dm in DMS[1:]]
             chis = [f["chi_host"][i].to("cuda", non_blocking=True) if host_io is not None else f["chi_dev"][i]
                     for i in range(len(DMS))]

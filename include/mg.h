@@ -438,6 +438,42 @@ int mg_setup_learned(mg_ctx **ctx, const mg_geom *g, const void *U, double m, co
  * / (steps - 1)) (steps >= 2). d = 2. */
 int mg_convergence_rate(mg_ctx *ctx, int steps, uint64_t seed, double *rate);
 
+/*
+ * MG-preconditioned conjugate gradients on the normal equations: the paper's own experiment
+ * (numerical-results section; Eq. vcycle in its hermitian form). The operator is A = D^dagger D;
+ * the hierarchy is built by the adaptive procedure on A (Eq. relax with nu_setup MR steps on
+ * A x = 0 from Philox vectors, block Gram-Schmidt, n_pass - 1 adaptive passes v <- v - V(A v),
+ * level by level); the coarse operators P^dagger A P are 9-point stencils (D^dagger D reaches the
+ * diagonal neighbours); every non-coarsest level relaxes with the degree-2 MR polynomial whose
+ * coefficients come from two MR steps (omega) on a fixed Philox vector and are then held fixed, so
+ * R = R^dagger and the V-cycle is hermitian; the coarsest level is solved by dense LU (at most 4096
+ * dofs). All arithmetic is FP64.
+ *   mg_cg_setup: g (d = 2, Nc = 1), U device complex128 [x][mu] (copied), mass m, parameters p
+ *     (levels, block, Nv, n_pass, nu_setup, omega and seed are used; blocks at least 2 x 2, and
+ *     every coarse extent at least 3). Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA, NAN.
+ *   mg_cg_solve: psi = D^{-1} chi through A psi = D^dagger chi by CG from psi = 0, preconditioned
+ *     by one V-cycle per iteration when `precondition` is nonzero (plain CG otherwise), until the
+ *     recursive residual is at most tol |D^dagger chi| or after max_iter iterations. chi, psi:
+ *     device complex128 [x][s]. st (may be NULL): iterations, the recomputed relative residual of
+ *     the normal equations, and the fine A applications of the call (the paper's cost measure: 6
+ *     per MG-CG iteration, 1 per CG iteration). NOT_CONVERGED leaves the last iterate in psi.
+ *   mg_cg_get_coarse_op: the level-l (l >= 1) stencil Y[j][o][row][col] (o = 3 (o1 + 1) + (o0 + 1)
+ *     for the neighbour j + o), device complex128, nsites x 9 x N x N.
+ */
+typedef struct mg_cg_ctx mg_cg_ctx;
+typedef struct {
+  int iters;              /* CG iterations */
+  int converged;          /* 1 if the recomputed residual met the tolerance */
+  double rel_residual;    /* |D^dagger chi - A psi| / |D^dagger chi|, recomputed in FP64 */
+  long long fine_apps;    /* fine A = D^dagger D applications of the iterations */
+  double ms;              /* wall time of the call, stream-synchronised */
+} mg_cg_stats;
+int mg_cg_setup(mg_cg_ctx **ctx, const mg_geom *g, const void *U, double m, const mg_params *p, void *stream);
+int mg_cg_solve(mg_cg_ctx *ctx, const void *chi, void *psi, double tol, int max_iter, int precondition,
+                mg_cg_stats *st);
+int mg_cg_get_coarse_op(mg_cg_ctx *ctx, int level, void *out);
+int mg_cg_destroy(mg_cg_ctx *ctx);
+
 /* Launch shapes picked by the library's autotuner so far (the tensor-core coarse apply
  * times its six tile shapes -- warps per CTA x vector tiles per warp -- on first use for
  * each lattice and vector count, and keeps the fastest; all shapes give bitwise the same

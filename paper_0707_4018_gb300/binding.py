@@ -54,6 +54,15 @@ class mg_stats(ctypes.Structure):
                     fine_D_apps=self.fine_D_apps)
 
 
+class mg_cg_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("fine_apps", ctypes.c_longlong), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return dict(iters=self.iters, converged=bool(self.converged), rel_residual=self.rel_residual,
+                    fine_apps=self.fine_apps, ms=self.ms)
+
+
 _lib = None
 
 
@@ -116,6 +125,10 @@ def load():
         "mg_coarsest_solve": (I, [ctxp, VP, VP, P(ctypes.c_longlong), P(D)]),
         "mg_selftest_barrier": (I, [I, VP]),
         "mg_autotune_report": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
+        "mg_cg_setup": (I, [P(ctxp), P(mg_geom), VP, D, P(mg_params), VP]),
+        "mg_cg_solve": (I, [ctxp, VP, VP, D, I, I, P(mg_cg_stats)]),
+        "mg_cg_get_coarse_op": (I, [ctxp, I, VP]),
+        "mg_cg_destroy": (I, [ctxp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -135,7 +148,7 @@ def exported_symbols():
             "mg_load_setup", "mg_context_info", "mg_nullnet_create", "mg_nullnet_destroy", "mg_nullnet_weight_count",
             "mg_nullnet_get_weights", "mg_nullnet_set_weights", "mg_nullnet_forward", "mg_nullnet_gradient",
             "mg_nullnet_train", "mg_setup_learned", "mg_convergence_rate", "mg_alu_peak", "mg_solve_multi",
-            "mg_half_convert"]
+            "mg_half_convert", "mg_cg_setup", "mg_cg_solve", "mg_cg_get_coarse_op", "mg_cg_destroy"]
 
 
 def autotune_report() -> dict:
@@ -542,6 +555,58 @@ class Context:
         out = torch.empty((n, 9 if self.four else 5, k, k), dtype=torch.complex128, device="cuda")
         _check(load().mg_get_coarse_op(self._need(), level, _ptr(out)))
         return out
+
+
+class CgContext:
+    """MG-preconditioned CG on the normal equations (wraps mg_cg_ctx*): the paper's own experiment."""
+
+    def __init__(self, handle, dims, params, stream):
+        self._h, self.dims, self.params, self.stream = handle, tuple(dims), params, stream
+        self.volume = int(dims[0]) * int(dims[1])
+
+    @classmethod
+    def setup(cls, U: torch.Tensor, m: float, dims, params: mg_params, stream=None) -> "CgContext":
+        """mg_cg_setup: the adaptive hierarchy for A = D^dagger D (2d U(1) links U[x][mu])."""
+        g = make_geom(dims)
+        h = ctypes.c_void_p()
+        s = _stream(stream)
+        V = int(dims[0]) * int(dims[1])
+        _check(load().mg_cg_setup(ctypes.byref(h), ctypes.byref(g), _ptr(U, torch.complex128, 2 * V), float(m),
+                                  ctypes.byref(params), s))
+        return cls(h, dims, params, s)
+
+    def _need(self):
+        if self._h is None:
+            raise MGError(1, "context closed")
+        return self._h
+
+    def solve(self, chi: torch.Tensor, psi: torch.Tensor, tol: float, max_iter: int = 100000,
+              precondition: bool = True, raise_on_fail: bool = True) -> dict:
+        """mg_cg_solve: psi = D^-1 chi through the normal equations by (MG-preconditioned) CG."""
+        st = mg_cg_stats()
+        n = 2 * self.volume
+        code = load().mg_cg_solve(self._need(), _ptr(chi, torch.complex128, n), _ptr(psi, torch.complex128, n),
+                                  float(tol), int(max_iter), 1 if precondition else 0, ctypes.byref(st))
+        if raise_on_fail or code not in (0, 4):
+            _check(code)
+        return st.as_dict()
+
+    def coarse_op(self, level: int, nsites: int, N: int) -> torch.Tensor:
+        """mg_cg_get_coarse_op: the 9-point stencil of level `level` as [site][o][row][col]."""
+        out = torch.empty((nsites, 9, N, N), dtype=torch.complex128, device="cuda")
+        _check(load().mg_cg_get_coarse_op(self._need(), int(level), _ptr(out)))
+        return out
+
+    def close(self):
+        if self._h is not None:
+            load().mg_cg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class NullNet:
