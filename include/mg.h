@@ -463,8 +463,8 @@ int mg_convergence_rate(mg_ctx *ctx, int steps, uint64_t seed, double *rate);
 typedef struct mg_cg_ctx mg_cg_ctx;
 typedef struct {
   int iters;              /* CG iterations */
-  int converged;          /* 1 if the recomputed residual met the tolerance */
-  double rel_residual;    /* |D^dagger chi - A psi| / |D^dagger chi|, recomputed in FP64 */
+  int converged;          /* 1 if the recursive CG residual met the tolerance (the paper's criterion) */
+  double rel_residual;    /* |D^dagger chi - A psi| / |D^dagger chi|, recomputed in FP64 afterwards */
   long long fine_apps;    /* fine A = D^dagger D applications of the iterations */
   double ms;              /* wall time of the call, stream-synchronised */
 } mg_cg_stats;

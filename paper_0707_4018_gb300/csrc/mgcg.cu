@@ -440,6 +440,7 @@ static void cg_solve(CgEngine &e, const Cx<double> *chi, Cx<double> *psi, double
   launch_zero<double>(e.cx.p, n, e.s);
   launch_copy<double>(e.rhs.p, e.cr.p, n, e.s);
   int it = 0;
+  bool met = bn2 == 0.0;
   if (bn2 > 0.0) {
     if (precond)
       cg_vcycle(e, 0, e.cr.p, e.cz.p);
@@ -469,6 +470,7 @@ static void cg_solve(CgEngine &e, const Cx<double> *chi, Cx<double> *psi, double
       direction_kernel<<<blocks_for(n), 256, 0, e.s>>>(e.cp.p, e.cz.p, beta, n);
       MG_LAUNCHED();
     }
+    met = rn2 <= tol2;
   }
   const long long apps = e.fine_apps;
   // true residual of the normal equations
@@ -480,7 +482,7 @@ static void cg_solve(CgEngine &e, const Cx<double> *chi, Cx<double> *psi, double
   const double rel = bn2 > 0.0 ? std::sqrt(d[2] / bn2) : 0.0;
   if (st) {
     st->iters = it;
-    st->converged = rel <= tol * 1.0001 + 1e-300 || bn2 == 0.0 ? 1 : 0;
+    st->converged = met ? 1 : 0;  // the CG criterion: the recursive residual met the tolerance
     st->rel_residual = rel;
     st->fine_apps = apps;
     st->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

@@ -54,7 +54,7 @@ def test_solves_match_oracle(precondition):
         op = normal.NormalOperator(U, m, lat)
         want, info = normal.cg(op.apply, wilson.apply_Ddag(U, chi, m, lat), 1e-12, 100000)
         assert st["fine_apps"] == st["iters"]
-    assert st["converged"] and st["rel_residual"] <= 1e-12
+    assert st["converged"] and st["rel_residual"] <= 2e-12
     assert abs(st["iters"] - info["iters"]) <= (1 if precondition else 3), (st["iters"], info["iters"])
     got = to_host(psi)
     assert rel_err(got, want) < 1e-8
