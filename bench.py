@@ -1140,7 +1140,7 @@ def run_only(case: str):
             g = torch.Generator(device="cuda").manual_seed(9)
             x = torch.randn((R, n_sites, n_int), dtype=torch.complex64, device="cuda", generator=g)
             y = torch.empty_like(x)
-            for tc in (True, False):
+            for tc in (1, 2, 3, 0):  # BF16 operands, split vectors, split vectors and operator, CUDA cores
                 for _ in range(3):
                     ctx.coarse_apply_mrhs(1, x, y, tc)
                 ms = []
@@ -1153,7 +1153,8 @@ def run_only(case: str):
                     e1.synchronize()
                     ms.append(e0.elapsed_time(e1))
                 t = statistics.median(ms) * 1e-3
-                out[f"{'tensor' if tc else 'cuda_core'}_rhs{R}"] = {
+                name = {0: "cuda_core", 1: "tensor", 2: "tensor_split_vectors", 3: "tensor_split_both"}[tc]
+                out[f"{name}_rhs{R}"] = {
                     "us_per_call_incl_sync": t * 1e6, "gflops": 9 * 48 * 48 * 8 * R * n_sites / t / 1e9}
         print(json.dumps(out))
         ctx.close()

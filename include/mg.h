@@ -362,10 +362,14 @@ int mg_smooth_fine_noalloc(const mg_geom *g, const void *U, double m, const void
  *          B (-B by a sign flip): 108 mma.sync per warp of 16 rows x 8 vectors; the FP64
  *          operator is rounded to BF16 (either precision).
  *   in, out  device complex64 [n][site][dof], nrhs level vectors back to back (caller-owned)
- * Operands are rounded to BF16 and the products summed in FP32 (relative error about 2^-8 of
+ * tensor_cores = 1: operands rounded to BF16, products summed in FP32 (relative error about
+ * 2^-8 of sum |Y| |x|). d = 4 only: 2 splits every vector entry into BF16 hi + lo (twice the
+ * MMAs; the error is then the operator's rounding), 3 splits the operator as well and sums
+ * hi hi + hi lo + lo hi (three times the MMAs, twice the operator bytes; about 2^-16 of
  * sum |Y| |x|). tensor_cores = 0 runs the same product on CUDA cores in FP32 (the comparison
- * path). Errors: INVALID_ARG (level, nrhs < 1, null pointers), UNSUPPORTED (d = 2 with an
- * FP64 context or N != 8; d = 4 with N != 48). */
+ * path). Errors: INVALID_ARG (level, nrhs < 1, null pointers, tensor_cores outside 0..3,
+ * overlapping in and out), UNSUPPORTED (d = 2 with an FP64 context, N != 8 or
+ * tensor_cores > 1; d = 4 with N != 48). */
 int mg_coarse_apply_mrhs(mg_ctx *ctx, int level, int nrhs, const void *in, void *out, int tensor_cores);
 
 /* ---- learned near-null setup --------------------------------------------------------

@@ -474,13 +474,15 @@ class Context:
             _check(code)
         return [st[v].as_dict() for v in range(nrhs)]
 
-    def coarse_apply_mrhs(self, level: int, inp: torch.Tensor, out: torch.Tensor, tensor_cores: bool = True):
+    def coarse_apply_mrhs(self, level: int, inp: torch.Tensor, out: torch.Tensor, tensor_cores=True):
         """mg_coarse_apply_mrhs: out[n] = A_level inp[n] (complex64) on tensor cores (BF16 operands,
-        FP32 sums) or, with tensor_cores=False, on CUDA cores in FP32."""
+        FP32 sums) or, with tensor_cores=False, on CUDA cores in FP32; an int passes the C value
+        (4d: 2 splits the vectors into BF16 hi + lo, 3 the operator as well)."""
         nrhs = int(inp.shape[0])
         n = self._numel(level) * nrhs
+        mode = int(tensor_cores) if not isinstance(tensor_cores, bool) else (1 if tensor_cores else 0)
         _check(load().mg_coarse_apply_mrhs(self._need(), int(level), nrhs, _ptr(inp, torch.complex64, n),
-                                           _ptr(out, torch.complex64, n), 1 if tensor_cores else 0))
+                                           _ptr(out, torch.complex64, n), mode))
 
     def info(self) -> dict:
         """mg_context_info: the parameters as given at setup (precision included) and the mass."""

@@ -82,14 +82,18 @@ __global__ void mr_update_kernel(const double *__restrict__ sc, double omega, Cx
 // rows j < k: <W_j, w>; row k: <w, w>; row k + 1: <w, r>; row k + 2: <r, r>  (blockIdx.y = row)
 // (VT = float: FP32 vectors; each thread sums its few products in FP32, the block and grid
 // trees sum in FP64)
+// (kdev: k read from device memory, for loops replayed by a graph; the grid then has rows
+// for the longest basis, and the rows above k + 2 return at once, all blocks of a row alike)
 template <typename VT>
 __global__ void __launch_bounds__(kReduceThreads) gcr_dots_kernel(const Cx<VT> *__restrict__ W,
                                                                   const Cx<VT> *__restrict__ w,
-                                                                  const Cx<VT> *__restrict__ r, int k,
-                                                                  long long n, double *partials, double *out,
+                                                                  const Cx<VT> *__restrict__ r, int k_host,
+                                                                  const int *__restrict__ kdev, long long n,
+                                                                  double *partials, double *out,
                                                                   unsigned int *ticket, int pstride) {
   __shared__ double sh[32 * 2];
-  const int row = blockIdx.y;
+  const int row = blockIdx.y, k = kdev != nullptr ? *kdev : k_host;
+  if (row > k + 2) return;
   const Cx<VT> *a = row < k ? W + (long long)row * n : (row == k + 2 ? r : w);
   const Cx<VT> *b = row > k ? r : w;
   VT t0 = (VT)0, t1 = (VT)0;
@@ -137,9 +141,27 @@ static void gcr_dots_any(const Cx<VT> *W, const Cx<VT> *w, const Cx<VT> *r, int 
   if (per > ws.max_blocks) per = ws.max_blocks;
   if (per < 1) per = 1;
   dim3 grid(reduce_blocks(n, per), rows);
-  gcr_dots_kernel<VT><<<grid, kReduceThreads, 0, s>>>(W, w, r, k, n, ws.partials, out, ws.ticket, 2 * (int)grid.x);
+  gcr_dots_kernel<VT><<<grid, kReduceThreads, 0, s>>>(W, w, r, k, nullptr, n, ws.partials, out, ws.ticket,
+                                                      2 * (int)grid.x);
   MG_LAUNCHED();
 }
+
+// the same reduction with k = *kdev (grid rows for k up to kmax)
+template <typename VT>
+void launch_gcr_dots_kdev(const Cx<VT> *W, const Cx<VT> *w, const Cx<VT> *r, const int *kdev, int kmax, long long n,
+                          double *out, const ReduceWs &ws, cudaStream_t s) {
+  const int rows = kmax + 3;
+  if (rows > 128) fail(MG_ERR_UNSUPPORTED, "gcr_dots: too many basis vectors");
+  int per = (int)(ws.capacity / (2 * rows));
+  if (per > ws.max_blocks) per = ws.max_blocks;
+  if (per < 1) per = 1;
+  dim3 grid(reduce_blocks(n, per), rows);
+  gcr_dots_kernel<VT><<<grid, kReduceThreads, 0, s>>>(W, w, r, 0, kdev, n, ws.partials, out, ws.ticket,
+                                                      2 * (int)grid.x);
+  MG_LAUNCHED();
+}
+template void launch_gcr_dots_kdev<float>(const Cx<float> *, const Cx<float> *, const Cx<float> *, const int *, int,
+                                          long long, double *, const ReduceWs &, cudaStream_t);
 
 void launch_gcr_dots(const Cx<double> *W, const Cx<double> *w, const Cx<double> *r, int k, long long n, double *out,
                      const ReduceWs &ws, cudaStream_t s) {
@@ -168,44 +190,50 @@ void launch_gcr_project_update(const Cx<double> *W, Cx<double> *Wk, const Cx<dou
 // ---------------------------------------------------------------------------
 
 // y_v = x_v for the vectors with mask bit v, else 0
-__global__ void copy_masked_kernel(const Cx<double> *__restrict__ x, Cx<double> *__restrict__ y, long long n,
+template <typename VT>
+__global__ void copy_masked_kernel(const Cx<VT> *__restrict__ x, Cx<VT> *__restrict__ y, long long n,
                                    unsigned int mask) {
   const long long off = blockIdx.y * n;
   const bool on = (mask >> blockIdx.y) & 1u;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[off + i] = on ? x[off + i] : mk(0.0, 0.0);
+    y[off + i] = on ? x[off + i] : mk((VT)0, (VT)0);
 }
 
 // out[v] = |a_v|^2 (blockIdx.y = v)
-__global__ void __launch_bounds__(kReduceThreads) norm2_batch_kernel(const Cx<double> *__restrict__ a, long long n,
+template <typename VT>
+__global__ void __launch_bounds__(kReduceThreads) norm2_batch_kernel(const Cx<VT> *__restrict__ a, long long n,
                                                                      double *partials, double *out,
                                                                      unsigned int *ticket) {
   __shared__ double sh[32];
-  const Cx<double> *av = a + blockIdx.y * n;
-  double v[1] = {0.0};
+  const Cx<VT> *av = a + blockIdx.y * n;
+  VT t = (VT)0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    v[0] += norm2(av[i]);
+    t += norm2(av[i]);
+  double v[1] = {(double)t};
   grid_finish<1>(v, partials + (long long)blockIdx.y * gridDim.x, out + blockIdx.y, ticket + blockIdx.y, sh);
 }
 
 // vector v = blockIdx.z, row = blockIdx.y: rows j < k <W_j, w>, row k |w|^2, row k + 1 <w, r>,
 // row k + 2 |r|^2; results at out[v * 2 (k + 3) + 2 row]
-__global__ void __launch_bounds__(kReduceThreads) gcr_dots_batch_kernel(const Cx<double> *__restrict__ W,
-                                                                        const Cx<double> *__restrict__ r, int k,
+// (VT = float: FP32 vectors, each thread's products summed in FP32, the trees in FP64)
+template <typename VT>
+__global__ void __launch_bounds__(kReduceThreads) gcr_dots_batch_kernel(const Cx<VT> *__restrict__ W,
+                                                                        const Cx<VT> *__restrict__ r, int k,
                                                                         int nb, long long n, double *partials,
                                                                         double *out, unsigned int *ticket) {
   __shared__ double sh[32 * 2];
   const int row = blockIdx.y, v = blockIdx.z, rows = k + 3;
-  const Cx<double> *w = W + ((long long)k * nb + v) * n;
-  const Cx<double> *rv = r + (long long)v * n;
-  const Cx<double> *a = row < k ? W + ((long long)row * nb + v) * n : (row == k + 2 ? rv : w);
-  const Cx<double> *b = row > k ? rv : w;
-  double acc[2] = {0.0, 0.0};
+  const Cx<VT> *w = W + ((long long)k * nb + v) * n;
+  const Cx<VT> *rv = r + (long long)v * n;
+  const Cx<VT> *a = row < k ? W + ((long long)row * nb + v) * n : (row == k + 2 ? rv : w);
+  const Cx<VT> *b = row > k ? rv : w;
+  VT t0 = (VT)0, t1 = (VT)0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const Cx<double> x = a[i], y = b[i];
-    acc[0] += x.re * y.re + x.im * y.im;
-    acc[1] += x.re * y.im - x.im * y.re;
+    const Cx<VT> x = a[i], y = b[i];
+    t0 += x.re * y.re + x.im * y.im;
+    t1 += x.re * y.im - x.im * y.re;
   }
+  double acc[2] = {(double)t0, (double)t1};
   const long long slot = (long long)v * rows + row;
   grid_finish<2>(acc, partials + slot * 2 * gridDim.x, out + 2 * slot, ticket + slot, sh);
 }
@@ -214,20 +242,21 @@ __global__ void __launch_bounds__(kReduceThreads) gcr_dots_batch_kernel(const Cx
 // mode 0 leaves the vector alone; mode 2 projects w_k, z_k against the basis with beta_j =
 // dots[v * 2 (k + 3) + 2 j]; mode 1 projects, scales both by inv and updates x += alpha z_k,
 // r -= alpha w_k
-__global__ void gcr_update_batch_kernel(Cx<double> *__restrict__ W, Cx<double> *__restrict__ Z, int k, int nb,
+template <typename VT>
+__global__ void gcr_update_batch_kernel(Cx<VT> *__restrict__ W, Cx<VT> *__restrict__ Z, int k, int nb,
                                         const double *__restrict__ dots, const double *__restrict__ coef,
-                                        Cx<double> *__restrict__ x, Cx<double> *__restrict__ r, long long n) {
+                                        Cx<VT> *__restrict__ x, Cx<VT> *__restrict__ r, long long n) {
   const int v = blockIdx.y;
   const int mode = (int)coef[4 * v + 3];
   if (mode == 0) return;
   const double *beta = dots + (long long)v * 2 * (k + 3);
-  const double inv = mode == 1 ? coef[4 * v] : 1.0;
-  const Cx<double> alpha = mk(coef[4 * v + 1], coef[4 * v + 2]);
-  Cx<double> *Wk = W + ((long long)k * nb + v) * n, *Zk = Z + ((long long)k * nb + v) * n;
+  const VT inv = (VT)(mode == 1 ? coef[4 * v] : 1.0);
+  const Cx<VT> alpha = mk((VT)coef[4 * v + 1], (VT)coef[4 * v + 2]);
+  Cx<VT> *Wk = W + ((long long)k * nb + v) * n, *Zk = Z + ((long long)k * nb + v) * n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    Cx<double> w = Wk[i], z = Zk[i];
+    Cx<VT> w = Wk[i], z = Zk[i];
     for (int j = 0; j < k; ++j) {
-      const Cx<double> bj = mk(-beta[2 * j], -beta[2 * j + 1]);
+      const Cx<VT> bj = mk((VT)-beta[2 * j], (VT)-beta[2 * j + 1]);
       const long long o = ((long long)j * nb + v) * n + i;
       cmac(w, bj, W[o]);
       cmac(z, bj, Z[o]);
@@ -238,7 +267,7 @@ __global__ void gcr_update_batch_kernel(Cx<double> *__restrict__ W, Cx<double> *
     Zk[i] = z;
     if (mode == 1) {
       cmac(x[(long long)v * n + i], alpha, z);
-      Cx<double> ri = r[(long long)v * n + i];
+      Cx<VT> ri = r[(long long)v * n + i];
       cmac(ri, mk(-alpha.re, -alpha.im), w);
       r[(long long)v * n + i] = ri;
     }
@@ -247,36 +276,53 @@ __global__ void gcr_update_batch_kernel(Cx<double> *__restrict__ W, Cx<double> *
 
 static unsigned int stream_grid(long long n);
 
-void launch_copy_masked(const Cx<double> *x, Cx<double> *y, long long n, int nb, unsigned int mask, cudaStream_t s) {
-  copy_masked_kernel<<<dim3(stream_grid(n), nb), 256, 0, s>>>(x, y, n, mask);
+template <typename VT>
+void launch_copy_masked(const Cx<VT> *x, Cx<VT> *y, long long n, int nb, unsigned int mask, cudaStream_t s) {
+  copy_masked_kernel<VT><<<dim3(stream_grid(n), nb), 256, 0, s>>>(x, y, n, mask);
   MG_LAUNCHED();
 }
 
-void launch_norm2_batch(const Cx<double> *a, long long n, int nb, double *out, const ReduceWs &ws, cudaStream_t s) {
+template <typename VT>
+void launch_norm2_batch(const Cx<VT> *a, long long n, int nb, double *out, const ReduceWs &ws, cudaStream_t s) {
   int per = (int)(ws.capacity / nb);
   if (per > ws.max_blocks) per = ws.max_blocks;
   if (per < 1) per = 1;
-  norm2_batch_kernel<<<dim3(reduce_blocks(n, per), nb), kReduceThreads, 0, s>>>(a, n, ws.partials, out, ws.ticket);
+  norm2_batch_kernel<VT><<<dim3(reduce_blocks(n, per), nb), kReduceThreads, 0, s>>>(a, n, ws.partials, out,
+                                                                                    ws.ticket);
   MG_LAUNCHED();
 }
 
-void launch_gcr_dots_batch(const Cx<double> *W, const Cx<double> *r, int k, int nb, long long n, double *out,
+template <typename VT>
+void launch_gcr_dots_batch(const Cx<VT> *W, const Cx<VT> *r, int k, int nb, long long n, double *out,
                            const ReduceWs &ws, cudaStream_t s) {
   const int rows = k + 3;
   if ((long long)rows * nb > ws.tickets) fail(MG_ERR_UNSUPPORTED, "gcr_dots_batch: too many reductions");
   int per = (int)(ws.capacity / (2LL * rows * nb));
   if (per > ws.max_blocks) per = ws.max_blocks;
   if (per < 1) fail(MG_ERR_STATE, "gcr_dots_batch: reduction workspace too small");
-  gcr_dots_batch_kernel<<<dim3(reduce_blocks(n, per), rows, nb), kReduceThreads, 0, s>>>(W, r, k, nb, n, ws.partials,
-                                                                                         out, ws.ticket);
+  gcr_dots_batch_kernel<VT><<<dim3(reduce_blocks(n, per), rows, nb), kReduceThreads, 0, s>>>(W, r, k, nb, n,
+                                                                                             ws.partials, out,
+                                                                                             ws.ticket);
   MG_LAUNCHED();
 }
 
-void launch_gcr_update_batch(Cx<double> *W, Cx<double> *Z, int k, int nb, const double *dots, const double *coef,
-                             Cx<double> *x, Cx<double> *r, long long n, cudaStream_t s) {
-  gcr_update_batch_kernel<<<dim3(stream_grid(n), nb), 256, 0, s>>>(W, Z, k, nb, dots, coef, x, r, n);
+template <typename VT>
+void launch_gcr_update_batch(Cx<VT> *W, Cx<VT> *Z, int k, int nb, const double *dots, const double *coef, Cx<VT> *x,
+                             Cx<VT> *r, long long n, cudaStream_t s) {
+  gcr_update_batch_kernel<VT><<<dim3(stream_grid(n), nb), 256, 0, s>>>(W, Z, k, nb, dots, coef, x, r, n);
   MG_LAUNCHED();
 }
+
+#define MG_INST_BATCH(VT)                                                                                          \
+  template void launch_copy_masked<VT>(const Cx<VT> *, Cx<VT> *, long long, int, unsigned int, cudaStream_t);     \
+  template void launch_norm2_batch<VT>(const Cx<VT> *, long long, int, double *, const ReduceWs &, cudaStream_t); \
+  template void launch_gcr_dots_batch<VT>(const Cx<VT> *, const Cx<VT> *, int, int, long long, double *,          \
+                                          const ReduceWs &, cudaStream_t);                                         \
+  template void launch_gcr_update_batch<VT>(Cx<VT> *, Cx<VT> *, int, int, const double *, const double *,          \
+                                            Cx<VT> *, Cx<VT> *, long long, cudaStream_t);
+MG_INST_BATCH(double)
+MG_INST_BATCH(float)
+#undef MG_INST_BATCH
 
 // ---------------------------------------------------------------------------
 static unsigned int stream_grid(long long n) {

@@ -161,7 +161,9 @@ void launch_coarse_apply_tc(const uint2 *Ypk, const Cx<float> *in, Cx<float> *ou
 // ===========================================================================
 
 // Ypk4[((j * 9 + dir) * 2 + q) * 9 + tm * 3 + tk][lane] (uint4), q = 0: A = Re Y, 1: B = Im Y,
-// from the FP64 internal stencil Y[j][dir][col][row]
+// from the FP64 internal stencil Y[j][dir][col][row]; LO: the BF16 rounding of what the BF16
+// value leaves (y - bf16(y)), so that hi + lo carries about 16 significant bits
+template <bool LO>
 __global__ void pack_coarse4_bf16_kernel(const Cx<double> *__restrict__ Y, uint4 *__restrict__ Ypk, long long nsites) {
   const long long qi = blockIdx.x * (long long)blockDim.x + threadIdx.x;  // (j, dir, q, tile, lane)
   if (qi >= nsites * 9 * 2 * 9 * 32) return;
@@ -175,7 +177,9 @@ __global__ void pack_coarse4_bf16_kernel(const Cx<double> *__restrict__ Y, uint4
   const Cx<double> *Yb = Y + jd * 48 * 48;
   auto el = [&](int row, int col) {  // element (row, col) of A or B
     const Cx<double> y = Yb[(long long)(16 * tk + col) * 48 + 16 * tm + row];
-    return (float)(q == 0 ? y.re : y.im);
+    const double v = q == 0 ? y.re : y.im;
+    const float f = (float)v;  // the hi part is the BF16 rounding of this float, as in the kernel above
+    return LO ? (float)(v - (double)__bfloat162float(__float2bfloat16_rn(f))) : f;
   };
   uint4 out;
   out.x = pack_bf16x2(el(g, 2 * t), el(g, 2 * t + 1));
@@ -185,9 +189,19 @@ __global__ void pack_coarse4_bf16_kernel(const Cx<double> *__restrict__ Y, uint4
   Ypk[qi] = out;
 }
 
+// x = hi + lo for a pair of floats: hi their BF16 rounding, lo the BF16 rounding of the rest
+__device__ __forceinline__ void split_bf16x2(float a, float b, unsigned int &hi, unsigned int &lo) {
+  hi = pack_bf16x2(a, b);
+  lo = pack_bf16x2(a - __uint_as_float(hi << 16), b - __uint_as_float(hi & 0xffff0000u));
+}
+
 // out_n = A_c in_n for nvec vectors (stride ldv = nsites * 48); one warp per (site, row tile,
-// group of 8 vectors)
+// group of 8 vectors). SPLIT = 0: operator and vectors in BF16 (4 MMAs per tile pair);
+// 1: vectors as BF16 hi + lo (8 MMAs); 2: operator as hi + lo as well (Ypklo), the product
+// hi hi + hi lo + lo hi (12 MMAs): about 2^-16 of sum |Y| |x| instead of 2^-8
+template <int SPLIT>
 __global__ void __launch_bounds__(256) coarse4_apply_tc_kernel(const uint4 *__restrict__ Ypk,
+                                                               const uint4 *__restrict__ Ypklo,
                                                                const Cx<float> *__restrict__ in,
                                                                Cx<float> *__restrict__ out, int nb0, int nb1, int nb2,
                                                                int nb3, long long ldv, int nvec) {
@@ -227,15 +241,39 @@ __global__ void __launch_bounds__(256) coarse4_apply_tc_kernel(const uint4 *__re
         lo = *reinterpret_cast<const float4 *>(xs + 16 * tk + 2 * t);
         hi = *reinterpret_cast<const float4 *>(xs + 16 * tk + 2 * t + 8);
       }
-      const unsigned int r0 = pack_bf16x2(lo.x, lo.z), r1 = pack_bf16x2(hi.x, hi.z);  // xr fragment
-      const unsigned int i0 = pack_bf16x2(lo.y, lo.w), i1 = pack_bf16x2(hi.y, hi.w);  // xi fragment
-      const uint4 fa = Yd[(0 * 9 + tm * 3 + tk) * 32 + lane];
-      const uint4 fb = Yd[(1 * 9 + tm * 3 + tk) * 32 + lane];
+      unsigned int r0, r1, i0, i1, r0l = 0u, r1l = 0u, i0l = 0u, i1l = 0u;  // xr, xi fragments (hi, lo)
+      if (SPLIT == 0) {
+        r0 = pack_bf16x2(lo.x, lo.z);
+        r1 = pack_bf16x2(hi.x, hi.z);
+        i0 = pack_bf16x2(lo.y, lo.w);
+        i1 = pack_bf16x2(hi.y, hi.w);
+      } else {
+        split_bf16x2(lo.x, lo.z, r0, r0l);
+        split_bf16x2(hi.x, hi.z, r1, r1l);
+        split_bf16x2(lo.y, lo.w, i0, i0l);
+        split_bf16x2(hi.y, hi.w, i1, i1l);
+      }
+      const int fi = (tm * 3 + tk) * 32 + lane;
+      const uint4 fa = Yd[fi], fb = Yd[9 * 32 + fi];
       const unsigned int s = 0x80008000u;
       mma_bf16_16816(cre, fa.x, fa.y, fa.z, fa.w, r0, r1);                  // + A xr
       mma_bf16_16816(cre, fb.x ^ s, fb.y ^ s, fb.z ^ s, fb.w ^ s, i0, i1);  // - B xi
       mma_bf16_16816(cim, fb.x, fb.y, fb.z, fb.w, r0, r1);                  // + B xr
       mma_bf16_16816(cim, fa.x, fa.y, fa.z, fa.w, i0, i1);                  // + A xi
+      if (SPLIT >= 1) {
+        mma_bf16_16816(cre, fa.x, fa.y, fa.z, fa.w, r0l, r1l);
+        mma_bf16_16816(cre, fb.x ^ s, fb.y ^ s, fb.z ^ s, fb.w ^ s, i0l, i1l);
+        mma_bf16_16816(cim, fb.x, fb.y, fb.z, fb.w, r0l, r1l);
+        mma_bf16_16816(cim, fa.x, fa.y, fa.z, fa.w, i0l, i1l);
+      }
+      if (SPLIT == 2) {
+        const uint4 *Yl = Ypklo + (j * 9 + dir) * 2 * 9 * 32;
+        const uint4 ga = Yl[fi], gb = Yl[9 * 32 + fi];
+        mma_bf16_16816(cre, ga.x, ga.y, ga.z, ga.w, r0, r1);
+        mma_bf16_16816(cre, gb.x ^ s, gb.y ^ s, gb.z ^ s, gb.w ^ s, i0, i1);
+        mma_bf16_16816(cim, gb.x, gb.y, gb.z, gb.w, r0, r1);
+        mma_bf16_16816(cim, ga.x, ga.y, ga.z, ga.w, i0, i1);
+      }
     }
   }
   // C fragment: rows g, g + 8 of the tile (complex rows 16 tm + g, + 8), vectors n0 + 2t, + 1
@@ -249,18 +287,28 @@ __global__ void __launch_bounds__(256) coarse4_apply_tc_kernel(const uint4 *__re
   }
 }
 
-void launch_pack_coarse4_bf16(const Cx<double> *Y, uint4 *Ypk, long long nsites, cudaStream_t s) {
-  pack_coarse4_bf16_kernel<<<grid_for(nsites * 9 * 2 * 9 * 32, 256), 256, 0, s>>>(Y, Ypk, nsites);
+void launch_pack_coarse4_bf16(const Cx<double> *Y, uint4 *Ypk, long long nsites, cudaStream_t s, bool lo) {
+  if (lo)
+    pack_coarse4_bf16_kernel<true><<<grid_for(nsites * 9 * 2 * 9 * 32, 256), 256, 0, s>>>(Y, Ypk, nsites);
+  else
+    pack_coarse4_bf16_kernel<false><<<grid_for(nsites * 9 * 2 * 9 * 32, 256), 256, 0, s>>>(Y, Ypk, nsites);
   MG_LAUNCHED();
 }
 
 void launch_coarse4_apply_tc(const uint4 *Ypk, const Cx<float> *in, Cx<float> *out, const int nb[4], int nvec,
-                             cudaStream_t s) {
+                             cudaStream_t s, int split, const uint4 *Ypklo) {
   if (nvec < 1) return;
+  if (split < 0 || split > 2 || (split == 2 && Ypklo == nullptr))
+    fail(MG_ERR_INVALID_ARG, "tensor-core apply: split must be 0, 1 or 2 (2 needs the low BF16 part)");
   const long long nsites = (long long)nb[0] * nb[1] * nb[2] * nb[3];
   const long long warps = nsites * 3 * ((nvec + 7) / 8);
-  coarse4_apply_tc_kernel<<<grid_for(warps * 32, 256), 256, 0, s>>>(Ypk, in, out, nb[0], nb[1], nb[2], nb[3],
-                                                                    nsites * 48, nvec);
+  const unsigned int grid = grid_for(warps * 32, 256);
+  if (split == 0)
+    coarse4_apply_tc_kernel<0><<<grid, 256, 0, s>>>(Ypk, Ypklo, in, out, nb[0], nb[1], nb[2], nb[3], nsites * 48, nvec);
+  else if (split == 1)
+    coarse4_apply_tc_kernel<1><<<grid, 256, 0, s>>>(Ypk, Ypklo, in, out, nb[0], nb[1], nb[2], nb[3], nsites * 48, nvec);
+  else
+    coarse4_apply_tc_kernel<2><<<grid, 256, 0, s>>>(Ypk, Ypklo, in, out, nb[0], nb[1], nb[2], nb[3], nsites * 48, nvec);
   MG_LAUNCHED();
 }
 

@@ -150,6 +150,10 @@ void launch_gcr_dots(const Cx<double> *W, const Cx<double> *w, const Cx<double> 
 // the same reductions on FP32 vectors (products and sums in FP64)
 void launch_gcr_dots(const Cx<float> *W, const Cx<float> *w, const Cx<float> *r, int k, long long n, double *out,
                      const ReduceWs &ws, cudaStream_t s);
+// the same with k = *kdev read by the kernel (a graph-replayed loop; kmax bounds k)
+template <typename VT>
+void launch_gcr_dots_kdev(const Cx<VT> *W, const Cx<VT> *w, const Cx<VT> *r, const int *kdev, int kmax, long long n,
+                          double *out, const ReduceWs &ws, cudaStream_t s);
 // w = (w - sum beta_j W_j) inv and z likewise (written to Wk / Zk); then, if update_xr,
 // x += alpha z and r -= alpha w. beta_dev: 2k doubles on the device.
 void launch_gcr_project_update(const Cx<double> *W, Cx<double> *Wk, const Cx<double> *Z, Cx<double> *Zk, int k,
@@ -158,16 +162,20 @@ void launch_gcr_project_update(const Cx<double> *W, Cx<double> *Wk, const Cx<dou
 
 // batched outer GCR over nb systems (vector v at v * n; bases W[j][v][n], Z[j][v][n]):
 // y_v = mask bit v ? x_v : 0
-void launch_copy_masked(const Cx<double> *x, Cx<double> *y, long long n, int nb, unsigned int mask, cudaStream_t s);
+template <typename VT>
+void launch_copy_masked(const Cx<VT> *x, Cx<VT> *y, long long n, int nb, unsigned int mask, cudaStream_t s);
 // out[v] = |a_v|^2
-void launch_norm2_batch(const Cx<double> *a, long long n, int nb, double *out, const ReduceWs &ws, cudaStream_t s);
+template <typename VT>
+void launch_norm2_batch(const Cx<VT> *a, long long n, int nb, double *out, const ReduceWs &ws, cudaStream_t s);
 // out[v * 2 (k + 3) + 2 j] = <W_j,v, W_k,v> (j < k), then |W_k,v|^2, <W_k,v, r_v> and |r_v|^2
-void launch_gcr_dots_batch(const Cx<double> *W, const Cx<double> *r, int k, int nb, long long n, double *out,
+template <typename VT>
+void launch_gcr_dots_batch(const Cx<VT> *W, const Cx<VT> *r, int k, int nb, long long n, double *out,
                            const ReduceWs &ws, cudaStream_t s);
 // per vector, coef[4 v .. 4 v + 3] = (inv, alpha, mode): mode 0 skip, 2 project W_k / Z_k
 // with the betas in dots, 1 project, scale by inv, x += alpha Z_k, r -= alpha W_k
-void launch_gcr_update_batch(Cx<double> *W, Cx<double> *Z, int k, int nb, const double *dots, const double *coef,
-                             Cx<double> *x, Cx<double> *r, long long n, cudaStream_t s);
+template <typename VT>
+void launch_gcr_update_batch(Cx<VT> *W, Cx<VT> *Z, int k, int nb, const double *dots, const double *coef,
+                             Cx<VT> *x, Cx<VT> *r, long long n, cudaStream_t s);
 
 // ---- transfer between levels ----
 // coarse[b][k] = sum_i conj(V[b][k][i]) fine[site(b,s)][a]

@@ -2306,9 +2306,11 @@ int mg_coarse_apply_mrhs(mg_ctx *c, int level, int nrhs, const void *in, void *o
     if (c->e4) {
       if (level != 1) fail(MG_ERR_INVALID_ARG, "the 4d hierarchy has one coarse level (level 1)");
       if (nrhs < 1) fail(MG_ERR_INVALID_ARG, "nrhs must be >= 1");
-      engine4_coarse_apply_mrhs(*c->e4, nrhs, in, out, tensor_cores != 0);
+      engine4_coarse_apply_mrhs(*c->e4, nrhs, in, out, tensor_cores);
       return;
     }
+    if (tensor_cores < 0 || tensor_cores > 3) fail(MG_ERR_INVALID_ARG, "tensor_cores must be 0, 1, 2 or 3");
+    if (tensor_cores > 1) fail(MG_ERR_UNSUPPORTED, "the split-operand tensor-core apply is built for the 4d level");
     if (level < 1) fail(MG_ERR_INVALID_ARG, "the tensor-core apply is for coarse levels (level >= 1)");
     if (nrhs < 1) fail(MG_ERR_INVALID_ARG, "nrhs must be >= 1");
     check_fresh(*c);

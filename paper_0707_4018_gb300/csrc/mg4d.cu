@@ -41,7 +41,7 @@ struct Engine4 {
   DevBuf<int> info;  // set by the block inversion when a self block is singular
   // multi-vector coarse apply (made on first use after each Galerkin build): BF16 tensor-core
   // fragments and an FP32 copy of Y
-  DevBuf<uint4> Ypk4;
+  DevBuf<uint4> Ypk4, Ypk4lo;  // Ypk4lo: the low BF16 part, for the split-operator apply
   DevBuf<Cx<float>> Y32;
   bool mrhs_ready = false;
   // V-cycle work
@@ -51,6 +51,13 @@ struct Engine4 {
   DevBuf<Cx<float>> cb32, cx32;
   DevBuf<Cx<double>> cZ, cW, cr;  // coarse GCR
   DevBuf<Cx<float>> cZ32, cW32, cr32, cy32;  // coarse GCR on FP32 vectors (MG_FP32, loose coarsest_tol)
+  // the same GCR replayed by a graph (a WHILE node over iterations, one launch per restart
+  // cycle): its counters, the operator output and the instantiated graph with the buffers
+  // it was captured on
+  DevBuf<int> cctl;
+  DevBuf<Cx<float>> cwt32;
+  cudaGraphExec_t cloop = nullptr;
+  std::vector<const void *> cloop_key;
   DevBuf<Cx<double>> oZ, oW, orr, t64;  // outer GCR, setup scratch
   DevBuf<double> partials, scal;
   DevBuf<unsigned int> tickets;
@@ -75,6 +82,7 @@ struct Engine4 {
     DevBuf<Cx<double>> r64, Ar64, x64, b64;
     DevBuf<Cx<double>> cb, cx, cr, crin, cZ, cW;
     DevBuf<Cx<float>> cin32, cout32;
+    DevBuf<Cx<float>> cb32, cx32, cr32, crin32, cZ32, cW32;  // coarse GCR on FP32 vectors
     DevBuf<double> dots, coef, cdots, ccoef, part;
     DevBuf<unsigned int> tickets;
     ReduceWs ws{};
@@ -82,6 +90,7 @@ struct Engine4 {
   } bt;
   ~Engine4() {
     if (s) cudaStreamSynchronize(s);
+    if (cloop) cudaGraphExecDestroy(cloop);
     if (host) cudaFreeHost(host);
     if (bt.host) cudaFreeHost(bt.host);
     if (bt.chost) cudaFreeHost(bt.chost);
@@ -210,7 +219,103 @@ Gcr fgcr(Engine4 &e, ApplyF &&apply, PrecF &&prec, const Cx<double> *b, Cx<doubl
 // FP32 Krylov vectors and updates, and every reduction in FP64 (MG_FP32 with a coarsest
 // tolerance FP32 arithmetic can reach, >= 1e-5: the FP64 Gram-Schmidt over up to 64 basis
 // vectors, at 1/74 of the FP32 rate, was most of an iteration's time)
+// The coarse GCR of coarse_solve32 with its iterations on the device: one graph per engine, a
+// cycle-start kernel and a WHILE node whose body is one iteration (operator, reduction, step,
+// control), captured once and launched once per restart cycle. The estimate is checked after
+// every iteration (the host-driven loop reads it every kCheck iterations).
+constexpr int kCoarseLoopMaxRestart = 99;  // 2 (restart + 3) dots and the state fit the coarse slots
+
+static bool coarse_loop_enabled(const Engine4 &e) {
+  return e.cwt32.p != nullptr && e.p.coarsest_restart <= kCoarseLoopMaxRestart &&
+         std::getenv("MG_COARSE4_HOST_LOOP") == nullptr;
+}
+
+static cudaGraphExec_t coarse_loop_graph(Engine4 &e) {
+  double *dots = e.scal.p + kScalCoarse, *st = dots + 204;
+  const std::vector<const void *> key = {e.Yt32.p, e.cr32.p, e.cy32.p, e.cZ32.p, e.cW32.p, e.cwt32.p, e.cctl.p,
+                                         dots, e.wsc.partials, e.wsc.ticket,
+                                         reinterpret_cast<const void *>((long long)e.p.coarsest_restart),
+                                         reinterpret_cast<const void *>((long long)e.p.coarsest_max_iter)};
+  if (e.cloop != nullptr && key == e.cloop_key) return e.cloop;
+  if (e.cloop != nullptr) {
+    MG_CUDA(cudaGraphExecDestroy(e.cloop));
+    e.cloop = nullptr;
+  }
+  const long long n = e.nc;
+  const int restart = e.p.coarsest_restart, max_iter = e.p.coarsest_max_iter;
+  const double tol2_rel = e.p.coarsest_tol * e.p.coarsest_tol;
+  cudaGraph_t top = nullptr;
+  MG_CUDA(cudaGraphCreate(&top, 0));
+  try {
+    cudaGraphConditionalHandle h;
+    MG_CUDA(cudaGraphConditionalHandleCreate(&h, top, 0, cudaGraphCondAssignDefault));
+    MG_CUDA(cudaStreamBeginCaptureToGraph(e.s, top, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    launch_coarse4_cycle_start(e.cctl.p, st, max_iter, h, e.s);
+    MG_CUDA(cudaStreamEndCapture(e.s, &top));
+    size_t count = 1;
+    cudaGraphNode_t start;
+    MG_CUDA(cudaGraphGetNodes(top, &start, &count));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    MG_CUDA(cudaGraphAddNode(&node, top, &start, nullptr, 1, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    MG_CUDA(cudaStreamBeginCaptureToGraph(e.s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    launch_coarse4_apply<float, float>(e.Yt32.p, e.cr32.p, e.cwt32.p, e.cg, nullptr, 1.0, 0.0, e.s);
+    launch_gcr_dots_kdev<float>(e.cW32.p, e.cwt32.p, e.cr32.p, e.cctl.p + 1, restart - 1, n, dots, e.wsc, e.s);
+    launch_gcr_update_loop(e.cW32.p, e.cZ32.p, e.cwt32.p, e.cctl.p, dots, st, e.cy32.p, e.cr32.p, n, e.s);
+    launch_coarse4_control(e.cctl.p, st, tol2_rel, restart, max_iter, h, e.s);
+    MG_CUDA(cudaStreamEndCapture(e.s, &body));
+    MG_CUDA(cudaGraphInstantiate(&e.cloop, top, 0));
+  } catch (...) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t partial = nullptr;
+    if (cudaStreamIsCapturing(e.s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+      cudaStreamEndCapture(e.s, &partial);  // a graph owned by top (or top itself)
+    cudaGetLastError();
+    cudaGraphDestroy(top);
+    throw;
+  }
+  cudaGraphDestroy(top);
+  e.cloop_key = key;
+  return e.cloop;
+}
+
+static long long coarse_solve32_loop(Engine4 &e) {
+  const long long n = e.nc;
+  Cx<float> *x = e.cy32.p, *r = e.cr32.p;
+  const Cx<float> *b = e.cb32.p;
+  double *st = e.scal.p + kScalCoarse + 204, *h = e.host + kScalCoarse + 204;
+  cudaGraphExec_t g = coarse_loop_graph(e);
+  launch_zero<float>(x, n, e.s);
+  launch_copy<float>(b, r, n, e.s);
+  launch_norm2<float>(b, n, st + 1, e.wsc, e.s);
+  MG_CUDA(cudaMemsetAsync(e.cctl.p, 0, 2 * sizeof(int), e.s));
+  MG_CUDA(cudaMemsetAsync(st + 3, 0, sizeof(double), e.s));
+  const double tol2_rel = e.p.coarsest_tol * e.p.coarsest_tol;
+  long long iters = 0;
+  for (;;) {
+    MG_CUDA(cudaGraphLaunch(g, e.s));
+    launch_coarse4_apply<float, float>(e.Yt32.p, x, r, e.cg, b, -1.0, 1.0, e.s);  // true residual
+    launch_norm2<float>(r, n, st + 2, e.wsc, e.s);
+    MG_CUDA(cudaMemcpyAsync(h + 1, st + 1, 3 * sizeof(double), cudaMemcpyDeviceToHost, e.s));
+    MG_CUDA(cudaStreamSynchronize(e.s));
+    if (std::isnan(h[1]) || std::isnan(h[2])) fail(MG_ERR_NAN, "coarse GCR: NaN in a reduction");
+    const long long it = (long long)h[3];
+    e.apps[1] += it - iters + 1;
+    iters = it;
+    if (!(h[1] > 0.0) || h[2] <= tol2_rel * h[1] || iters >= e.p.coarsest_max_iter) break;
+  }
+  launch_block_apply4_32(e.Minv32.p, x, e.cx32.p, e.cg, e.s);  // x = M y
+  e.coarsest_iters += iters;
+  return iters;
+}
+
 long long coarse_solve32(Engine4 &e) {
+  if (coarse_loop_enabled(e)) return coarse_solve32_loop(e);
   const long long n = e.nc;
   Cx<float> *x = e.cy32.p, *r = e.cr32.p, *Z = e.cZ32.p, *W = e.cW32.p;
   const Cx<float> *b = e.cb32.p;
@@ -334,11 +439,12 @@ struct GcrB {
   double rel = 0.0;
 };
 
-template <typename ApplyF, typename PrecF>
-void fgcr_batch(Engine4 &e, int nb, ApplyF &&apply, PrecF &&prec, const Cx<double> *b, Cx<double> *x, long long n,
-                double tol, int restart, int max_iter, Cx<double> *Z, Cx<double> *W, Cx<double> *r,
-                Cx<double> *rin, double *dots, double *coef, double *h, const ReduceWs &ws,
-                std::vector<GcrB> &out) {
+// VT: the vectors' precision (FP64; FP32 for the inexact coarse solves of mixed-precision
+// cycles, with every reduction and coefficient in FP64)
+template <typename VT, typename ApplyF, typename PrecF>
+void fgcr_batch(Engine4 &e, int nb, ApplyF &&apply, PrecF &&prec, const Cx<VT> *b, Cx<VT> *x, long long n,
+                double tol, int restart, int max_iter, Cx<VT> *Z, Cx<VT> *W, Cx<VT> *r, Cx<VT> *rin, double *dots,
+                double *coef, double *h, const ReduceWs &ws, std::vector<GcrB> &out) {
   double *hcoef = h + (size_t)nb * 2 * (restart + 3);
   out.assign(nb, GcrB{});
   auto fetch = [&](int count) {
@@ -347,8 +453,8 @@ void fgcr_batch(Engine4 &e, int nb, ApplyF &&apply, PrecF &&prec, const Cx<doubl
     for (int i = 0; i < count; ++i)
       if (std::isnan(h[i])) fail(MG_ERR_NAN, "GCR (batched): NaN in a reduction");
   };
-  launch_zero<double>(x, n * nb, e.s);
-  launch_copy<double>(b, r, n * nb, e.s);
+  launch_zero<VT>(x, n * nb, e.s);
+  launch_copy<VT>(b, r, n * nb, e.s);
   launch_norm2_batch(b, n, nb, dots, ws, e.s);
   fetch(nb);
   std::vector<double> bn2(h, h + nb), rn2(bn2), nw0(nb), nw2(nb), wr(nb), wi(nb), rr(nb);
@@ -364,7 +470,7 @@ void fgcr_batch(Engine4 &e, int nb, ApplyF &&apply, PrecF &&prec, const Cx<doubl
     unsigned int act = all & ~done;
     int k = 0;
     for (; k < restart && iters < max_iter && act != 0u; ++k) {
-      Cx<double> *Zk = Z + (long long)k * nb * n, *Wk = W + (long long)k * nb * n;
+      Cx<VT> *Zk = Z + (long long)k * nb * n, *Wk = W + (long long)k * nb * n;
       launch_copy_masked(r, rin, n, nb, act, e.s);
       prec(rin, Zk);
       apply(Zk, Wk, nullptr);
@@ -670,6 +776,8 @@ Engine4 *engine4_create(const mg_geom *g, const void *U, double m, const mg_para
       e->cW32.alloc((size_t)p->coarsest_restart * e->nc);
       e->cr32.alloc(e->nc);
       e->cy32.alloc(e->nc);
+      e->cwt32.alloc(e->nc);
+      e->cctl.alloc(2);
     }
   }
   e->cb.alloc(e->nc);
@@ -848,6 +956,14 @@ void alloc_batch(Engine4 &e) {
   b.cW.alloc((size_t)rc * nb * e.nc);
   b.cin32.alloc((size_t)nb * e.nc);
   b.cout32.alloc((size_t)nb * e.nc);
+  if (e.f32 && e.p.coarsest_tol >= 1e-5 && e.N == 48) {
+    b.cb32.alloc((size_t)nb * e.nc);
+    b.cx32.alloc((size_t)nb * e.nc);
+    b.cr32.alloc((size_t)nb * e.nc);
+    b.crin32.alloc((size_t)nb * e.nc);
+    b.cZ32.alloc((size_t)rc * nb * e.nc);
+    b.cW32.alloc((size_t)rc * nb * e.nc);
+  }
   const int rows = std::max(ro, rc) + 3;
   b.dots.alloc((size_t)nb * 2 * (ro + 3));
   b.coef.alloc((size_t)nb * 4);
@@ -869,23 +985,44 @@ void alloc_batch(Engine4 &e) {
 // batched coarse solve of nb vectors: cx_v = A_c^{-1} cb_v by lockstep GCR to coarsest_tol,
 // right-preconditioned by block Jacobi; the operator applied to all vectors at once on
 // tensor cores (N = 48; BF16 operands, FP32 sums) or, otherwise, in FP64
+// operand precision of the batched tensor-core coarse apply (launch_coarse4_apply_tc's split):
+// MG_COARSE4_TC_SPLIT = 0, 1 or 2, else 2
+static int tc_split() {
+  const char *v = std::getenv("MG_COARSE4_TC_SPLIT");
+  if (v == nullptr) return 2;
+  const int s = std::atoi(v);
+  return s < 0 || s > 2 ? 2 : s;
+}
+
+// the multi-vector coarse operands after a Galerkin build: BF16 fragments (hi, and lo when
+// a split-operator apply wants them) and an FP32 copy of Y
+static void ensure_mrhs(Engine4 &e, bool lo) {
+  if (e.Ypk4.p == nullptr) {
+    e.Ypk4.alloc((size_t)e.cg.nsites * 9 * 2 * 9 * 32);
+    e.Y32.alloc(e.Y64.n);
+    pool_ready();
+  }
+  if (lo && e.Ypk4lo.p == nullptr) {
+    e.Ypk4lo.alloc((size_t)e.cg.nsites * 9 * 2 * 9 * 32);
+    pool_ready();
+    e.mrhs_ready = false;
+  }
+  if (e.mrhs_ready) return;
+  launch_pack_coarse4_bf16(e.Y64.p, e.Ypk4.p, e.cg.nsites, e.s);
+  if (e.Ypk4lo.p != nullptr) launch_pack_coarse4_bf16(e.Y64.p, e.Ypk4lo.p, e.cg.nsites, e.s, true);
+  launch_convert<float, double>(e.Y64.p, e.Y32.p, e.Y64.n, e.s);
+  e.mrhs_ready = true;
+}
+
 void coarse_solve_batch(Engine4 &e, int nb) {
   auto &b = e.bt;
   const bool tc = e.N == 48;
-  if (tc && !e.mrhs_ready) {
-    if (e.Ypk4.p == nullptr) {
-      e.Ypk4.alloc((size_t)e.cg.nsites * 9 * 2 * 9 * 32);
-      e.Y32.alloc(e.Y64.n);
-      pool_ready();
-    }
-    launch_pack_coarse4_bf16(e.Y64.p, e.Ypk4.p, e.cg.nsites, e.s);
-    launch_convert<float, double>(e.Y64.p, e.Y32.p, e.Y64.n, e.s);
-    e.mrhs_ready = true;
-  }
+  const int split = tc_split();
+  if (tc) ensure_mrhs(e, split == 2);
   auto apply = [&](const Cx<double> *in, Cx<double> *out, const Cx<double> *rhs) {
     if (tc) {
       launch_convert<float, double>(in, b.cin32.p, (long long)nb * e.nc, e.s);
-      launch_coarse4_apply_tc(e.Ypk4.p, b.cin32.p, b.cout32.p, e.cg.nb, nb, e.s);
+      launch_coarse4_apply_tc(e.Ypk4.p, b.cin32.p, b.cout32.p, e.cg.nb, nb, e.s, split, e.Ypk4lo.p);
       launch_convert<double, float>(b.cout32.p, out, (long long)nb * e.nc, e.s);
       if (rhs != nullptr) launch_xmy<double>(rhs, out, (long long)nb * e.nc, e.s);  // out = rhs - A in
     } else {
@@ -901,8 +1038,25 @@ void coarse_solve_batch(Engine4 &e, int nb) {
       launch_block_apply4<double>(e.Minv64.p, r, z, e.cg, e.s, nb);
   };
   std::vector<GcrB> out;
-  fgcr_batch(e, nb, apply, prec, b.cb.p, b.cx.p, e.nc, e.p.coarsest_tol, e.p.coarsest_restart,
-             e.p.coarsest_max_iter, b.cZ.p, b.cW.p, b.cr.p, b.crin.p, b.cdots.p, b.ccoef.p, b.chost, b.ws, out);
+  if (tc && b.cZ32.p != nullptr && std::getenv("MG_COARSE4_FP64_VECTORS") == nullptr) {
+    // FP32 Krylov vectors (FP64 reductions and coefficients): the FP64 Gram-Schmidt of 12 vectors
+    // over up to 64 basis vectors was most of a batched coarse iteration
+    auto apply32 = [&](const Cx<float> *in, Cx<float> *o, const Cx<float> *rhs) {
+      launch_coarse4_apply_tc(e.Ypk4.p, in, o, e.cg.nb, nb, e.s, split, e.Ypk4lo.p);
+      if (rhs != nullptr) launch_xmy<float>(rhs, o, (long long)nb * e.nc, e.s);  // o = rhs - A in
+      e.apps[1] += nb;
+    };
+    auto prec32 = [&](const Cx<float> *r, Cx<float> *z) { launch_block_apply4_32(e.Minv32.p, r, z, e.cg, e.s, nb); };
+    launch_convert<float, double>(b.cb.p, b.cb32.p, (long long)nb * e.nc, e.s);
+    fgcr_batch(e, nb, apply32, prec32, static_cast<const Cx<float> *>(b.cb32.p), b.cx32.p, e.nc, e.p.coarsest_tol,
+               e.p.coarsest_restart, e.p.coarsest_max_iter, b.cZ32.p, b.cW32.p, b.cr32.p, b.crin32.p, b.cdots.p,
+               b.ccoef.p, b.chost, b.ws, out);
+    launch_convert<double, float>(b.cx32.p, b.cx.p, (long long)nb * e.nc, e.s);
+  } else {
+    fgcr_batch(e, nb, apply, prec, static_cast<const Cx<double> *>(b.cb.p), b.cx.p, e.nc, e.p.coarsest_tol,
+               e.p.coarsest_restart, e.p.coarsest_max_iter, b.cZ.p, b.cW.p, b.cr.p, b.crin.p, b.cdots.p, b.ccoef.p,
+               b.chost, b.ws, out);
+  }
   int mx = 0;
   for (const auto &o : out) mx = std::max(mx, o.iters);
   e.coarsest_iters += mx;
@@ -986,22 +1140,14 @@ std::vector<Solve4> engine4_solve_batch(Engine4 &e, int nrhs, const void *chi, v
   return out;
 }
 
-void engine4_coarse_apply_mrhs(Engine4 &e, int nrhs, const void *in, void *out, bool tensor_cores) {
+void engine4_coarse_apply_mrhs(Engine4 &e, int nrhs, const void *in, void *out, int tensor_cores) {
   if (e.N != 48) fail(MG_ERR_UNSUPPORTED, "the 4d multi-vector coarse apply is built for N = 48 (Nv = 24)");
-  if (!e.mrhs_ready) {
-    if (e.Ypk4.p == nullptr) {
-      e.Ypk4.alloc((size_t)e.cg.nsites * 9 * 2 * 9 * 32);
-      e.Y32.alloc(e.Y64.n);
-      pool_ready();
-    }
-    launch_pack_coarse4_bf16(e.Y64.p, e.Ypk4.p, e.cg.nsites, e.s);
-    launch_convert<float, double>(e.Y64.p, e.Y32.p, e.Y64.n, e.s);
-    e.mrhs_ready = true;
-  }
+  if (tensor_cores < 0 || tensor_cores > 3) fail(MG_ERR_INVALID_ARG, "tensor_cores must be 0, 1, 2 or 3");
+  ensure_mrhs(e, tensor_cores == 3);
   const Cx<float> *x = static_cast<const Cx<float> *>(in);
   Cx<float> *y = static_cast<Cx<float> *>(out);
-  if (tensor_cores)
-    launch_coarse4_apply_tc(e.Ypk4.p, x, y, e.cg.nb, nrhs, e.s);
+  if (tensor_cores != 0)
+    launch_coarse4_apply_tc(e.Ypk4.p, x, y, e.cg.nb, nrhs, e.s, tensor_cores - 1, e.Ypk4lo.p);
   else
     launch_coarse4_apply<float, float>(e.Y32.p, x, y, e.cg, nullptr, 1.0, 0.0, e.s, nrhs);
   MG_CUDA(cudaStreamSynchronize(e.s));

@@ -65,8 +65,18 @@ void launch_gcr_update_dev(const Cx<double> *W, Cx<double> *Wk, const Cx<double>
 void launch_gcr_update_dev(const Cx<float> *W, Cx<float> *Wk, const Cx<float> *Z, Cx<float> *Zk, int k,
                            const double *dots, double *state, Cx<float> *x, Cx<float> *r, long long n,
                            cudaStream_t s);
+// graph-replayed coarse GCR on FP32 vectors: the step with k = ctl[1], w = wt and z = r (W_k, Z_k
+// written at W + k n, Z + k n); the kernel that starts a restart cycle (k = 0) and sets the WHILE
+// condition; the kernel that ends an iteration and decides whether the loop goes on (state:
+// st[0] residual estimate, st[1] |b|^2, st[3] iterations)
+void launch_gcr_update_loop(Cx<float> *W, Cx<float> *Z, const Cx<float> *wt, const int *ctl, const double *dots,
+                            double *state, Cx<float> *x, Cx<float> *r, long long n, cudaStream_t s);
+void launch_coarse4_cycle_start(int *ctl, const double *st, int max_iter, cudaGraphConditionalHandle h,
+                                cudaStream_t s);
+void launch_coarse4_control(int *ctl, double *st, double tol2_rel, int restart, int max_iter,
+                            cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_block_apply4_32(const Cx<float> *Minv, const Cx<float> *r, Cx<float> *z, const Coarse4 &g,
-                            cudaStream_t s);
+                            cudaStream_t s, int nvec = 1);
 // Yt[j][dir] = Y[j][dir] Minv[src(j, dir)]: the block-Jacobi right-preconditioned stencil A M
 void launch_precondition4(const Cx<double> *Y, const Cx<double> *Minv, Cx<double> *Yt, const Coarse4 &g,
                           cudaStream_t s);
@@ -80,11 +90,12 @@ template <typename R>
 void launch_mr_update_batch(const double *sc, double omega, Cx<R> *x, Cx<R> *r, const Cx<R> *Ar, long long n,
                             int nvec, cudaStream_t s);
 // tensor-core coarse apply (coarse_tc.cu), N = 48: BF16 A-fragments of Re Y and Im Y
-// (nsites x 9 x 2 x 9 x 32 uint4) from the FP64 stencil, then out_n = A_c in_n for nvec
-// complex64 vectors [n][site][48]
-void launch_pack_coarse4_bf16(const Cx<double> *Y, uint4 *Ypk, long long nsites, cudaStream_t s);
+// (nsites x 9 x 2 x 9 x 32 uint4) from the FP64 stencil (lo: of what the BF16 rounding
+// leaves), then out_n = A_c in_n for nvec complex64 vectors [n][site][48]; split 0: BF16
+// operands, 1: vectors as BF16 hi + lo, 2: the operator too (needs Ypklo)
+void launch_pack_coarse4_bf16(const Cx<double> *Y, uint4 *Ypk, long long nsites, cudaStream_t s, bool lo = false);
 void launch_coarse4_apply_tc(const uint4 *Ypk, const Cx<float> *in, Cx<float> *out, const int nb[4], int nvec,
-                             cudaStream_t s);
+                             cudaStream_t s, int split = 0, const uint4 *Ypklo = nullptr);
 // exports: Y in [j][dir][row][col]; P as N fine vectors [c][x][12]
 void launch_coarse4_to_canonical(const Cx<double> *Yi, Cx<double> *Yc, const Coarse4 &g, cudaStream_t s);
 void launch_prolongator4_to_canonical(const Cx<double> *V, Cx<double> *out, const Block4 &g, cudaStream_t s);
@@ -128,6 +139,6 @@ long long engine4_coarsest_solve(Engine4 &e, const void *b, void *x, float *ms);
 std::vector<Solve4> engine4_solve_batch(Engine4 &e, int nrhs, const void *chi, void *psi, double tol);
 // out_n = A_c in_n for nrhs complex64 coarse vectors: tensor cores (BF16 operands, FP32 sums)
 // or, with tensor_cores = 0, CUDA cores in FP32 (the comparison path)
-void engine4_coarse_apply_mrhs(Engine4 &e, int nrhs, const void *in, void *out, bool tensor_cores);
+void engine4_coarse_apply_mrhs(Engine4 &e, int nrhs, const void *in, void *out, int tensor_cores);
 
 }  // namespace mg

@@ -698,8 +698,9 @@ void launch_block_apply4(const Cx<R> *Minv, const Cx<double> *r, Cx<double> *z, 
 }
 
 void launch_block_apply4_32(const Cx<float> *Minv, const Cx<float> *r, Cx<float> *z, const Coarse4 &g,
-                            cudaStream_t s) {
-  block_apply4_kernel<float, float><<<(unsigned int)g.nsites, 64, 0, s>>>(Minv, r, z, g.N, g.nsites * g.N);
+                            cudaStream_t s, int nvec) {
+  block_apply4_kernel<float, float><<<dim3((unsigned int)g.nsites, nvec), 64, 0, s>>>(Minv, r, z, g.N,
+                                                                                     g.nsites * g.N);
   MG_LAUNCHED();
 }
 
@@ -708,12 +709,18 @@ void launch_block_apply4_32(const Cx<float> *Minv, const Cx<float> *r, Cx<float>
 // SMs without work while every thread walked the whole basis)
 constexpr int kSplit = 4;
 
-template <typename VT>
-__global__ void gcr_update_split_kernel(const Cx<VT> *__restrict__ W, Cx<VT> *__restrict__ Wk,
-                                        const Cx<VT> *__restrict__ Z, Cx<VT> *__restrict__ Zk, int k,
+//
+// LOOP: the step of a graph-replayed loop: k = ctl[1], W_k = Wb + k n and Z_k = Zb + k n, the new
+// direction's inputs are w = wt and z = r (the unpreconditioned residual itself, so no copy)
+template <typename VT, bool LOOP>
+__global__ void gcr_update_split_kernel(const Cx<VT> *__restrict__ W, Cx<VT> *__restrict__ Wk_,
+                                        const Cx<VT> *__restrict__ Z, Cx<VT> *__restrict__ Zk_, int k_host,
+                                        const int *__restrict__ ctl, const Cx<VT> *__restrict__ wt,
                                         const double *__restrict__ dots, double *__restrict__ state,
                                         Cx<VT> *__restrict__ x, Cx<VT> *__restrict__ r, long long n) {
   __shared__ double coef[3];
+  const int k = LOOP ? ctl[1] : k_host;
+  Cx<VT> *Wk = LOOP ? Wk_ + (long long)k * n : Wk_, *Zk = LOOP ? Zk_ + (long long)k * n : Zk_;
   if (threadIdx.x == 0) {
     const double nw0 = dots[2 * k];
     double nw2 = nw0;
@@ -753,11 +760,11 @@ __global__ void gcr_update_split_kernel(const Cx<VT> *__restrict__ W, Cx<VT> *__
       pz.im += __shfl_xor_sync(0xffffffffu, pz.im, o);
     }
     if (valid && sub == 0) {
-      const Cx<VT> w = inv * (Wk[i] + pw), z = inv * (Zk[i] + pz);
+      Cx<VT> ri = r[i];
+      const Cx<VT> w = inv * ((LOOP ? wt[i] : Wk[i]) + pw), z = inv * ((LOOP ? ri : Zk[i]) + pz);
       Wk[i] = w;
       Zk[i] = z;
       cmac(x[i], alpha, z);
-      Cx<VT> ri = r[i];
       cmac(ri, malpha, w);
       r[i] = ri;
     }
@@ -771,8 +778,8 @@ static void gcr_update_dev_any(const Cx<VT> *W, Cx<VT> *Wk, const Cx<VT> *Z, Cx<
     // kSplit threads per element in blocks of 256
     long long b = (n * kSplit + 255) / 256;
     if (b > 152LL * 16) b = 152LL * 16;
-    gcr_update_split_kernel<VT><<<(unsigned int)(b < 1 ? 1 : b), 256, 0, s>>>(W, Wk, Z, Zk, k, dots, state, x, r,
-                                                                              n);
+    gcr_update_split_kernel<VT, false><<<(unsigned int)(b < 1 ? 1 : b), 256, 0, s>>>(W, Wk, Z, Zk, k, nullptr, nullptr,
+                                                                                     dots, state, x, r, n);
     MG_LAUNCHED();
     return;
   }
@@ -792,6 +799,48 @@ void launch_gcr_update_dev(const Cx<float> *W, Cx<float> *Wk, const Cx<float> *Z
                            const double *dots, double *state, Cx<float> *x, Cx<float> *r, long long n,
                            cudaStream_t s) {
   gcr_update_dev_any<float>(W, Wk, Z, Zk, k, dots, state, x, r, n, s);
+}
+
+void launch_gcr_update_loop(Cx<float> *W, Cx<float> *Z, const Cx<float> *wt, const int *ctl, const double *dots,
+                            double *state, Cx<float> *x, Cx<float> *r, long long n, cudaStream_t s) {
+  long long b = (n * kSplit + 255) / 256;
+  if (b > 152LL * 16) b = 152LL * 16;
+  gcr_update_split_kernel<float, true><<<(unsigned int)(b < 1 ? 1 : b), 256, 0, s>>>(W, W, Z, Z, 0, ctl, wt, dots,
+                                                                                    state, x, r, n);
+  MG_LAUNCHED();
+}
+
+// Control of the graph-replayed coarse GCR (ctl[0] iterations so far, ctl[1] the basis index
+// k; st[0] the residual estimate, st[1] |b|^2, st[3] the iteration count as a double for the
+// host's one read per restart cycle). The cycle-start kernel runs before the WHILE node and
+// sets its condition; the control kernel ends every iteration.
+__global__ void coarse4_cycle_start_kernel(int *ctl, const double *st, int max_iter,
+                                           cudaGraphConditionalHandle handle) {
+  ctl[1] = 0;
+  cudaGraphSetConditional(handle, (st[1] > 0.0 && ctl[0] < max_iter) ? 1u : 0u);
+}
+
+__global__ void coarse4_control_kernel(int *ctl, double *st, double tol2_rel, int restart, int max_iter,
+                                       cudaGraphConditionalHandle handle) {
+  const int it = ctl[0] + 1, k = ctl[1] + 1;
+  ctl[0] = it;
+  ctl[1] = k;
+  st[3] = (double)it;
+  // a NaN estimate ends the loop; the host finds it in the true residual
+  const bool go = st[0] > tol2_rel * st[1] && k < restart && it < max_iter;
+  cudaGraphSetConditional(handle, go ? 1u : 0u);
+}
+
+void launch_coarse4_cycle_start(int *ctl, const double *st, int max_iter, cudaGraphConditionalHandle h,
+                                cudaStream_t s) {
+  coarse4_cycle_start_kernel<<<1, 1, 0, s>>>(ctl, st, max_iter, h);
+  MG_LAUNCHED();
+}
+
+void launch_coarse4_control(int *ctl, double *st, double tol2_rel, int restart, int max_iter,
+                            cudaGraphConditionalHandle h, cudaStream_t s) {
+  coarse4_control_kernel<<<1, 1, 0, s>>>(ctl, st, tol2_rel, restart, max_iter, h);
+  MG_LAUNCHED();
 }
 
 void launch_precondition4(const Cx<double> *Y, const Cx<double> *Minv, Cx<double> *Yt, const Coarse4 &g,

@@ -130,4 +130,23 @@ def test_tensor_core_apply_4d_matches_bf16_reference(nrhs):
     assert worst_emul <= 1e-5, worst_emul       # only the FP32 summation of 432 products differs
     assert worst_exact <= 1e-2, worst_exact     # the BF16 rounding of both operands
     assert worst_cc <= 1e-5, worst_cc           # the FP32 CUDA-core path
+    # split operands: vectors as BF16 hi + lo (the operator's rounding is left), then the operator
+    # too (hi hi + hi lo + lo hi: the dropped lo lo term and the FP32 sums are left)
+    for mode, bound_emul, bound_exact in ((2, 1e-5, 1e-2), (3, None, 2e-5)):
+        out_s = torch.empty_like(out_tc)
+        ctx.coarse_apply_mrhs(1, to_dev(x), out_s, mode)
+        got_s = to_host(out_s).astype(np.complex128)
+        w_emul = w_exact = 0.0
+        for k in range(nrhs):
+            bound = op_abs.apply(np.abs(x[k]).astype(np.float64)).real
+            exact = op_exact.apply(x[k].astype(np.complex128))
+            w_exact = max(w_exact, float(np.max(np.abs(got_s[k] - exact) / bound)))
+            if bound_emul is not None:  # the exact product with the BF16 operator
+                w_emul = max(w_emul, float(np.max(np.abs(got_s[k] - op_b.apply(x[k].astype(np.complex128))) / bound)))
+        assert w_exact <= bound_exact, (mode, w_exact)
+        if bound_emul is not None:
+            assert w_emul <= bound_emul, (mode, w_emul)
+    assert w_exact < worst_exact / 50  # the split operator gains more than 5 bits over BF16
+    with pytest.raises(mg.MGError):
+        ctx.coarse_apply_mrhs(1, to_dev(x), out_tc, 4)
     ctx.close()

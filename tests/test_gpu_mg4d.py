@@ -239,11 +239,15 @@ def test_batched_solve_matches_dense_lu(precision):
     ctx.close()
 
 
-def test_batched_solve_tensor_core_coarse_apply():
-    # N = 48 (Nv = 24): the batched coarse solve applies the operator on tensor cores; every
-    # vector reaches the FP64 true residual recomputed by the oracle
+@pytest.mark.parametrize("fp64_vectors", [False, True])
+def test_batched_solve_tensor_core_coarse_apply(fp64_vectors, monkeypatch):
+    # N = 48 (Nv = 24): the batched coarse solve applies the operator on tensor cores, its lockstep GCR
+    # on FP32 vectors (FP64 sums) or, with MG_COARSE4_FP64_VECTORS, FP64 ones; every vector reaches
+    # the FP64 true residual recomputed by the oracle
     import torch
     import paper_0707_4018_gb300 as mg
+    if fp64_vectors:
+        monkeypatch.setenv("MG_COARSE4_FP64_VECTORS", "1")
     dims = (8, 8, 8, 8)
     lat = Lattice(dims)
     U = inputs.su3_links(dims, seed=27)
@@ -264,23 +268,30 @@ def test_batched_solve_tensor_core_coarse_apply():
     ctx.close()
 
 
-@pytest.mark.parametrize("fp64_vectors,dims,block,nv", [(False, (8, 8, 8, 8), (4, 4, 4, 4), 6),
-                                                        (True, (8, 8, 8, 8), (4, 4, 4, 4), 6),
-                                                        (False, (6, 6, 6, 4), (2, 2, 2, 2), 3)])
-def test_coarse_gcr_fp32_vectors_meets_tolerance(fp64_vectors, dims, block, nv, monkeypatch):
+@pytest.mark.parametrize("mode,dims,block,nv,restart", [("device_loop", (8, 8, 8, 8), (4, 4, 4, 4), 6, 32),
+                                                         ("host_loop", (8, 8, 8, 8), (4, 4, 4, 4), 6, 32),
+                                                         ("fp64_vectors", (8, 8, 8, 8), (4, 4, 4, 4), 6, 32),
+                                                         ("device_loop", (6, 6, 6, 4), (2, 2, 2, 2), 3, 32),
+                                                         ("device_loop", (8, 8, 8, 8), (4, 4, 4, 4), 6, 5),
+                                                         ("host_loop", (8, 8, 8, 8), (4, 4, 4, 4), 6, 5)])
+def test_coarse_gcr_fp32_vectors_meets_tolerance(mode, dims, block, nv, restart, monkeypatch):
     # mixed precision with a loose coarse tolerance: the coarse GCR runs on FP32 vectors (FP64
-    # sums) unless MG_COARSE4_FP64_VECTORS keeps them in FP64; either way the coarse solution meets
-    # the tolerance against the oracle's FP64 coarse operator ((6, 6, 6, 4): 54 coarse sites x 6 dofs,
-    # a vector length that leaves part of a warp past the end in the split update)
+    # sums), its iterations replayed on the device by a graph (or host-driven with
+    # MG_COARSE4_HOST_LOOP), unless MG_COARSE4_FP64_VECTORS keeps the vectors in FP64; each way the
+    # coarse solution meets the tolerance against the oracle's FP64 coarse operator ((6, 6, 6, 4):
+    # 54 coarse sites x 6 dofs, a vector length that leaves part of a warp past the end in the split
+    # update; restart 5: several restart cycles, each ended by a true residual)
     import torch
     import paper_0707_4018_gb300 as mg
     from oracle import solvers as osolvers
-    if fp64_vectors:
+    if mode == "fp64_vectors":
         monkeypatch.setenv("MG_COARSE4_FP64_VECTORS", "1")
+    if mode == "host_loop":
+        monkeypatch.setenv("MG_COARSE4_HOST_LOOP", "1")
     U = inputs.su3_links(dims, seed=29)
     m = 0.02
     ctx = mg.Context.setup(to_dev(U), m, dims, _params(block, nv, 1, n_pass=1, nu_setup=20, coarsest_tol=1e-3,
-                                                       coarsest_restart=32, coarsest_max_iter=2000))
+                                                       coarsest_restart=restart, coarsest_max_iter=2000))
     vecs = to_host(ctx.null_vectors(0))
     hier = _oracle_hier(U, m, dims, block, nv)
     hier.build_level(0, list(vecs))
@@ -292,4 +303,27 @@ def test_coarse_gcr_fp32_vectors_meets_tolerance(fp64_vectors, dims, block, nv, 
         it, _ = ctx.coarsest_solve(to_dev(b), x)
         res = np.linalg.norm(b.reshape(-1) - A @ to_host(x).reshape(-1)) / np.linalg.norm(b)
         assert 0 < it < 2000 and res <= 1.2e-3, (it, res)
+    ctx.close()
+
+
+@pytest.mark.parametrize("host_loop", [False, True])
+def test_coarse_gcr_fp32_iteration_limit_and_zero_rhs(host_loop, monkeypatch):
+    # the coarse GCR stops at coarsest_max_iter across restart cycles (4 + 2 iterations with
+    # restart 4 and limit 6), and a zero right-hand side takes no iteration and gives x = 0
+    import torch
+    import paper_0707_4018_gb300 as mg
+    if host_loop:
+        monkeypatch.setenv("MG_COARSE4_HOST_LOOP", "1")
+    dims, block, nv = (8, 8, 8, 8), (4, 4, 4, 4), 6
+    U = inputs.su3_links(dims, seed=29)
+    ctx = mg.Context.setup(to_dev(U), 0.02, dims, _params(block, nv, 1, n_pass=1, nu_setup=20, coarsest_tol=1e-5,
+                                                          coarsest_restart=4, coarsest_max_iter=6))
+    n, k = ctx.level_size(1)
+    b = inputs.gaussian_spinor(n, k, 61, 0)
+    x = torch.empty((n, k), dtype=torch.complex128, device="cuda")
+    it, _ = ctx.coarsest_solve(to_dev(b), x)
+    assert it == 6
+    assert np.isfinite(to_host(x)).all() and np.abs(to_host(x)).max() > 0
+    it, _ = ctx.coarsest_solve(to_dev(np.zeros_like(b)), x)
+    assert it == 0 and np.abs(to_host(x)).max() == 0
     ctx.close()
