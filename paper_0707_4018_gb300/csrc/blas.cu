@@ -274,6 +274,56 @@ __global__ void gcr_update_batch_kernel(Cx<VT> *__restrict__ W, Cx<VT> *__restri
   }
 }
 
+// the same step with kLanes consecutive lanes per element, each summing the basis vectors
+// j = lane, lane + kLanes, ... (short coarse vectors: one thread per element left most SMs idle
+// while each thread walked the whole basis); the loop is steered by the warp's first element
+// so that every lane takes part in every shuffle
+constexpr int kLanes = 4;
+
+template <typename VT>
+__global__ void gcr_update_batch_split_kernel(Cx<VT> *__restrict__ W, Cx<VT> *__restrict__ Z, int k, int nb,
+                                              const double *__restrict__ dots, const double *__restrict__ coef,
+                                              Cx<VT> *__restrict__ x, Cx<VT> *__restrict__ r, long long n) {
+  const int v = blockIdx.y;
+  const int mode = (int)coef[4 * v + 3];
+  if (mode == 0) return;
+  const double *beta = dots + (long long)v * 2 * (k + 3);
+  const VT inv = (VT)(mode == 1 ? coef[4 * v] : 1.0);
+  const Cx<VT> alpha = mk((VT)coef[4 * v + 1], (VT)coef[4 * v + 2]);
+  Cx<VT> *Wk = W + ((long long)k * nb + v) * n, *Zk = Z + ((long long)k * nb + v) * n;
+  const int sub = threadIdx.x % kLanes, lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * (blockDim.x / kLanes);
+  long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / kLanes;
+  for (long long i0 = i - lane / kLanes; i0 < n; i0 += stride, i += stride) {
+    const bool valid = i < n;
+    Cx<VT> pw = mk((VT)0, (VT)0), pz = mk((VT)0, (VT)0);
+    for (int j = sub; valid && j < k; j += kLanes) {
+      const Cx<VT> bj = mk((VT)-beta[2 * j], (VT)-beta[2 * j + 1]);
+      const long long o = ((long long)j * nb + v) * n + i;
+      cmac(pw, bj, W[o]);
+      cmac(pz, bj, Z[o]);
+    }
+#pragma unroll
+    for (int o = kLanes / 2; o > 0; o >>= 1) {
+      pw.re += __shfl_xor_sync(0xffffffffu, pw.re, o);
+      pw.im += __shfl_xor_sync(0xffffffffu, pw.im, o);
+      pz.re += __shfl_xor_sync(0xffffffffu, pz.re, o);
+      pz.im += __shfl_xor_sync(0xffffffffu, pz.im, o);
+    }
+    if (valid && sub == 0) {
+      const Cx<VT> w = inv * (Wk[i] + pw), z = inv * (Zk[i] + pz);
+      Wk[i] = w;
+      Zk[i] = z;
+      if (mode == 1) {
+        cmac(x[(long long)v * n + i], alpha, z);
+        Cx<VT> ri = r[(long long)v * n + i];
+        cmac(ri, mk(-alpha.re, -alpha.im), w);
+        r[(long long)v * n + i] = ri;
+      }
+    }
+  }
+}
+
 static unsigned int stream_grid(long long n);
 
 template <typename VT>
@@ -309,6 +359,12 @@ void launch_gcr_dots_batch(const Cx<VT> *W, const Cx<VT> *r, int k, int nb, long
 template <typename VT>
 void launch_gcr_update_batch(Cx<VT> *W, Cx<VT> *Z, int k, int nb, const double *dots, const double *coef, Cx<VT> *x,
                              Cx<VT> *r, long long n, cudaStream_t s) {
+  if (n < (1LL << 18)) {  // short (coarse) vectors: kLanes lanes per element
+    gcr_update_batch_split_kernel<VT><<<dim3(stream_grid(n * kLanes), nb), 256, 0, s>>>(W, Z, k, nb, dots, coef, x,
+                                                                                        r, n);
+    MG_LAUNCHED();
+    return;
+  }
   gcr_update_batch_kernel<VT><<<dim3(stream_grid(n), nb), 256, 0, s>>>(W, Z, k, nb, dots, coef, x, r, n);
   MG_LAUNCHED();
 }
@@ -523,34 +579,37 @@ void launch_gcr_control(int *ctl, double *st, int restart, int max_iter, cudaGra
 // ---------------------------------------------------------------------------
 namespace mg {
 
-__global__ void copy_active_kernel(const Cx<double> *__restrict__ x, Cx<double> *__restrict__ y, long long n,
+// (VT: the vectors' type; FP32 vectors keep each thread's products in FP32, the trees in FP64)
+template <typename VT>
+__global__ void copy_active_kernel(const Cx<VT> *__restrict__ x, Cx<VT> *__restrict__ y, long long n,
                                    const int *__restrict__ act) {
   const long long off = blockIdx.y * n;
   const bool on = act[blockIdx.y] != 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[off + i] = on ? x[off + i] : mk(0.0, 0.0);
+    y[off + i] = on ? x[off + i] : mk((VT)0, (VT)0);
 }
 
-// vector v = blockIdx.z, row = blockIdx.y < restart + 3 (rows above k + 2 empty), k = ctl[1]
+// vector v = blockIdx.z, row = blockIdx.y < restart + 3, k = ctl[1]; the rows above k + 2
+// return at once (all blocks of such a row alike, so their tickets stay untouched)
+template <typename VT>
 __global__ void __launch_bounds__(kReduceThreads) gcr_dots_batch_devk_kernel(
-    const Cx<double> *__restrict__ W, const Cx<double> *__restrict__ w, const Cx<double> *__restrict__ r,
+    const Cx<VT> *__restrict__ W, const Cx<VT> *__restrict__ w, const Cx<VT> *__restrict__ r,
     const int *__restrict__ ctl, int nb, int restart, long long n, double *partials, double *out,
     unsigned int *ticket) {
   __shared__ double sh[32 * 2];
   const int row = blockIdx.y, v = blockIdx.z, rows = restart + 3, k = ctl[1];
-  double acc[2] = {0.0, 0.0};
-  if (row <= k + 2) {
-    const Cx<double> *wv = w + (long long)v * n;
-    const Cx<double> *rv = r + (long long)v * n;
-    const Cx<double> *a = row < k ? W + ((long long)row * nb + v) * n : (row == k + 2 ? rv : wv);
-    const Cx<double> *b = row > k ? rv : wv;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-      const Cx<double> x = a[i], y = b[i];
-      acc[0] += x.re * y.re + x.im * y.im;
-      acc[1] += x.re * y.im - x.im * y.re;
-    }
+  if (row > k + 2) return;
+  const Cx<VT> *wv = w + (long long)v * n;
+  const Cx<VT> *rv = r + (long long)v * n;
+  const Cx<VT> *a = row < k ? W + ((long long)row * nb + v) * n : (row == k + 2 ? rv : wv);
+  const Cx<VT> *b = row > k ? rv : wv;
+  VT t0 = (VT)0, t1 = (VT)0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const Cx<VT> x = a[i], y = b[i];
+    t0 += x.re * y.re + x.im * y.im;
+    t1 += x.re * y.im - x.im * y.re;
   }
+  double acc[2] = {(double)t0, (double)t1};
   const long long slot = (long long)v * rows + row;
   grid_finish<2>(acc, partials + slot * 2 * gridDim.x, out + 2 * slot, ticket + slot, sh);
 }
@@ -587,22 +646,23 @@ __global__ void gcr_coef_batch_kernel(const double *__restrict__ dots, const int
 }
 
 // W_{k,v} = (w_v - sum_j beta_j W_{j,v}) inv, Z likewise from z_v; x_v += alpha Z_{k,v}; r_v -= alpha W_{k,v}
-__global__ void gcr_update_batch_devk_kernel(Cx<double> *__restrict__ W, Cx<double> *__restrict__ Z,
-                                             const Cx<double> *__restrict__ w, const Cx<double> *__restrict__ z,
+template <typename VT>
+__global__ void gcr_update_batch_devk_kernel(Cx<VT> *__restrict__ W, Cx<VT> *__restrict__ Z,
+                                             const Cx<VT> *__restrict__ w, const Cx<VT> *__restrict__ z,
                                              const int *__restrict__ ctl, int nb, int restart,
                                              const double *__restrict__ dots, const double *__restrict__ coef,
-                                             Cx<double> *__restrict__ x, Cx<double> *__restrict__ r, long long n) {
+                                             Cx<VT> *__restrict__ x, Cx<VT> *__restrict__ r, long long n) {
   const int v = blockIdx.y, k = ctl[1];
   if (coef[4 * v + 3] == 0.0) return;
   const double *beta = dots + (long long)v * 2 * (restart + 3);
-  const double inv = coef[4 * v];
-  const Cx<double> alpha = mk(coef[4 * v + 1], coef[4 * v + 2]);
-  Cx<double> *Wk = W + ((long long)k * nb + v) * n, *Zk = Z + ((long long)k * nb + v) * n;
-  const Cx<double> *wv = w + (long long)v * n, *zv = z + (long long)v * n;
+  const VT inv = (VT)coef[4 * v];
+  const Cx<VT> alpha = mk((VT)coef[4 * v + 1], (VT)coef[4 * v + 2]);
+  Cx<VT> *Wk = W + ((long long)k * nb + v) * n, *Zk = Z + ((long long)k * nb + v) * n;
+  const Cx<VT> *wv = w + (long long)v * n, *zv = z + (long long)v * n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    Cx<double> wi = wv[i], zi = zv[i];
+    Cx<VT> wi = wv[i], zi = zv[i];
     for (int j = 0; j < k; ++j) {
-      const Cx<double> bj = mk(-beta[2 * j], -beta[2 * j + 1]);
+      const Cx<VT> bj = mk((VT)-beta[2 * j], (VT)-beta[2 * j + 1]);
       const long long o = ((long long)j * nb + v) * n + i;
       cmac(wi, bj, W[o]);
       cmac(zi, bj, Z[o]);
@@ -612,7 +672,7 @@ __global__ void gcr_update_batch_devk_kernel(Cx<double> *__restrict__ W, Cx<doub
     Wk[i] = wi;
     Zk[i] = zi;
     cmac(x[(long long)v * n + i], alpha, zi);
-    Cx<double> ri = r[(long long)v * n + i];
+    Cx<VT> ri = r[(long long)v * n + i];
     cmac(ri, mk(-alpha.re, -alpha.im), wi);
     r[(long long)v * n + i] = ri;
   }
@@ -632,19 +692,21 @@ __global__ void gcr_control_batch_kernel(int *ctl, const int *act, int nb, int r
   cudaGraphSetConditional(handle, reason == 0 ? 1u : 0u);
 }
 
-void launch_copy_active(const Cx<double> *x, Cx<double> *y, long long n, int nb, const int *act, cudaStream_t s) {
-  copy_active_kernel<<<dim3(stream_grid(n), nb), 256, 0, s>>>(x, y, n, act);
+template <typename VT>
+void launch_copy_active(const Cx<VT> *x, Cx<VT> *y, long long n, int nb, const int *act, cudaStream_t s) {
+  copy_active_kernel<VT><<<dim3(stream_grid(n), nb), 256, 0, s>>>(x, y, n, act);
   MG_LAUNCHED();
 }
 
-void launch_gcr_dots_batch_devk(const Cx<double> *W, const Cx<double> *w, const Cx<double> *r, const int *ctl,
-                                int nb, int restart, long long n, double *out, const ReduceWs &ws, cudaStream_t s) {
+template <typename VT>
+void launch_gcr_dots_batch_devk(const Cx<VT> *W, const Cx<VT> *w, const Cx<VT> *r, const int *ctl, int nb,
+                                int restart, long long n, double *out, const ReduceWs &ws, cudaStream_t s) {
   const int rows = restart + 3;
   int per = (int)(ws.capacity / (2LL * rows * nb));
   if (per > ws.max_blocks) per = ws.max_blocks;
   if (per < 1) per = 1;
   if ((long long)rows * nb > ws.tickets) fail(MG_ERR_UNSUPPORTED, "gcr_dots_batch: too many reduction slots");
-  gcr_dots_batch_devk_kernel<<<dim3(reduce_blocks(n, per), rows, nb), kReduceThreads, 0, s>>>(
+  gcr_dots_batch_devk_kernel<VT><<<dim3(reduce_blocks(n, per), rows, nb), kReduceThreads, 0, s>>>(
       W, w, r, ctl, nb, restart, n, ws.partials, out, ws.ticket);
   MG_LAUNCHED();
 }
@@ -655,13 +717,25 @@ void launch_gcr_coef_batch(const double *dots, const int *ctl, int nb, int resta
   MG_LAUNCHED();
 }
 
-void launch_gcr_update_batch_devk(Cx<double> *W, Cx<double> *Z, const Cx<double> *w, const Cx<double> *z,
-                                  const int *ctl, int nb, int restart, const double *dots, const double *coef,
-                                  Cx<double> *x, Cx<double> *r, long long n, cudaStream_t s) {
-  gcr_update_batch_devk_kernel<<<dim3(stream_grid(n), nb), 256, 0, s>>>(W, Z, w, z, ctl, nb, restart, dots, coef, x,
-                                                                          r, n);
+template <typename VT>
+void launch_gcr_update_batch_devk(Cx<VT> *W, Cx<VT> *Z, const Cx<VT> *w, const Cx<VT> *z, const int *ctl, int nb,
+                                  int restart, const double *dots, const double *coef, Cx<VT> *x, Cx<VT> *r,
+                                  long long n, cudaStream_t s) {
+  gcr_update_batch_devk_kernel<VT><<<dim3(stream_grid(n), nb), 256, 0, s>>>(W, Z, w, z, ctl, nb, restart, dots, coef,
+                                                                              x, r, n);
   MG_LAUNCHED();
 }
+
+#define MG_INST_DEVK(VT)                                                                                           \
+  template void launch_copy_active<VT>(const Cx<VT> *, Cx<VT> *, long long, int, const int *, cudaStream_t);     \
+  template void launch_gcr_dots_batch_devk<VT>(const Cx<VT> *, const Cx<VT> *, const Cx<VT> *, const int *, int,   \
+                                               int, long long, double *, const ReduceWs &, cudaStream_t);        \
+  template void launch_gcr_update_batch_devk<VT>(Cx<VT> *, Cx<VT> *, const Cx<VT> *, const Cx<VT> *, const int *, \
+                                                 int, int, const double *, const double *, Cx<VT> *, Cx<VT> *,    \
+                                                 long long, cudaStream_t);
+MG_INST_DEVK(double)
+MG_INST_DEVK(float)
+#undef MG_INST_DEVK
 
 void launch_gcr_control_batch(int *ctl, const int *act, int nb, int restart, int max_iter,
                               cudaGraphConditionalHandle handle, cudaStream_t s) {

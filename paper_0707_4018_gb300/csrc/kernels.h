@@ -99,14 +99,18 @@ void launch_gcr_control(int *ctl, double *st, int restart, int max_iter, cudaGra
 
 // batched (nb vectors in lockstep): act[v] iterating flags, stv[2 v] |r_v|^2 estimate and
 // stv[2 v + 1] tol^2 |b_v|^2, coef[4 v ..] (inv, alpha, mode); dots stride 2 (restart + 3) per vector
-void launch_copy_active(const Cx<double> *x, Cx<double> *y, long long n, int nb, const int *act, cudaStream_t s);
-void launch_gcr_dots_batch_devk(const Cx<double> *W, const Cx<double> *w, const Cx<double> *r, const int *ctl,
-                                int nb, int restart, long long n, double *out, const ReduceWs &ws, cudaStream_t s);
+// (VT double or float: the vectors' type; reductions and coefficients in FP64)
+template <typename VT>
+void launch_copy_active(const Cx<VT> *x, Cx<VT> *y, long long n, int nb, const int *act, cudaStream_t s);
+template <typename VT>
+void launch_gcr_dots_batch_devk(const Cx<VT> *W, const Cx<VT> *w, const Cx<VT> *r, const int *ctl, int nb,
+                                int restart, long long n, double *out, const ReduceWs &ws, cudaStream_t s);
 void launch_gcr_coef_batch(const double *dots, const int *ctl, int nb, int restart, int *act, double *stv,
                            double *coef, cudaStream_t s);
-void launch_gcr_update_batch_devk(Cx<double> *W, Cx<double> *Z, const Cx<double> *w, const Cx<double> *z,
-                                  const int *ctl, int nb, int restart, const double *dots, const double *coef,
-                                  Cx<double> *x, Cx<double> *r, long long n, cudaStream_t s);
+template <typename VT>
+void launch_gcr_update_batch_devk(Cx<VT> *W, Cx<VT> *Z, const Cx<VT> *w, const Cx<VT> *z, const int *ctl, int nb,
+                                  int restart, const double *dots, const double *coef, Cx<VT> *x, Cx<VT> *r,
+                                  long long n, cudaStream_t s);
 void launch_gcr_control_batch(int *ctl, const int *act, int nb, int restart, int max_iter,
                               cudaGraphConditionalHandle handle, cudaStream_t s);
 

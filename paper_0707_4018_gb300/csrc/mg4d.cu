@@ -83,14 +83,23 @@ struct Engine4 {
     DevBuf<Cx<double>> cb, cx, cr, crin, cZ, cW;
     DevBuf<Cx<float>> cin32, cout32;
     DevBuf<Cx<float>> cb32, cx32, cr32, crin32, cZ32, cW32;  // coarse GCR on FP32 vectors
+    // its iterations replayed by a graph: preconditioned and operator outputs, counters, active
+    // flags, estimates, |b|^2 and |r|^2 per vector, the graph and what it was captured for
+    DevBuf<Cx<float>> czt32, cwt32;
+    DevBuf<int> cctl, cact;
+    DevBuf<double> cstv, cnorm;
+    cudaGraphExec_t loop = nullptr;
+    std::vector<const void *> loop_key;
     DevBuf<double> dots, coef, cdots, ccoef, part;
     DevBuf<unsigned int> tickets;
     ReduceWs ws{};
+    ReduceWs wsc{};  // the same workspace with few blocks per reduction, for the short coarse vectors
     double *host = nullptr, *chost = nullptr;  // pinned: dots, then coefficients (outer / coarse)
   } bt;
   ~Engine4() {
     if (s) cudaStreamSynchronize(s);
     if (cloop) cudaGraphExecDestroy(cloop);
+    if (bt.loop) cudaGraphExecDestroy(bt.loop);
     if (host) cudaFreeHost(host);
     if (bt.host) cudaFreeHost(bt.host);
     if (bt.chost) cudaFreeHost(bt.chost);
@@ -430,7 +439,8 @@ long long coarse_solve(Engine4 &e) {
 // Flexible GCR over nb systems in lockstep (FP64, vectors [v][n], bases [k][v][n]): one
 // batched preconditioner, one batched operator apply and one batched reduction per
 // iteration; the host forms every vector's coefficients from one fetch, with a second
-// projection where |w - W beta|^2 shows cancellation. A vector whose tracked residual meets
+// projection where |w - W beta|^2 <= reproject |w|^2 shows cancellation (reproject 0: only
+// where nothing is left, as the one-pass single-vector coarse GCR). A vector whose tracked residual meets
 // tol (or whose basis breaks down) rests until the next restart, where the true residuals
 // decide which vectors go on; a resting vector's preconditioner input is zero.
 struct GcrB {
@@ -444,7 +454,7 @@ struct GcrB {
 template <typename VT, typename ApplyF, typename PrecF>
 void fgcr_batch(Engine4 &e, int nb, ApplyF &&apply, PrecF &&prec, const Cx<VT> *b, Cx<VT> *x, long long n,
                 double tol, int restart, int max_iter, Cx<VT> *Z, Cx<VT> *W, Cx<VT> *r, Cx<VT> *rin, double *dots,
-                double *coef, double *h, const ReduceWs &ws, std::vector<GcrB> &out) {
+                double *coef, double *h, const ReduceWs &ws, std::vector<GcrB> &out, double reproject = 0.5) {
   double *hcoef = h + (size_t)nb * 2 * (restart + 3);
   out.assign(nb, GcrB{});
   auto fetch = [&](int count) {
@@ -485,7 +495,7 @@ void fgcr_batch(Engine4 &e, int nb, ApplyF &&apply, PrecF &&prec, const Cx<VT> *
         for (int j = 0; j < k; ++j) nw2[v] -= hv[2 * j] * hv[2 * j] + hv[2 * j + 1] * hv[2 * j + 1];
         wr[v] = hv[2 * k + 2];
         wi[v] = hv[2 * k + 3];
-        if (((act >> v) & 1u) && k > 0 && !(nw2[v] > 0.5 * nw0[v])) cancel |= 1u << v;
+        if (((act >> v) & 1u) && k > 0 && !(nw2[v] > reproject * nw0[v])) cancel |= 1u << v;
       }
       if (cancel != 0u) {  // project those vectors once, then take fresh coefficients for them
         for (int v = 0; v < nb; ++v) {
@@ -654,11 +664,28 @@ void prepare_coarse(Engine4 &e) {
   launch_convert<float, double>(e.Minv64.p, e.Minv32.p, e.Minv64.n, e.s);
 }
 
+// Galerkin products in FP32 arithmetic (from the FP32 links and prolongator) for mixed-precision
+// hierarchies whose coarse solve is inexact anyway (coarsest_tol >= 1e-5): the operator then
+// differs from the FP64 one by FP32 rounding, far below what that solve leaves;
+// MG_FP64_GALERKIN keeps FP64
+static bool galerkin4_f32(const Engine4 &e) {
+  return e.f32 && e.p.coarsest_tol >= 1e-5 && std::getenv("MG_FP64_GALERKIN") == nullptr;
+}
+
+static void galerkin4(Engine4 &e) {
+  if (galerkin4_f32(e)) {
+    launch_convert<float, double>(e.V64.p, e.V32.p, e.V64.n, e.s);
+    launch_galerkin4<float>(e.U32.p, diag4(e), e.V32.p, e.Y64.p, e.bg, e.s);
+  } else {
+    launch_galerkin4<double>(e.U64.p, diag4(e), e.V64.p, e.Y64.p, e.bg, e.s);
+  }
+}
+
 // chirality split, block Gram-Schmidt and Galerkin operator from the current vectors
 void build(Engine4 &e) {
   launch_gather_split4(e.nullv.p, e.nf, e.V64.p, e.bg, e.s);
   launch_block_gs4(e.V64.p, e.bg, e.s);
-  launch_galerkin4(e.U64.p, diag4(e), e.V64.p, e.Y64.p, e.bg, e.s);
+  galerkin4(e);
   prepare_coarse(e);
 }
 
@@ -855,7 +882,7 @@ Solve4 engine4_solve(Engine4 &e, const void *chi, void *psi, double tol) {
 
 void engine4_update_mass(Engine4 &e, double m) {
   e.m = m;
-  launch_galerkin4(e.U64.p, diag4(e), e.V64.p, e.Y64.p, e.bg, e.s);
+  galerkin4(e);
   prepare_coarse(e);
   check_info(e);
 }
@@ -963,6 +990,12 @@ void alloc_batch(Engine4 &e) {
     b.crin32.alloc((size_t)nb * e.nc);
     b.cZ32.alloc((size_t)rc * nb * e.nc);
     b.cW32.alloc((size_t)rc * nb * e.nc);
+    b.czt32.alloc((size_t)nb * e.nc);
+    b.cwt32.alloc((size_t)nb * e.nc);
+    b.cctl.alloc(3);
+    b.cact.alloc((size_t)nb);
+    b.cstv.alloc((size_t)2 * nb);
+    b.cnorm.alloc((size_t)2 * nb);
   }
   const int rows = std::max(ro, rc) + 3;
   b.dots.alloc((size_t)nb * 2 * (ro + 3));
@@ -980,11 +1013,12 @@ void alloc_batch(Engine4 &e) {
   MG_CUDA(cudaMemsetAsync(b.tickets.p, 0, b.ws.tickets * sizeof(unsigned int), e.s));
   b.ws.partials = b.part.p;
   b.ws.ticket = b.tickets.p;
+  // 64 blocks per reduction suit the fine vectors; on 512 x 48 coarse dofs they made 12 x (k + 3)
+  // x 64 blocks of 1.5 elements per thread, and the batched dots took 164 us per launch
+  b.wsc = b.ws;
+  b.wsc.max_blocks = 8;
 }
 
-// batched coarse solve of nb vectors: cx_v = A_c^{-1} cb_v by lockstep GCR to coarsest_tol,
-// right-preconditioned by block Jacobi; the operator applied to all vectors at once on
-// tensor cores (N = 48; BF16 operands, FP32 sums) or, otherwise, in FP64
 // operand precision of the batched tensor-core coarse apply (launch_coarse4_apply_tc's split):
 // MG_COARSE4_TC_SPLIT = 0, 1 or 2, else 2
 static int tc_split() {
@@ -1014,11 +1048,121 @@ static void ensure_mrhs(Engine4 &e, bool lo) {
   e.mrhs_ready = true;
 }
 
+// batched coarse solve of nb vectors: cx_v = A_c^{-1} cb_v by lockstep GCR to coarsest_tol,
+// right-preconditioned by block Jacobi; the operator applied to all vectors at once on
+// tensor cores (N = 48; BF16 operands split as tc_split says, FP32 sums) or, otherwise, in FP64
+// The batched coarse GCR on FP32 vectors with its iterations on the device: a cycle-start kernel
+// and a WHILE node whose body is one lockstep iteration (masked copy of r, block-Jacobi
+// preconditioner, tensor-core operator, reduction with k read from device memory, per-vector
+// coefficients, update, control), captured once per batch size and launched once per restart
+// cycle; the host reads the true residuals after each launch. Classical Gram-Schmidt in one
+// pass, as the single-vector coarse GCR.
+static cudaGraphExec_t coarse_batch_loop_graph(Engine4 &e, int nb, int split) {
+  auto &b = e.bt;
+  const std::vector<const void *> key = {reinterpret_cast<const void *>((long long)nb),
+                                         reinterpret_cast<const void *>((long long)split), e.Ypk4.p, e.Ypk4lo.p,
+                                         e.Minv32.p, b.cZ32.p, b.cW32.p, b.cdots.p, b.ccoef.p, b.wsc.partials};
+  if (b.loop != nullptr && key == b.loop_key) return b.loop;
+  if (b.loop != nullptr) {
+    MG_CUDA(cudaGraphExecDestroy(b.loop));
+    b.loop = nullptr;
+  }
+  const long long n = e.nc;
+  const int restart = e.p.coarsest_restart, max_iter = e.p.coarsest_max_iter;
+  cudaGraph_t top = nullptr;
+  MG_CUDA(cudaGraphCreate(&top, 0));
+  try {
+    cudaGraphConditionalHandle h;
+    MG_CUDA(cudaGraphConditionalHandleCreate(&h, top, 0, cudaGraphCondAssignDefault));
+    MG_CUDA(cudaStreamBeginCaptureToGraph(e.s, top, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    launch_coarse4_batch_cycle_start(b.cctl.p, b.cact.p, nb, max_iter, h, e.s);
+    MG_CUDA(cudaStreamEndCapture(e.s, &top));
+    size_t count = 1;
+    cudaGraphNode_t start;
+    MG_CUDA(cudaGraphGetNodes(top, &start, &count));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    MG_CUDA(cudaGraphAddNode(&node, top, &start, nullptr, 1, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    MG_CUDA(cudaStreamBeginCaptureToGraph(e.s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    launch_copy_active<float>(b.cr32.p, b.crin32.p, n, nb, b.cact.p, e.s);
+    launch_block_apply4_32(e.Minv32.p, b.crin32.p, b.czt32.p, e.cg, e.s, nb);
+    launch_coarse4_apply_tc(e.Ypk4.p, b.czt32.p, b.cwt32.p, e.cg.nb, nb, e.s, split, e.Ypk4lo.p);
+    launch_gcr_dots_batch_devk<float>(b.cW32.p, b.cwt32.p, b.cr32.p, b.cctl.p, nb, restart, n, b.cdots.p, b.wsc, e.s);
+    launch_gcr_coef_batch(b.cdots.p, b.cctl.p, nb, restart, b.cact.p, b.cstv.p, b.ccoef.p, e.s);
+    launch_gcr_update_batch_devk<float>(b.cW32.p, b.cZ32.p, b.cwt32.p, b.czt32.p, b.cctl.p, nb, restart, b.cdots.p,
+                                        b.ccoef.p, b.cx32.p, b.cr32.p, n, e.s);
+    launch_gcr_control_batch(b.cctl.p, b.cact.p, nb, restart, max_iter, h, e.s);
+    MG_CUDA(cudaStreamEndCapture(e.s, &body));
+    MG_CUDA(cudaGraphInstantiate(&b.loop, top, 0));
+  } catch (...) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t partial = nullptr;
+    if (cudaStreamIsCapturing(e.s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+      cudaStreamEndCapture(e.s, &partial);  // a graph owned by top (or top itself)
+    cudaGetLastError();
+    cudaGraphDestroy(top);
+    throw;
+  }
+  cudaGraphDestroy(top);
+  b.loop_key = key;
+  return b.loop;
+}
+
+// cb (FP64, nb vectors) -> cx by the graph-replayed lockstep GCR; returns the lockstep iterations
+static long long coarse_solve_batch32_loop(Engine4 &e, int nb, int split) {
+  auto &b = e.bt;
+  const long long n = e.nc, nn = (long long)nb * n;
+  cudaGraphExec_t g = coarse_batch_loop_graph(e, nb, split);
+  launch_convert<float, double>(b.cb.p, b.cb32.p, nn, e.s);
+  launch_zero<float>(b.cx32.p, nn, e.s);
+  launch_copy<float>(b.cb32.p, b.cr32.p, nn, e.s);
+  double *bn2 = b.cnorm.p, *rn2 = b.cnorm.p + nb;
+  launch_norm2_batch(static_cast<const Cx<float> *>(b.cb32.p), n, nb, bn2, b.wsc, e.s);
+  const double tol = e.p.coarsest_tol;
+  launch_coarse4_batch_init(bn2, tol * tol, nb, b.cstv.p, b.cact.p, e.s);
+  MG_CUDA(cudaMemsetAsync(b.cctl.p, 0, 3 * sizeof(int), e.s));
+  std::vector<double> hn(2 * nb);
+  std::vector<int> act(nb);
+  int ctl[3] = {0, 0, 0};
+  for (;;) {
+    MG_CUDA(cudaGraphLaunch(g, e.s));
+    // true residuals r_v = b_v - A x_v
+    launch_coarse4_apply_tc(e.Ypk4.p, b.cx32.p, b.cr32.p, e.cg.nb, nb, e.s, split, e.Ypk4lo.p);
+    launch_xmy<float>(b.cb32.p, b.cr32.p, nn, e.s);
+    launch_norm2_batch(static_cast<const Cx<float> *>(b.cr32.p), n, nb, rn2, b.wsc, e.s);
+    MG_CUDA(cudaMemcpyAsync(hn.data(), b.cnorm.p, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, e.s));
+    MG_CUDA(cudaMemcpyAsync(ctl, b.cctl.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, e.s));
+    MG_CUDA(cudaStreamSynchronize(e.s));
+    e.apps[1] += (long long)nb;
+    int left = 0;
+    for (int v = 0; v < nb; ++v) {
+      if (std::isnan(hn[v]) || std::isnan(hn[nb + v])) fail(MG_ERR_NAN, "GCR (batched): NaN in a reduction");
+      act[v] = hn[v] > 0.0 && hn[nb + v] > tol * tol * hn[v] ? 1 : 0;
+      left += act[v];
+    }
+    if (left == 0 || ctl[0] >= e.p.coarsest_max_iter) break;
+    MG_CUDA(cudaMemcpyAsync(b.cact.p, act.data(), nb * sizeof(int), cudaMemcpyHostToDevice, e.s));
+  }
+  e.apps[1] += (long long)ctl[0] * nb;
+  launch_convert<double, float>(b.cx32.p, b.cx.p, nn, e.s);
+  return ctl[0];
+}
+
 void coarse_solve_batch(Engine4 &e, int nb) {
   auto &b = e.bt;
   const bool tc = e.N == 48;
   const int split = tc_split();
   if (tc) ensure_mrhs(e, split == 2);
+  if (tc && b.czt32.p != nullptr && nb <= 32 && e.p.coarsest_restart <= kCoarseLoopMaxRestart &&
+      std::getenv("MG_COARSE4_FP64_VECTORS") == nullptr && std::getenv("MG_COARSE4_HOST_LOOP") == nullptr) {
+    e.coarsest_iters += coarse_solve_batch32_loop(e, nb, split);
+    return;
+  }
   auto apply = [&](const Cx<double> *in, Cx<double> *out, const Cx<double> *rhs) {
     if (tc) {
       launch_convert<float, double>(in, b.cin32.p, (long long)nb * e.nc, e.s);
@@ -1050,12 +1194,12 @@ void coarse_solve_batch(Engine4 &e, int nb) {
     launch_convert<float, double>(b.cb.p, b.cb32.p, (long long)nb * e.nc, e.s);
     fgcr_batch(e, nb, apply32, prec32, static_cast<const Cx<float> *>(b.cb32.p), b.cx32.p, e.nc, e.p.coarsest_tol,
                e.p.coarsest_restart, e.p.coarsest_max_iter, b.cZ32.p, b.cW32.p, b.cr32.p, b.crin32.p, b.cdots.p,
-               b.ccoef.p, b.chost, b.ws, out);
+               b.ccoef.p, b.chost, b.wsc, out, 0.0);
     launch_convert<double, float>(b.cx32.p, b.cx.p, (long long)nb * e.nc, e.s);
   } else {
     fgcr_batch(e, nb, apply, prec, static_cast<const Cx<double> *>(b.cb.p), b.cx.p, e.nc, e.p.coarsest_tol,
                e.p.coarsest_restart, e.p.coarsest_max_iter, b.cZ.p, b.cW.p, b.cr.p, b.crin.p, b.cdots.p, b.ccoef.p,
-               b.chost, b.ws, out);
+               b.chost, b.wsc, out);
   }
   int mx = 0;
   for (const auto &o : out) mx = std::max(mx, o.iters);

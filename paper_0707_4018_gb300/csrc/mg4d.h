@@ -41,9 +41,10 @@ void launch_prolong4(const Cx<R> *V, const Cx<R> *coarse, Cx<R> *fine, const Blo
 void launch_gather_split4(const Cx<double> *vecs, long long vstride, Cx<double> *V, const Block4 &g, cudaStream_t s);
 // modified Gram-Schmidt, twice, of the Nv columns of each (block, chirality), in place
 void launch_block_gs4(Cx<double> *V, const Block4 &g, cudaStream_t s);
-// Y = P^dagger D P (FP64) for the fine Wilson operator with diagonal `diag`
-void launch_galerkin4(const Cx<double> *U, double diag, const Cx<double> *V, Cx<double> *Y, const Block4 &g,
-                      cudaStream_t s);
+// Y = P^dagger D P (written in FP64) for the fine Wilson operator with diagonal `diag`; CT the
+// links', prolongator's and arithmetic's type (float: FP32 products for mixed hierarchies)
+template <typename CT>
+void launch_galerkin4(const Cx<CT> *U, double diag, const Cx<CT> *V, Cx<double> *Y, const Block4 &g, cudaStream_t s);
 // out = a (A + shift_v) in + c b on the coarse lattice (nvec vectors, stride nsites * N);
 // the operator's precision RY may be below the vectors' RV (float / double: FP32 sums)
 template <typename RY, typename RV>
@@ -75,6 +76,12 @@ void launch_coarse4_cycle_start(int *ctl, const double *st, int max_iter, cudaGr
                                 cudaStream_t s);
 void launch_coarse4_control(int *ctl, double *st, double tol2_rel, int restart, int max_iter,
                             cudaGraphConditionalHandle h, cudaStream_t s);
+// its batched form (nb <= 32 vectors): estimates, thresholds and active flags from |b_v|^2, and
+// the kernel that starts a restart cycle (the iterations use the batched device-k kernels of
+// kernels.h)
+void launch_coarse4_batch_init(const double *bn2, double tol2_rel, int nb, double *stv, int *act, cudaStream_t s);
+void launch_coarse4_batch_cycle_start(int *ctl, const int *act, int nb, int max_iter, cudaGraphConditionalHandle h,
+                                      cudaStream_t s);
 void launch_block_apply4_32(const Cx<float> *Minv, const Cx<float> *r, Cx<float> *z, const Coarse4 &g,
                             cudaStream_t s, int nvec = 1);
 // Yt[j][dir] = Y[j][dir] Minv[src(j, dir)]: the block-Jacobi right-preconditioned stencil A M

@@ -177,13 +177,17 @@ __global__ void __launch_bounds__(256) block_gs4_kernel(Cx<double> *__restrict__
 // ---------------------------------------------------------------------------
 constexpr int kGalPairs = 16;  // (row, col) pairs per thread: N <= 64
 
-__global__ void __launch_bounds__(256) galerkin4_kernel(const Cx<double> *__restrict__ U, double diag,
-                                                        const Cx<double> *__restrict__ V, Cx<double> *__restrict__ Y,
+// CT: the arithmetic (and the links' and prolongator's storage) type; Y is written in FP64.
+// FP32 for mixed-precision hierarchies with an inexact coarse solve: the kernel is FP64-ALU
+// bound on this part (73 ms at 16^3 x 32 with Nv = 24).
+template <typename CT>
+__global__ void __launch_bounds__(256) galerkin4_kernel(const Cx<CT> *__restrict__ U, double diag,
+                                                        const Cx<CT> *__restrict__ V, Cx<double> *__restrict__ Y,
                                                         Block4 g) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int N = 2 * g.Nv, Nh = g.bvol * 6;
-  Cx<double> *Hs = reinterpret_cast<Cx<double> *>(sm_raw);  // [N][12]
-  Cx<double> *Vs = Hs + N * 12;                              // [N][6]
+  Cx<CT> *Hs = reinterpret_cast<Cx<CT> *>(sm_raw);  // [N][12]
+  Cx<CT> *Vs = Hs + N * 12;                          // [N][6]
   const int j = blockIdx.x, dir = blockIdx.y, tid = threadIdx.x;
   int jc[4];
   {
@@ -209,9 +213,9 @@ __global__ void __launch_bounds__(256) galerkin4_kernel(const Cx<double> *__rest
     fst[m2] = fst[m2 - 1] * g.L[m2 - 1];
   }
   const int npairs = N * N;
-  Cx<double> acc[kGalPairs];
+  Cx<CT> acc[kGalPairs];
 #pragma unroll
-  for (int i = 0; i < kGalPairs; ++i) acc[i] = mk(0.0, 0.0);
+  for (int i = 0; i < kGalPairs; ++i) acc[i] = mk((CT)0, (CT)0);
   const int nvisit = dir == 0 ? g.bvol : g.bvol / g.B[mu];
   for (int q = 0; q < nvisit; ++q) {
     // in-block position s of the q-th site (for a face: coordinate mu fixed)
@@ -242,30 +246,30 @@ __global__ void __launch_bounds__(256) galerkin4_kernel(const Cx<double> *__rest
     }
     if (tid < N) {
       const int c = tid, chi = c / g.Nv;
-      Cx<double> hacc[12];
+      Cx<CT> hacc[12];
 #pragma unroll
-      for (int i = 0; i < 12; ++i) hacc[i] = mk(0.0, 0.0);
-      Cx<double> p[12];
+      for (int i = 0; i < 12; ++i) hacc[i] = mk((CT)0, (CT)0);
+      Cx<CT> p[12];
       auto load_col = [&](int blk, int spos) {
 #pragma unroll
-        for (int i = 0; i < 12; ++i) p[i] = mk(0.0, 0.0);
-        const Cx<double> *src = V + ((long long)blk * N + c) * Nh + spos * 6;
+        for (int i = 0; i < 12; ++i) p[i] = mk((CT)0, (CT)0);
+        const Cx<CT> *src = V + ((long long)blk * N + c) * Nh + spos * 6;
 #pragma unroll
         for (int d6 = 0; d6 < 6; ++d6) p[6 * chi + d6] = src[d6];
       };
-      Cx<double> h[12];
+      Cx<CT> h[12];
       if (dir == 0) {
         load_col(j, s);
 #pragma unroll
-        for (int i = 0; i < 12; ++i) h[i] = diag * p[i];
+        for (int i = 0; i < 12; ++i) h[i] = (CT)diag * p[i];
         for (int m2 = 0; m2 < 4; ++m2) {
           if (sc[m2] + 1 < g.B[m2]) {  // x + m2 inside the block
             load_col(j, s + bst[m2]);
-            hop_dispatch<double>(2 * m2, p, U + ((long long)x * 4 + m2) * 9, hacc);
+            hop_dispatch<CT>(2 * m2, p, U + ((long long)x * 4 + m2) * 9, hacc);
           }
           if (sc[m2] > 0) {  // x - m2 inside the block
             load_col(j, s - bst[m2]);
-            hop_dispatch<double>(2 * m2 + 1, p, U + ((long long)(x - fst[m2]) * 4 + m2) * 9, hacc);
+            hop_dispatch<CT>(2 * m2 + 1, p, U + ((long long)(x - fst[m2]) * 4 + m2) * 9, hacc);
           }
         }
       } else {
@@ -273,11 +277,12 @@ __global__ void __launch_bounds__(256) galerkin4_kernel(const Cx<double> *__rest
         load_col(jsrc, sn);
         const int xn = fine_site4(g, jsrc, sn);
 #pragma unroll
-        for (int i = 0; i < 12; ++i) h[i] = mk(0.0, 0.0);
-        hop_dispatch<double>(fwd ? 2 * mu : 2 * mu + 1, p, U + ((long long)(fwd ? x : xn) * 4 + mu) * 9, hacc);
+        for (int i = 0; i < 12; ++i) h[i] = mk((CT)0, (CT)0);
+        hop_dispatch<CT>(fwd ? 2 * mu : 2 * mu + 1, p, U + ((long long)(fwd ? x : xn) * 4 + mu) * 9, hacc);
       }
 #pragma unroll
-      for (int i = 0; i < 12; ++i) Hs[c * 12 + i] = mk(h[i].re - 0.5 * hacc[i].re, h[i].im - 0.5 * hacc[i].im);
+      for (int i = 0; i < 12; ++i)
+        Hs[c * 12 + i] = mk(h[i].re - (CT)0.5 * hacc[i].re, h[i].im - (CT)0.5 * hacc[i].im);
     }
     __syncthreads();
 #pragma unroll
@@ -285,7 +290,7 @@ __global__ void __launch_bounds__(256) galerkin4_kernel(const Cx<double> *__rest
       const int pr = tid + 256 * i;
       if (pr < npairs) {
         const int col = pr / N, row = pr - col * N, chr = row / g.Nv;
-        Cx<double> a = acc[i];
+        Cx<CT> a = acc[i];
 #pragma unroll
         for (int d6 = 0; d6 < 6; ++d6) cmac_conj(a, Vs[row * 6 + d6], Hs[col * 12 + 6 * chr + d6]);
         acc[i] = a;
@@ -295,7 +300,7 @@ __global__ void __launch_bounds__(256) galerkin4_kernel(const Cx<double> *__rest
 #pragma unroll
   for (int i = 0; i < kGalPairs; ++i) {
     const int pr = tid + 256 * i;
-    if (pr < npairs) Y[((long long)j * 9 + dir) * npairs + pr] = acc[i];
+    if (pr < npairs) Y[((long long)j * 9 + dir) * npairs + pr] = mk((double)acc[i].re, (double)acc[i].im);
   }
 }
 
@@ -661,13 +666,17 @@ void launch_block_gs4(Cx<double> *V, const Block4 &g, cudaStream_t s) {
   MG_LAUNCHED();
 }
 
-void launch_galerkin4(const Cx<double> *U, double diag, const Cx<double> *V, Cx<double> *Y, const Block4 &g,
-                      cudaStream_t s) {
+template <typename CT>
+void launch_galerkin4(const Cx<CT> *U, double diag, const Cx<CT> *V, Cx<double> *Y, const Block4 &g, cudaStream_t s) {
   const int N = 2 * g.Nv;
-  const size_t smem = (size_t)N * 18 * sizeof(Cx<double>);
-  galerkin4_kernel<<<dim3(g.nblocks, 9), 256, smem, s>>>(U, diag, V, Y, g);
+  const size_t smem = (size_t)N * 18 * sizeof(Cx<CT>);
+  galerkin4_kernel<CT><<<dim3(g.nblocks, 9), 256, smem, s>>>(U, diag, V, Y, g);
   MG_LAUNCHED();
 }
+template void launch_galerkin4<double>(const Cx<double> *, double, const Cx<double> *, Cx<double> *, const Block4 &,
+                                       cudaStream_t);
+template void launch_galerkin4<float>(const Cx<float> *, double, const Cx<float> *, Cx<double> *, const Block4 &,
+                                      cudaStream_t);
 
 template <typename RY, typename RV>
 void launch_coarse4_apply(const Cx<RY> *Y, const Cx<RV> *in, Cx<RV> *out, const Coarse4 &g, const Cx<RV> *b,
@@ -829,6 +838,36 @@ __global__ void coarse4_control_kernel(int *ctl, double *st, double tol2_rel, in
   // a NaN estimate ends the loop; the host finds it in the true residual
   const bool go = st[0] > tol2_rel * st[1] && k < restart && it < max_iter;
   cudaGraphSetConditional(handle, go ? 1u : 0u);
+}
+
+// batched form: stv[2 v] = |b_v|^2 (the first estimate), stv[2 v + 1] = tol^2 |b_v|^2, act[v] = b_v != 0
+__global__ void coarse4_batch_init_kernel(const double *bn2, double tol2_rel, int nb, double *stv, int *act) {
+  const int v = threadIdx.x;
+  if (v >= nb) return;
+  stv[2 * v] = bn2[v];
+  stv[2 * v + 1] = tol2_rel * bn2[v];
+  act[v] = bn2[v] > 0.0 ? 1 : 0;
+}
+
+// starts a restart cycle of the batched loop (k = 0); it runs while a vector is active and the
+// iteration limit is not reached
+__global__ void coarse4_batch_cycle_start_kernel(int *ctl, const int *act, int nb, int max_iter,
+                                                 cudaGraphConditionalHandle handle) {
+  ctl[1] = 0;
+  int any = 0;
+  for (int v = 0; v < nb; ++v) any |= act[v];
+  cudaGraphSetConditional(handle, (any && ctl[0] < max_iter) ? 1u : 0u);
+}
+
+void launch_coarse4_batch_init(const double *bn2, double tol2_rel, int nb, double *stv, int *act, cudaStream_t s) {
+  coarse4_batch_init_kernel<<<1, 32, 0, s>>>(bn2, tol2_rel, nb, stv, act);
+  MG_LAUNCHED();
+}
+
+void launch_coarse4_batch_cycle_start(int *ctl, const int *act, int nb, int max_iter, cudaGraphConditionalHandle h,
+                                      cudaStream_t s) {
+  coarse4_batch_cycle_start_kernel<<<1, 1, 0, s>>>(ctl, act, nb, max_iter, h);
+  MG_LAUNCHED();
 }
 
 void launch_coarse4_cycle_start(int *ctl, const double *st, int max_iter, cudaGraphConditionalHandle h,

@@ -61,6 +61,33 @@ def test_build_level_matches_oracle(dims, block, nv):
     ctx.close()
 
 
+@pytest.mark.parametrize("fp64_galerkin", [False, True])
+def test_mixed_galerkin_fp32_arithmetic(fp64_galerkin, monkeypatch):
+    # a mixed-precision context with an inexact coarse solve forms P^dagger D P in FP32 arithmetic
+    # from FP32 links and prolongator (MG_FP64_GALERKIN keeps FP64): the stencil agrees with the
+    # oracle's FP64 Galerkin product of the same vectors to FP32 rounding (to FP64 rounding)
+    import paper_0707_4018_gb300 as mg
+    if fp64_galerkin:
+        monkeypatch.setenv("MG_FP64_GALERKIN", "1")
+    dims, block, nv = (8, 8, 8, 8), (4, 4, 4, 4), 6
+    lat = Lattice(dims)
+    U = inputs.su3_links(dims, seed=21)
+    m = 0.1
+    ctx = mg.Context.setup(to_dev(U), m, dims, _params(block, nv, 1, n_pass=1, nu_setup=2, coarsest_tol=0.1))
+    vecs = np.stack([inputs.gaussian_spinor(lat.volume, 12, 40, k) for k in range(nv)])
+    ctx.build_level(0, to_dev(vecs))
+    hier = _oracle_hier(U, m, dims, block, nv)
+    hier.build_level(0, list(vecs))
+    Y = to_host(ctx.coarse_op(1))
+    err = np.abs(Y - hier.ops[1].Y).max() / np.abs(hier.ops[1].Y).max()
+    # FP32: an entry of the self block sums 4^4 sites x 6 dofs = 1536 products in sequence, a
+    # random-walk rounding error of about sqrt(1536) 2^-24 = 2.3e-6 of the sum of |terms|
+    assert err < (1e-12 if fp64_galerkin else 1e-5), err
+    if not fp64_galerkin:
+        assert err > 1e-12  # the FP32 path ran
+    ctx.close()
+
+
 def test_first_pass_vectors_match_oracle():
     # the relaxed vectors of pass 1 from the same Philox draws
     import paper_0707_4018_gb300 as mg
@@ -239,21 +266,29 @@ def test_batched_solve_matches_dense_lu(precision):
     ctx.close()
 
 
-@pytest.mark.parametrize("fp64_vectors", [False, True])
-def test_batched_solve_tensor_core_coarse_apply(fp64_vectors, monkeypatch):
-    # N = 48 (Nv = 24): the batched coarse solve applies the operator on tensor cores, its lockstep GCR
-    # on FP32 vectors (FP64 sums) or, with MG_COARSE4_FP64_VECTORS, FP64 ones; every vector reaches
-    # the FP64 true residual recomputed by the oracle
+@pytest.mark.parametrize("mode,split,restart", [("device_loop", None, 64), ("device_loop", None, 3),
+                                                ("device_loop", "0", 64), ("host_loop", None, 64),
+                                                ("fp64_vectors", None, 64)])
+def test_batched_solve_tensor_core_coarse_apply(mode, split, restart, monkeypatch):
+    # N = 48 (Nv = 24): the batched coarse solve applies the operator on tensor cores (BF16 hi + lo
+    # operands by default, BF16 alone with split 0), its lockstep GCR on FP32 vectors (FP64 sums)
+    # replayed on the device by a graph (restart 3: several restarts inside one launch), host-driven
+    # with MG_COARSE4_HOST_LOOP, or on FP64 vectors with MG_COARSE4_FP64_VECTORS; every vector
+    # reaches the FP64 true residual recomputed by the oracle
     import torch
     import paper_0707_4018_gb300 as mg
-    if fp64_vectors:
+    if mode == "fp64_vectors":
         monkeypatch.setenv("MG_COARSE4_FP64_VECTORS", "1")
+    if mode == "host_loop":
+        monkeypatch.setenv("MG_COARSE4_HOST_LOOP", "1")
+    if split is not None:
+        monkeypatch.setenv("MG_COARSE4_TC_SPLIT", split)
     dims = (8, 8, 8, 8)
     lat = Lattice(dims)
     U = inputs.su3_links(dims, seed=27)
     m = 0.02
     ctx = mg.Context.setup(to_dev(U), m, dims, _params((4, 4, 4, 4), 24, 1, n_pass=1, nu_setup=50,
-                                                       coarsest_tol=0.05, max_rhs=5))
+                                                       coarsest_tol=0.05, coarsest_restart=restart, max_rhs=5))
     chi = np.stack([inputs.gaussian_spinor(lat.volume, 12, 46, k) for k in range(5)])
     psi = torch.empty((5, lat.volume, 12), dtype=torch.complex128, device="cuda")
     st = ctx.solve_batch(to_dev(chi), psi, 1e-10)
