@@ -729,12 +729,14 @@ def su3_params(precision: int):
     which lower the quality of well-relaxed 4d vectors, in the oracle too), MR 4 + 4, coarse
     GCR(64) to 0.3 with block Jacobi, at most 128 coarse iterations per cycle (near m_c an
     inexact coarse solve costs fewer operations than an exact one; the outer flexible GCR absorbs
-    it). At m_c + 0.005 these settings took 144 ms per solve and 0.47 s of setup, against 227 ms
-    and 0.30 s with 200 relaxation steps and a coarse tolerance of 0.05."""
+    it), outer restart 32 (the 22-25 outer iterations then run without a restart). At m_c + 0.005
+    these settings took 144 ms per solve and 0.47 s of setup, against 227 ms and 0.30 s with 200
+    relaxation steps and a coarse tolerance of 0.05; the batch of 12 took 553 / 542 / 550 / 526 ms
+    with outer restarts 16 / 8 / 12 / 24 (24-26 outer iterations, 22 with 24)."""
     import paper_0707_4018_gb300 as mg
     return mg.mg_default_params(levels=2, blocks=[(4, 4, 4, 4)], Nv=[24], precision=precision, chiral_split=1,
                                 n_pass=1, nu_setup=400, coarsest_tol=0.3, coarsest_restart=64,
-                                coarsest_max_iter=128, max_iter=300, max_rhs=SU3_RHS)
+                                coarsest_max_iter=128, gcr_restart=32, max_iter=300, max_rhs=SU3_RHS)
 
 
 def su3_workload(precisions=(1, 0), nrhs: int = SU3_RHS, batched: bool = True, singles: bool = True):

@@ -60,8 +60,9 @@ __global__ void __launch_bounds__(128) restrict_kernel(const Cx<R> *__restrict__
 // (16 KB in FP32), and reads it with 16-byte loads in order (four per thread): every
 // load instruction of a warp covers 512 contiguous bytes. A 16-byte vector holds CPV
 // complex numbers (2 in FP32, 1 in FP64) of one (block, k) row and of one site (n_int is
-// a multiple of CPV), so the matching residual entries are one 16-byte load too (served
-// from L1/L2 for the other seven k). The Nb / CPV vectors of a row belong to consecutive
+// a multiple of CPV), so the matching residual entries are one 16-byte vector too; the CTA
+// stages its blocks' residual entries in shared memory once, and the eight rows k of a block
+// read them there (loading them once per k from L1/L2 held the kernel at 0.54 of HBM). The Nb / CPV vectors of a row belong to consecutive
 // lanes and are summed by a shuffle tree within that lane group.
 template <typename R>
 struct Vec16;
@@ -106,13 +107,11 @@ __global__ void __launch_bounds__(256) restrict8_stream_kernel(const Cx<R> *__re
   // bandwidth, bounded the first version of this kernel)
   const int b0i = (int)b0;
   const int c1_0 = b0i / g.nb0, c0_0 = b0i - c1_0 * g.nb0;
-  // all loads first: ITERS tile vectors and their residual vectors in flight together
-  T vv[ITERS], rr[ITERS];
-#pragma unroll
-  for (int u = 0; u < ITERS; ++u) {
-    const int f = threadIdx.x + 256 * u;
-    const int row = f / PER_ROW, j = f - row * PER_ROW;
-    const int bl = row / NV;
+  // the residual entries of the CTA's blocks, one 16-byte vector per (block, j)
+  __shared__ T rs[BPC * PER_ROW];
+  for (int q = threadIdx.x; q < BPC * PER_ROW; q += 256) {
+    const int bl = q / PER_ROW, j = q - bl * PER_ROW;
+    T val = T{};
     if (b0i + bl < g.nblocks) {
       int c0 = c0_0 + bl, c1 = c1_0;
       while (c0 >= g.nb0) {  // the CTA's blocks are consecutive in x, wrapping into the next row
@@ -122,12 +121,25 @@ __global__ void __launch_bounds__(256) restrict8_stream_kernel(const Cx<R> *__re
       const int i = j * CPV, st = i / g.nint, a = i - st * g.nint;
       const int sy = st / g.B0, sx = st - sy * g.B0;
       const long long site = (long long)(c0 * g.B0 + sx) + (long long)g.L0 * (c1 * g.B1 + sy);
-      vv[u] = tile[f];
-      rr[u] = *reinterpret_cast<const T *>(fine + site * g.nint + a);
-    } else {
-      vv[u] = T{};
-      rr[u] = T{};
+      val = *reinterpret_cast<const T *>(fine + site * g.nint + a);
     }
+    rs[q] = val;
+  }
+  // all tile loads first: ITERS tile vectors in flight together
+  T vv[ITERS];
+#pragma unroll
+  for (int u = 0; u < ITERS; ++u) {
+    const int f = threadIdx.x + 256 * u;
+    const int bl = f / PER_ROW / NV;
+    vv[u] = b0i + bl < g.nblocks ? tile[f] : T{};
+  }
+  __syncthreads();
+  T rr[ITERS];
+#pragma unroll
+  for (int u = 0; u < ITERS; ++u) {
+    const int f = threadIdx.x + 256 * u;
+    const int row = f / PER_ROW, j = f - row * PER_ROW;
+    rr[u] = rs[(row / NV) * PER_ROW + j];
   }
 #pragma unroll
   for (int u = 0; u < ITERS; ++u) {
