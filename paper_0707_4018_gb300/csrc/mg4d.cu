@@ -38,6 +38,8 @@ struct Engine4 {
   int N = 0;
   DevBuf<Cx<double>> U64, nullv, V64, Y64, Minv64, Yt64;  // Yt: A M, the preconditioned stencil
   DevBuf<Cx<float>> U32, V32, Yt32, Minv32;
+  // A M in FP16 for the single-vector coarse GCR when its tolerance is loose (>= 0.05)
+  DevBuf<unsigned int> Yth;
   DevBuf<int> info;  // set by the block inversion when a self block is singular
   // multi-vector coarse apply (made on first use after each Galerkin build): BF16 tensor-core
   // fragments and an FP32 copy of Y
@@ -228,6 +230,14 @@ Gcr fgcr(Engine4 &e, ApplyF &&apply, PrecF &&prec, const Cx<double> *b, Cx<doubl
 // FP32 Krylov vectors and updates, and every reduction in FP64 (MG_FP32 with a coarsest
 // tolerance FP32 arithmetic can reach, >= 1e-5: the FP64 Gram-Schmidt over up to 64 basis
 // vectors, at 1/74 of the FP32 rate, was most of an iteration's time)
+// out = A M in (rhs: out = rhs - A M in) on FP32 vectors, with the FP16 operator when there is one
+static void apply_coarse32(Engine4 &e, const Cx<float> *in, Cx<float> *out, const Cx<float> *rhs) {
+  if (e.Yth.p != nullptr)
+    launch_coarse4_apply_h(e.Yth.p, in, out, e.cg, rhs, rhs ? -1.0 : 1.0, rhs ? 1.0 : 0.0, e.s);
+  else
+    launch_coarse4_apply<float, float>(e.Yt32.p, in, out, e.cg, rhs, rhs ? -1.0 : 1.0, rhs ? 1.0 : 0.0, e.s);
+}
+
 // The coarse GCR of coarse_solve32 with its iterations on the device: one graph per engine, a
 // cycle-start kernel and a WHILE node whose body is one iteration (operator, reduction, step,
 // control), captured once and launched once per restart cycle. The estimate is checked after
@@ -241,7 +251,7 @@ static bool coarse_loop_enabled(const Engine4 &e) {
 
 static cudaGraphExec_t coarse_loop_graph(Engine4 &e) {
   double *dots = e.scal.p + kScalCoarse, *st = dots + 204;
-  const std::vector<const void *> key = {e.Yt32.p, e.cr32.p, e.cy32.p, e.cZ32.p, e.cW32.p, e.cwt32.p, e.cctl.p,
+  const std::vector<const void *> key = {e.Yt32.p, e.Yth.p, e.cr32.p, e.cy32.p, e.cZ32.p, e.cW32.p, e.cwt32.p, e.cctl.p,
                                          dots, e.wsc.partials, e.wsc.ticket,
                                          reinterpret_cast<const void *>((long long)e.p.coarsest_restart),
                                          reinterpret_cast<const void *>((long long)e.p.coarsest_max_iter)};
@@ -273,7 +283,7 @@ static cudaGraphExec_t coarse_loop_graph(Engine4 &e) {
     MG_CUDA(cudaGraphAddNode(&node, top, &start, nullptr, 1, &np));
     cudaGraph_t body = np.conditional.phGraph_out[0];
     MG_CUDA(cudaStreamBeginCaptureToGraph(e.s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    launch_coarse4_apply<float, float>(e.Yt32.p, e.cr32.p, e.cwt32.p, e.cg, nullptr, 1.0, 0.0, e.s);
+    apply_coarse32(e, e.cr32.p, e.cwt32.p, nullptr);
     launch_gcr_dots_kdev<float>(e.cW32.p, e.cwt32.p, e.cr32.p, e.cctl.p + 1, restart - 1, n, dots, e.wsc, e.s);
     launch_gcr_update_loop(e.cW32.p, e.cZ32.p, e.cwt32.p, e.cctl.p, dots, st, e.cy32.p, e.cr32.p, n, e.s);
     launch_coarse4_control(e.cctl.p, st, tol2_rel, restart, max_iter, h, e.s);
@@ -308,7 +318,7 @@ static long long coarse_solve32_loop(Engine4 &e) {
   long long iters = 0;
   for (;;) {
     MG_CUDA(cudaGraphLaunch(g, e.s));
-    launch_coarse4_apply<float, float>(e.Yt32.p, x, r, e.cg, b, -1.0, 1.0, e.s);  // true residual
+    apply_coarse32(e, x, r, b);  // true residual
     launch_norm2<float>(r, n, st + 2, e.wsc, e.s);
     MG_CUDA(cudaMemcpyAsync(h + 1, st + 1, 3 * sizeof(double), cudaMemcpyDeviceToHost, e.s));
     MG_CUDA(cudaStreamSynchronize(e.s));
@@ -329,7 +339,7 @@ long long coarse_solve32(Engine4 &e) {
   Cx<float> *x = e.cy32.p, *r = e.cr32.p, *Z = e.cZ32.p, *W = e.cW32.p;
   const Cx<float> *b = e.cb32.p;
   auto apply = [&](const Cx<float> *in, Cx<float> *out, const Cx<float> *rhs = nullptr) {
-    launch_coarse4_apply<float, float>(e.Yt32.p, in, out, e.cg, rhs, rhs ? -1.0 : 1.0, rhs ? 1.0 : 0.0, e.s);
+    apply_coarse32(e, in, out, rhs);
     ++e.apps[1];
   };
   double *dots = e.scal.p + kScalCoarse, *state = dots + 204;
@@ -662,6 +672,7 @@ void prepare_coarse(Engine4 &e) {
   launch_convert<float, double>(e.V64.p, e.V32.p, e.V64.n, e.s);
   launch_convert<float, double>(e.Yt64.p, e.Yt32.p, e.Yt64.n, e.s);
   launch_convert<float, double>(e.Minv64.p, e.Minv32.p, e.Minv64.n, e.s);
+  if (e.Yth.p != nullptr) launch_pack_half2(e.Yt64.p, e.Yth.p, e.Yt64.n, e.s);
 }
 
 // Galerkin products in FP32 arithmetic (from the FP32 links and prolongator) for mixed-precision
@@ -805,6 +816,8 @@ Engine4 *engine4_create(const mg_geom *g, const void *U, double m, const mg_para
       e->cy32.alloc(e->nc);
       e->cwt32.alloc(e->nc);
       e->cctl.alloc(2);
+      // the FP16 operator: its rounding (2^-11 of each entry) is far below a loose coarse tolerance
+      if (p->coarsest_tol >= 0.05 && std::getenv("MG_COARSE4_FP32_OPERATOR") == nullptr) e->Yth.alloc(e->Yt64.n);
     }
   }
   e->cb.alloc(e->nc);

@@ -66,6 +66,11 @@ void launch_gcr_update_dev(const Cx<double> *W, Cx<double> *Wk, const Cx<double>
 void launch_gcr_update_dev(const Cx<float> *W, Cx<float> *Wk, const Cx<float> *Z, Cx<float> *Zk, int k,
                            const double *dots, double *state, Cx<float> *x, Cx<float> *r, long long n,
                            cudaStream_t s);
+// coarse apply with the operator in FP16 (32-bit words, real part in the low half, laid out as
+// Y) and FP32 vectors and sums: out = a A in + c b (one vector); the FP16 copy of an FP64 stencil
+void launch_coarse4_apply_h(const unsigned int *Yh, const Cx<float> *in, Cx<float> *out, const Coarse4 &g,
+                            const Cx<float> *b, double a, double c, cudaStream_t s);
+void launch_pack_half2(const Cx<double> *in, unsigned int *out, long long n, cudaStream_t s);
 // graph-replayed coarse GCR on FP32 vectors: the step with k = ctl[1], w = wt and z = r (W_k, Z_k
 // written at W + k n, Z + k n); the kernel that starts a restart cycle (k = 0) and sets the WHILE
 // condition; the kernel that ends an iteration and decides whether the loop goes on (state:

@@ -7,6 +7,7 @@
 // V[b][c][s][d6], c < N = 2 Nv, s < bvol, d6 < 6, is dof 6 chi + d6 (chi = c / Nv)
 // of site s of block b; per column Nh = 6 bvol complex, contiguous, so the block
 // reductions and the prolongation read V with unit stride.
+#include <cuda_fp16.h>
 #include <algorithm>
 
 #include <cstdlib>
@@ -685,6 +686,87 @@ void launch_coarse4_apply(const Cx<RY> *Y, const Cx<RV> *in, Cx<RV> *out, const 
   const size_t smem = (size_t)(9 + qp) * g.N * sizeof(Cx<RY>);
   coarse4_apply_kernel<RY, RV><<<dim3((unsigned int)g.nsites, nvec), qp * g.N, smem, s>>>(
       Y, in, out, g, b, (RV)a, (RV)c, g.nsites * g.N, shift);
+  MG_LAUNCHED();
+}
+
+// The same apply with the operator stored in FP16 (one 32-bit word per complex entry, the real
+// part in the low half; [j][dir][col][row] as Y) and the vectors and sums in FP32: half the
+// bytes of the FP32 operator, for coarse solves whose tolerance is far looser than the FP16
+// rounding (2^-11 of each entry)
+__global__ void coarse4_apply_h_kernel(const unsigned int *__restrict__ Yh, const Cx<float> *__restrict__ in,
+                                       Cx<float> *__restrict__ out, Coarse4 g, const Cx<float> *__restrict__ b,
+                                       float a, float c) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int N = g.N;
+  const int QP = blockDim.x / N;
+  Cx<float> *xs = reinterpret_cast<Cx<float> *>(sm_raw);  // [9][N]
+  Cx<float> *red = xs + 9 * N;                             // [QP][N]
+  const int j = blockIdx.x;
+  int jc[4];
+  {
+    int r = j;
+    for (int mu = 0; mu < 4; ++mu) {
+      jc[mu] = r % g.nb[mu];
+      r /= g.nb[mu];
+    }
+  }
+  for (int e = threadIdx.x; e < 9 * N; e += blockDim.x) {
+    const int dir = e / N, col = e - dir * N;
+    int src = j;
+    if (dir != 0) {
+      const int mu = (dir - 1) >> 1;
+      int cc[4] = {jc[0], jc[1], jc[2], jc[3]};
+      cc[mu] = ((dir - 1) & 1) == 0 ? (cc[mu] + 1) % g.nb[mu] : (cc[mu] + g.nb[mu] - 1) % g.nb[mu];
+      src = cc[0] + g.nb[0] * (cc[1] + g.nb[1] * (cc[2] + g.nb[2] * cc[3]));
+    }
+    xs[e] = in[(long long)src * N + col];
+  }
+  __syncthreads();
+  const int row = threadIdx.x % N, q = threadIdx.x / N;
+  const unsigned int *Yj = Yh + (long long)j * 9 * N * N;
+  float re = 0.f, im = 0.f;
+#pragma unroll 4
+  for (int p = q; p < 9 * N; p += QP) {
+    const unsigned int w = Yj[(long long)p * N + row];
+    const float2 y = __half22float2(*reinterpret_cast<const __half2 *>(&w));
+    const Cx<float> xv = xs[p];
+    re += y.x * xv.re - y.y * xv.im;
+    im += y.x * xv.im + y.y * xv.re;
+  }
+  red[q * N + row] = mk(re, im);
+  __syncthreads();
+  if (q == 0) {
+    float sre = 0.f, sim = 0.f;
+    for (int i = 0; i < QP; ++i) {
+      sre += red[i * N + row].re;
+      sim += red[i * N + row].im;
+    }
+    Cx<float> o = mk(a * sre, a * sim);
+    if (b != nullptr) {
+      const Cx<float> bb = b[(long long)j * N + row];
+      o = mk(o.re + c * bb.re, o.im + c * bb.im);
+    }
+    out[(long long)j * N + row] = o;
+  }
+}
+
+__global__ void pack_half2_kernel(const Cx<double> *__restrict__ in, unsigned int *__restrict__ out, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const __half2 h = __floats2half2_rn((float)in[i].re, (float)in[i].im);
+  out[i] = *reinterpret_cast<const unsigned int *>(&h);
+}
+
+void launch_pack_half2(const Cx<double> *in, unsigned int *out, long long n, cudaStream_t s) {
+  pack_half2_kernel<<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+  MG_LAUNCHED();
+}
+
+void launch_coarse4_apply_h(const unsigned int *Yh, const Cx<float> *in, Cx<float> *out, const Coarse4 &g,
+                            const Cx<float> *b, double a, double c, cudaStream_t s) {
+  const int qp = std::max(1, std::min(8, 512 / g.N));
+  const size_t smem = (size_t)(9 + qp) * g.N * sizeof(Cx<float>);
+  coarse4_apply_h_kernel<<<(unsigned int)g.nsites, qp * g.N, smem, s>>>(Yh, in, out, g, b, (float)a, (float)c);
   MG_LAUNCHED();
 }
 

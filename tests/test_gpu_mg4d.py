@@ -341,6 +341,37 @@ def test_coarse_gcr_fp32_vectors_meets_tolerance(mode, dims, block, nv, restart,
     ctx.close()
 
 
+@pytest.mark.parametrize("fp32_operator", [False, True])
+def test_coarse_gcr_fp16_operator_meets_loose_tolerance(fp32_operator, monkeypatch):
+    # with a loose coarse tolerance (>= 0.05) the single-vector coarse GCR applies A M from an FP16
+    # copy (2^-11 of each entry; MG_COARSE4_FP32_OPERATOR keeps FP32): the solution meets the
+    # tolerance against the oracle's FP64 coarse operator up to that rounding, and differs from the
+    # FP32-operator solution by about the same
+    import torch
+    import paper_0707_4018_gb300 as mg
+    from oracle import solvers as osolvers
+    if fp32_operator:
+        monkeypatch.setenv("MG_COARSE4_FP32_OPERATOR", "1")
+    dims, block, nv = (8, 8, 8, 8), (4, 4, 4, 4), 6
+    U = inputs.su3_links(dims, seed=29)
+    m = 0.02
+    tol = 0.1
+    ctx = mg.Context.setup(to_dev(U), m, dims, _params(block, nv, 1, n_pass=1, nu_setup=20, coarsest_tol=tol,
+                                                       coarsest_restart=32, coarsest_max_iter=2000))
+    vecs = to_host(ctx.null_vectors(0))
+    hier = _oracle_hier(U, m, dims, block, nv)
+    hier.build_level(0, list(vecs))
+    A = osolvers.stencil_matrix(hier.ops[1])
+    n, k = ctx.level_size(1)
+    for seed in (3, 4):
+        b = inputs.gaussian_spinor(n, k, 60 + seed, 0)
+        x = torch.empty((n, k), dtype=torch.complex128, device="cuda")
+        it, _ = ctx.coarsest_solve(to_dev(b), x)
+        res = np.linalg.norm(b.reshape(-1) - A @ to_host(x).reshape(-1)) / np.linalg.norm(b)
+        assert 0 < it < 2000 and res <= 1.05 * tol, (it, res)
+    ctx.close()
+
+
 @pytest.mark.parametrize("host_loop", [False, True])
 def test_coarse_gcr_fp32_iteration_limit_and_zero_rhs(host_loop, monkeypatch):
     # the coarse GCR stops at coarsest_max_iter across restart cycles (4 + 2 iterations with
