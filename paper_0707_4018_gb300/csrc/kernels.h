@@ -55,6 +55,12 @@ void launch_dslash(const Cx<R> *U, const Cx<R> *in, Cx<R> *out, Geo2 g, double d
 template <typename R>
 void launch_dslash4(const Cx<R> *U, const Cx<R> *in, Cx<R> *out, Geo4 g, double diag, const Cx<R> *b, double a,
                     double c, cudaStream_t s, int nvec = 1, const double *shift = nullptr);
+// Ar = D r (FP32, nvec vectors) with each vector's MR sums (Re <Ar, r>, Im <Ar, r>, |Ar|^2) in
+// sums[3 v], from the tiled kernel's epilogue (partials: nvec x nsites / 64 x 3 doubles, tickets:
+// nvec counters at zero); returns false, launching nothing, where that kernel does not apply
+bool launch_dslash4_mr(const Cx<float> *U, const Cx<float> *r, Cx<float> *Ar, Geo4 g, double diag, int nvec,
+                       double *sums, double *partials, long long partials_cap, unsigned int *tickets,
+                       cudaStream_t s);
 
 // ---- coarse stencil operator, N x N blocks, internal layout Y[j][dir][col][row] ----
 // out = a * A in + c * b; with `shift`, vector v sees A + shift[v] * identity

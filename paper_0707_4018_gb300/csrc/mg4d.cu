@@ -567,8 +567,16 @@ constexpr int kMrBlocks = 152 * 4;  // grid cap of the batched MR reductions
 template <typename R>
 void mr_fine(Engine4 &e, Cx<R> *x, Cx<R> *r, Cx<R> *Ar, int nu, int nvec = 1) {
   for (int it = 0; it < nu; ++it) {
-    launch_dslash4<R>(U_of<R>(e), r, Ar, e.fg, diag4(e), nullptr, 1.0, 0.0, e.s, nvec);
     e.apps[0] += nvec;
+    if constexpr (sizeof(R) == 4) {
+      // the tiled FP32 apply forms the MR sums in its epilogue (no second pass over r and A r)
+      if (launch_dslash4_mr(U_of<R>(e), r, Ar, e.fg, diag4(e), nvec, e.bsc.p, e.bpart.p, e.bpart.n, e.btickets.p,
+                            e.s)) {
+        launch_mr_update_batch<R>(e.bsc.p, e.p.omega, x, r, Ar, e.nf, nvec, e.s);
+        continue;
+      }
+    }
+    launch_dslash4<R>(U_of<R>(e), r, Ar, e.fg, diag4(e), nullptr, 1.0, 0.0, e.s, nvec);
     launch_dot_norm_batch<R>(Ar, r, e.nf, nvec, e.bsc.p, e.bpart.p, e.btickets.p, kMrBlocks, e.s);
     launch_mr_update_batch<R>(e.bsc.p, e.p.omega, x, r, Ar, e.nf, nvec, e.s);
   }
@@ -838,7 +846,9 @@ Engine4 *engine4_create(const mg_geom *g, const void *U, double m, const mg_para
   e->tickets.alloc((size_t)e->ws.tickets);
   e->scal.alloc(kScalCount);
   const int nbat = std::max(e->bg.Nv, std::max(1, p->max_rhs));  // vectors of a batched MR
-  e->bpart.alloc((size_t)nbat * kMrBlocks * 3 + 16);
+  // per-block partials of the batched MR sums: the reduction kernel's grid, or the tiled Wilson
+  // apply's tiles when it forms the sums itself (64 sites per tile)
+  e->bpart.alloc((size_t)nbat * std::max<long long>(kMrBlocks, e->fg.nsites / 64) * 3 + 16);
   e->bsc.alloc((size_t)nbat * 3);
   e->btickets.alloc((size_t)nbat);
   if (e->f32) {

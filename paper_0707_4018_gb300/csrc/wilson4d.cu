@@ -359,13 +359,23 @@ __device__ __forceinline__ void tile_hops(const Cx<float> *__restrict__ U, const
   __syncthreads();
 }
 
-template <class T, int MINB, bool SHIFT>
+// DOTS: also the sums of an MR step on each vector (blockIdx.y), (<out, in>, |out|^2) as
+// (re, im, norm), formed from the values the kernel holds anyway (its input and output at the
+// site): per-thread and per-block in FP32, FP64 partials and final sum, into mr.out[3 v]
+struct MrSums {
+  double *partials;  // [vector][tile][3]
+  double *out;       // [vector][3]
+  unsigned int *tickets;
+};
+
+template <class T, int MINB, bool SHIFT, bool DOTS = false>
 __global__ void __launch_bounds__(T::sites, MINB) dslash4_tile_kernel(const Cx<float> *__restrict__ U,
                                                                       const Cx<float> *__restrict__ in,
                                                                       Cx<float> *__restrict__ out, Geo4 g,
                                                                       float diag, const Cx<float> *__restrict__ b,
                                                                       float a, float c, long long ldv,
-                                                                      const double *__restrict__ shift) {
+                                                                      const double *__restrict__ shift,
+                                                                      MrSums mr = MrSums{}) {
   constexpr int A0 = T::template n<0>(), A1 = T::template n<1>(), A2 = T::template n<2>();
   __shared__ float2 sF[6][T::sites], sM[6][T::sites];
   if (SHIFT) diag += (float)shift[blockIdx.y];
@@ -393,9 +403,17 @@ __global__ void __launch_bounds__(T::sites, MINB) dslash4_tile_kernel(const Cx<f
   tile_hops<T, 1>(U, in, p, x, t, l1, c1, g.L[1], s1, sF, sM, acc);
   tile_hops<T, 2>(U, in, p, x, t, l2, c2, g.L[2], s2, sF, sM, acc);
   tile_hops<T, 3>(U, in, p, x, t, l3, c3, g.L[3], s3, sF, sM, acc);
+  float sums[3] = {0.f, 0.f, 0.f};  // <out, in> and |out|^2 at this site (DOTS)
 #pragma unroll
-  for (int i = 0; i < 12; ++i)
-    p[i] = mk(a * (diag * p[i].re - 0.5f * acc[i].re), a * (diag * p[i].im - 0.5f * acc[i].im));
+  for (int i = 0; i < 12; ++i) {
+    const Cx<float> o = mk(a * (diag * p[i].re - 0.5f * acc[i].re), a * (diag * p[i].im - 0.5f * acc[i].im));
+    if (DOTS) {
+      sums[0] += o.re * p[i].re + o.im * p[i].im;
+      sums[1] += o.re * p[i].im - o.im * p[i].re;
+      sums[2] += o.re * o.re + o.im * o.im;
+    }
+    p[i] = o;
+  }
   if (b != nullptr) {
     Cx<float> q[12];
     load_spinor32(b, x, q);
@@ -405,6 +423,11 @@ __global__ void __launch_bounds__(T::sites, MINB) dslash4_tile_kernel(const Cx<f
   float4 *o = reinterpret_cast<float4 *>(out) + (long long)x * 6;
 #pragma unroll
   for (int i = 0; i < 6; ++i) o[i] = make_float4(p[2 * i].re, p[2 * i].im, p[2 * i + 1].re, p[2 * i + 1].im);
+  if (DOTS) {
+    __shared__ float sh[32 * 3];
+    grid_finish_t<3, float>(sums, mr.partials + (long long)blockIdx.y * gridDim.x * 3, mr.out + 3 * blockIdx.y,
+                            mr.tickets + blockIdx.y, sh);
+  }
 }
 
 // tile shapes of the tiled kernel; MG_DSLASH4_TILE picks one (default 7, the fastest at 32^3 x 64:
@@ -483,6 +506,24 @@ static bool try_tile4(const Cx<float> *U, const Cx<float> *in, Cx<float> *out, G
     return true;
   }
   return false;
+}
+
+// Ar = D r for nvec FP32 vectors together with the MR sums (<Ar, r>, |Ar|^2) of each, by the
+// default tiled kernel; false (nothing launched) when that kernel does not take this lattice
+// or another variant is selected
+bool launch_dslash4_mr(const Cx<float> *U, const Cx<float> *r, Cx<float> *Ar, Geo4 g, double diag, int nvec,
+                       double *sums, double *partials, long long partials_cap, unsigned int *tickets,
+                       cudaStream_t s) {
+  if (std::getenv("MG_DSLASH4_GATHER") != nullptr || std::getenv("MG_DSLASH4_TILE") != nullptr) return false;
+  if (!tile_divides<TileF>(g)) return false;
+  const long long tiles = g.nsites / TileF::sites;
+  if (tiles * 3 * nvec > partials_cap) return false;
+  const dim3 grid((unsigned int)tiles, nvec);
+  dslash4_tile_kernel<TileF, 8, false, true><<<grid, TileF::sites, 0, s>>>(U, r, Ar, g, (float)diag, nullptr, 1.f,
+                                                                           0.f, 12 * g.nsites, nullptr,
+                                                                           MrSums{partials, sums, tickets});
+  MG_LAUNCHED();
+  return true;
 }
 
 template <typename R>
