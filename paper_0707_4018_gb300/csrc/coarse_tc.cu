@@ -195,6 +195,97 @@ __device__ __forceinline__ void split_bf16x2(float a, float b, unsigned int &hi,
   lo = pack_bf16x2(a - __uint_as_float(hi << 16), b - __uint_as_float(hi & 0xffff0000u));
 }
 
+// out_n = A_c in_n with one warp per (site, row tile, group of 8 vectors): the form taken for
+// SPLIT 0 and 1, where it beats the per-site form below (more CTAs in flight; 19.6 against
+// 25.9 us for SPLIT 0 at 512 sites x 12 vectors). The operands as in the per-site form.
+template <int SPLIT>
+__global__ void __launch_bounds__(256) coarse4_apply_tc_warp_kernel(const uint4 *__restrict__ Ypk,
+                                                               const uint4 *__restrict__ Ypklo,
+                                                               const Cx<float> *__restrict__ in,
+                                                               Cx<float> *__restrict__ out, int nb0, int nb1, int nb2,
+                                                               int nb3, long long ldv, int nvec) {
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const long long nsites = (long long)nb0 * nb1 * nb2 * nb3;
+  const int tiles = (nvec + 7) >> 3;
+  if (w >= nsites * 3 * tiles) return;  // whole warps
+  const long long j = w / (3 * tiles);
+  const int rem = (int)(w - j * 3 * tiles), tm = rem / tiles, n0 = (rem - tm * tiles) * 8;
+  const int nb[4] = {nb0, nb1, nb2, nb3};
+  int jc[4];
+  {
+    long long q = j;
+    for (int mu = 0; mu < 4; ++mu) {
+      jc[mu] = (int)(q % nb[mu]);
+      q /= nb[mu];
+    }
+  }
+  const int nv = n0 + g;  // this lane's vector in the B fragments
+  const bool bcol = nv < nvec;
+  float cre[4] = {0.f, 0.f, 0.f, 0.f}, cim[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int dir = 0; dir < 9; ++dir) {
+    long long src = j;
+    if (dir != 0) {
+      const int mu = (dir - 1) >> 1;
+      int cc[4] = {jc[0], jc[1], jc[2], jc[3]};
+      cc[mu] = ((dir - 1) & 1) == 0 ? (cc[mu] + 1) % nb[mu] : (cc[mu] + nb[mu] - 1) % nb[mu];
+      src = cc[0] + (long long)nb[0] * (cc[1] + (long long)nb[1] * (cc[2] + (long long)nb[2] * cc[3]));
+    }
+    const Cx<float> *xs = in + nv * ldv + src * 48;
+    const uint4 *Yd = Ypk + (j * 9 + dir) * 2 * 9 * 32;
+#pragma unroll
+    for (int tk = 0; tk < 3; ++tk) {
+      float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;  // x[16 tk + 2t .. +1], x[16 tk + 2t + 8 .. +9]
+      if (bcol) {
+        lo = *reinterpret_cast<const float4 *>(xs + 16 * tk + 2 * t);
+        hi = *reinterpret_cast<const float4 *>(xs + 16 * tk + 2 * t + 8);
+      }
+      unsigned int r0, r1, i0, i1, r0l = 0u, r1l = 0u, i0l = 0u, i1l = 0u;  // xr, xi fragments (hi, lo)
+      if (SPLIT == 0) {
+        r0 = pack_bf16x2(lo.x, lo.z);
+        r1 = pack_bf16x2(hi.x, hi.z);
+        i0 = pack_bf16x2(lo.y, lo.w);
+        i1 = pack_bf16x2(hi.y, hi.w);
+      } else {
+        split_bf16x2(lo.x, lo.z, r0, r0l);
+        split_bf16x2(hi.x, hi.z, r1, r1l);
+        split_bf16x2(lo.y, lo.w, i0, i0l);
+        split_bf16x2(hi.y, hi.w, i1, i1l);
+      }
+      const int fi = (tm * 3 + tk) * 32 + lane;
+      const uint4 fa = Yd[fi], fb = Yd[9 * 32 + fi];
+      const unsigned int s = 0x80008000u;
+      mma_bf16_16816(cre, fa.x, fa.y, fa.z, fa.w, r0, r1);                  // + A xr
+      mma_bf16_16816(cre, fb.x ^ s, fb.y ^ s, fb.z ^ s, fb.w ^ s, i0, i1);  // - B xi
+      mma_bf16_16816(cim, fb.x, fb.y, fb.z, fb.w, r0, r1);                  // + B xr
+      mma_bf16_16816(cim, fa.x, fa.y, fa.z, fa.w, i0, i1);                  // + A xi
+      if (SPLIT >= 1) {
+        mma_bf16_16816(cre, fa.x, fa.y, fa.z, fa.w, r0l, r1l);
+        mma_bf16_16816(cre, fb.x ^ s, fb.y ^ s, fb.z ^ s, fb.w ^ s, i0l, i1l);
+        mma_bf16_16816(cim, fb.x, fb.y, fb.z, fb.w, r0l, r1l);
+        mma_bf16_16816(cim, fa.x, fa.y, fa.z, fa.w, i0l, i1l);
+      }
+      if (SPLIT == 2) {
+        const uint4 *Yl = Ypklo + (j * 9 + dir) * 2 * 9 * 32;
+        const uint4 ga = Yl[fi], gb = Yl[9 * 32 + fi];
+        mma_bf16_16816(cre, ga.x, ga.y, ga.z, ga.w, r0, r1);
+        mma_bf16_16816(cre, gb.x ^ s, gb.y ^ s, gb.z ^ s, gb.w ^ s, i0, i1);
+        mma_bf16_16816(cim, gb.x, gb.y, gb.z, gb.w, r0, r1);
+        mma_bf16_16816(cim, ga.x, ga.y, ga.z, ga.w, i0, i1);
+      }
+    }
+  }
+  // C fragment: rows g, g + 8 of the tile (complex rows 16 tm + g, + 8), vectors n0 + 2t, + 1
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int n = n0 + 2 * t + h;
+    if (n >= nvec) continue;
+    Cx<float> *o = out + n * ldv + j * 48 + 16 * tm;
+    o[g] = mk(cre[h], cim[h]);
+    o[g + 8] = mk(cre[2 + h], cim[2 + h]);
+  }
+}
+
 // out_n = A_c in_n for nvec vectors (stride ldv = nsites * 48). A CTA takes one site and up to
 // 16 vectors (two 8-vector groups, blockIdx.y selects the pair); its 9 warps are (row tile tm,
 // direction group dg): warp (tm, dg) applies the directions 3 dg .. 3 dg + 2 of row tile tm to
@@ -335,17 +426,20 @@ void launch_coarse4_apply_tc(const uint4 *Ypk, const Cx<float> *in, Cx<float> *o
   if (split < 0 || split > 2 || (split == 2 && Ypklo == nullptr))
     fail(MG_ERR_INVALID_ARG, "tensor-core apply: split must be 0, 1 or 2 (2 needs the low BF16 part)");
   const long long nsites = (long long)nb[0] * nb[1] * nb[2] * nb[3];
-  const dim3 grid((unsigned int)nsites, (unsigned int)((nvec + 15) / 16));
-  const int threads = 32 * kTcWarps;
-  if (split == 0)
-    coarse4_apply_tc_kernel<0><<<grid, threads, 0, s>>>(Ypk, Ypklo, in, out, nb[0], nb[1], nb[2], nb[3], nsites * 48,
-                                                        nvec);
-  else if (split == 1)
-    coarse4_apply_tc_kernel<1><<<grid, threads, 0, s>>>(Ypk, Ypklo, in, out, nb[0], nb[1], nb[2], nb[3], nsites * 48,
-                                                        nvec);
-  else
-    coarse4_apply_tc_kernel<2><<<grid, threads, 0, s>>>(Ypk, Ypklo, in, out, nb[0], nb[1], nb[2], nb[3], nsites * 48,
-                                                        nvec);
+  if (split < 2) {  // a warp per (site, row tile, 8 vectors)
+    const long long warps = nsites * 3 * ((nvec + 7) / 8);
+    const unsigned int grid = grid_for(warps * 32, 256);
+    if (split == 0)
+      coarse4_apply_tc_warp_kernel<0><<<grid, 256, 0, s>>>(Ypk, Ypklo, in, out, nb[0], nb[1], nb[2], nb[3],
+                                                           nsites * 48, nvec);
+    else
+      coarse4_apply_tc_warp_kernel<1><<<grid, 256, 0, s>>>(Ypk, Ypklo, in, out, nb[0], nb[1], nb[2], nb[3],
+                                                           nsites * 48, nvec);
+  } else {  // a CTA per (site, 16 vectors)
+    const dim3 grid((unsigned int)nsites, (unsigned int)((nvec + 15) / 16));
+    coarse4_apply_tc_kernel<2><<<grid, 32 * kTcWarps, 0, s>>>(Ypk, Ypklo, in, out, nb[0], nb[1], nb[2], nb[3],
+                                                              nsites * 48, nvec);
+  }
   MG_LAUNCHED();
 }
 
