@@ -108,6 +108,28 @@ def test_first_pass_vectors_match_oracle():
     ctx.close()
 
 
+def test_fp32_first_pass_vectors_close_to_oracle():
+    # mixed precision on a lattice the tiled FP32 Wilson apply takes (x extent a multiple of 8):
+    # the setup relaxation's MR sums come from that kernel's epilogue; the relaxed vectors follow
+    # the oracle's FP64 MR iterations from the same Philox draws to FP32 accuracy, and the
+    # Galerkin operator built from them matches the oracle's
+    import paper_0707_4018_gb300 as mg
+    dims, block, nv = (8, 8, 8, 8), (4, 4, 4, 4), 6
+    U = inputs.su3_links(dims, seed=22)
+    m = 0.05
+    p = _params(block, nv, 1, n_pass=1, nu_setup=12)
+    ctx = mg.Context.setup(to_dev(U), m, dims, p)
+    got = to_host(ctx.null_vectors(0))
+    hier = _oracle_hier(U, m, dims, block, nv, seed=int(p.seed), n_pass=1, nu_setup=12)
+    want = [setup.relax_null(hier, 0, v) for v in setup.initial_vectors(hier, 0)]
+    for k in range(nv):
+        assert rel_err(got[k], want[k]) < 1e-4, k
+    hier.build_level(0, want)
+    Y = to_host(ctx.coarse_op(1))
+    assert np.abs(Y - hier.ops[1].Y).max() < 1e-3 * np.abs(hier.ops[1].Y).max()
+    ctx.close()
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_vcycle_matches_oracle(precision):
     import torch
