@@ -95,6 +95,11 @@ def test_autotuner_picks_a_tile_shape_and_keeps_results():
     key = "coarse_apply_tc/8x8/nvec11"
     assert key in rep and 0 <= rep[key] < 6, rep
     assert torch.equal(y1, y2)
+    # the split-operand forms are built for the 4d level only; out-of-range modes are rejected
+    for mode, code in ((2, 6), (3, 6), (4, 1), (-1, 1)):
+        with pytest.raises(mg.MGError) as e:
+            ctx.coarse_apply_mrhs(1, x, y2, mode)
+        assert e.value.code == code, (mode, e.value.code)
 
 
 @pytest.mark.parametrize("nrhs", [1, 8, 12, 16])
