@@ -217,6 +217,32 @@ def test_su3_workload_16x16x16x32_true_residual():
     ctx.close()
 
 
+def test_su3_workload_batched_true_residual():
+    # the 4d workload's batched form at full size, with the bench's parameters (outer restart 32): 4
+    # sources in lockstep, the coarse GCR on FP32 vectors replayed by a graph, the coarse operator
+    # on tensor cores with split BF16 operands; the oracle recomputes every FP64 true residual
+    import torch
+    import paper_0707_4018_gb300 as mg
+    dims = (16, 16, 16, 32)
+    lat = Lattice(dims)
+    U = inputs.su3_links(dims, seed=inputs.workload_seed(3, 16, 0.0))
+    row = mcrit_table().get("w3_su3_16x16x16x32")
+    m = row["m_crit"] + 0.005 if row and row["links_digest"] == inputs.field_digest(U) else 0.0
+    nb = 4
+    ctx = mg.Context.setup(to_dev(U), m, dims, _params((4, 4, 4, 4), 24, 1, n_pass=1, nu_setup=400,
+                                                       coarsest_tol=0.3, coarsest_restart=64,
+                                                       coarsest_max_iter=128, gcr_restart=32, max_iter=300,
+                                                       max_rhs=nb))
+    chi = np.stack([inputs.gaussian_spinor(lat.volume, 12, 15, k) for k in range(nb)])
+    psi = torch.empty((nb, lat.volume, 12), dtype=torch.complex128, device="cuda")
+    st = ctx.solve_batch(to_dev(chi), psi, 1e-10)
+    got = to_host(psi)
+    for k in range(nb):
+        res = np.linalg.norm(chi[k] - wilson.apply_D(U, got[k].reshape(-1, 4, 3), m, lat).reshape(chi[k].shape))
+        assert st[k]["converged"] and res <= 1e-10 * np.linalg.norm(chi[k]) * 1.01, (k, st[k])
+    ctx.close()
+
+
 def test_update_mass_rebuilds_galerkin_like_oracle():
     import paper_0707_4018_gb300 as mg
     dims, block, nv = (4, 4, 4, 8), (2, 2, 2, 2), 4
